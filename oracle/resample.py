@@ -1,0 +1,166 @@
+"""Resampling: fixed-point CDF and the four ancestor-selection schemes.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Sec. 2.1 (eq:resample and the paragraph after it): resampling draws integer
+replication counts R_i >= 0 with sum N such that the resampled system has the
+same expectation; the multinomial distribution with the normalised weights is
+one such law, and Douc et al. (2005) list the commonly used alternatives
+(stratified, systematic, residual).  Sec. 4.1.2 fixes the output convention:
+copy_from[k] is the parent of new particle k.
+
+Readings (the paper is silent on the arithmetic; the same readings bind the
+CUDA path):
+* Fixed-point weights.  With m = max lw and F = 61 - ceil(log2 N) fraction
+  bits, q_i = floor(exp(lw_i - m) * 2^F) and Q_i = q_0 + ... + q_i are exact
+  integers (Q_N <= N 2^F <= 2^61).  Resampling is exact, order-independent
+  and deterministic in this representation; a particle whose weight is below
+  2^-F of the largest one gets weight zero.
+* Targets are rationals P_k / D with D = N 2^25 and the uniform
+  u = (2j + 1) / 2^25 of ``oracle.philox``:
+    systematic  P_k = 2^25 k + 2j + 1, one j per iteration;
+    stratified  P_k = 2^25 k + 2j_k + 1, j_k independent;
+    multinomial P_k = N (2 j_(k) + 1), j_(k) the k-th smallest of N iid j's
+                (sorting the iid uniforms does not change the multiset of
+                ancestors, and the ancestor multiset defines the scheme).
+* Selection: a_k = min{ i : Q_i D > Q_N P_k } (an upper bound).  Particles
+  with q_i = 0 are never selected.  The ancestors come out sorted.
+* Residual (multinomial residual step): d_i = floor(N q_i / Q_N) copies,
+  rem_i = N q_i - d_i Q_N, R = N - sum d_i residual draws; the residual
+  weights are r_i = rem_i >> s with s = max(0, bitlength(R Q_N) - 62)
+  (sum rem_i = R Q_N exactly, so the residual CDF fits in 62 bits and is
+  nonzero whenever R > 0); the R residual ancestors come from multinomial
+  selection on the r-CDF with R sorted iid uniforms; the final ancestors are
+  the sorted expansion of the counts d_i + (residual draws of i).
+
+Parity pins (tests/test_oracle_resample.py): sum of counts = N; exact
+unbiasedness E[o_i] = N q_i / Q_N by enumeration of all 2^24 systematic
+uniforms for tiny N; Monte Carlo unbiasedness (5 sigma) for stratified,
+multinomial and residual; systematic counts within {floor, ceil} of N W_i;
+residual counts >= floor(N W_i); sorted output; zero-weight particles never
+selected.
+"""
+import math
+
+import numpy as np
+
+from . import philox
+
+
+def frac_bits(n):
+    """F = 61 - ceil(log2 N)."""
+    return 61 - max(0, (int(n) - 1).bit_length())
+
+
+def quantise(lw):
+    """q_i = floor(exp(lw_i - m) 2^F) as Python ints (object array)."""
+    lw = np.asarray(lw, dtype=np.float64)
+    n = lw.shape[0]
+    m = float(np.max(lw))
+    if not math.isfinite(m):
+        raise FloatingPointError("all log-weights are -inf or NaN")
+    scale = 2.0 ** frac_bits(n)
+    e = np.exp(lw - m)
+    return np.array([int(math.floor(v * scale)) for v in e], dtype=object)
+
+
+def cdf(q):
+    """Inclusive prefix sums Q_i of the fixed-point weights (exact)."""
+    out = np.empty(len(q), dtype=object)
+    acc = 0
+    for i, v in enumerate(q):
+        acc += int(v)
+        out[i] = acc
+    return out
+
+
+def select(Q, P, D):
+    """a_k = min{i : Q_i D > Q_N P_k}, for non-decreasing numerators P."""
+    Q = [int(v) for v in Q]
+    QN = Q[-1]
+    if QN <= 0:
+        raise FloatingPointError("total fixed-point weight is zero")
+    # Q_i D > Q_N P_k  <=>  Q_i > floor(Q_N P_k / D)   (Q_i integer)
+    thr = [(QN * int(p)) // int(D) for p in P]
+    import bisect
+    return np.array([bisect.bisect_right(Q, t) for t in thr], dtype=np.int64)
+
+
+def systematic_targets(n, j):
+    return [(k << 25) + 2 * int(j) + 1 for k in range(n)], n << 25
+
+
+def stratified_targets(n, js):
+    return [(k << 25) + 2 * int(js[k]) + 1 for k in range(n)], n << 25
+
+
+def multinomial_targets(n, js):
+    s = sorted(int(v) for v in js)
+    return [n * (2 * v + 1) for v in s], n << 25
+
+
+def systematic(Q, seed, t, stream=0):
+    n = len(Q)
+    P, D = systematic_targets(n, philox.systematic_u24(seed, t, stream))
+    return select(Q, P, D)
+
+
+def stratified(Q, seed, t, stream=0):
+    n = len(Q)
+    P, D = stratified_targets(n, philox.resample_u24(seed, t, n, stream))
+    return select(Q, P, D)
+
+
+def multinomial(Q, seed, t, stream=0):
+    n = len(Q)
+    P, D = multinomial_targets(n, philox.resample_u24(seed, t, n, stream))
+    return select(Q, P, D)
+
+
+def residual_parts(q):
+    """Deterministic copies d_i, residual draw count R, residual weights r_i
+    and the shift s (see the module docstring)."""
+    q = [int(v) for v in q]
+    n = len(q)
+    QN = sum(q)
+    d = [(n * v) // QN for v in q]
+    rem = [n * v - di * QN for v, di in zip(q, d)]
+    R = n - sum(d)
+    s = max(0, (R * QN).bit_length() - 62)
+    r = [v >> s for v in rem]
+    return d, R, r, s
+
+
+def residual(q, seed, t, stream=0):
+    """Residual resampling from the fixed-point weights q (not their CDF:
+    the deterministic part needs the individual q_i)."""
+    n = len(q)
+    d, R, r, _ = residual_parts(q)
+    counts = np.array(d, dtype=np.int64)
+    if R > 0:
+        RQ = cdf(r)
+        P, D = multinomial_targets(R, philox.resample_u24(seed, t, R, stream))
+        # multinomial_targets scales by its own count R: P = R (2 j + 1), D = R 2^25
+        extra = select(RQ, P, D)
+        counts += np.bincount(extra, minlength=n)
+    return expand(counts)
+
+
+def expand(counts):
+    """Sorted ancestor array in which i appears counts[i] times."""
+    return np.repeat(np.arange(len(counts), dtype=np.int64), np.asarray(counts, dtype=np.int64))
+
+
+def offspring(a, n):
+    """Replication counts R_i of the paper (Sec. 2.1) from ancestors."""
+    return np.bincount(np.asarray(a, dtype=np.int64), minlength=n)
+
+
+def resample(scheme, lw, seed, t, stream=0):
+    """Ancestors for the named scheme from raw log-weights."""
+    q = quantise(lw)
+    if scheme == "residual":
+        return residual(q, seed, t, stream)
+    Q = cdf(q)
+    return {"systematic": systematic, "stratified": stratified,
+            "multinomial": multinomial}[scheme](Q, seed, t, stream)
