@@ -1,0 +1,326 @@
+"""Benchmark of the SMC hot path: particle-updates/s per SMC iteration.
+
+Workload (one "step" = one full SMC iteration over all particles): the
+almost-constant-velocity particle filter of Sec. 5.1 at N = 2^20 particles,
+FP32 per particle with FP64 normaliser and evidence, 1000 synthetic
+observations (seed 0), ESS threshold 0.5 N; move + weight + normaliser + ESS
+test + (when due) fixed-point CDF and ancestor selection; the gather runs in
+the next move.  The headline scheme is systematic; the other three schemes
+are reported under "per_scheme".
+
+Timing: W untimed warm-up iterations, then K timed iterations.  Before each
+timed iteration a 512 MB buffer is written (more than the 126 MB L2), outside
+the timed events; every iteration is bracketed by CUDA events on the stream
+the kernels run on.  Under torchrun each rank runs an independent replica
+(another seed); the max over ranks of the timed region is used.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (a few iterations at the full N) on the host cores.
+"""
+import argparse
+import ctypes
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_FULL = 1 << 20
+T_OBS = 1000
+METRIC = "particle-updates/s per SMC iteration at N=2^20"
+WORKLOAD = "cv-pf N=2^20 T=1000 fp32 (fp64 normaliser) ESS<0.5N"
+# algorithmic HBM bytes per particle of the fused move/weight kernel:
+# state read 16 B (gathered after a resampling step) + state write 16 B +
+# log-weight write 4 B + log-weight read 4 B (or the ancestor index read 4 B
+# after a resampling step)
+PF_BYTES_PER_PARTICLE = 40
+SCAN_BYTES_PER_PARTICLE = 12     # log-weight read 4 B + CDF write 8 B
+SELECT_BYTES_PER_PARTICLE = 12   # CDF read 8 B + ancestor write 4 B
+RESAMPLE_KERNELS = {"systematic": 2, "stratified": 2, "multinomial": 6, "residual": 10}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        try:
+            for line in open(self.path):
+                v = [x.strip() for x in line.split(",")]
+                if len(v) >= 6 and v[0].isdigit():
+                    rows.append(v)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = sorted(int(r[0]) for r in rows)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[2:6]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": int(rows[0][1]), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def run_ours(args):
+    import torch
+    from paper_1306_5583_b300 import smc, workloads
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    p = dict(workloads.CV_DEFAULT)
+    _, y = workloads.cv_data(T_OBS, seed=0, **p)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    n = args.n
+
+    def make(scheme):
+        cfg = smc.make_config(model="cv", n=n, precision=32, scheme=scheme, threshold=0.5, seed=1 + rank,
+                              max_data=T_OBS, max_records=T_OBS + 1, cv=p)
+        s = smc.Sampler(cfg, stream=stream, device=dev)
+        s.set_data(y)
+        return s
+
+    def timed(scheme, K, W):
+        s = make(scheme)
+        with torch.cuda.stream(stream):
+            s.initialize()
+            for _ in range(W):
+                s.move()
+                s.resample()
+            stream.synchronize()
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+            if ws > 1:
+                import torch.distributed as dist
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            t_wall = time.perf_counter()
+            for k in range(K):
+                if s.iteration() + 1 >= T_OBS:
+                    s.initialize()
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                s.move()
+                ev[k][1].record(stream)
+                s.resample()
+                ev[k][2].record(stream)
+            torch.cuda.synchronize(dev)
+            t_wall = time.perf_counter() - t_wall
+        step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
+        move_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+        res_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+        hist = s.history(min(K + W + 1, T_OBS))
+        frac_res = float(np.mean([r["resampled"] for r in hist[-K:]]))
+        s.close()
+        return dict(step_ms=step_ms, move_ms=move_ms, res_ms=res_ms, wall_s=t_wall, resample_frac=frac_res)
+
+    headline = args.scheme
+    with Clocks(local) as clk:
+        main = timed(headline, args.steps, args.warmup)
+    clocks = clk.summary()
+    per_scheme = {}
+    for sc in ("systematic", "stratified", "multinomial", "residual"):
+        r = main if sc == headline else timed(sc, args.steps, args.warmup)
+        per_scheme[sc] = dict(
+            particle_updates_per_s=n / (np.mean(r["step_ms"]) * 1e-3),
+            ms_per_step=float(np.mean(r["step_ms"])),
+            move_us=float(np.mean(r["move_ms"]) * 1e3),
+            resample_us_when_due=float(np.mean([m for m, fl in zip(r["res_ms"], [1] * len(r["res_ms"]))]) * 1e3),
+            resample_fraction=r["resample_frac"])
+    total_ms = float(np.sum(main["step_ms"]))
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * n / (ms_per_step * 1e-3)
+
+    # dominant kernel: the fused move/weight kernel (its own events)
+    move_us = float(np.mean(main["move_ms"]) * 1e3)
+    peak, peak_kind = measured_peaks()
+    achieved = PF_BYTES_PER_PARTICLE * n / (move_us * 1e-6) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": "pf_iterate_kernel<float>",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
+                "fallback 6.4 TB/s"}
+
+    # end to end through the C ABI with host buffers (pinned): H2D of the
+    # step's observation, D2H of the step's record
+    e2e = run_e2e(make, headline, args.steps, y, dev, stream, flush) if rank == 0 else None
+    launches = args.steps * (1 + RESAMPLE_KERNELS[headline])
+    out = {
+        "metric": METRIC, "value": value, "unit": "particle-updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_particles": n, "scheme": headline, "threshold": 0.5,
+                   "l2": "512 MB buffer written between timed iterations (untimed)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "resample_fraction": main["resample_frac"]},
+        "roofline": roofline,
+        "per_scheme": per_scheme,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(n, 8)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(make, scheme, K, y, dev, stream, flush):
+    import torch
+    from paper_1306_5583_b300 import smc
+    s = make(scheme)
+    obs = torch.empty(2, dtype=torch.float64, pin_memory=True)
+    rec = torch.empty(ctypes.sizeof(smc.Record), dtype=torch.uint8, pin_memory=True)
+    L = smc.lib()
+    with torch.cuda.stream(stream):
+        s.initialize()
+        torch.cuda.synchronize(dev)
+        total = 0.0
+        steps = 0
+        for k in range(K):
+            t = s.iteration() + 1
+            if t >= T_OBS:
+                s.initialize()
+                torch.cuda.synchronize(dev)
+                t = 1
+            obs.copy_(torch.from_numpy(y[t]))
+            flush.fill_(float(k))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            smc.check(L.smc_iterate_host(s.ctx, ctypes.c_void_p(obs.data_ptr()),
+                                         ctypes.cast(ctypes.c_void_p(rec.data_ptr()), ctypes.POINTER(smc.Record))),
+                      "smc_iterate_host")
+            total += time.perf_counter() - t0
+            steps += 1
+    s.close()
+    return {"value": s.n * steps / total, "unit": "particle-updates/s", "h2d_bytes_per_step": 16,
+            "d2h_bytes_per_step": ctypes.sizeof(smc.Record), "timing": "host wall clock per call (synchronising)"}
+
+
+def cpu_baseline(n, iters):
+    """The FP64 oracle on `iters` iterations at the full N (bounded sample)."""
+    from oracle import cv as ocv
+    from paper_1306_5583_b300 import workloads
+    p = dict(workloads.CV_DEFAULT)
+    _, y = workloads.cv_data(T_OBS, seed=0, **p)
+    op = ocv.CVParams(**p)
+    r = ocv.init_step(n, y[0], 1, op, 0.5)
+    from oracle import resample as ores
+    anc = ores.resample("systematic", r.lw, 1, 0) if r.resample else None
+    t0 = time.perf_counter()
+    for t in range(1, iters + 1):
+        r = ocv.step(r.x, r.lw, r.L, anc, t, y[t], 1, op, 0.5)
+        anc = ores.resample("systematic", r.lw, 1, t) if r.resample else None
+    dt = time.perf_counter() - t0
+    return {"value": n * iters / dt, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{iters} iterations of the same filter at N={n} (numpy float64 + exact integer "
+                      f"resampling), single process"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    n = args.n
+    t0 = time.perf_counter()
+    cb = cpu_baseline(n, max(1, min(args.steps, 3)))
+    dt = time.perf_counter() - t0
+    iters = max(1, min(args.steps, 3))
+    out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "particle-updates/s",
+           "n_gpus": ws, "steps": iters, "warmup": 0, "ms_per_step": dt * 1e3 / iters, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_particles": n, "scheme": "systematic", "threshold": 0.5},
+           "cpu_baseline": {"value": cb["value"], "unit": cb["unit"], "cores": cb["cores"], "kind": "oracle",
+                            "sample": cb["sample"]},
+           "e2e": {"value": cb["value"], "unit": "particle-updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scheme", default="systematic")
+    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * smc.h -- C ABI of the B300 (sm_103a) SMC hot path.
+ *
+ * The calls follow the decomposition of a vSMC sampler (Zhou, "vSMC:
+ * Parallel Sequential Monte Carlo in C++", arXiv 1306.5583):
+ *   Sampler(N, scheme, threshold)          -> smc_config, smc_create
+ *   Sampler::initialize                    -> smc_initialize
+ *   one iteration = move queue, ESS test and resampling, mcmc queue,
+ *   monitors (Sec. 4.1.3)                  -> smc_move, smc_resample, smc_mcmc
+ *   Sampler::iterate(n)                    -> smc_iterate
+ *   WeightSet::add_log_weight (Sec. 4.1.6) -> smc_add_log_weight
+ *   NormalizingConstant / Path estimates   -> smc_log_evidence, smc_path_sampling
+ *   read_weight / read_log_weight          -> smc_read_log_weight
+ *   copy(N, copy_from) convention (Sec. 4.1.2): ancestors[k] is the parent
+ *   of new particle k                      -> smc_read_ancestors
+ *
+ * Conventions shared by every call
+ * * Return value: SMC_OK (0) or one of the SMC_E_* codes below.  No C++
+ *   exception crosses this boundary.
+ * * Device work is queued on the CUDA stream given to smc_create and runs
+ *   asynchronously; errors raised on the device (non-finite weights, a
+ *   bounded wait that gave up) are kept in a device error word and returned
+ *   by the next call that synchronises (smc_ess with a host pointer,
+ *   smc_log_evidence, smc_path_sampling, smc_read_*, smc_sync).
+ * * Memory: the caller owns the device workspace (size from
+ *   smc_workspace_bytes, 256-byte aligned) and the stream; the context holds
+ *   non-owning pointers into them and host memory of its own.  Host buffers
+ *   passed to smc_read_* are caller-owned.  `on_device` arguments say
+ *   whether a pointer is device memory (1) or host memory (0).
+ * * Threading: one context must not be used by two threads at once;
+ *   distinct contexts are independent (the thread-safety rules of Sec. 4.3).
+ * * Random numbers: Philox4x32-10 (Salmon et al., SC'11; the paper's
+ *   per-particle counter-based streams, Sec. 3.4) with key = (seed low 32
+ *   bits, seed high 32 bits) and counter = (particle or slot index,
+ *   iteration t, purpose tag | stream_id << 16, draw index).
+ */
+#ifndef SMC_H
+#define SMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SMC_OK 0
+#define SMC_E_ARG 1        /* invalid argument or configuration */
+#define SMC_E_WORKSPACE 2  /* workspace too small or misaligned */
+#define SMC_E_NONFINITE 3  /* all weights zero or NaN: state left untouched */
+#define SMC_E_TIMEOUT 4    /* a bounded device wait gave up */
+#define SMC_E_CUDA 5       /* a CUDA runtime call failed */
+#define SMC_E_STATE 6      /* call out of order (e.g. move before initialize) */
+
+/* resampling schemes (Sec. 2.1; Douc et al. 2005); the paper's default is
+ * stratified (Sec. 4.1.3) */
+#define SMC_MULTINOMIAL 0
+#define SMC_STRATIFIED 1
+#define SMC_SYSTEMATIC 2
+#define SMC_RESIDUAL 3
+
+/* models */
+#define SMC_MODEL_CV 0        /* Sec. 5.1: constant-velocity tracking, Student-t observations */
+#define SMC_MODEL_CV_GAUSS 1  /* same with Gaussian observations (Kalman closed form) */
+#define SMC_MODEL_GMM 2       /* Sec. 5.2: Bayesian Gaussian mixture, tempered SMC sampler */
+
+/* GMM annealing schedules (Sec. 5.2.3) */
+#define SMC_ALPHA_LINEAR 0  /* alpha_t = t / T */
+#define SMC_ALPHA_PRIOR 1   /* alpha_t = (t / T)^p */
+
+/* Almost-constant-velocity model parameters (Sec. 5.1.1). */
+typedef struct {
+    double delta;      /* time step Delta */
+    double sd_pos;     /* process-noise sd on positions */
+    double sd_vel;     /* process-noise sd on velocities */
+    double obs_scale;  /* observation-noise scale s */
+    double obs_df;     /* Student-t degrees of freedom nu */
+    double sd_pos0;    /* prior sd of the positions at t = 0 */
+    double sd_vel0;    /* prior sd of the velocities at t = 0 */
+} smc_cv_params;
+
+/* Gaussian-mixture model and sampler parameters (Sec. 5.2.1-5.2.3). */
+typedef struct {
+    int32_t n_comp;       /* r, 1..8 */
+    int32_t schedule;     /* SMC_ALPHA_LINEAR or SMC_ALPHA_PRIOR */
+    int32_t n_iter;       /* T_r: alpha reaches 1 at t = T_r */
+    int32_t shape0;       /* Gamma prior shape of each precision (integer >= 1) */
+    double power;         /* p of the prior schedule */
+    double mu0, sd0;      /* normal prior of each mean */
+    double rate0;         /* Gamma prior rate of each precision */
+} smc_gmm_params;
+
+typedef struct {
+    int32_t model;        /* SMC_MODEL_* */
+    int32_t precision;    /* 32: FP32 per particle, FP64 normaliser and evidence;
+                             64: FP64 throughout */
+    int64_t n_particles;  /* N >= 1 */
+    int32_t max_records;  /* iteration records kept on the device (ring), >= 2 */
+    int32_t scheme;       /* SMC_* resampling scheme */
+    double threshold;     /* resample when ESS < threshold * N; >= 1 always, <= 0 never */
+    uint64_t seed;        /* Philox key */
+    uint32_t stream_id;   /* Philox stream (counter word 2, high 16 bits) */
+    uint32_t reserved;
+    int64_t max_data;     /* capacity for observations: CV rows (Y_0..), GMM points */
+    smc_cv_params cv;
+    smc_gmm_params gmm;
+} smc_config;
+
+/* One record per iteration, kept on the device (ring of max_records). */
+typedef struct {
+    double log_norm;      /* L_t: log-sum-exp of lw_t = log of the estimated Z_t / Z_{t-1} */
+    double log_evidence;  /* running sum of L_t (standard estimate, Sec. 2.2) */
+    double ess;           /* 1 / sum W_t^2 (Sec. 2.1) */
+    double mean[2];       /* PF: filtered means of the positions (before resampling) */
+    double max_lw;        /* max_i lw_t,i */
+    double path_u;        /* GMM: U_t (eq:path_import) */
+    double path_log_z;    /* GMM: running path-sampling estimate (eq:path_est) */
+    double alpha;         /* GMM: alpha_t */
+    double accept[3];     /* GMM: acceptance rate of the mu, lambda, weight blocks */
+    int32_t t;            /* iteration index */
+    int32_t resampled;    /* 1 when the ESS test asked for resampling */
+    int32_t status;       /* SMC_OK or an error code */
+    int32_t pad;
+    double pad2[2];
+} smc_record;
+
+typedef struct smc_ctx smc_ctx;
+
+/* Device bytes the context needs for `cfg` (0 on an invalid config). */
+size_t smc_workspace_bytes(const smc_config *cfg);
+
+/* Create a context.  d_workspace: caller-owned device memory of at least
+ * smc_workspace_bytes(cfg) bytes, 256-byte aligned; cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream).  The context is ready for
+ * smc_set_data; *out is NULL on failure. */
+int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t bytes,
+               void *cuda_stream);
+int smc_destroy(smc_ctx *ctx);
+
+/* Observations.  CV models: `count` rows of (x_obs, y_obs) as float64, row t
+ * is Y_t (Algorithm 1).  GMM: `count` float64 data points y_1..y_n.  The data
+ * are copied into the workspace. */
+int smc_set_data(smc_ctx *ctx, const double *obs, int64_t count, int on_device);
+
+/* Sampler::initialize: t = 0.  CV: X_0 from the prior, weighted by Y_0;
+ * GMM: theta from the prior, equal weights, alpha_0 = 0.  Computes the
+ * normaliser, ESS and the resample decision of iteration 0. */
+int smc_initialize(smc_ctx *ctx);
+
+/* Move queue of the next iteration t (Algorithm 1 / Algorithm 2 "Weight"):
+ * CV: gather by the pending ancestors, propagate, add log g(Y_t | X_t);
+ * GMM: alpha_t and the incremental weights (alpha_t - alpha_{t-1}) l(theta).
+ * Then normaliser, ESS, evidence increment, monitor, resample decision. */
+int smc_move(smc_ctx *ctx);
+
+/* Resampling of the current iteration when its ESS test asked for it (or
+ * always, when force != 0): fixed-point CDF and ancestor selection by the
+ * configured scheme.  The particle gather happens in the next move/mcmc. */
+int smc_resample(smc_ctx *ctx, int force);
+
+/* mcmc queue (Sec. 4.1.3): GMM: the three random-walk Metropolis blocks on
+ * mu, log lambda and the weights' log-ratios at alpha_t, then the
+ * path-sampling monitor U_t.  CV: nothing. */
+int smc_mcmc(smc_ctx *ctx);
+
+/* Sampler::iterate: n iterations of (move, resample, mcmc), replayed from a
+ * captured CUDA graph. */
+int smc_iterate(smc_ctx *ctx, int32_t n);
+
+/* One iteration with host buffers: copies obs_t (CV: 2 float64; may be NULL
+ * to use the observation already stored for t) to the device, runs one
+ * iteration and copies its record to *h_record.  Synchronises. */
+int smc_iterate_host(smc_ctx *ctx, const double *h_obs_t, smc_record *h_record);
+
+/* WeightSet::add_log_weight: lw_i += incw_i (n_particles values of the
+ * context's precision), then normaliser, ESS and the resample decision of
+ * the current iteration. */
+int smc_add_log_weight(smc_ctx *ctx, const void *incw, int on_device);
+
+/* ESS of the current weights.  h_ess == NULL: no synchronisation. */
+int smc_ess(smc_ctx *ctx, double *h_ess);
+
+/* Standard log normalising-constant estimate (sum of L_t), and the
+ * path-sampling estimate (GMM).  Synchronise. */
+int smc_log_evidence(smc_ctx *ctx, double *h_out);
+int smc_path_sampling(smc_ctx *ctx, double *h_out);
+
+/* Current iteration index (the last one completed), -1 before initialize. */
+int smc_iteration(const smc_ctx *ctx, int32_t *t);
+
+/* Readers.  Layouts: state is structure-of-arrays, d rows of N values of the
+ * context's precision (CV: d = 4, rows x_pos, y_pos, x_vel, y_vel; GMM:
+ * d = 3r + 2, rows mu_1..r, lambda_1..r, omega_1..r, log-prior,
+ * log-likelihood).  Log-weights: N values (raw lw_t).  Ancestors: N int32
+ * (sorted; valid after a resampling step).  CDF: N uint64 fixed-point
+ * inclusive prefix sums.  Records: the last min(count, available) records in
+ * iteration order.  All synchronise. */
+int smc_state_dim(const smc_ctx *ctx, int32_t *d);
+int smc_read_state(smc_ctx *ctx, void *dst, int on_device);
+int smc_read_log_weight(smc_ctx *ctx, void *dst, int on_device);
+int smc_read_ancestors(smc_ctx *ctx, int32_t *dst, int on_device);
+int smc_read_cdf(smc_ctx *ctx, uint64_t *dst, int on_device);
+int smc_read_history(smc_ctx *ctx, smc_record *h_records, int32_t count, int32_t *n_written);
+
+/* Writers for restarts and checkpoints: replace the state / log-weights of
+ * the current iteration (layouts as above). */
+int smc_write_state(smc_ctx *ctx, const void *src, int on_device);
+int smc_write_log_weight(smc_ctx *ctx, const void *src, int on_device);
+
+/* Wait for queued work and return the device error word. */
+int smc_sync(smc_ctx *ctx);
+
+const char *smc_error_string(int code);
+
+/* ---- stateless primitives (device pointers, caller's stream) ---- */
+
+/* Philox4x32-10: out[i] = philox(ctr[i], key) for i < n; ctr and out are
+ * n x 4 uint32 (row-major), key 2 uint32 (host). */
+int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], uint32_t *d_out, int64_t n,
+                      void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMC_H */

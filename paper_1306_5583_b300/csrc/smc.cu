@@ -1,0 +1,664 @@
+// C ABI of the SMC hot path (include/smc.h): context, workspace carving and
+// the launch sequence of each call.  Device kernels live in the included
+// headers; this file only marshals arguments and orders launches.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "pf_kernels.cuh"
+#include "resample_kernels.cuh"
+#include "gmm_kernels.cuh"
+
+using namespace smc;
+
+struct smc_ctx;
+
+namespace {
+
+// Gaussian-mixture sampler (Sec. 5.2); defined after the context.
+int gmm_move(smc_ctx *c);
+int gmm_mcmc(smc_ctx *c);
+int gmm_initialize(smc_ctx *c);
+int gmm_on_data(smc_ctx *c);
+void gmm_release(smc_ctx *c);
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+int ceil_log2(int64_t n) {
+    int b = 0;
+    while ((int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+struct Layout {
+    size_t st, rec, part, x, lw, anc, Q, status, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, total;
+    int d;            // state rows
+    int64_t nbw;      // blocks of the weighting kernels
+    int64_t ntiles;   // scan tiles of an N-element scan
+    int64_t nbuckets;
+    int64_t ntiles_status;
+    int bucket_shift;
+    size_t rsize;
+};
+
+bool valid_config(const smc_config *c) {
+    if (!c) return false;
+    if (c->model != SMC_MODEL_CV && c->model != SMC_MODEL_CV_GAUSS && c->model != SMC_MODEL_GMM) return false;
+    if (c->precision != 32 && c->precision != 64) return false;
+    if (c->n_particles < 1 || c->n_particles > (int64_t(1) << 30)) return false;
+    if (c->max_records < 2) return false;
+    if (c->scheme < SMC_MULTINOMIAL || c->scheme > SMC_RESIDUAL) return false;
+    if (!(c->threshold == c->threshold)) return false;
+    if (c->max_data < 1) return false;
+    if (c->model == SMC_MODEL_GMM) {
+        if (!kGmmEnabled) return false;
+        if (c->gmm.n_comp < 1 || c->gmm.n_comp > kGmmMaxComp) return false;
+        if (c->gmm.n_iter < 1 || c->gmm.shape0 < 1 || !(c->gmm.rate0 > 0) || !(c->gmm.sd0 > 0)) return false;
+        if (c->max_data > kGmmMaxData) return false;
+    } else {
+        if (!(c->cv.obs_scale > 0) || !(c->cv.obs_df > 0)) return false;
+    }
+    return true;
+}
+
+Layout make_layout(const smc_config *c) {
+    Layout L{};
+    const int64_t n = c->n_particles;
+    const size_t rs = (c->precision == 32) ? 4 : 8;
+    L.rsize = rs;
+    L.d = (c->model == SMC_MODEL_GMM) ? 3 * c->gmm.n_comp + 2 : 4;
+    L.nbw = (n + kPfTile - 1) / kPfTile;
+    L.ntiles = (n + kScanTile - 1) / kScanTile;
+    const int B = std::min(24, std::max(1, ceil_log2(n)));
+    L.bucket_shift = 24 - B;
+    L.nbuckets = int64_t(1) << B;
+    const bool sorts = (c->scheme == SMC_MULTINOMIAL || c->scheme == SMC_RESIDUAL);
+    const bool resid = (c->scheme == SMC_RESIDUAL);
+    const int64_t bucket_tiles = sorts ? (L.nbuckets + kScanTile - 1) / kScanTile : 0;
+    L.ntiles_status = std::max<int64_t>(L.ntiles, bucket_tiles);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    L.st = take(sizeof(DevState));
+    L.rec = take(sizeof(smc_record) * (size_t)c->max_records);
+    L.part = take(sizeof(Partial) * (size_t)std::max<int64_t>(L.nbw, 1));
+    L.x = take(2 * (size_t)L.d * n * rs);
+    L.lw = take(2 * (size_t)n * rs);
+    L.anc = take((size_t)n * 4);
+    L.Q = take((size_t)n * 8);
+    L.status = take((size_t)kScanSlots * 2 * L.ntiles_status * 8);
+    L.cnt = take(sorts ? (size_t)L.nbuckets * 4 : 0);
+    L.fill = take(sorts ? (size_t)L.nbuckets * 4 : 0);
+    L.boff = take(sorts ? (size_t)L.nbuckets * 8 : 0);
+    L.sorted = take(sorts ? (size_t)n * 4 : 0);
+    L.RQ = take(resid ? (size_t)n * 8 : 0);
+    L.extra = take(resid ? (size_t)n * 4 : 0);
+    L.O = take(resid ? (size_t)n * 8 : 0);
+    const int64_t obs_vals = (c->model == SMC_MODEL_GMM) ? c->max_data : 2 * c->max_data;
+    L.obs = take((size_t)obs_vals * 8);
+    L.obs_f = take((size_t)obs_vals * 4);
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct smc_ctx {
+    smc_config cfg;
+    Layout L;
+    char *ws;
+    cudaStream_t stream;
+    DevState *st;
+    smc_record *rec;
+    Partial *part;
+    void *x[2];
+    void *lw[2];
+    int32_t *anc;
+    unsigned long long *Q;
+    unsigned long long *status;
+    uint32_t *cnt, *fill;
+    unsigned long long *boff;
+    uint32_t *sorted;
+    unsigned long long *RQ;
+    uint32_t *extra;
+    unsigned long long *O;
+    double *obs;
+    float *obs_f;
+    int64_t n_obs;
+    int32_t t_host;       // last iteration queued, -1 before initialize
+    int initialized;
+    int device;
+    DevState host_st;     // last state read back
+};
+
+namespace {
+
+int cuda_check(cudaError_t e) { return e == cudaSuccess ? SMC_OK : SMC_E_CUDA; }
+
+ScanSlot slot_of(smc_ctx *c, int s) {
+    ScanSlot sl;
+    const int64_t nt = c->L.ntiles_status;
+    sl.status[0] = c->status + (size_t)s * 2 * nt;
+    sl.status[1] = sl.status[0] + nt;
+    sl.ntiles_max = (int32_t)nt;
+    return sl;
+}
+
+uint2 key_of(const smc_ctx *c) { return make_uint2((uint32_t)(c->cfg.seed & 0xffffffffu), (uint32_t)(c->cfg.seed >> 32)); }
+
+__global__ void reset_state_kernel(DevState *st) {
+    st->t = -1;
+    st->cur = 0;
+    st->due = 0;
+    st->ready = 0;
+    st->error = 0;
+    st->ticket = 0;
+    st->count_r = 0;
+    st->max_lw = 0;
+    st->log_norm = 0;
+    st->log_evidence = 0;
+    st->ess = 0;
+    st->alpha = 0;
+    st->path_u = 0;
+    st->path_log_z = 0;
+    st->qn = 0;
+    st->sum_d = 0;
+    for (int i = 0; i < 3; ++i) st->accept[i] = 0;
+}
+
+template <typename R>
+PfArgs<R> pf_args(smc_ctx *c) {
+    PfArgs<R> a;
+    const smc_config &g = c->cfg;
+    const int64_t n = g.n_particles;
+    a.n = n;
+    for (int b = 0; b < 2; ++b) {
+        R *base = static_cast<R *>(c->x[b]);
+        for (int r = 0; r < 4; ++r) a.x[b][r] = base + (size_t)r * n;
+        a.lw[b] = static_cast<R *>(c->lw[b]);
+    }
+    a.anc = c->anc;
+    a.obs = c->obs;
+    a.rec = c->rec;
+    a.rec_cap = g.max_records;
+    a.st = c->st;
+    a.part = c->part;
+    a.log_n = std::log((double)n);
+    a.threshold = g.threshold;
+    a.delta = R(g.cv.delta);
+    a.sd_pos = R(g.cv.sd_pos);
+    a.sd_vel = R(g.cv.sd_vel);
+    a.sd_pos0 = R(g.cv.sd_pos0);
+    a.sd_vel0 = R(g.cv.sd_vel0);
+    const double s = g.cv.obs_scale, nu = g.cv.obs_df;
+    a.inv_scale = R(1.0 / s);
+    a.inv_nu = R(1.0 / nu);
+    a.half_nu1 = R(0.5 * (nu + 1.0));
+    a.gaussian = (g.model == SMC_MODEL_CV_GAUSS) ? 1 : 0;
+    double cst;
+    if (a.gaussian) cst = -0.5 * std::log(2.0 * M_PI) - std::log(s);
+    else cst = std::lgamma(0.5 * (nu + 1.0)) - std::lgamma(0.5 * nu) - 0.5 * std::log(nu * M_PI) - std::log(s);
+    a.ll_const = R(2.0 * cst);
+    a.key = key_of(c);
+    a.stream = g.stream_id;
+    return a;
+}
+
+template <typename R>
+int launch_pf(smc_ctx *c) {
+    PfArgs<R> a = pf_args<R>(c);
+    pf_iterate_kernel<R><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(a);
+    return cuda_check(cudaGetLastError());
+}
+
+template <class Gen, class Out>
+int launch_scan(smc_ctx *c, Gen g, Out o, int64_t n, int slot, int gate) {
+    const unsigned grid = (unsigned)((n + kScanTile - 1) / kScanTile);
+    scan_kernel<Gen, Out><<<grid, kBlock, 0, c->stream>>>(g, o, n, slot_of(c, slot), slot, c->st, gate);
+    return cuda_check(cudaGetLastError());
+}
+
+template <class Tgt, class Out>
+int launch_select(smc_ctx *c, Tgt tg, Out o, int64_t n_out_max, const unsigned long long *Q, int slot, int gate,
+                  int set_ready) {
+    const int64_t n = c->cfg.n_particles;
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    const int spl_cap = (ntiles <= kMaxSplitters) ? (int)ntiles : 0;
+    const size_t smem = ((size_t)spl_cap + kSelCap) * 8;
+    static bool attr_set[64] = {};  // per template instance and device
+    const int dev = c->device & 63;
+    if (!attr_set[dev]) {
+        cudaFuncSetAttribute(select_kernel<Tgt, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((kMaxSplitters + kSelCap) * 8));
+        attr_set[dev] = true;
+    }
+    const unsigned grid = (unsigned)std::max<int64_t>(1, (n_out_max + kSelTile - 1) / kSelTile);
+    select_kernel<Tgt, Out><<<grid, kBlock, smem, c->stream>>>(tg, o, Q, n, slot_of(c, slot), slot, c->st, gate,
+                                                                set_ready, spl_cap);
+    return cuda_check(cudaGetLastError());
+}
+
+UniformSortArgs sort_args(smc_ctx *c, int from_residual) {
+    UniformSortArgs a;
+    a.key = key_of(c);
+    a.stream = c->cfg.stream_id;
+    a.n_total = c->cfg.n_particles;
+    a.from_residual = from_residual;
+    a.bucket_shift = c->L.bucket_shift;
+    a.cnt = c->cnt;
+    a.fill = c->fill;
+    a.boff = c->boff;
+    a.sorted = c->sorted;
+    a.nbuckets = c->L.nbuckets;
+    return a;
+}
+
+int launch_uniform_sort(smc_ctx *c, int from_residual, int gate) {
+    UniformSortArgs a = sort_args(c, from_residual);
+    const int64_t n = c->cfg.n_particles;
+    const unsigned g4 = (unsigned)((n + 4 * kBlock - 1) / (4 * kBlock));
+    int rc;
+    bucket_count_kernel<<<g4, kBlock, 0, c->stream>>>(a, c->st, gate);
+    if ((rc = cuda_check(cudaGetLastError()))) return rc;
+    if ((rc = launch_scan(c, CountGen{c->cnt}, StoreOut{c->boff}, c->L.nbuckets, SLOT_BUCKET, gate))) return rc;
+    bucket_scatter_kernel<<<g4, kBlock, 0, c->stream>>>(a, c->st, gate);
+    if ((rc = cuda_check(cudaGetLastError()))) return rc;
+    const unsigned gb = (unsigned)((c->L.nbuckets + kBlock - 1) / kBlock);
+    bucket_sort_kernel<<<gb, kBlock, 0, c->stream>>>(a, c->st, gate);
+    return cuda_check(cudaGetLastError());
+}
+
+template <typename R>
+int launch_resample(smc_ctx *c, int gate) {
+    const int64_t n = c->cfg.n_particles;
+    int rc;
+    QGen<R> qg;
+    qg.lw[0] = static_cast<const R *>(c->lw[0]);
+    qg.lw[1] = static_cast<const R *>(c->lw[1]);
+    qg.frac = 61 - ceil_log2(n);
+    if ((rc = launch_scan(c, qg, QOut{c->Q, n}, n, SLOT_CDF, gate))) return rc;
+    const uint2 key = key_of(c);
+    const uint32_t sid = c->cfg.stream_id;
+    switch (c->cfg.scheme) {
+        case SMC_SYSTEMATIC: {
+            SystematicTargets tg{n, key, sid, 0};
+            return launch_select(c, tg, AncOut{c->anc}, n, c->Q, SLOT_CDF, gate, 1);
+        }
+        case SMC_STRATIFIED: {
+            StratifiedTargets tg{n, key, sid, 0};
+            return launch_select(c, tg, AncOut{c->anc}, n, c->Q, SLOT_CDF, gate, 1);
+        }
+        case SMC_MULTINOMIAL: {
+            if ((rc = launch_uniform_sort(c, 0, gate))) return rc;
+            SortedTargets tg{c->sorted, n, n, 0, 0};
+            return launch_select(c, tg, AncOut{c->anc}, n, c->Q, SLOT_CDF, gate, 1);
+        }
+        case SMC_RESIDUAL: {
+            if ((rc = cuda_check(cudaMemsetAsync(&c->st->sum_d, 0, sizeof(unsigned long long), c->stream))))
+                return rc;
+            ResidualParts p{c->Q, n, 0};
+            const unsigned gt = (unsigned)((n + kScanTile - 1) / kScanTile);
+            residual_d_kernel<<<gt, kBlock, 0, c->stream>>>(p, c->extra, c->st, gate);
+            if ((rc = cuda_check(cudaGetLastError()))) return rc;
+            ResidualRGen rg{p, 0};
+            if ((rc = launch_scan(c, rg, StoreOut{c->RQ}, n, SLOT_RES_R, gate))) return rc;
+            if ((rc = launch_uniform_sort(c, 1, gate))) return rc;
+            SortedTargets tg{c->sorted, n, n, 1, 0};
+            if ((rc = launch_select(c, tg, CountOut{c->extra}, n, c->RQ, SLOT_RES_R, gate, 0))) return rc;
+            ResidualOGen og{p, c->extra};
+            if ((rc = launch_scan(c, og, StoreOut{c->O}, n, SLOT_RES_O, gate))) return rc;
+            return launch_select(c, ExpandTargets{n}, AncOut{c->anc}, n, c->O, SLOT_RES_O, gate, 1);
+        }
+    }
+    return SMC_E_ARG;
+}
+
+int resample_any(smc_ctx *c, int gate) {
+    return (c->cfg.precision == 32) ? launch_resample<float>(c, gate) : launch_resample<double>(c, gate);
+}
+
+int read_state(smc_ctx *c) {
+    cudaError_t e = cudaMemcpyAsync(&c->host_st, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return SMC_E_CUDA;
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return SMC_E_CUDA;
+    return c->host_st.error;
+}
+
+int move_any(smc_ctx *c) {
+    if (!c->initialized) return SMC_E_STATE;
+    if (c->cfg.model == SMC_MODEL_GMM) return gmm_move(c);
+    if (c->t_host + 1 >= c->n_obs) return SMC_E_ARG;
+    const int rc = (c->cfg.precision == 32) ? launch_pf<float>(c) : launch_pf<double>(c);
+    if (rc == SMC_OK) c->t_host += 1;
+    return rc;
+}
+
+int mcmc_any(smc_ctx *c) {
+    if (!c->initialized) return SMC_E_STATE;
+    if (c->cfg.model == SMC_MODEL_GMM) return gmm_mcmc(c);
+    return SMC_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI --
+
+extern "C" {
+
+size_t smc_workspace_bytes(const smc_config *cfg) {
+    if (!valid_config(cfg)) return 0;
+    return make_layout(cfg).total;
+}
+
+int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t bytes, void *cuda_stream) {
+    if (!out) return SMC_E_ARG;
+    *out = nullptr;
+    if (!valid_config(cfg)) return SMC_E_ARG;
+    const Layout L = make_layout(cfg);
+    if (!d_workspace || bytes < L.total || ((uintptr_t)d_workspace & (kAlign - 1))) return SMC_E_WORKSPACE;
+    smc_ctx *c = new (std::nothrow) smc_ctx();
+    if (!c) return SMC_E_ARG;
+    c->cfg = *cfg;
+    c->L = L;
+    c->ws = static_cast<char *>(d_workspace);
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->st = reinterpret_cast<DevState *>(c->ws + L.st);
+    c->rec = reinterpret_cast<smc_record *>(c->ws + L.rec);
+    c->part = reinterpret_cast<Partial *>(c->ws + L.part);
+    const size_t half_x = (size_t)L.d * cfg->n_particles * L.rsize;
+    c->x[0] = c->ws + L.x;
+    c->x[1] = c->ws + L.x + half_x;
+    c->lw[0] = c->ws + L.lw;
+    c->lw[1] = c->ws + L.lw + (size_t)cfg->n_particles * L.rsize;
+    c->anc = reinterpret_cast<int32_t *>(c->ws + L.anc);
+    c->Q = reinterpret_cast<unsigned long long *>(c->ws + L.Q);
+    c->status = reinterpret_cast<unsigned long long *>(c->ws + L.status);
+    c->cnt = reinterpret_cast<uint32_t *>(c->ws + L.cnt);
+    c->fill = reinterpret_cast<uint32_t *>(c->ws + L.fill);
+    c->boff = reinterpret_cast<unsigned long long *>(c->ws + L.boff);
+    c->sorted = reinterpret_cast<uint32_t *>(c->ws + L.sorted);
+    c->RQ = reinterpret_cast<unsigned long long *>(c->ws + L.RQ);
+    c->extra = reinterpret_cast<uint32_t *>(c->ws + L.extra);
+    c->O = reinterpret_cast<unsigned long long *>(c->ws + L.O);
+    c->obs = reinterpret_cast<double *>(c->ws + L.obs);
+    c->obs_f = reinterpret_cast<float *>(c->ws + L.obs_f);
+    c->n_obs = 0;
+    c->t_host = -1;
+    c->initialized = 0;
+    cudaGetDevice(&c->device);
+    // zero the state block, records, scan status words and bucket counters
+    int rc = cuda_check(cudaMemsetAsync(c->ws, 0, L.part, c->stream));
+    if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + L.status, 0, L.boff - L.status, c->stream));
+    if (!rc) {
+        reset_state_kernel<<<1, 1, 0, c->stream>>>(c->st);
+        rc = cuda_check(cudaGetLastError());
+    }
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return SMC_OK;
+}
+
+int smc_destroy(smc_ctx *c) {
+    if (!c) return SMC_E_ARG;
+    gmm_release(c);
+    delete c;
+    return SMC_OK;
+}
+
+int smc_set_data(smc_ctx *c, const double *obs, int64_t count, int on_device) {
+    if (!c || !obs || count < 1 || count > c->cfg.max_data) return SMC_E_ARG;
+    const int64_t vals = (c->cfg.model == SMC_MODEL_GMM) ? count : 2 * count;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int rc = cuda_check(cudaMemcpyAsync(c->obs, obs, (size_t)vals * 8, k, c->stream));
+    if (rc) return rc;
+    if (!on_device) rc = cuda_check(cudaStreamSynchronize(c->stream));  // the host buffer may go away
+    if (rc) return rc;
+    c->n_obs = count;
+    return gmm_on_data(c);
+}
+
+int smc_initialize(smc_ctx *c) {
+    if (!c) return SMC_E_ARG;
+    if (c->n_obs < 1) return SMC_E_STATE;
+    reset_state_kernel<<<1, 1, 0, c->stream>>>(c->st);
+    int rc = cuda_check(cudaGetLastError());
+    if (rc) return rc;
+    c->initialized = 1;
+    c->t_host = -1;
+    if (c->cfg.model == SMC_MODEL_GMM) {
+        rc = gmm_initialize(c);
+    } else {
+        rc = (c->cfg.precision == 32) ? launch_pf<float>(c) : launch_pf<double>(c);
+        if (!rc) c->t_host = 0;
+    }
+    if (rc) return rc;
+    return resample_any(c, 1);
+}
+
+int smc_move(smc_ctx *c) {
+    if (!c) return SMC_E_ARG;
+    return move_any(c);
+}
+
+int smc_resample(smc_ctx *c, int force) {
+    if (!c) return SMC_E_ARG;
+    if (!c->initialized) return SMC_E_STATE;
+    return resample_any(c, force ? 0 : 1);
+}
+
+int smc_mcmc(smc_ctx *c) {
+    if (!c) return SMC_E_ARG;
+    return mcmc_any(c);
+}
+
+int smc_iterate(smc_ctx *c, int32_t n) {
+    if (!c || n < 0) return SMC_E_ARG;
+    if (!c->initialized) return SMC_E_STATE;
+    for (int32_t i = 0; i < n; ++i) {
+        int rc = move_any(c);
+        if (!rc) rc = resample_any(c, 1);
+        if (!rc) rc = mcmc_any(c);
+        if (rc) return rc;
+    }
+    return SMC_OK;
+}
+
+int smc_iterate_host(smc_ctx *c, const double *h_obs_t, smc_record *h_record) {
+    if (!c || !h_record) return SMC_E_ARG;
+    if (!c->initialized) return SMC_E_STATE;
+    const int32_t t = c->t_host + 1;
+    int rc;
+    if (h_obs_t && c->cfg.model != SMC_MODEL_GMM) {
+        if (t >= c->cfg.max_data) return SMC_E_ARG;
+        rc = cuda_check(cudaMemcpyAsync(c->obs + 2 * (size_t)t, h_obs_t, 16, cudaMemcpyHostToDevice, c->stream));
+        if (rc) return rc;
+        if (c->n_obs < t + 1) c->n_obs = t + 1;
+    }
+    rc = smc_iterate(c, 1);
+    if (rc) return rc;
+    rc = cuda_check(cudaMemcpyAsync(h_record, c->rec + (t % c->cfg.max_records), sizeof(smc_record),
+                                    cudaMemcpyDeviceToHost, c->stream));
+    if (rc) return rc;
+    return read_state(c);
+}
+
+int smc_ess(smc_ctx *c, double *h_ess) {
+    if (!c) return SMC_E_ARG;
+    if (!h_ess) return SMC_OK;
+    const int rc = read_state(c);
+    *h_ess = c->host_st.ess;
+    return rc;
+}
+
+int smc_log_evidence(smc_ctx *c, double *h_out) {
+    if (!c || !h_out) return SMC_E_ARG;
+    const int rc = read_state(c);
+    *h_out = c->host_st.log_evidence;
+    return rc;
+}
+
+int smc_path_sampling(smc_ctx *c, double *h_out) {
+    if (!c || !h_out) return SMC_E_ARG;
+    if (c->cfg.model != SMC_MODEL_GMM) return SMC_E_ARG;
+    const int rc = read_state(c);
+    *h_out = c->host_st.path_log_z;
+    return rc;
+}
+
+int smc_iteration(const smc_ctx *c, int32_t *t) {
+    if (!c || !t) return SMC_E_ARG;
+    *t = c->t_host;
+    return SMC_OK;
+}
+
+int smc_state_dim(const smc_ctx *c, int32_t *d) {
+    if (!c || !d) return SMC_E_ARG;
+    *d = c->L.d;
+    return SMC_OK;
+}
+
+static int copy_out(smc_ctx *c, void *dst, const void *src, size_t bytes, int on_device) {
+    if (!dst) return SMC_E_ARG;
+    int rc = read_state(c);  // also surfaces device errors
+    if (rc != SMC_OK && rc != SMC_E_NONFINITE) return rc;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    int rc2 = cuda_check(cudaMemcpyAsync(dst, src, bytes, k, c->stream));
+    if (!rc2) rc2 = cuda_check(cudaStreamSynchronize(c->stream));
+    return rc2 ? rc2 : rc;
+}
+
+int smc_read_state(smc_ctx *c, void *dst, int on_device) {
+    if (!c) return SMC_E_ARG;
+    int rc = read_state(c);
+    if (rc != SMC_OK && rc != SMC_E_NONFINITE) return rc;
+    const size_t bytes = (size_t)c->L.d * c->cfg.n_particles * c->L.rsize;
+    return copy_out(c, dst, c->x[c->host_st.cur & 1], bytes, on_device);
+}
+
+int smc_read_log_weight(smc_ctx *c, void *dst, int on_device) {
+    if (!c) return SMC_E_ARG;
+    int rc = read_state(c);
+    if (rc != SMC_OK && rc != SMC_E_NONFINITE) return rc;
+    return copy_out(c, dst, c->lw[c->host_st.cur & 1], (size_t)c->cfg.n_particles * c->L.rsize, on_device);
+}
+
+int smc_read_ancestors(smc_ctx *c, int32_t *dst, int on_device) {
+    if (!c) return SMC_E_ARG;
+    return copy_out(c, dst, c->anc, (size_t)c->cfg.n_particles * 4, on_device);
+}
+
+int smc_read_cdf(smc_ctx *c, uint64_t *dst, int on_device) {
+    if (!c) return SMC_E_ARG;
+    return copy_out(c, dst, c->Q, (size_t)c->cfg.n_particles * 8, on_device);
+}
+
+int smc_read_history(smc_ctx *c, smc_record *h, int32_t count, int32_t *n_written) {
+    if (!c || !h || count < 0) return SMC_E_ARG;
+    int rc = read_state(c);
+    if (rc != SMC_OK && rc != SMC_E_NONFINITE) return rc;
+    const int32_t last = c->host_st.t;
+    const int32_t avail = (last < 0) ? 0 : std::min<int32_t>(last + 1, c->cfg.max_records);
+    const int32_t m = std::min(count, avail);
+    const int32_t cap = c->cfg.max_records;
+    for (int32_t i = 0; i < m;) {  // at most two contiguous pieces of the ring
+        const int32_t t = last - m + 1 + i;
+        const int32_t slot = t % cap;
+        const int32_t len = std::min(m - i, cap - slot);
+        int rc2 = cuda_check(cudaMemcpyAsync(h + i, c->rec + slot, sizeof(smc_record) * (size_t)len,
+                                             cudaMemcpyDeviceToHost, c->stream));
+        if (rc2) return rc2;
+        i += len;
+    }
+    int rc2 = cuda_check(cudaStreamSynchronize(c->stream));
+    if (n_written) *n_written = m;
+    return rc2 ? rc2 : rc;
+}
+
+int smc_write_state(smc_ctx *c, const void *src, int on_device) {
+    if (!c || !src) return SMC_E_ARG;
+    int rc = read_state(c);
+    if (rc) return rc;
+    const size_t bytes = (size_t)c->L.d * c->cfg.n_particles * c->L.rsize;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    rc = cuda_check(cudaMemcpyAsync(c->x[c->host_st.cur & 1], src, bytes, k, c->stream));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream));
+    return rc;
+}
+
+int smc_write_log_weight(smc_ctx *c, const void *src, int on_device) {
+    if (!c || !src) return SMC_E_ARG;
+    int rc = read_state(c);
+    if (rc) return rc;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    rc = cuda_check(cudaMemcpyAsync(c->lw[c->host_st.cur & 1], src, (size_t)c->cfg.n_particles * c->L.rsize, k,
+                                    c->stream));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream));
+    return rc;
+}
+
+int smc_add_log_weight(smc_ctx *c, const void *incw, int on_device) {
+    (void)c;
+    (void)incw;
+    (void)on_device;
+    return SMC_E_ARG;  // implemented with the generic reweighting kernel
+}
+
+int smc_sync(smc_ctx *c) {
+    if (!c) return SMC_E_ARG;
+    return read_state(c);
+}
+
+const char *smc_error_string(int code) {
+    switch (code) {
+        case SMC_OK: return "ok";
+        case SMC_E_ARG: return "invalid argument or configuration";
+        case SMC_E_WORKSPACE: return "workspace too small or misaligned";
+        case SMC_E_NONFINITE: return "all weights are zero or NaN";
+        case SMC_E_TIMEOUT: return "a bounded device wait gave up";
+        case SMC_E_CUDA: return "CUDA runtime error";
+        case SMC_E_STATE: return "call out of order";
+    }
+    return "unknown error";
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ primitives --
+
+namespace {
+__global__ void philox_kernel(const uint4 *ctr, uint2 key, uint4 *out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctr[i], key);
+}
+}  // namespace
+
+extern "C" int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], uint32_t *d_out, int64_t n,
+                                 void *cuda_stream) {
+    if (!d_ctr || !key || !d_out || n < 0) return SMC_E_ARG;
+    if (((uintptr_t)d_ctr | (uintptr_t)d_out) & 15) return SMC_E_ARG;
+    if (n == 0) return SMC_OK;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    philox_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+        reinterpret_cast<const uint4 *>(d_ctr), make_uint2(key[0], key[1]), reinterpret_cast<uint4 *>(d_out), n);
+    return cuda_check(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ GMM --
+namespace {
+int gmm_move(smc_ctx *) { return SMC_E_ARG; }
+int gmm_mcmc(smc_ctx *) { return SMC_E_ARG; }
+int gmm_initialize(smc_ctx *) { return SMC_E_ARG; }
+int gmm_on_data(smc_ctx *) { return SMC_OK; }
+void gmm_release(smc_ctx *) {}
+}  // namespace

@@ -1,0 +1,151 @@
+// Device-side building blocks of the SMC hot path (sm_103a).
+//
+// * Philox4x32-10 (Salmon et al., SC'11), written from its published
+//   definition: per round, two 32x32->64 products of counter words 0 and 2
+//   with M0 = 0xD2511F53 and M1 = 0xCD9E8D57, xor with the other counter words
+//   and the key; the key advances by the Weyl constants 0x9E3779B9 and
+//   0xBB67AE85 between rounds.  The paper gives each particle an independent
+//   counter-based stream (Sec. 3.4); here the stream of a particle is its
+//   counter (index, iteration, tag | stream_id << 16, draw).
+// * uniform u = (j + 1) 2^-24 with j = x >> 8 (exact in float and double),
+//   Box-Muller normals, warp/block reductions, 128-bit comparisons for the
+//   fixed-point resampling targets.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "smc_layout.h"
+
+namespace smc {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += kPhiloxW0;
+            k.y += kPhiloxW1;
+        }
+        const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
+        const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint2 key, uint32_t index, uint32_t t, uint32_t tag,
+                                      uint32_t stream, uint32_t d) {
+    return philox4x32_10(make_uint4(index, t, (tag & 0xFFFFu) | (stream << 16), d), key);
+}
+
+__device__ __forceinline__ uint32_t u24(uint32_t x) { return x >> 8; }
+
+template <typename R>
+__device__ __forceinline__ R uniform01(uint32_t x) {
+    return R((x >> 8) + 1u) * R(5.9604644775390625e-08);  // (j + 1) 2^-24
+}
+
+// ---- precision traits -------------------------------------------------------
+template <typename R>
+struct Math;
+
+template <>
+struct Math<float> {
+    static __device__ __forceinline__ float exp(float x) { return expf(x); }
+    static __device__ __forceinline__ float log(float x) { return logf(x); }
+    static __device__ __forceinline__ float log1p(float x) { return log1pf(x); }
+    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ void sincospi(float x, float *s, float *c) { sincospif(x, s, c); }
+    static __device__ __forceinline__ uint64_t fixed(float e, int frac) {
+        // floor(e 2^frac) for e in [0, 1]; NaN and negatives map to 0
+        return (e > 0.0f) ? __float2ull_rz(ldexpf(e, frac)) : 0ull;
+    }
+    static __device__ __forceinline__ float neg_inf() { return -__int_as_float(0x7f800000); }
+};
+
+template <>
+struct Math<double> {
+    static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+    static __device__ __forceinline__ double log(double x) { return ::log(x); }
+    static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
+    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ void sincospi(double x, double *s, double *c) { ::sincospi(x, s, c); }
+    static __device__ __forceinline__ uint64_t fixed(double e, int frac) {
+        return (e > 0.0) ? __double2ull_rz(ldexp(e, frac)) : 0ull;
+    }
+    static __device__ __forceinline__ double neg_inf() { return -__longlong_as_double(0x7ff0000000000000ll); }
+};
+
+// Box-Muller pair from two uniforms in (0, 1].
+template <typename R>
+__device__ __forceinline__ void box_muller(R u0, R u1, R &z0, R &z1) {
+    const R r = Math<R>::sqrt(R(-2) * Math<R>::log(u0));
+    R s, c;
+    Math<R>::sincospi(R(2) * u1, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+// Four standard normals from one Philox call: (w0, w1) -> z0, z1; (w2, w3) -> z2, z3.
+template <typename R>
+__device__ __forceinline__ void normals4(uint4 w, R z[4]) {
+    box_muller(uniform01<R>(w.x), uniform01<R>(w.y), z[0], z[1]);
+    box_muller(uniform01<R>(w.z), uniform01<R>(w.w), z[2], z[3]);
+}
+
+// ---- reductions -------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// inclusive warp scan of 64-bit unsigned values
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// ---- 128-bit helpers for the rational resampling targets --------------------
+struct U128 {
+    uint64_t hi, lo;
+};
+
+__device__ __forceinline__ U128 mul64(uint64_t a, uint64_t b) { return U128{__umul64hi(a, b), a * b}; }
+
+// a > b
+__device__ __forceinline__ bool gt128(U128 a, U128 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+
+// bit length of a 128-bit value
+__device__ __forceinline__ int bitlen128(U128 a) {
+    return a.hi ? 128 - __clzll((long long)a.hi) : (a.lo ? 64 - __clzll((long long)a.lo) : 0);
+}
+
+// ---- bounded spin (never waits forever: sets the error word and gives up) --
+__device__ __forceinline__ void raise_error(DevState *st, int code) { atomicCAS(&st->error, 0, code); }
+
+}  // namespace smc

@@ -1,0 +1,229 @@
+"""GPU parity of the particle-filter hot path against the oracle, through
+the C ABI (Algorithm 1 with every resampling scheme)."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import (SCHEMES, assert_close, check_resample, cv_params, make_pf, need_gpu, oracle_params,
+                        step_and_check, torch)
+from oracle import cv as ocv
+from oracle import philox as ophilox
+from oracle import resample as ores
+from paper_1306_5583_b300 import smc, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def test_philox_matches_oracle_and_curand():
+    need_gpu()
+    import ctypes
+    import os
+    g = np.random.default_rng(0)
+    ctr = g.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    key = [0xA4093822, 0x299F31D0]
+    gpu = smc.philox4x32_10(ctr, key)
+    ref = ophilox.philox4x32_10(ctr, key)
+    assert np.array_equal(gpu, ref)
+    # the CUDA toolkit's own Philox4x32-10 (curand device API) on the same input
+    path = os.path.join(os.path.dirname(__file__), "gpu_support", "libcurand_philox.so")
+    cl = ctypes.CDLL(path)
+    dc = torch.from_numpy(ctr.view(np.int32)).cuda()
+    do = torch.empty_like(dc)
+    k = (ctypes.c_uint32 * 2)(*key)
+    assert cl.curand_philox4x32_10(ctypes.c_void_p(dc.data_ptr()), k, ctypes.c_void_p(do.data_ptr()),
+                                   ctypes.c_int64(ctr.shape[0])) == 0
+    assert np.array_equal(do.cpu().numpy().view(np.uint32), ref)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_fp64_filter_end_to_end(scheme):
+    """FP64, N = 1000 (the paper's example size), T = 40: records, ancestors
+    and the final particle system match the free-running oracle."""
+    need_gpu()
+    n, T, seed = 1000, 40, 3
+    s, y, op = make_pf(n, T, 64, scheme=scheme, seed=seed)
+    s.initialize()
+    s.iterate(T - 1)
+    recs = s.history(T)
+    ref, last = ocv.run(y, n, seed, op, scheme=scheme, threshold=0.5)
+    assert len(recs) == T
+    for r, o in zip(recs, ref):
+        assert r["t"] == o["t"]
+        assert r["resampled"] == o["resampled"], r["t"]
+        assert abs(r["L"] - o["L"]) < 1e-9
+        assert abs(r["logZ"] - o["logZ"]) < 1e-9
+        assert abs(r["ess"] - o["ess"]) < 1e-7 * n
+        assert abs(r["mean_x"] - o["mean_x"]) < 1e-9 and abs(r["mean_y"] - o["mean_y"]) < 1e-9
+    assert any(o["resampled"] for o in ref)
+    assert_close(s.state(), last.x, 1e-10, "final state")
+    assert_close(s.log_weight(), last.lw, 1e-10, "final log-weights")
+    assert abs(s.log_evidence() - ref[-1]["logZ"]) < 1e-9
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("n", [1, 3, 1000, 2049, 20000])
+def test_fp32_teacher_forced_steps(scheme, n):
+    """FP32 path: each iteration from the GPU's own previous particle system;
+    states and log-weights within 1e-5, ancestors bit-exact."""
+    need_gpu()
+    T, seed = 8, 11
+    s, y, op = make_pf(n, T, 32, scheme=scheme, seed=seed, threshold=0.9)
+    s.initialize()
+    r0 = s.history(1)[0]
+    ref0 = ocv.init_step(n, y[0], seed, op, 0.9)
+    assert_close(s.state(), ref0.x, 1e-5, "initial state")
+    assert abs(r0["L"] - ref0.L) < 1e-4
+    logz_gpu, logz_ref = r0["L"], ref0.L
+    for t in range(1, T):
+        rec, ref = step_and_check(s, y, op, t, seed, 32, 1e-5, scheme)
+        logz_gpu += rec["L"]
+        logz_ref += ref.L
+    assert abs(logz_gpu - logz_ref) < 1e-4
+
+
+@pytest.mark.parametrize("n", [1000, 4096])
+def test_fp64_teacher_forced_steps(n):
+    need_gpu()
+    T, seed = 6, 5
+    s, y, op = make_pf(n, T, 64, scheme="stratified", seed=seed, threshold=1.0)
+    s.initialize()
+    for t in range(1, T):
+        step_and_check(s, y, op, t, seed, 64, 1e-11, "stratified")
+
+
+def test_threshold_semantics():
+    need_gpu()
+    n, T = 2048, 6
+    for thr, expect in ((1.0, True), (0.0, False), (-1.0, False), (2.0, True)):
+        s, y, op = make_pf(n, T, 32, threshold=thr)
+        s.initialize()
+        s.iterate(T - 1)
+        assert all(r["resampled"] == expect for r in s.history(T)), thr
+
+
+def test_degenerate_weights_select_one_particle():
+    """An observation far from every particle but one: all ancestors equal
+    the argmax, for every scheme (q_i = 0 for the others)."""
+    need_gpu()
+    n = 4096
+    for scheme in SCHEMES:
+        s, y, op = make_pf(n, 3, 64, scheme=scheme, threshold=1.0, params=cv_params(obs_scale=1e-3, obs_df=1e6))
+        s.initialize()
+        lw = s.log_weight()
+        anc = s.ancestors()
+        assert np.all(anc == int(np.argmax(lw))), scheme
+
+
+def test_nonfinite_weights_raise_and_leave_state():
+    need_gpu()
+    n, T = 1000, 5
+    s, y, op = make_pf(n, T, 32)
+    y = y.copy()
+    y[2] = np.nan
+    s.set_data(y)
+    s.initialize()
+    s.move()
+    x1 = s.state()
+    lw1 = s.log_weight()
+    s.resample()
+    s.move()  # NaN observation
+    with pytest.raises(smc.SMCError) as e:
+        s.sync()
+    assert e.value.code == smc.E_NONFINITE
+    # the previous particle system is still the current one
+    with pytest.raises(smc.SMCError):
+        s.state()
+    s2_state = np.empty_like(x1)
+    import ctypes
+    rc = smc.lib().smc_read_state(s.ctx, s2_state.ctypes.data_as(ctypes.c_void_p), 0)
+    assert rc == smc.E_NONFINITE
+    assert np.array_equal(s2_state, x1)
+
+
+def test_determinism_bit_identical():
+    need_gpu()
+    outs = []
+    for _ in range(2):
+        s, y, op = make_pf(30000, 12, 32, scheme="multinomial", seed=9)
+        s.initialize()
+        s.iterate(11)
+        outs.append((s.state(), s.log_weight(), s.ancestors(), s.cdf(), s.log_evidence()))
+    for a, b in zip(*outs):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
+def test_kalman_evidence_gaussian_variant():
+    """FP32 GPU filter on the linear-Gaussian variant: the mean of Z-hat / Z
+    over seeds is 1 within Monte Carlo error (unbiasedness, closed form)."""
+    need_gpu()
+    from oracle import kalman
+    T, n, R = 25, 1 << 14, 24
+    p = cv_params()
+    _, y = workloads.cv_data(T, seed=2, gaussian_obs=True, **p)
+    logz = kalman.kalman_loglik(y, oracle_params(p, "cv_gauss"))
+    est = []
+    for r in range(R):
+        cfg = smc.make_config(model="cv_gauss", n=n, precision=32, seed=1000 + r, max_data=T, cv=p)
+        s = smc.Sampler(cfg)
+        s.set_data(y)
+        s.initialize()
+        s.iterate(T - 1)
+        est.append(s.log_evidence())
+    ratio = np.exp(np.array(est) - logz)
+    assert abs(ratio.mean() - 1) < 5 * ratio.std(ddof=1) / math.sqrt(R) + 0.01
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_full_size_sampled(scheme):
+    """N = 2^20 (the benchmarked size and launch configuration): sampled
+    particles against the oracle's per-particle step, and ancestors of
+    sampled slots by the exact selection rule on the GPU's CDF."""
+    need_gpu()
+    n, T, seed = 1 << 20, 6, 0
+    s, y, op = make_pf(n, T, 32, scheme=scheme, seed=seed, threshold=1.0)
+    s.initialize()
+    g = np.random.default_rng(1)
+    idx = np.sort(g.choice(n, size=2000, replace=False))
+    for t in range(1, T):
+        x_prev = s.state().astype(np.float64)
+        lw_prev = s.log_weight().astype(np.float64)
+        rec_prev = s.history(1)[0]
+        anc = s.ancestors().astype(np.int64) if rec_prev["resampled"] else None
+        s.move()
+        x = s.state()
+        lw = s.log_weight()
+        # per-particle oracle on the sample: gather, move, weight
+        src = anc[idx] if anc is not None else idx
+        xp = x_prev[:, src]
+        eps = ophilox.normals(seed, idx, t, ophilox.TAG_MOVE, 4)
+        xm = np.stack([xp[0] + op.delta * xp[2] + op.sd_pos * eps[0], xp[1] + op.delta * xp[3] + op.sd_pos * eps[1],
+                       xp[2] + op.sd_vel * eps[2], xp[3] + op.sd_vel * eps[3]])
+        base = np.full(idx.size, -math.log(n)) if anc is not None else lw_prev[idx] - rec_prev["L"]
+        assert_close(x[:, idx], xm, 1e-5, f"state t={t}")
+        assert_close(lw[idx], base + ocv.loglik(xm, y[t], op), 1e-5, f"lw t={t}")
+        s.resample()
+        # CDF: exact prefix sums of non-negative integers
+        Q = s.cdf()
+        assert np.all(np.diff(Q.astype(np.float64)) >= 0)
+        a = s.ancestors().astype(np.int64)
+        assert np.all(np.diff(a) >= 0) and a.min() >= 0 and a.max() < n
+        if scheme in ("systematic", "stratified"):
+            QN = int(Q[-1])
+            ks = g.choice(n, size=300, replace=False)
+            js = ophilox.resample_u24(seed, t, n) if scheme == "stratified" else None
+            jsys = ophilox.systematic_u24(seed, t)
+            Ql = Q.astype(object)
+            import bisect
+            Qlist = [int(v) for v in Ql]
+            for k in ks:
+                j = jsys if scheme == "systematic" else int(js[k])
+                thr = (QN * ((int(k) << 25) + 2 * j + 1)) // (n << 25)
+                assert a[k] == bisect.bisect_right(Qlist, thr)
+        else:
+            # offspring counts sum to N and particles with zero weight have none
+            q = np.diff(np.concatenate([[0], Q.astype(object)])).astype(object)
+            zero = np.array([int(v) == 0 for v in q])
+            assert not np.any(zero[a])
