@@ -60,6 +60,9 @@ extern "C" {
 #define SMC_SYSTEMATIC 2
 #define SMC_RESIDUAL 3
 
+/* config flags */
+#define SMC_FLAG_KEEP_CDF 1u  /* store the fixed-point CDF of each resampling step (smc_read_cdf) */
+
 /* models */
 #define SMC_MODEL_CV 0        /* Sec. 5.1: constant-velocity tracking, Student-t observations */
 #define SMC_MODEL_CV_GAUSS 1  /* same with Gaussian observations (Kalman closed form) */
@@ -101,7 +104,7 @@ typedef struct {
     double threshold;     /* resample when ESS < threshold * N; >= 1 always, <= 0 never */
     uint64_t seed;        /* Philox key */
     uint32_t stream_id;   /* Philox stream (counter word 2, high 16 bits) */
-    uint32_t reserved;
+    uint32_t flags;       /* SMC_FLAG_* */
     int64_t max_data;     /* capacity for observations: CV rows (Y_0..), GMM points */
     smc_cv_params cv;
     smc_gmm_params gmm;
@@ -194,7 +197,8 @@ int smc_iteration(const smc_ctx *ctx, int32_t *t);
  * d = 3r + 2, rows mu_1..r, lambda_1..r, omega_1..r, log-prior,
  * log-likelihood).  Log-weights: N values (raw lw_t).  Ancestors: N int32
  * (sorted; valid after a resampling step).  CDF: N uint64 fixed-point
- * inclusive prefix sums.  Records: the last min(count, available) records in
+ * inclusive prefix sums (kept only with SMC_FLAG_KEEP_CDF; otherwise
+ * smc_read_cdf returns SMC_E_STATE).  Records: the last min(count, available) records in
  * iteration order.  All synchronise. */
 int smc_state_dim(const smc_ctx *ctx, int32_t *d);
 int smc_read_state(smc_ctx *ctx, void *dst, int on_device);

@@ -1,12 +1,501 @@
-// Gaussian-mixture SMC sampler kernels (Sec. 5.2).
+// Tempered SMC sampler for the Bayesian Gaussian mixture (Sec. 5.2,
+// Algorithm 2).
+//
+// Kernels per iteration t:
+//   gmm_reweight_kernel  lw_t = log W_{t-1} + (alpha_t - alpha_{t-1}) l(theta_{t-1})
+//                        (eq:inc_weight_mcmc), normaliser = standard evidence
+//                        increment (eq:smc-ds in Algorithm 2's form), ESS test;
+//   resampling           the shared fixed-point CDF / selection kernels;
+//   gmm_mcmc_kernel      gather by the ancestors, then the three random-walk
+//                        Metropolis blocks on mu, log lambda and the weights'
+//                        log-ratios at alpha_t (Sec. 5.2.1 list), then the
+//                        path-sampling integrand U_t = sum_i W_t,i l(theta_t,i)
+//                        (eq:path_import) and the trapezoid update (eq:path_est).
+//
+// The likelihood l(theta) = sum_k log sum_j omega_j sqrt(lambda_j / 2 pi)
+// exp(-lambda_j (y_k - mu_j)^2 / 2) is the hot loop: the data tile is staged in
+// shared memory by a bulk (TMA) copy, four lanes share one particle (each
+// takes every fourth datum), each datum is a log-sum-exp over the components
+// in base 2 (MUFU ex2), and the per-datum logs are folded into one lg2 per
+// group of 8 data (the sum of logs is the log of the product; every factor
+// is in [1, r]).  Group sums are accumulated with Kahan compensation in
+// float, the quad's partial sums in float64.
 #pragma once
 
 #include "weight_reduce.cuh"
 
 namespace smc {
 
-constexpr bool kGmmEnabled = false;
+constexpr bool kGmmEnabled = true;
 constexpr int kGmmMaxComp = 8;
 constexpr int64_t kGmmMaxData = 8192;
+constexpr int kQuad = 4;                      // lanes per particle in the likelihood loop
+constexpr int kGmmGroup = 8;                  // data per lg2
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr double kLog2e = 1.44269504088896340736;
+
+template <typename R>
+struct GmmArgs {
+    int64_t n;
+    int32_t nd;             // data points
+    const R *y;             // data (16-byte aligned, padded to a multiple of 16 bytes)
+    R *x[2];                // state buffers; row j at x[b] + j * n
+    R *lw[2];
+    const int32_t *anc;
+    const double *alpha;    // alpha_t, t = 0..T
+    int32_t T;
+    smc_record *rec;
+    int32_t rec_cap;
+    DevState *st;
+    Partial *part;
+    double log_n;
+    double threshold;
+    // prior: lp = lp_const + sum_j [-(mu_j - mu0)^2 / (2 sd0^2) + (a - 1) log lambda_j - b lambda_j]
+    double mu0, sd0, inv_sd0, lp_const, shape_m1, rate;
+    double half_nd_log2pi;  // nd log(2 pi) / 2
+    uint2 key;
+    uint32_t stream;
+};
+
+// ---- per-datum math in base 2 ---------------------------------------------
+template <typename R>
+struct Base2;
+
+template <>
+struct Base2<float> {
+    static __device__ __forceinline__ float ex2(float x) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    static __device__ __forceinline__ float lg2(float x) {
+        float y;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+};
+
+template <>
+struct Base2<double> {
+    static __device__ __forceinline__ double ex2(double x) { return ::exp2(x); }
+    static __device__ __forceinline__ double lg2(double x) { return ::log2(x); }
+};
+
+// Kahan-compensated accumulator
+template <typename R>
+struct Kahan {
+    R s = 0, c = 0;
+    __device__ __forceinline__ void add(R v) {
+        const R y = v - c;
+        const R t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+// Log-likelihood of one particle: lanes q = 0..3 of a quad each take data
+// k = q, q + 4, ...; returns the full l(theta) (float64) in all four lanes.
+template <typename R, int NC>
+__device__ __forceinline__ double gmm_loglik_quad(const R (&mu)[NC], const R (&lam)[NC], const R (&om)[NC],
+                                                  const R *__restrict__ ys, int nd, int q, double half_nd_log2pi) {
+    R c2[NC], h2[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        // log2(omega_j sqrt(lambda_j)) and lambda_j log2(e) / 2
+        c2[j] = Base2<R>::lg2(om[j]) + R(0.5) * Base2<R>::lg2(lam[j]);
+        h2[j] = R(0.5 * kLog2e) * lam[j];
+    }
+    Kahan<R> acc;
+    int k = q;
+    while (k < nd) {
+        R msum = 0, prod = 1;
+#pragma unroll 1
+        for (int g = 0; g < kGmmGroup && k < nd; ++g, k += kQuad) {
+            const R yk = ys[k];
+            R a[NC];
+            R m = -INFINITY;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                const R d = yk - mu[j];
+                a[j] = c2[j] - h2[j] * d * d;
+                m = fmax(m, a[j]);
+            }
+            R s = 0;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) s += Base2<R>::ex2(a[j] - m);
+            msum += m;
+            prod *= s;
+        }
+        acc.add(msum + Base2<R>::lg2(prod));
+    }
+    double v = double(acc.s) - double(acc.c);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    return v * kLn2 - half_nd_log2pi;
+}
+
+template <typename R, int NC>
+__device__ __forceinline__ double gmm_log_prior(const GmmArgs<R> &a, const R (&mu)[NC], const R (&lam)[NC],
+                                                const R (&om)[NC]) {
+    double lp = a.lp_const;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const double z = (double(mu[j]) - a.mu0) * a.inv_sd0;
+        lp += -0.5 * z * z - a.rate * double(lam[j]);
+        if (a.shape_m1 != 0.0) lp += a.shape_m1 * double(Math<R>::log(lam[j]));
+        bad |= !(lam[j] > R(0)) || !(om[j] >= R(0));
+    }
+    return bad ? -INFINITY : lp;
+}
+
+// r standard normals from draws 0 and 1 of (index, t, tag)
+template <typename R, int NC>
+__device__ __forceinline__ void gmm_normals(uint2 key, uint32_t i, uint32_t t, uint32_t tag, uint32_t stream,
+                                            R (&z)[NC]) {
+    R w[8];
+    normals4<R>(draw(key, i, t, tag, stream, 0u), w);
+    if (NC > 4) normals4<R>(draw(key, i, t, tag, stream, 1u), w + 4);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) z[j] = w[j];
+}
+
+template <typename R>
+__device__ __forceinline__ R mh_log_uniform(uint2 key, uint32_t i, uint32_t t, uint32_t tag, uint32_t stream) {
+    return Math<R>::log(uniform01<R>(draw(key, i, t, tag, stream, DRAW_MH_UNIFORM).x));
+}
+
+// Bulk-copy (TMA) the data into shared memory; bounded wait on the mbarrier.
+__device__ __forceinline__ void stage_data(void *smem_dst, const void *gsrc, uint32_t bytes, DevState *st) {
+    __shared__ alignas(8) unsigned long long s_mbar;
+    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+            "l"(gsrc), "r"(bytes), "r"(mbar)
+            : "memory");
+    }
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(mbar)
+            : "memory");
+    }
+    if (!done) raise_error(st, SMC_E_TIMEOUT);
+    __syncthreads();
+}
+
+// ---- state rows -------------------------------------------------------------
+template <typename R, int NC>
+struct Theta {
+    R mu[NC], lam[NC], om[NC];
+    R lp, ll;
+};
+
+template <typename R, int NC>
+__device__ __forceinline__ void load_theta(const R *x, int64_t n, int64_t i, Theta<R, NC> &th) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        th.mu[j] = x[(int64_t)j * n + i];
+        th.lam[j] = x[(int64_t)(NC + j) * n + i];
+        th.om[j] = x[(int64_t)(2 * NC + j) * n + i];
+    }
+    th.lp = x[(int64_t)(3 * NC) * n + i];
+    th.ll = x[(int64_t)(3 * NC + 1) * n + i];
+}
+
+template <typename R, int NC>
+__device__ __forceinline__ void store_theta(R *x, int64_t n, int64_t i, const Theta<R, NC> &th) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        x[(int64_t)j * n + i] = th.mu[j];
+        x[(int64_t)(NC + j) * n + i] = th.lam[j];
+        x[(int64_t)(2 * NC + j) * n + i] = th.om[j];
+    }
+    x[(int64_t)(3 * NC) * n + i] = th.lp;
+    x[(int64_t)(3 * NC + 1) * n + i] = th.ll;
+}
+
+// ---- init: theta ~ prior, equal weights, U_0 --------------------------------
+template <typename R, int NC>
+__global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    const R *ys = reinterpret_cast<const R *>(s_raw);
+    DevState *st = a.st;
+    if (*(volatile int32_t *)&st->error) return;
+    stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st);
+    const int q = threadIdx.x & (kQuad - 1);
+    const int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kQuad;
+    const bool active = i < a.n;
+    const int64_t ii = active ? i : a.n - 1;  // inactive lanes compute a copy, keep the shuffles full
+    Theta<R, NC> th;
+    {
+        R z[NC];
+        gmm_normals<R, NC>(a.key, (uint32_t)ii, 0u, TAG_INIT, a.stream, z);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) th.mu[j] = R(a.mu0) + R(a.sd0) * z[j];
+        const int shape = (int)a.shape_m1 + 1;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            R e = 0;
+            for (int m = 0; m < shape; ++m) {
+                const int idx = j * shape + m;
+                const uint4 w = draw(a.key, (uint32_t)ii, 0u, TAG_INIT, a.stream, 8u + (uint32_t)(idx >> 2));
+                const uint32_t ww = (idx & 3) == 0 ? w.x : (idx & 3) == 1 ? w.y : (idx & 3) == 2 ? w.z : w.w;
+                e -= Math<R>::log(uniform01<R>(ww));
+            }
+            th.lam[j] = e / R(a.rate);
+        }
+        R E[NC], sum = 0;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const uint4 w = draw(a.key, (uint32_t)ii, 0u, TAG_INIT, a.stream, 64u + (uint32_t)(j >> 2));
+            const uint32_t ww = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
+            E[j] = -Math<R>::log(uniform01<R>(ww));
+            sum += E[j];
+        }
+#pragma unroll
+        for (int j = 0; j < NC; ++j) th.om[j] = E[j] / sum;
+    }
+    th.lp = R(gmm_log_prior<R, NC>(a, th.mu, th.lam, th.om));
+    const double ll = gmm_loglik_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi);
+    th.ll = R(ll);
+    const int cur = st->cur, cur_lw = st->cur_lw;
+    const R lw0 = R(-a.log_n);
+    if (active && q == 0) {
+        store_theta<R, NC>(a.x[cur ^ 1], a.n, i, th);
+        a.lw[cur_lw ^ 1][i] = lw0;
+    }
+    R lwv[1] = {(active && q == 0) ? lw0 : Math<R>::neg_inf()};
+    R h0[1] = {th.ll}, zero[1] = {R(0)};
+    block_partial<R, 1>(lwv, h0, zero, zero, &a.part[blockIdx.x]);
+    Combined c;
+    if (!last_block_combine<R>(st, a.part, &c)) return;
+    if (threadIdx.x == 0) {
+        FinalizeArgs f{st, a.rec, a.rec_cap, 0, 0, a.n, a.threshold, 0.0};
+        double L;
+        if (finalize_weights(f, c, &L)) {
+            const double U0 = c.Sa / c.S1;
+            smc_record *r = &a.rec[0];
+            r->path_u = U0;
+            r->path_log_z = 0.0;
+            r->log_evidence = 0.0;  // the prior is normalised: log Z_0 = 0
+            st->log_evidence = 0.0;
+            st->path_u = U0;
+            st->path_log_z = 0.0;
+            st->alpha = 0.0;
+            st->base_shift = L;
+            st->t = 0;
+            st->cur = cur ^ 1;
+            st->cur_lw = cur_lw ^ 1;
+            st->ready = 0;
+            st->gathered = 0;
+            st->accept[0] = st->accept[1] = st->accept[2] = 0;
+        }
+    }
+}
+
+// ---- reweight: lw_t = log W_{t-1} + dalpha l ---------------------------------
+template <typename R, int NC>
+__global__ void __launch_bounds__(kBlock) gmm_reweight_kernel(GmmArgs<R> a) {
+    DevState *st = a.st;
+    if (*(volatile int32_t *)&st->error) return;
+    const int32_t t = st->t + 1;
+    const double a_t = a.alpha[t], a_p = a.alpha[t - 1];
+    const R dal = R(a_t - a_p);
+    const Shift<R> base(st->base_shift);
+    const int cur = st->cur, cur_lw = st->cur_lw;
+    const R *lw_in = a.lw[cur_lw];
+    R *lw_out = a.lw[cur_lw ^ 1];
+    const R *ll = a.x[cur] + (int64_t)(3 * NC + 1) * a.n;
+    R lwv[kPfItems], zero[kPfItems];
+    const int64_t b0 = (int64_t)blockIdx.x * kPfTile + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kPfItems; ++j) {
+        const int64_t i = b0 + j * kBlock;
+        lwv[j] = Math<R>::neg_inf();
+        zero[j] = R(0);
+        if (i < a.n) {
+            lwv[j] = base.sub_from(lw_in[i]) + dal * ll[i];
+            lw_out[i] = lwv[j];
+        }
+    }
+    block_partial<R, kPfItems>(lwv, zero, zero, zero, &a.part[blockIdx.x]);
+    Combined c;
+    if (!last_block_combine<R>(st, a.part, &c)) return;
+    if (threadIdx.x == 0) {
+        FinalizeArgs f{st, a.rec, a.rec_cap, t, 0, a.n, a.threshold, a_t};
+        double L;
+        if (finalize_weights(f, c, &L)) {
+            smc_record *r = &a.rec[t % a.rec_cap];
+            r->path_u = st->path_u;
+            r->path_log_z = st->path_log_z;
+            st->alpha = a_t;
+            st->base_shift = L;
+            st->t = t;
+            st->cur_lw = cur_lw ^ 1;
+            st->accept[0] = st->accept[1] = st->accept[2] = 0;
+        }
+    }
+}
+
+// ---- mcmc: gather, three Metropolis blocks, path sampling -------------------
+template <typename R, int NC>
+__global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    __shared__ uint32_t s_acc[3];
+    const R *ys = reinterpret_cast<const R *>(s_raw);
+    DevState *st = a.st;
+    if (*(volatile int32_t *)&st->error) return;
+    if (threadIdx.x < 3) s_acc[threadIdx.x] = 0;
+    stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st);
+    const int32_t t = st->t;
+    const double a_t = a.alpha[t], a_p = (t > 0) ? a.alpha[t - 1] : 0.0;
+    const double aclamp = fmax(a_t, 0.02);
+    const R s_mu = R(0.15 / aclamp);
+    const R s_lam = R((1.0 + sqrt(1.0 / aclamp)) * 0.15);
+    const R s_om = R((1.0 + sqrt(1.0 / aclamp)) * 0.2);
+    const bool gather = st->ready != 0;
+    const int cur = st->cur, cur_lw = st->cur_lw;
+    const int q = threadIdx.x & (kQuad - 1);
+    const int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kQuad;
+    const bool active = i < a.n;
+    const int64_t ii = active ? i : a.n - 1;
+    const int64_t src = gather ? (int64_t)__ldg(&a.anc[ii]) : ii;
+    Theta<R, NC> th;
+    load_theta<R, NC>(a.x[cur], a.n, src, th);
+    double ll = double(th.ll), lp = double(th.lp);
+    uint32_t acc_mask = 0;
+    // block 1: mu
+    {
+        R z[NC], mu2[NC];
+        gmm_normals<R, NC>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_MU, a.stream, z);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) mu2[j] = th.mu[j] + s_mu * z[j];
+        const double lp2 = gmm_log_prior<R, NC>(a, mu2, th.lam, th.om);
+        const double ll2 = gmm_loglik_quad<R, NC>(mu2, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi);
+        const double delta = (lp2 + a_t * ll2) - (lp + a_t * ll);
+        const R lu = mh_log_uniform<R>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_MU, a.stream);
+        if (double(lu) <= delta) {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) th.mu[j] = mu2[j];
+            lp = lp2;
+            ll = ll2;
+            acc_mask |= 1u;
+        }
+    }
+    // block 2: log lambda
+    {
+        R z[NC], lam2[NC];
+        gmm_normals<R, NC>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_LAMBDA, a.stream, z);
+        double jac = 0;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const R dz = s_lam * z[j];
+            lam2[j] = Math<R>::exp(Math<R>::log(th.lam[j]) + dz);
+            jac += double(dz);
+        }
+        const double lp2 = gmm_log_prior<R, NC>(a, th.mu, lam2, th.om);
+        const double ll2 = gmm_loglik_quad<R, NC>(th.mu, lam2, th.om, ys, a.nd, q, a.half_nd_log2pi);
+        const double delta = (lp2 + a_t * ll2) - (lp + a_t * ll) + jac;
+        const R lu = mh_log_uniform<R>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_LAMBDA, a.stream);
+        if (double(lu) <= delta) {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) th.lam[j] = lam2[j];
+            lp = lp2;
+            ll = ll2;
+            acc_mask |= 2u;
+        }
+    }
+    // block 3: additive log-ratios of the weights
+    if (NC > 1) {
+        R z[NC], om2[NC];
+        gmm_normals<R, NC>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_WEIGHT, a.stream, z);
+        R v[NC];
+        R vmax = 0;  // the last log-ratio is 0
+#pragma unroll
+        for (int j = 0; j < NC - 1; ++j) {
+            v[j] = Math<R>::log(th.om[j] / th.om[NC - 1]) + s_om * z[j];
+            vmax = fmax(vmax, v[j]);
+        }
+        v[NC - 1] = 0;
+        R sum = 0;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            om2[j] = Math<R>::exp(v[j] - vmax);
+            sum += om2[j];
+        }
+        double jac = 0;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            om2[j] = om2[j] / sum;
+            jac += double(Math<R>::log(om2[j])) - double(Math<R>::log(th.om[j]));
+        }
+        const double lp2 = gmm_log_prior<R, NC>(a, th.mu, th.lam, om2);
+        const double ll2 = gmm_loglik_quad<R, NC>(th.mu, th.lam, om2, ys, a.nd, q, a.half_nd_log2pi);
+        const double delta = (lp2 + a_t * ll2) - (lp + a_t * ll) + jac;
+        const R lu = mh_log_uniform<R>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_WEIGHT, a.stream);
+        if (double(lu) <= delta) {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) th.om[j] = om2[j];
+            lp = lp2;
+            ll = ll2;
+            acc_mask |= 4u;
+        }
+    } else {
+        acc_mask |= 4u;
+    }
+    th.lp = R(lp);
+    th.ll = R(ll);
+    R lwi = R(-a.log_n);
+    if (active && q == 0) {
+        store_theta<R, NC>(a.x[cur ^ 1], a.n, i, th);
+        if (gather) a.lw[cur_lw][i] = lwi;  // equal weights after resampling
+        else lwi = a.lw[cur_lw][i];
+        atomicAdd(&s_acc[0], acc_mask & 1u);
+        atomicAdd(&s_acc[1], (acc_mask >> 1) & 1u);
+        atomicAdd(&s_acc[2], (acc_mask >> 2) & 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        if (s_acc[threadIdx.x]) atomicAdd(&st->accept[threadIdx.x], s_acc[threadIdx.x]);
+        __threadfence();
+    }
+    R lwv[1] = {(active && q == 0) ? lwi : Math<R>::neg_inf()};
+    R h0[1] = {th.ll}, zero[1] = {R(0)};
+    block_partial<R, 1>(lwv, h0, zero, zero, &a.part[blockIdx.x]);
+    Combined c;
+    if (!last_block_combine<R>(st, a.part, &c)) return;
+    if (threadIdx.x == 0) {
+        smc_record *r = &a.rec[t % a.rec_cap];
+        if (!(c.S1 > 0.0)) {
+            raise_error(st, SMC_E_NONFINITE);
+            r->status = SMC_E_NONFINITE;
+            st->ticket = 0;
+            return;
+        }
+        st->ticket = 0;
+        const double U = c.Sa / c.S1;
+        const double plz = st->path_log_z + 0.5 * (a_t - a_p) * (U + st->path_u);
+        r->path_u = U;
+        r->path_log_z = plz;
+        for (int b = 0; b < 3; ++b) r->accept[b] = double(*(volatile uint32_t *)&st->accept[b]) / double(a.n);
+        st->path_u = U;
+        st->path_log_z = plz;
+        st->cur = cur ^ 1;
+        if (gather) st->base_shift = 0.0;
+        st->gathered = gather ? 1 : 0;
+        st->ready = 0;
+    }
+}
 
 }  // namespace smc

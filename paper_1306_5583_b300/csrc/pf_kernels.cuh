@@ -35,21 +35,18 @@ struct PfArgs {
     uint32_t stream;
 };
 
+// log g(Y_t | X_t): full Student-t (or Gaussian) density of both position
+// coordinates.  FP32 uses log(1 + a) on the MUFU pipe (absolute error of a
+// few 1e-7, well inside the 1e-5 tolerance of the FP32 path).
 template <typename R>
 __device__ __forceinline__ R cv_loglik(const PfArgs<R> &a, R yx, R yy, R px, R py) {
     const R zx = (yx - px) * a.inv_scale, zy = (yy - py) * a.inv_scale;
     if (a.gaussian) return a.ll_const - R(0.5) * (zx * zx + zy * zy);
-    return a.ll_const - a.half_nu1 * (Math<R>::log1p(zx * zx * a.inv_nu) + Math<R>::log1p(zy * zy * a.inv_nu));
+    if constexpr (sizeof(R) == 4)
+        return a.ll_const - a.half_nu1 * (__logf(1.0f + zx * zx * a.inv_nu) + __logf(1.0f + zy * zy * a.inv_nu));
+    else
+        return a.ll_const - a.half_nu1 * (Math<R>::log1p(zx * zx * a.inv_nu) + Math<R>::log1p(zy * zy * a.inv_nu));
 }
-
-// Subtract a float64 scalar from a value of precision R with one rounding
-// less than a plain conversion (hi/lo split of the scalar).
-template <typename R>
-struct Shift {
-    R hi, lo;
-    __device__ __forceinline__ explicit Shift(double v) : hi(R(v)), lo(R(v - double(R(v)))) {}
-    __device__ __forceinline__ R sub_from(R x) const { return (x - hi) - lo; }
-};
 
 template <typename R>
 __global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
@@ -61,38 +58,47 @@ __global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
     const Shift<R> Lprev(st->log_norm);
     const R yx = R(a.obs[2 * t]), yy = R(a.obs[2 * t + 1]);
     const R base_eq = R(-a.log_n);
-    const R *__restrict__ lw_in = a.lw[cur];
-    R *__restrict__ lw_out = a.lw[cur ^ 1];
+    const int cur_lw = st->cur_lw;
+    const R *__restrict__ lw_in = a.lw[cur_lw];
+    R *__restrict__ lw_out = a.lw[cur_lw ^ 1];
+    const R *__restrict__ x0s = a.x[cur][0];
+    const R *__restrict__ x1s = a.x[cur][1];
+    const R *__restrict__ x2s = a.x[cur][2];
+    const R *__restrict__ x3s = a.x[cur][3];
+    R *__restrict__ x0d = a.x[cur ^ 1][0];
+    R *__restrict__ x1d = a.x[cur ^ 1][1];
+    R *__restrict__ x2d = a.x[cur ^ 1][2];
+    R *__restrict__ x3d = a.x[cur ^ 1][3];
+    const uint32_t n = (uint32_t)a.n;
 
     R lwv[kPfItems], px[kPfItems], py[kPfItems], zero[kPfItems];
-    const int64_t base = (int64_t)blockIdx.x * kPfTile + threadIdx.x;
+    const uint32_t base = blockIdx.x * (uint32_t)kPfTile + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < kPfItems; ++j) {
-        const int64_t i = base + j * kBlock;
+        const uint32_t i = base + (uint32_t)(j * kBlock);
         lwv[j] = Math<R>::neg_inf();
         px[j] = py[j] = zero[j] = R(0);
-        if (i < a.n) {
+        if (i < n) {
             R s0, s1, s2, s3, z[4];
             if (t == 0) {
-                normals4<R>(draw(a.key, (uint32_t)i, 0u, TAG_INIT, a.stream, 0u), z);
+                normals4_fast<R>(draw(a.key, i, 0u, TAG_INIT, a.stream, 0u), z);
                 s0 = a.sd_pos0 * z[0];
                 s1 = a.sd_pos0 * z[1];
                 s2 = a.sd_vel0 * z[2];
                 s3 = a.sd_vel0 * z[3];
             } else {
-                const int64_t src = gather ? (int64_t)__ldg(&a.anc[i]) : i;
-                const R x0 = a.x[cur][0][src], x1 = a.x[cur][1][src];
-                const R x2 = a.x[cur][2][src], x3 = a.x[cur][3][src];
-                normals4<R>(draw(a.key, (uint32_t)i, (uint32_t)t, TAG_MOVE, a.stream, 0u), z);
-                s0 = x0 + a.delta * x2 + a.sd_pos * z[0];
-                s1 = x1 + a.delta * x3 + a.sd_pos * z[1];
-                s2 = x2 + a.sd_vel * z[2];
-                s3 = x3 + a.sd_vel * z[3];
+                const uint32_t src = gather ? (uint32_t)__ldg(&a.anc[i]) : i;
+                const R v0 = x0s[src], v1 = x1s[src], v2 = x2s[src], v3 = x3s[src];
+                normals4_fast<R>(draw(a.key, i, (uint32_t)t, TAG_MOVE, a.stream, 0u), z);
+                s0 = v0 + a.delta * v2 + a.sd_pos * z[0];
+                s1 = v1 + a.delta * v3 + a.sd_pos * z[1];
+                s2 = v2 + a.sd_vel * z[2];
+                s3 = v3 + a.sd_vel * z[3];
             }
-            a.x[cur ^ 1][0][i] = s0;
-            a.x[cur ^ 1][1][i] = s1;
-            a.x[cur ^ 1][2][i] = s2;
-            a.x[cur ^ 1][3][i] = s3;
+            x0d[i] = s0;
+            x1d[i] = s1;
+            x2d[i] = s2;
+            x3d[i] = s3;
             const R b = (t == 0 || gather) ? base_eq : Lprev.sub_from(lw_in[i]);
             lwv[j] = b + cv_loglik(a, yx, yy, s0, s1);
             lw_out[i] = lwv[j];
@@ -109,6 +115,7 @@ __global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
         if (finalize_weights(f, c, &L)) {
             st->t = t;
             st->cur = cur ^ 1;
+            st->cur_lw = cur_lw ^ 1;
             st->ready = 0;
         }
     }

@@ -1,154 +1,27 @@
 // Resampling (Sec. 2.1, eq:resample; Douc et al. 2005 schemes; copy_from
 // convention of Sec. 4.1.2) on exact 64-bit fixed-point weights.
 //
-// Weights: q_i = floor(exp(lw_i - M) 2^F), F = 61 - ceil(log2 N), so the
-// inclusive prefix sums Q_i are exact integers below 2^62: the CDF is
-// order-independent and bit-reproducible, and the decoupled look-back scan
-// may add either predecessor aggregates or inclusive prefixes.
-// Targets are rationals P_k / D (D = N 2^25, u = (2j + 1) / 2^25):
-//   systematic  P_k = 2^25 k + 2j + 1         (one j per iteration)
-//   stratified  P_k = 2^25 k + 2j_k + 1       (j_k independent)
-//   multinomial P_k = N (2 j_(k) + 1)         (j_(k) sorted iid j's)
-// and a_k = min{ i : Q_i D > Q_N P_k }, found by binary search over CDF
-// tiles staged in shared memory.  Residual resampling keeps
-// floor(N q_i / Q_N) copies and draws the rest multinomially from the
-// remainders (multinomial residual step).
+// Weights: q_i = floor(exp(lw_i - M) 2^F), F = 61 - ceil(log2 N), so every
+// prefix sum Q_i is an exact integer below 2^62: the CDF is order-independent
+// and bit-reproducible.
+// Targets are rationals P_k / D (u = (2j + 1) / 2^25):
+//   systematic  P_k = 2^25 k + 2j + 1        D = N 2^25  (one j per iteration)
+//   stratified  P_k = 2^25 k + 2j_k + 1      D = N 2^25  (j_k independent)
+//   multinomial P_k = m (2 j_(k) + 1)        D = m 2^25  (j_(k) the sorted iid j's)
+//   expansion   P_k = k                      D = N       (offspring CDF, O_N = N)
+// and a_k = min{ i : Q_i D > Q_N P_k }.
+//
+// Scans are reduce-then-scan (no inter-block waits): a tile-sum pass, then a
+// pass in which each tile adds the sums of the tiles before it, scans its
+// own values in shared memory and, when targets are given, selects the
+// ancestors whose targets fall in its CDF range (a contiguous range of
+// outputs, found in closed form or from the bucket ends of the sorted
+// uniforms) by a search over the shared-memory CDF tile.
 #pragma once
 
 #include "smc_device.cuh"
 
 namespace smc {
-
-// ---------------------------------------------------------------- scans --
-
-__device__ __forceinline__ unsigned long long ld_status(const unsigned long long *p) {
-    return *(const volatile unsigned long long *)p;
-}
-__device__ __forceinline__ void st_status(unsigned long long *p, unsigned long long v) {
-    *(volatile unsigned long long *)p = v;
-}
-
-// Warp 0: exclusive prefix of tile `tile` from its predecessors' status
-// words.  Waits are bounded; on timeout the error word is set and the
-// missing predecessor counts as zero.
-__device__ __forceinline__ unsigned long long lookback(const unsigned long long *status, int tile,
-                                                       DevState *st) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long prefix = 0;
-    int pred = tile - 1;
-    while (true) {
-        const int idx = pred - lane;
-        unsigned long long s = kStatIncl;  // before tile 0: an inclusive zero
-        if (idx >= 0) {
-            uint32_t spins = 0;
-            s = ld_status(&status[idx]);
-            while ((s & kStatMask) == 0) {
-                if (++spins > kSpinLimit) {
-                    raise_error(st, SMC_E_TIMEOUT);
-                    s = kStatIncl;
-                    break;
-                }
-                if (spins > 64) __nanosleep(64);
-                s = ld_status(&status[idx]);
-            }
-        }
-        const unsigned incl = __ballot_sync(0xffffffffu, (s & kStatMask) == kStatIncl);
-        const int stop = incl ? __ffs(incl) - 1 : 32;
-        const unsigned long long v = (lane <= stop) ? (s & ~kStatMask) : 0ull;
-        prefix += warp_sum(v);
-        if (incl) break;
-        pred -= 32;
-    }
-    return prefix;
-}
-
-// Exact inclusive scan out(i, sum_{j <= i} gen(j)), i < n, one tile of
-// kScanTile elements per block, tiles taken in launch order from a
-// per-slot counter (so every predecessor has started: the look-back always
-// finishes).  Each launch clears its tiles' entries of the other status
-// array and the last block to finish flips the slot's parity.
-template <class Gen, class Out>
-__global__ void __launch_bounds__(kBlock) scan_kernel(Gen gen, Out out, int64_t n, ScanSlot slot, int slot_id,
-                                                      DevState *st, int gate) {
-    __shared__ unsigned long long s_v[kScanTile];
-    __shared__ unsigned long long s_warp[kBlock / 32];
-    __shared__ unsigned long long s_prefix;
-    __shared__ int s_tile;
-    if (*(volatile int32_t *)&st->error) return;
-    if (gate && !*(volatile int32_t *)&st->due) return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        const unsigned tile = atomicAdd(&st->scan_counter[slot_id], 1u);
-        if (tile == gridDim.x - 1) st->scan_counter[slot_id] = 0;
-        s_tile = (int)tile;
-    }
-    __syncthreads();
-    const int tile = s_tile;
-    const int parity = (int)(*(volatile uint32_t *)&st->scan_parity[slot_id] & 1u);
-    unsigned long long *status = slot.status[parity];
-    unsigned long long *other = slot.status[parity ^ 1];
-    Gen g = gen;
-    g.prepare(st);
-    const int64_t t0 = (int64_t)tile * kScanTile;
-#pragma unroll
-    for (int r = 0; r < kScanItems; ++r) {
-        const int64_t i = t0 + r * kBlock + tid;
-        s_v[r * kBlock + tid] = (i < n) ? g(i) : 0ull;
-    }
-    __syncthreads();
-    unsigned long long loc[kScanItems];
-    unsigned long long acc = 0;
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        acc += s_v[tid * kScanItems + j];
-        loc[j] = acc;
-    }
-    const unsigned long long winc = warp_incl_scan(acc);
-    if (lane == 31) s_warp[warp] = winc;
-    __syncthreads();
-    unsigned long long wpre = 0, agg = 0;
-#pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) {
-        const unsigned long long v = s_warp[w];
-        if (w < warp) wpre += v;
-        agg += v;
-    }
-    const unsigned long long texcl = wpre + (winc - acc);
-    if (warp == 0) {
-        unsigned long long prefix = 0;
-        if (tile == 0) {
-            if (lane == 0) st_status(&status[0], kStatIncl | agg);
-        } else {
-            if (lane == 0) st_status(&status[tile], kStatAgg | agg);
-            prefix = lookback(status, tile, st);
-            if (lane == 0) st_status(&status[tile], kStatIncl | (prefix + agg));
-        }
-        if (lane == 0) {
-            other[tile] = 0ull;
-            s_prefix = prefix;
-        }
-    }
-    __syncthreads();
-    const unsigned long long pre = s_prefix + texcl;
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j) s_v[tid * kScanItems + j] = pre + loc[j];
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kScanItems; ++r) {
-        const int64_t i = t0 + r * kBlock + tid;
-        if (i < n) out(i, s_v[r * kBlock + tid], st);
-    }
-    // the last block to finish flips the parity of this slot
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        const unsigned done = atomicAdd(&st->scan_done[slot_id], 1u);
-        if (done == gridDim.x - 1) {
-            st->scan_done[slot_id] = 0;
-            st->scan_parity[slot_id] ^= 1u;
-        }
-    }
-}
 
 // ----------------------------------------------------------- generators --
 
@@ -160,20 +33,11 @@ struct QGen {
     const R *cur_lw;
     R m;
     __device__ __forceinline__ void prepare(const DevState *st) {
-        cur_lw = lw[*(const volatile int32_t *)&st->cur];
+        cur_lw = lw[*(const volatile int32_t *)&st->cur_lw];
         m = R(*(const volatile double *)&st->max_lw);
     }
     __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
         return Math<R>::fixed(Math<R>::exp(cur_lw[i] - m), frac);
-    }
-};
-
-struct QOut {
-    unsigned long long *Q;
-    int64_t n;
-    __device__ __forceinline__ void operator()(int64_t i, unsigned long long v, DevState *st) const {
-        Q[i] = v;
-        if (i == n - 1) st->qn = v;
     }
 };
 
@@ -182,11 +46,6 @@ struct CountGen {
     const uint32_t *cnt;
     __device__ __forceinline__ void prepare(const DevState *) {}
     __device__ __forceinline__ unsigned long long operator()(int64_t i) const { return cnt[i]; }
-};
-
-struct StoreOut {
-    unsigned long long *dst;
-    __device__ __forceinline__ void operator()(int64_t i, unsigned long long v, DevState *) const { dst[i] = v; }
 };
 
 // floor(n q / qn) for q <= qn < 2^62, n < 2^31 (exact: float estimate, then
@@ -198,242 +57,348 @@ __device__ __forceinline__ unsigned long long floor_nq_over(unsigned long long n
     float est = (float(n) * float(q)) / float(qn);
     unsigned long long d = (unsigned long long)fmaxf(est, 0.0f);
     if (d > n) d = n;
-    // d * qn <= num < (d + 1) * qn
     while (d > 0 && gt128(mul64(d, qn), num)) --d;
     while (!gt128(mul64(d + 1, qn), num)) ++d;
     return d;
 }
 
-// residual: deterministic copies d_i and remainders rem_i = n q_i - d_i Q_N
+// residual resampling: deterministic copies d_i = floor(N q_i / Q_N)
+template <typename R>
 struct ResidualParts {
-    const unsigned long long *Q;
+    QGen<R> qg;
     int64_t n;
     unsigned long long qn;
-    __device__ __forceinline__ void prepare(const DevState *st) { qn = *(const volatile unsigned long long *)&st->qn; }
-    __device__ __forceinline__ unsigned long long q(int64_t i) const { return i ? Q[i] - Q[i - 1] : Q[0]; }
-    __device__ __forceinline__ unsigned long long d(int64_t i) const {
-        return floor_nq_over((unsigned long long)n, q(i), qn);
+    __device__ __forceinline__ void prepare(const DevState *st) {
+        qg.prepare(st);
+        qn = *(const volatile unsigned long long *)&st->qn;
+    }
+    __device__ __forceinline__ unsigned long long q(int64_t i) const { return qg(i); }
+    __device__ __forceinline__ unsigned long long d_of(unsigned long long qi) const {
+        return floor_nq_over((unsigned long long)n, qi, qn);
     }
 };
 
-// residual weights r_i = rem_i >> s, s = max(0, bitlen(R Q_N) - 62)
+// residual weights r_i = rem_i >> s, rem_i = N q_i - d_i Q_N,
+// s = max(0, bitlen(R Q_N) - 62)
+template <typename R>
 struct ResidualRGen {
-    ResidualParts p;
+    ResidualParts<R> p;
     int shift;
     __device__ __forceinline__ void prepare(const DevState *st) {
         p.prepare(st);
         const unsigned long long sd = *(const volatile unsigned long long *)&st->sum_d;
-        const unsigned long long R = sd < (unsigned long long)p.n ? (unsigned long long)p.n - sd : 0ull;
-        shift = max(0, bitlen128(mul64(R, p.qn)) - 62);
+        const unsigned long long Rn = sd < (unsigned long long)p.n ? (unsigned long long)p.n - sd : 0ull;
+        shift = max(0, bitlen128(mul64(Rn, p.qn)) - 62);
     }
     __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
         const unsigned long long qi = p.q(i);
-        const unsigned long long di = floor_nq_over((unsigned long long)p.n, qi, p.qn);
+        const unsigned long long di = p.d_of(qi);
         const unsigned long long rem = (unsigned long long)p.n * qi - di * p.qn;  // < Q_N, exact mod 2^64
         return rem >> shift;
     }
 };
 
-// final offspring o_i = d_i + (residual draws of i)
+// final offspring counts o_i = d_i + (residual draws of i)
+template <typename R>
 struct ResidualOGen {
-    ResidualParts p;
+    ResidualParts<R> p;
     const uint32_t *extra;
     __device__ __forceinline__ void prepare(const DevState *st) { p.prepare(st); }
-    __device__ __forceinline__ unsigned long long operator()(int64_t i) const { return p.d(i) + extra[i]; }
+    __device__ __forceinline__ unsigned long long operator()(int64_t i) const { return p.d_of(p.q(i)) + extra[i]; }
+};
+
+// ---------------------------------------------------------------- sinks --
+
+struct NoSink {
+    static constexpr bool kActive = false;
+    __device__ __forceinline__ void operator()(int64_t, unsigned long long, DevState *) const {}
+};
+
+struct StoreSink {  // inclusive prefix sums to an array (the fixed-point CDF, bucket ends)
+    static constexpr bool kActive = true;
+    unsigned long long *dst;
+    __device__ __forceinline__ void operator()(int64_t i, unsigned long long v, DevState *) const {
+        if (dst) dst[i] = v;
+    }
 };
 
 // --------------------------------------------------------------- targets --
 
-// P_k numerators for 4 consecutive outputs k4..k4+3 (k4 % 4 == 0), common
-// denominator D, and the number of outputs.
-struct SystematicTargets {
-    int64_t n;
-    uint2 key;
-    uint32_t stream;
-    unsigned long long j2p1;
-    __device__ __forceinline__ void prepare(const DevState *st) {
-        const uint32_t t = (uint32_t)*(const volatile int32_t *)&st->t;
-        j2p1 = 2ull * u24(draw(key, 0u, t, TAG_RESAMPLE, stream, 0u).x) + 1ull;
-    }
-    __device__ __forceinline__ int64_t count(const DevState *) const { return n; }
-    __device__ __forceinline__ unsigned long long denom(const DevState *) const { return (unsigned long long)n << 25; }
-    __device__ __forceinline__ void get4(int64_t k4, unsigned long long P[4]) const {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) P[j] = ((unsigned long long)(k4 + j) << 25) + j2p1;
-    }
+struct NoTargets {
+    static constexpr bool kActive = false;
+    __device__ __forceinline__ void prepare(const DevState *) {}
+    __device__ __forceinline__ int64_t count() const { return 0; }
+    __device__ __forceinline__ unsigned long long denom() const { return 1; }
+    __device__ __forceinline__ unsigned long long P(int64_t) const { return 0; }
+    __device__ __forceinline__ int64_t first_at_least(unsigned long long, unsigned long long) const { return 0; }
 };
 
 __device__ __forceinline__ uint4 resample_words(uint2 key, uint32_t stream, uint32_t t, int64_t k4) {
     return draw(key, (uint32_t)(k4 >> 2), t, TAG_RESAMPLE, stream, 0u);
 }
 
-struct StratifiedTargets {
+// j_k of resampling draw k at iteration t (word k % 4 of call k / 4)
+__device__ __forceinline__ uint32_t resample_u24_at(uint2 key, uint32_t stream, uint32_t t, int64_t k) {
+    const uint4 w = resample_words(key, stream, t, k & ~3ll);
+    const uint32_t ww = ((k & 3) == 0) ? w.x : ((k & 3) == 1) ? w.y : ((k & 3) == 2) ? w.z : w.w;
+    return u24(ww);
+}
+
+// Systematic (one u per iteration) and stratified (u_k per output) targets.
+// The first output whose target reaches X (Q_N P_k >= X D) is k0 or k0 + 1
+// with k0 = floor(X D / (Q_N 2^25)), since P_k / 2^25 lies in (k, k + 1).
+template <bool kStratified>
+struct GridTargets {
+    static constexpr bool kActive = true;
     int64_t n;
     uint2 key;
     uint32_t stream;
     uint32_t t;
-    __device__ __forceinline__ void prepare(const DevState *st) { t = (uint32_t)*(const volatile int32_t *)&st->t; }
-    __device__ __forceinline__ int64_t count(const DevState *) const { return n; }
-    __device__ __forceinline__ unsigned long long denom(const DevState *) const { return (unsigned long long)n << 25; }
-    __device__ __forceinline__ void get4(int64_t k4, unsigned long long P[4]) const {
-        const uint4 w = resample_words(key, stream, t, k4);
-        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) P[j] = ((unsigned long long)(k4 + j) << 25) + 2ull * u24(ww[j]) + 1ull;
+    unsigned long long c;  // 2j + 1 (systematic)
+    __device__ __forceinline__ void prepare(const DevState *st) {
+        t = (uint32_t)*(const volatile int32_t *)&st->t;
+        c = 2ull * u24(draw(key, 0u, t, TAG_RESAMPLE, stream, 0u).x) + 1ull;
+    }
+    __device__ __forceinline__ int64_t count() const { return n; }
+    __device__ __forceinline__ unsigned long long denom() const { return (unsigned long long)n << 25; }
+    __device__ __forceinline__ unsigned long long P(int64_t k) const {
+        const unsigned long long ck = kStratified ? 2ull * resample_u24_at(key, stream, t, k) + 1ull : c;
+        return ((unsigned long long)k << 25) + ck;
+    }
+    // first k in [0, n] with QN P_k >= X D
+    __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long QN) const {
+        const unsigned long long D = denom();
+        const unsigned __int128 z = ((unsigned __int128)X * D) / QN;
+        const int64_t k0 = (int64_t)(z >> 25);
+        if (k0 >= n) return n;
+        return gt128(mul64(X, D), mul64(QN, P(k0))) ? k0 + 1 : k0;
     }
 };
 
-// sorted j's; m = number of draws (N, or R for the residual step)
+// Sorted iid draws j_(0) <= ... <= j_(m-1) (multinomial selection, also the
+// residual step with m = R).  The rank of a threshold comes from the bucket
+// ends of the sort plus a scan of one (small) bucket.
 struct SortedTargets {
+    static constexpr bool kActive = true;
     const uint32_t *sorted;
-    int64_t n;        // used when from_residual == 0
-    int64_t n_total;  // N (for R = N - sum_d)
+    const unsigned long long *bend;  // inclusive bucket ends
+    int bucket_shift;
+    int64_t n_total;
     int from_residual;
     unsigned long long m;
     __device__ __forceinline__ void prepare(const DevState *st) {
         const unsigned long long sd = *(const volatile unsigned long long *)&st->sum_d;
         m = from_residual ? (sd < (unsigned long long)n_total ? (unsigned long long)n_total - sd : 0ull)
-                          : (unsigned long long)n;
+                          : (unsigned long long)n_total;
     }
-    __device__ __forceinline__ int64_t count(const DevState *) const { return (int64_t)m; }
-    __device__ __forceinline__ unsigned long long denom(const DevState *) const { return m << 25; }
-    __device__ __forceinline__ void get4(int64_t k4, unsigned long long P[4]) const {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t k = k4 + j;
-            P[j] = (k < (int64_t)m) ? m * (2ull * sorted[k] + 1ull) : 0ull;
-        }
+    __device__ __forceinline__ int64_t count() const { return (int64_t)m; }
+    __device__ __forceinline__ unsigned long long denom() const { return m << 25; }
+    __device__ __forceinline__ unsigned long long P(int64_t k) const { return m * (2ull * sorted[k] + 1ull); }
+    // first k with QN m (2 s_k + 1) >= X m 2^25, i.e. 2 s_k + 1 >= X 2^25 / QN,
+    // i.e. s_k >= v with v the smallest s such that 2 s + 1 >= ceil(X 2^25 / QN)
+    __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long QN) const {
+        if (m == 0) return 0;
+        const unsigned __int128 y = ((unsigned __int128)X) << 25;
+        const unsigned __int128 c = (y + QN - 1) / QN;
+        if (c > ((unsigned __int128)1 << 25)) return (int64_t)m;
+        const unsigned long long cc = (unsigned long long)c;
+        const unsigned long long v = cc / 2;
+        if (v >= (1ull << 24)) return (int64_t)m;
+        const int64_t b = (int64_t)(v >> bucket_shift);
+        int64_t lo = b ? (int64_t)bend[b - 1] : 0;
+        const int64_t hi = (int64_t)bend[b];
+        while (lo < hi && sorted[lo] < v) ++lo;
+        return lo;
     }
 };
 
-// expansion of an offspring CDF O (O_N = n): a_k = min{i : O_i > k}
+// Expansion of an offspring CDF O (O_N = N): a_k = min{i : O_i > k}.
 struct ExpandTargets {
+    static constexpr bool kActive = true;
     int64_t n;
     __device__ __forceinline__ void prepare(const DevState *) {}
-    __device__ __forceinline__ int64_t count(const DevState *) const { return n; }
-    __device__ __forceinline__ unsigned long long denom(const DevState *) const { return (unsigned long long)n; }
-    __device__ __forceinline__ void get4(int64_t k4, unsigned long long P[4]) const {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) P[j] = (unsigned long long)(k4 + j);
+    __device__ __forceinline__ int64_t count() const { return n; }
+    __device__ __forceinline__ unsigned long long denom() const { return (unsigned long long)n; }
+    __device__ __forceinline__ unsigned long long P(int64_t k) const { return (unsigned long long)k; }
+    __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long) const {
+        return (int64_t)min(X, (unsigned long long)n);
     }
 };
 
-// ------------------------------------------------------------ selection --
+// ----------------------------------------------------------------- outputs --
 
 struct AncOut {
     int32_t *anc;
-    __device__ __forceinline__ void operator()(int64_t k, int64_t a) const { anc[k] = (int32_t)a; }
+    __device__ __forceinline__ void operator()(int64_t k, int32_t a) const { anc[k] = a; }
 };
 
 struct CountOut {  // residual draws: histogram of the selected particles
     uint32_t *extra;
-    __device__ __forceinline__ void operator()(int64_t, int64_t a) const { atomicAdd(&extra[a], 1u); }
+    __device__ __forceinline__ void operator()(int64_t, int32_t a) const { atomicAdd(&extra[a], 1u); }
 };
 
-// first i in [lo, hi) with Q_i D > target (hi when none)
-__device__ __forceinline__ int64_t upper_bound_global(const unsigned long long *Q, int64_t lo, int64_t hi,
-                                                      unsigned long long D, U128 target) {
-    while (lo < hi) {
-        const int64_t mid = lo + ((hi - lo) >> 1);
-        if (gt128(mul64(__ldcg(&Q[mid]), D), target)) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo;
+// ---------------------------------------------------------------- kernels --
+
+__device__ __forceinline__ bool gated_out(DevState *st, int gate) {
+    if (*(volatile int32_t *)&st->error) return true;
+    return gate && !*(volatile int32_t *)&st->due;
 }
 
-__device__ __forceinline__ int upper_bound_smem(const unsigned long long *s, int lo, int hi, unsigned long long D,
-                                                U128 target) {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (gt128(mul64(s[mid], D), target)) hi = mid;
-        else lo = mid + 1;
+// Sum of gen(i) over each tile of kScanTile elements -> tsum[tile]; the last
+// block writes the exact total to *total.
+template <class Gen>
+__global__ void __launch_bounds__(kBlock) tile_reduce_kernel(Gen gen, int64_t n, unsigned long long *tsum,
+                                                             unsigned long long *total, uint32_t *ticket,
+                                                             DevState *st, int gate) {
+    __shared__ unsigned long long s_w[kBlock / 32];
+    __shared__ bool s_last;
+    if (gated_out(st, gate)) return;
+    Gen g = gen;
+    g.prepare(st);
+    const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const int64_t i = t0 + r * kBlock + threadIdx.x;
+        if (i < n) acc += g(i);
     }
-    return lo;
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) s += s_w[w];
+        tsum[blockIdx.x] = s;
+        __threadfence();
+        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    unsigned long long tot = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kBlock) tot += __ldcg(&tsum[b]);
+    tot = warp_sum(tot);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = tot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) s += s_w[w];
+        *total = s;
+        *ticket = 0;
+    }
 }
 
-// a_k = min{ i : Q_i D > Q_N P_k } for k < count.  Block b handles outputs
-// [b kSelTile, (b + 1) kSelTile); the tile ends of the CDF scan (its
-// inclusive status words) locate the CDF tiles that hold the block's
-// ancestors, which are staged in shared memory when they fit (at most
-// kSelCap entries), else searched in global memory.
-template <class Tgt, class Out>
-__global__ void __launch_bounds__(kBlock) select_kernel(Tgt tgt, Out out, const unsigned long long *Q, int64_t n_cdf,
-                                                        ScanSlot cdf_slot, int cdf_slot_id, DevState *st, int gate,
-                                                        int set_ready, int spl_cap) {
-    extern __shared__ unsigned long long s_dyn[];
-    unsigned long long *s_spl = s_dyn;                   // [spl_cap] CDF tile ends
-    unsigned long long *s_q = s_dyn + spl_cap;           // [kSelCap] staged CDF entries
-    __shared__ int s_range[2];
-    if (*(volatile int32_t *)&st->error) return;
-    if (gate && !*(volatile int32_t *)&st->due) return;
+// Per tile: exclusive prefix from the tile sums, inclusive scan of the
+// tile's values in shared memory (optionally stored through `sink`), then
+// the ancestors of every output whose target falls in the tile's CDF range.
+template <class Gen, class Tgt, class Out, class Sink>
+__global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, Out out, Sink sink, int64_t n,
+                                                             const unsigned long long *tsum,
+                                                             const unsigned long long *total, DevState *st, int gate,
+                                                             int set_ready) {
+    __shared__ unsigned long long s_q[kScanTile];
+    __shared__ int32_t s_a[kScanTile];
+    __shared__ unsigned long long s_w[kBlock / 32];
+    __shared__ unsigned long long s_pre;
+    if (gated_out(st, gate)) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    if (set_ready && tile == 0 && tid == 0) st->ready = 1;
+    // exclusive prefix of this tile
+    unsigned long long pre = 0;
+    for (int b = tid; b < tile; b += kBlock) pre += __ldcg(&tsum[b]);
+    pre = warp_sum(pre);
+    if (lane == 0) s_w[warp] = pre;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long s = 0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) s += s_w[w];
+        s_pre = s;
+    }
+    Gen g = gen;
+    g.prepare(st);
+    const int64_t t0 = (int64_t)tile * kScanTile;
+    const int len = (int)min((int64_t)kScanTile, n - t0);
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const int idx = r * kBlock + tid;
+        s_q[idx] = (idx < len) ? g(t0 + idx) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long loc[kScanItems];
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        acc += s_q[tid * kScanItems + j];
+        loc[j] = acc;
+    }
+    const unsigned long long winc = warp_incl_scan(acc);
+    __syncthreads();
+    if (lane == 31) s_w[warp] = winc;
+    __syncthreads();
+    unsigned long long wpre = 0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w)
+        if (w < warp) wpre += s_w[w];
+    const unsigned long long base = s_pre + wpre + (winc - acc);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) s_q[tid * kScanItems + j] = base + loc[j];
+    __syncthreads();
+    if (Sink::kActive) {
+#pragma unroll
+        for (int r = 0; r < kScanItems; ++r) {
+            const int idx = r * kBlock + tid;
+            if (idx < len) sink(t0 + idx, s_q[idx], st);
+        }
+    }
+    if (!Tgt::kActive) return;
     Tgt tg = tgt;
     tg.prepare(st);
-    const int64_t count = tg.count(st);
-    const int64_t k0 = (int64_t)blockIdx.x * kSelTile;
-    if (set_ready && blockIdx.x == 0 && threadIdx.x == 0) st->ready = 1;
-    if (k0 >= count) return;
-    const unsigned long long D = tg.denom(st);
-    const unsigned long long QN = __ldcg(&Q[n_cdf - 1]);
-    const int ntiles = (int)((n_cdf + kScanTile - 1) / kScanTile);
-    // the scan's parity was flipped when it finished: its status words are
-    // in the other array
-    const int parity = (int)((*(volatile uint32_t *)&st->scan_parity[cdf_slot_id] & 1u) ^ 1u);
-    const unsigned long long *spl = cdf_slot.status[parity];
-    const bool use_spl = ntiles <= spl_cap;
-    if (use_spl) {
-        for (int i = threadIdx.x; i < ntiles; i += kBlock) s_spl[i] = __ldcg(&spl[i]) & ~kStatMask;
-    }
-    // this thread's targets
-    const int64_t k4 = k0 + 4 * (int64_t)threadIdx.x;
-    unsigned long long P[4];
-    tg.get4(k4, P);
-    U128 T[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) T[j] = mul64(QN, P[j]);
-    __syncthreads();
-    // CDF range of the block: tiles holding a_{k0} and a_{last}
-    const int64_t k_last = min(k0 + kSelTile, count) - 1;
-    if (threadIdx.x == 0 || threadIdx.x == kBlock - 1) {
-        const int64_t k = (threadIdx.x == 0) ? k0 : k_last;
-        unsigned long long Pk[4];
-        tg.get4(k & ~3ll, Pk);
-        const U128 Tk = mul64(QN, Pk[k & 3]);
-        int tl = 0;
-        if (use_spl) tl = upper_bound_smem(s_spl, 0, ntiles, D, Tk);
-        else tl = (threadIdx.x == 0) ? 0 : ntiles - 1;
-        if (tl > ntiles - 1) tl = ntiles - 1;
-        s_range[threadIdx.x == 0 ? 0 : 1] = tl;
-    }
-    __syncthreads();
-    const int64_t lo = (int64_t)s_range[0] * kScanTile;
-    const int64_t hi = min((int64_t)(s_range[1] + 1) * kScanTile, n_cdf);
-    const bool staged = use_spl && (hi - lo) <= kSelCap;
-    if (staged) {
-        for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) s_q[i - lo] = __ldcg(&Q[i]);
-    }
-    __syncthreads();
-    int64_t prev = lo;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int64_t k = k4 + j;
-        if (k >= count) break;
-        int64_t a;
-        if (staged) a = lo + upper_bound_smem(s_q, (int)(prev - lo), (int)(hi - lo), D, T[j]);
-        else a = upper_bound_global(Q, prev, n_cdf, D, T[j]);
-        if (a >= n_cdf) a = n_cdf - 1;  // unreachable in exact arithmetic (P_k < D)
-        out(k, a);
-        prev = a;
+    const unsigned long long QN = *(const volatile unsigned long long *)total;
+    if (QN == 0) return;
+    const unsigned long long D = tg.denom();
+    const unsigned long long q_lo = s_pre, q_hi = s_q[len - 1];
+    const int64_t cnt = tg.count();
+    const int64_t k_lo = min(tg.first_at_least(q_lo, QN), cnt);
+    const int64_t k_hi = (t0 + len >= n) ? cnt : min(tg.first_at_least(q_hi, QN), cnt);
+    // outputs [k_lo, k_hi) have their ancestor in this tile; rounds of
+    // kScanTile outputs, kScanItems consecutive outputs per thread
+    for (int64_t kb = k_lo; kb < k_hi; kb += kScanTile) {
+        const int m = (int)min((int64_t)kScanTile, k_hi - kb);
+        const int j0 = tid * kScanItems;
+        int i = 0;
+        for (int j = j0; j < min(m, j0 + kScanItems); ++j) {
+            const U128 T = mul64(QN, tg.P(kb + j));
+            if (j == j0 || !gt128(mul64(s_q[i], D), T)) {
+                if (j == j0) i = 0;
+                int steps = 0;
+                while (i < len && !gt128(mul64(s_q[i], D), T) && steps < 8) {
+                    ++i;
+                    ++steps;
+                }
+                if (i < len && !gt128(mul64(s_q[i], D), T)) {  // binary search the rest
+                    int lo = i, hi = len;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (gt128(mul64(s_q[mid], D), T)) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    i = lo;
+                }
+            }
+            s_a[j] = (int32_t)(t0 + min(i, len - 1));
+        }
+        __syncthreads();
+        for (int j = tid; j < m; j += kBlock) out(kb + j, s_a[j]);
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------- sorting iid uniforms --
-
-// j_k of resampling draw k at iteration t (word k % 4 of call k / 4)
-__device__ __forceinline__ uint32_t resample_u24_at(uint2 key, uint32_t stream, uint32_t t, int64_t k) {
-    const uint4 w = resample_words(key, stream, t, k & ~3ll);
-    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-    return u24(ww[k & 3]);
-}
 
 struct UniformSortArgs {
     uint2 key;
@@ -443,7 +408,7 @@ struct UniformSortArgs {
     int bucket_shift;     // bucket = j >> bucket_shift
     uint32_t *cnt;        // [nbuckets], zero on entry
     uint32_t *fill;       // [nbuckets], zero on entry
-    unsigned long long *boff;  // [nbuckets] inclusive bucket ends
+    unsigned long long *bend;  // [nbuckets] inclusive bucket ends
     uint32_t *sorted;     // [N]
     int64_t nbuckets;
 };
@@ -455,8 +420,7 @@ __device__ __forceinline__ int64_t draw_count(const UniformSortArgs &a, const De
 }
 
 __global__ void __launch_bounds__(kBlock) bucket_count_kernel(UniformSortArgs a, DevState *st, int gate) {
-    if (*(volatile int32_t *)&st->error) return;
-    if (gate && !*(volatile int32_t *)&st->due) return;
+    if (gated_out(st, gate)) return;
     const int64_t count = draw_count(a, st);
     const uint32_t t = (uint32_t)st->t;
     const int64_t k4 = 4 * ((int64_t)blockIdx.x * kBlock + threadIdx.x);
@@ -469,8 +433,7 @@ __global__ void __launch_bounds__(kBlock) bucket_count_kernel(UniformSortArgs a,
 }
 
 __global__ void __launch_bounds__(kBlock) bucket_scatter_kernel(UniformSortArgs a, DevState *st, int gate) {
-    if (*(volatile int32_t *)&st->error) return;
-    if (gate && !*(volatile int32_t *)&st->due) return;
+    if (gated_out(st, gate)) return;
     const int64_t count = draw_count(a, st);
     const uint32_t t = (uint32_t)st->t;
     const int64_t k4 = 4 * ((int64_t)blockIdx.x * kBlock + threadIdx.x);
@@ -482,7 +445,7 @@ __global__ void __launch_bounds__(kBlock) bucket_scatter_kernel(UniformSortArgs 
         if (k4 + j < count) {
             const uint32_t jj = u24(ww[j]);
             const int64_t b = jj >> a.bucket_shift;
-            const unsigned long long start = a.boff[b] - a.cnt[b];
+            const unsigned long long start = a.bend[b] - a.cnt[b];
             const uint32_t pos = atomicAdd(&a.fill[b], 1u);
             a.sorted[start + pos] = jj;
         }
@@ -492,13 +455,12 @@ __global__ void __launch_bounds__(kBlock) bucket_scatter_kernel(UniformSortArgs 
 // one thread per bucket: insertion sort of the (few) values in the bucket,
 // then clear the counters for the next use
 __global__ void __launch_bounds__(kBlock) bucket_sort_kernel(UniformSortArgs a, DevState *st, int gate) {
-    if (*(volatile int32_t *)&st->error) return;
-    if (gate && !*(volatile int32_t *)&st->due) return;
+    if (gated_out(st, gate)) return;
     const int64_t b = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     if (b >= a.nbuckets) return;
     const uint32_t c = a.cnt[b];
     if (c > 1) {
-        const unsigned long long lo = a.boff[b] - c;
+        const unsigned long long lo = a.bend[b] - c;
         for (uint32_t i = 1; i < c; ++i) {
             const uint32_t v = a.sorted[lo + i];
             uint32_t j = i;
@@ -515,13 +477,14 @@ __global__ void __launch_bounds__(kBlock) bucket_sort_kernel(UniformSortArgs a, 
 
 // ----------------------------------------------------------- residual ----
 
-// sum_i d_i -> st->sum_d (zeroed by the weighting kernel); clears the
-// residual draw histogram
-__global__ void __launch_bounds__(kBlock) residual_d_kernel(ResidualParts p, uint32_t *extra, DevState *st, int gate) {
+// sum_i d_i -> st->sum_d (zeroed before the launch); clears the residual
+// draw histogram
+template <typename R>
+__global__ void __launch_bounds__(kBlock) residual_d_kernel(ResidualParts<R> p, uint32_t *extra, DevState *st,
+                                                            int gate) {
     __shared__ unsigned long long s_w[kBlock / 32];
-    if (*(volatile int32_t *)&st->error) return;
-    if (gate && !*(volatile int32_t *)&st->due) return;
-    ResidualParts pp = p;
+    if (gated_out(st, gate)) return;
+    ResidualParts<R> pp = p;
     pp.prepare(st);
     const int64_t i0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
     unsigned long long acc = 0;
@@ -529,7 +492,7 @@ __global__ void __launch_bounds__(kBlock) residual_d_kernel(ResidualParts p, uin
     for (int r = 0; r < kScanItems; ++r) {
         const int64_t i = i0 + r * kBlock;
         if (i < pp.n) {
-            acc += pp.d(i);
+            acc += pp.d_of(pp.q(i));
             extra[i] = 0u;
         }
     }

@@ -22,6 +22,7 @@ int gmm_move(smc_ctx *c);
 int gmm_mcmc(smc_ctx *c);
 int gmm_initialize(smc_ctx *c);
 int gmm_on_data(smc_ctx *c);
+int gmm_setup(smc_ctx *c);
 void gmm_release(smc_ctx *c);
 
 constexpr size_t kAlign = 256;
@@ -35,7 +36,7 @@ int ceil_log2(int64_t n) {
 }
 
 struct Layout {
-    size_t st, rec, part, x, lw, anc, Q, status, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, total;
+    size_t st, rec, part, x, lw, anc, Q, tsum, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, alpha, total;
     int d;            // state rows
     int64_t nbw;      // blocks of the weighting kernels
     int64_t ntiles;   // scan tiles of an N-element scan
@@ -88,12 +89,14 @@ Layout make_layout(const smc_config *c) {
     };
     L.st = take(sizeof(DevState));
     L.rec = take(sizeof(smc_record) * (size_t)c->max_records);
-    L.part = take(sizeof(Partial) * (size_t)std::max<int64_t>(L.nbw, 1));
+    const int64_t nblk = (c->model == SMC_MODEL_GMM) ? std::max<int64_t>(L.nbw, (kQuad * n + kBlock - 1) / kBlock)
+                                                     : L.nbw;
+    L.part = take(sizeof(Partial) * (size_t)std::max<int64_t>(nblk, 1));
     L.x = take(2 * (size_t)L.d * n * rs);
     L.lw = take(2 * (size_t)n * rs);
     L.anc = take((size_t)n * 4);
     L.Q = take((size_t)n * 8);
-    L.status = take((size_t)kScanSlots * 2 * L.ntiles_status * 8);
+    L.tsum = take((size_t)kScanSlots * L.ntiles_status * 8);
     L.cnt = take(sorts ? (size_t)L.nbuckets * 4 : 0);
     L.fill = take(sorts ? (size_t)L.nbuckets * 4 : 0);
     L.boff = take(sorts ? (size_t)L.nbuckets * 8 : 0);
@@ -104,6 +107,7 @@ Layout make_layout(const smc_config *c) {
     const int64_t obs_vals = (c->model == SMC_MODEL_GMM) ? c->max_data : 2 * c->max_data;
     L.obs = take((size_t)obs_vals * 8);
     L.obs_f = take((size_t)obs_vals * 4);
+    L.alpha = take((c->model == SMC_MODEL_GMM) ? ((size_t)c->gmm.n_iter + 1) * 8 : 0);
     L.total = off;
     return L;
 }
@@ -122,7 +126,7 @@ struct smc_ctx {
     void *lw[2];
     int32_t *anc;
     unsigned long long *Q;
-    unsigned long long *status;
+    unsigned long long *tsum;
     uint32_t *cnt, *fill;
     unsigned long long *boff;
     uint32_t *sorted;
@@ -131,6 +135,7 @@ struct smc_ctx {
     unsigned long long *O;
     double *obs;
     float *obs_f;
+    double *alpha;
     int64_t n_obs;
     int32_t t_host;       // last iteration queued, -1 before initialize
     int initialized;
@@ -142,20 +147,14 @@ namespace {
 
 int cuda_check(cudaError_t e) { return e == cudaSuccess ? SMC_OK : SMC_E_CUDA; }
 
-ScanSlot slot_of(smc_ctx *c, int s) {
-    ScanSlot sl;
-    const int64_t nt = c->L.ntiles_status;
-    sl.status[0] = c->status + (size_t)s * 2 * nt;
-    sl.status[1] = sl.status[0] + nt;
-    sl.ntiles_max = (int32_t)nt;
-    return sl;
-}
-
 uint2 key_of(const smc_ctx *c) { return make_uint2((uint32_t)(c->cfg.seed & 0xffffffffu), (uint32_t)(c->cfg.seed >> 32)); }
 
 __global__ void reset_state_kernel(DevState *st) {
     st->t = -1;
     st->cur = 0;
+    st->cur_lw = 0;
+    st->base_shift = 0;
+    st->gathered = 0;
     st->due = 0;
     st->ready = 0;
     st->error = 0;
@@ -218,30 +217,23 @@ int launch_pf(smc_ctx *c) {
     return cuda_check(cudaGetLastError());
 }
 
-template <class Gen, class Out>
-int launch_scan(smc_ctx *c, Gen g, Out o, int64_t n, int slot, int gate) {
+unsigned long long *tsum_of(smc_ctx *c, int slot) { return c->tsum + (size_t)slot * c->L.ntiles_status; }
+
+// tile-sum pass: tsum[slot][tile], exact total -> st->scan_total[slot]
+template <class Gen>
+int launch_reduce(smc_ctx *c, Gen g, int64_t n, int slot, int gate) {
     const unsigned grid = (unsigned)((n + kScanTile - 1) / kScanTile);
-    scan_kernel<Gen, Out><<<grid, kBlock, 0, c->stream>>>(g, o, n, slot_of(c, slot), slot, c->st, gate);
+    tile_reduce_kernel<Gen><<<grid, kBlock, 0, c->stream>>>(g, n, tsum_of(c, slot), &c->st->scan_total[slot],
+                                                             &c->st->scan_ticket[slot], c->st, gate);
     return cuda_check(cudaGetLastError());
 }
 
-template <class Tgt, class Out>
-int launch_select(smc_ctx *c, Tgt tg, Out o, int64_t n_out_max, const unsigned long long *Q, int slot, int gate,
-                  int set_ready) {
-    const int64_t n = c->cfg.n_particles;
-    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
-    const int spl_cap = (ntiles <= kMaxSplitters) ? (int)ntiles : 0;
-    const size_t smem = ((size_t)spl_cap + kSelCap) * 8;
-    static bool attr_set[64] = {};  // per template instance and device
-    const int dev = c->device & 63;
-    if (!attr_set[dev]) {
-        cudaFuncSetAttribute(select_kernel<Tgt, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((kMaxSplitters + kSelCap) * 8));
-        attr_set[dev] = true;
-    }
-    const unsigned grid = (unsigned)std::max<int64_t>(1, (n_out_max + kSelTile - 1) / kSelTile);
-    select_kernel<Tgt, Out><<<grid, kBlock, smem, c->stream>>>(tg, o, Q, n, slot_of(c, slot), slot, c->st, gate,
-                                                                set_ready, spl_cap);
+// scan pass (after launch_reduce on the same slot) with optional selection
+template <class Gen, class Tgt, class Out, class Sink>
+int launch_scan_select(smc_ctx *c, Gen g, Tgt tg, Out o, Sink sk, int64_t n, int slot, int gate, int set_ready) {
+    const unsigned grid = (unsigned)((n + kScanTile - 1) / kScanTile);
+    scan_select_kernel<Gen, Tgt, Out, Sink><<<grid, kBlock, 0, c->stream>>>(
+        g, tg, o, sk, n, tsum_of(c, slot), &c->st->scan_total[slot], c->st, gate, set_ready);
     return cuda_check(cudaGetLastError());
 }
 
@@ -254,12 +246,13 @@ UniformSortArgs sort_args(smc_ctx *c, int from_residual) {
     a.bucket_shift = c->L.bucket_shift;
     a.cnt = c->cnt;
     a.fill = c->fill;
-    a.boff = c->boff;
+    a.bend = c->boff;
     a.sorted = c->sorted;
     a.nbuckets = c->L.nbuckets;
     return a;
 }
 
+// sorted iid 24-bit uniforms (N of them, or R for the residual step)
 int launch_uniform_sort(smc_ctx *c, int from_residual, int gate) {
     UniformSortArgs a = sort_args(c, from_residual);
     const int64_t n = c->cfg.n_particles;
@@ -267,7 +260,10 @@ int launch_uniform_sort(smc_ctx *c, int from_residual, int gate) {
     int rc;
     bucket_count_kernel<<<g4, kBlock, 0, c->stream>>>(a, c->st, gate);
     if ((rc = cuda_check(cudaGetLastError()))) return rc;
-    if ((rc = launch_scan(c, CountGen{c->cnt}, StoreOut{c->boff}, c->L.nbuckets, SLOT_BUCKET, gate))) return rc;
+    if ((rc = launch_reduce(c, CountGen{c->cnt}, c->L.nbuckets, SLOT_BUCKET, gate))) return rc;
+    if ((rc = launch_scan_select(c, CountGen{c->cnt}, NoTargets{}, AncOut{nullptr}, StoreSink{c->boff},
+                                 c->L.nbuckets, SLOT_BUCKET, gate, 0)))
+        return rc;
     bucket_scatter_kernel<<<g4, kBlock, 0, c->stream>>>(a, c->st, gate);
     if ((rc = cuda_check(cudaGetLastError()))) return rc;
     const unsigned gb = (unsigned)((c->L.nbuckets + kBlock - 1) / kBlock);
@@ -275,46 +271,65 @@ int launch_uniform_sort(smc_ctx *c, int from_residual, int gate) {
     return cuda_check(cudaGetLastError());
 }
 
+SortedTargets sorted_targets(smc_ctx *c, int from_residual) {
+    SortedTargets tg;
+    tg.sorted = c->sorted;
+    tg.bend = c->boff;
+    tg.bucket_shift = c->L.bucket_shift;
+    tg.n_total = c->cfg.n_particles;
+    tg.from_residual = from_residual;
+    tg.m = 0;
+    return tg;
+}
+
 template <typename R>
 int launch_resample(smc_ctx *c, int gate) {
     const int64_t n = c->cfg.n_particles;
+    const bool keep = (c->cfg.flags & SMC_FLAG_KEEP_CDF) != 0;
     int rc;
     QGen<R> qg;
     qg.lw[0] = static_cast<const R *>(c->lw[0]);
     qg.lw[1] = static_cast<const R *>(c->lw[1]);
     qg.frac = 61 - ceil_log2(n);
-    if ((rc = launch_scan(c, qg, QOut{c->Q, n}, n, SLOT_CDF, gate))) return rc;
+    qg.cur_lw = nullptr;
+    qg.m = 0;
+    const StoreSink qsink{keep ? c->Q : nullptr};
+    // tile sums of the fixed-point weights; total Q_N -> st->scan_total[SLOT_CDF]
+    if ((rc = launch_reduce(c, qg, n, SLOT_CDF, gate))) return rc;
     const uint2 key = key_of(c);
     const uint32_t sid = c->cfg.stream_id;
     switch (c->cfg.scheme) {
-        case SMC_SYSTEMATIC: {
-            SystematicTargets tg{n, key, sid, 0};
-            return launch_select(c, tg, AncOut{c->anc}, n, c->Q, SLOT_CDF, gate, 1);
-        }
-        case SMC_STRATIFIED: {
-            StratifiedTargets tg{n, key, sid, 0};
-            return launch_select(c, tg, AncOut{c->anc}, n, c->Q, SLOT_CDF, gate, 1);
-        }
-        case SMC_MULTINOMIAL: {
+        case SMC_SYSTEMATIC:
+            return launch_scan_select(c, qg, GridTargets<false>{n, key, sid, 0, 0}, AncOut{c->anc}, qsink, n,
+                                      SLOT_CDF, gate, 1);
+        case SMC_STRATIFIED:
+            return launch_scan_select(c, qg, GridTargets<true>{n, key, sid, 0, 0}, AncOut{c->anc}, qsink, n,
+                                      SLOT_CDF, gate, 1);
+        case SMC_MULTINOMIAL:
             if ((rc = launch_uniform_sort(c, 0, gate))) return rc;
-            SortedTargets tg{c->sorted, n, n, 0, 0};
-            return launch_select(c, tg, AncOut{c->anc}, n, c->Q, SLOT_CDF, gate, 1);
-        }
+            return launch_scan_select(c, qg, sorted_targets(c, 0), AncOut{c->anc}, qsink, n, SLOT_CDF, gate, 1);
         case SMC_RESIDUAL: {
+            if (keep && (rc = launch_scan_select(c, qg, NoTargets{}, AncOut{nullptr}, qsink, n, SLOT_CDF, gate, 0)))
+                return rc;
+            // Q_N for the residual generators
+            if ((rc = cuda_check(cudaMemcpyAsync(&c->st->qn, &c->st->scan_total[SLOT_CDF], 8,
+                                                 cudaMemcpyDeviceToDevice, c->stream))))
+                return rc;
             if ((rc = cuda_check(cudaMemsetAsync(&c->st->sum_d, 0, sizeof(unsigned long long), c->stream))))
                 return rc;
-            ResidualParts p{c->Q, n, 0};
+            ResidualParts<R> p{qg, n, 0};
             const unsigned gt = (unsigned)((n + kScanTile - 1) / kScanTile);
-            residual_d_kernel<<<gt, kBlock, 0, c->stream>>>(p, c->extra, c->st, gate);
+            residual_d_kernel<R><<<gt, kBlock, 0, c->stream>>>(p, c->extra, c->st, gate);
             if ((rc = cuda_check(cudaGetLastError()))) return rc;
-            ResidualRGen rg{p, 0};
-            if ((rc = launch_scan(c, rg, StoreOut{c->RQ}, n, SLOT_RES_R, gate))) return rc;
+            ResidualRGen<R> rg{p, 0};
+            if ((rc = launch_reduce(c, rg, n, SLOT_RES_R, gate))) return rc;
             if ((rc = launch_uniform_sort(c, 1, gate))) return rc;
-            SortedTargets tg{c->sorted, n, n, 1, 0};
-            if ((rc = launch_select(c, tg, CountOut{c->extra}, n, c->RQ, SLOT_RES_R, gate, 0))) return rc;
-            ResidualOGen og{p, c->extra};
-            if ((rc = launch_scan(c, og, StoreOut{c->O}, n, SLOT_RES_O, gate))) return rc;
-            return launch_select(c, ExpandTargets{n}, AncOut{c->anc}, n, c->O, SLOT_RES_O, gate, 1);
+            if ((rc = launch_scan_select(c, rg, sorted_targets(c, 1), CountOut{c->extra}, NoSink{}, n, SLOT_RES_R,
+                                         gate, 0)))
+                return rc;
+            ResidualOGen<R> og{p, c->extra};
+            if ((rc = launch_reduce(c, og, n, SLOT_RES_O, gate))) return rc;
+            return launch_scan_select(c, og, ExpandTargets{n}, AncOut{c->anc}, NoSink{}, n, SLOT_RES_O, gate, 1);
         }
     }
     return SMC_E_ARG;
@@ -380,7 +395,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->lw[1] = c->ws + L.lw + (size_t)cfg->n_particles * L.rsize;
     c->anc = reinterpret_cast<int32_t *>(c->ws + L.anc);
     c->Q = reinterpret_cast<unsigned long long *>(c->ws + L.Q);
-    c->status = reinterpret_cast<unsigned long long *>(c->ws + L.status);
+    c->tsum = reinterpret_cast<unsigned long long *>(c->ws + L.tsum);
     c->cnt = reinterpret_cast<uint32_t *>(c->ws + L.cnt);
     c->fill = reinterpret_cast<uint32_t *>(c->ws + L.fill);
     c->boff = reinterpret_cast<unsigned long long *>(c->ws + L.boff);
@@ -390,17 +405,19 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->O = reinterpret_cast<unsigned long long *>(c->ws + L.O);
     c->obs = reinterpret_cast<double *>(c->ws + L.obs);
     c->obs_f = reinterpret_cast<float *>(c->ws + L.obs_f);
+    c->alpha = reinterpret_cast<double *>(c->ws + L.alpha);
     c->n_obs = 0;
     c->t_host = -1;
     c->initialized = 0;
     cudaGetDevice(&c->device);
     // zero the state block, records, scan status words and bucket counters
     int rc = cuda_check(cudaMemsetAsync(c->ws, 0, L.part, c->stream));
-    if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + L.status, 0, L.boff - L.status, c->stream));
+    if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + L.tsum, 0, L.boff - L.tsum, c->stream));
     if (!rc) {
         reset_state_kernel<<<1, 1, 0, c->stream>>>(c->st);
         rc = cuda_check(cudaGetLastError());
     }
+    if (!rc && cfg->model == SMC_MODEL_GMM) rc = gmm_setup(c);
     if (rc) {
         delete c;
         return rc;
@@ -550,7 +567,7 @@ int smc_read_log_weight(smc_ctx *c, void *dst, int on_device) {
     if (!c) return SMC_E_ARG;
     int rc = read_state(c);
     if (rc != SMC_OK && rc != SMC_E_NONFINITE) return rc;
-    return copy_out(c, dst, c->lw[c->host_st.cur & 1], (size_t)c->cfg.n_particles * c->L.rsize, on_device);
+    return copy_out(c, dst, c->lw[c->host_st.cur_lw & 1], (size_t)c->cfg.n_particles * c->L.rsize, on_device);
 }
 
 int smc_read_ancestors(smc_ctx *c, int32_t *dst, int on_device) {
@@ -560,6 +577,7 @@ int smc_read_ancestors(smc_ctx *c, int32_t *dst, int on_device) {
 
 int smc_read_cdf(smc_ctx *c, uint64_t *dst, int on_device) {
     if (!c) return SMC_E_ARG;
+    if (!(c->cfg.flags & SMC_FLAG_KEEP_CDF)) return SMC_E_STATE;
     return copy_out(c, dst, c->Q, (size_t)c->cfg.n_particles * 8, on_device);
 }
 
@@ -601,7 +619,7 @@ int smc_write_log_weight(smc_ctx *c, const void *src, int on_device) {
     int rc = read_state(c);
     if (rc) return rc;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    rc = cuda_check(cudaMemcpyAsync(c->lw[c->host_st.cur & 1], src, (size_t)c->cfg.n_particles * c->L.rsize, k,
+    rc = cuda_check(cudaMemcpyAsync(c->lw[c->host_st.cur_lw & 1], src, (size_t)c->cfg.n_particles * c->L.rsize, k,
                                     c->stream));
     if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream));
     return rc;
@@ -656,9 +674,136 @@ extern "C" int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], u
 
 // ------------------------------------------------------------------ GMM --
 namespace {
-int gmm_move(smc_ctx *) { return SMC_E_ARG; }
-int gmm_mcmc(smc_ctx *) { return SMC_E_ARG; }
-int gmm_initialize(smc_ctx *) { return SMC_E_ARG; }
-int gmm_on_data(smc_ctx *) { return SMC_OK; }
+
+__global__ void to_float_kernel(const double *src, float *dst, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (float)src[i];
+}
+
+double gmm_alpha(const smc_gmm_params &g, int32_t t) {
+    const double x = (double)t / (double)g.n_iter;
+    double a = (g.schedule == SMC_ALPHA_LINEAR) ? x : std::pow(x, g.power);
+    return std::min(1.0, std::max(0.0, a));
+}
+
+int gmm_setup(smc_ctx *c) {
+    const smc_gmm_params &g = c->cfg.gmm;
+    double *tab = new (std::nothrow) double[(size_t)g.n_iter + 1];
+    if (!tab) return SMC_E_ARG;
+    for (int32_t t = 0; t <= g.n_iter; ++t) tab[t] = gmm_alpha(g, t);
+    int rc = cuda_check(cudaMemcpyAsync(c->alpha, tab, ((size_t)g.n_iter + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream));
+    delete[] tab;
+    return rc;
+}
+
+int gmm_on_data(smc_ctx *c) {
+    if (c->cfg.model != SMC_MODEL_GMM) return SMC_OK;
+    const int64_t n = c->n_obs;
+    to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->obs, c->obs_f, n);
+    return cuda_check(cudaGetLastError());
+}
+
 void gmm_release(smc_ctx *) {}
+
+template <typename R>
+GmmArgs<R> gmm_args(smc_ctx *c) {
+    GmmArgs<R> a;
+    const smc_config &cfg = c->cfg;
+    const smc_gmm_params &g = cfg.gmm;
+    const int64_t n = cfg.n_particles;
+    a.n = n;
+    a.nd = (int32_t)c->n_obs;
+    a.y = (sizeof(R) == 4) ? reinterpret_cast<const R *>(c->obs_f) : reinterpret_cast<const R *>(c->obs);
+    for (int b = 0; b < 2; ++b) {
+        a.x[b] = static_cast<R *>(c->x[b]);
+        a.lw[b] = static_cast<R *>(c->lw[b]);
+    }
+    a.anc = c->anc;
+    a.alpha = c->alpha;
+    a.T = g.n_iter;
+    a.rec = c->rec;
+    a.rec_cap = cfg.max_records;
+    a.st = c->st;
+    a.part = c->part;
+    a.log_n = std::log((double)n);
+    a.threshold = cfg.threshold;
+    const int r = g.n_comp;
+    const double shape = (double)g.shape0;
+    a.mu0 = g.mu0;
+    a.sd0 = g.sd0;
+    a.inv_sd0 = 1.0 / g.sd0;
+    a.lp_const = r * (-0.5 * std::log(2.0 * M_PI * g.sd0 * g.sd0) + shape * std::log(g.rate0) - std::lgamma(shape)) +
+                 std::lgamma((double)r);
+    a.shape_m1 = shape - 1.0;
+    a.rate = g.rate0;
+    a.half_nd_log2pi = 0.5 * (double)c->n_obs * std::log(2.0 * M_PI);
+    a.key = key_of(c);
+    a.stream = cfg.stream_id;
+    return a;
+}
+
+enum GmmKernel { GMM_INIT, GMM_REWEIGHT, GMM_MCMC };
+
+template <typename R, int NC>
+int gmm_launch_nc(smc_ctx *c, GmmKernel k) {
+    GmmArgs<R> a = gmm_args<R>(c);
+    const size_t smem = (((size_t)a.nd * sizeof(R)) + 15) & ~size_t(15);
+    const unsigned gq = (unsigned)((kQuad * a.n + kBlock - 1) / kBlock);
+    const unsigned gw = (unsigned)c->L.nbw;
+    switch (k) {
+        case GMM_INIT:
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(gmm_init_kernel<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            gmm_init_kernel<R, NC><<<gq, kBlock, smem, c->stream>>>(a);
+            break;
+        case GMM_REWEIGHT:
+            gmm_reweight_kernel<R, NC><<<gw, kBlock, 0, c->stream>>>(a);
+            break;
+        case GMM_MCMC:
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(gmm_mcmc_kernel<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            gmm_mcmc_kernel<R, NC><<<gq, kBlock, smem, c->stream>>>(a);
+            break;
+    }
+    return cuda_check(cudaGetLastError());
+}
+
+template <typename R>
+int gmm_launch(smc_ctx *c, GmmKernel k) {
+    switch (c->cfg.gmm.n_comp) {
+        case 1: return gmm_launch_nc<R, 1>(c, k);
+        case 2: return gmm_launch_nc<R, 2>(c, k);
+        case 3: return gmm_launch_nc<R, 3>(c, k);
+        case 4: return gmm_launch_nc<R, 4>(c, k);
+        case 5: return gmm_launch_nc<R, 5>(c, k);
+        case 6: return gmm_launch_nc<R, 6>(c, k);
+        case 7: return gmm_launch_nc<R, 7>(c, k);
+        case 8: return gmm_launch_nc<R, 8>(c, k);
+    }
+    return SMC_E_ARG;
+}
+
+int gmm_launch_any(smc_ctx *c, GmmKernel k) {
+    return (c->cfg.precision == 32) ? gmm_launch<float>(c, k) : gmm_launch<double>(c, k);
+}
+
+int gmm_initialize(smc_ctx *c) {
+    const int rc = gmm_launch_any(c, GMM_INIT);
+    if (!rc) c->t_host = 0;
+    return rc;
+}
+
+int gmm_move(smc_ctx *c) {
+    if (c->t_host + 1 > c->cfg.gmm.n_iter) return SMC_E_ARG;
+    const int rc = gmm_launch_any(c, GMM_REWEIGHT);
+    if (!rc) c->t_host += 1;
+    return rc;
+}
+
+int gmm_mcmc(smc_ctx *c) {
+    if (c->t_host < 1) return SMC_OK;  // nothing to move at t = 0 (equal weights, alpha = 0)
+    return gmm_launch_any(c, GMM_MCMC);
+}
+
 }  // namespace

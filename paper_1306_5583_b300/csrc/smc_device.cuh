@@ -57,6 +57,8 @@ struct Math;
 template <>
 struct Math<float> {
     static __device__ __forceinline__ float exp(float x) { return expf(x); }
+    static __device__ __forceinline__ float fast_exp(float x) { return __expf(x); }
+    static __device__ __forceinline__ float fast_log(float x) { return __logf(x); }
     static __device__ __forceinline__ float log(float x) { return logf(x); }
     static __device__ __forceinline__ float log1p(float x) { return log1pf(x); }
     static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
@@ -71,6 +73,8 @@ struct Math<float> {
 template <>
 struct Math<double> {
     static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+    static __device__ __forceinline__ double fast_exp(double x) { return ::exp(x); }
+    static __device__ __forceinline__ double fast_log(double x) { return ::log(x); }
     static __device__ __forceinline__ double log(double x) { return ::log(x); }
     static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
     static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
@@ -81,7 +85,8 @@ struct Math<double> {
     static __device__ __forceinline__ double neg_inf() { return -__longlong_as_double(0x7ff0000000000000ll); }
 };
 
-// Box-Muller pair from two uniforms in (0, 1].
+// Box-Muller pair from two uniforms in (0, 1]: z0 = r cos(2 pi u1),
+// z1 = r sin(2 pi u1), r = sqrt(-2 ln u0).
 template <typename R>
 __device__ __forceinline__ void box_muller(R u0, R u1, R &z0, R &z1) {
     const R r = Math<R>::sqrt(R(-2) * Math<R>::log(u0));
@@ -91,11 +96,34 @@ __device__ __forceinline__ void box_muller(R u0, R u1, R &z0, R &z1) {
     z1 = r * s;
 }
 
+// FP32 Box-Muller on the MUFU pipe: the angle is taken in (-pi, pi], where
+// the hardware sine/cosine are accurate to about 2^-21 absolute, using
+// cos(2 pi u) = -cos(2 pi u - pi) and sin(2 pi u) = -sin(2 pi u - pi).
+__device__ __forceinline__ void box_muller_fast(float u0, float u1, float &z0, float &z1) {
+    const float r = sqrtf(-2.0f * __logf(u0));
+    const float th = fmaf(6.2831853071795864769f, u1, -3.14159265358979323846f);
+    float s, c;
+    __sincosf(th, &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
+}
+
 // Four standard normals from one Philox call: (w0, w1) -> z0, z1; (w2, w3) -> z2, z3.
 template <typename R>
 __device__ __forceinline__ void normals4(uint4 w, R z[4]) {
     box_muller(uniform01<R>(w.x), uniform01<R>(w.y), z[0], z[1]);
     box_muller(uniform01<R>(w.z), uniform01<R>(w.w), z[2], z[3]);
+}
+
+// Same draws with the MUFU-pipe transforms for float (the hot loops).
+template <typename R>
+__device__ __forceinline__ void normals4_fast(uint4 w, R z[4]) {
+    if constexpr (sizeof(R) == 4) {
+        box_muller_fast(uniform01<float>(w.x), uniform01<float>(w.y), z[0], z[1]);
+        box_muller_fast(uniform01<float>(w.z), uniform01<float>(w.w), z[2], z[3]);
+    } else {
+        normals4<R>(w, z);
+    }
 }
 
 // ---- reductions -------------------------------------------------------------

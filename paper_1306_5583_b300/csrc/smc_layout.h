@@ -13,10 +13,6 @@ constexpr int kPfItems = 4;                     // particles per thread, weighti
 constexpr int kPfTile = kBlock * kPfItems;      // 1024 particles per block
 constexpr int kScanItems = 8;                   // elements per thread, scans
 constexpr int kScanTile = kBlock * kScanItems;  // 2048 elements per scan tile
-constexpr int kSelItems = 4;                    // outputs per thread, ancestor selection
-constexpr int kSelTile = kBlock * kSelItems;    // 1024 outputs per block
-constexpr int kSelCap = 2 * kScanTile;          // CDF entries staged in shared memory
-constexpr int kMaxSplitters = 4096;             // scan tiles whose ends fit in shared memory
 constexpr int kScanSlots = 6;                   // independent scans per iteration
 constexpr uint32_t kSpinLimit = 1u << 24;       // bounded waits (about 1 s with backoff)
 
@@ -42,7 +38,7 @@ struct DevState {
     int32_t due;      // the ESS test of iteration t asked for resampling
     int32_t ready;    // ancestors for the next gather are in place
     int32_t error;    // device error word (SMC_E_*)
-    int32_t pad_e;
+    int32_t cur_lw;   // which log-weight buffer is current
     uint32_t ticket;  // last-block ticket of the weighting kernels
     uint32_t count_r; // residual: number of residual draws R
     double max_lw;    // M_t = max_i lw_t,i (the fixed-point shift)
@@ -52,14 +48,13 @@ struct DevState {
     double alpha;     // GMM alpha_t
     double path_u;    // GMM U_t
     double path_log_z;
-    double pad0;
+    double base_shift;  // log W_i = lw_i - base_shift (GMM; 0 after a gather resets lw to -log N)
     unsigned long long qn;     // fixed-point total of the last weight CDF
     unsigned long long sum_d;  // residual: sum of the deterministic copies
-    uint32_t scan_counter[kScanSlots];  // tile ids handed out by a running scan
-    uint32_t scan_done[kScanSlots];     // tiles finished by a running scan
-    uint32_t scan_parity[kScanSlots];   // which status array a scan uses
+    uint32_t scan_ticket[kScanSlots];   // last-block tickets of the tile-sum passes
+    unsigned long long scan_total[kScanSlots];  // exact totals of the tile-sum passes
     uint32_t accept[3];                 // GMM accepted moves per block (last mcmc)
-    uint32_t pad1;
+    int32_t gathered;                   // GMM: the last mcmc gathered by ancestors
 };
 
 struct Partial {  // one per block of a weighting kernel
@@ -67,15 +62,5 @@ struct Partial {  // one per block of a weighting kernel
     double pad[2];
 };
 
-// Tile status word of the decoupled look-back scans: bits 62-63 hold the
-// status (1 = tile aggregate, 2 = inclusive prefix), bits 0-61 the value.
-constexpr unsigned long long kStatAgg = 1ull << 62;
-constexpr unsigned long long kStatIncl = 2ull << 62;
-constexpr unsigned long long kStatMask = 3ull << 62;
-
-struct ScanSlot {
-    unsigned long long *status[2];  // [parity][tile]
-    int32_t ntiles_max;
-};
 
 }  // namespace smc

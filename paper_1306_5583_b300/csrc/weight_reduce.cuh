@@ -9,6 +9,15 @@
 
 namespace smc {
 
+// Subtract a float64 scalar from a value of precision R with one rounding
+// less than a plain conversion (hi/lo split of the scalar).
+template <typename R>
+struct Shift {
+    R hi, lo;
+    __device__ __forceinline__ explicit Shift(double v) : hi(R(v)), lo(R(v - double(R(v)))) {}
+    __device__ __forceinline__ R sub_from(R x) const { return (x - hi) - lo; }
+};
+
 // What the last block does with the combined sums.
 struct FinalizeArgs {
     DevState *st;
@@ -21,14 +30,82 @@ struct FinalizeArgs {
     double alpha;         // GMM alpha_t (recorded)
 };
 
+// ---- compensated float ("double-float") sums ------------------------------
+// FP64 runs at 1/64 of the FP32 rate on B300, so the FP32 path keeps its
+// reductions on the FP32 pipe with error-free transformations (Knuth's
+// TwoSum, Dekker's FastTwoSum, FMA-based TwoProduct) and converts to float64
+// only for the final scalars.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = a + b;
+    const float bp = s - a;
+    return DF{s, (a - (s - bp)) + (b - bp)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const DF s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + a.lo + b.lo);
+}
+__device__ __forceinline__ DF df_mul(DF a, float b) {
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
+    return DF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ double df_to_double(DF a) { return double(a.hi) + double(a.lo); }
+
+// Per-block partial (max, sum e, sum e^2, sum e h0, sum e h1, sum e h2) with
+// e = exp(lw - max): float64 fields for the FP64 path, (hi, lo) float pairs
+// for the FP32 path, in the same 64 bytes.
+template <typename R>
+struct PartialIO;
+
+template <>
+struct PartialIO<double> {
+    static __device__ __forceinline__ void store(Partial *p, double m, const double (&s)[5]) {
+        p->m = m;
+        p->s1 = s[0];
+        p->s2 = s[1];
+        p->sx = s[2];
+        p->sy = s[3];
+        p->su = s[4];
+    }
+};
+
+template <>
+struct PartialIO<float> {
+    static __device__ __forceinline__ void store(Partial *p, float m, const DF (&s)[5]) {
+        float *f = reinterpret_cast<float *>(p);
+        f[0] = m;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            f[1 + 2 * j] = s[j].hi;
+            f[2 + 2 * j] = s[j].lo;
+        }
+    }
+    static __device__ __forceinline__ float m(const Partial *p) { return __ldcg(reinterpret_cast<const float *>(p)); }
+    static __device__ __forceinline__ DF s(const Partial *p, int j) {
+        const float *f = reinterpret_cast<const float *>(p);
+        return DF{__ldcg(f + 1 + 2 * j), __ldcg(f + 2 + 2 * j)};
+    }
+};
+
 // Block-level partial of E items per thread.  lw = -inf marks inactive
-// items.  Per-thread and per-warp sums run in R; the 8 warp sums are
-// combined in float64.
+// items.  Per-thread and per-warp sums run in R; the warp sums are combined
+// in float64 (FP64 path) or compensated float (FP32 path).
 template <typename R, int E>
 __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E], const R (&h1)[E],
                                               const R (&h2)[E], Partial *out) {
     __shared__ R s_max[kBlock / 32];
-    __shared__ double s_sum[kBlock / 32][5];
+    __shared__ R s_sum[kBlock / 32][5];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     R m = Math<R>::neg_inf();
@@ -41,58 +118,41 @@ __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E]
 #pragma unroll
     for (int w = 1; w < kBlock / 32; ++w) m = fmax(m, s_max[w]);
 
-    R s1 = 0, s2 = 0, sa = 0, sb = 0, sc = 0;
+    R v[5] = {0, 0, 0, 0, 0};
     if (m > Math<R>::neg_inf()) {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const R e = (lw[j] > Math<R>::neg_inf()) ? Math<R>::exp(lw[j] - m) : R(0);
-            s1 += e;
-            s2 += e * e;
-            sa += e * h0[j];
-            sb += e * h1[j];
-            sc += e * h2[j];
+            const R e = (lw[j] > Math<R>::neg_inf()) ? Math<R>::fast_exp(lw[j] - m) : R(0);
+            v[0] += e;
+            v[1] += e * e;
+            v[2] += e * h0[j];
+            v[3] += e * h1[j];
+            v[4] += e * h2[j];
         }
     }
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    sa = warp_sum(sa);
-    sb = warp_sum(sb);
-    sc = warp_sum(sc);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) v[q] = warp_sum(v[q]);
     if (lane == 0) {
-        s_sum[warp][0] = double(s1);
-        s_sum[warp][1] = double(s2);
-        s_sum[warp][2] = double(sa);
-        s_sum[warp][3] = double(sb);
-        s_sum[warp][4] = double(sc);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) s_sum[warp][q] = v[q];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t1 = 0, t2 = 0, ta = 0, tb = 0, tc = 0;
+        if constexpr (sizeof(R) == 8) {
+            double t[5] = {0, 0, 0, 0, 0};
+            for (int w = 0; w < kBlock / 32; ++w)
+                for (int q = 0; q < 5; ++q) t[q] += s_sum[w][q];
+            PartialIO<double>::store(out, double(m), t);
+        } else {
+            DF t[5];
 #pragma unroll
-        for (int w = 0; w < kBlock / 32; ++w) {
-            t1 += s_sum[w][0];
-            t2 += s_sum[w][1];
-            ta += s_sum[w][2];
-            tb += s_sum[w][3];
-            tc += s_sum[w][4];
+            for (int q = 0; q < 5; ++q) t[q] = DF{float(s_sum[0][q]), 0.0f};
+            for (int w = 1; w < kBlock / 32; ++w)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) t[q] = df_add(t[q], DF{float(s_sum[w][q]), 0.0f});
+            PartialIO<float>::store(out, float(m), t);
         }
-        Partial p;
-        p.m = double(m);
-        p.s1 = t1;
-        p.s2 = t2;
-        p.sx = ta;
-        p.sy = tb;
-        p.su = tc;
-        p.pad[0] = p.pad[1] = 0;
-        *out = p;
     }
-}
-
-// Scale factor exp(mb - M) in the kernel's precision.
-template <typename R>
-__device__ __forceinline__ double partial_scale(double mb, double M) {
-    if (!(mb > -INFINITY)) return 0.0;
-    return double(Math<R>::exp(R(mb - M)));
 }
 
 // Returns true in the one block that arrives last; that block then holds
@@ -102,9 +162,8 @@ struct Combined {
 };
 
 template <typename R>
-__device__ __forceinline__ bool last_block_combine(DevState *st, const Partial *part, Combined *out) {
+__device__ __forceinline__ bool take_ticket(DevState *st) {
     __shared__ bool s_last;
-    __shared__ double s_red[kBlock / 32][6];
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -114,52 +173,92 @@ __device__ __forceinline__ bool last_block_combine(DevState *st, const Partial *
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
+    return true;
+}
+
+template <typename R>
+__device__ __forceinline__ bool last_block_combine(DevState *st, const Partial *part, Combined *out) {
+    if (!take_ticket<R>(st)) return false;
     const int nb = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double M = -INFINITY;
-    for (int b = threadIdx.x; b < nb; b += kBlock) M = fmax(M, __ldcg(&part[b].m));
-    M = warp_max(M);
-    if (lane == 0) s_red[warp][0] = M;
-    __syncthreads();
-    M = s_red[0][0];
+    if constexpr (sizeof(R) == 8) {
+        __shared__ double s_red[kBlock / 32][6];
+        double M = -INFINITY;
+        for (int b = threadIdx.x; b < nb; b += kBlock) M = fmax(M, __ldcg(&part[b].m));
+        M = warp_max(M);
+        if (lane == 0) s_red[warp][0] = M;
+        __syncthreads();
+        M = s_red[0][0];
+        for (int w = 1; w < kBlock / 32; ++w) M = fmax(M, s_red[w][0]);
+        __syncthreads();
+        double S[5] = {0, 0, 0, 0, 0};
+        if (M > -INFINITY) {
+            for (int b = threadIdx.x; b < nb; b += kBlock) {
+                const double mb = __ldcg(&part[b].m);
+                const double sc = (mb > -INFINITY) ? exp(mb - M) : 0.0;
+                S[0] += __ldcg(&part[b].s1) * sc;
+                S[1] += __ldcg(&part[b].s2) * sc * sc;
+                S[2] += __ldcg(&part[b].sx) * sc;
+                S[3] += __ldcg(&part[b].sy) * sc;
+                S[4] += __ldcg(&part[b].su) * sc;
+            }
+        }
+        for (int q = 0; q < 5; ++q) S[q] = warp_sum(S[q]);
+        if (lane == 0)
+            for (int q = 0; q < 5; ++q) s_red[warp][1 + q] = S[q];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Combined c{M, 0, 0, 0, 0, 0};
+            for (int w = 0; w < kBlock / 32; ++w) {
+                c.S1 += s_red[w][1];
+                c.S2 += s_red[w][2];
+                c.Sa += s_red[w][3];
+                c.Sb += s_red[w][4];
+                c.Sc += s_red[w][5];
+            }
+            *out = c;
+        }
+    } else {
+        __shared__ float s_m[kBlock / 32];
+        __shared__ DF s_df[kBlock / 32][5];
+        float M = -INFINITY;
+        for (int b = threadIdx.x; b < nb; b += kBlock) M = fmaxf(M, PartialIO<float>::m(&part[b]));
+        M = warp_maxf(M);
+        if (lane == 0) s_m[warp] = M;
+        __syncthreads();
+        M = s_m[0];
+        for (int w = 1; w < kBlock / 32; ++w) M = fmaxf(M, s_m[w]);
+        DF S[5];
 #pragma unroll
-    for (int w = 1; w < kBlock / 32; ++w) M = fmax(M, s_red[w][0]);
-    __syncthreads();
-    double S1 = 0, S2 = 0, Sa = 0, Sb = 0, Sc = 0;
-    if (M > -INFINITY) {
-        for (int b = threadIdx.x; b < nb; b += kBlock) {
-            const double sc = partial_scale<R>(__ldcg(&part[b].m), M);
-            const double sc2 = sc * sc;
-            S1 += __ldcg(&part[b].s1) * sc;
-            S2 += __ldcg(&part[b].s2) * sc2;
-            Sa += __ldcg(&part[b].sx) * sc;
-            Sb += __ldcg(&part[b].sy) * sc;
-            Sc += __ldcg(&part[b].su) * sc;
+        for (int q = 0; q < 5; ++q) S[q] = DF{0.0f, 0.0f};
+        if (M > -INFINITY) {
+            for (int b = threadIdx.x; b < nb; b += kBlock) {
+                const float mb = PartialIO<float>::m(&part[b]);
+                const float sc = (mb > -INFINITY) ? expf(mb - M) : 0.0f;
+                S[0] = df_add(S[0], df_mul(PartialIO<float>::s(&part[b], 0), sc));
+                S[1] = df_add(S[1], df_mul(df_mul(PartialIO<float>::s(&part[b], 1), sc), sc));
+#pragma unroll
+                for (int q = 2; q < 5; ++q) S[q] = df_add(S[q], df_mul(PartialIO<float>::s(&part[b], q), sc));
+            }
         }
-    }
-    S1 = warp_sum(S1);
-    S2 = warp_sum(S2);
-    Sa = warp_sum(Sa);
-    Sb = warp_sum(Sb);
-    Sc = warp_sum(Sc);
-    if (lane == 0) {
-        s_red[warp][1] = S1;
-        s_red[warp][2] = S2;
-        s_red[warp][3] = Sa;
-        s_red[warp][4] = Sb;
-        s_red[warp][5] = Sc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Combined c{M, 0, 0, 0, 0, 0};
-        for (int w = 0; w < kBlock / 32; ++w) {
-            c.S1 += s_red[w][1];
-            c.S2 += s_red[w][2];
-            c.Sa += s_red[w][3];
-            c.Sb += s_red[w][4];
-            c.Sc += s_red[w][5];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) S[q] = df_add(S[q], df_shfl_xor(S[q], o));
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) s_df[warp][q] = S[q];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DF T[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) T[q] = s_df[0][q];
+            for (int w = 1; w < kBlock / 32; ++w)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) T[q] = df_add(T[q], s_df[w][q]);
+            *out = Combined{double(M), df_to_double(T[0]), df_to_double(T[1]), df_to_double(T[2]),
+                            df_to_double(T[3]), df_to_double(T[4])};
         }
-        *out = c;
     }
     return true;
 }

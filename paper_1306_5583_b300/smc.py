@@ -34,7 +34,7 @@ class GMMParams(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_particles", ctypes.c_int64),
                 ("max_records", ctypes.c_int32), ("scheme", ctypes.c_int32), ("threshold", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("max_data", ctypes.c_int64), ("cv", CVParams), ("gmm", GMMParams)]
 
 
@@ -113,8 +113,11 @@ def check(code, where):
         raise SMCError(code, where)
 
 
+FLAG_KEEP_CDF = 1
+
+
 def make_config(model="cv", n=1024, precision=32, scheme="systematic", threshold=0.5, seed=0, stream_id=0,
-                max_records=None, max_data=1000, cv=None, gmm=None):
+                max_records=None, max_data=1000, cv=None, gmm=None, keep_cdf=True):
     c = Config()
     c.model = {"cv": MODEL_CV, "cv_gauss": MODEL_CV_GAUSS, "gmm": MODEL_GMM}[model]
     c.precision = precision
@@ -123,6 +126,7 @@ def make_config(model="cv", n=1024, precision=32, scheme="systematic", threshold
     c.threshold = float(threshold)
     c.seed = int(seed)
     c.stream_id = int(stream_id)
+    c.flags = FLAG_KEEP_CDF if keep_cdf else 0
     c.max_data = int(max_data)
     c.max_records = int(max_records if max_records is not None else max(2, max_data + 1))
     p = dict(delta=0.1, sd_pos=0.02, sd_vel=1.0, obs_scale=0.5, obs_df=10.0, sd_pos0=1.0, sd_vel0=1.0)

@@ -1,0 +1,219 @@
+"""GPU parity of the Gaussian-mixture SMC sampler (Sec. 5.2, Algorithm 2)
+against the oracle, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import assert_close, check_resample, need_gpu, torch
+from oracle import gmm as ogmm
+from oracle import philox as ophilox
+from oracle import resample as ores
+from paper_1306_5583_b300 import smc, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def make_gmm(n, nd=1000, r=4, T=500, precision=32, scheme="systematic", threshold=0.5, seed=0, data_seed=0,
+             schedule="prior", power=5.0, shape0=1, rate0=1.0):
+    y = workloads.gmm_data(nd, seed=data_seed)
+    cfg = smc.make_config(model="gmm", n=n, precision=precision, scheme=scheme, threshold=threshold, seed=seed,
+                          max_data=nd, max_records=T + 1,
+                          gmm=dict(n_comp=r, n_iter=T, power=power, shape0=shape0, rate0=rate0,
+                                   schedule=smc.ALPHA_LINEAR if schedule == "linear" else smc.ALPHA_PRIOR))
+    s = smc.Sampler(cfg)
+    s.set_data(y)
+    op = ogmm.GMMParams(r=r, T=T, power=power, schedule=schedule, shape0=shape0, rate0=rate0)
+    return s, y, op
+
+
+def split_state(x, r):
+    return x[:r], x[r:2 * r], x[2 * r:3 * r], x[3 * r], x[3 * r + 1]
+
+
+def test_init_matches_oracle_fp64():
+    need_gpu()
+    n, r = 3000, 4
+    s, y, op = make_gmm(n, nd=200, r=r, precision=64, seed=2)
+    s.initialize()
+    x = s.state()
+    mu, lam, om, lp, ll = split_state(x, r)
+    ref = ogmm.init_state(n, y, 2, op)
+    assert_close(mu, ref.mu, 1e-12, "mu")
+    assert_close(lam, ref.lam, 1e-12, "lambda")
+    assert_close(om, ref.om, 1e-12, "omega")
+    assert_close(lp, ref.lprior, 1e-12, "log-prior")
+    assert_close(ll, ref.llik, 1e-11, "log-likelihood")
+    rec = s.history(1)[0]
+    assert abs(rec["path_u"] - ref.llik.mean()) < 1e-9 * abs(ref.llik.mean())
+    assert abs(rec["ess"] - n) < 1e-6
+
+
+@pytest.mark.parametrize("precision,r", [(64, 4), (32, 4), (32, 1), (32, 3), (32, 6)])
+def test_teacher_forced_iterations(precision, r):
+    """Each iteration from the GPU's own particle system: reweight,
+    resampling (ancestors bit-exact on the GPU's CDF), the three Metropolis
+    blocks (states within tolerance wherever no acceptance decision is a
+    near tie) and the path-sampling integrand."""
+    need_gpu()
+    n, nd, T, seed = 4096 + 37, 300, 40, 5
+    s, y, op = make_gmm(n, nd=nd, r=r, T=T, precision=precision, seed=seed, threshold=0.8)
+    rel = 1e-11 if precision == 64 else 1e-5
+    tie = 1e-9 if precision == 64 else 2e-3
+    s.initialize()
+    ties_total = 0
+    for t in range(1, 7):
+        x_prev = s.state().astype(np.float64)
+        lw_prev = s.log_weight().astype(np.float64)
+        rec_prev = s.history(1)[0]
+        s.move()
+        lw = s.log_weight()
+        rec = s.history(1)[0]
+        a_t, a_p = ogmm.alpha(t, op), ogmm.alpha(t - 1, op)
+        ll_prev = x_prev[3 * r + 1]
+        # lw_prev is normalised by its own log-sum-exp (or equal after a gather)
+        base = lw_prev - ogmm.weights.log_sum_exp(lw_prev)[1]
+        ref_lw = base + (a_t - a_p) * ll_prev
+        assert_close(lw, ref_lw, rel, f"reweight t={t}")
+        L_ref = ogmm.weights.log_sum_exp(ref_lw)[1]
+        assert abs(rec["L"] - L_ref) < 10 * rel * max(1, abs(L_ref))
+        assert abs(rec["alpha"] - a_t) < 1e-15
+        s.resample()
+        anc = None
+        if rec["resampled"]:
+            anc = check_resample(s, lw, t, "systematic", seed, precision)
+        s.mcmc()
+        x = s.state().astype(np.float64)
+        src = anc if anc is not None else np.arange(n)
+        xin = x_prev[:, src]
+        mu, lam, om, lp, ll = split_state(xin, r)
+        st = ogmm.State(mu.copy(), lam.copy(), om.copy(), lp.copy(), ll.copy())
+        # recompute the cached values in float64 from the GPU's parameters
+        st.lprior = ogmm.log_prior(st.mu, st.lam, st.om, op)
+        st.llik = ogmm.log_lik(st.mu, st.lam, st.om, y)
+        near = np.zeros(n, dtype=bool)
+        for block in ("mu", "lambda", "weight") if r > 1 else ("mu", "lambda"):
+            st, acc, delta, logu = ogmm.mh_block(st, block, a_t, t, y, seed, op, return_delta=True)
+            near |= np.abs(delta - logu) < tie * np.maximum(1.0, np.abs(delta))
+        ok = ~near
+        ties_total += int(near.sum())
+        gm, gl, go, glp, gll = split_state(x, r)
+        assert_close(gm[:, ok], st.mu[:, ok], rel, f"mu t={t}")
+        assert_close(gl[:, ok], st.lam[:, ok], rel, f"lambda t={t}")
+        assert_close(go[:, ok], st.om[:, ok], rel, f"omega t={t}")
+        assert_close(glp[ok], st.lprior[ok], rel, f"log-prior t={t}")
+        assert_close(gll[ok], st.llik[ok], rel, f"log-likelihood t={t}")
+        rec = s.history(1)[0]
+        # U_t from the GPU's own particles (weights after resampling are equal)
+        lw_now = s.log_weight().astype(np.float64)
+        W = np.exp(lw_now - ogmm.weights.log_sum_exp(lw_now)[1])
+        assert abs(rec["path_u"] - np.sum(W * gll)) < 10 * rel * abs(rec["path_u"])
+    assert ties_total < 0.01 * n * 6
+
+
+def test_full_run_fp64_matches_oracle():
+    """FP64, every iteration free-running on both sides: identical
+    resampling decisions, standard and path-sampling estimates within 1e-8."""
+    need_gpu()
+    n, nd, r, T, seed = 2048, 100, 2, 30, 3
+    s, y, op = make_gmm(n, nd=nd, r=r, T=T, precision=64, seed=seed)
+    s.initialize()
+    s.iterate(T)
+    ds_ref, ps_ref, recs = ogmm.run(y, n, seed, op)
+    gpu = s.history(T + 1)[1:]
+    assert [g["resampled"] for g in gpu] == [o.resampled for o in recs]
+    assert abs(s.log_evidence() - ds_ref) < 1e-8
+    assert abs(s.path_sampling() - ps_ref) < 1e-8
+    for g, o in zip(gpu, recs):
+        assert abs(g["path_u"] - o.U) < 1e-8 * abs(o.U)
+        assert np.allclose(g["accept"], o.accept, atol=2.0 / n)
+
+
+def test_r1_evidence_against_quadrature_fp32():
+    """FP32 GPU sampler on the r = 1 model: both estimators agree with the
+    quadrature value of log p(y) within Monte Carlo error."""
+    need_gpu()
+    import sys
+    sys.path.insert(0, __file__.rsplit("/", 1)[0])
+    from test_oracle_gmm import _r1_log_evidence
+    g = np.random.default_rng(4)
+    y = 1.0 + g.standard_normal(20)
+    op = ogmm.GMMParams(r=1, T=60, power=4.0)
+    truth = _r1_log_evidence(y, op)
+    ds, ps = [], []
+    for seed in range(4):
+        cfg = smc.make_config(model="gmm", n=1 << 14, precision=32, scheme="systematic", threshold=0.5, seed=seed,
+                              max_data=20, max_records=61, gmm=dict(n_comp=1, n_iter=60, power=4.0))
+        s = smc.Sampler(cfg)
+        s.set_data(y)
+        s.initialize()
+        s.iterate(60)
+        ds.append(s.log_evidence())
+        ps.append(s.path_sampling())
+    assert abs(np.mean(ds) - truth) < 0.03, (ds, truth)
+    assert abs(np.mean(ps) - truth) < 0.1, (ps, truth)
+
+
+def test_benchmark_size_sampled():
+    """N = 2^16, n = 1000, r = 4 (the benchmarked GMM workload, same launch
+    configuration): a few iterations, sampled particles against the oracle."""
+    need_gpu()
+    n, r, seed = 1 << 16, 4, 0
+    s, y, op = make_gmm(n, nd=1000, r=r, T=500, precision=32, seed=seed)
+    s.initialize()
+    g = np.random.default_rng(7)
+    idx = np.sort(g.choice(n, size=512, replace=False))
+    for t in range(1, 4):
+        x_prev = s.state().astype(np.float64)
+        s.move()
+        rec = s.history(1)[0]
+        s.resample()
+        anc = s.ancestors().astype(np.int64) if rec["resampled"] else None
+        s.mcmc()
+        x = s.state().astype(np.float64)
+        src = anc[idx] if anc is not None else idx
+        mu, lam, om, lp, ll = split_state(x_prev[:, src], r)
+        st = ogmm.State(mu.copy(), lam.copy(), om.copy(), ogmm.log_prior(mu, lam, om, op),
+                        ogmm.log_lik(mu, lam, om, y))
+        # per-particle oracle moves use the particle's own counter (its slot)
+        near = np.zeros(idx.size, dtype=bool)
+        a_t = ogmm.alpha(t, op)
+        for block in ("mu", "lambda", "weight"):
+            st, acc, delta, logu = _mh_block_at(st, block, a_t, t, y, seed, op, idx)
+            near |= np.abs(delta - logu) < 2e-3 * np.maximum(1.0, np.abs(delta))
+        ok = ~near
+        gm, gl, go, glp, gll = split_state(x[:, idx], r)
+        assert_close(gm[:, ok], st.mu[:, ok], 1e-5, f"mu t={t}")
+        assert_close(gll[ok], st.llik[ok], 1e-5, f"l t={t}")
+        assert near.sum() <= 10
+
+
+def _mh_block_at(s, block, a_t, t, y, seed, p, idx):
+    """oracle.gmm.mh_block for particles at slots idx (counter = slot)."""
+    import oracle.gmm as m
+    s_mu, s_lam, s_om = m.proposal_scales(a_t)
+    tag = {"mu": ophilox.TAG_MH_MU, "lambda": ophilox.TAG_MH_LAMBDA, "weight": ophilox.TAG_MH_WEIGHT}[block]
+    r = p.r
+    mu, lam, om = s.mu.copy(), s.lam.copy(), s.om.copy()
+    jac = np.zeros(idx.size)
+    if block == "mu":
+        mu = mu + s_mu * ophilox.normals(seed, idx, t, tag, r)
+    elif block == "lambda":
+        z = s_lam * ophilox.normals(seed, idx, t, tag, r)
+        lam = np.exp(np.log(lam) + z)
+        jac = z.sum(axis=0)
+    else:
+        zr = np.log(om[:-1] / om[-1:]) + s_om * ophilox.normals(seed, idx, t, tag, r - 1)
+        full = np.concatenate([zr, np.zeros((1, idx.size))])
+        e = np.exp(full - full.max(axis=0))
+        om = e / e.sum(axis=0)
+        jac = np.log(om).sum(axis=0) - np.log(s.om).sum(axis=0)
+    lp = m.log_prior(mu, lam, om, p)
+    ll = m.log_lik(mu, lam, om, y)
+    delta = (lp + a_t * ll) - (s.lprior + a_t * s.llik) + jac
+    w = ophilox.draw_words(seed, idx, t, tag, 0, ophilox.DRAW_MH_UNIFORM)
+    logu = np.log(ophilox.uniform(w[:, 0]))
+    acc = logu <= delta
+    new = m.State(np.where(acc, mu, s.mu), np.where(acc, lam, s.lam), np.where(acc, om, s.om),
+                  np.where(acc, lp, s.lprior), np.where(acc, ll, s.llik))
+    return new, acc, delta, logu
