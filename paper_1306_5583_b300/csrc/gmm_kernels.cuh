@@ -37,9 +37,10 @@ constexpr double kLog2e = 1.44269504088896340736;
 template <typename R>
 struct GmmArgs {
     int64_t n;
+    int64_t ld;             // row pitch of the state and log-weight arrays
     int32_t nd;             // data points
     const R *y;             // data (16-byte aligned, padded to a multiple of 16 bytes)
-    R *x[2];                // state buffers; row j at x[b] + j * n
+    R *x[2];                // state buffers; row j at x[b] + j * ld
     R *lw[2];
     const int32_t *anc;
     const double *alpha;    // alpha_t, t = 0..T
@@ -203,6 +204,7 @@ struct Theta {
 
 template <typename R, int NC>
 __device__ __forceinline__ void load_theta(const R *x, int64_t n, int64_t i, Theta<R, NC> &th) {
+    // n is the row pitch
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         th.mu[j] = x[(int64_t)j * n + i];
@@ -215,6 +217,7 @@ __device__ __forceinline__ void load_theta(const R *x, int64_t n, int64_t i, The
 
 template <typename R, int NC>
 __device__ __forceinline__ void store_theta(R *x, int64_t n, int64_t i, const Theta<R, NC> &th) {
+    // n is the row pitch
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         x[(int64_t)j * n + i] = th.mu[j];
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
     const int cur = st->cur, cur_lw = st->cur_lw;
     const R lw0 = R(-a.log_n);
     if (active && q == 0) {
-        store_theta<R, NC>(a.x[cur ^ 1], a.n, i, th);
+        store_theta<R, NC>(a.x[cur ^ 1], a.ld, i, th);
         a.lw[cur_lw ^ 1][i] = lw0;
     }
     R lwv[1] = {(active && q == 0) ? lw0 : Math<R>::neg_inf()};
@@ -316,7 +319,7 @@ __global__ void __launch_bounds__(kBlock) gmm_reweight_kernel(GmmArgs<R> a) {
     const int cur = st->cur, cur_lw = st->cur_lw;
     const R *lw_in = a.lw[cur_lw];
     R *lw_out = a.lw[cur_lw ^ 1];
-    const R *ll = a.x[cur] + (int64_t)(3 * NC + 1) * a.n;
+    const R *ll = a.x[cur] + (int64_t)(3 * NC + 1) * a.ld;
     R lwv[kPfItems], zero[kPfItems];
     const int64_t b0 = (int64_t)blockIdx.x * kPfTile + threadIdx.x;
 #pragma unroll
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     const int64_t ii = active ? i : a.n - 1;
     const int64_t src = gather ? (int64_t)__ldg(&a.anc[ii]) : ii;
     Theta<R, NC> th;
-    load_theta<R, NC>(a.x[cur], a.n, src, th);
+    load_theta<R, NC>(a.x[cur], a.ld, src, th);
     double ll = double(th.ll), lp = double(th.lp);
     uint32_t acc_mask = 0;
     // block 1: mu
@@ -458,7 +461,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     th.ll = R(ll);
     R lwi = R(-a.log_n);
     if (active && q == 0) {
-        store_theta<R, NC>(a.x[cur ^ 1], a.n, i, th);
+        store_theta<R, NC>(a.x[cur ^ 1], a.ld, i, th);
         if (gather) a.lw[cur_lw][i] = lwi;  // equal weights after resampling
         else lwi = a.lw[cur_lw][i];
         atomicAdd(&s_acc[0], acc_mask & 1u);

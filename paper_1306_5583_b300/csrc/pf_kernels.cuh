@@ -48,65 +48,73 @@ __device__ __forceinline__ R cv_loglik(const PfArgs<R> &a, R yx, R yy, R px, R p
         return a.ll_const - a.half_nu1 * (Math<R>::log1p(zx * zx * a.inv_nu) + Math<R>::log1p(zy * zy * a.inv_nu));
 }
 
+// One thread owns kPfItems consecutive particles: every input is fetched
+// with 16-byte vector loads (or, after resampling, as independent gathers
+// through one vector load of ancestor indices) before any arithmetic, so
+// the memory system sees all of a thread's requests at once.
 template <typename R>
 __global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
+    constexpr int E = kPfItems;
     DevState *st = a.st;
     if (*(volatile int32_t *)&st->error) return;
     const int32_t t = st->t + 1;
     const int cur = st->cur;
     const bool gather = (t > 0) && (st->ready != 0);
+    const int cur_lw = st->cur_lw;
+    const uint32_t n = (uint32_t)a.n;
+    const uint32_t i0 = (blockIdx.x * (uint32_t)kBlock + threadIdx.x) * (uint32_t)E;
+
+    R v0[E], v1[E], v2[E], v3[E], lwin[E];
+    if (t > 0) {
+        if (gather) {
+            int32_t src[E];
+            load_idx4(a.anc, i0, n, src);
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const uint32_t sidx = (i0 + j < n) ? (uint32_t)src[j] : 0u;
+                v0[j] = __ldg(a.x[cur][0] + sidx);
+                v1[j] = __ldg(a.x[cur][1] + sidx);
+                v2[j] = __ldg(a.x[cur][2] + sidx);
+                v3[j] = __ldg(a.x[cur][3] + sidx);
+            }
+        } else {
+            load_k<R, E>(a.x[cur][0], i0, n, v0);
+            load_k<R, E>(a.x[cur][1], i0, n, v1);
+            load_k<R, E>(a.x[cur][2], i0, n, v2);
+            load_k<R, E>(a.x[cur][3], i0, n, v3);
+            load_k<R, E>(a.lw[cur_lw], i0, n, lwin);
+        }
+    }
     const Shift<R> Lprev(st->log_norm);
     const R yx = R(a.obs[2 * t]), yy = R(a.obs[2 * t + 1]);
     const R base_eq = R(-a.log_n);
-    const int cur_lw = st->cur_lw;
-    const R *__restrict__ lw_in = a.lw[cur_lw];
-    R *__restrict__ lw_out = a.lw[cur_lw ^ 1];
-    const R *__restrict__ x0s = a.x[cur][0];
-    const R *__restrict__ x1s = a.x[cur][1];
-    const R *__restrict__ x2s = a.x[cur][2];
-    const R *__restrict__ x3s = a.x[cur][3];
-    R *__restrict__ x0d = a.x[cur ^ 1][0];
-    R *__restrict__ x1d = a.x[cur ^ 1][1];
-    R *__restrict__ x2d = a.x[cur ^ 1][2];
-    R *__restrict__ x3d = a.x[cur ^ 1][3];
-    const uint32_t n = (uint32_t)a.n;
-
-    R lwv[kPfItems], px[kPfItems], py[kPfItems], zero[kPfItems];
-    const uint32_t base = blockIdx.x * (uint32_t)kPfTile + threadIdx.x;
+    R s0[E], s1[E], s2[E], s3[E], lwv[E], zero[E];
 #pragma unroll
-    for (int j = 0; j < kPfItems; ++j) {
-        const uint32_t i = base + (uint32_t)(j * kBlock);
-        lwv[j] = Math<R>::neg_inf();
-        px[j] = py[j] = zero[j] = R(0);
-        if (i < n) {
-            R s0, s1, s2, s3, z[4];
-            if (t == 0) {
-                normals4_fast<R>(draw(a.key, i, 0u, TAG_INIT, a.stream, 0u), z);
-                s0 = a.sd_pos0 * z[0];
-                s1 = a.sd_pos0 * z[1];
-                s2 = a.sd_vel0 * z[2];
-                s3 = a.sd_vel0 * z[3];
-            } else {
-                const uint32_t src = gather ? (uint32_t)__ldg(&a.anc[i]) : i;
-                const R v0 = x0s[src], v1 = x1s[src], v2 = x2s[src], v3 = x3s[src];
-                normals4_fast<R>(draw(a.key, i, (uint32_t)t, TAG_MOVE, a.stream, 0u), z);
-                s0 = v0 + a.delta * v2 + a.sd_pos * z[0];
-                s1 = v1 + a.delta * v3 + a.sd_pos * z[1];
-                s2 = v2 + a.sd_vel * z[2];
-                s3 = v3 + a.sd_vel * z[3];
-            }
-            x0d[i] = s0;
-            x1d[i] = s1;
-            x2d[i] = s2;
-            x3d[i] = s3;
-            const R b = (t == 0 || gather) ? base_eq : Lprev.sub_from(lw_in[i]);
-            lwv[j] = b + cv_loglik(a, yx, yy, s0, s1);
-            lw_out[i] = lwv[j];
-            px[j] = s0;
-            py[j] = s1;
+    for (int j = 0; j < E; ++j) {
+        R z[4];
+        zero[j] = R(0);
+        if (t == 0) {
+            normals4_fast<R>(draw(a.key, i0 + j, 0u, TAG_INIT, a.stream, 0u), z);
+            s0[j] = a.sd_pos0 * z[0];
+            s1[j] = a.sd_pos0 * z[1];
+            s2[j] = a.sd_vel0 * z[2];
+            s3[j] = a.sd_vel0 * z[3];
+        } else {
+            normals4_fast<R>(draw(a.key, i0 + j, (uint32_t)t, TAG_MOVE, a.stream, 0u), z);
+            s0[j] = v0[j] + a.delta * v2[j] + a.sd_pos * z[0];
+            s1[j] = v1[j] + a.delta * v3[j] + a.sd_pos * z[1];
+            s2[j] = v2[j] + a.sd_vel * z[2];
+            s3[j] = v3[j] + a.sd_vel * z[3];
         }
+        const R b = (t == 0 || gather) ? base_eq : Lprev.sub_from(lwin[j]);
+        lwv[j] = (i0 + j < n) ? b + cv_loglik(a, yx, yy, s0[j], s1[j]) : Math<R>::neg_inf();
     }
-    block_partial<R, kPfItems>(lwv, px, py, zero, &a.part[blockIdx.x]);
+    store_k<R, E>(a.x[cur ^ 1][0], i0, n, s0);
+    store_k<R, E>(a.x[cur ^ 1][1], i0, n, s1);
+    store_k<R, E>(a.x[cur ^ 1][2], i0, n, s2);
+    store_k<R, E>(a.x[cur ^ 1][3], i0, n, s3);
+    store_k<R, E>(a.lw[cur_lw ^ 1], i0, n, lwv);
+    block_partial<R, E>(lwv, s0, s1, zero, &a.part[blockIdx.x]);
     Combined c;
     if (!last_block_combine<R>(st, a.part, &c)) return;
     if (threadIdx.x == 0) {

@@ -39,7 +39,36 @@ struct QGen {
     __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
         return Math<R>::fixed(Math<R>::exp(cur_lw[i] - m), frac);
     }
+    // kScanItems consecutive values from 16-byte vector loads
+    static constexpr bool kVec = true;
+    __device__ __forceinline__ void load8(uint32_t i0, uint32_t n, unsigned long long (&v)[kScanItems]) const {
+        R w[kScanItems];
+        load_k<R, kScanItems>(cur_lw, i0, n, w);
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j)
+            v[j] = (i0 + j < n) ? Math<R>::fixed(Math<R>::exp(w[j] - m), frac) : 0ull;
+    }
 };
+
+// kScanItems consecutive generator values starting at i0 (0 past n)
+template <class Gen, typename = void>
+struct HasVec {
+    static constexpr bool value = false;
+};
+template <class Gen>
+struct HasVec<Gen, decltype((void)Gen::kVec, void())> {
+    static constexpr bool value = Gen::kVec;
+};
+
+template <class Gen>
+__device__ __forceinline__ void gen_items(const Gen &g, int64_t i0, int64_t n, unsigned long long (&v)[kScanItems]) {
+    if constexpr (HasVec<Gen>::value) {
+        g.load8((uint32_t)i0, (uint32_t)n, v);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) v[j] = (i0 + j < n) ? g(i0 + j) : 0ull;
+    }
+}
 
 // values read from an array (bucket counts)
 struct CountGen {
@@ -255,13 +284,12 @@ __global__ void __launch_bounds__(kBlock) tile_reduce_kernel(Gen gen, int64_t n,
     if (gated_out(st, gate)) return;
     Gen g = gen;
     g.prepare(st);
-    const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+    const int64_t i0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    unsigned long long v[kScanItems];
+    gen_items(g, i0, n, v);
     unsigned long long acc = 0;
 #pragma unroll
-    for (int r = 0; r < kScanItems; ++r) {
-        const int64_t i = t0 + r * kBlock + threadIdx.x;
-        if (i < n) acc += g(i);
-    }
+    for (int j = 0; j < kScanItems; ++j) acc += v[j];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -323,17 +351,12 @@ __global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, O
     g.prepare(st);
     const int64_t t0 = (int64_t)tile * kScanTile;
     const int len = (int)min((int64_t)kScanTile, n - t0);
-#pragma unroll
-    for (int r = 0; r < kScanItems; ++r) {
-        const int idx = r * kBlock + tid;
-        s_q[idx] = (idx < len) ? g(t0 + idx) : 0ull;
-    }
-    __syncthreads();
     unsigned long long loc[kScanItems];
+    gen_items(g, t0 + (int64_t)tid * kScanItems, n, loc);
     unsigned long long acc = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        acc += s_q[tid * kScanItems + j];
+        acc += loc[j];
         loc[j] = acc;
     }
     const unsigned long long winc = warp_incl_scan(acc);

@@ -38,6 +38,7 @@ int ceil_log2(int64_t n) {
 struct Layout {
     size_t st, rec, part, x, lw, anc, Q, tsum, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, alpha, total;
     int d;            // state rows
+    int64_t ld;       // row pitch in elements (N rounded up to 64: 16-byte aligned rows)
     int64_t nbw;      // blocks of the weighting kernels
     int64_t ntiles;   // scan tiles of an N-element scan
     int64_t nbuckets;
@@ -72,6 +73,7 @@ Layout make_layout(const smc_config *c) {
     const size_t rs = (c->precision == 32) ? 4 : 8;
     L.rsize = rs;
     L.d = (c->model == SMC_MODEL_GMM) ? 3 * c->gmm.n_comp + 2 : 4;
+    L.ld = (n + 63) & ~int64_t(63);
     L.nbw = (n + kPfTile - 1) / kPfTile;
     L.ntiles = (n + kScanTile - 1) / kScanTile;
     const int B = std::min(24, std::max(1, ceil_log2(n)));
@@ -92,9 +94,9 @@ Layout make_layout(const smc_config *c) {
     const int64_t nblk = (c->model == SMC_MODEL_GMM) ? std::max<int64_t>(L.nbw, (kQuad * n + kBlock - 1) / kBlock)
                                                      : L.nbw;
     L.part = take(sizeof(Partial) * (size_t)std::max<int64_t>(nblk, 1));
-    L.x = take(2 * (size_t)L.d * n * rs);
-    L.lw = take(2 * (size_t)n * rs);
-    L.anc = take((size_t)n * 4);
+    L.x = take(2 * (size_t)L.d * L.ld * rs);
+    L.lw = take(2 * (size_t)L.ld * rs);
+    L.anc = take((size_t)L.ld * 4);
     L.Q = take((size_t)n * 8);
     L.tsum = take((size_t)kScanSlots * L.ntiles_status * 8);
     L.cnt = take(sorts ? (size_t)L.nbuckets * 4 : 0);
@@ -180,7 +182,7 @@ PfArgs<R> pf_args(smc_ctx *c) {
     a.n = n;
     for (int b = 0; b < 2; ++b) {
         R *base = static_cast<R *>(c->x[b]);
-        for (int r = 0; r < 4; ++r) a.x[b][r] = base + (size_t)r * n;
+        for (int r = 0; r < 4; ++r) a.x[b][r] = base + (size_t)r * c->L.ld;
         a.lw[b] = static_cast<R *>(c->lw[b]);
     }
     a.anc = c->anc;
@@ -388,11 +390,11 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->st = reinterpret_cast<DevState *>(c->ws + L.st);
     c->rec = reinterpret_cast<smc_record *>(c->ws + L.rec);
     c->part = reinterpret_cast<Partial *>(c->ws + L.part);
-    const size_t half_x = (size_t)L.d * cfg->n_particles * L.rsize;
+    const size_t half_x = (size_t)L.d * L.ld * L.rsize;
     c->x[0] = c->ws + L.x;
     c->x[1] = c->ws + L.x + half_x;
     c->lw[0] = c->ws + L.lw;
-    c->lw[1] = c->ws + L.lw + (size_t)cfg->n_particles * L.rsize;
+    c->lw[1] = c->ws + L.lw + (size_t)L.ld * L.rsize;
     c->anc = reinterpret_cast<int32_t *>(c->ws + L.anc);
     c->Q = reinterpret_cast<unsigned long long *>(c->ws + L.Q);
     c->tsum = reinterpret_cast<unsigned long long *>(c->ws + L.tsum);
@@ -555,12 +557,24 @@ static int copy_out(smc_ctx *c, void *dst, const void *src, size_t bytes, int on
     return rc2 ? rc2 : rc;
 }
 
+// state rows are stored with a pitch of ld elements; callers see d x N packed
+static int copy_rows(smc_ctx *c, void *dst, const void *src, int rows, bool to_caller, int on_device) {
+    const size_t w = (size_t)c->cfg.n_particles * c->L.rsize, pitch = (size_t)c->L.ld * c->L.rsize;
+    cudaMemcpyKind k;
+    if (to_caller) k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    else k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t dpitch = to_caller ? w : pitch, spitch = to_caller ? pitch : w;
+    int rc = cuda_check(cudaMemcpy2DAsync(dst, dpitch, src, spitch, w, (size_t)rows, k, c->stream));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream));
+    return rc;
+}
+
 int smc_read_state(smc_ctx *c, void *dst, int on_device) {
-    if (!c) return SMC_E_ARG;
+    if (!c || !dst) return SMC_E_ARG;
     int rc = read_state(c);
     if (rc != SMC_OK && rc != SMC_E_NONFINITE) return rc;
-    const size_t bytes = (size_t)c->L.d * c->cfg.n_particles * c->L.rsize;
-    return copy_out(c, dst, c->x[c->host_st.cur & 1], bytes, on_device);
+    const int rc2 = copy_rows(c, dst, c->x[c->host_st.cur & 1], c->L.d, true, on_device);
+    return rc2 ? rc2 : rc;
 }
 
 int smc_read_log_weight(smc_ctx *c, void *dst, int on_device) {
@@ -607,11 +621,7 @@ int smc_write_state(smc_ctx *c, const void *src, int on_device) {
     if (!c || !src) return SMC_E_ARG;
     int rc = read_state(c);
     if (rc) return rc;
-    const size_t bytes = (size_t)c->L.d * c->cfg.n_particles * c->L.rsize;
-    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    rc = cuda_check(cudaMemcpyAsync(c->x[c->host_st.cur & 1], src, bytes, k, c->stream));
-    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream));
-    return rc;
+    return copy_rows(c, c->x[c->host_st.cur & 1], src, c->L.d, false, on_device);
 }
 
 int smc_write_log_weight(smc_ctx *c, const void *src, int on_device) {
@@ -713,6 +723,7 @@ GmmArgs<R> gmm_args(smc_ctx *c) {
     const smc_gmm_params &g = cfg.gmm;
     const int64_t n = cfg.n_particles;
     a.n = n;
+    a.ld = c->L.ld;
     a.nd = (int32_t)c->n_obs;
     a.y = (sizeof(R) == 4) ? reinterpret_cast<const R *>(c->obs_f) : reinterpret_cast<const R *>(c->obs);
     for (int b = 0; b < 2; ++b) {

@@ -100,7 +100,9 @@ __device__ __forceinline__ void box_muller(R u0, R u1, R &z0, R &z1) {
 // the hardware sine/cosine are accurate to about 2^-21 absolute, using
 // cos(2 pi u) = -cos(2 pi u - pi) and sin(2 pi u) = -sin(2 pi u - pi).
 __device__ __forceinline__ void box_muller_fast(float u0, float u1, float &z0, float &z1) {
-    const float r = sqrtf(-2.0f * __logf(u0));
+    // the radius needs an accurate log: near u0 = 1 the MUFU log has an
+    // absolute (not relative) error that would dominate sqrt(-2 ln u0)
+    const float r = sqrtf(-2.0f * logf(u0));
     const float th = fmaf(6.2831853071795864769f, u1, -3.14159265358979323846f);
     float s, c;
     __sincosf(th, &s, &c);
@@ -123,6 +125,51 @@ __device__ __forceinline__ void normals4_fast(uint4 w, R z[4]) {
         box_muller_fast(uniform01<float>(w.z), uniform01<float>(w.w), z[2], z[3]);
     } else {
         normals4<R>(w, z);
+    }
+}
+
+// ---- vector loads of K consecutive elements ----------------------------------
+// Thread-contiguous items let every load be a 16-byte vector load; a partial
+// group (the ragged tail) falls back to guarded scalar loads.
+template <typename R, int K>
+__device__ __forceinline__ void load_k(const R *__restrict__ p, uint32_t i0, uint32_t n, R (&v)[K]) {
+    static_assert((K * sizeof(R)) % 16 == 0, "vector width");
+    if (i0 + K <= n) {
+        const float4 *q = reinterpret_cast<const float4 *>(p + i0);
+#pragma unroll
+        for (int c = 0; c < (int)(K * sizeof(R) / 16); ++c) {
+            const float4 w = __ldg(q + c);
+            reinterpret_cast<float4 *>(v)[c] = w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) v[j] = (i0 + j < n) ? p[i0 + j] : R(0);
+    }
+}
+
+template <typename R, int K>
+__device__ __forceinline__ void store_k(R *__restrict__ p, uint32_t i0, uint32_t n, const R (&v)[K]) {
+    if (i0 + K <= n) {
+        float4 *q = reinterpret_cast<float4 *>(p + i0);
+#pragma unroll
+        for (int c = 0; c < (int)(K * sizeof(R) / 16); ++c) q[c] = reinterpret_cast<const float4 *>(v)[c];
+    } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (i0 + j < n) p[i0 + j] = v[j];
+    }
+}
+
+__device__ __forceinline__ void load_idx4(const int32_t *__restrict__ p, uint32_t i0, uint32_t n, int32_t (&v)[4]) {
+    if (i0 + 4 <= n) {
+        const int4 w = __ldg(reinterpret_cast<const int4 *>(p + i0));
+        v[0] = w.x;
+        v[1] = w.y;
+        v[2] = w.z;
+        v[3] = w.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = (i0 + j < n) ? p[i0 + j] : 0;
     }
 }
 
