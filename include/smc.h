@@ -217,6 +217,46 @@ int smc_sync(smc_ctx *ctx);
 
 const char *smc_error_string(int code);
 
+/* ---- batched form: many independent filters in one launch per kernel ----
+ *
+ * n_filters constant-velocity particle filters (cfg->model SMC_MODEL_CV or
+ * SMC_MODEL_CV_GAUSS, systematic or stratified resampling) that share the
+ * model constants, the precision, the threshold and the seed of cfg, each
+ * with its own particle count n_particles[b] (1..2^30), its own number of
+ * iterations n_iter[b] (= its number of observations) and its own Philox
+ * stream cfg->stream_id + b.  Every iteration advances all filters that
+ * have observations left with one launch per kernel (a persistent grid over
+ * the active filters' tiles); a filter's results equal, bit for bit, a
+ * plain context's run on the same stream.  Workspace, stream and error
+ * conventions are the plain context's.
+ */
+typedef struct smc_batch smc_batch;
+
+size_t smc_batch_workspace_bytes(const smc_config *cfg, const int64_t *n_particles, const int32_t *n_iter,
+                                 int32_t n_filters);
+int smc_batch_create(smc_batch **out, const smc_config *cfg, const int64_t *n_particles, const int32_t *n_iter,
+                     int32_t n_filters, void *d_workspace, size_t bytes, void *cuda_stream);
+int smc_batch_destroy(smc_batch *b);
+/* observations of filter `filter`: n_iter[filter] rows of (x_obs, y_obs) float64 */
+int smc_batch_set_data(smc_batch *b, int32_t filter, const double *obs, int on_device);
+/* iteration 0 of every filter (prior draw, weighting by Y_0, resampling) */
+int smc_batch_initialize(smc_batch *b);
+/* n further iterations of every filter with observations left (CUDA graph
+ * replay when the stream is not the legacy default stream) */
+int smc_batch_iterate(smc_batch *b, int32_t n);
+/* initialize, then iterate until every filter has used all its observations */
+int smc_batch_run(smc_batch *b);
+/* autotuner: times the persistent grid sizes 1, 2, 4 and 8 blocks per SM on
+ * the first iterations, keeps the fastest (returned in *blocks_per_sm) and
+ * re-initializes */
+int smc_batch_tune(smc_batch *b, int32_t *blocks_per_sm);
+/* per-filter log-evidence estimates, n_filters values in caller order */
+int smc_batch_log_evidence(smc_batch *b, double *h_out);
+int smc_batch_read_history(smc_batch *b, int32_t filter, smc_record *h_records, int32_t count,
+                           int32_t *n_written);
+/* state of one filter: 4 rows of n_particles[filter] values */
+int smc_batch_read_state(smc_batch *b, int32_t filter, void *dst, int on_device);
+
 /* ---- stateless primitives (device pointers, caller's stream) ---- */
 
 /* Philox4x32-10: out[i] = philox(ctr[i], key) for i < n; ctr and out are

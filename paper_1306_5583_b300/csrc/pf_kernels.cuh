@@ -48,22 +48,18 @@ __device__ __forceinline__ R cv_loglik(const PfArgs<R> &a, R yx, R yy, R px, R p
         return a.ll_const - a.half_nu1 * (Math<R>::log1p(zx * zx * a.inv_nu) + Math<R>::log1p(zy * zy * a.inv_nu));
 }
 
-// One thread owns kPfItems consecutive particles: every input is fetched
-// with 16-byte vector loads (or, after resampling, as independent gathers
+// One tile (kPfTile particles, block-local index blk) of the fused
+// gather + move + weight step, ending in the tile's block partial.  One
+// thread owns kPfItems consecutive particles: every input is fetched with
+// 16-byte vector loads (or, after resampling, as independent gathers
 // through one vector load of ancestor indices) before any arithmetic, so
 // the memory system sees all of a thread's requests at once.
 template <typename R>
-__global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
+__device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_t t, int cur, int cur_lw,
+                                        bool gather, double log_norm_prev) {
     constexpr int E = kPfItems;
-    DevState *st = a.st;
-    if (*(volatile int32_t *)&st->error) return;
-    const int32_t t = st->t + 1;
-    const int cur = st->cur;
-    const bool gather = (t > 0) && (st->ready != 0);
-    const int cur_lw = st->cur_lw;
     const uint32_t n = (uint32_t)a.n;
-    const uint32_t i0 = (blockIdx.x * (uint32_t)kBlock + threadIdx.x) * (uint32_t)E;
-
+    const uint32_t i0 = (blk * (uint32_t)kBlock + threadIdx.x) * (uint32_t)E;
     R v0[E], v1[E], v2[E], v3[E], lwin[E];
     if (t > 0) {
         if (gather) {
@@ -85,7 +81,7 @@ __global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
             load_k<R, E>(a.lw[cur_lw], i0, n, lwin);
         }
     }
-    const Shift<R> Lprev(st->log_norm);
+    const Shift<R> Lprev(log_norm_prev);
     const R yx = R(a.obs[2 * t]), yy = R(a.obs[2 * t + 1]);
     const R base_eq = R(-a.log_n);
     R s0[E], s1[E], s2[E], s3[E], lwv[E], zero[E];
@@ -114,9 +110,16 @@ __global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
     store_k<R, E>(a.x[cur ^ 1][2], i0, n, s2);
     store_k<R, E>(a.x[cur ^ 1][3], i0, n, s3);
     store_k<R, E>(a.lw[cur_lw ^ 1], i0, n, lwv);
-    block_partial<R, E>(lwv, s0, s1, zero, &a.part[blockIdx.x]);
+    block_partial<R, E>(lwv, s0, s1, zero, &a.part[blk]);
+}
+
+// Last tile of a filter: combine its nblk partials, write the record of
+// iteration t and advance the filter's state.
+template <typename R>
+__device__ __forceinline__ void pf_finalize(const PfArgs<R> &a, DevState *st, int nblk, int32_t t, int cur,
+                                            int cur_lw) {
     Combined c;
-    if (!last_block_combine<R>(st, a.part, &c)) return;
+    combine_partials<R>(a.part, nblk, &c);
     if (threadIdx.x == 0) {
         FinalizeArgs f{st, a.rec, a.rec_cap, t, 0, a.n, a.threshold, 0.0};
         double L;
@@ -127,6 +130,18 @@ __global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
             st->ready = 0;
         }
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
+    DevState *st = a.st;
+    if (*(volatile int32_t *)&st->error) return;
+    const int32_t t = st->t + 1;
+    const int cur = st->cur, cur_lw = st->cur_lw;
+    const bool gather = (t > 0) && (st->ready != 0);
+    pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, st->log_norm);
+    if (!take_ticket<R>(st)) return;
+    pf_finalize<R>(a, st, gridDim.x, t, cur, cur_lw);
 }
 
 }  // namespace smc

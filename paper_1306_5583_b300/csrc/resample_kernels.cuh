@@ -19,7 +19,7 @@
 // uniforms) by a search over the shared-memory CDF tile.
 #pragma once
 
-#include "smc_device.cuh"
+#include "weight_reduce.cuh"
 
 namespace smc {
 
@@ -273,72 +273,81 @@ __device__ __forceinline__ bool gated_out(DevState *st, int gate) {
     return gate && !*(volatile int32_t *)&st->due;
 }
 
-// Sum of gen(i) over each tile of kScanTile elements -> tsum[tile]; the last
-// block writes the exact total to *total.
+// Sum of gen(i) over tile `tile` (kScanTile elements), returned to thread 0.
 template <class Gen>
-__global__ void __launch_bounds__(kBlock) tile_reduce_kernel(Gen gen, int64_t n, unsigned long long *tsum,
-                                                             unsigned long long *total, uint32_t *ticket,
-                                                             DevState *st, int gate) {
+__device__ __forceinline__ unsigned long long tile_sum(const Gen &g, int64_t n, int tile) {
     __shared__ unsigned long long s_w[kBlock / 32];
-    __shared__ bool s_last;
-    if (gated_out(st, gate)) return;
-    Gen g = gen;
-    g.prepare(st);
-    const int64_t i0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    const int64_t i0 = (int64_t)tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
     unsigned long long v[kScanItems];
     gen_items(g, i0, n, v);
     unsigned long long acc = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) acc += v[j];
     acc = warp_sum(acc);
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long s = 0;
+    unsigned long long s = 0;
+    if (threadIdx.x == 0)
 #pragma unroll
         for (int w = 0; w < kBlock / 32; ++w) s += s_w[w];
-        tsum[blockIdx.x] = s;
-        __threadfence();
-        s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    return s;
+}
+
+// Exact sum of nt tile sums by the whole block (thread 0 receives it).
+__device__ __forceinline__ unsigned long long sum_tiles(const unsigned long long *tsum, int nt) {
+    __shared__ unsigned long long s_w[kBlock / 32];
     unsigned long long tot = 0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += kBlock) tot += __ldcg(&tsum[b]);
+    for (int b = threadIdx.x; b < nt; b += kBlock) tot += __ldcg(&tsum[b]);
     tot = warp_sum(tot);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = tot;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long s = 0;
+    unsigned long long s = 0;
+    if (threadIdx.x == 0)
 #pragma unroll
         for (int w = 0; w < kBlock / 32; ++w) s += s_w[w];
-        *total = s;
+    return s;
+}
+
+// Sum of gen(i) over each tile of kScanTile elements -> tsum[tile]; the last
+// block writes the exact total to *total.
+template <class Gen>
+__global__ void __launch_bounds__(kBlock) tile_reduce_kernel(Gen gen, int64_t n, unsigned long long *tsum,
+                                                             unsigned long long *total, uint32_t *ticket,
+                                                             DevState *st, int gate) {
+    if (gated_out(st, gate)) return;
+    Gen g = gen;
+    g.prepare(st);
+    const unsigned long long s = tile_sum(g, n, blockIdx.x);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = s;
+    if (!last_arrival(ticket, gridDim.x)) return;
+    const unsigned long long tot = sum_tiles(tsum, gridDim.x);
+    if (threadIdx.x == 0) {
+        *total = tot;
         *ticket = 0;
     }
 }
 
-// Per tile: exclusive prefix from the tile sums, inclusive scan of the
-// tile's values in shared memory (optionally stored through `sink`), then
-// the ancestors of every output whose target falls in the tile's CDF range.
+// One tile: exclusive prefix from the tile sums before it, inclusive scan
+// of the tile's values in shared memory (optionally stored through `sink`),
+// then the ancestors of every output whose target falls in the tile's CDF
+// range.  g and tg are prepared by the caller; tsum[0] is the scan's first
+// tile.
 template <class Gen, class Tgt, class Out, class Sink>
-__global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, Out out, Sink sink, int64_t n,
-                                                             const unsigned long long *tsum,
-                                                             const unsigned long long *total, DevState *st, int gate,
-                                                             int set_ready) {
+__device__ __forceinline__ void scan_select_tile(const Gen &g, const Tgt &tg, const Out &out, const Sink &sink,
+                                                 int64_t n, int tile, const unsigned long long *tsum,
+                                                 unsigned long long QN, DevState *st) {
     __shared__ unsigned long long s_q[kScanTile];
     __shared__ int32_t s_a[kScanTile];
     __shared__ unsigned long long s_w[kBlock / 32];
     __shared__ unsigned long long s_pre;
-    if (gated_out(st, gate)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
-    if (set_ready && tile == 0 && tid == 0) st->ready = 1;
     // exclusive prefix of this tile
     unsigned long long pre = 0;
     for (int b = tid; b < tile; b += kBlock) pre += __ldcg(&tsum[b]);
     pre = warp_sum(pre);
+    __syncthreads();
     if (lane == 0) s_w[warp] = pre;
     __syncthreads();
     if (tid == 0) {
@@ -347,8 +356,6 @@ __global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, O
         for (int w = 0; w < kBlock / 32; ++w) s += s_w[w];
         s_pre = s;
     }
-    Gen g = gen;
-    g.prepare(st);
     const int64_t t0 = (int64_t)tile * kScanTile;
     const int len = (int)min((int64_t)kScanTile, n - t0);
     unsigned long long loc[kScanItems];
@@ -378,11 +385,10 @@ __global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, O
             if (idx < len) sink(t0 + idx, s_q[idx], st);
         }
     }
-    if (!Tgt::kActive) return;
-    Tgt tg = tgt;
-    tg.prepare(st);
-    const unsigned long long QN = *(const volatile unsigned long long *)total;
-    if (QN == 0) return;
+    if (!Tgt::kActive || QN == 0) {
+        __syncthreads();
+        return;
+    }
     const unsigned long long D = tg.denom();
     const unsigned long long q_lo = s_pre, q_hi = s_q[len - 1];
     const int64_t cnt = tg.count();
@@ -419,6 +425,21 @@ __global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, O
         for (int j = tid; j < m; j += kBlock) out(kb + j, s_a[j]);
         __syncthreads();
     }
+}
+
+template <class Gen, class Tgt, class Out, class Sink>
+__global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, Out out, Sink sink, int64_t n,
+                                                             const unsigned long long *tsum,
+                                                             const unsigned long long *total, DevState *st, int gate,
+                                                             int set_ready) {
+    if (gated_out(st, gate)) return;
+    if (set_ready && blockIdx.x == 0 && threadIdx.x == 0) st->ready = 1;
+    Gen g = gen;
+    g.prepare(st);
+    Tgt tg = tgt;
+    tg.prepare(st);
+    const unsigned long long QN = *(const volatile unsigned long long *)total;
+    scan_select_tile(g, tg, out, sink, n, blockIdx.x, tsum, QN, st);
 }
 
 // ------------------------------------------------- sorting iid uniforms --

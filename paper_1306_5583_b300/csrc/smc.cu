@@ -4,12 +4,16 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
+#include <numeric>
+#include <vector>
 
 #include "pf_kernels.cuh"
 #include "resample_kernels.cuh"
 #include "gmm_kernels.cuh"
+#include "batch_kernels.cuh"
 
 using namespace smc;
 
@@ -818,3 +822,451 @@ int gmm_mcmc(smc_ctx *c) {
 }
 
 }  // namespace
+
+// ============================================================== batched ==
+
+namespace {
+
+struct BatchPlan {
+    int32_t nf = 0, tmax = 0, ntiles = 0, nstiles = 0;
+    int64_t ntot = 0;  // concatenated particles (each filter padded to 64)
+    std::vector<int32_t> perm;  // internal -> caller index
+    std::vector<int64_t> n, off, obs_off, rec_off;
+    std::vector<int32_t> T, tfirst, sfirst, tile_filter, stile_filter, act_tiles, act_stiles, frac;
+    std::vector<uint32_t> stream_of;
+    std::vector<double> log_n;
+    size_t o_fst, o_bs, o_rec, o_part, o_tsum, o_x, o_lw, o_anc, o_obs, o_n, o_off, o_obs_off, o_rec_off, o_T,
+        o_tfirst, o_sfirst, o_tf, o_stf, o_act, o_acts, o_stream, o_logn, o_frac, total = 0;
+    size_t rsize = 4;
+};
+
+bool batch_valid(const smc_config *cfg, const int64_t *n, const int32_t *T, int32_t nf) {
+    if (!cfg || !n || !T || nf < 1 || nf > 65536) return false;
+    if (cfg->model != SMC_MODEL_CV && cfg->model != SMC_MODEL_CV_GAUSS) return false;
+    if (cfg->precision != 32 && cfg->precision != 64) return false;
+    if (cfg->scheme != SMC_SYSTEMATIC && cfg->scheme != SMC_STRATIFIED) return false;
+    if (!(cfg->threshold == cfg->threshold) || !(cfg->cv.obs_scale > 0) || !(cfg->cv.obs_df > 0)) return false;
+    for (int32_t b = 0; b < nf; ++b)
+        if (n[b] < 1 || n[b] > (int64_t(1) << 30) || T[b] < 1) return false;
+    return true;
+}
+
+bool batch_plan(const smc_config *cfg, const int64_t *n, const int32_t *T, int32_t nf, BatchPlan &P) {
+    if (!batch_valid(cfg, n, T, nf)) return false;
+    P.nf = nf;
+    P.rsize = (cfg->precision == 32) ? 4 : 8;
+    P.perm.resize(nf);
+    std::iota(P.perm.begin(), P.perm.end(), 0);
+    std::stable_sort(P.perm.begin(), P.perm.end(), [&](int32_t a, int32_t b) { return T[a] > T[b]; });
+    P.n.resize(nf);
+    P.off.resize(nf);
+    P.obs_off.resize(nf);
+    P.rec_off.resize(nf);
+    P.T.resize(nf);
+    P.tfirst.resize(nf + 1);
+    P.sfirst.resize(nf + 1);
+    P.frac.resize(nf);
+    P.stream_of.resize(nf);
+    P.log_n.resize(nf);
+    int64_t o = 0, oo = 0;
+    int32_t tf = 0, sf = 0;
+    for (int32_t i = 0; i < nf; ++i) {
+        const int32_t b = P.perm[i];
+        P.n[i] = n[b];
+        P.T[i] = T[b];
+        P.off[i] = o;
+        o += (n[b] + 63) & ~int64_t(63);
+        P.obs_off[i] = oo;
+        P.rec_off[i] = oo;
+        oo += T[b];
+        P.tfirst[i] = tf;
+        tf += (int32_t)((n[b] + kPfTile - 1) / kPfTile);
+        P.sfirst[i] = sf;
+        sf += (int32_t)((n[b] + kScanTile - 1) / kScanTile);
+        P.frac[i] = 61 - ceil_log2(n[b]);
+        P.stream_of[i] = cfg->stream_id + (uint32_t)b;
+        P.log_n[i] = std::log((double)n[b]);
+    }
+    P.tfirst[nf] = tf;
+    P.sfirst[nf] = sf;
+    P.ntot = o;
+    P.ntiles = tf;
+    P.nstiles = sf;
+    P.tmax = P.T[0];
+    P.tile_filter.resize(tf);
+    P.stile_filter.resize(sf);
+    for (int32_t i = 0; i < nf; ++i) {
+        for (int32_t k = P.tfirst[i]; k < P.tfirst[i + 1]; ++k) P.tile_filter[k] = i;
+        for (int32_t k = P.sfirst[i]; k < P.sfirst[i + 1]; ++k) P.stile_filter[k] = i;
+    }
+    // filters active at iteration t: those with T > t, a prefix in this order
+    P.act_tiles.assign(P.tmax, 0);
+    P.act_stiles.assign(P.tmax, 0);
+    int32_t a = nf;
+    for (int32_t t = 0; t < P.tmax; ++t) {
+        while (a > 0 && P.T[a - 1] <= t) --a;
+        P.act_tiles[t] = P.tfirst[a];
+        P.act_stiles[t] = P.sfirst[a];
+    }
+    size_t off_b = 0;
+    auto take = [&](size_t bytes) {
+        const size_t r = off_b;
+        off_b += align_up(bytes);
+        return r;
+    };
+    P.o_fst = take(sizeof(DevState) * nf);
+    P.o_bs = take(sizeof(BatchState));
+    P.o_rec = take(sizeof(smc_record) * (size_t)oo);
+    P.o_part = take(sizeof(Partial) * (size_t)tf);
+    P.o_tsum = take(8 * (size_t)sf);
+    P.o_x = take(2 * 4 * (size_t)P.ntot * P.rsize);
+    P.o_lw = take(2 * (size_t)P.ntot * P.rsize);
+    P.o_anc = take(4 * (size_t)P.ntot);
+    P.o_obs = take(16 * (size_t)oo);
+    P.o_n = take(8 * (size_t)nf);
+    P.o_off = take(8 * (size_t)nf);
+    P.o_obs_off = take(8 * (size_t)nf);
+    P.o_rec_off = take(8 * (size_t)nf);
+    P.o_T = take(4 * (size_t)nf);
+    P.o_tfirst = take(4 * (size_t)(nf + 1));
+    P.o_sfirst = take(4 * (size_t)(nf + 1));
+    P.o_tf = take(4 * (size_t)tf);
+    P.o_stf = take(4 * (size_t)sf);
+    P.o_act = take(4 * (size_t)P.tmax);
+    P.o_acts = take(4 * (size_t)P.tmax);
+    P.o_stream = take(4 * (size_t)nf);
+    P.o_logn = take(8 * (size_t)nf);
+    P.o_frac = take(4 * (size_t)nf);
+    P.total = off_b;
+    return true;
+}
+
+}  // namespace
+
+struct smc_batch {
+    smc_config cfg;
+    BatchPlan P;
+    char *ws;
+    cudaStream_t stream;
+    int device, nsm;
+    int32_t t_host;
+    int initialized;
+    int grid_per_sm;
+    cudaGraphExec_t graph;
+    int graph_grid;
+    std::vector<int32_t> inv;  // caller -> internal
+};
+
+namespace {
+
+template <typename T>
+T *at(smc_batch *b, size_t o) {
+    return reinterpret_cast<T *>(b->ws + o);
+}
+
+template <typename R>
+BatchArgs<R> batch_args(smc_batch *bt) {
+    const BatchPlan &P = bt->P;
+    BatchArgs<R> B;
+    PfArgs<R> &a = B.proto;
+    std::memset(&a, 0, sizeof(a));
+    const smc_config &g = bt->cfg;
+    a.threshold = g.threshold;
+    a.delta = R(g.cv.delta);
+    a.sd_pos = R(g.cv.sd_pos);
+    a.sd_vel = R(g.cv.sd_vel);
+    a.sd_pos0 = R(g.cv.sd_pos0);
+    a.sd_vel0 = R(g.cv.sd_vel0);
+    const double s = g.cv.obs_scale, nu = g.cv.obs_df;
+    a.inv_scale = R(1.0 / s);
+    a.inv_nu = R(1.0 / nu);
+    a.half_nu1 = R(0.5 * (nu + 1.0));
+    a.gaussian = (g.model == SMC_MODEL_CV_GAUSS) ? 1 : 0;
+    double cst;
+    if (a.gaussian) cst = -0.5 * std::log(2.0 * M_PI) - std::log(s);
+    else cst = std::lgamma(0.5 * (nu + 1.0)) - std::lgamma(0.5 * nu) - 0.5 * std::log(nu * M_PI) - std::log(s);
+    a.ll_const = R(2.0 * cst);
+    a.key = make_uint2((uint32_t)(g.seed & 0xffffffffu), (uint32_t)(g.seed >> 32));
+    for (int k = 0; k < 2; ++k) {
+        R *base = at<R>(bt, P.o_x) + (size_t)k * 4 * P.ntot;
+        for (int r = 0; r < 4; ++r) B.x[k][r] = base + (size_t)r * P.ntot;
+        B.lw[k] = at<R>(bt, P.o_lw) + (size_t)k * P.ntot;
+    }
+    B.anc = at<int32_t>(bt, P.o_anc);
+    B.obs = at<double>(bt, P.o_obs);
+    B.rec = at<smc_record>(bt, P.o_rec);
+    B.part = at<Partial>(bt, P.o_part);
+    B.tsum = at<unsigned long long>(bt, P.o_tsum);
+    B.fst = at<DevState>(bt, P.o_fst);
+    B.bs = at<BatchState>(bt, P.o_bs);
+    B.n = at<int64_t>(bt, P.o_n);
+    B.off = at<int64_t>(bt, P.o_off);
+    B.tfirst = at<int32_t>(bt, P.o_tfirst);
+    B.sfirst = at<int32_t>(bt, P.o_sfirst);
+    B.tile_filter = at<int32_t>(bt, P.o_tf);
+    B.stile_filter = at<int32_t>(bt, P.o_stf);
+    B.act_tiles = at<int32_t>(bt, P.o_act);
+    B.act_stiles = at<int32_t>(bt, P.o_acts);
+    B.obs_off = at<int64_t>(bt, P.o_obs_off);
+    B.rec_off = at<int64_t>(bt, P.o_rec_off);
+    B.n_iter = at<int32_t>(bt, P.o_T);
+    B.stream_of = at<uint32_t>(bt, P.o_stream);
+    B.log_n = at<double>(bt, P.o_logn);
+    B.frac = at<int32_t>(bt, P.o_frac);
+    B.tmax = P.tmax;
+    B.stratified = (g.scheme == SMC_STRATIFIED) ? 1 : 0;
+    return B;
+}
+
+template <typename R>
+int batch_launch_iteration(smc_batch *bt, int grid) {
+    const BatchArgs<R> B = batch_args<R>(bt);
+    batch_pf_kernel<R><<<grid, kBlock, 0, bt->stream>>>(B);
+    batch_reduce_kernel<R><<<grid, kBlock, 0, bt->stream>>>(B);
+    batch_select_kernel<R><<<grid, kBlock, 0, bt->stream>>>(B);
+    return cuda_check(cudaGetLastError());
+}
+
+int batch_iteration(smc_batch *bt, int grid) {
+    return (bt->cfg.precision == 32) ? batch_launch_iteration<float>(bt, grid)
+                                     : batch_launch_iteration<double>(bt, grid);
+}
+
+int batch_grid(smc_batch *bt) { return bt->grid_per_sm * bt->nsm; }
+
+int batch_reset_and_init(smc_batch *bt) {
+    const int nf = bt->P.nf;
+    batch_reset_kernel<<<(nf + 255) / 256, 256, 0, bt->stream>>>(at<DevState>(bt, bt->P.o_fst), nf,
+                                                                  at<BatchState>(bt, bt->P.o_bs));
+    int rc = cuda_check(cudaGetLastError());
+    if (rc) return rc;
+    rc = batch_iteration(bt, batch_grid(bt));
+    if (rc) return rc;
+    bt->t_host = 0;
+    bt->initialized = 1;
+    return SMC_OK;
+}
+
+int batch_graph(smc_batch *bt) {
+    const int grid = batch_grid(bt);
+    if (bt->graph && bt->graph_grid == grid) return SMC_OK;
+    if (bt->graph) {
+        cudaGraphExecDestroy(bt->graph);
+        bt->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SMC_E_CUDA;
+    const int rc = batch_iteration(bt, grid);
+    const cudaError_t e = cudaStreamEndCapture(bt->stream, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return SMC_E_CUDA;
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&bt->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        bt->graph = nullptr;
+        return SMC_E_CUDA;
+    }
+    bt->graph_grid = grid;
+    return SMC_OK;
+}
+
+int batch_read_states(smc_batch *bt, std::vector<DevState> &h) {
+    h.resize(bt->P.nf);
+    int rc = cuda_check(cudaMemcpyAsync(h.data(), at<DevState>(bt, bt->P.o_fst), sizeof(DevState) * bt->P.nf,
+                                        cudaMemcpyDeviceToHost, bt->stream));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(bt->stream));
+    if (rc) return rc;
+    for (const DevState &d : h)
+        if (d.error) return d.error;
+    return SMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t smc_batch_workspace_bytes(const smc_config *cfg, const int64_t *n, const int32_t *T, int32_t nf) {
+    BatchPlan P;
+    if (!batch_plan(cfg, n, T, nf, P)) return 0;
+    return P.total;
+}
+
+int smc_batch_create(smc_batch **out, const smc_config *cfg, const int64_t *n, const int32_t *T, int32_t nf,
+                     void *d_ws, size_t bytes, void *cuda_stream) {
+    if (!out) return SMC_E_ARG;
+    *out = nullptr;
+    smc_batch *bt = new (std::nothrow) smc_batch();
+    if (!bt) return SMC_E_ARG;
+    if (!batch_plan(cfg, n, T, nf, bt->P)) {
+        delete bt;
+        return SMC_E_ARG;
+    }
+    const BatchPlan &P = bt->P;
+    if (!d_ws || bytes < P.total || ((uintptr_t)d_ws & (kAlign - 1))) {
+        delete bt;
+        return SMC_E_WORKSPACE;
+    }
+    bt->cfg = *cfg;
+    bt->ws = static_cast<char *>(d_ws);
+    bt->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaGetDevice(&bt->device);
+    cudaDeviceGetAttribute(&bt->nsm, cudaDevAttrMultiProcessorCount, bt->device);
+    bt->grid_per_sm = 4;
+    bt->graph = nullptr;
+    bt->graph_grid = 0;
+    bt->t_host = -1;
+    bt->initialized = 0;
+    bt->inv.resize(nf);
+    for (int32_t i = 0; i < nf; ++i) bt->inv[P.perm[i]] = i;
+    auto up = [&](size_t o, const void *src, size_t nbytes) {
+        return cuda_check(cudaMemcpyAsync(bt->ws + o, src, nbytes, cudaMemcpyHostToDevice, bt->stream));
+    };
+    int rc = cuda_check(cudaMemsetAsync(bt->ws, 0, P.o_x, bt->stream));
+    if (!rc) rc = up(P.o_n, P.n.data(), 8 * (size_t)nf);
+    if (!rc) rc = up(P.o_off, P.off.data(), 8 * (size_t)nf);
+    if (!rc) rc = up(P.o_obs_off, P.obs_off.data(), 8 * (size_t)nf);
+    if (!rc) rc = up(P.o_rec_off, P.rec_off.data(), 8 * (size_t)nf);
+    if (!rc) rc = up(P.o_T, P.T.data(), 4 * (size_t)nf);
+    if (!rc) rc = up(P.o_tfirst, P.tfirst.data(), 4 * (size_t)(nf + 1));
+    if (!rc) rc = up(P.o_sfirst, P.sfirst.data(), 4 * (size_t)(nf + 1));
+    if (!rc) rc = up(P.o_tf, P.tile_filter.data(), 4 * (size_t)P.ntiles);
+    if (!rc) rc = up(P.o_stf, P.stile_filter.data(), 4 * (size_t)P.nstiles);
+    if (!rc) rc = up(P.o_act, P.act_tiles.data(), 4 * (size_t)P.tmax);
+    if (!rc) rc = up(P.o_acts, P.act_stiles.data(), 4 * (size_t)P.tmax);
+    if (!rc) rc = up(P.o_stream, P.stream_of.data(), 4 * (size_t)nf);
+    if (!rc) rc = up(P.o_logn, P.log_n.data(), 8 * (size_t)nf);
+    if (!rc) rc = up(P.o_frac, P.frac.data(), 4 * (size_t)nf);
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(bt->stream));
+    if (rc) {
+        delete bt;
+        return rc;
+    }
+    *out = bt;
+    return SMC_OK;
+}
+
+int smc_batch_destroy(smc_batch *bt) {
+    if (!bt) return SMC_E_ARG;
+    if (bt->graph) cudaGraphExecDestroy(bt->graph);
+    delete bt;
+    return SMC_OK;
+}
+
+int smc_batch_set_data(smc_batch *bt, int32_t filter, const double *obs, int on_device) {
+    if (!bt || !obs || filter < 0 || filter >= bt->P.nf) return SMC_E_ARG;
+    const int32_t i = bt->inv[filter];
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int rc = cuda_check(cudaMemcpyAsync(at<double>(bt, bt->P.o_obs) + 2 * bt->P.obs_off[i], obs,
+                                        16 * (size_t)bt->P.T[i], k, bt->stream));
+    if (!rc && !on_device) rc = cuda_check(cudaStreamSynchronize(bt->stream));
+    return rc;
+}
+
+int smc_batch_initialize(smc_batch *bt) {
+    if (!bt) return SMC_E_ARG;
+    return batch_reset_and_init(bt);
+}
+
+int smc_batch_iterate(smc_batch *bt, int32_t n) {
+    if (!bt || n < 0) return SMC_E_ARG;
+    if (!bt->initialized) return SMC_E_STATE;
+    if (bt->t_host + n > bt->P.tmax - 1) return SMC_E_ARG;
+    const bool use_graph = bt->stream != nullptr;
+    if (use_graph) {
+        int rc = batch_graph(bt);
+        if (rc) return rc;
+        for (int32_t i = 0; i < n; ++i)
+            if (cudaGraphLaunch(bt->graph, bt->stream) != cudaSuccess) return SMC_E_CUDA;
+    } else {
+        for (int32_t i = 0; i < n; ++i) {
+            int rc = batch_iteration(bt, batch_grid(bt));
+            if (rc) return rc;
+        }
+    }
+    bt->t_host += n;
+    return SMC_OK;
+}
+
+int smc_batch_run(smc_batch *bt) {
+    if (!bt) return SMC_E_ARG;
+    int rc = batch_reset_and_init(bt);
+    if (rc) return rc;
+    return smc_batch_iterate(bt, bt->P.tmax - 1);
+}
+
+int smc_batch_tune(smc_batch *bt, int32_t *blocks_per_sm) {
+    if (!bt) return SMC_E_ARG;
+    const int cand[4] = {1, 2, 4, 8};
+    float best = 1e30f;
+    int best_g = bt->grid_per_sm;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SMC_E_CUDA;
+    const int reps = std::min(3, bt->P.tmax - 1);
+    for (int c : cand) {
+        bt->grid_per_sm = c;
+        int rc = batch_reset_and_init(bt);
+        if (rc) return rc;
+        cudaEventRecord(e0, bt->stream);
+        for (int r = 0; r < reps; ++r)
+            if ((rc = batch_iteration(bt, batch_grid(bt)))) return rc;
+        cudaEventRecord(e1, bt->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return SMC_E_CUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_g = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bt->grid_per_sm = best_g;
+    if (blocks_per_sm) *blocks_per_sm = best_g;
+    return batch_reset_and_init(bt);
+}
+
+int smc_batch_log_evidence(smc_batch *bt, double *h_out) {
+    if (!bt || !h_out) return SMC_E_ARG;
+    std::vector<DevState> h;
+    const int rc = batch_read_states(bt, h);
+    for (int32_t f = 0; f < bt->P.nf; ++f) h_out[f] = h.empty() ? 0.0 : h[bt->inv[f]].log_evidence;
+    return rc;
+}
+
+int smc_batch_read_history(smc_batch *bt, int32_t filter, smc_record *hr, int32_t count, int32_t *n_written) {
+    if (!bt || !hr || count < 0 || filter < 0 || filter >= bt->P.nf) return SMC_E_ARG;
+    std::vector<DevState> h;
+    const int rc = batch_read_states(bt, h);
+    if (rc && rc != SMC_E_NONFINITE) return rc;
+    const int32_t i = bt->inv[filter];
+    const int32_t last = h[i].t;
+    const int32_t m = std::min(count, last + 1);
+    if (m > 0) {
+        const int rc2 = cuda_check(cudaMemcpyAsync(hr, at<smc_record>(bt, bt->P.o_rec) + bt->P.rec_off[i] + (last - m + 1),
+                                                   sizeof(smc_record) * (size_t)m, cudaMemcpyDeviceToHost, bt->stream));
+        if (rc2) return rc2;
+        if (cudaStreamSynchronize(bt->stream) != cudaSuccess) return SMC_E_CUDA;
+    }
+    if (n_written) *n_written = std::max(m, 0);
+    return rc;
+}
+
+int smc_batch_read_state(smc_batch *bt, int32_t filter, void *dst, int on_device) {
+    if (!bt || !dst || filter < 0 || filter >= bt->P.nf) return SMC_E_ARG;
+    std::vector<DevState> h;
+    const int rc = batch_read_states(bt, h);
+    if (rc && rc != SMC_E_NONFINITE) return rc;
+    const BatchPlan &P = bt->P;
+    const int32_t i = bt->inv[filter];
+    const size_t rs = P.rsize;
+    const char *base = bt->ws + P.o_x + (size_t)(h[i].cur & 1) * 4 * P.ntot * rs + (size_t)P.off[i] * rs;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    int rc2 = cuda_check(cudaMemcpy2DAsync(dst, (size_t)P.n[i] * rs, base, (size_t)P.ntot * rs, (size_t)P.n[i] * rs, 4,
+                                           k, bt->stream));
+    if (!rc2) rc2 = cuda_check(cudaStreamSynchronize(bt->stream));
+    return rc2 ? rc2 : rc;
+}
+
+}  // extern "C"

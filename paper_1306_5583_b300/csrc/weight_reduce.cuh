@@ -161,14 +161,15 @@ struct Combined {
     double M, S1, S2, Sa, Sb, Sc;
 };
 
-template <typename R>
-__device__ __forceinline__ bool take_ticket(DevState *st) {
+// Block-level "am I the last of `count` arrivals" on a counter (the
+// counter is reset by the caller's finalisation).
+__device__ __forceinline__ bool last_arrival(uint32_t *counter, uint32_t count) {
     __shared__ bool s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned prev = atomicAdd(&st->ticket, 1u);
-        s_last = (prev == gridDim.x - 1);
+        const unsigned prev = atomicAdd(counter, 1u);
+        s_last = (prev == count - 1);
     }
     __syncthreads();
     if (!s_last) return false;
@@ -177,9 +178,15 @@ __device__ __forceinline__ bool take_ticket(DevState *st) {
 }
 
 template <typename R>
-__device__ __forceinline__ bool last_block_combine(DevState *st, const Partial *part, Combined *out) {
-    if (!take_ticket<R>(st)) return false;
-    const int nb = gridDim.x;
+__device__ __forceinline__ bool take_ticket(DevState *st) {
+    return last_arrival(&st->ticket, gridDim.x);
+}
+
+// Grid-wide sums of nb block partials, by the whole calling block (thread 0
+// receives the result).  The same order of operations for every caller, so
+// a filter gets bit-identical results alone or inside a batch.
+template <typename R>
+__device__ __forceinline__ void combine_partials(const Partial *part, int nb, Combined *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if constexpr (sizeof(R) == 8) {
         __shared__ double s_red[kBlock / 32][6];
@@ -260,6 +267,13 @@ __device__ __forceinline__ bool last_block_combine(DevState *st, const Partial *
                             df_to_double(T[3]), df_to_double(T[4])};
         }
     }
+    __syncthreads();
+}
+
+template <typename R>
+__device__ __forceinline__ bool last_block_combine(DevState *st, const Partial *part, Combined *out) {
+    if (!take_ticket<R>(st)) return false;
+    combine_partials<R>(part, gridDim.x, out);
     return true;
 }
 

@@ -81,6 +81,19 @@ _SIGS = {
     "smc_sync": (_I, [_P]),
     "smc_error_string": (ctypes.c_char_p, [_I]),
     "smc_philox4x32_10": (_I, [_P, ctypes.POINTER(ctypes.c_uint32), _P, ctypes.c_int64, _P]),
+    "smc_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), _P, _P, ctypes.c_int32]),
+    "smc_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Config), _P, _P, ctypes.c_int32, _P,
+                              ctypes.c_size_t, _P]),
+    "smc_batch_destroy": (_I, [_P]),
+    "smc_batch_set_data": (_I, [_P, ctypes.c_int32, _P, _I]),
+    "smc_batch_initialize": (_I, [_P]),
+    "smc_batch_iterate": (_I, [_P, ctypes.c_int32]),
+    "smc_batch_run": (_I, [_P]),
+    "smc_batch_tune": (_I, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "smc_batch_log_evidence": (_I, [_P, _P]),
+    "smc_batch_read_history": (_I, [_P, ctypes.c_int32, ctypes.POINTER(Record), ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32)]),
+    "smc_batch_read_state": (_I, [_P, ctypes.c_int32, _P, _I]),
 }
 
 _lib = None
@@ -297,3 +310,79 @@ def philox4x32_10(ctr, key):
                                   _P(torch.cuda.current_stream().cuda_stream)), "smc_philox4x32_10")
     torch.cuda.synchronize()
     return do.cpu().numpy().view(np.uint32)
+
+
+class Batch:
+    """Many independent constant-velocity filters advanced together
+    (smc_batch_* of the C ABI).  n_particles and n_iter are per filter."""
+
+    def __init__(self, config, n_particles, n_iter, stream=None, device=None):
+        import torch
+        self.cfg = config
+        self.device = torch.device(device or "cuda")
+        self.n = np.ascontiguousarray(np.asarray(n_particles, dtype=np.int64))
+        self.T = np.ascontiguousarray(np.asarray(n_iter, dtype=np.int32))
+        self.nf = int(self.n.shape[0])
+        L = lib()
+        nbytes = L.smc_batch_workspace_bytes(ctypes.byref(config), self.n.ctypes.data_as(_P),
+                                             self.T.ctypes.data_as(_P), self.nf)
+        if nbytes == 0:
+            raise SMCError(E_ARG, "smc_batch_workspace_bytes")
+        self.nbytes = nbytes
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = (self.ws.data_ptr() + 255) & ~255
+        self.ctx = _P()
+        check(L.smc_batch_create(ctypes.byref(self.ctx), ctypes.byref(config), self.n.ctypes.data_as(_P),
+                                 self.T.ctypes.data_as(_P), self.nf, _P(self.ws_ptr), nbytes,
+                                 _P(self.stream.cuda_stream)), "smc_batch_create")
+        self.rdtype = np.float32 if config.precision == 32 else np.float64
+
+    def close(self):
+        if self.ctx:
+            lib().smc_batch_destroy(self.ctx)
+            self.ctx = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_data(self, filter_index, obs):
+        a = np.ascontiguousarray(np.asarray(obs, dtype=np.float64))
+        assert a.shape == (int(self.T[filter_index]), 2)
+        check(lib().smc_batch_set_data(self.ctx, int(filter_index), a.ctypes.data_as(_P), 0), "smc_batch_set_data")
+
+    def initialize(self):
+        check(lib().smc_batch_initialize(self.ctx), "smc_batch_initialize")
+
+    def iterate(self, n):
+        check(lib().smc_batch_iterate(self.ctx, int(n)), "smc_batch_iterate")
+
+    def run(self):
+        check(lib().smc_batch_run(self.ctx), "smc_batch_run")
+
+    def tune(self):
+        v = ctypes.c_int32()
+        check(lib().smc_batch_tune(self.ctx, ctypes.byref(v)), "smc_batch_tune")
+        return v.value
+
+    def log_evidence(self):
+        out = np.empty(self.nf, dtype=np.float64)
+        check(lib().smc_batch_log_evidence(self.ctx, out.ctypes.data_as(_P)), "smc_batch_log_evidence")
+        return out
+
+    def history(self, filter_index, count):
+        recs = (Record * count)()
+        n = ctypes.c_int32()
+        check(lib().smc_batch_read_history(self.ctx, int(filter_index), recs, count, ctypes.byref(n)),
+              "smc_batch_read_history")
+        return [recs[i].as_dict() for i in range(n.value)]
+
+    def state(self, filter_index):
+        out = np.empty((4, int(self.n[filter_index])), dtype=self.rdtype)
+        check(lib().smc_batch_read_state(self.ctx, int(filter_index), out.ctypes.data_as(_P), 0),
+              "smc_batch_read_state")
+        return out
