@@ -80,12 +80,13 @@ __global__ void __launch_bounds__(kBlock) batch_pf_kernel(BatchArgs<R> B) {
     for (int tile = blockIdx.x; tile < nact; tile += gridDim.x) {
         const int b = B.tile_filter[tile];
         DevState *st = &B.fst[b];
-        if (*(volatile int32_t *)&st->error) continue;
+        const DevState *sv = snapshot(st);
+        if (sv->error) continue;
         const PfArgs<R> a = filter_args(B, b);
-        const int cur = st->cur, cur_lw = st->cur_lw;
-        const bool gather = (t > 0) && (st->ready != 0);
+        const int cur = sv->cur, cur_lw = sv->cur_lw;
+        const bool gather = (t > 0) && (sv->ready != 0);
         const int nblk = B.tfirst[b + 1] - B.tfirst[b];
-        pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, st->log_norm);
+        pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, sv->log_norm);
         if (last_arrival(&st->ticket, (uint32_t)nblk)) pf_finalize<R>(a, st, nblk, t, cur, cur_lw);
     }
     if (last_arrival(&B.bs->ticket, gridDim.x) && threadIdx.x == 0) {
@@ -114,8 +115,9 @@ __global__ void __launch_bounds__(kBlock) batch_reduce_kernel(BatchArgs<R> B) {
     for (int tile = blockIdx.x; tile < nact; tile += gridDim.x) {
         const int b = B.stile_filter[tile];
         DevState *st = &B.fst[b];
-        if (gated_out(st, 1)) continue;
-        const QGen<R> g = filter_qgen(B, b, st);
+        const DevState *sv = snapshot(st);
+        if (gated_out(sv, 1)) continue;
+        const QGen<R> g = filter_qgen(B, b, sv);
         const int ns = B.sfirst[b + 1] - B.sfirst[b];
         const unsigned long long s = tile_sum(g, B.n[b], tile - B.sfirst[b]);
         if (threadIdx.x == 0) B.tsum[tile] = s;
@@ -130,17 +132,18 @@ __global__ void __launch_bounds__(kBlock) batch_reduce_kernel(BatchArgs<R> B) {
 }
 
 template <typename R, bool kStratified>
-__device__ __forceinline__ void batch_select_tile(const BatchArgs<R> &B, int tile, int b, DevState *st) {
-    const QGen<R> g = filter_qgen(B, b, st);
+__device__ __forceinline__ void batch_select_tile(const BatchArgs<R> &B, int tile, int b, DevState *st,
+                                                  const DevState *sv) {
+    const QGen<R> g = filter_qgen(B, b, sv);
     GridTargets<kStratified> tg{B.n[b], B.proto.key, B.stream_of[b], 0, 0};
-    tg.prepare(st);
+    tg.prepare(sv);
     const int lt = tile - B.sfirst[b];
     if (lt == 0 && threadIdx.x == 0) st->ready = 1;
-    const unsigned long long QN = *(const volatile unsigned long long *)&st->scan_total[SLOT_CDF];
+    const unsigned long long QN = sv->scan_total[SLOT_CDF];
     scan_select_tile(g, tg, AncOut{B.anc + B.off[b]}, NoSink{}, B.n[b], lt, B.tsum + B.sfirst[b], QN, st);
 }
 
-template <typename R>
+template <typename R, bool kStratified>
 __global__ void __launch_bounds__(kBlock) batch_select_kernel(BatchArgs<R> B) {
     const int32_t t = B.bs->t;
     if (t < 0 || t >= B.tmax) return;
@@ -148,9 +151,9 @@ __global__ void __launch_bounds__(kBlock) batch_select_kernel(BatchArgs<R> B) {
     for (int tile = blockIdx.x; tile < nact; tile += gridDim.x) {
         const int b = B.stile_filter[tile];
         DevState *st = &B.fst[b];
-        if (gated_out(st, 1)) continue;
-        if (B.stratified) batch_select_tile<R, true>(B, tile, b, st);
-        else batch_select_tile<R, false>(B, tile, b, st);
+        const DevState *sv = snapshot(st);
+        if (gated_out(sv, 1)) continue;
+        batch_select_tile<R, kStratified>(B, tile, b, st, sv);
     }
 }
 

@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     const R *ys = reinterpret_cast<const R *>(s_raw);
     DevState *st = a.st;
-    if (*(volatile int32_t *)&st->error) return;
+    const DevState *sv = snapshot(st);
+    if (sv->error) return;
     stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st);
     const int q = threadIdx.x & (kQuad - 1);
     const int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kQuad;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
     th.lp = R(gmm_log_prior<R, NC>(a, th.mu, th.lam, th.om));
     const double ll = gmm_loglik_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi);
     th.ll = R(ll);
-    const int cur = st->cur, cur_lw = st->cur_lw;
+    const int cur = sv->cur, cur_lw = sv->cur_lw;
     const R lw0 = R(-a.log_n);
     if (active && q == 0) {
         store_theta<R, NC>(a.x[cur ^ 1], a.ld, i, th);
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
     }
     R lwv[1] = {(active && q == 0) ? lw0 : Math<R>::neg_inf()};
     R h0[1] = {th.ll}, zero[1] = {R(0)};
-    block_partial<R, 1>(lwv, h0, zero, zero, &a.part[blockIdx.x]);
+    block_partial<R, 1, 1>(lwv, h0, zero, zero, &a.part[blockIdx.x]);
     Combined c;
     if (!last_block_combine<R>(st, a.part, &c)) return;
     if (threadIdx.x == 0) {
@@ -311,12 +312,13 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
 template <typename R, int NC>
 __global__ void __launch_bounds__(kBlock) gmm_reweight_kernel(GmmArgs<R> a) {
     DevState *st = a.st;
-    if (*(volatile int32_t *)&st->error) return;
-    const int32_t t = st->t + 1;
+    const DevState *sv = snapshot(st);
+    if (sv->error) return;
+    const int32_t t = sv->t + 1;
     const double a_t = a.alpha[t], a_p = a.alpha[t - 1];
     const R dal = R(a_t - a_p);
-    const Shift<R> base(st->base_shift);
-    const int cur = st->cur, cur_lw = st->cur_lw;
+    const Shift<R> base(sv->base_shift);
+    const int cur = sv->cur, cur_lw = sv->cur_lw;
     const R *lw_in = a.lw[cur_lw];
     R *lw_out = a.lw[cur_lw ^ 1];
     const R *ll = a.x[cur] + (int64_t)(3 * NC + 1) * a.ld;
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(kBlock) gmm_reweight_kernel(GmmArgs<R> a) {
             lw_out[i] = lwv[j];
         }
     }
-    block_partial<R, kPfItems>(lwv, zero, zero, zero, &a.part[blockIdx.x]);
+    block_partial<R, kPfItems, 0>(lwv, zero, zero, zero, &a.part[blockIdx.x]);
     Combined c;
     if (!last_block_combine<R>(st, a.part, &c)) return;
     if (threadIdx.x == 0) {
@@ -358,17 +360,18 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     __shared__ uint32_t s_acc[3];
     const R *ys = reinterpret_cast<const R *>(s_raw);
     DevState *st = a.st;
-    if (*(volatile int32_t *)&st->error) return;
+    const DevState *sv = snapshot(st);
+    if (sv->error) return;
     if (threadIdx.x < 3) s_acc[threadIdx.x] = 0;
     stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st);
-    const int32_t t = st->t;
+    const int32_t t = sv->t;
     const double a_t = a.alpha[t], a_p = (t > 0) ? a.alpha[t - 1] : 0.0;
     const double aclamp = fmax(a_t, 0.02);
     const R s_mu = R(0.15 / aclamp);
     const R s_lam = R((1.0 + sqrt(1.0 / aclamp)) * 0.15);
     const R s_om = R((1.0 + sqrt(1.0 / aclamp)) * 0.2);
-    const bool gather = st->ready != 0;
-    const int cur = st->cur, cur_lw = st->cur_lw;
+    const bool gather = sv->ready != 0;
+    const int cur = sv->cur, cur_lw = sv->cur_lw;
     const int q = threadIdx.x & (kQuad - 1);
     const int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kQuad;
     const bool active = i < a.n;
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     }
     R lwv[1] = {(active && q == 0) ? lwi : Math<R>::neg_inf()};
     R h0[1] = {th.ll}, zero[1] = {R(0)};
-    block_partial<R, 1>(lwv, h0, zero, zero, &a.part[blockIdx.x]);
+    block_partial<R, 1, 1>(lwv, h0, zero, zero, &a.part[blockIdx.x]);
     Combined c;
     if (!last_block_combine<R>(st, a.part, &c)) return;
     if (threadIdx.x == 0) {

@@ -60,6 +60,13 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
     constexpr int E = kPfItems;
     const uint32_t n = (uint32_t)a.n;
     const uint32_t i0 = (blk * (uint32_t)kBlock + threadIdx.x) * (uint32_t)E;
+    // buffer selection by value (no dynamic indexing of the pointer table)
+    const R *xs0 = cur ? a.x[1][0] : a.x[0][0], *xs1 = cur ? a.x[1][1] : a.x[0][1];
+    const R *xs2 = cur ? a.x[1][2] : a.x[0][2], *xs3 = cur ? a.x[1][3] : a.x[0][3];
+    R *xd0 = cur ? a.x[0][0] : a.x[1][0], *xd1 = cur ? a.x[0][1] : a.x[1][1];
+    R *xd2 = cur ? a.x[0][2] : a.x[1][2], *xd3 = cur ? a.x[0][3] : a.x[1][3];
+    const R *lws = cur_lw ? a.lw[1] : a.lw[0];
+    R *lwd = cur_lw ? a.lw[0] : a.lw[1];
     R v0[E], v1[E], v2[E], v3[E], lwin[E];
     if (t > 0) {
         if (gather) {
@@ -68,17 +75,17 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 const uint32_t sidx = (i0 + j < n) ? (uint32_t)src[j] : 0u;
-                v0[j] = __ldg(a.x[cur][0] + sidx);
-                v1[j] = __ldg(a.x[cur][1] + sidx);
-                v2[j] = __ldg(a.x[cur][2] + sidx);
-                v3[j] = __ldg(a.x[cur][3] + sidx);
+                v0[j] = __ldg(xs0 + sidx);
+                v1[j] = __ldg(xs1 + sidx);
+                v2[j] = __ldg(xs2 + sidx);
+                v3[j] = __ldg(xs3 + sidx);
             }
         } else {
-            load_k<R, E>(a.x[cur][0], i0, n, v0);
-            load_k<R, E>(a.x[cur][1], i0, n, v1);
-            load_k<R, E>(a.x[cur][2], i0, n, v2);
-            load_k<R, E>(a.x[cur][3], i0, n, v3);
-            load_k<R, E>(a.lw[cur_lw], i0, n, lwin);
+            load_k<R, E>(xs0, i0, n, v0);
+            load_k<R, E>(xs1, i0, n, v1);
+            load_k<R, E>(xs2, i0, n, v2);
+            load_k<R, E>(xs3, i0, n, v3);
+            load_k<R, E>(lws, i0, n, lwin);
         }
     }
     const Shift<R> Lprev(log_norm_prev);
@@ -105,12 +112,12 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
         const R b = (t == 0 || gather) ? base_eq : Lprev.sub_from(lwin[j]);
         lwv[j] = (i0 + j < n) ? b + cv_loglik(a, yx, yy, s0[j], s1[j]) : Math<R>::neg_inf();
     }
-    store_k<R, E>(a.x[cur ^ 1][0], i0, n, s0);
-    store_k<R, E>(a.x[cur ^ 1][1], i0, n, s1);
-    store_k<R, E>(a.x[cur ^ 1][2], i0, n, s2);
-    store_k<R, E>(a.x[cur ^ 1][3], i0, n, s3);
-    store_k<R, E>(a.lw[cur_lw ^ 1], i0, n, lwv);
-    block_partial<R, E>(lwv, s0, s1, zero, &a.part[blk]);
+    store_k<R, E>(xd0, i0, n, s0);
+    store_k<R, E>(xd1, i0, n, s1);
+    store_k<R, E>(xd2, i0, n, s2);
+    store_k<R, E>(xd3, i0, n, s3);
+    store_k<R, E>(lwd, i0, n, lwv);
+    block_partial<R, E, 2>(lwv, s0, s1, zero, &a.part[blk]);
 }
 
 // Last tile of a filter: combine its nblk partials, write the record of
@@ -135,11 +142,12 @@ __device__ __forceinline__ void pf_finalize(const PfArgs<R> &a, DevState *st, in
 template <typename R>
 __global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
     DevState *st = a.st;
-    if (*(volatile int32_t *)&st->error) return;
-    const int32_t t = st->t + 1;
-    const int cur = st->cur, cur_lw = st->cur_lw;
-    const bool gather = (t > 0) && (st->ready != 0);
-    pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, st->log_norm);
+    const DevState *sv = snapshot(st);
+    if (sv->error) return;
+    const int32_t t = sv->t + 1;
+    const int cur = sv->cur, cur_lw = sv->cur_lw;
+    const bool gather = (t > 0) && (sv->ready != 0);
+    pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, sv->log_norm);
     if (!take_ticket<R>(st)) return;
     pf_finalize<R>(a, st, gridDim.x, t, cur, cur_lw);
 }

@@ -33,8 +33,8 @@ struct QGen {
     const R *cur_lw;
     R m;
     __device__ __forceinline__ void prepare(const DevState *st) {
-        cur_lw = lw[*(const volatile int32_t *)&st->cur_lw];
-        m = R(*(const volatile double *)&st->max_lw);
+        cur_lw = st->cur_lw ? lw[1] : lw[0];
+        m = R(st->max_lw);
     }
     __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
         return Math<R>::fixed(Math<R>::exp(cur_lw[i] - m), frac);
@@ -99,7 +99,7 @@ struct ResidualParts {
     unsigned long long qn;
     __device__ __forceinline__ void prepare(const DevState *st) {
         qg.prepare(st);
-        qn = *(const volatile unsigned long long *)&st->qn;
+        qn = st->qn;
     }
     __device__ __forceinline__ unsigned long long q(int64_t i) const { return qg(i); }
     __device__ __forceinline__ unsigned long long d_of(unsigned long long qi) const {
@@ -115,7 +115,7 @@ struct ResidualRGen {
     int shift;
     __device__ __forceinline__ void prepare(const DevState *st) {
         p.prepare(st);
-        const unsigned long long sd = *(const volatile unsigned long long *)&st->sum_d;
+        const unsigned long long sd = st->sum_d;
         const unsigned long long Rn = sd < (unsigned long long)p.n ? (unsigned long long)p.n - sd : 0ull;
         shift = max(0, bitlen128(mul64(Rn, p.qn)) - 62);
     }
@@ -185,7 +185,7 @@ struct GridTargets {
     uint32_t t;
     unsigned long long c;  // 2j + 1 (systematic)
     __device__ __forceinline__ void prepare(const DevState *st) {
-        t = (uint32_t)*(const volatile int32_t *)&st->t;
+        t = (uint32_t)st->t;
         c = 2ull * u24(draw(key, 0u, t, TAG_RESAMPLE, stream, 0u).x) + 1ull;
     }
     __device__ __forceinline__ int64_t count() const { return n; }
@@ -216,7 +216,7 @@ struct SortedTargets {
     int from_residual;
     unsigned long long m;
     __device__ __forceinline__ void prepare(const DevState *st) {
-        const unsigned long long sd = *(const volatile unsigned long long *)&st->sum_d;
+        const unsigned long long sd = st->sum_d;
         m = from_residual ? (sd < (unsigned long long)n_total ? (unsigned long long)n_total - sd : 0ull)
                           : (unsigned long long)n_total;
     }
@@ -268,9 +268,10 @@ struct CountOut {  // residual draws: histogram of the selected particles
 
 // ---------------------------------------------------------------- kernels --
 
-__device__ __forceinline__ bool gated_out(DevState *st, int gate) {
-    if (*(volatile int32_t *)&st->error) return true;
-    return gate && !*(volatile int32_t *)&st->due;
+// sv: the block's snapshot of the state block
+__device__ __forceinline__ bool gated_out(const DevState *sv, int gate) {
+    if (sv->error) return true;
+    return gate && !sv->due;
 }
 
 // Sum of gen(i) over tile `tile` (kScanTile elements), returned to thread 0.
@@ -316,9 +317,10 @@ template <class Gen>
 __global__ void __launch_bounds__(kBlock) tile_reduce_kernel(Gen gen, int64_t n, unsigned long long *tsum,
                                                              unsigned long long *total, uint32_t *ticket,
                                                              DevState *st, int gate) {
-    if (gated_out(st, gate)) return;
+    const DevState *sv = snapshot(st);
+    if (gated_out(sv, gate)) return;
     Gen g = gen;
-    g.prepare(st);
+    g.prepare(sv);
     const unsigned long long s = tile_sum(g, n, blockIdx.x);
     if (threadIdx.x == 0) tsum[blockIdx.x] = s;
     if (!last_arrival(ticket, gridDim.x)) return;
@@ -432,13 +434,17 @@ __global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, O
                                                              const unsigned long long *tsum,
                                                              const unsigned long long *total, DevState *st, int gate,
                                                              int set_ready) {
-    if (gated_out(st, gate)) return;
+    const DevState *sv = snapshot(st);
+    if (gated_out(sv, gate)) return;
     if (set_ready && blockIdx.x == 0 && threadIdx.x == 0) st->ready = 1;
     Gen g = gen;
-    g.prepare(st);
+    g.prepare(sv);
     Tgt tg = tgt;
-    tg.prepare(st);
-    const unsigned long long QN = *(const volatile unsigned long long *)total;
+    tg.prepare(sv);
+    __shared__ unsigned long long s_qn;
+    if (threadIdx.x == 0) s_qn = __ldcg(total);
+    __syncthreads();
+    const unsigned long long QN = s_qn;
     scan_select_tile(g, tg, out, sink, n, blockIdx.x, tsum, QN, st);
 }
 
@@ -459,14 +465,15 @@ struct UniformSortArgs {
 
 __device__ __forceinline__ int64_t draw_count(const UniformSortArgs &a, const DevState *st) {
     if (!a.from_residual) return a.n_total;
-    const unsigned long long sd = *(const volatile unsigned long long *)&st->sum_d;
+    const unsigned long long sd = st->sum_d;
     return sd < (unsigned long long)a.n_total ? a.n_total - (int64_t)sd : 0;
 }
 
 __global__ void __launch_bounds__(kBlock) bucket_count_kernel(UniformSortArgs a, DevState *st, int gate) {
-    if (gated_out(st, gate)) return;
-    const int64_t count = draw_count(a, st);
-    const uint32_t t = (uint32_t)st->t;
+    const DevState *sv = snapshot(st);
+    if (gated_out(sv, gate)) return;
+    const int64_t count = draw_count(a, sv);
+    const uint32_t t = (uint32_t)sv->t;
     const int64_t k4 = 4 * ((int64_t)blockIdx.x * kBlock + threadIdx.x);
     if (k4 >= count) return;
     const uint4 w = resample_words(a.key, a.stream, t, k4);
@@ -477,9 +484,10 @@ __global__ void __launch_bounds__(kBlock) bucket_count_kernel(UniformSortArgs a,
 }
 
 __global__ void __launch_bounds__(kBlock) bucket_scatter_kernel(UniformSortArgs a, DevState *st, int gate) {
-    if (gated_out(st, gate)) return;
-    const int64_t count = draw_count(a, st);
-    const uint32_t t = (uint32_t)st->t;
+    const DevState *sv = snapshot(st);
+    if (gated_out(sv, gate)) return;
+    const int64_t count = draw_count(a, sv);
+    const uint32_t t = (uint32_t)sv->t;
     const int64_t k4 = 4 * ((int64_t)blockIdx.x * kBlock + threadIdx.x);
     if (k4 >= count) return;
     const uint4 w = resample_words(a.key, a.stream, t, k4);
@@ -499,7 +507,8 @@ __global__ void __launch_bounds__(kBlock) bucket_scatter_kernel(UniformSortArgs 
 // one thread per bucket: insertion sort of the (few) values in the bucket,
 // then clear the counters for the next use
 __global__ void __launch_bounds__(kBlock) bucket_sort_kernel(UniformSortArgs a, DevState *st, int gate) {
-    if (gated_out(st, gate)) return;
+    const DevState *sv = snapshot(st);
+    if (gated_out(sv, gate)) return;
     const int64_t b = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     if (b >= a.nbuckets) return;
     const uint32_t c = a.cnt[b];
@@ -527,9 +536,10 @@ template <typename R>
 __global__ void __launch_bounds__(kBlock) residual_d_kernel(ResidualParts<R> p, uint32_t *extra, DevState *st,
                                                             int gate) {
     __shared__ unsigned long long s_w[kBlock / 32];
-    if (gated_out(st, gate)) return;
+    const DevState *sv = snapshot(st);
+    if (gated_out(sv, gate)) return;
     ResidualParts<R> pp = p;
-    pp.prepare(st);
+    pp.prepare(sv);
     const int64_t i0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
     unsigned long long acc = 0;
 #pragma unroll

@@ -1023,7 +1023,8 @@ int batch_launch_iteration(smc_batch *bt, int grid) {
     const BatchArgs<R> B = batch_args<R>(bt);
     batch_pf_kernel<R><<<grid, kBlock, 0, bt->stream>>>(B);
     batch_reduce_kernel<R><<<grid, kBlock, 0, bt->stream>>>(B);
-    batch_select_kernel<R><<<grid, kBlock, 0, bt->stream>>>(B);
+    if (B.stratified) batch_select_kernel<R, true><<<grid, kBlock, 0, bt->stream>>>(B);
+    else batch_select_kernel<R, false><<<grid, kBlock, 0, bt->stream>>>(B);
     return cuda_check(cudaGetLastError());
 }
 

@@ -27,13 +27,11 @@ constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k.x += kPhiloxW0;
-            k.y += kPhiloxW1;
-        }
-        const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
-        const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        // one 32x32 -> 64-bit product gives both halves
+        const unsigned long long p0 = (unsigned long long)kPhiloxM0 * c.x;
+        const unsigned long long p1 = (unsigned long long)kPhiloxM1 * c.z;
+        const uint32_t kx = k.x + (uint32_t)r * kPhiloxW0, ky = k.y + (uint32_t)r * kPhiloxW1;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ kx, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ ky, (uint32_t)p0);
     }
     return c;
 }
@@ -102,7 +100,8 @@ __device__ __forceinline__ void box_muller(R u0, R u1, R &z0, R &z1) {
 __device__ __forceinline__ void box_muller_fast(float u0, float u1, float &z0, float &z1) {
     // the radius needs an accurate log: near u0 = 1 the MUFU log has an
     // absolute (not relative) error that would dominate sqrt(-2 ln u0)
-    const float r = sqrtf(-2.0f * logf(u0));
+    const float r2 = -2.0f * logf(u0);
+    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));  // sqrt on the MUFU pipe (r2 = 0 gives 0)
     const float th = fmaf(6.2831853071795864769f, u1, -3.14159265358979323846f);
     float s, c;
     __sincosf(th, &s, &c);
@@ -222,5 +221,21 @@ __device__ __forceinline__ int bitlen128(U128 a) {
 
 // ---- bounded spin (never waits forever: sets the error word and gives up) --
 __device__ __forceinline__ void raise_error(DevState *st, int code) { atomicCAS(&st->error, 0, code); }
+
+// Copy of the device state block in shared memory, read once per block:
+// every block of a kernel reads the same few words, and letting every warp
+// load them serialises on one L2 line.  Writes still go to the global block.
+// Must be called by all threads of the block.
+__device__ __forceinline__ const DevState *snapshot(const DevState *st) {
+    __shared__ __align__(16) DevState s_st;
+    constexpr int W = (int)(sizeof(DevState) / 4);
+    static_assert(sizeof(DevState) % 4 == 0, "DevState size");
+    __syncthreads();  // a previous snapshot in the same block may still be read
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(st);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&s_st);
+    for (int i = threadIdx.x; i < W; i += blockDim.x) dst[i] = __ldcg(src + i);
+    __syncthreads();
+    return &s_st;
+}
 
 }  // namespace smc

@@ -101,9 +101,11 @@ struct PartialIO<float> {
 // Block-level partial of E items per thread.  lw = -inf marks inactive
 // items.  Per-thread and per-warp sums run in R; the warp sums are combined
 // in float64 (FP64 path) or compensated float (FP32 path).
-template <typename R, int E>
+template <typename R, int E, int NH = 3>
 __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E], const R (&h1)[E],
                                               const R (&h2)[E], Partial *out) {
+    // NH: how many of h0, h1, h2 are monitored (the rest is reported as 0)
+    constexpr int NV = 2 + NH;
     __shared__ R s_max[kBlock / 32];
     __shared__ R s_sum[kBlock / 32][5];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -125,16 +127,16 @@ __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E]
             const R e = (lw[j] > Math<R>::neg_inf()) ? Math<R>::fast_exp(lw[j] - m) : R(0);
             v[0] += e;
             v[1] += e * e;
-            v[2] += e * h0[j];
-            v[3] += e * h1[j];
-            v[4] += e * h2[j];
+            if (NH > 0) v[2] += e * h0[j];
+            if (NH > 1) v[3] += e * h1[j];
+            if (NH > 2) v[4] += e * h2[j];
         }
     }
 #pragma unroll
-    for (int q = 0; q < 5; ++q) v[q] = warp_sum(v[q]);
+    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
     if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) s_sum[warp][q] = v[q];
+        for (int q = 0; q < 5; ++q) s_sum[warp][q] = (q < NV) ? v[q] : R(0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
