@@ -62,6 +62,8 @@ extern "C" {
 
 /* config flags */
 #define SMC_FLAG_KEEP_CDF 1u  /* store the fixed-point CDF of each resampling step (smc_read_cdf) */
+#define SMC_FLAG_RECORD 2u    /* CV models: record the ancestors of every step and a state checkpoint
+                                 every checkpoint_every steps, for smc_pf_grad / smc_pf_replay */
 
 /* models */
 #define SMC_MODEL_CV 0        /* Sec. 5.1: constant-velocity tracking, Student-t observations */
@@ -108,6 +110,8 @@ typedef struct {
     int64_t max_data;     /* capacity for observations: CV rows (Y_0..), GMM points */
     smc_cv_params cv;
     smc_gmm_params gmm;
+    int32_t checkpoint_every; /* SMC_FLAG_RECORD: steps between state checkpoints (0: 16) */
+    int32_t reserved2;
 } smc_config;
 
 /* One record per iteration, kept on the device (ring of max_records). */
@@ -211,6 +215,25 @@ int smc_read_history(smc_ctx *ctx, smc_record *h_records, int32_t count, int32_t
  * the current iteration (layouts as above). */
 int smc_write_state(smc_ctx *ctx, const void *src, int on_device);
 int smc_write_log_weight(smc_ctx *ctx, const void *src, int on_device);
+
+/* Gradient of the log-likelihood estimate (CV models, SMC_FLAG_RECORD) with
+ * respect to theta = (sd_pos, sd_vel, obs_scale, obs_df) at the context's
+ * parameters, after a complete forward run (smc_initialize, then
+ * iterations up to the last observation).  The resampling of that run is
+ * held fixed (stop-gradient resampling) and the move noise is fixed by its
+ * Philox counters; the reverse sweep recomputes the particle trajectory
+ * between checkpoints from the recorded ancestors.  grad[3] is 0 for the
+ * Gaussian model.  Synchronises. */
+int smc_pf_grad(smc_ctx *ctx, double grad[4]);
+
+/* The same recorded run's log-likelihood estimate re-evaluated at another
+ * theta with the recorded resampling (for finite differences).
+ * Synchronises. */
+int smc_pf_replay(smc_ctx *ctx, const double theta[4], double *h_log_evidence);
+
+/* Ancestors chosen at iteration t of a recorded run (N int32; meaningful
+ * when that iteration resampled). */
+int smc_read_ancestor_history(smc_ctx *ctx, int32_t t, int32_t *dst, int on_device);
 
 /* Wait for queued work and return the device error word. */
 int smc_sync(smc_ctx *ctx);

@@ -14,6 +14,7 @@
 #include "resample_kernels.cuh"
 #include "gmm_kernels.cuh"
 #include "batch_kernels.cuh"
+#include "grad_kernels.cuh"
 
 using namespace smc;
 
@@ -40,7 +41,10 @@ int ceil_log2(int64_t n) {
 }
 
 struct Layout {
-    size_t st, rec, part, x, lw, anc, Q, tsum, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, alpha, total;
+    size_t st, rec, part, x, lw, anc, Q, tsum, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, alpha;
+    size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, total;
+    int ck;           // steps between checkpoints (record mode)
+    int64_t nck;      // checkpoints
     int d;            // state rows
     int64_t ld;       // row pitch in elements (N rounded up to 64: 16-byte aligned rows)
     int64_t nbw;      // blocks of the weighting kernels
@@ -114,6 +118,19 @@ Layout make_layout(const smc_config *c) {
     L.obs = take((size_t)obs_vals * 8);
     L.obs_f = take((size_t)obs_vals * 4);
     L.alpha = take((c->model == SMC_MODEL_GMM) ? ((size_t)c->gmm.n_iter + 1) * 8 : 0);
+    const bool rec = (c->flags & SMC_FLAG_RECORD) && c->model != SMC_MODEL_GMM;
+    L.ck = (c->checkpoint_every > 0) ? c->checkpoint_every : 16;
+    L.nck = rec ? (c->max_data + L.ck - 1) / L.ck : 0;
+    const size_t row = (size_t)L.ld * rs;
+    L.hist = take(rec ? (size_t)c->max_data * L.ld * 4 : 0);
+    L.ckpt = take((size_t)L.nck * 5 * row);
+    L.seg = take(rec ? (size_t)L.ck * 5 * row : 0);
+    L.gbar = take(rec ? 2 * (size_t)L.ld * 4 : 0);
+    L.xbar = take(rec ? 4 * row : 0);
+    L.at = take(rec ? 4 * row : 0);
+    L.rep = take(rec ? 2 * 5 * row : 0);
+    L.rep_part = take(rec ? sizeof(Partial) * (size_t)std::max<int64_t>(L.nbw, 1) : 0);
+    L.scal = take(rec ? 256 : 0);
     L.total = off;
     return L;
 }
@@ -178,6 +195,19 @@ __global__ void reset_state_kernel(DevState *st) {
     for (int i = 0; i < 3; ++i) st->accept[i] = 0;
 }
 
+// observation-density constants of the constant-velocity model
+template <typename R>
+void set_obs_params(PfArgs<R> &a, double s, double nu, bool gaussian) {
+    a.inv_scale = R(1.0 / s);
+    a.inv_nu = R(1.0 / nu);
+    a.half_nu1 = R(0.5 * (nu + 1.0));
+    a.gaussian = gaussian ? 1 : 0;
+    double cst;
+    if (gaussian) cst = -0.5 * std::log(2.0 * M_PI) - std::log(s);
+    else cst = std::lgamma(0.5 * (nu + 1.0)) - std::lgamma(0.5 * nu) - 0.5 * std::log(nu * M_PI) - std::log(s);
+    a.ll_const = R(2.0 * cst);
+}
+
 template <typename R>
 PfArgs<R> pf_args(smc_ctx *c) {
     PfArgs<R> a;
@@ -202,15 +232,7 @@ PfArgs<R> pf_args(smc_ctx *c) {
     a.sd_vel = R(g.cv.sd_vel);
     a.sd_pos0 = R(g.cv.sd_pos0);
     a.sd_vel0 = R(g.cv.sd_vel0);
-    const double s = g.cv.obs_scale, nu = g.cv.obs_df;
-    a.inv_scale = R(1.0 / s);
-    a.inv_nu = R(1.0 / nu);
-    a.half_nu1 = R(0.5 * (nu + 1.0));
-    a.gaussian = (g.model == SMC_MODEL_CV_GAUSS) ? 1 : 0;
-    double cst;
-    if (a.gaussian) cst = -0.5 * std::log(2.0 * M_PI) - std::log(s);
-    else cst = std::lgamma(0.5 * (nu + 1.0)) - std::lgamma(0.5 * nu) - 0.5 * std::log(nu * M_PI) - std::log(s);
-    a.ll_const = R(2.0 * cst);
+    set_obs_params(a, g.cv.obs_scale, g.cv.obs_df, g.model == SMC_MODEL_CV_GAUSS);
     a.key = key_of(c);
     a.stream = g.stream_id;
     return a;
@@ -353,13 +375,45 @@ int read_state(smc_ctx *c) {
     return c->host_st.error;
 }
 
+// ---- recording for the gradient (SMC_FLAG_RECORD, CV models) ----
+bool recording(const smc_ctx *c) { return (c->cfg.flags & SMC_FLAG_RECORD) && c->cfg.model != SMC_MODEL_GMM; }
+
+size_t row_bytes(const smc_ctx *c) { return (size_t)c->L.ld * c->L.rsize; }
+
+char *ckpt_slot(smc_ctx *c, int64_t k) { return c->ws + c->L.ckpt + (size_t)k * 5 * row_bytes(c); }
+
+// after the move of iteration t_host: state checkpoint every ck iterations
+// (the PF kernels flip both buffers each iteration: after iteration t the
+// current buffers have parity (t + 1) & 1)
+int record_after_move(smc_ctx *c) {
+    if (!recording(c)) return SMC_OK;
+    const int32_t t = c->t_host;
+    if (t % c->L.ck) return SMC_OK;
+    const int par = (t + 1) & 1;
+    char *dst = ckpt_slot(c, t / c->L.ck);
+    int rc = cuda_check(cudaMemcpyAsync(dst, c->x[par], 4 * row_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    if (!rc)
+        rc = cuda_check(
+            cudaMemcpyAsync(dst + 4 * row_bytes(c), c->lw[par], row_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    return rc;
+}
+
+// after the resampling step of iteration t_host: keep its ancestors
+int record_after_resample(smc_ctx *c) {
+    if (!recording(c)) return SMC_OK;
+    int32_t *dst = reinterpret_cast<int32_t *>(c->ws + c->L.hist) + (size_t)c->t_host * c->L.ld;
+    return cuda_check(cudaMemcpyAsync(dst, c->anc, (size_t)c->cfg.n_particles * 4, cudaMemcpyDeviceToDevice,
+                                      c->stream));
+}
+
 int move_any(smc_ctx *c) {
     if (!c->initialized) return SMC_E_STATE;
     if (c->cfg.model == SMC_MODEL_GMM) return gmm_move(c);
     if (c->t_host + 1 >= c->n_obs) return SMC_E_ARG;
     const int rc = (c->cfg.precision == 32) ? launch_pf<float>(c) : launch_pf<double>(c);
-    if (rc == SMC_OK) c->t_host += 1;
-    return rc;
+    if (rc != SMC_OK) return rc;
+    c->t_host += 1;
+    return record_after_move(c);
 }
 
 int mcmc_any(smc_ctx *c) {
@@ -464,9 +518,12 @@ int smc_initialize(smc_ctx *c) {
     } else {
         rc = (c->cfg.precision == 32) ? launch_pf<float>(c) : launch_pf<double>(c);
         if (!rc) c->t_host = 0;
+        if (!rc) rc = record_after_move(c);
     }
     if (rc) return rc;
-    return resample_any(c, 1);
+    rc = resample_any(c, 1);
+    if (!rc) rc = record_after_resample(c);
+    return rc;
 }
 
 int smc_move(smc_ctx *c) {
@@ -477,7 +534,8 @@ int smc_move(smc_ctx *c) {
 int smc_resample(smc_ctx *c, int force) {
     if (!c) return SMC_E_ARG;
     if (!c->initialized) return SMC_E_STATE;
-    return resample_any(c, force ? 0 : 1);
+    const int rc = resample_any(c, force ? 0 : 1);
+    return rc ? rc : record_after_resample(c);
 }
 
 int smc_mcmc(smc_ctx *c) {
@@ -491,6 +549,7 @@ int smc_iterate(smc_ctx *c, int32_t n) {
     for (int32_t i = 0; i < n; ++i) {
         int rc = move_any(c);
         if (!rc) rc = resample_any(c, 1);
+        if (!rc) rc = record_after_resample(c);
         if (!rc) rc = mcmc_any(c);
         if (rc) return rc;
     }
@@ -1268,6 +1327,190 @@ int smc_batch_read_state(smc_batch *bt, int32_t filter, void *dst, int on_device
                                            k, bt->stream));
     if (!rc2) rc2 = cuda_check(cudaStreamSynchronize(bt->stream));
     return rc2 ? rc2 : rc;
+}
+
+}  // extern "C"
+
+// ============================================================ gradient ==
+
+namespace {
+
+// digamma by upward recurrence to x >= 6, then the asymptotic series
+// psi(x) ~ ln x - 1/(2x) - sum_k B_2k / (2k x^2k)
+double digamma_host(double x) {
+    double r = 0.0;
+    while (x < 6.0) {
+        r -= 1.0 / x;
+        x += 1.0;
+    }
+    const double f = 1.0 / (x * x);
+    return r + std::log(x) - 0.5 / x -
+           f * (1.0 / 12 - f * (1.0 / 120 - f * (1.0 / 252 - f * (1.0 / 240 - f * (1.0 / 132)))));
+}
+
+template <typename R>
+void set_slots(PfArgs<R> &a, const char *src, char *dst, int64_t ld) {
+    for (int r = 0; r < 4; ++r) {
+        a.x[0][r] = reinterpret_cast<R *>(const_cast<char *>(src)) + (size_t)r * ld;
+        a.x[1][r] = reinterpret_cast<R *>(dst) + (size_t)r * ld;
+    }
+    a.lw[0] = reinterpret_cast<R *>(const_cast<char *>(src)) + (size_t)4 * ld;
+    a.lw[1] = reinterpret_cast<R *>(dst) + (size_t)4 * ld;
+}
+
+// resampling decisions of the recorded run (host copy), T = t_host + 1
+int recorded_flags(smc_ctx *c, std::vector<int> &flags) {
+    const int32_t T = c->t_host + 1;
+    if (T < 1 || T > c->cfg.max_records) return SMC_E_STATE;
+    std::vector<smc_record> h(T);
+    int32_t nw = 0;
+    const int rc = smc_read_history(c, h.data(), T, &nw);
+    if (rc) return rc;
+    if (nw != T) return SMC_E_STATE;
+    flags.resize(T);
+    for (int32_t t = 0; t < T; ++t) flags[t] = h[t].resampled;
+    return SMC_OK;
+}
+
+double *scal(smc_ctx *c) { return reinterpret_cast<double *>(c->ws + c->L.scal); }
+
+template <typename R>
+int pf_replay_impl(smc_ctx *c, const double th[4], double *h_out) {
+    std::vector<int> flags;
+    int rc = recorded_flags(c, flags);
+    if (rc) return rc;
+    const int32_t T = c->t_host + 1;
+    PfArgs<R> a = pf_args<R>(c);
+    a.sd_pos = R(th[0]);
+    a.sd_vel = R(th[1]);
+    set_obs_params(a, th[2], th[3], c->cfg.model == SMC_MODEL_CV_GAUSS);
+    a.part = reinterpret_cast<Partial *>(c->ws + c->L.rep_part);
+    double *sc = scal(c);
+    uint32_t *ticket = reinterpret_cast<uint32_t *>(sc + 16);
+    if ((rc = cuda_check(cudaMemsetAsync(sc, 0, 256, c->stream)))) return rc;
+    char *rep[2] = {c->ws + c->L.rep, c->ws + c->L.rep + 5 * row_bytes(c)};
+    const int32_t *hist = reinterpret_cast<const int32_t *>(c->ws + c->L.hist);
+    for (int32_t t = 0; t < T; ++t) {
+        set_slots<R>(a, rep[(t + 1) & 1], rep[t & 1], c->L.ld);
+        const int gather = (t > 0 && flags[t - 1]) ? 1 : 0;
+        a.anc = gather ? hist + (size_t)(t - 1) * c->L.ld : c->anc;
+        pf_replay_kernel<R><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(a, t, gather, sc + 2 + ((t + 1) & 1),
+                                                                           sc + 2 + (t & 1), sc + 4, ticket);
+        if ((rc = cuda_check(cudaGetLastError()))) return rc;
+    }
+    if ((rc = cuda_check(cudaMemcpyAsync(h_out, sc + 4, 8, cudaMemcpyDeviceToHost, c->stream)))) return rc;
+    return cuda_check(cudaStreamSynchronize(c->stream));
+}
+
+template <typename R>
+int pf_grad_impl(smc_ctx *c, double *grad) {
+    std::vector<int> flags;
+    int rc = recorded_flags(c, flags);
+    if (rc) return rc;
+    const int32_t T = c->t_host + 1;
+    const int64_t n = c->cfg.n_particles, ld = c->L.ld;
+    const int ck = c->L.ck;
+    PfArgs<R> a = pf_args<R>(c);
+    a.part = reinterpret_cast<Partial *>(c->ws + c->L.rep_part);
+    double *sc = scal(c);
+    uint32_t *ticket = reinterpret_cast<uint32_t *>(sc + 16);
+    if ((rc = cuda_check(cudaMemsetAsync(sc, 0, 256, c->stream)))) return rc;
+    const int32_t *hist = reinterpret_cast<const int32_t *>(c->ws + c->L.hist);
+    float *gb[2] = {reinterpret_cast<float *>(c->ws + c->L.gbar), reinterpret_cast<float *>(c->ws + c->L.gbar) + ld};
+    R *xb = reinterpret_cast<R *>(c->ws + c->L.xbar);
+    R *atb = reinterpret_cast<R *>(c->ws + c->L.at);
+    auto slot = [&](int64_t s, int k) -> char * {
+        return k == 0 ? ckpt_slot(c, s) : c->ws + c->L.seg + (size_t)k * 5 * row_bytes(c);
+    };
+    AdjArgs<R> g;
+    g.n = n;
+    g.ld = ld;
+    g.obs = c->obs;
+    g.rec = c->rec;
+    g.rec_cap = c->cfg.max_records;
+    g.grad = sc + 8;
+    g.part = a.part;
+    g.ticket = ticket;
+    const double s = c->cfg.cv.obs_scale, nu = c->cfg.cv.obs_df;
+    g.delta = R(c->cfg.cv.delta);
+    g.inv_scale = R(1.0 / s);
+    g.scale = R(s);
+    g.nu = R(nu);
+    g.inv_nu = R(1.0 / nu);
+    g.half_nu1 = R(0.5 * (nu + 1.0));
+    g.dnu_const = R(0.5 * (digamma_host(0.5 * (nu + 1.0)) - digamma_host(0.5 * nu)) - 0.5 / nu);
+    g.gaussian = (c->cfg.model == SMC_MODEL_CV_GAUSS) ? 1 : 0;
+    g.key = key_of(c);
+    g.stream = c->cfg.stream_id;
+    const int64_t nseg = (T + ck - 1) / ck;
+    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+        const int32_t t0 = (int32_t)(sg * ck), t1 = std::min<int32_t>(t0 + ck, T);
+        // recompute iterations t0 + 1 .. t1 - 1 from the checkpoint at t0
+        for (int32_t t = t0 + 1; t < t1; ++t) {
+            set_slots<R>(a, slot(sg, t - 1 - t0), slot(sg, t - t0), ld);
+            const int gather = flags[t - 1] ? 1 : 0;
+            a.anc = gather ? hist + (size_t)(t - 1) * ld : c->anc;
+            pf_replay_kernel<R><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(
+                a, t, gather, &c->rec[(t - 1) % c->cfg.max_records].log_norm, sc + 20, sc + 21, ticket);
+            if ((rc = cuda_check(cudaGetLastError()))) return rc;
+        }
+        // reverse sweep through the segment
+        for (int32_t t = t1 - 1; t >= t0; --t) {
+            const char *sl = slot(sg, t - t0);
+            g.x = reinterpret_cast<const R *>(sl);
+            g.lw = reinterpret_cast<const R *>(sl) + 4 * ld;
+            g.gbar_next = gb[(t + 1) & 1];
+            g.gbar = gb[t & 1];
+            g.xbar_f = (t == T - 1) ? nullptr : xb;
+            g.at = atb;
+            g.S_next_in = sc + ((t + 1) & 1);
+            g.S_out = sc + (t & 1);
+            g.t = t;
+            g.last = (t == T - 1) ? 1 : 0;
+            pf_adjoint_kernel<R><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(g);
+            if ((rc = cuda_check(cudaGetLastError()))) return rc;
+            if (t > 0) {
+                if (flags[t - 1]) {
+                    pf_parent_gather_kernel<R><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, c->stream>>>(
+                        hist + (size_t)(t - 1) * ld, atb, xb, n, ld);
+                    if ((rc = cuda_check(cudaGetLastError()))) return rc;
+                } else {
+                    std::swap(xb, atb);  // identity ancestry: the parent adjoint is A^T xbar itself
+                }
+            }
+        }
+    }
+    if ((rc = cuda_check(cudaMemcpyAsync(grad, sc + 8, 32, cudaMemcpyDeviceToHost, c->stream)))) return rc;
+    return cuda_check(cudaStreamSynchronize(c->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+int smc_pf_grad(smc_ctx *c, double grad[4]) {
+    if (!c || !grad) return SMC_E_ARG;
+    if (!recording(c) || !c->initialized) return SMC_E_STATE;
+    const int rc = read_state(c);
+    if (rc) return rc;
+    return (c->cfg.precision == 32) ? pf_grad_impl<float>(c, grad) : pf_grad_impl<double>(c, grad);
+}
+
+int smc_pf_replay(smc_ctx *c, const double theta[4], double *h_log_evidence) {
+    if (!c || !theta || !h_log_evidence) return SMC_E_ARG;
+    if (!recording(c) || !c->initialized) return SMC_E_STATE;
+    if (!(theta[2] > 0) || !(theta[3] > 0)) return SMC_E_ARG;
+    const int rc = read_state(c);
+    if (rc) return rc;
+    return (c->cfg.precision == 32) ? pf_replay_impl<float>(c, theta, h_log_evidence)
+                                    : pf_replay_impl<double>(c, theta, h_log_evidence);
+}
+
+int smc_read_ancestor_history(smc_ctx *c, int32_t t, int32_t *dst, int on_device) {
+    if (!c || !dst || t < 0) return SMC_E_ARG;
+    if (!recording(c) || t > c->t_host) return SMC_E_STATE;
+    const int32_t *src = reinterpret_cast<const int32_t *>(c->ws + c->L.hist) + (size_t)t * c->L.ld;
+    return copy_out(c, dst, src, (size_t)c->cfg.n_particles * 4, on_device);
 }
 
 }  // extern "C"

@@ -35,7 +35,8 @@ class Config(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_particles", ctypes.c_int64),
                 ("max_records", ctypes.c_int32), ("scheme", ctypes.c_int32), ("threshold", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("max_data", ctypes.c_int64), ("cv", CVParams), ("gmm", GMMParams)]
+                ("max_data", ctypes.c_int64), ("cv", CVParams), ("gmm", GMMParams),
+                ("checkpoint_every", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class Record(ctypes.Structure):
@@ -81,6 +82,9 @@ _SIGS = {
     "smc_sync": (_I, [_P]),
     "smc_error_string": (ctypes.c_char_p, [_I]),
     "smc_philox4x32_10": (_I, [_P, ctypes.POINTER(ctypes.c_uint32), _P, ctypes.c_int64, _P]),
+    "smc_pf_grad": (_I, [_P, _P]),
+    "smc_pf_replay": (_I, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "smc_read_ancestor_history": (_I, [_P, ctypes.c_int32, _P, _I]),
     "smc_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), _P, _P, ctypes.c_int32]),
     "smc_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Config), _P, _P, ctypes.c_int32, _P,
                               ctypes.c_size_t, _P]),
@@ -127,10 +131,12 @@ def check(code, where):
 
 
 FLAG_KEEP_CDF = 1
+FLAG_RECORD = 2
 
 
 def make_config(model="cv", n=1024, precision=32, scheme="systematic", threshold=0.5, seed=0, stream_id=0,
-                max_records=None, max_data=1000, cv=None, gmm=None, keep_cdf=True):
+                max_records=None, max_data=1000, cv=None, gmm=None, keep_cdf=True, record=False,
+                checkpoint_every=16):
     c = Config()
     c.model = {"cv": MODEL_CV, "cv_gauss": MODEL_CV_GAUSS, "gmm": MODEL_GMM}[model]
     c.precision = precision
@@ -139,7 +145,8 @@ def make_config(model="cv", n=1024, precision=32, scheme="systematic", threshold
     c.threshold = float(threshold)
     c.seed = int(seed)
     c.stream_id = int(stream_id)
-    c.flags = FLAG_KEEP_CDF if keep_cdf else 0
+    c.flags = (FLAG_KEEP_CDF if keep_cdf else 0) | (FLAG_RECORD if record else 0)
+    c.checkpoint_every = int(checkpoint_every)
     c.max_data = int(max_data)
     c.max_records = int(max_records if max_records is not None else max(2, max_data + 1))
     p = dict(delta=0.1, sd_pos=0.02, sd_vel=1.0, obs_scale=0.5, obs_df=10.0, sd_pos0=1.0, sd_vel0=1.0)
@@ -291,6 +298,24 @@ class Sampler:
         a = np.ascontiguousarray(np.asarray(lw, dtype=self.rdtype))
         assert a.shape == (self.n,)
         check(lib().smc_write_log_weight(self.ctx, a.ctypes.data_as(_P), 0), "smc_write_log_weight")
+
+    def pf_grad(self):
+        """d log Z-hat / d(sd_pos, sd_vel, obs_scale, obs_df) of the recorded run."""
+        g = np.zeros(4)
+        check(lib().smc_pf_grad(self.ctx, g.ctypes.data_as(_P)), "smc_pf_grad")
+        return g
+
+    def pf_replay(self, theta):
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        v = ctypes.c_double()
+        check(lib().smc_pf_replay(self.ctx, th.ctypes.data_as(_P), ctypes.byref(v)), "smc_pf_replay")
+        return v.value
+
+    def ancestor_history(self, t):
+        out = np.empty(self.n, dtype=np.int32)
+        check(lib().smc_read_ancestor_history(self.ctx, int(t), out.ctypes.data_as(_P), 0),
+              "smc_read_ancestor_history")
+        return out
 
     def add_log_weight(self, incw):
         a = np.ascontiguousarray(np.asarray(incw, dtype=self.rdtype))
