@@ -248,3 +248,105 @@ def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, keep=False)
                               s if keep else None, U, accs))
         U_prev, a_prev = U, a_t
     return logz_ds, logz_ps, recs
+
+
+# ---------------------------------------------------------------- MALA --
+# Not in the paper: the differentiable move asked of the hot path.  The
+# Metropolis-adjusted Langevin move acts jointly on the unconstrained
+# coordinates u = (mu_1..r, log lambda_1..r, z_1..r-1), z_j = log(omega_j /
+# omega_r), targeting gamma_t(u) = log-prior + alpha_t l + log|Jacobian|
+# (sum_j log lambda_j + sum_j log omega_j; the same Jacobians as the
+# random-walk blocks).  With responsibilities rho_kj = omega_j N_kj / sum_i
+# omega_i N_ki:
+#   d gamma / d mu_j       = -(mu_j - mu0)/sd0^2 + alpha sum_k rho_kj lambda_j (y_k - mu_j)
+#   d gamma / d log lam_j  = (shape0 - 1) - rate0 lambda_j + 1
+#                            + alpha sum_k rho_kj (1 - lambda_j (y_k - mu_j)^2) / 2
+#   d gamma / d z_j        = 1 - r omega_j + alpha sum_k (rho_kj - omega_j)
+# Proposal u' = u + eps^2/2 grad(u) + eps xi; accept when
+# log U <= gamma(u') - gamma(u) + log q(u | u') - log q(u' | u),
+# log q(b | a) = -|b - a - eps^2/2 grad(a)|^2 / (2 eps^2).
+# Random numbers: 3r - 1 normals from draws 0-2 of tag TAG_MALA, the
+# acceptance uniform at draw 16.
+
+
+def to_unconstrained(mu, lam, om):
+    return np.concatenate([mu, np.log(lam), np.log(om[:-1] / om[-1:])])
+
+
+def from_unconstrained(u, r):
+    mu = u[:r]
+    lam = np.exp(u[r:2 * r])
+    full = np.concatenate([u[2 * r:], np.zeros((1, u.shape[1]))])
+    full = full - np.max(full, axis=0)
+    e = np.exp(full)
+    return mu, lam, e / np.sum(e, axis=0)
+
+
+def loglik_grad(mu, lam, om, y, chunk=1024):
+    """l(theta) and its gradient in u: returns (l, d/dmu, d/dloglam, d/dz)."""
+    r, N = mu.shape
+    ll = np.empty(N)
+    gmu = np.empty((r, N))
+    glam = np.empty((r, N))
+    gz = np.empty((max(r - 1, 0), N))
+    for s in range(0, N, chunk):
+        m = mu[:, s:s + chunk, None]
+        l_ = lam[:, s:s + chunk, None]
+        w = om[:, s:s + chunk, None]
+        d = y[None, None, :] - m
+        with np.errstate(divide="ignore"):
+            a = np.log(w) + 0.5 * np.log(l_) - 0.5 * LOG_2PI - 0.5 * l_ * d * d
+        amax = np.max(a, axis=0)
+        e = np.exp(a - amax[None])
+        se = np.sum(e, axis=0)
+        ll[s:s + chunk] = np.sum(amax + np.log(se), axis=1)
+        rho = e / se[None]
+        gmu[:, s:s + chunk] = np.sum(rho * l_ * d, axis=2)
+        glam[:, s:s + chunk] = np.sum(rho * 0.5 * (1 - l_ * d * d), axis=2)
+        if r > 1:
+            gz[:, s:s + chunk] = np.sum(rho[:-1] - w[:-1], axis=2)
+    return ll, gmu, glam, gz
+
+
+def log_target_u(u, a_t, y, p):
+    mu, lam, om = from_unconstrained(u, p.r)
+    with np.errstate(divide="ignore"):
+        jac = np.sum(np.log(lam), axis=0) + np.sum(np.log(om), axis=0)
+    return log_prior(mu, lam, om, p) + a_t * log_lik(mu, lam, om, y) + jac
+
+
+def grad_log_target_u(u, a_t, y, p):
+    r = p.r
+    mu, lam, om = from_unconstrained(u, r)
+    ll, gmu, glam, gz = loglik_grad(mu, lam, om, y)
+    g_mu = -(mu - p.mu0) / p.sd0 ** 2 + a_t * gmu
+    g_lam = (p.shape0 - 1) - p.rate0 * lam + 1 + a_t * glam
+    g_z = (1 - r * om[:-1]) + a_t * gz
+    return np.concatenate([g_mu, g_lam, g_z]), ll
+
+
+def mala_step(s, a_t, t, y, seed, p, eps=0.05, stream=0, return_delta=False):
+    n = s.mu.shape[1]
+    r = p.r
+    idx = np.arange(n)
+    u = to_unconstrained(s.mu, s.lam, s.om)
+    g, _ = grad_log_target_u(u, a_t, y, p)
+    xi = philox.normals(seed, idx, t, philox.TAG_MALA, 3 * r - 1, stream)
+    up = u + 0.5 * eps * eps * g + eps * xi
+    gp, llp = grad_log_target_u(up, a_t, y, p)
+    mu, lam, om = from_unconstrained(up, r)
+    lp = log_prior(mu, lam, om, p)
+    with np.errstate(divide="ignore"):
+        gam_p = lp + a_t * llp + np.sum(np.log(lam), axis=0) + np.sum(np.log(om), axis=0)
+        gam = s.lprior + a_t * s.llik + np.sum(np.log(s.lam), axis=0) + np.sum(np.log(s.om), axis=0)
+    fwd = -np.sum((up - u - 0.5 * eps * eps * g) ** 2, axis=0) / (2 * eps * eps)
+    bwd = -np.sum((u - up - 0.5 * eps * eps * gp) ** 2, axis=0) / (2 * eps * eps)
+    delta = gam_p - gam + bwd - fwd
+    w = philox.draw_words(seed, idx, t, philox.TAG_MALA, stream, philox.DRAW_MH_UNIFORM)
+    logu = np.log(philox.uniform(w[:, 0]))
+    acc = logu <= delta
+    new = State(np.where(acc, mu, s.mu), np.where(acc, lam, s.lam), np.where(acc, om, s.om),
+                np.where(acc, lp, s.lprior), np.where(acc, llp, s.llik))
+    if return_delta:
+        return new, acc, delta, logu
+    return new, acc

@@ -153,3 +153,33 @@ def test_schedules():
     assert abs(gmm.alpha(3, pl) - 0.3) < 1e-15
     assert gmm.proposal_scales(1.0) == (0.15, 0.3, 0.4)
     assert gmm.proposal_scales(0.0) == gmm.proposal_scales(0.02)
+
+
+def test_mala_gradient_matches_central_differences():
+    p = gmm.GMMParams(r=3, shape0=2, rate0=1.5)
+    y = workloads.gmm_data(60, seed=8)
+    mu, lam, om = _theta(5, 3, 11)
+    u = gmm.to_unconstrained(mu, lam, om)
+    for a_t in (0.0, 0.3, 1.0):
+        g, _ = gmm.grad_log_target_u(u, a_t, y, p)
+        h = 1e-5
+        for k in range(u.shape[0]):
+            up, um = u.copy(), u.copy()
+            up[k] += h
+            um[k] -= h
+            fd = (gmm.log_target_u(up, a_t, y, p) - gmm.log_target_u(um, a_t, y, p)) / (2 * h)
+            assert np.allclose(g[k], fd, rtol=1e-6, atol=1e-5), (a_t, k, g[k], fd)
+
+
+def test_mala_leaves_the_prior_invariant():
+    p = gmm.GMMParams(r=3)
+    y = workloads.gmm_data(30, seed=2)
+    s = gmm.init_state(20000, y, 9, p)
+    accs = []
+    for rnd in range(8):
+        s, acc = gmm.mala_step(s, 0.0, 300 + rnd, y, 9, p, eps=0.5)
+        accs.append(acc.mean())
+    assert 0.05 < np.mean(accs) < 0.99
+    assert stats.kstest(s.mu[0], stats.norm(0, 10).cdf).pvalue > 1e-4
+    assert stats.kstest(s.lam[1], stats.expon().cdf).pvalue > 1e-4
+    assert stats.kstest(s.om[2], stats.beta(1, 2).cdf).pvalue > 1e-4
