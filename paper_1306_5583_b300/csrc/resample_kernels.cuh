@@ -194,13 +194,19 @@ struct GridTargets {
         const unsigned long long ck = kStratified ? 2ull * resample_u24_at(key, stream, t, k) + 1ull : c;
         return ((unsigned long long)k << 25) + ck;
     }
-    // first k in [0, n] with QN P_k >= X D
+    // first k in [0, n] with QN P_k >= X D.  With k0 = floor(X N / QN) the
+    // answer is k0 or k0 + 1 (P_k / 2^25 lies in (k, k + 1)); k0 comes from a
+    // float64 estimate (error below 1) corrected with exact 128-bit products.
     __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long QN) const {
-        const unsigned long long D = denom();
-        const unsigned __int128 z = ((unsigned __int128)X * D) / QN;
-        const int64_t k0 = (int64_t)(z >> 25);
+        const unsigned long long N = (unsigned long long)n;
+        int64_t k0 = (int64_t)floor(double(X) * double(N) / double(QN));
+        if (k0 < 0) k0 = 0;
+        if (k0 > n) k0 = n;
+        const U128 xn = mul64(X, N);
+        while (k0 > 0 && gt128(mul64((unsigned long long)k0, QN), xn)) --k0;  // k0 QN <= X N
+        while (k0 < n && !gt128(mul64((unsigned long long)k0 + 1, QN), xn)) ++k0;  // X N < (k0 + 1) QN
         if (k0 >= n) return n;
-        return gt128(mul64(X, D), mul64(QN, P(k0))) ? k0 + 1 : k0;
+        return gt128(mul64(X, denom()), mul64(QN, P(k0))) ? k0 + 1 : k0;
     }
 };
 
@@ -227,10 +233,15 @@ struct SortedTargets {
     // i.e. s_k >= v with v the smallest s such that 2 s + 1 >= ceil(X 2^25 / QN)
     __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long QN) const {
         if (m == 0) return 0;
-        const unsigned __int128 y = ((unsigned __int128)X) << 25;
-        const unsigned __int128 c = (y + QN - 1) / QN;
-        if (c > ((unsigned __int128)1 << 25)) return (int64_t)m;
-        const unsigned long long cc = (unsigned long long)c;
+        // c = ceil(X 2^25 / QN) <= 2^25 (X <= QN): float64 estimate, exact correction
+        const U128 y{X >> 39, X << 25};
+        long long c0 = (long long)ceil(double(X) * 33554432.0 / double(QN));
+        if (c0 < 0) c0 = 0;
+        if (c0 > (1ll << 25) + 1) c0 = (1ll << 25) + 1;
+        unsigned long long cc = (unsigned long long)c0;
+        while (cc > 0 && !gt128(y, mul64(cc - 1, QN))) --cc;  // (cc - 1) QN < y
+        while (gt128(y, mul64(cc, QN))) ++cc;                  // y <= cc QN
+        if (cc > (1ull << 25)) return (int64_t)m;
         const unsigned long long v = cc / 2;
         if (v >= (1ull << 24)) return (int64_t)m;
         const int64_t b = (int64_t)(v >> bucket_shift);

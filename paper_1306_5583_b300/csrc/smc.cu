@@ -29,6 +29,8 @@ int gmm_initialize(smc_ctx *c);
 int gmm_on_data(smc_ctx *c);
 int gmm_setup(smc_ctx *c);
 void gmm_release(smc_ctx *c);
+int gmm_launch_reweight(smc_ctx *c);
+int gmm_launch_mcmc(smc_ctx *c);
 
 constexpr size_t kAlign = 256;
 
@@ -164,6 +166,7 @@ struct smc_ctx {
     int initialized;
     int device;
     DevState host_st;     // last state read back
+    cudaGraphExec_t graph;  // one captured iteration (move, resampling, mcmc)
 };
 
 namespace {
@@ -416,6 +419,40 @@ int move_any(smc_ctx *c) {
     return record_after_move(c);
 }
 
+// The kernels of one iteration, without host bookkeeping (capturable).
+int launch_iteration(smc_ctx *c) {
+    int rc;
+    if (c->cfg.model == SMC_MODEL_GMM) {
+        rc = gmm_launch_reweight(c);
+        if (!rc) rc = resample_any(c, 1);
+        if (!rc) rc = gmm_launch_mcmc(c);
+    } else {
+        rc = (c->cfg.precision == 32) ? launch_pf<float>(c) : launch_pf<double>(c);
+        if (!rc) rc = resample_any(c, 1);
+    }
+    return rc;
+}
+
+int build_graph(smc_ctx *c) {
+    if (c->graph) return SMC_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SMC_E_CUDA;
+    const int rc = launch_iteration(c);
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc ? rc : SMC_E_CUDA;
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        c->graph = nullptr;
+        return SMC_E_CUDA;
+    }
+    return SMC_OK;
+}
+
 int mcmc_any(smc_ctx *c) {
     if (!c->initialized) return SMC_E_STATE;
     if (c->cfg.model == SMC_MODEL_GMM) return gmm_mcmc(c);
@@ -469,6 +506,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->n_obs = 0;
     c->t_host = -1;
     c->initialized = 0;
+    c->graph = nullptr;
     cudaGetDevice(&c->device);
     // zero the state block, records, scan status words and bucket counters
     int rc = cuda_check(cudaMemsetAsync(c->ws, 0, L.part, c->stream));
@@ -488,6 +526,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
 
 int smc_destroy(smc_ctx *c) {
     if (!c) return SMC_E_ARG;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
     gmm_release(c);
     delete c;
     return SMC_OK;
@@ -546,6 +585,19 @@ int smc_mcmc(smc_ctx *c) {
 int smc_iterate(smc_ctx *c, int32_t n) {
     if (!c || n < 0) return SMC_E_ARG;
     if (!c->initialized) return SMC_E_STATE;
+    // graph replay: every kernel reads the iteration index from the device
+    // state, so one captured iteration serves every t (host bookkeeping and
+    // the recording copies are not captured)
+    const int64_t limit = (c->cfg.model == SMC_MODEL_GMM) ? c->cfg.gmm.n_iter : c->n_obs - 1;
+    if (c->stream != nullptr && !recording(c) && n > 0) {
+        if (c->t_host + (int64_t)n > limit) return SMC_E_ARG;
+        int rc = build_graph(c);
+        if (rc) return rc;
+        for (int32_t i = 0; i < n; ++i)
+            if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return SMC_E_CUDA;
+        c->t_host += n;
+        return SMC_OK;
+    }
     for (int32_t i = 0; i < n; ++i) {
         int rc = move_any(c);
         if (!rc) rc = resample_any(c, 1);
@@ -861,6 +913,9 @@ int gmm_launch(smc_ctx *c, GmmKernel k) {
 int gmm_launch_any(smc_ctx *c, GmmKernel k) {
     return (c->cfg.precision == 32) ? gmm_launch<float>(c, k) : gmm_launch<double>(c, k);
 }
+
+int gmm_launch_reweight(smc_ctx *c) { return gmm_launch_any(c, GMM_REWEIGHT); }
+int gmm_launch_mcmc(smc_ctx *c) { return gmm_launch_any(c, GMM_MCMC); }
 
 int gmm_initialize(smc_ctx *c) {
     const int rc = gmm_launch_any(c, GMM_INIT);
