@@ -70,6 +70,14 @@ extern "C" {
 #define SMC_MODEL_CV_GAUSS 1  /* same with Gaussian observations (Kalman closed form) */
 #define SMC_MODEL_GMM 2       /* Sec. 5.2: Bayesian Gaussian mixture, tempered SMC sampler */
 
+/* GMM mcmc moves: the paper's three random-walk Metropolis blocks, a
+ * Metropolis-adjusted Langevin move on all unconstrained coordinates driven by
+ * the gradient of the tempered log-target, or the blocks followed by one
+ * Langevin move */
+#define SMC_GMM_RW 0
+#define SMC_GMM_MALA 1
+#define SMC_GMM_RW_MALA 2
+
 /* GMM annealing schedules (Sec. 5.2.3) */
 #define SMC_ALPHA_LINEAR 0  /* alpha_t = t / T */
 #define SMC_ALPHA_PRIOR 1   /* alpha_t = (t / T)^p */
@@ -94,6 +102,9 @@ typedef struct {
     double power;         /* p of the prior schedule */
     double mu0, sd0;      /* normal prior of each mean */
     double rate0;         /* Gamma prior rate of each precision */
+    int32_t move;         /* SMC_GMM_RW, SMC_GMM_MALA or SMC_GMM_RW_MALA */
+    int32_t reserved;
+    double mala_step;     /* Langevin step size epsilon */
 } smc_gmm_params;
 
 typedef struct {
@@ -129,7 +140,8 @@ typedef struct {
     int32_t resampled;    /* 1 when the ESS test asked for resampling */
     int32_t status;       /* SMC_OK or an error code */
     int32_t pad;
-    double pad2[2];
+    double accept_mala;   /* GMM: acceptance rate of the Langevin move */
+    double pad2;
 } smc_record;
 
 typedef struct smc_ctx smc_ctx;
@@ -199,7 +211,8 @@ int smc_iteration(const smc_ctx *ctx, int32_t *t);
 /* Readers.  Layouts: state is structure-of-arrays, d rows of N values of the
  * context's precision (CV: d = 4, rows x_pos, y_pos, x_vel, y_vel; GMM:
  * d = 3r + 2, rows mu_1..r, lambda_1..r, omega_1..r, log-prior,
- * log-likelihood).  Log-weights: N values (raw lw_t).  Ancestors: N int32
+ * log-likelihood, followed for the Langevin moves by 3r - 1 rows of the
+ * log-likelihood's gradient in (mu, log lambda, log(omega_j / omega_r))).  Log-weights: N values (raw lw_t).  Ancestors: N int32
  * (sorted; valid after a resampling step).  CDF: N uint64 fixed-point
  * inclusive prefix sums (kept only with SMC_FLAG_KEEP_CDF; otherwise
  * smc_read_cdf returns SMC_E_STATE).  Records: the last min(count, available) records in

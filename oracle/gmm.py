@@ -220,8 +220,10 @@ def path_u(lw, L, resampled, llik):
     return float(np.sum(np.exp(lw - L) * llik))
 
 
-def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, keep=False):
-    """Whole sampler.  Returns (log Z standard, log Z path sampling, records)."""
+def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, keep=False, move="rw", eps=0.05):
+    """Whole sampler.  Returns (log Z standard, log Z path sampling, records).
+    move: "rw" (the three random-walk blocks), "mala" (one Langevin move) or
+    "rw_mala" (the blocks, then one Langevin move)."""
     s = init_state(n, y, seed, p, stream)
     lw = np.full(n, -math.log(n))
     L = 0.0
@@ -240,7 +242,12 @@ def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, keep=False)
         if resampled:
             anc = resample.resample(scheme, lw, seed, t, stream)
             s = s.take(anc)
-        s, accs = mcmc(s, a_t, t, y, seed, p, stream)
+        accs = [0.0, 0.0, 0.0]
+        if move in ("rw", "rw_mala"):
+            s, accs = mcmc(s, a_t, t, y, seed, p, stream)
+        if move in ("mala", "rw_mala"):
+            s, am = mala_step(s, a_t, t, y, seed, p, eps, stream)
+            accs = accs + [float(np.mean(am))]
         U = path_u(lw, L, resampled, s.llik)
         logz_ds += L
         logz_ps += 0.5 * (a_t - a_prev) * (U + U_prev)

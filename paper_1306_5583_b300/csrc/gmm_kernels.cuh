@@ -54,9 +54,15 @@ struct GmmArgs {
     // prior: lp = lp_const + sum_j [-(mu_j - mu0)^2 / (2 sd0^2) + (a - 1) log lambda_j - b lambda_j]
     double mu0, sd0, inv_sd0, lp_const, shape_m1, rate;
     double half_nd_log2pi;  // nd log(2 pi) / 2
+    double mala_eps;        // Langevin step size
     uint2 key;
     uint32_t stream;
 };
+
+// moves of the mcmc kernel
+constexpr int kMoveRW = 0;
+constexpr int kMoveMALA = 1;
+constexpr int kMoveRWMALA = 2;
 
 // ---- per-datum math in base 2 ---------------------------------------------
 template <typename R>
@@ -135,6 +141,74 @@ __device__ __forceinline__ double gmm_loglik_quad(const R (&mu)[NC], const R (&l
     return v * kLn2 - half_nd_log2pi;
 }
 
+// Log-likelihood and its gradient in (mu, log lambda, log(omega_j / omega_r))
+// for one particle (quad-split data as above).  gm, gl, gz receive
+// sum_k rho_kj lambda_j (y_k - mu_j), sum_k rho_kj (1 - lambda_j (y_k - mu_j)^2) / 2
+// and sum_k (rho_kj - omega_j), with rho the responsibilities.
+template <typename R, int NC>
+__device__ __forceinline__ double gmm_loglik_grad_quad(const R (&mu)[NC], const R (&lam)[NC], const R (&om)[NC],
+                                                       const R *__restrict__ ys, int nd, int q,
+                                                       double half_nd_log2pi, R (&gm)[NC], R (&gl)[NC],
+                                                       R (&gz)[NC]) {
+    R c2[NC], h2[NC], sd[NC], sl[NC], sr[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        c2[j] = Base2<R>::lg2(om[j]) + R(0.5) * Base2<R>::lg2(lam[j]);
+        h2[j] = R(0.5 * kLog2e) * lam[j];
+        sd[j] = sl[j] = sr[j] = R(0);
+    }
+    Kahan<R> acc;
+    int k = q;
+    while (k < nd) {
+        R msum = 0, prod = 1;
+#pragma unroll 1
+        for (int g = 0; g < kGmmGroup && k < nd; ++g, k += kQuad) {
+            const R yk = ys[k];
+            R a[NC], d[NC];
+            R m = -INFINITY;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                d[j] = yk - mu[j];
+                a[j] = c2[j] - h2[j] * d[j] * d[j];
+                m = fmax(m, a[j]);
+            }
+            R e[NC], s = 0;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                e[j] = Base2<R>::ex2(a[j] - m);
+                s += e[j];
+            }
+            const R inv = R(1) / s;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                const R rho = e[j] * inv;
+                sd[j] += rho * d[j];
+                sl[j] += rho * d[j] * d[j];
+                sr[j] += rho;
+            }
+            msum += m;
+            prod *= s;
+        }
+        acc.add(msum + Base2<R>::lg2(prod));
+    }
+    double v = double(acc.s) - double(acc.c);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        sd[j] += __shfl_xor_sync(0xffffffffu, sd[j], 1);
+        sd[j] += __shfl_xor_sync(0xffffffffu, sd[j], 2);
+        sl[j] += __shfl_xor_sync(0xffffffffu, sl[j], 1);
+        sl[j] += __shfl_xor_sync(0xffffffffu, sl[j], 2);
+        sr[j] += __shfl_xor_sync(0xffffffffu, sr[j], 1);
+        sr[j] += __shfl_xor_sync(0xffffffffu, sr[j], 2);
+        gm[j] = lam[j] * sd[j];
+        gl[j] = R(0.5) * (sr[j] - lam[j] * sl[j]);
+        gz[j] = sr[j] - R(nd) * om[j];
+    }
+    return v * kLn2 - half_nd_log2pi;
+}
+
 template <typename R, int NC>
 __device__ __forceinline__ double gmm_log_prior(const GmmArgs<R> &a, const R (&mu)[NC], const R (&lam)[NC],
                                                 const R (&om)[NC]) {
@@ -200,36 +274,150 @@ template <typename R, int NC>
 struct Theta {
     R mu[NC], lam[NC], om[NC];
     R lp, ll;
+    R gm[NC], gl[NC], gz[NC];  // cached likelihood gradient (Langevin moves)
 };
 
-template <typename R, int NC>
-__device__ __forceinline__ void load_theta(const R *x, int64_t n, int64_t i, Theta<R, NC> &th) {
-    // n is the row pitch
+// rows: mu (NC), lambda (NC), omega (NC), log-prior, log-likelihood, then
+// with G the gradient: d/dmu (NC), d/dlog lambda (NC), d/dz (NC - 1)
+template <typename R, int NC, bool G>
+__device__ __forceinline__ void load_theta(const R *x, int64_t ld, int64_t i, Theta<R, NC> &th) {
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        th.mu[j] = x[(int64_t)j * n + i];
-        th.lam[j] = x[(int64_t)(NC + j) * n + i];
-        th.om[j] = x[(int64_t)(2 * NC + j) * n + i];
+        th.mu[j] = x[(int64_t)j * ld + i];
+        th.lam[j] = x[(int64_t)(NC + j) * ld + i];
+        th.om[j] = x[(int64_t)(2 * NC + j) * ld + i];
     }
-    th.lp = x[(int64_t)(3 * NC) * n + i];
-    th.ll = x[(int64_t)(3 * NC + 1) * n + i];
+    th.lp = x[(int64_t)(3 * NC) * ld + i];
+    th.ll = x[(int64_t)(3 * NC + 1) * ld + i];
+    if (G) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            th.gm[j] = x[(int64_t)(3 * NC + 2 + j) * ld + i];
+            th.gl[j] = x[(int64_t)(4 * NC + 2 + j) * ld + i];
+            th.gz[j] = (j < NC - 1) ? x[(int64_t)(5 * NC + 2 + j) * ld + i] : R(0);
+        }
+    }
 }
 
-template <typename R, int NC>
-__device__ __forceinline__ void store_theta(R *x, int64_t n, int64_t i, const Theta<R, NC> &th) {
-    // n is the row pitch
+template <typename R, int NC, bool G>
+__device__ __forceinline__ void store_theta(R *x, int64_t ld, int64_t i, const Theta<R, NC> &th) {
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        x[(int64_t)j * n + i] = th.mu[j];
-        x[(int64_t)(NC + j) * n + i] = th.lam[j];
-        x[(int64_t)(2 * NC + j) * n + i] = th.om[j];
+        x[(int64_t)j * ld + i] = th.mu[j];
+        x[(int64_t)(NC + j) * ld + i] = th.lam[j];
+        x[(int64_t)(2 * NC + j) * ld + i] = th.om[j];
     }
-    x[(int64_t)(3 * NC) * n + i] = th.lp;
-    x[(int64_t)(3 * NC + 1) * n + i] = th.ll;
+    x[(int64_t)(3 * NC) * ld + i] = th.lp;
+    x[(int64_t)(3 * NC + 1) * ld + i] = th.ll;
+    if (G) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            x[(int64_t)(3 * NC + 2 + j) * ld + i] = th.gm[j];
+            x[(int64_t)(4 * NC + 2 + j) * ld + i] = th.gl[j];
+            if (j < NC - 1) x[(int64_t)(5 * NC + 2 + j) * ld + i] = th.gz[j];
+        }
+    }
+}
+
+// One Metropolis-adjusted Langevin move on u = (mu, log lambda, z), z_j =
+// log(omega_j / omega_r), targeting gamma = log-prior + alpha l + sum log lambda
+// + sum log omega, from the cached likelihood gradient at the current point.
+// Returns 1 when accepted.  All four lanes of a quad take the same decision.
+template <typename R, int NC>
+__device__ __forceinline__ uint32_t mala_move(const GmmArgs<R> &a, Theta<R, NC> &th, double &lp, double &ll,
+                                              double a_t, uint32_t ii, uint32_t t, const R *ys, int q) {
+    constexpr int D = 3 * NC - 1;
+    const double eps = a.mala_eps, h = 0.5 * eps * eps;
+    const double a_m1 = a.shape_m1;
+    // gradient of gamma at the current point
+    R u[D], g[D], xi[D];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        u[j] = th.mu[j];
+        u[NC + j] = Math<R>::log(th.lam[j]);
+        g[j] = R(-(double(th.mu[j]) - a.mu0) * a.inv_sd0 * a.inv_sd0 + a_t * double(th.gm[j]));
+        g[NC + j] = R(a_m1 - a.rate * double(th.lam[j]) + 1.0 + a_t * double(th.gl[j]));
+        if (j < NC - 1) {
+            u[2 * NC + j] = Math<R>::log(th.om[j] / th.om[NC - 1]);
+            g[2 * NC + j] = R(1.0 - NC * double(th.om[j]) + a_t * double(th.gz[j]));
+        }
+    }
+    // 3r - 1 normals from draws 0, 1, 2, ... of TAG_MALA
+#pragma unroll
+    for (int c = 0; c < (D + 3) / 4; ++c) {
+        R z4[4];
+        normals4<R>(draw(a.key, ii, t, TAG_MALA, a.stream, (uint32_t)c), z4);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (4 * c + m < D) xi[4 * c + m] = z4[m];
+    }
+    R up[D];
+    double xi2 = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        up[k] = R(double(u[k]) + h * double(g[k]) + eps * double(xi[k]));
+        xi2 += double(xi[k]) * double(xi[k]);
+    }
+    Theta<R, NC> p2;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        p2.mu[j] = up[j];
+        p2.lam[j] = Math<R>::exp(up[NC + j]);
+    }
+    R vmax = 0;
+#pragma unroll
+    for (int j = 0; j < NC - 1; ++j) vmax = fmax(vmax, up[2 * NC + j]);
+    R sum = 0;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        p2.om[j] = Math<R>::exp(((j < NC - 1) ? up[2 * NC + j] : R(0)) - vmax);
+        sum += p2.om[j];
+    }
+#pragma unroll
+    for (int j = 0; j < NC; ++j) p2.om[j] = p2.om[j] / sum;
+    const double lp2 = gmm_log_prior<R, NC>(a, p2.mu, p2.lam, p2.om);
+    const double ll2 =
+        gmm_loglik_grad_quad<R, NC>(p2.mu, p2.lam, p2.om, ys, a.nd, q, a.half_nd_log2pi, p2.gm, p2.gl, p2.gz);
+    double jac = 0, jac2 = 0, bwd = 0;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        jac += double(u[NC + j]) + double(Math<R>::log(th.om[j]));
+        jac2 += double(up[NC + j]) + double(Math<R>::log(p2.om[j]));
+    }
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const double gpm = -(double(p2.mu[j]) - a.mu0) * a.inv_sd0 * a.inv_sd0 + a_t * double(p2.gm[j]);
+        const double gpl = a_m1 - a.rate * double(p2.lam[j]) + 1.0 + a_t * double(p2.gl[j]);
+        const double rm = double(u[j]) - double(up[j]) - h * gpm;
+        const double rl = double(u[NC + j]) - double(up[NC + j]) - h * gpl;
+        bwd += rm * rm + rl * rl;
+        if (j < NC - 1) {
+            const double gpz = 1.0 - NC * double(p2.om[j]) + a_t * double(p2.gz[j]);
+            const double rz = double(u[2 * NC + j]) - double(up[2 * NC + j]) - h * gpz;
+            bwd += rz * rz;
+        }
+    }
+    const double delta = (lp2 + a_t * ll2 + jac2) - (lp + a_t * ll + jac) - bwd / (2.0 * eps * eps) + 0.5 * xi2;
+    const R lu = mh_log_uniform<R>(a.key, ii, t, TAG_MALA, a.stream);
+    if (double(lu) <= delta) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            th.mu[j] = p2.mu[j];
+            th.lam[j] = p2.lam[j];
+            th.om[j] = p2.om[j];
+            th.gm[j] = p2.gm[j];
+            th.gl[j] = p2.gl[j];
+            th.gz[j] = p2.gz[j];
+        }
+        lp = lp2;
+        ll = ll2;
+        return 1u;
+    }
+    return 0u;
 }
 
 // ---- init: theta ~ prior, equal weights, U_0 --------------------------------
-template <typename R, int NC>
+template <typename R, int NC, bool G>
 __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     const R *ys = reinterpret_cast<const R *>(s_raw);
@@ -271,12 +459,14 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
         for (int j = 0; j < NC; ++j) th.om[j] = E[j] / sum;
     }
     th.lp = R(gmm_log_prior<R, NC>(a, th.mu, th.lam, th.om));
-    const double ll = gmm_loglik_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi);
+    const double ll = G ? gmm_loglik_grad_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi, th.gm,
+                                                      th.gl, th.gz)
+                        : gmm_loglik_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi);
     th.ll = R(ll);
     const int cur = sv->cur, cur_lw = sv->cur_lw;
     const R lw0 = R(-a.log_n);
     if (active && q == 0) {
-        store_theta<R, NC>(a.x[cur ^ 1], a.ld, i, th);
+        store_theta<R, NC, G>(a.x[cur ^ 1], a.ld, i, th);
         a.lw[cur_lw ^ 1][i] = lw0;
     }
     R lwv[1] = {(active && q == 0) ? lw0 : Math<R>::neg_inf()};
@@ -303,7 +493,7 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
             st->cur_lw = cur_lw ^ 1;
             st->ready = 0;
             st->gathered = 0;
-            st->accept[0] = st->accept[1] = st->accept[2] = 0;
+            st->accept[0] = st->accept[1] = st->accept[2] = st->accept[3] = 0;
         }
     }
 }
@@ -348,21 +538,22 @@ __global__ void __launch_bounds__(kBlock) gmm_reweight_kernel(GmmArgs<R> a) {
             st->base_shift = L;
             st->t = t;
             st->cur_lw = cur_lw ^ 1;
-            st->accept[0] = st->accept[1] = st->accept[2] = 0;
+            st->accept[0] = st->accept[1] = st->accept[2] = st->accept[3] = 0;
         }
     }
 }
 
 // ---- mcmc: gather, three Metropolis blocks, path sampling -------------------
-template <typename R, int NC>
+template <typename R, int NC, int MOVE>
 __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
+    constexpr bool G = (MOVE != kMoveRW);
     extern __shared__ __align__(16) unsigned char s_raw[];
-    __shared__ uint32_t s_acc[3];
+    __shared__ uint32_t s_acc[4];
     const R *ys = reinterpret_cast<const R *>(s_raw);
     DevState *st = a.st;
     const DevState *sv = snapshot(st);
     if (sv->error) return;
-    if (threadIdx.x < 3) s_acc[threadIdx.x] = 0;
+    if (threadIdx.x < 4) s_acc[threadIdx.x] = 0;
     stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st);
     const int32_t t = sv->t;
     const double a_t = a.alpha[t], a_p = (t > 0) ? a.alpha[t - 1] : 0.0;
@@ -378,9 +569,10 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     const int64_t ii = active ? i : a.n - 1;
     const int64_t src = gather ? (int64_t)__ldg(&a.anc[ii]) : ii;
     Theta<R, NC> th;
-    load_theta<R, NC>(a.x[cur], a.ld, src, th);
+    load_theta<R, NC, G>(a.x[cur], a.ld, src, th);
     double ll = double(th.ll), lp = double(th.lp);
     uint32_t acc_mask = 0;
+    if (MOVE != kMoveMALA) {
     // block 1: mu
     {
         R z[NC], mu2[NC];
@@ -460,22 +652,26 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     } else {
         acc_mask |= 4u;
     }
+    }  // random-walk blocks
+    if (MOVE == kMoveRWMALA) {
+        // the blocks moved theta: refresh the cached gradient at the current point
+        ll = gmm_loglik_grad_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi, th.gm, th.gl, th.gz);
+    }
+    if (G) acc_mask |= mala_move<R, NC>(a, th, lp, ll, a_t, (uint32_t)ii, (uint32_t)t, ys, q) << 3;
     th.lp = R(lp);
     th.ll = R(ll);
     R lwi = R(-a.log_n);
     if (active && q == 0) {
-        store_theta<R, NC>(a.x[cur ^ 1], a.ld, i, th);
+        store_theta<R, NC, G>(a.x[cur ^ 1], a.ld, i, th);
         if (gather) a.lw[cur_lw][i] = lwi;  // equal weights after resampling
         else lwi = a.lw[cur_lw][i];
         atomicAdd(&s_acc[0], acc_mask & 1u);
         atomicAdd(&s_acc[1], (acc_mask >> 1) & 1u);
         atomicAdd(&s_acc[2], (acc_mask >> 2) & 1u);
+        atomicAdd(&s_acc[3], (acc_mask >> 3) & 1u);
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
-        if (s_acc[threadIdx.x]) atomicAdd(&st->accept[threadIdx.x], s_acc[threadIdx.x]);
-        __threadfence();
-    }
+    if (threadIdx.x < 4 && s_acc[threadIdx.x]) atomicAdd(&st->accept[threadIdx.x], s_acc[threadIdx.x]);
     R lwv[1] = {(active && q == 0) ? lwi : Math<R>::neg_inf()};
     R h0[1] = {th.ll}, zero[1] = {R(0)};
     block_partial<R, 1, 1>(lwv, h0, zero, zero, &a.part[blockIdx.x]);
@@ -494,7 +690,9 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
         const double plz = st->path_log_z + 0.5 * (a_t - a_p) * (U + st->path_u);
         r->path_u = U;
         r->path_log_z = plz;
-        for (int b = 0; b < 3; ++b) r->accept[b] = double(*(volatile uint32_t *)&st->accept[b]) / double(a.n);
+        for (int b = 0; b < 3; ++b)
+            r->accept[b] = (MOVE == kMoveMALA) ? 0.0 : double(*(volatile uint32_t *)&st->accept[b]) / double(a.n);
+        r->accept_mala = G ? double(*(volatile uint32_t *)&st->accept[3]) / double(a.n) : 0.0;
         st->path_u = U;
         st->path_log_z = plz;
         st->cur = cur ^ 1;

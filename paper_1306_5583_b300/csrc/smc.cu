@@ -70,6 +70,8 @@ bool valid_config(const smc_config *c) {
         if (!kGmmEnabled) return false;
         if (c->gmm.n_comp < 1 || c->gmm.n_comp > kGmmMaxComp) return false;
         if (c->gmm.n_iter < 1 || c->gmm.shape0 < 1 || !(c->gmm.rate0 > 0) || !(c->gmm.sd0 > 0)) return false;
+        if (c->gmm.move < SMC_GMM_RW || c->gmm.move > SMC_GMM_RW_MALA) return false;
+        if (c->gmm.move != SMC_GMM_RW && !(c->gmm.mala_step > 0)) return false;
         if (c->max_data > kGmmMaxData) return false;
     } else {
         if (!(c->cv.obs_scale > 0) || !(c->cv.obs_df > 0)) return false;
@@ -82,7 +84,9 @@ Layout make_layout(const smc_config *c) {
     const int64_t n = c->n_particles;
     const size_t rs = (c->precision == 32) ? 4 : 8;
     L.rsize = rs;
-    L.d = (c->model == SMC_MODEL_GMM) ? 3 * c->gmm.n_comp + 2 : 4;
+    L.d = (c->model == SMC_MODEL_GMM)
+              ? 3 * c->gmm.n_comp + 2 + ((c->gmm.move != SMC_GMM_RW) ? 3 * c->gmm.n_comp - 1 : 0)
+              : 4;
     L.ld = (n + 63) & ~int64_t(63);
     L.nbw = (n + kPfTile - 1) / kPfTile;
     L.ntiles = (n + kScanTile - 1) / kScanTile;
@@ -195,7 +199,7 @@ __global__ void reset_state_kernel(DevState *st) {
     st->path_log_z = 0;
     st->qn = 0;
     st->sum_d = 0;
-    for (int i = 0; i < 3; ++i) st->accept[i] = 0;
+    for (int i = 0; i < 4; ++i) st->accept[i] = 0;
 }
 
 // observation-density constants of the constant-velocity model
@@ -864,6 +868,7 @@ GmmArgs<R> gmm_args(smc_ctx *c) {
     a.shape_m1 = shape - 1.0;
     a.rate = g.rate0;
     a.half_nd_log2pi = 0.5 * (double)c->n_obs * std::log(2.0 * M_PI);
+    a.mala_eps = g.mala_step;
     a.key = key_of(c);
     a.stream = cfg.stream_id;
     return a;
@@ -871,8 +876,9 @@ GmmArgs<R> gmm_args(smc_ctx *c) {
 
 enum GmmKernel { GMM_INIT, GMM_REWEIGHT, GMM_MCMC };
 
-template <typename R, int NC>
-int gmm_launch_nc(smc_ctx *c, GmmKernel k) {
+template <typename R, int NC, int MOVE>
+int gmm_launch_move(smc_ctx *c, GmmKernel k) {
+    constexpr bool G = (MOVE != kMoveRW);
     GmmArgs<R> a = gmm_args<R>(c);
     const size_t smem = (((size_t)a.nd * sizeof(R)) + 15) & ~size_t(15);
     const unsigned gq = (unsigned)((kQuad * a.n + kBlock - 1) / kBlock);
@@ -880,19 +886,31 @@ int gmm_launch_nc(smc_ctx *c, GmmKernel k) {
     switch (k) {
         case GMM_INIT:
             if (smem > 48 * 1024)
-                cudaFuncSetAttribute(gmm_init_kernel<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            gmm_init_kernel<R, NC><<<gq, kBlock, smem, c->stream>>>(a);
+                cudaFuncSetAttribute(gmm_init_kernel<R, NC, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            gmm_init_kernel<R, NC, G><<<gq, kBlock, smem, c->stream>>>(a);
             break;
         case GMM_REWEIGHT:
             gmm_reweight_kernel<R, NC><<<gw, kBlock, 0, c->stream>>>(a);
             break;
         case GMM_MCMC:
             if (smem > 48 * 1024)
-                cudaFuncSetAttribute(gmm_mcmc_kernel<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            gmm_mcmc_kernel<R, NC><<<gq, kBlock, smem, c->stream>>>(a);
+                cudaFuncSetAttribute(gmm_mcmc_kernel<R, NC, MOVE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            gmm_mcmc_kernel<R, NC, MOVE><<<gq, kBlock, smem, c->stream>>>(a);
             break;
     }
     return cuda_check(cudaGetLastError());
+}
+
+template <typename R, int NC>
+int gmm_launch_nc(smc_ctx *c, GmmKernel k) {
+    switch (c->cfg.gmm.move) {
+        case SMC_GMM_RW: return gmm_launch_move<R, NC, kMoveRW>(c, k);
+        case SMC_GMM_MALA: return gmm_launch_move<R, NC, kMoveMALA>(c, k);
+        case SMC_GMM_RW_MALA: return gmm_launch_move<R, NC, kMoveRWMALA>(c, k);
+    }
+    return SMC_E_ARG;
 }
 
 template <typename R>

@@ -53,8 +53,9 @@ struct DevState {
     unsigned long long sum_d;  // residual: sum of the deterministic copies
     uint32_t scan_ticket[kScanSlots];   // last-block tickets of the tile-sum passes
     unsigned long long scan_total[kScanSlots];  // exact totals of the tile-sum passes
-    uint32_t accept[3];                 // GMM accepted moves per block (last mcmc)
+    uint32_t accept[4];                 // GMM accepted moves per block and Langevin (last mcmc)
     int32_t gathered;                   // GMM: the last mcmc gathered by ancestors
+    int32_t pad2;
 };
 
 struct Partial {  // one per block of a weighting kernel

@@ -164,19 +164,23 @@ struct Combined {
 };
 
 // Block-level "am I the last of `count` arrivals" on a counter (the
-// counter is reset by the caller's finalisation).
+// counter is reset by the caller's finalisation).  The block barrier orders
+// the block's writes before thread 0's arrival, an acquire-release atomic
+// (no sequentially consistent fence) publishes them, and the last arrival's
+// acquire plus the barrier make every block's writes visible to the whole
+// last block (which reads them through L2).
+__device__ __forceinline__ unsigned atomic_add_acq_rel(uint32_t *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ bool last_arrival(uint32_t *counter, uint32_t count) {
     __shared__ bool s_last;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(counter, 1u);
-        s_last = (prev == count - 1);
-    }
+    if (threadIdx.x == 0) s_last = (atomic_add_acq_rel(counter, 1u) == count - 1);
     __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    return true;
+    return s_last;
 }
 
 template <typename R>

@@ -17,6 +17,7 @@ SCHEMES = {"multinomial": MULTINOMIAL, "stratified": STRATIFIED, "systematic": S
            "residual": RESIDUAL}
 MODEL_CV, MODEL_CV_GAUSS, MODEL_GMM = range(3)
 ALPHA_LINEAR, ALPHA_PRIOR = range(2)
+GMM_RW, GMM_MALA, GMM_RW_MALA = range(3)
 
 
 class CVParams(ctypes.Structure):
@@ -28,7 +29,8 @@ class CVParams(ctypes.Structure):
 class GMMParams(ctypes.Structure):
     _fields_ = [("n_comp", ctypes.c_int32), ("schedule", ctypes.c_int32), ("n_iter", ctypes.c_int32),
                 ("shape0", ctypes.c_int32), ("power", ctypes.c_double), ("mu0", ctypes.c_double),
-                ("sd0", ctypes.c_double), ("rate0", ctypes.c_double)]
+                ("sd0", ctypes.c_double), ("rate0", ctypes.c_double), ("move", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("mala_step", ctypes.c_double)]
 
 
 class Config(ctypes.Structure):
@@ -44,13 +46,13 @@ class Record(ctypes.Structure):
                 ("mean", ctypes.c_double * 2), ("max_lw", ctypes.c_double), ("path_u", ctypes.c_double),
                 ("path_log_z", ctypes.c_double), ("alpha", ctypes.c_double), ("accept", ctypes.c_double * 3),
                 ("t", ctypes.c_int32), ("resampled", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("pad2", ctypes.c_double * 2)]
+                ("pad", ctypes.c_int32), ("accept_mala", ctypes.c_double), ("pad2", ctypes.c_double)]
 
     def as_dict(self):
         return dict(t=self.t, L=self.log_norm, logZ=self.log_evidence, ess=self.ess, mean_x=self.mean[0],
                     mean_y=self.mean[1], max_lw=self.max_lw, path_u=self.path_u, path_log_z=self.path_log_z,
-                    alpha=self.alpha, accept=tuple(self.accept), resampled=bool(self.resampled),
-                    status=self.status)
+                    alpha=self.alpha, accept=tuple(self.accept), accept_mala=self.accept_mala,
+                    resampled=bool(self.resampled), status=self.status)
 
 
 _P = ctypes.c_void_p
@@ -153,7 +155,8 @@ def make_config(model="cv", n=1024, precision=32, scheme="systematic", threshold
     p.update(cv or {})
     for k, v in p.items():
         setattr(c.cv, k, float(v))
-    g = dict(n_comp=4, schedule=ALPHA_PRIOR, n_iter=500, shape0=1, power=5.0, mu0=0.0, sd0=10.0, rate0=1.0)
+    g = dict(n_comp=4, schedule=ALPHA_PRIOR, n_iter=500, shape0=1, power=5.0, mu0=0.0, sd0=10.0, rate0=1.0,
+             move=GMM_RW, mala_step=0.05)
     g.update(gmm or {})
     for k, v in g.items():
         setattr(c.gmm, k, v)

@@ -15,11 +15,13 @@ pytestmark = pytest.mark.gpu
 
 
 def make_gmm(n, nd=1000, r=4, T=500, precision=32, scheme="systematic", threshold=0.5, seed=0, data_seed=0,
-             schedule="prior", power=5.0, shape0=1, rate0=1.0):
+             schedule="prior", power=5.0, shape0=1, rate0=1.0, move="rw", eps=0.05):
     y = workloads.gmm_data(nd, seed=data_seed)
+    mv = {"rw": smc.GMM_RW, "mala": smc.GMM_MALA, "rw_mala": smc.GMM_RW_MALA}[move]
     cfg = smc.make_config(model="gmm", n=n, precision=precision, scheme=scheme, threshold=threshold, seed=seed,
                           max_data=nd, max_records=T + 1,
-                          gmm=dict(n_comp=r, n_iter=T, power=power, shape0=shape0, rate0=rate0,
+                          gmm=dict(n_comp=r, n_iter=T, power=power, shape0=shape0, rate0=rate0, move=mv,
+                                   mala_step=eps,
                                    schedule=smc.ALPHA_LINEAR if schedule == "linear" else smc.ALPHA_PRIOR))
     s = smc.Sampler(cfg)
     s.set_data(y)
@@ -217,3 +219,66 @@ def _mh_block_at(s, block, a_t, t, y, seed, p, idx):
     new = m.State(np.where(acc, mu, s.mu), np.where(acc, lam, s.lam), np.where(acc, om, s.om),
                   np.where(acc, lp, s.lprior), np.where(acc, ll, s.llik))
     return new, acc, delta, logu
+
+
+@pytest.mark.parametrize("precision,move,r", [(64, "mala", 4), (32, "mala", 4), (32, "rw_mala", 3), (32, "mala", 1)])
+def test_langevin_moves_teacher_forced(precision, move, r):
+    """MALA (and random walk followed by MALA): the cached likelihood
+    gradient equals the oracle's, and each move matches the oracle from the
+    GPU's own particles wherever no decision is a near tie."""
+    need_gpu()
+    n, nd, T, seed, eps = 2048 + 19, 200, 30, 6, 0.05
+    s, y, op = make_gmm(n, nd=nd, r=r, T=T, precision=precision, seed=seed, threshold=0.8, move=move, eps=eps)
+    rel = 1e-10 if precision == 64 else 1e-5
+    grel = 1e-9 if precision == 64 else 2e-4
+    tie = 1e-9 if precision == 64 else 2e-3
+    s.initialize()
+    near_total = 0
+    for t in range(1, 6):
+        s.move()
+        rec = s.history(1)[0]
+        s.resample()
+        anc = s.ancestors().astype(np.int64) if rec["resampled"] else None
+        x_prev = s.state().astype(np.float64)
+        src = anc if anc is not None else np.arange(n)
+        xin = x_prev[:, src]
+        mu, lam, om = xin[:r], xin[r:2 * r], xin[2 * r:3 * r]
+        st = ogmm.State(mu.copy(), lam.copy(), om.copy(), ogmm.log_prior(mu, lam, om, op), ogmm.log_lik(mu, lam, om, y))
+        if move == "mala":
+            # cached gradient rows of the GPU against the oracle at the GPU's parameters
+            _, gm, gl, gz = ogmm.loglik_grad(st.mu, st.lam, st.om, y)
+            g_gpu = xin[3 * r + 2:]
+            ref = np.concatenate([gm, gl, gz])
+            assert_close(g_gpu, ref, grel * np.max(np.abs(ref)), f"cached gradient t={t}")
+        a_t = ogmm.alpha(t, op)
+        near = np.zeros(n, dtype=bool)
+        if move == "rw_mala":
+            for block in ("mu", "lambda", "weight") if r > 1 else ("mu", "lambda"):
+                st, acc, delta, logu = ogmm.mh_block(st, block, a_t, t, y, seed, op, return_delta=True)
+                near |= np.abs(delta - logu) < tie * np.maximum(1.0, np.abs(delta))
+        st, acc, delta, logu = ogmm.mala_step(st, a_t, t, y, seed, op, eps=eps, return_delta=True)
+        near |= np.abs(delta - logu) < tie * np.maximum(1.0, np.abs(delta))
+        s.mcmc()
+        x = s.state().astype(np.float64)
+        ok = ~near
+        near_total += int(near.sum())
+        assert_close(x[:r][:, ok], st.mu[:, ok], rel, f"mu t={t}")
+        assert_close(x[r:2 * r][:, ok], st.lam[:, ok], rel, f"lambda t={t}")
+        assert_close(x[2 * r:3 * r][:, ok], st.om[:, ok], rel, f"omega t={t}")
+        assert_close(x[3 * r + 1][ok], st.llik[ok], rel, f"log-likelihood t={t}")
+        rec = s.history(1)[0]
+        assert abs(rec["accept_mala"] - acc.mean()) <= (near.sum() + 1) / n
+    assert near_total < 0.01 * n * 5
+
+
+def test_mala_full_run_fp64_matches_oracle():
+    need_gpu()
+    n, nd, r, T, seed = 1024, 80, 2, 20, 4
+    s, y, op = make_gmm(n, nd=nd, r=r, T=T, precision=64, seed=seed, move="mala", eps=0.1)
+    s.initialize()
+    s.iterate(T)
+    ds_ref, ps_ref, recs = ogmm.run(y, n, seed, op, move="mala", eps=0.1)
+    gpu = s.history(T + 1)[1:]
+    assert [g["resampled"] for g in gpu] == [o.resampled for o in recs]
+    assert abs(s.log_evidence() - ds_ref) < 1e-8
+    assert abs(s.path_sampling() - ps_ref) < 1e-8
