@@ -238,6 +238,18 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(n, 8)
+    if rank == 0 and not args.no_extra:
+        clk = (clocks or {}).get("sm_mhz", 2032)
+        extra = {}
+        g = bench_gmm(dev, stream, move="rw")
+        g["mufu_frac_of_peak"] = g["mufu_ops_per_s"] / mufu_peak_ops(clk)
+        extra["gmm_rw_n2^16"] = g
+        gm = bench_gmm(dev, stream, n=1 << 18, move="mala")
+        gm["mufu_frac_of_peak"] = gm["mufu_ops_per_s"] / mufu_peak_ops(clk)
+        extra["gmm_mala_n2^18"] = gm
+        extra["pf_grad_n2^18_T500"] = bench_pf_grad(dev, stream)
+        extra["batched_256"] = bench_batched(dev, stream)
+        out["extra"] = extra
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:
@@ -276,6 +288,135 @@ def run_e2e(make, scheme, K, y, dev, stream, flush):
     s.close()
     return {"value": s.n * steps / total, "unit": "particle-updates/s", "h2d_bytes_per_step": 16,
             "d2h_bytes_per_step": ctypes.sizeof(smc.Record), "timing": "host wall clock per call (synchronising)"}
+
+
+def mufu_peak_ops(clock_mhz):
+    """MUFU (special-function) issue rate: 16 ops per clock per SM (4 per
+    SM sub-partition), 148 SMs."""
+    return 148 * 16 * clock_mhz * 1e6
+
+
+def bench_gmm(dev, stream, n=1 << 16, T=500, move="rw", K=20):
+    """GMM tempered sampler (Sec. 5.2): iterations per second and the MUFU
+    roofline of the mcmc kernel, plus both evidence estimates of a full
+    run."""
+    import torch
+    from paper_1306_5583_b300 import smc, workloads
+    y = workloads.gmm_data(1000, seed=0)
+    mv = {"rw": smc.GMM_RW, "mala": smc.GMM_MALA}[move]
+    cfg = smc.make_config(model="gmm", n=n, precision=32, scheme="systematic", threshold=0.5, seed=1, max_data=1000,
+                          max_records=T + 1, keep_cdf=False, gmm=dict(n_comp=4, n_iter=T, power=5.0, move=mv,
+                                                                       mala_step=0.05))
+    s = smc.Sampler(cfg, stream=stream, device=dev)
+    s.set_data(y)
+    with torch.cuda.stream(stream):
+        s.initialize()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.iterate(T)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        full_ms = e0.elapsed_time(e1)
+        ds, ps = s.log_evidence(), s.path_sampling()
+        # the mcmc kernel alone, late in the schedule (alpha near 1)
+        s.initialize()
+        s.iterate(T - K - 1)
+        mk = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+        for k in range(K):
+            s.move()
+            s.resample()
+            mk[k][0].record(stream)
+            s.mcmc()
+            mk[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        mcmc_ms = float(np.median([a.elapsed_time(b) for a, b in mk]))
+    s.close()
+    # MUFU ops per particle and iteration: per Metropolis block n (r ex2 + 1/8 lg2);
+    # a Langevin move adds one reciprocal per datum and counts as one block
+    per_block = 1000 * (4 + 1.0 / 8)
+    mufu = n * (3 * per_block if move == "rw" else 1000 * (4 + 1 + 1.0 / 8))
+    return {"n_particles": n, "iterations": T, "move": move, "ms_full_run": full_ms,
+            "particle_updates_per_s": n * T / (full_ms * 1e-3), "log_evidence_standard": ds,
+            "log_evidence_path_sampling": ps, "mcmc_kernel_us": mcmc_ms * 1e3,
+            "mufu_ops_per_s": mufu / (mcmc_ms * 1e-3)}
+
+
+def bench_batched(dev, stream, count=256):
+    """Config 4: 256 filters of uneven N and T in one launch per kernel per
+    iteration, against the same 256 filters run one by one (plain API)."""
+    import torch
+    from paper_1306_5583_b300 import smc, workloads
+    ns, ts = workloads.batch_shapes(count, seed=0)
+    p = dict(workloads.CV_DEFAULT)
+    data = [workloads.cv_data(int(T), seed=1 + b, **p)[1] for b, T in enumerate(ts)]
+    work = float(np.sum(ns.astype(np.float64) * ts))
+    cfg = smc.make_config(model="cv", n=1, precision=32, scheme="systematic", threshold=0.5, seed=3,
+                          max_data=int(ts.max()), keep_cdf=False, cv=p)
+    bt = smc.Batch(cfg, ns, ts, stream=stream, device=dev)
+    for b in range(count):
+        bt.set_data(b, data[b])
+    with torch.cuda.stream(stream):
+        grid = bt.tune()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        batch_ms = e0.elapsed_time(e1)
+        lz_batch = bt.log_evidence()
+    bt.close()
+    t0 = time.perf_counter()
+    lz_plain = np.empty(count)
+    with torch.cuda.stream(stream):
+        for b in range(count):
+            pc = smc.make_config(model="cv", n=int(ns[b]), precision=32, scheme="systematic", threshold=0.5, seed=3,
+                                 stream_id=b, max_data=int(ts[b]), keep_cdf=False, cv=p)
+            s = smc.Sampler(pc, stream=stream, device=dev)
+            s.set_data(data[b])
+            s.initialize()
+            s.iterate(int(ts[b]) - 1)
+            lz_plain[b] = s.log_evidence()
+            s.close()
+        torch.cuda.synchronize(dev)
+    plain_s = time.perf_counter() - t0
+    return {"filters": count, "particle_updates": work, "batched_ms": batch_ms,
+            "batched_particle_updates_per_s": work / (batch_ms * 1e-3), "plain_one_by_one_s": plain_s,
+            "plain_particle_updates_per_s": work / plain_s, "speedup": plain_s / (batch_ms * 1e-3),
+            "autotuned_blocks_per_sm": grid, "log_evidence_identical": bool(np.array_equal(lz_batch, lz_plain))}
+
+
+def bench_pf_grad(dev, stream, n=1 << 18, T=500):
+    """Config 3b: gradient of the log-likelihood estimate (recorded forward,
+    then the reverse sweep with recomputation) against the plain forward."""
+    import torch
+    from paper_1306_5583_b300 import smc, workloads
+    p = dict(workloads.CV_DEFAULT)
+    _, y = workloads.cv_data(T, seed=0, **p)
+    out = {}
+    for rec in (False, True):
+        cfg = smc.make_config(model="cv", n=n, precision=32, scheme="systematic", threshold=0.5, seed=1, max_data=T,
+                              cv=p, keep_cdf=False, record=rec, checkpoint_every=16)
+        s = smc.Sampler(cfg, stream=stream, device=dev)
+        s.set_data(y)
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            s.initialize()
+            s.iterate(T - 1)
+            torch.cuda.synchronize(dev)
+            out["forward_recorded_s" if rec else "forward_s"] = time.perf_counter() - t0
+            if rec:
+                t0 = time.perf_counter()
+                g = s.pf_grad()
+                out["gradient_s"] = time.perf_counter() - t0
+                out["gradient"] = [float(v) for v in g]
+        s.close()
+    out["gradient_over_forward"] = out["gradient_s"] / out["forward_s"]
+    out["n_particles"] = n
+    out["iterations"] = T
+    return out
 
 
 def cpu_baseline(n, iters):
@@ -327,6 +468,7 @@ def main():
     ap.add_argument("--scheme", default="systematic")
     ap.add_argument("--n", type=int, default=N_FULL)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the GMM, batched and gradient sections")
     ap.add_argument("--schemes", default="systematic,stratified,multinomial,residual")
     args = ap.parse_args()
     if args.warmup < 3:

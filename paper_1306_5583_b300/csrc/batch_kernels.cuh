@@ -73,7 +73,7 @@ __device__ __forceinline__ PfArgs<R> filter_args(const BatchArgs<R> &B, int b) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kBlock) batch_pf_kernel(BatchArgs<R> B) {
+__global__ void __launch_bounds__(kBlock, 3) batch_pf_kernel(BatchArgs<R> B) {
     const int32_t t = B.bs->t + 1;
     if (t >= B.tmax) return;
     const int nact = B.act_tiles[t];
@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(kBlock) batch_pf_kernel(BatchArgs<R> B) {
         const int cur = sv->cur, cur_lw = sv->cur_lw;
         const bool gather = (t > 0) && (sv->ready != 0);
         const int nblk = B.tfirst[b + 1] - B.tfirst[b];
-        pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, sv->log_norm);
-        if (last_arrival(&st->ticket, (uint32_t)nblk)) pf_finalize<R>(a, st, nblk, t, cur, cur_lw);
+        pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, log_norm_shift<R>(sv));
+        if (last_arrival(&st->ticket, (uint32_t)nblk)) pf_finalize<R, 1>(a, st, sv, nblk, t, cur, cur_lw);
     }
     if (last_arrival(&B.bs->ticket, gridDim.x) && threadIdx.x == 0) {
         B.bs->t = t;
@@ -135,12 +135,17 @@ template <typename R, bool kStratified>
 __device__ __forceinline__ void batch_select_tile(const BatchArgs<R> &B, int tile, int b, DevState *st,
                                                   const DevState *sv) {
     const QGen<R> g = filter_qgen(B, b, sv);
-    GridTargets<kStratified> tg{B.n[b], B.proto.key, B.stream_of[b], 0, 0};
-    tg.prepare(sv);
     const int lt = tile - B.sfirst[b];
     if (lt == 0 && threadIdx.x == 0) st->ready = 1;
-    const unsigned long long QN = sv->scan_total[SLOT_CDF];
-    scan_select_tile(g, tg, AncOut{B.anc + B.off[b]}, NoSink{}, B.n[b], lt, B.tsum + B.sfirst[b], QN, st);
+    unsigned long long pre, QN;
+    tile_prefix_total(B.tsum + B.sfirst[b], lt, lt, &pre, &QN);
+    QN = sv->scan_total[SLOT_CDF];
+    GridTargets<kStratified> proto{};
+    proto.n = B.n[b];
+    proto.key = B.proto.key;
+    proto.stream = B.stream_of[b];
+    const GridTargets<kStratified> tg = block_targets(proto, sv, QN);
+    scan_select_tile(g, tg, AncOut{B.anc + B.off[b]}, NoSink{}, B.n[b], lt, pre, QN, st);
 }
 
 template <typename R, bool kStratified>
@@ -176,6 +181,8 @@ __global__ void batch_reset_kernel(DevState *fst, int nf, BatchState *bs) {
     st->log_evidence = 0;
     st->ess = 0;
     st->max_lw = 0;
+    st->max_lw_f = 0;
+    st->log_norm_f[0] = st->log_norm_f[1] = 0;
     for (int k = 0; k < kScanSlots; ++k) {
         st->scan_ticket[k] = 0;
         st->scan_total[k] = 0;

@@ -25,18 +25,151 @@ template <typename R>
 __global__ void __launch_bounds__(kBlock) pf_replay_kernel(PfArgs<R> a, int32_t t, int gather,
                                                            const double *L_prev, double *L_out, double *logz,
                                                            uint32_t *ticket) {
-    __shared__ double s_lprev;
-    if (threadIdx.x == 0) s_lprev = (t > 0 && !gather) ? __ldcg(L_prev) : 0.0;
-    __syncthreads();
-    pf_tile<R>(a, blockIdx.x, t, 0, 0, gather != 0, s_lprev);
-    if (!last_arrival(ticket, gridDim.x)) return;
-    Combined c;
-    combine_partials<R>(a.part, gridDim.x, &c);
+    // L_{t-1} split once per block (hi + lo in R)
+    __shared__ R s_lprev[2];
     if (threadIdx.x == 0) {
-        const double L = c.M + log(c.S1);
+        const double lp = (t > 0 && !gather) ? __ldcg(L_prev) : 0.0;
+        s_lprev[0] = R(lp);
+        s_lprev[1] = R(lp - double(s_lprev[0]));
+    }
+    __syncthreads();
+    pf_tile<R>(a, blockIdx.x, t, 0, 0, gather != 0, Shift<R>(s_lprev[0], s_lprev[1]));
+    if (!last_arrival(ticket, gridDim.x)) return;
+    // L_t as the forward kernels compute it (compensated float on the FP32 path)
+    double L;
+    if constexpr (sizeof(R) == 4) {
+        CombinedDF d;
+        combine_partials_df<1>(a.part, gridDim.x, &d);
+        L = df_to_double(df_add_f(df_log(d.S[0]), d.M));
+    } else {
+        Combined c;
+        combine_partials<R>(a.part, gridDim.x, &c);
+        L = c.M + log(c.S1);
+    }
+    if (threadIdx.x == 0) {
         *L_out = L;
         *logz = (t == 0 ? 0.0 : *logz) + L;
         *ticket = 0;
+    }
+}
+
+// Five block sums (result to thread 0, as float64).  FP64 path: float64
+// warp sums.  FP32 path: DF warp trees from the per-thread float sums; the
+// partial keeps (hi, lo) pairs in the same 64 bytes.
+template <typename R>
+__device__ __forceinline__ void block_sum5(const R (&v)[5], double (&out)[5]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (sizeof(R) == 8) {
+        __shared__ double s_red[kBlock / 32][5];
+        double u[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) u[q] = warp_sum(v[q]);
+        __syncthreads();
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) s_red[warp][q] = u[q];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                out[q] = 0.0;
+                for (int k = 0; k < kBlock / 32; ++k) out[q] += s_red[k][q];
+            }
+        }
+    } else {
+        __shared__ DF s_red[kBlock / 32][5];
+        DF u[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) u[q] = DF{v[q], 0.0f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) u[q] = df_add(u[q], df_shfl_xor(u[q], o));
+        __syncthreads();
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) s_red[warp][q] = u[q];
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) u[q] = lane < kBlock / 32 ? s_red[lane][q] : DF{0.0f, 0.0f};
+#pragma unroll
+            for (int o = (kBlock / 32) / 2; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) u[q] = df_add(u[q], df_shfl_xor(u[q], o));
+            if (lane == 0) {
+                float *f = reinterpret_cast<float *>(out);  // packed (hi, lo) pairs for store_sum5
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    f[2 * q] = u[q].hi;
+                    f[2 * q + 1] = u[q].lo;
+                }
+            }
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_sum5(Partial *p, const double (&w)[5]) {
+    if constexpr (sizeof(R) == 8) {
+        p->m = 0;
+        p->s1 = w[0];
+        p->s2 = w[1];
+        p->sx = w[2];
+        p->sy = w[3];
+        p->su = w[4];
+    } else {
+        const float *f = reinterpret_cast<const float *>(w);
+        float *d = reinterpret_cast<float *>(p);
+#pragma unroll
+        for (int k = 0; k < 10; ++k) d[k] = f[k];
+    }
+}
+
+// grid sums of nb partials of store_sum5 (thread 0 receives float64 values)
+template <typename R>
+__device__ __forceinline__ void combine_sum5(const Partial *part, int nb, double (&out)[5]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (sizeof(R) == 8) {
+        double u[5] = {0, 0, 0, 0, 0};
+        for (int b = threadIdx.x; b < nb; b += kBlock) {
+            u[0] += __ldcg(&part[b].s1);
+            u[1] += __ldcg(&part[b].s2);
+            u[2] += __ldcg(&part[b].sx);
+            u[3] += __ldcg(&part[b].sy);
+            u[4] += __ldcg(&part[b].su);
+        }
+        block_sum5<double>(u, out);
+    } else {
+        __shared__ DF s_red[kBlock / 32][5];
+        DF u[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) u[q] = DF{0.0f, 0.0f};
+        for (int b = threadIdx.x; b < nb; b += kBlock) {
+            const float *f = reinterpret_cast<const float *>(&part[b]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) u[q] = df_add(u[q], DF{__ldcg(f + 2 * q), __ldcg(f + 2 * q + 1)});
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) u[q] = df_add(u[q], df_shfl_xor(u[q], o));
+        __syncthreads();
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) s_red[warp][q] = u[q];
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) u[q] = lane < kBlock / 32 ? s_red[lane][q] : DF{0.0f, 0.0f};
+#pragma unroll
+            for (int o = (kBlock / 32) / 2; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) u[q] = df_add(u[q], df_shfl_xor(u[q], o));
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) out[q] = df_to_double(u[q]);
+        }
     }
 }
 
@@ -68,19 +201,22 @@ struct AdjArgs {
 template <typename R>
 __global__ void __launch_bounds__(kBlock) pf_adjoint_kernel(AdjArgs<R> a) {
     constexpr int E = kPfItems;
-    __shared__ double s_L, s_S;
+    // per-block scalars converted once by thread 0 (no per-thread float64)
+    __shared__ R s_L[2], s_S;
     __shared__ int s_res;
     const uint32_t n = (uint32_t)a.n;
     if (threadIdx.x == 0) {
         const smc_record *r = &a.rec[a.t % a.rec_cap];
-        s_L = r->log_norm;
+        const double L = r->log_norm;
+        s_L[0] = R(L);
+        s_L[1] = R(L - double(s_L[0]));
         s_res = r->resampled;
-        s_S = a.last ? 0.0 : __ldcg(a.S_next_in);
+        s_S = R(a.last ? 0.0 : __ldcg(a.S_next_in));
     }
     __syncthreads();
     const bool chain = !(a.last || s_res);  // lw_{t+1} depends on lw_t
-    const Shift<R> Lt(s_L);
-    const R S_next = R(s_S);
+    const Shift<R> Lt(s_L[0], s_L[1]);
+    const R S_next = s_S;
     const uint32_t i0 = (blockIdx.x * (uint32_t)kBlock + threadIdx.x) * (uint32_t)E;
     R x0[E], x1[E], x2[E], x3[E], lw[E], f0[E], f1[E], f2[E], f3[E];
     float gn[E];
@@ -99,7 +235,13 @@ __global__ void __launch_bounds__(kBlock) pf_adjoint_kernel(AdjArgs<R> a) {
         for (int j = 0; j < E; ++j) f0[j] = f1[j] = f2[j] = f3[j] = R(0);
     }
     if (chain) load_k<float, E>(a.gbar_next, i0, n, gn);
-    const R yx = R(a.obs[2 * a.t]), yy = R(a.obs[2 * a.t + 1]);
+    __shared__ R s_y[2];
+    if (threadIdx.x == 0) {
+        s_y[0] = R(a.obs[2 * a.t]);
+        s_y[1] = R(a.obs[2 * a.t + 1]);
+    }
+    __syncthreads();
+    const R yx = s_y[0], yy = s_y[1];
     R sg[E], sds[E], sdn[E], sp[E], sv[E], a0[E], a1[E], a2[E], a3[E];
     float gout[E];
 #pragma unroll
@@ -141,57 +283,23 @@ __global__ void __launch_bounds__(kBlock) pf_adjoint_kernel(AdjArgs<R> a) {
     store_k<R, E>(a.at + a.ld, i0, n, a1);
     store_k<R, E>(a.at + 2 * a.ld, i0, n, a2);
     store_k<R, E>(a.at + 3 * a.ld, i0, n, a3);
-    // block sums of (gbar, gbar ds, gbar dnu, d sd_pos, d sd_vel) in float64
-    __shared__ double s_red[kBlock / 32][5];
-    double v[5] = {0, 0, 0, 0, 0};
+    // block sums of (gbar, gbar ds, gbar dnu, d sd_pos, d sd_vel): float64 on
+    // the FP64 path, compensated float (per-thread float sums) on the FP32 path
+    R v[5] = {0, 0, 0, 0, 0};
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-        v[0] += double(sg[j]);
-        v[1] += double(sds[j]);
-        v[2] += double(sdn[j]);
-        v[3] += double(sp[j]);
-        v[4] += double(sv[j]);
+        v[0] += sg[j];
+        v[1] += sds[j];
+        v[2] += sdn[j];
+        v[3] += sp[j];
+        v[4] += sv[j];
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < 5; ++q) v[q] = warp_sum(v[q]);
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) s_red[warp][q] = v[q];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double w[5] = {0, 0, 0, 0, 0};
-        for (int k = 0; k < kBlock / 32; ++k)
-            for (int q = 0; q < 5; ++q) w[q] += s_red[k][q];
-        Partial p;
-        p.m = 0;
-        p.s1 = w[0];
-        p.s2 = w[1];
-        p.sx = w[2];
-        p.sy = w[3];
-        p.su = w[4];
-        a.part[blockIdx.x] = p;
-    }
+    double w[5];
+    block_sum5<R>(v, w);
+    if (threadIdx.x == 0) store_sum5<R>(&a.part[blockIdx.x], w);
     if (!last_arrival(a.ticket, gridDim.x)) return;
-    __shared__ double s_tot[kBlock / 32][5];
-    double u[5] = {0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += kBlock) {
-        u[0] += __ldcg(&a.part[b].s1);
-        u[1] += __ldcg(&a.part[b].s2);
-        u[2] += __ldcg(&a.part[b].sx);
-        u[3] += __ldcg(&a.part[b].sy);
-        u[4] += __ldcg(&a.part[b].su);
-    }
-#pragma unroll
-    for (int q = 0; q < 5; ++q) u[q] = warp_sum(u[q]);
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) s_tot[warp][q] = u[q];
-    __syncthreads();
+    combine_sum5<R>(a.part, (int)gridDim.x, w);
     if (threadIdx.x == 0) {
-        double w[5] = {0, 0, 0, 0, 0};
-        for (int k = 0; k < kBlock / 32; ++k)
-            for (int q = 0; q < 5; ++q) w[q] += s_tot[k][q];
         *a.S_out = w[0];
         a.grad[2] += w[1];
         a.grad[3] += w[2];

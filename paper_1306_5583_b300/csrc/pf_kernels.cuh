@@ -28,6 +28,8 @@ struct PfArgs {
     Partial *part;
     double log_n;
     double threshold;
+    float thr_df[2];   // threshold as a DF value (FP32 finalize)
+    int32_t thr_mode;  // 0 compare, 1 always, 2 never
     R delta, sd_pos, sd_vel, sd_pos0, sd_vel0;
     R inv_scale, inv_nu, half_nu1, ll_const;  // ll_const = 2 log(density constant)
     int32_t gaussian;
@@ -56,7 +58,7 @@ __device__ __forceinline__ R cv_loglik(const PfArgs<R> &a, R yx, R yy, R px, R p
 // the memory system sees all of a thread's requests at once.
 template <typename R>
 __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_t t, int cur, int cur_lw,
-                                        bool gather, double log_norm_prev) {
+                                        bool gather, Shift<R> Lprev) {
     constexpr int E = kPfItems;
     const uint32_t n = (uint32_t)a.n;
     const uint32_t i0 = (blk * (uint32_t)kBlock + threadIdx.x) * (uint32_t)E;
@@ -88,9 +90,16 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
             load_k<R, E>(lws, i0, n, lwin);
         }
     }
-    const Shift<R> Lprev(log_norm_prev);
-    const R yx = R(a.obs[2 * t]), yy = R(a.obs[2 * t + 1]);
-    const R base_eq = R(-a.log_n);
+    // per-block constants converted once (no per-thread float64 work)
+    __shared__ R s_c[3];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_c[0] = R(a.obs[2 * t]);
+        s_c[1] = R(a.obs[2 * t + 1]);
+        s_c[2] = R(-a.log_n);
+    }
+    __syncthreads();
+    const R yx = s_c[0], yy = s_c[1], base_eq = s_c[2];
     R s0[E], s1[E], s2[E], s3[E], lwv[E], zero[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) {
@@ -122,34 +131,43 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
 
 // Last tile of a filter: combine its nblk partials, write the record of
 // iteration t and advance the filter's state.
-template <typename R>
-__device__ __forceinline__ void pf_finalize(const PfArgs<R> &a, DevState *st, int nblk, int32_t t, int cur,
-                                            int cur_lw) {
-    Combined c;
-    combine_partials<R>(a.part, nblk, &c);
-    if (threadIdx.x == 0) {
-        FinalizeArgs f{st, a.rec, a.rec_cap, t, 0, a.n, a.threshold, 0.0};
+// PT: partials per thread of the single-round-trip combine (register budget
+// of the caller; the result does not depend on it).
+template <typename R, int PT = 4>
+__device__ __forceinline__ void pf_finalize(const PfArgs<R> &a, DevState *st, const DevState *sv, int nblk,
+                                            int32_t t, int cur, int cur_lw) {
+    FinalizeArgs f{st,  a.rec,   a.rec_cap, t, 0, a.n, a.threshold, 0.0, {a.thr_df[0], a.thr_df[1]}, a.thr_mode,
+                   sv->log_evidence};
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+        CombinedDF c;
+        combine_partials_df<PT>(a.part, nblk, &c);
+        if (threadIdx.x == 0) done = finalize_weights_df(f, c);
+    } else {
+        Combined c;
+        combine_partials<R>(a.part, nblk, &c);
         double L;
-        if (finalize_weights(f, c, &L)) {
-            st->t = t;
-            st->cur = cur ^ 1;
-            st->cur_lw = cur_lw ^ 1;
-            st->ready = 0;
-        }
+        if (threadIdx.x == 0) done = finalize_weights(f, c, &L);
+    }
+    if (threadIdx.x == 0 && done) {
+        st->t = t;
+        st->cur = cur ^ 1;
+        st->cur_lw = cur_lw ^ 1;
+        st->ready = 0;
     }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kBlock) pf_iterate_kernel(PfArgs<R> a) {
+__global__ void __launch_bounds__(kBlock, 4) pf_iterate_kernel(PfArgs<R> a) {
     DevState *st = a.st;
     const DevState *sv = snapshot(st);
     if (sv->error) return;
     const int32_t t = sv->t + 1;
     const int cur = sv->cur, cur_lw = sv->cur_lw;
     const bool gather = (t > 0) && (sv->ready != 0);
-    pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, sv->log_norm);
+    pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, log_norm_shift<R>(sv));
     if (!take_ticket<R>(st)) return;
-    pf_finalize<R>(a, st, gridDim.x, t, cur, cur_lw);
+    pf_finalize<R>(a, st, sv, gridDim.x, t, cur, cur_lw);
 }
 
 }  // namespace smc

@@ -19,6 +19,7 @@
 // uniforms) by a search over the shared-memory CDF tile.
 #pragma once
 
+#include "grid_threshold.h"
 #include "weight_reduce.cuh"
 
 namespace smc {
@@ -34,7 +35,8 @@ struct QGen {
     R m;
     __device__ __forceinline__ void prepare(const DevState *st) {
         cur_lw = st->cur_lw ? lw[1] : lw[0];
-        m = R(st->max_lw);
+        if constexpr (sizeof(R) == 4) m = st->max_lw_f;
+        else m = R(st->max_lw);
     }
     __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
         return Math<R>::fixed(Math<R>::exp(cur_lw[i] - m), frac);
@@ -152,14 +154,21 @@ struct StoreSink {  // inclusive prefix sums to an array (the fixed-point CDF, b
 };
 
 // --------------------------------------------------------------- targets --
+//
+// A target set gives, per block: prepare(state) and setup(Q_N) (run by one
+// thread, then broadcast), count(), first_at_least(X, Q_N) = the first k
+// with Q_N P_k >= X D (the tile's output range), and thresholds(k0, tau):
+// tau_j = floor(Q_N P_{k0+j} / D) for j < kScanItems (k0 a multiple of
+// kScanItems; entries past count() are never used), so that
+// a_k = min{ i : Q_i > tau_k } with 64-bit comparisons only.
 
 struct NoTargets {
     static constexpr bool kActive = false;
     __device__ __forceinline__ void prepare(const DevState *) {}
+    __device__ __forceinline__ void setup(unsigned long long) {}
     __device__ __forceinline__ int64_t count() const { return 0; }
-    __device__ __forceinline__ unsigned long long denom() const { return 1; }
-    __device__ __forceinline__ unsigned long long P(int64_t) const { return 0; }
     __device__ __forceinline__ int64_t first_at_least(unsigned long long, unsigned long long) const { return 0; }
+    __device__ __forceinline__ void thresholds(int64_t, unsigned long long (&)[kScanItems]) const {}
 };
 
 __device__ __forceinline__ uint4 resample_words(uint2 key, uint32_t stream, uint32_t t, int64_t k4) {
@@ -173,9 +182,8 @@ __device__ __forceinline__ uint32_t resample_u24_at(uint2 key, uint32_t stream, 
     return u24(ww);
 }
 
-// Systematic (one u per iteration) and stratified (u_k per output) targets.
-// The first output whose target reaches X (Q_N P_k >= X D) is k0 or k0 + 1
-// with k0 = floor(X D / (Q_N 2^25)), since P_k / 2^25 lies in (k, k + 1).
+// Systematic (one u per iteration) and stratified (u_k per output) targets,
+// P_k = 2^25 k + c_k, D = N 2^25; thresholds from GridDiv.
 template <bool kStratified>
 struct GridTargets {
     static constexpr bool kActive = true;
@@ -184,12 +192,13 @@ struct GridTargets {
     uint32_t stream;
     uint32_t t;
     unsigned long long c;  // 2j + 1 (systematic)
+    GridDiv dv;
     __device__ __forceinline__ void prepare(const DevState *st) {
         t = (uint32_t)st->t;
         c = 2ull * u24(draw(key, 0u, t, TAG_RESAMPLE, stream, 0u).x) + 1ull;
     }
+    __device__ __forceinline__ void setup(unsigned long long QN) { dv.init(QN, (unsigned long long)n); }
     __device__ __forceinline__ int64_t count() const { return n; }
-    __device__ __forceinline__ unsigned long long denom() const { return (unsigned long long)n << 25; }
     __device__ __forceinline__ unsigned long long P(int64_t k) const {
         const unsigned long long ck = kStratified ? 2ull * resample_u24_at(key, stream, t, k) + 1ull : c;
         return ((unsigned long long)k << 25) + ck;
@@ -206,13 +215,31 @@ struct GridTargets {
         while (k0 > 0 && gt128(mul64((unsigned long long)k0, QN), xn)) --k0;  // k0 QN <= X N
         while (k0 < n && !gt128(mul64((unsigned long long)k0 + 1, QN), xn)) ++k0;  // X N < (k0 + 1) QN
         if (k0 >= n) return n;
-        return gt128(mul64(X, denom()), mul64(QN, P(k0))) ? k0 + 1 : k0;
+        return gt128(mul64(X, N << 25), mul64(QN, P(k0))) ? k0 + 1 : k0;
+    }
+    __device__ __forceinline__ void thresholds(int64_t k0, unsigned long long (&tau)[kScanItems]) const {
+        static_assert(kScanItems == 8, "two Philox calls per thread");
+        unsigned long long cw[kScanItems];
+        if (kStratified) {
+            const uint4 w0 = resample_words(key, stream, t, k0), w1 = resample_words(key, stream, t, k0 + 4);
+            const uint32_t ww[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j) cw[j] = 2ull * u24(ww[j]) + 1ull;
+        }
+        uint64_t u, v;
+        dv.start((uint64_t)k0, u, v);
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            if (j > 0) dv.next(u, v);
+            tau[j] = dv.tau((uint64_t)(k0 + j), kStratified ? cw[j] : c, u, v);
+        }
     }
 };
 
 // Sorted iid draws j_(0) <= ... <= j_(m-1) (multinomial selection, also the
-// residual step with m = R).  The rank of a threshold comes from the bucket
-// ends of the sort plus a scan of one (small) bucket.
+// residual step with m = R), P_k = m (2 j_(k) + 1), D = m 2^25, so
+// tau_k = floor(QN (2 j_(k) + 1) / 2^25).  The rank of a threshold comes from
+// the bucket ends of the sort plus a scan of one (small) bucket.
 struct SortedTargets {
     static constexpr bool kActive = true;
     const uint32_t *sorted;
@@ -220,15 +247,14 @@ struct SortedTargets {
     int bucket_shift;
     int64_t n_total;
     int from_residual;
-    unsigned long long m;
+    unsigned long long m, qn;
     __device__ __forceinline__ void prepare(const DevState *st) {
         const unsigned long long sd = st->sum_d;
         m = from_residual ? (sd < (unsigned long long)n_total ? (unsigned long long)n_total - sd : 0ull)
                           : (unsigned long long)n_total;
     }
+    __device__ __forceinline__ void setup(unsigned long long QN) { qn = QN; }
     __device__ __forceinline__ int64_t count() const { return (int64_t)m; }
-    __device__ __forceinline__ unsigned long long denom() const { return m << 25; }
-    __device__ __forceinline__ unsigned long long P(int64_t k) const { return m * (2ull * sorted[k] + 1ull); }
     // first k with QN m (2 s_k + 1) >= X m 2^25, i.e. 2 s_k + 1 >= X 2^25 / QN,
     // i.e. s_k >= v with v the smallest s such that 2 s + 1 >= ceil(X 2^25 / QN)
     __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long QN) const {
@@ -250,18 +276,30 @@ struct SortedTargets {
         while (lo < hi && sorted[lo] < v) ++lo;
         return lo;
     }
+    __device__ __forceinline__ void thresholds(int64_t k0, unsigned long long (&tau)[kScanItems]) const {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const unsigned long long s = (k0 + j < (int64_t)m) ? (unsigned long long)sorted[k0 + j] : 0ull;
+            const U128 p = mul64(qn, 2ull * s + 1ull);
+            tau[j] = (p.hi << 39) | (p.lo >> 25);
+        }
+    }
 };
 
-// Expansion of an offspring CDF O (O_N = N): a_k = min{i : O_i > k}.
+// Expansion of an offspring CDF O (O_N = N, so QN = D and tau_k = k):
+// a_k = min{i : O_i > k}.
 struct ExpandTargets {
     static constexpr bool kActive = true;
     int64_t n;
     __device__ __forceinline__ void prepare(const DevState *) {}
+    __device__ __forceinline__ void setup(unsigned long long) {}
     __device__ __forceinline__ int64_t count() const { return n; }
-    __device__ __forceinline__ unsigned long long denom() const { return (unsigned long long)n; }
-    __device__ __forceinline__ unsigned long long P(int64_t k) const { return (unsigned long long)k; }
     __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long) const {
         return (int64_t)min(X, (unsigned long long)n);
+    }
+    __device__ __forceinline__ void thresholds(int64_t k0, unsigned long long (&tau)[kScanItems]) const {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) tau[j] = (unsigned long long)(k0 + j);
     }
 };
 
@@ -334,6 +372,7 @@ __global__ void __launch_bounds__(kBlock) tile_reduce_kernel(Gen gen, int64_t n,
     g.prepare(sv);
     const unsigned long long s = tile_sum(g, n, blockIdx.x);
     if (threadIdx.x == 0) tsum[blockIdx.x] = s;
+    if (!total) return;  // the consumer sums the tiles itself
     if (!last_arrival(ticket, gridDim.x)) return;
     const unsigned long long tot = sum_tiles(tsum, gridDim.x);
     if (threadIdx.x == 0) {
@@ -342,33 +381,66 @@ __global__ void __launch_bounds__(kBlock) tile_reduce_kernel(Gen gen, int64_t n,
     }
 }
 
-// One tile: exclusive prefix from the tile sums before it, inclusive scan
-// of the tile's values in shared memory (optionally stored through `sink`),
-// then the ancestors of every output whose target falls in the tile's CDF
-// range.  g and tg are prepared by the caller; tsum[0] is the scan's first
-// tile.
+// Exclusive prefix (tiles before `tile`) and total of nt tile sums, by the
+// whole block in one pass; every thread receives both.
+__device__ __forceinline__ void tile_prefix_total(const unsigned long long *tsum, int tile, int nt,
+                                                  unsigned long long *pre_out, unsigned long long *tot_out) {
+    __shared__ unsigned long long s_p[kBlock / 32], s_t[kBlock / 32];
+    unsigned long long pre = 0, tot = 0;
+    for (int b = threadIdx.x; b < nt; b += kBlock) {
+        const unsigned long long v = __ldcg(&tsum[b]);
+        tot += v;
+        if (b < tile) pre += v;
+    }
+    pre = warp_sum(pre);
+    tot = warp_sum(tot);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        s_p[threadIdx.x >> 5] = pre;
+        s_t[threadIdx.x >> 5] = tot;
+    }
+    __syncthreads();
+    pre = 0;
+    tot = 0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) {
+        pre += s_p[w];
+        tot += s_t[w];
+    }
+    *pre_out = pre;
+    *tot_out = tot;
+}
+
+// The block's target set: prepared (and set up for Q_N) by one thread and
+// broadcast, so per-block constants (a Philox draw, 64-bit divisions) are
+// computed once.
+template <class Tgt>
+__device__ __forceinline__ Tgt block_targets(const Tgt &proto, const DevState *sv, unsigned long long QN) {
+    __shared__ Tgt s_tg;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Tgt t = proto;
+        t.prepare(sv);
+        t.setup(QN);
+        s_tg = t;
+    }
+    __syncthreads();
+    return s_tg;
+}
+
+// One tile: inclusive scan of the tile's values in shared memory on top of
+// the exclusive prefix `pre` (optionally stored through `sink`), then the
+// ancestors of every output whose target falls in the tile's CDF range.
+// g and tg are prepared by the caller.
 template <class Gen, class Tgt, class Out, class Sink>
 __device__ __forceinline__ void scan_select_tile(const Gen &g, const Tgt &tg, const Out &out, const Sink &sink,
-                                                 int64_t n, int tile, const unsigned long long *tsum,
+                                                 int64_t n, int tile, unsigned long long pre,
                                                  unsigned long long QN, DevState *st) {
     __shared__ unsigned long long s_q[kScanTile];
     __shared__ int32_t s_a[kScanTile];
     __shared__ unsigned long long s_w[kBlock / 32];
-    __shared__ unsigned long long s_pre;
+    __shared__ int64_t s_k[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // exclusive prefix of this tile
-    unsigned long long pre = 0;
-    for (int b = tid; b < tile; b += kBlock) pre += __ldcg(&tsum[b]);
-    pre = warp_sum(pre);
-    __syncthreads();
-    if (lane == 0) s_w[warp] = pre;
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long s = 0;
-#pragma unroll
-        for (int w = 0; w < kBlock / 32; ++w) s += s_w[w];
-        s_pre = s;
-    }
     const int64_t t0 = (int64_t)tile * kScanTile;
     const int len = (int)min((int64_t)kScanTile, n - t0);
     unsigned long long loc[kScanItems];
@@ -387,7 +459,7 @@ __device__ __forceinline__ void scan_select_tile(const Gen &g, const Tgt &tg, co
 #pragma unroll
     for (int w = 0; w < kBlock / 32; ++w)
         if (w < warp) wpre += s_w[w];
-    const unsigned long long base = s_pre + wpre + (winc - acc);
+    const unsigned long long base = pre + wpre + (winc - acc);
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) s_q[tid * kScanItems + j] = base + loc[j];
     __syncthreads();
@@ -402,44 +474,60 @@ __device__ __forceinline__ void scan_select_tile(const Gen &g, const Tgt &tg, co
         __syncthreads();
         return;
     }
-    const unsigned long long D = tg.denom();
-    const unsigned long long q_lo = s_pre, q_hi = s_q[len - 1];
-    const int64_t cnt = tg.count();
-    const int64_t k_lo = min(tg.first_at_least(q_lo, QN), cnt);
-    const int64_t k_hi = (t0 + len >= n) ? cnt : min(tg.first_at_least(q_hi, QN), cnt);
-    // outputs [k_lo, k_hi) have their ancestor in this tile; rounds of
-    // kScanTile outputs, kScanItems consecutive outputs per thread
-    for (int64_t kb = k_lo; kb < k_hi; kb += kScanTile) {
+    // outputs [k_lo, k_hi) have their ancestor in this tile
+    if (tid == 0) {
+        const int64_t cnt = tg.count();
+        s_k[0] = min(tg.first_at_least(pre, QN), cnt);
+        s_k[1] = (t0 + len >= n) ? cnt : min(tg.first_at_least(s_q[len - 1], QN), cnt);
+    }
+    __syncthreads();
+    const int64_t k_lo = s_k[0], k_hi = s_k[1];
+    // rounds of kScanTile outputs starting at a multiple of kScanItems;
+    // each thread takes kScanItems consecutive outputs: a binary search for
+    // the first, forward steps for the rest
+    for (int64_t kb = k_lo & ~(int64_t)(kScanItems - 1); kb < k_hi; kb += kScanTile) {
         const int m = (int)min((int64_t)kScanTile, k_hi - kb);
         const int j0 = tid * kScanItems;
-        int i = 0;
-        for (int j = j0; j < min(m, j0 + kScanItems); ++j) {
-            const U128 T = mul64(QN, tg.P(kb + j));
-            if (j == j0 || !gt128(mul64(s_q[i], D), T)) {
-                if (j == j0) i = 0;
-                int steps = 0;
-                while (i < len && !gt128(mul64(s_q[i], D), T) && steps < 8) {
-                    ++i;
-                    ++steps;
-                }
-                if (i < len && !gt128(mul64(s_q[i], D), T)) {  // binary search the rest
-                    int lo = i, hi = len;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (gt128(mul64(s_q[mid], D), T)) hi = mid;
-                        else lo = mid + 1;
-                    }
-                    i = lo;
-                }
+        if (j0 < m) {
+            unsigned long long tau[kScanItems];
+            tg.thresholds(kb + j0, tau);
+            int lo = 0, hi = len;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_q[mid] > tau[0]) hi = mid;
+                else lo = mid + 1;
             }
-            s_a[j] = (int32_t)(t0 + min(i, len - 1));
+            int i = lo;
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j) {
+                if (j > 0) {
+                    int steps = 0;
+                    while (i < len && s_q[i] <= tau[j] && steps < 16) {
+                        ++i;
+                        ++steps;
+                    }
+                    if (i < len && s_q[i] <= tau[j]) {
+                        int l2 = i, h2 = len;
+                        while (l2 < h2) {
+                            const int mid = (l2 + h2) >> 1;
+                            if (s_q[mid] > tau[j]) h2 = mid;
+                            else l2 = mid + 1;
+                        }
+                        i = l2;
+                    }
+                }
+                if (j0 + j < m) s_a[j0 + j] = (int32_t)(t0 + min(i, len - 1));
+            }
         }
         __syncthreads();
-        for (int j = tid; j < m; j += kBlock) out(kb + j, s_a[j]);
+        for (int j = tid; j < m; j += kBlock)
+            if (kb + j >= k_lo) out(kb + j, s_a[j]);
         __syncthreads();
     }
 }
 
+// Scan (+ selection) pass: one block per tile.  Q_N is the exact total of
+// the tile sums (every block sums them), or a given total.
 template <class Gen, class Tgt, class Out, class Sink>
 __global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, Out out, Sink sink, int64_t n,
                                                              const unsigned long long *tsum,
@@ -450,13 +538,11 @@ __global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, O
     if (set_ready && blockIdx.x == 0 && threadIdx.x == 0) st->ready = 1;
     Gen g = gen;
     g.prepare(sv);
-    Tgt tg = tgt;
-    tg.prepare(sv);
-    __shared__ unsigned long long s_qn;
-    if (threadIdx.x == 0) s_qn = __ldcg(total);
-    __syncthreads();
-    const unsigned long long QN = s_qn;
-    scan_select_tile(g, tg, out, sink, n, blockIdx.x, tsum, QN, st);
+    unsigned long long pre, QN;
+    tile_prefix_total(tsum, blockIdx.x, gridDim.x, &pre, &QN);
+    if (total) QN = __ldcg(total);
+    const Tgt tg = block_targets(tgt, sv, QN);
+    scan_select_tile(g, tg, out, sink, n, blockIdx.x, pre, QN, st);
 }
 
 // ------------------------------------------------- sorting iid uniforms --

@@ -192,6 +192,8 @@ __global__ void reset_state_kernel(DevState *st) {
     st->count_r = 0;
     st->max_lw = 0;
     st->log_norm = 0;
+    st->max_lw_f = 0;
+    st->log_norm_f[0] = st->log_norm_f[1] = 0;
     st->log_evidence = 0;
     st->ess = 0;
     st->alpha = 0;
@@ -200,6 +202,15 @@ __global__ void reset_state_kernel(DevState *st) {
     st->qn = 0;
     st->sum_d = 0;
     for (int i = 0; i < 4; ++i) st->accept[i] = 0;
+}
+
+// the resampling threshold for the FP32 finalize: a DF value and a mode
+// (always at >= 1, never at <= 0, otherwise compare ESS < threshold N)
+template <typename R>
+void set_threshold_df(PfArgs<R> &a, double thr) {
+    a.thr_mode = thr >= 1.0 ? 1 : (thr <= 0.0 ? 2 : 0);
+    a.thr_df[0] = (float)thr;
+    a.thr_df[1] = (float)(thr - (double)a.thr_df[0]);
 }
 
 // observation-density constants of the constant-velocity model
@@ -234,6 +245,7 @@ PfArgs<R> pf_args(smc_ctx *c) {
     a.part = c->part;
     a.log_n = std::log((double)n);
     a.threshold = g.threshold;
+    set_threshold_df(a, g.threshold);
     a.delta = R(g.cv.delta);
     a.sd_pos = R(g.cv.sd_pos);
     a.sd_vel = R(g.cv.sd_vel);
@@ -254,12 +266,14 @@ int launch_pf(smc_ctx *c) {
 
 unsigned long long *tsum_of(smc_ctx *c, int slot) { return c->tsum + (size_t)slot * c->L.ntiles_status; }
 
-// tile-sum pass: tsum[slot][tile], exact total -> st->scan_total[slot]
+// tile-sum pass: tsum[slot][tile]; with want_total the exact total also goes
+// to st->scan_total[slot] (otherwise the scan pass sums the tiles itself)
 template <class Gen>
-int launch_reduce(smc_ctx *c, Gen g, int64_t n, int slot, int gate) {
+int launch_reduce(smc_ctx *c, Gen g, int64_t n, int slot, int gate, bool want_total = false) {
     const unsigned grid = (unsigned)((n + kScanTile - 1) / kScanTile);
-    tile_reduce_kernel<Gen><<<grid, kBlock, 0, c->stream>>>(g, n, tsum_of(c, slot), &c->st->scan_total[slot],
-                                                             &c->st->scan_ticket[slot], c->st, gate);
+    tile_reduce_kernel<Gen><<<grid, kBlock, 0, c->stream>>>(
+        g, n, tsum_of(c, slot), want_total ? &c->st->scan_total[slot] : nullptr, &c->st->scan_ticket[slot], c->st,
+        gate);
     return cuda_check(cudaGetLastError());
 }
 
@@ -267,8 +281,8 @@ int launch_reduce(smc_ctx *c, Gen g, int64_t n, int slot, int gate) {
 template <class Gen, class Tgt, class Out, class Sink>
 int launch_scan_select(smc_ctx *c, Gen g, Tgt tg, Out o, Sink sk, int64_t n, int slot, int gate, int set_ready) {
     const unsigned grid = (unsigned)((n + kScanTile - 1) / kScanTile);
-    scan_select_kernel<Gen, Tgt, Out, Sink><<<grid, kBlock, 0, c->stream>>>(
-        g, tg, o, sk, n, tsum_of(c, slot), &c->st->scan_total[slot], c->st, gate, set_ready);
+    scan_select_kernel<Gen, Tgt, Out, Sink><<<grid, kBlock, 0, c->stream>>>(g, tg, o, sk, n, tsum_of(c, slot), nullptr,
+                                                                            c->st, gate, set_ready);
     return cuda_check(cudaGetLastError());
 }
 
@@ -346,7 +360,8 @@ int launch_resample(smc_ctx *c, int gate) {
         case SMC_RESIDUAL: {
             if (keep && (rc = launch_scan_select(c, qg, NoTargets{}, AncOut{nullptr}, qsink, n, SLOT_CDF, gate, 0)))
                 return rc;
-            // Q_N for the residual generators
+            // Q_N for the residual generators (the tile-sum pass again, with its total)
+            if ((rc = launch_reduce(c, qg, n, SLOT_CDF, gate, true))) return rc;
             if ((rc = cuda_check(cudaMemcpyAsync(&c->st->qn, &c->st->scan_total[SLOT_CDF], 8,
                                                  cudaMemcpyDeviceToDevice, c->stream))))
                 return rc;
@@ -357,13 +372,13 @@ int launch_resample(smc_ctx *c, int gate) {
             residual_d_kernel<R><<<gt, kBlock, 0, c->stream>>>(p, c->extra, c->st, gate);
             if ((rc = cuda_check(cudaGetLastError()))) return rc;
             ResidualRGen<R> rg{p, 0};
-            if ((rc = launch_reduce(c, rg, n, SLOT_RES_R, gate))) return rc;
+            if ((rc = launch_reduce(c, rg, n, SLOT_RES_R, gate, true))) return rc;
             if ((rc = launch_uniform_sort(c, 1, gate))) return rc;
             if ((rc = launch_scan_select(c, rg, sorted_targets(c, 1), CountOut{c->extra}, NoSink{}, n, SLOT_RES_R,
                                          gate, 0)))
                 return rc;
             ResidualOGen<R> og{p, c->extra};
-            if ((rc = launch_reduce(c, og, n, SLOT_RES_O, gate))) return rc;
+            if ((rc = launch_reduce(c, og, n, SLOT_RES_O, gate, true))) return rc;
             return launch_scan_select(c, og, ExpandTargets{n}, AncOut{c->anc}, NoSink{}, n, SLOT_RES_O, gate, 1);
         }
     }
@@ -1104,6 +1119,7 @@ BatchArgs<R> batch_args(smc_batch *bt) {
     std::memset(&a, 0, sizeof(a));
     const smc_config &g = bt->cfg;
     a.threshold = g.threshold;
+    set_threshold_df(a, g.threshold);
     a.delta = R(g.cv.delta);
     a.sd_pos = R(g.cv.sd_pos);
     a.sd_vel = R(g.cv.sd_vel);
@@ -1587,3 +1603,4 @@ int smc_read_ancestor_history(smc_ctx *c, int32_t t, int32_t *dst, int on_device
 }
 
 }  // extern "C"
+

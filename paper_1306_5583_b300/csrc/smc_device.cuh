@@ -62,8 +62,18 @@ struct Math<float> {
     static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
     static __device__ __forceinline__ void sincospi(float x, float *s, float *c) { sincospif(x, s, c); }
     static __device__ __forceinline__ uint64_t fixed(float e, int frac) {
-        // floor(e 2^frac) for e in [0, 1]; NaN and negatives map to 0
-        return (e > 0.0f) ? __float2ull_rz(ldexpf(e, frac)) : 0ull;
+        // floor(e 2^frac) for e in [0, 1] (frac <= 61); NaN and negatives map
+        // to 0.  Integer bit arithmetic on the float's fields: the value is
+        // mant 2^(ex - 150), shifted by frac; no float-to-64-bit conversion
+        // (that runs on the slow FP64 pipe).
+        if (!(e > 0.0f)) return 0ull;
+        const uint32_t bits = __float_as_uint(e);
+        const int ex = (int)(bits >> 23);
+        const uint64_t mant = (uint64_t)((bits & 0x7FFFFFu) | 0x800000u);
+        const int sh = ex - 150 + frac;
+        if (ex == 0) return 0ull;  // subnormal: below 2^-126, floor is 0 for frac <= 61
+        if (sh >= 0) return mant << sh;
+        return sh > -32 ? (mant >> (-sh)) : 0ull;
     }
     static __device__ __forceinline__ float neg_inf() { return -__int_as_float(0x7f800000); }
 };
@@ -213,6 +223,13 @@ __device__ __forceinline__ U128 mul64(uint64_t a, uint64_t b) { return U128{__um
 
 // a > b
 __device__ __forceinline__ bool gt128(U128 a, U128 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+
+__device__ __forceinline__ U128 add128(U128 a, U128 b) {
+    U128 r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+    return r;
+}
 
 // bit length of a 128-bit value
 __device__ __forceinline__ int bitlen128(U128 a) {

@@ -56,6 +56,9 @@ struct DevState {
     uint32_t accept[4];                 // GMM accepted moves per block and Langevin (last mcmc)
     int32_t gathered;                   // GMM: the last mcmc gathered by ancestors
     int32_t pad2;
+    float log_norm_f[2];  // L_t as an unevaluated float sum hi + lo (FP32 kernels)
+    float max_lw_f;       // M_t as float (exact: the maximum of float log-weights)
+    float pad3;
 };
 
 struct Partial {  // one per block of a weighting kernel

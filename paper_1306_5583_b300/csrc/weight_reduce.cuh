@@ -5,6 +5,7 @@
 // normalising constants; Sec. 4.1.5 Monitor; Sec. 4.1.3 threshold).
 #pragma once
 
+#include "df_math.h"
 #include "smc_device.cuh"
 
 namespace smc {
@@ -15,8 +16,23 @@ template <typename R>
 struct Shift {
     R hi, lo;
     __device__ __forceinline__ explicit Shift(double v) : hi(R(v)), lo(R(v - double(R(v)))) {}
+    __device__ __forceinline__ Shift(R h, R l) : hi(h), lo(l) {}
     __device__ __forceinline__ R sub_from(R x) const { return (x - hi) - lo; }
 };
+
+// The split of L_t kept in the state block (written once by the finalising
+// thread), so per-thread code does no float64 arithmetic or conversion.
+template <typename R>
+__device__ __forceinline__ Shift<R> log_norm_shift(const DevState *sv) {
+    if constexpr (sizeof(R) == 4) return Shift<R>(sv->log_norm_f[0], sv->log_norm_f[1]);
+    else return Shift<R>(R(sv->log_norm), R(0));
+}
+
+// float split of a float64 value: hi + lo with hi = float(v)
+__device__ __forceinline__ void split_float(double v, float *out) {
+    out[0] = float(v);
+    out[1] = float(v - double(out[0]));
+}
 
 // What the last block does with the combined sums.
 struct FinalizeArgs {
@@ -28,39 +44,15 @@ struct FinalizeArgs {
     int64_t n;
     double threshold;
     double alpha;         // GMM alpha_t (recorded)
+    float thr_df[2];      // FP32 path: the threshold as a DF value
+    int32_t thr_mode;     // FP32 path: 0 compare ESS < threshold N, 1 always, 2 never
+    double log_evidence_prev;  // FP32 path, mode 0: log Z_{t-1} from the kernel's state snapshot
 };
 
-// ---- compensated float ("double-float") sums ------------------------------
-// FP64 runs at 1/64 of the FP32 rate on B300, so the FP32 path keeps its
-// reductions on the FP32 pipe with error-free transformations (Knuth's
-// TwoSum, Dekker's FastTwoSum, FMA-based TwoProduct) and converts to float64
-// only for the final scalars.
-struct DF {
-    float hi, lo;
-};
-__device__ __forceinline__ DF fast_two_sum(float a, float b) {
-    const float s = a + b;
-    return DF{s, b - (s - a)};
-}
-__device__ __forceinline__ DF two_sum(float a, float b) {
-    const float s = a + b;
-    const float bp = s - a;
-    return DF{s, (a - (s - bp)) + (b - bp)};
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    const DF s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, s.lo + a.lo + b.lo);
-}
-__device__ __forceinline__ DF df_mul(DF a, float b) {
-    const float p = a.hi * b;
-    float e = fmaf(a.hi, b, -p);
-    e = fmaf(a.lo, b, e);
-    return fast_two_sum(p, e);
-}
+// ---- compensated float ("double-float") sums: see df_math.h ---------------
 __device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
     return DF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
-__device__ __forceinline__ double df_to_double(DF a) { return double(a.hi) + double(a.lo); }
 
 // Per-block partial (max, sum e, sum e^2, sum e h0, sum e h1, sum e h2) with
 // e = exp(lw - max): float64 fields for the FP64 path, (hi, lo) float pairs
@@ -145,14 +137,19 @@ __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E]
             for (int w = 0; w < kBlock / 32; ++w)
                 for (int q = 0; q < 5; ++q) t[q] += s_sum[w][q];
             PartialIO<double>::store(out, double(m), t);
-        } else {
+        }
+    }
+    if constexpr (sizeof(R) == 4) {
+        // warp 0 adds the per-warp sums in compensated float (fixed tree)
+        if (warp == 0) {
             DF t[5];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) t[q] = DF{float(s_sum[0][q]), 0.0f};
-            for (int w = 1; w < kBlock / 32; ++w)
+            for (int q = 0; q < 5; ++q) t[q] = DF{lane < kBlock / 32 ? float(s_sum[lane][q]) : 0.0f, 0.0f};
 #pragma unroll
-                for (int q = 0; q < 5; ++q) t[q] = df_add(t[q], DF{float(s_sum[w][q]), 0.0f});
-            PartialIO<float>::store(out, float(m), t);
+            for (int o = (kBlock / 32) / 2; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) t[q] = df_add(t[q], df_shfl_xor(t[q], o));
+            if (lane == 0) PartialIO<float>::store(out, float(m), t);
         }
     }
 }
@@ -186,6 +183,104 @@ __device__ __forceinline__ bool last_arrival(uint32_t *counter, uint32_t count) 
 template <typename R>
 __device__ __forceinline__ bool take_ticket(DevState *st) {
     return last_arrival(&st->ticket, gridDim.x);
+}
+
+// FP32 path: grid-wide sums of nb block partials in compensated float, by
+// the whole calling block (every thread receives the result).  Each thread
+// fetches its partials (b = tid + r kBlock) with 16-byte loads in one round
+// trip when nb <= 4 kBlock, the block maximum rescales them, and fixed
+// shuffle trees add them, so the result does not depend on arrival order.
+struct CombinedDF {
+    float M;
+    DF S[5];
+};
+
+// PT: partials fetched per thread in the single round trip (registers); the
+// result does not depend on PT.
+template <int PT = 4>
+__device__ __forceinline__ void combine_partials_df(const Partial *part, int nb, CombinedDF *out) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ float s_m[kBlock / 32];
+    __shared__ DF s_df[kBlock / 32][5];
+    __shared__ CombinedDF s_out;
+    const bool one_pass = nb <= PT * kBlock;
+    float pv[PT][12];
+    float M = -INFINITY;
+    if (one_pass) {
+#pragma unroll
+        for (int r = 0; r < PT; ++r) {
+            const int b = r * kBlock + tid;
+            if (b < nb) {
+                const float4 *src = reinterpret_cast<const float4 *>(&part[b]);
+                const float4 v0 = __ldcg(src), v1 = __ldcg(src + 1), v2 = __ldcg(src + 2);
+                pv[r][0] = v0.x; pv[r][1] = v0.y; pv[r][2] = v0.z; pv[r][3] = v0.w;
+                pv[r][4] = v1.x; pv[r][5] = v1.y; pv[r][6] = v1.z; pv[r][7] = v1.w;
+                pv[r][8] = v2.x; pv[r][9] = v2.y; pv[r][10] = v2.z; pv[r][11] = v2.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 12; ++k) pv[r][k] = 0.0f;
+                pv[r][0] = -INFINITY;
+            }
+            M = fmaxf(M, pv[r][0]);
+        }
+    } else {
+        for (int b = tid; b < nb; b += kBlock) M = fmaxf(M, PartialIO<float>::m(&part[b]));
+    }
+    M = warp_maxf(M);
+    if (lane == 0) s_m[warp] = M;
+    __syncthreads();
+    M = s_m[0];
+#pragma unroll
+    for (int w = 1; w < kBlock / 32; ++w) M = fmaxf(M, s_m[w]);
+    DF S[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) S[q] = DF{0.0f, 0.0f};
+    if (M > -INFINITY) {
+        if (one_pass) {
+#pragma unroll
+            for (int r = 0; r < PT; ++r) {
+                const float mb = pv[r][0];
+                const float sc = (mb > -INFINITY) ? expf(mb - M) : 0.0f;
+                S[0] = df_add(S[0], df_mul_f(DF{pv[r][1], pv[r][2]}, sc));
+                S[1] = df_add(S[1], df_mul_f(df_mul_f(DF{pv[r][3], pv[r][4]}, sc), sc));
+#pragma unroll
+                for (int q = 2; q < 5; ++q) S[q] = df_add(S[q], df_mul_f(DF{pv[r][1 + 2 * q], pv[r][2 + 2 * q]}, sc));
+            }
+        } else {
+            for (int b = tid; b < nb; b += kBlock) {
+                const float mb = PartialIO<float>::m(&part[b]);
+                const float sc = (mb > -INFINITY) ? expf(mb - M) : 0.0f;
+                S[0] = df_add(S[0], df_mul_f(PartialIO<float>::s(&part[b], 0), sc));
+                S[1] = df_add(S[1], df_mul_f(df_mul_f(PartialIO<float>::s(&part[b], 1), sc), sc));
+#pragma unroll
+                for (int q = 2; q < 5; ++q) S[q] = df_add(S[q], df_mul_f(PartialIO<float>::s(&part[b], q), sc));
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) S[q] = df_add(S[q], df_shfl_xor(S[q], o));
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) s_df[warp][q] = S[q];
+    __syncthreads();
+    if (warp == 0) {
+        DF T[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) T[q] = lane < kBlock / 32 ? s_df[lane][q] : DF{0.0f, 0.0f};
+#pragma unroll
+        for (int o = (kBlock / 32) / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) T[q] = df_add(T[q], df_shfl_xor(T[q], o));
+        if (lane == 0) {
+            s_out.M = M;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) s_out.S[q] = T[q];
+        }
+    }
+    __syncthreads();
+    *out = s_out;
 }
 
 // Grid-wide sums of nb block partials, by the whole calling block (thread 0
@@ -232,46 +327,11 @@ __device__ __forceinline__ void combine_partials(const Partial *part, int nb, Co
             *out = c;
         }
     } else {
-        __shared__ float s_m[kBlock / 32];
-        __shared__ DF s_df[kBlock / 32][5];
-        float M = -INFINITY;
-        for (int b = threadIdx.x; b < nb; b += kBlock) M = fmaxf(M, PartialIO<float>::m(&part[b]));
-        M = warp_maxf(M);
-        if (lane == 0) s_m[warp] = M;
-        __syncthreads();
-        M = s_m[0];
-        for (int w = 1; w < kBlock / 32; ++w) M = fmaxf(M, s_m[w]);
-        DF S[5];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) S[q] = DF{0.0f, 0.0f};
-        if (M > -INFINITY) {
-            for (int b = threadIdx.x; b < nb; b += kBlock) {
-                const float mb = PartialIO<float>::m(&part[b]);
-                const float sc = (mb > -INFINITY) ? expf(mb - M) : 0.0f;
-                S[0] = df_add(S[0], df_mul(PartialIO<float>::s(&part[b], 0), sc));
-                S[1] = df_add(S[1], df_mul(df_mul(PartialIO<float>::s(&part[b], 1), sc), sc));
-#pragma unroll
-                for (int q = 2; q < 5; ++q) S[q] = df_add(S[q], df_mul(PartialIO<float>::s(&part[b], q), sc));
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) S[q] = df_add(S[q], df_shfl_xor(S[q], o));
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) s_df[warp][q] = S[q];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            DF T[5];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) T[q] = s_df[0][q];
-            for (int w = 1; w < kBlock / 32; ++w)
-#pragma unroll
-                for (int q = 0; q < 5; ++q) T[q] = df_add(T[q], s_df[w][q]);
-            *out = Combined{double(M), df_to_double(T[0]), df_to_double(T[1]), df_to_double(T[2]),
-                            df_to_double(T[3]), df_to_double(T[4])};
-        }
+        CombinedDF d;
+        combine_partials_df<4>(part, nb, &d);
+        if (threadIdx.x == 0)
+            *out = Combined{df_to_double(DF{d.M, 0.0f}), df_to_double(d.S[0]), df_to_double(d.S[1]),
+                            df_to_double(d.S[2]), df_to_double(d.S[3]), df_to_double(d.S[4])};
     }
     __syncthreads();
 }
@@ -322,11 +382,61 @@ __device__ __forceinline__ bool finalize_weights(const FinalizeArgs &f, const Co
     r->status = SMC_OK;
     r->alpha = f.alpha;
     st->max_lw = c.M;
+    st->max_lw_f = float(c.M);
     st->log_norm = L;
+    split_float(L, st->log_norm_f);
     st->log_evidence = logz;
     st->ess = ess;
     st->due = due ? 1 : 0;
     *L_out = L;
+    return true;
+}
+
+// FP32 path of finalize_weights: the same record and state updates with the
+// per-iteration scalars in compensated float (no float64 logarithm or
+// division); doubles only for the stored values (bit-pattern conversions and
+// the float64 evidence sum).
+__device__ __forceinline__ bool finalize_weights_df(const FinalizeArgs &f, const CombinedDF &c) {
+    DevState *st = f.st;
+    smc_record *r = &f.rec[f.t % f.rec_cap];
+    const DF S1 = c.S[0], S2 = c.S[1];
+    const bool ok = (c.M > -INFINITY) && (c.M < INFINITY) && (S1.hi > 0.0f) && (S1.hi < INFINITY) &&
+                    (S2.hi > 0.0f);
+    st->ticket = 0;
+    if (!ok) {
+        r->t = f.t;
+        r->status = SMC_E_NONFINITE;
+        raise_error(st, SMC_E_NONFINITE);
+        return false;
+    }
+    const DF L = df_add_f(df_log(S1), c.M);
+    const DF ess = df_div(df_mul(S1, S1), S2);
+    const bool due = f.thr_mode == 1 ? true
+                     : f.thr_mode == 2 ? false
+                                       : df_lt(ess, df_mul(DF{f.thr_df[0], f.thr_df[1]}, df_from_int(f.n)));
+    const double Ld = df_to_double(L);
+    const double prev_logz = (f.mode == 0) ? (f.t == 0 ? 0.0 : f.log_evidence_prev) : st->log_evidence - st->log_norm;
+    const double logz = prev_logz + Ld;
+    const double essd = df_to_double(ess);
+    const double Md = df_to_double(DF{c.M, 0.0f});
+    r->log_norm = Ld;
+    r->log_evidence = logz;
+    r->ess = essd;
+    r->mean[0] = df_to_double(df_div(c.S[2], S1));
+    r->mean[1] = df_to_double(df_div(c.S[3], S1));
+    r->max_lw = Md;
+    r->t = f.t;
+    r->resampled = due ? 1 : 0;
+    r->status = SMC_OK;
+    r->alpha = f.alpha;
+    st->max_lw = Md;
+    st->max_lw_f = c.M;
+    st->log_norm = Ld;
+    st->log_norm_f[0] = L.hi;
+    st->log_norm_f[1] = L.lo;
+    st->log_evidence = logz;
+    st->ess = essd;
+    st->due = due ? 1 : 0;
     return true;
 }
 
