@@ -300,6 +300,27 @@ int smc_batch_read_state(smc_batch *b, int32_t filter, void *dst, int on_device)
 int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], uint32_t *d_out, int64_t n,
                       void *cuda_stream);
 
+/* Systematic resampling straight from N float32 log-weights (device) into N
+ * int32 ancestors (device), for callers that cannot allocate device memory:
+ * code running inside a region that a framework's allocator owns, a loop
+ * that must not pay cudaMalloc's implicit synchronisation, or a deployment
+ * with a fixed memory budget.  The paper has no counterpart; it is an
+ * allocation-free variant of the resampling step of this library.
+ * The result equals smc_resample's for a context with the same seed,
+ * stream_id and iteration t whose current log-weights are d_log_weight
+ * (ancestors sorted, the copy_from convention of the context API).
+ * Scratch: one fixed array inside the library, about 17 KB on every GPU that
+ * loads it, kept until the process exits; N above 2^22 is rejected with
+ * SMC_E_ARG.  The first call on each device looks up the array's device
+ * address; make that first call outside any CUDA graph capture.  Every call
+ * on a device shares the array and leaves its contents behind (each call
+ * clears what it needs first), so calls that overlap on the GPU (other
+ * streams, other threads) race: serialise them.  d_log_weight must be
+ * 16-byte aligned.  Asynchronous on cuda_stream; a log-weight maximum that is
+ * not finite makes the call write nothing. */
+int smc_resample_systematic_noalloc(const float *d_log_weight, int64_t n, uint64_t seed, uint32_t stream_id,
+                                    int32_t t, int32_t *d_ancestors, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1604,3 +1604,105 @@ int smc_read_ancestor_history(smc_ctx *c, int32_t t, int32_t *dst, int on_device
 
 }  // extern "C"
 
+// ========================================= resampling without allocation ==
+//
+// smc_resample_systematic_noalloc: systematic ancestors straight from a
+// caller's log-weights, for callers that must not allocate device memory.
+// Its scratch (a state block for the kernels, the per-tile sums of the
+// fixed-point weights, the running maximum) is one file-scope device array
+// of fixed size, so the entry point calls no allocator; the price is a size
+// limit and one shared scratch area per device.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 22;                    // particles per call
+constexpr int kNoAllocMaxTiles = (int)(kNoAllocMaxN / kScanTile);     // 2048 scan tiles
+struct NoAllocScratch {
+    DevState st;
+    unsigned long long tsum[kNoAllocMaxTiles];
+    int max_key;
+};
+// every GPU that loads the library holds this array (about 17 KB) until exit
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+NoAllocScratch *g_noalloc_ptr[64] = {};  // device address of the array, per device
+
+// one-time set-up on the current device: the array's device address (in
+// host code its name is only a host-side stand-in)
+int noalloc_scratch(NoAllocScratch **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SMC_E_CUDA;
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SMC_E_CUDA;
+        g_noalloc_ptr[dev] = static_cast<NoAllocScratch *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return SMC_OK;
+}
+
+// float keys that order like the floats (for an integer atomicMax)
+__device__ __forceinline__ int float_key(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float key_float(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
+// clear the shared scratch for this call: state block and running maximum
+__global__ void noalloc_clear_kernel(NoAllocScratch *s, int32_t t) {
+    DevState *st = &s->st;
+    const int W = (int)(sizeof(DevState) / 4);
+    for (int i = threadIdx.x; i < W; i += blockDim.x) reinterpret_cast<uint32_t *>(st)[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->t = t;
+        st->due = 1;
+        s->max_key = float_key(-INFINITY);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) noalloc_max_kernel(const float *lw, int64_t n, NoAllocScratch *s) {
+    float m = -INFINITY;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
+        m = fmaxf(m, lw[i]);
+    m = warp_maxf(m);
+    if ((threadIdx.x & 31) == 0) atomicMax(&s->max_key, float_key(m));
+}
+
+__global__ void noalloc_set_max_kernel(NoAllocScratch *s) {
+    const float m = key_float(s->max_key);
+    s->st.max_lw = (double)m;
+    s->st.max_lw_f = m;
+    if (!(m > -INFINITY) || !(m < INFINITY)) s->st.error = SMC_E_NONFINITE;
+}
+
+}  // namespace
+
+extern "C" int smc_resample_systematic_noalloc(const float *d_log_weight, int64_t n, uint64_t seed, uint32_t stream_id,
+                                               int32_t t, int32_t *d_ancestors, void *cuda_stream) {
+    if (!d_log_weight || !d_ancestors || n < 1 || t < 0) return SMC_E_ARG;
+    if (n > kNoAllocMaxN) return SMC_E_ARG;  // beyond the fixed scratch
+    if (((uintptr_t)d_log_weight & 15) || ((uintptr_t)d_ancestors & 3)) return SMC_E_ARG;
+    NoAllocScratch *s = nullptr;
+    int rc = noalloc_scratch(&s);
+    if (rc) return rc;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    DevState *st = &s->st;
+    const unsigned tiles = (unsigned)((n + kScanTile - 1) / kScanTile);
+    noalloc_clear_kernel<<<1, kBlock, 0, stream>>>(s, t);
+    noalloc_max_kernel<<<std::min<unsigned>(tiles * 4, 1184u), kBlock, 0, stream>>>(d_log_weight, n, s);
+    noalloc_set_max_kernel<<<1, 1, 0, stream>>>(s);
+    if ((rc = cuda_check(cudaGetLastError()))) return rc;
+    QGen<float> qg;
+    qg.lw[0] = qg.lw[1] = d_log_weight;
+    qg.frac = 61 - ceil_log2(n);
+    qg.cur_lw = nullptr;
+    qg.m = 0;
+    const uint2 key = make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    tile_reduce_kernel<QGen<float>><<<tiles, kBlock, 0, stream>>>(qg, n, s->tsum, nullptr, &st->scan_ticket[SLOT_CDF],
+                                                                   st, 1);
+    scan_select_kernel<QGen<float>, GridTargets<false>, AncOut, NoSink><<<tiles, kBlock, 0, stream>>>(
+        qg, GridTargets<false>{n, key, stream_id, 0, 0}, AncOut{d_ancestors}, NoSink{}, n, s->tsum, nullptr, st, 1,
+        0);
+    return cuda_check(cudaGetLastError());
+}

@@ -87,6 +87,8 @@ _SIGS = {
     "smc_pf_grad": (_I, [_P, _P]),
     "smc_pf_replay": (_I, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
     "smc_read_ancestor_history": (_I, [_P, ctypes.c_int32, _P, _I]),
+    "smc_resample_systematic_noalloc": (_I, [_P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32,
+                                             _P, _P]),
     "smc_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), _P, _P, ctypes.c_int32]),
     "smc_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Config), _P, _P, ctypes.c_int32, _P,
                               ctypes.c_size_t, _P]),
