@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kBlock, 3) batch_pf_kernel(BatchArgs<R> B) {
         const int cur = sv->cur, cur_lw = sv->cur_lw;
         const bool gather = (t > 0) && (sv->ready != 0);
         const int nblk = B.tfirst[b + 1] - B.tfirst[b];
-        pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, log_norm_shift<R>(sv));
+        pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part);
         if (last_arrival(&st->ticket, (uint32_t)nblk)) pf_finalize<R, 1>(a, st, sv, nblk, t, cur, cur_lw);
     }
     if (last_arrival(&B.bs->ticket, gridDim.x) && threadIdx.x == 0) {
@@ -145,7 +145,9 @@ __device__ __forceinline__ void batch_select_tile(const BatchArgs<R> &B, int til
     proto.key = B.proto.key;
     proto.stream = B.stream_of[b];
     const GridTargets<kStratified> tg = block_targets(proto, sv, QN);
-    scan_select_tile(g, tg, AncOut{B.anc + B.off[b]}, NoSink{}, B.n[b], lt, pre, QN, st);
+    __shared__ TileBufs tb;
+    const unsigned long long ts = scan_tile_local(g, B.n[b], lt, tb);
+    select_tile(tg, AncOut{B.anc + B.off[b]}, NoSink{}, B.n[b], lt, pre, ts, QN, st, tb);
 }
 
 template <typename R, bool kStratified>

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kBlock) pf_replay_kernel(PfArgs<R> a, int32_t 
         s_lprev[1] = R(lp - double(s_lprev[0]));
     }
     __syncthreads();
-    pf_tile<R>(a, blockIdx.x, t, 0, 0, gather != 0, Shift<R>(s_lprev[0], s_lprev[1]));
+    pf_tile<R>(a, blockIdx.x, t, 0, 0, gather != 0, Shift<R>(s_lprev[0], s_lprev[1]), a.part);
     if (!last_arrival(ticket, gridDim.x)) return;
     // L_t as the forward kernels compute it (compensated float on the FP32 path)
     double L;

@@ -11,7 +11,8 @@
 //     tau_k = k a + H + u + floor((2^25 v + L N + c_k b) / (N 2^25)),
 // and the last numerator is below 3 N 2^25, so that term is 0, 1 or 2.
 // (u, v) advance from k to k + 1 by one addition of b and at most one
-// carry.  Bounds: N < 2^31, Q_N < 2^62.
+// carry; for a fixed c_k (systematic) tau itself advances with a remainder
+// modulo D.  Bounds: N < 2^31, Q_N < 2^62.
 #pragma once
 
 #include <cstdint>
@@ -64,15 +65,27 @@ struct GridDiv {
             ++u;
         }
     }
-    // tau_k from (u, v) of k and c_k
-    SMC_HD uint64_t tau(uint64_t k, uint64_t c, uint64_t u, uint64_t v) const {
+    // tau_k from (u, v) of k and c_k; *rem = Q_N P_k - tau_k D (in [0, D))
+    SMC_HD uint64_t tau(uint64_t k, uint64_t c, uint64_t u, uint64_t v, uint64_t *rem = nullptr) const {
         const uint64_t alc = al * c;               // < 2^50
         const uint64_t H = ah * c + (alc >> 25);   // floor(a c / 2^25)
         const uint64_t L = alc & ((1ull << 25) - 1);
         const uint64_t D = n << 25;
         const uint64_t X = (v << 25) + L * n + c * b;  // < 3 D
         const uint64_t r = (X >= D ? 1ull : 0ull) + (X >= 2 * D ? 1ull : 0ull);
+        if (rem) *rem = X - r * D;
         return k * a + H + u + r;
+    }
+    // Systematic targets (c fixed): Q_N P_{k+1} = Q_N P_k + a D + b 2^25, so
+    // (tau, rem) advance by a and b 2^25 with at most one carry (b 2^25 < D).
+    SMC_HD void advance(uint64_t &t, uint64_t &rem) const {
+        const uint64_t D = n << 25;
+        t += a;
+        rem += b << 25;
+        if (rem >= D) {
+            rem -= D;
+            ++t;
+        }
     }
 };
 

@@ -58,7 +58,7 @@ __device__ __forceinline__ R cv_loglik(const PfArgs<R> &a, R yx, R yy, R px, R p
 // the memory system sees all of a thread's requests at once.
 template <typename R>
 __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_t t, int cur, int cur_lw,
-                                        bool gather, Shift<R> Lprev) {
+                                        bool gather, Shift<R> Lprev, Partial *part) {
     constexpr int E = kPfItems;
     const uint32_t n = (uint32_t)a.n;
     const uint32_t i0 = (blk * (uint32_t)kBlock + threadIdx.x) * (uint32_t)E;
@@ -77,10 +77,10 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 const uint32_t sidx = (i0 + j < n) ? (uint32_t)src[j] : 0u;
-                v0[j] = __ldg(xs0 + sidx);
-                v1[j] = __ldg(xs1 + sidx);
-                v2[j] = __ldg(xs2 + sidx);
-                v3[j] = __ldg(xs3 + sidx);
+                v0[j] = __ldcg(xs0 + sidx);
+                v1[j] = __ldcg(xs1 + sidx);
+                v2[j] = __ldcg(xs2 + sidx);
+                v3[j] = __ldcg(xs3 + sidx);
             }
         } else {
             load_k<R, E>(xs0, i0, n, v0);
@@ -126,7 +126,7 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
     store_k<R, E>(xd2, i0, n, s2);
     store_k<R, E>(xd3, i0, n, s3);
     store_k<R, E>(lwd, i0, n, lwv);
-    block_partial<R, E, 2>(lwv, s0, s1, zero, &a.part[blk]);
+    block_partial<R, E, 2>(lwv, s0, s1, zero, &part[blk]);
 }
 
 // Last tile of a filter: combine its nblk partials, write the record of
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kBlock, 4) pf_iterate_kernel(PfArgs<R> a) {
     const int32_t t = sv->t + 1;
     const int cur = sv->cur, cur_lw = sv->cur_lw;
     const bool gather = (t > 0) && (sv->ready != 0);
-    pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, log_norm_shift<R>(sv));
+    pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part);
     if (!take_ticket<R>(st)) return;
     pf_finalize<R>(a, st, sv, gridDim.x, t, cur, cur_lw);
 }

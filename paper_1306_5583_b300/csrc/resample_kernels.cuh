@@ -39,7 +39,7 @@ struct QGen {
         else m = R(st->max_lw);
     }
     __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
-        return Math<R>::fixed(Math<R>::exp(cur_lw[i] - m), frac);
+        return Math<R>::fixed(Math<R>::fast_exp(__ldcg(cur_lw + i) - m), frac);
     }
     // kScanItems consecutive values from 16-byte vector loads
     static constexpr bool kVec = true;
@@ -48,7 +48,7 @@ struct QGen {
         load_k<R, kScanItems>(cur_lw, i0, n, w);
 #pragma unroll
         for (int j = 0; j < kScanItems; ++j)
-            v[j] = (i0 + j < n) ? Math<R>::fixed(Math<R>::exp(w[j] - m), frac) : 0ull;
+            v[j] = (i0 + j < n) ? Math<R>::fixed(Math<R>::fast_exp(w[j] - m), frac) : 0ull;
     }
 };
 
@@ -193,8 +193,9 @@ struct GridTargets {
     uint32_t t;
     unsigned long long c;  // 2j + 1 (systematic)
     GridDiv dv;
-    __device__ __forceinline__ void prepare(const DevState *st) {
-        t = (uint32_t)st->t;
+    __device__ __forceinline__ void prepare(const DevState *st) { prepare_at((uint32_t)st->t); }
+    __device__ __forceinline__ void prepare_at(uint32_t tt) {
+        t = tt;
         c = 2ull * u24(draw(key, 0u, t, TAG_RESAMPLE, stream, 0u).x) + 1ull;
     }
     __device__ __forceinline__ void setup(unsigned long long QN) { dv.init(QN, (unsigned long long)n); }
@@ -228,10 +229,21 @@ struct GridTargets {
         }
         uint64_t u, v;
         dv.start((uint64_t)k0, u, v);
+        if (kStratified) {
 #pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            if (j > 0) dv.next(u, v);
-            tau[j] = dv.tau((uint64_t)(k0 + j), kStratified ? cw[j] : c, u, v);
+            for (int j = 0; j < kScanItems; ++j) {
+                if (j > 0) dv.next(u, v);
+                tau[j] = dv.tau((uint64_t)(k0 + j), cw[j], u, v);
+            }
+        } else {
+            uint64_t rem;
+            uint64_t t = dv.tau((uint64_t)k0, c, u, v, &rem);
+            tau[0] = t;
+#pragma unroll
+            for (int j = 1; j < kScanItems; ++j) {
+                dv.advance(t, rem);
+                tau[j] = t;
+            }
         }
     }
 };
@@ -381,6 +393,19 @@ __global__ void __launch_bounds__(kBlock) tile_reduce_kernel(Gen gen, int64_t n,
     }
 }
 
+// Sum of one value per thread, returned to every thread.
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v) {
+    __shared__ unsigned long long s_w[kBlock / 32];
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) t += s_w[w];
+    return t;
+}
+
 // Exclusive prefix (tiles before `tile`) and total of nt tile sums, by the
 // whole block in one pass; every thread receives both.
 __device__ __forceinline__ void tile_prefix_total(const unsigned long long *tsum, int tile, int nt,
@@ -428,21 +453,28 @@ __device__ __forceinline__ Tgt block_targets(const Tgt &proto, const DevState *s
     return s_tg;
 }
 
-// One tile: inclusive scan of the tile's values in shared memory on top of
-// the exclusive prefix `pre` (optionally stored through `sink`), then the
-// ancestors of every output whose target falls in the tile's CDF range.
-// g and tg are prepared by the caller.
-template <class Gen, class Tgt, class Out, class Sink>
-__device__ __forceinline__ void scan_select_tile(const Gen &g, const Tgt &tg, const Out &out, const Sink &sink,
-                                                 int64_t n, int tile, unsigned long long pre,
-                                                 unsigned long long QN, DevState *st) {
-    __shared__ unsigned long long s_q[kScanTile];
-    __shared__ int32_t s_a[kScanTile];
-    __shared__ unsigned long long s_w[kBlock / 32];
-    __shared__ int64_t s_k[2];
+// Shared-memory buffers of one scan tile (declared once per kernel).  The
+// 64-bit arrays have one pad word after every kScanItems entries and the
+// ancestor array one after every 32: a thread owns kScanItems consecutive
+// entries, and without padding the 64-byte stride between threads would put
+// 16 threads of a warp on the same banks.
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+
+struct TileBufs {
+    unsigned long long q[kScanTile + kScanTile / 8];    // tile-relative inclusive prefix sums (pad8)
+    unsigned long long tau[kScanTile + kScanTile / 8];  // thresholds of one round, relative to the tile (pad8)
+    int32_t a[kScanTile + kScanTile / 32];              // ancestors of one round (pad32)
+    unsigned long long w[kBlock / 32];
+    int64_t k[2];                                       // the tile's output range
+};
+
+// Inclusive scan of the tile's values into tb.q (tile-relative; zeros past
+// n); returns the tile's total to every thread.
+template <class Gen>
+__device__ __forceinline__ unsigned long long scan_tile_local(const Gen &g, int64_t n, int tile, TileBufs &tb) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t t0 = (int64_t)tile * kScanTile;
-    const int len = (int)min((int64_t)kScanTile, n - t0);
     unsigned long long loc[kScanItems];
     gen_items(g, t0 + (int64_t)tid * kScanItems, n, loc);
     unsigned long long acc = 0;
@@ -452,76 +484,90 @@ __device__ __forceinline__ void scan_select_tile(const Gen &g, const Tgt &tg, co
         loc[j] = acc;
     }
     const unsigned long long winc = warp_incl_scan(acc);
-    __syncthreads();
-    if (lane == 31) s_w[warp] = winc;
+    __syncthreads();  // tb may still be read by a previous round
+    if (lane == 31) tb.w[warp] = winc;
     __syncthreads();
     unsigned long long wpre = 0;
 #pragma unroll
     for (int w = 0; w < kBlock / 32; ++w)
-        if (w < warp) wpre += s_w[w];
-    const unsigned long long base = pre + wpre + (winc - acc);
+        if (w < warp) wpre += tb.w[w];
+    const unsigned long long base = wpre + (winc - acc);
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) s_q[tid * kScanItems + j] = base + loc[j];
+    for (int j = 0; j < kScanItems; ++j) tb.q[pad8(tid * kScanItems + j)] = base + loc[j];
     __syncthreads();
+    return tb.q[pad8(kScanTile - 1)];
+}
+
+// Selection for one scanned tile (tb.q holds its tile-relative prefix sums,
+// pre the exclusive prefix before it, total its sum): the CDF is optionally
+// stored through `sink`, then every output k in the tile's range
+// [k_lo, k_hi) gets a_k = t0 + #{i : Q_i <= tau_k} (Q_i = pre + q_i).
+// Outputs go in rounds of kScanTile; a round merges its sorted thresholds
+// with the tile's sorted prefix sums along the merge path, so every thread
+// takes the same number of merge steps whatever the weights look like.
+template <class Tgt, class Out, class Sink>
+__device__ __forceinline__ void select_tile(const Tgt &tg, const Out &out, const Sink &sink, int64_t n, int tile,
+                                            unsigned long long pre, unsigned long long total,
+                                            unsigned long long QN, DevState *st, TileBufs &tb) {
+    constexpr int kSteps = 2 * kScanItems;  // merge steps per thread: (outputs + inputs) / threads
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t t0 = (int64_t)tile * kScanTile;
+    const int len = (int)min((int64_t)kScanTile, n - t0);
     if (Sink::kActive) {
 #pragma unroll
         for (int r = 0; r < kScanItems; ++r) {
             const int idx = r * kBlock + tid;
-            if (idx < len) sink(t0 + idx, s_q[idx], st);
+            if (idx < len) sink(t0 + idx, pre + tb.q[pad8(idx)], st);
         }
     }
-    if (!Tgt::kActive || QN == 0) {
-        __syncthreads();
-        return;
-    }
-    // outputs [k_lo, k_hi) have their ancestor in this tile
-    if (tid == 0) {
+    if (!Tgt::kActive || QN == 0) return;
+    if (lane == 0 && warp < 2) {  // the two ends of the output range, one warp each
         const int64_t cnt = tg.count();
-        s_k[0] = min(tg.first_at_least(pre, QN), cnt);
-        s_k[1] = (t0 + len >= n) ? cnt : min(tg.first_at_least(s_q[len - 1], QN), cnt);
+        if (warp == 0) tb.k[0] = min(tg.first_at_least(pre, QN), cnt);
+        else tb.k[1] = (t0 + len >= n) ? cnt : min(tg.first_at_least(pre + total, QN), cnt);
     }
     __syncthreads();
-    const int64_t k_lo = s_k[0], k_hi = s_k[1];
-    // rounds of kScanTile outputs starting at a multiple of kScanItems;
-    // each thread takes kScanItems consecutive outputs: a binary search for
-    // the first, forward steps for the rest
+    const int64_t k_lo = tb.k[0], k_hi = tb.k[1];
     for (int64_t kb = k_lo & ~(int64_t)(kScanItems - 1); kb < k_hi; kb += kScanTile) {
         const int m = (int)min((int64_t)kScanTile, k_hi - kb);
         const int j0 = tid * kScanItems;
         if (j0 < m) {
             unsigned long long tau[kScanItems];
             tg.thresholds(kb + j0, tau);
-            int lo = 0, hi = len;
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j)  // outputs before k_lo clamp to 0 (merged, never written)
+                tb.tau[pad8(j0 + j)] = tau[j] >= pre ? tau[j] - pre : 0ull;
+        }
+        __syncthreads();
+        const int tot = m + len;
+        const int d0 = tid * kSteps;
+        if (d0 < tot) {
+            // split of diagonal d0: k outputs and d0 - k inputs come first
+            int lo = max(0, d0 - len), hi = min(d0, m);
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (s_q[mid] > tau[0]) hi = mid;
-                else lo = mid + 1;
+                if (tb.tau[pad8(mid)] < tb.q[pad8(d0 - mid - 1)]) lo = mid + 1;
+                else hi = mid;
             }
-            int i = lo;
+            int k = lo, i = d0 - lo;
+            unsigned long long av = k < m ? tb.tau[pad8(k)] : ~0ull;
+            unsigned long long bv = i < len ? tb.q[pad8(i)] : ~0ull;
 #pragma unroll
-            for (int j = 0; j < kScanItems; ++j) {
-                if (j > 0) {
-                    int steps = 0;
-                    while (i < len && s_q[i] <= tau[j] && steps < 16) {
-                        ++i;
-                        ++steps;
-                    }
-                    if (i < len && s_q[i] <= tau[j]) {
-                        int l2 = i, h2 = len;
-                        while (l2 < h2) {
-                            const int mid = (l2 + h2) >> 1;
-                            if (s_q[mid] > tau[j]) h2 = mid;
-                            else l2 = mid + 1;
-                        }
-                        i = l2;
-                    }
+            for (int s = 0; s < kSteps; ++s) {
+                if (d0 + s >= tot) break;
+                if (k < m && (i >= len || av < bv)) {  // output k: inputs 0..i-1 have Q <= tau_k < Q_i
+                    tb.a[pad32(k)] = (int32_t)(t0 + min(i, len - 1));
+                    ++k;
+                    av = k < m ? tb.tau[pad8(k)] : ~0ull;
+                } else {
+                    ++i;
+                    bv = i < len ? tb.q[pad8(i)] : ~0ull;
                 }
-                if (j0 + j < m) s_a[j0 + j] = (int32_t)(t0 + min(i, len - 1));
             }
         }
         __syncthreads();
         for (int j = tid; j < m; j += kBlock)
-            if (kb + j >= k_lo) out(kb + j, s_a[j]);
+            if (kb + j >= k_lo) out(kb + j, tb.a[pad32(j)]);
         __syncthreads();
     }
 }
@@ -542,7 +588,59 @@ __global__ void __launch_bounds__(kBlock) scan_select_kernel(Gen gen, Tgt tgt, O
     tile_prefix_total(tsum, blockIdx.x, gridDim.x, &pre, &QN);
     if (total) QN = __ldcg(total);
     const Tgt tg = block_targets(tgt, sv, QN);
-    scan_select_tile(g, tg, out, sink, n, blockIdx.x, pre, QN, st);
+    __shared__ TileBufs tb;
+    const unsigned long long ts = scan_tile_local(g, n, blockIdx.x, tb);
+    select_tile(tg, out, sink, n, blockIdx.x, pre, ts, QN, st, tb);
+}
+
+// One-pass resampling for grid targets (systematic, stratified): a
+// cooperative launch of at most one wave, each block owning a contiguous
+// range of scan tiles.  Phase 1 scans its tiles and publishes the tile sums
+// and the block's sum; after a grid barrier phase 2 takes the block's prefix
+// and Q_N from the block sums and selects, starting with the last tile whose
+// scan is still in shared memory (a block with one tile never rescans).
+template <class Gen, bool kStratified, class Sink>
+__global__ void __launch_bounds__(kBlock, 4) grid_resample_kernel(Gen gen, GridTargets<kStratified> tgt, AncOut out,
+                                                               Sink sink, int64_t n, unsigned long long *tsum,
+                                                               unsigned long long *bsum, DevState *st, int gate) {
+    __shared__ TileBufs tb;
+    const DevState *sv = snapshot(st);
+    if (gated_out(sv, gate)) return;  // the same decision in every block
+    Gen g = gen;
+    g.prepare(sv);
+    const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+    const int G = gridDim.x, b = blockIdx.x;
+    const int t_lo = (int)((int64_t)ntiles * b / G), t_hi = (int)((int64_t)ntiles * (b + 1) / G);
+    // tile sums (the last tile scanned, its scan kept for phase 2)
+    unsigned long long bs = 0;
+    for (int tile = t_lo; tile < t_hi - 1; ++tile) {
+        const unsigned long long s = tile_sum(g, n, tile);  // to thread 0
+        if (threadIdx.x == 0) {
+            tsum[tile] = s;
+            bs += s;
+        }
+    }
+    const unsigned long long last = scan_tile_local(g, n, t_hi - 1, tb);
+    if (threadIdx.x == 0) {
+        tsum[t_hi - 1] = last;
+        bsum[b] = bs + last;
+    }
+    if (!grid_barrier(st, gridDim.x)) return;
+    if (b == 0 && threadIdx.x == 0) st->ready = 1;
+    unsigned long long pre, QN;
+    tile_prefix_total(bsum, b, G, &pre, &QN);
+    const GridTargets<kStratified> tg = block_targets(tgt, sv, QN);
+    // the last tile first (its scan is in tb), then the others rescanned
+    unsigned long long before_last = 0;  // sum of the block's other tiles
+    for (int tile = t_lo + (int)threadIdx.x; tile < t_hi - 1; tile += kBlock) before_last += __ldcg(&tsum[tile]);
+    before_last = block_sum_u64(before_last);
+    select_tile(tg, out, sink, n, t_hi - 1, pre + before_last, last, QN, st, tb);
+    for (int tile = t_lo; tile < t_hi - 1; ++tile) {
+        const unsigned long long ts = scan_tile_local(g, n, tile, tb);
+        select_tile(tg, out, sink, n, tile, pre, ts, QN, st, tb);
+        pre += ts;
+    }
+    grid_depart(st);
 }
 
 // ------------------------------------------------- sorting iid uniforms --

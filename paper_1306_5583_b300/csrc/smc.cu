@@ -33,6 +33,7 @@ int gmm_launch_reweight(smc_ctx *c);
 int gmm_launch_mcmc(smc_ctx *c);
 
 constexpr size_t kAlign = 256;
+constexpr int kMaxCoopGrid = 2048;  // blocks of a cooperative launch (B300: at most 148 x 8)
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -43,7 +44,7 @@ int ceil_log2(int64_t n) {
 }
 
 struct Layout {
-    size_t st, rec, part, x, lw, anc, Q, tsum, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, alpha;
+    size_t st, rec, part, x, lw, anc, Q, tsum, bsum, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, alpha;
     size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, total;
     int ck;           // steps between checkpoints (record mode)
     int64_t nck;      // checkpoints
@@ -113,6 +114,7 @@ Layout make_layout(const smc_config *c) {
     L.anc = take((size_t)L.ld * 4);
     L.Q = take((size_t)n * 8);
     L.tsum = take((size_t)kScanSlots * L.ntiles_status * 8);
+    L.bsum = take((size_t)kMaxCoopGrid * 8);  // block sums of the cooperative kernels
     L.cnt = take(sorts ? (size_t)L.nbuckets * 4 : 0);
     L.fill = take(sorts ? (size_t)L.nbuckets * 4 : 0);
     L.boff = take(sorts ? (size_t)L.nbuckets * 8 : 0);
@@ -156,6 +158,7 @@ struct smc_ctx {
     int32_t *anc;
     unsigned long long *Q;
     unsigned long long *tsum;
+    unsigned long long *bsum;  // block sums of the cooperative kernels (kMaxCoopGrid)
     uint32_t *cnt, *fill;
     unsigned long long *boff;
     uint32_t *sorted;
@@ -201,6 +204,8 @@ __global__ void reset_state_kernel(DevState *st) {
     st->path_log_z = 0;
     st->qn = 0;
     st->sum_d = 0;
+    st->grid_count = 0;
+    st->grid_depart = 0;
     for (int i = 0; i < 4; ++i) st->accept[i] = 0;
 }
 
@@ -331,6 +336,47 @@ SortedTargets sorted_targets(smc_ctx *c, int from_residual) {
     return tg;
 }
 
+// One-pass systematic / stratified resampling (grid_resample_kernel): a
+// cooperative launch, so every block is resident and the kernel's grid
+// barrier completes; at most one block per scan tile.
+
+template <typename R, bool kS, class Sink>
+int launch_grid_resample(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
+    const int64_t n = c->cfg.n_particles;
+    const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+    auto kern = grid_resample_kernel<QGen<R>, kS, Sink>;
+    static int per_sm[64] = {};  // resident blocks per SM, per device (this instantiation)
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SMC_E_CUDA;
+    if (!per_sm[dev]) {
+        int b = 0, m = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kBlock, 0) != cudaSuccess || b < 1)
+            return SMC_E_CUDA;
+        if (cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || m < 1)
+            return SMC_E_CUDA;
+        sms[dev] = m;
+        per_sm[dev] = b;
+    }
+    const int grid = std::max(1, std::min({ntiles, per_sm[dev] * sms[dev], kMaxCoopGrid}));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3(kBlock);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    GridTargets<kS> tg{};
+    tg.n = n;
+    tg.key = key_of(c);
+    tg.stream = c->cfg.stream_id;
+    return cuda_check(cudaLaunchKernelEx(&lc, kern, qg, tg, AncOut{c->anc}, sk, n, tsum_of(c, SLOT_CDF),
+                                         c->bsum, c->st, gate));
+}
+
 template <typename R>
 int launch_resample(smc_ctx *c, int gate) {
     const int64_t n = c->cfg.n_particles;
@@ -343,17 +389,19 @@ int launch_resample(smc_ctx *c, int gate) {
     qg.cur_lw = nullptr;
     qg.m = 0;
     const StoreSink qsink{keep ? c->Q : nullptr};
-    // tile sums of the fixed-point weights; total Q_N -> st->scan_total[SLOT_CDF]
-    if ((rc = launch_reduce(c, qg, n, SLOT_CDF, gate))) return rc;
-    const uint2 key = key_of(c);
-    const uint32_t sid = c->cfg.stream_id;
-    switch (c->cfg.scheme) {
+    switch (c->cfg.scheme) {  // one pass
         case SMC_SYSTEMATIC:
-            return launch_scan_select(c, qg, GridTargets<false>{n, key, sid, 0, 0}, AncOut{c->anc}, qsink, n,
-                                      SLOT_CDF, gate, 1);
+            return keep ? launch_grid_resample<R, false>(c, qg, qsink, gate)
+                        : launch_grid_resample<R, false>(c, qg, NoSink{}, gate);
         case SMC_STRATIFIED:
-            return launch_scan_select(c, qg, GridTargets<true>{n, key, sid, 0, 0}, AncOut{c->anc}, qsink, n,
-                                      SLOT_CDF, gate, 1);
+            return keep ? launch_grid_resample<R, true>(c, qg, qsink, gate)
+                        : launch_grid_resample<R, true>(c, qg, NoSink{}, gate);
+        default:
+            break;
+    }
+    // tile sums of the fixed-point weights
+    if ((rc = launch_reduce(c, qg, n, SLOT_CDF, gate))) return rc;
+    switch (c->cfg.scheme) {
         case SMC_MULTINOMIAL:
             if ((rc = launch_uniform_sort(c, 0, gate))) return rc;
             return launch_scan_select(c, qg, sorted_targets(c, 0), AncOut{c->anc}, qsink, n, SLOT_CDF, gate, 1);
@@ -512,6 +560,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->anc = reinterpret_cast<int32_t *>(c->ws + L.anc);
     c->Q = reinterpret_cast<unsigned long long *>(c->ws + L.Q);
     c->tsum = reinterpret_cast<unsigned long long *>(c->ws + L.tsum);
+    c->bsum = reinterpret_cast<unsigned long long *>(c->ws + L.bsum);
     c->cnt = reinterpret_cast<uint32_t *>(c->ws + L.cnt);
     c->fill = reinterpret_cast<uint32_t *>(c->ws + L.fill);
     c->boff = reinterpret_cast<unsigned long long *>(c->ws + L.boff);

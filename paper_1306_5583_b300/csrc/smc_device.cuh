@@ -139,7 +139,10 @@ __device__ __forceinline__ void normals4_fast(uint4 w, R z[4]) {
 
 // ---- vector loads of K consecutive elements ----------------------------------
 // Thread-contiguous items let every load be a 16-byte vector load; a partial
-// group (the ragged tail) falls back to guarded scalar loads.
+// group (the ragged tail) falls back to guarded scalar loads.  Loads go
+// through L2 (ld.global.cg): the persistent iteration kernel reads data that
+// other blocks wrote earlier in the same launch, which a per-SM L1 copy could
+// hold stale.
 template <typename R, int K>
 __device__ __forceinline__ void load_k(const R *__restrict__ p, uint32_t i0, uint32_t n, R (&v)[K]) {
     static_assert((K * sizeof(R)) % 16 == 0, "vector width");
@@ -147,12 +150,12 @@ __device__ __forceinline__ void load_k(const R *__restrict__ p, uint32_t i0, uin
         const float4 *q = reinterpret_cast<const float4 *>(p + i0);
 #pragma unroll
         for (int c = 0; c < (int)(K * sizeof(R) / 16); ++c) {
-            const float4 w = __ldg(q + c);
+            const float4 w = __ldcg(q + c);
             reinterpret_cast<float4 *>(v)[c] = w;
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < K; ++j) v[j] = (i0 + j < n) ? p[i0 + j] : R(0);
+        for (int j = 0; j < K; ++j) v[j] = (i0 + j < n) ? __ldcg(p + i0 + j) : R(0);
     }
 }
 
@@ -171,14 +174,14 @@ __device__ __forceinline__ void store_k(R *__restrict__ p, uint32_t i0, uint32_t
 
 __device__ __forceinline__ void load_idx4(const int32_t *__restrict__ p, uint32_t i0, uint32_t n, int32_t (&v)[4]) {
     if (i0 + 4 <= n) {
-        const int4 w = __ldg(reinterpret_cast<const int4 *>(p + i0));
+        const int4 w = __ldcg(reinterpret_cast<const int4 *>(p + i0));
         v[0] = w.x;
         v[1] = w.y;
         v[2] = w.z;
         v[3] = w.w;
     } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = (i0 + j < n) ? p[i0 + j] : 0;
+        for (int j = 0; j < 4; ++j) v[j] = (i0 + j < n) ? __ldcg(p + i0 + j) : 0;
     }
 }
 
@@ -224,12 +227,6 @@ __device__ __forceinline__ U128 mul64(uint64_t a, uint64_t b) { return U128{__um
 // a > b
 __device__ __forceinline__ bool gt128(U128 a, U128 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 
-__device__ __forceinline__ U128 add128(U128 a, U128 b) {
-    U128 r;
-    r.lo = a.lo + b.lo;
-    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
-    return r;
-}
 
 // bit length of a 128-bit value
 __device__ __forceinline__ int bitlen128(U128 a) {
@@ -238,6 +235,53 @@ __device__ __forceinline__ int bitlen128(U128 a) {
 
 // ---- bounded spin (never waits forever: sets the error word and gives up) --
 __device__ __forceinline__ void raise_error(DevState *st, int code) { atomicCAS(&st->error, 0, code); }
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t atom_add_release_u32(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Barrier over the whole grid of a cooperative launch (every block resident
+// at once).  Thread 0 publishes the block's writes and counts its arrival,
+// then polls with acquire loads, at most kSpinLimit times; on timeout it
+// raises SMC_E_TIMEOUT and the block gives up (returns false).  The k-th
+// barrier of a launch waits for k * gridDim.x arrivals (target); the counter
+// starts at zero and grid_depart() clears it at the end of the launch.
+__device__ __forceinline__ bool grid_barrier(DevState *st, uint32_t target) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atom_add_release_u32(&st->grid_count, 1u);
+        uint32_t it = 0;
+        bool ok = true;
+        while (ld_acquire_u32(&st->grid_count) < target) {
+            if (++it >= kSpinLimit) {
+                ok = false;
+                break;
+            }
+            __nanosleep(32);
+        }
+        if (!ok) raise_error(st, SMC_E_TIMEOUT);
+        s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+// After the barrier: the last block to leave clears the counters for the
+// next launch (every block has passed its wait by then).
+__device__ __forceinline__ void grid_depart(DevState *st) {
+    __syncthreads();
+    if (threadIdx.x == 0 && atom_add_release_u32(&st->grid_depart, 1u) == gridDim.x - 1) {
+        st->grid_count = 0;
+        st->grid_depart = 0;
+    }
+}
 
 // Copy of the device state block in shared memory, read once per block:
 // every block of a kernel reads the same few words, and letting every warp

@@ -58,7 +58,9 @@ struct DevState {
     int32_t pad2;
     float log_norm_f[2];  // L_t as an unevaluated float sum hi + lo (FP32 kernels)
     float max_lw_f;       // M_t as float (exact: the maximum of float log-weights)
-    float pad3;
+    uint32_t grid_count;  // grid barrier of the one-pass resampling kernel: arrivals
+    uint32_t grid_depart; // and departures (the last departure clears both)
+    uint32_t pad3;
 };
 
 struct Partial {  // one per block of a weighting kernel

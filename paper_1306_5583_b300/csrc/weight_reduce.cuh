@@ -395,29 +395,47 @@ __device__ __forceinline__ bool finalize_weights(const FinalizeArgs &f, const Co
 // FP32 path of finalize_weights: the same record and state updates with the
 // per-iteration scalars in compensated float (no float64 logarithm or
 // division); doubles only for the stored values (bit-pattern conversions and
-// the float64 evidence sum).
-__device__ __forceinline__ bool finalize_weights_df(const FinalizeArgs &f, const CombinedDF &c) {
+// the float64 evidence sum).  Split in two so that every block of the
+// persistent iteration kernel can take the decision (final_values_df) while
+// one block writes (write_final_df).
+struct FinalDF {
+    bool ok, due;
+    DF L, ess;
+};
+
+__device__ __forceinline__ FinalDF final_values_df(const FinalizeArgs &f, const CombinedDF &c) {
+    FinalDF v;
+    const DF S1 = c.S[0], S2 = c.S[1];
+    v.ok = (c.M > -INFINITY) && (c.M < INFINITY) && (S1.hi > 0.0f) && (S1.hi < INFINITY) && (S2.hi > 0.0f);
+    if (!v.ok) {
+        v.due = false;
+        v.L = v.ess = DF{0.0f, 0.0f};
+        return v;
+    }
+    v.L = df_add_f(df_log(S1), c.M);
+    v.ess = df_div(df_mul(S1, S1), S2);
+    v.due = f.thr_mode == 1 ? true
+            : f.thr_mode == 2 ? false
+                              : df_lt(v.ess, df_mul(DF{f.thr_df[0], f.thr_df[1]}, df_from_int(f.n)));
+    return v;
+}
+
+// Record of iteration f.t and the state block; returns log Z_t.
+__device__ __forceinline__ double write_final_df(const FinalizeArgs &f, const CombinedDF &c, const FinalDF &v) {
     DevState *st = f.st;
     smc_record *r = &f.rec[f.t % f.rec_cap];
-    const DF S1 = c.S[0], S2 = c.S[1];
-    const bool ok = (c.M > -INFINITY) && (c.M < INFINITY) && (S1.hi > 0.0f) && (S1.hi < INFINITY) &&
-                    (S2.hi > 0.0f);
     st->ticket = 0;
-    if (!ok) {
+    if (!v.ok) {
         r->t = f.t;
         r->status = SMC_E_NONFINITE;
         raise_error(st, SMC_E_NONFINITE);
-        return false;
+        return 0.0;
     }
-    const DF L = df_add_f(df_log(S1), c.M);
-    const DF ess = df_div(df_mul(S1, S1), S2);
-    const bool due = f.thr_mode == 1 ? true
-                     : f.thr_mode == 2 ? false
-                                       : df_lt(ess, df_mul(DF{f.thr_df[0], f.thr_df[1]}, df_from_int(f.n)));
-    const double Ld = df_to_double(L);
+    const DF S1 = c.S[0];
+    const double Ld = df_to_double(v.L);
     const double prev_logz = (f.mode == 0) ? (f.t == 0 ? 0.0 : f.log_evidence_prev) : st->log_evidence - st->log_norm;
     const double logz = prev_logz + Ld;
-    const double essd = df_to_double(ess);
+    const double essd = df_to_double(v.ess);
     const double Md = df_to_double(DF{c.M, 0.0f});
     r->log_norm = Ld;
     r->log_evidence = logz;
@@ -426,18 +444,24 @@ __device__ __forceinline__ bool finalize_weights_df(const FinalizeArgs &f, const
     r->mean[1] = df_to_double(df_div(c.S[3], S1));
     r->max_lw = Md;
     r->t = f.t;
-    r->resampled = due ? 1 : 0;
+    r->resampled = v.due ? 1 : 0;
     r->status = SMC_OK;
     r->alpha = f.alpha;
     st->max_lw = Md;
     st->max_lw_f = c.M;
     st->log_norm = Ld;
-    st->log_norm_f[0] = L.hi;
-    st->log_norm_f[1] = L.lo;
+    st->log_norm_f[0] = v.L.hi;
+    st->log_norm_f[1] = v.L.lo;
     st->log_evidence = logz;
     st->ess = essd;
-    st->due = due ? 1 : 0;
-    return true;
+    st->due = v.due ? 1 : 0;
+    return logz;
+}
+
+__device__ __forceinline__ bool finalize_weights_df(const FinalizeArgs &f, const CombinedDF &c) {
+    const FinalDF v = final_values_df(f, c);
+    write_final_df(f, c, v);
+    return v.ok;
 }
 
 }  // namespace smc

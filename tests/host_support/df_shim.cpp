@@ -20,16 +20,25 @@ void shim_df_from_int(long long x, float *out) {
     out[0] = r.hi;
     out[1] = r.lo;
 }
-// thresholds tau_{k0 + j}, j < count, with a constant c (systematic form)
+// thresholds tau_{k0 + j}, j < count, with a constant c: per-k form
+// (incremental = 0, as for stratified targets) or the advancing remainder
+// form of systematic targets (incremental = 1)
 void shim_grid_tau(unsigned long long qn, unsigned long long n, unsigned long long k0, unsigned long long c,
-                   int count, unsigned long long *out) {
+                   int count, int incremental, unsigned long long *out) {
     smc::GridDiv d;
     d.init(qn, n);
     uint64_t u, v;
     d.start(k0, u, v);
+    uint64_t rem = 0, t = 0;
     for (int j = 0; j < count; ++j) {
-        if (j > 0) d.next(u, v);
-        out[j] = d.tau(k0 + j, c, u, v);
+        if (incremental) {
+            if (j == 0) t = d.tau(k0, c, u, v, &rem);
+            else d.advance(t, rem);
+            out[j] = t;
+        } else {
+            if (j > 0) d.next(u, v);
+            out[j] = d.tau(k0 + j, c, u, v);
+        }
     }
 }
 }

@@ -227,3 +227,38 @@ def test_full_size_sampled(scheme):
             q = np.diff(np.concatenate([[0], Q.astype(object)])).astype(object)
             zero = np.array([int(v) == 0 for v in q])
             assert not np.any(zero[a])
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_bench_configuration_matches_cdf_path(scheme):
+    """The benchmarked launch configuration (no stored CDF, whole iterations
+    replayed from a CUDA graph, N = 2^20, ESS threshold 0.5) gives results
+    bit-identical to the step-by-step path with the CDF stored, whose
+    resampling the other tests check against the oracle."""
+    need_gpu()
+    n, T = 1 << 20, 12
+    p = cv_params()
+    _, y = workloads.cv_data(T, seed=0, **p)
+    outs = []
+    for keep in (True, False):
+        cfg = smc.make_config(model="cv", n=n, precision=32, scheme=scheme, threshold=0.5, seed=3, max_data=T,
+                              cv=p, keep_cdf=keep)
+        stream = torch.cuda.Stream()
+        s = smc.Sampler(cfg, stream=stream)
+        s.set_data(y)
+        with torch.cuda.stream(stream):
+            s.initialize()
+            if keep:
+                for _ in range(T - 1):
+                    s.move()
+                    s.resample()
+            else:
+                s.iterate(T - 1)
+        s.sync()
+        outs.append((s.state(), s.log_weight(), s.ancestors(), s.log_evidence(),
+                     [r["resampled"] for r in s.history(T)]))
+        s.close()
+    a, b = outs
+    assert sum(a[4]) > 0
+    for u, v in zip(a, b):
+        assert np.array_equal(np.asarray(u), np.asarray(v))

@@ -31,7 +31,7 @@ def shim(tmp_path_factory):
     lib.shim_df_to_double.argtypes = [ctypes.c_float, ctypes.c_float]
     lib.shim_df_to_double.restype = ctypes.c_double
     lib.shim_df_from_int.argtypes = [ctypes.c_longlong, ctypes.c_void_p]
-    lib.shim_grid_tau.argtypes = [ctypes.c_ulonglong] * 4 + [ctypes.c_int, ctypes.c_void_p]
+    lib.shim_grid_tau.argtypes = [ctypes.c_ulonglong] * 4 + [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
     return lib
 
 
@@ -51,12 +51,13 @@ def test_grid_thresholds_are_exact(shim):
             qn = int(qmax - rng.integers(0, 1000)) if rep % 3 == 0 else int(rng.integers(1, qmax))
             c = 2 * int(rng.integers(0, 1 << 24)) + 1
             k0 = int(rng.integers(0, n + 1))
-            shim.shim_grid_tau(qn, n, k0, c, 8, out)
-            for j in range(8):
-                k = k0 + j
-                if k > n:  # thresholds past the last output are never used
-                    break
-                assert out[j] == (qn * ((k << 25) + c)) // (n << 25), (n, qn, k, c)
+            for incremental in (0, 1):
+                shim.shim_grid_tau(qn, n, k0, c, 8, incremental, out)
+                for j in range(8):
+                    k = k0 + j
+                    if k > n:  # thresholds past the last output are never used
+                        break
+                    assert out[j] == (qn * ((k << 25) + c)) // (n << 25), (n, qn, k, c, incremental)
 
 
 def test_df_log_accuracy(shim):
