@@ -46,6 +46,7 @@ struct BatchArgs {
     const int64_t *rec_off;       // first record of each filter
     const int32_t *n_iter;        // iterations of each filter (= its observations)
     const uint32_t *stream_of;    // Philox stream of each filter
+    const unsigned long long *mrec;  // floor((2^64 - 1) / N) of each filter
     const double *log_n;          // log N of each filter
     const int32_t *frac;          // fixed-point fraction bits of each filter
     int32_t tmax;
@@ -144,6 +145,7 @@ __device__ __forceinline__ void batch_select_tile(const BatchArgs<R> &B, int til
     proto.n = B.n[b];
     proto.key = B.proto.key;
     proto.stream = B.stream_of[b];
+    proto.mrec = B.mrec[b];
     const GridTargets<kStratified> tg = block_targets(proto, sv, QN);
     __shared__ TileBufs tb;
     const unsigned long long ts = scan_tile_local(g, B.n[b], lt, tb);

@@ -103,6 +103,31 @@ DF_HD DF df_from_int(int64_t x) {
     return two_sum(h, l);
 }
 
+DF_HD int df_clz64(uint64_t x) {
+#if defined(__CUDA_ARCH__)
+    return __clzll((long long)x);
+#else
+    return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+// the top 24 bits of x (x >> sh < 2^24) as an exact float
+DF_HD float df_top24(uint64_t x, int sh) {
+    return float((uint32_t)(x >> sh)) * df_u2f((uint32_t)(127 + sh) << 23);
+}
+
+// 64-bit unsigned integer as a DF value (relative error below 2^-47), by
+// integer arithmetic and exact 24-bit conversions
+DF_HD DF df_from_u64(uint64_t x) {
+    if (x == 0) return DF{0.0f, 0.0f};
+    const int sh = 40 - df_clz64(x) > 0 ? 40 - df_clz64(x) : 0;
+    const float hi = df_top24(x, sh);
+    const uint64_t rest = x - ((x >> sh) << sh);  // below 2^sh
+    if (rest == 0) return DF{hi, 0.0f};
+    const int sh2 = 40 - df_clz64(rest) > 0 ? 40 - df_clz64(rest) : 0;
+    return fast_two_sum(hi, df_top24(rest, sh2));
+}
+
 // natural logarithm of a DF value with 2^-125 <= hi < 2^126
 DF_HD DF df_log(DF x) {
     constexpr double kLn2 = 0.693147180559945309417232121458;

@@ -39,11 +39,16 @@ struct GridDiv {
     uint64_t mrec;  // floor((2^64 - 1) / N): floor(x / N) for x < 2^62 up to one correction
     uint64_t ah, al;  // a = ah 2^25 + al
 
-    SMC_HD void init(uint64_t qn, uint64_t n_) {
+    // mrec_ = floor((2^64 - 1) / N) (host-computed: no device division)
+    SMC_HD void init(uint64_t qn, uint64_t n_, uint64_t mrec_) {
         n = n_;
-        a = qn / n;
+        mrec = mrec_;
+        a = umulhi64(qn, mrec);  // floor(qn / N) or one less
         b = qn - a * n;
-        mrec = ~0ull / n;
+        if (b >= n) {
+            b -= n;
+            ++a;
+        }
         ah = a >> 25;
         al = a & ((1ull << 25) - 1);
     }

@@ -192,13 +192,14 @@ struct GridTargets {
     uint32_t stream;
     uint32_t t;
     unsigned long long c;  // 2j + 1 (systematic)
+    unsigned long long mrec;  // floor((2^64 - 1) / n), from the host
     GridDiv dv;
     __device__ __forceinline__ void prepare(const DevState *st) { prepare_at((uint32_t)st->t); }
     __device__ __forceinline__ void prepare_at(uint32_t tt) {
         t = tt;
         c = 2ull * u24(draw(key, 0u, t, TAG_RESAMPLE, stream, 0u).x) + 1ull;
     }
-    __device__ __forceinline__ void setup(unsigned long long QN) { dv.init(QN, (unsigned long long)n); }
+    __device__ __forceinline__ void setup(unsigned long long QN) { dv.init(QN, (unsigned long long)n, mrec); }
     __device__ __forceinline__ int64_t count() const { return n; }
     __device__ __forceinline__ unsigned long long P(int64_t k) const {
         const unsigned long long ck = kStratified ? 2ull * resample_u24_at(key, stream, t, k) + 1ull : c;
@@ -206,11 +207,12 @@ struct GridTargets {
     }
     // first k in [0, n] with QN P_k >= X D.  With k0 = floor(X N / QN) the
     // answer is k0 or k0 + 1 (P_k / 2^25 lies in (k, k + 1)); k0 comes from a
-    // float64 estimate (error below 1) corrected with exact 128-bit products.
+    // double-float estimate (error far below 1) corrected with exact 128-bit
+    // products.
     __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long QN) const {
         const unsigned long long N = (unsigned long long)n;
-        int64_t k0 = (int64_t)floor(double(X) * double(N) / double(QN));
-        if (k0 < 0) k0 = 0;
+        const DF e = df_mul(df_div(df_from_u64(X), df_from_u64(QN)), df_from_int(n));
+        int64_t k0 = (int64_t)__float2uint_rd(fmaxf(e.hi, 0.0f));
         if (k0 > n) k0 = n;
         const U128 xn = mul64(X, N);
         while (k0 > 0 && gt128(mul64((unsigned long long)k0, QN), xn)) --k0;  // k0 QN <= X N
@@ -271,10 +273,10 @@ struct SortedTargets {
     // i.e. s_k >= v with v the smallest s such that 2 s + 1 >= ceil(X 2^25 / QN)
     __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long QN) const {
         if (m == 0) return 0;
-        // c = ceil(X 2^25 / QN) <= 2^25 (X <= QN): float64 estimate, exact correction
+        // c = ceil(X 2^25 / QN) <= 2^25 (X <= QN): double-float estimate, exact correction
         const U128 y{X >> 39, X << 25};
-        long long c0 = (long long)ceil(double(X) * 33554432.0 / double(QN));
-        if (c0 < 0) c0 = 0;
+        const DF e = df_div(df_from_u64(X), df_from_u64(QN));
+        long long c0 = (long long)__float2uint_ru(fmaxf(e.hi * 33554432.0f, 0.0f));
         if (c0 > (1ll << 25) + 1) c0 = (1ll << 25) + 1;
         unsigned long long cc = (unsigned long long)c0;
         while (cc > 0 && !gt128(y, mul64(cc - 1, QN))) --cc;  // (cc - 1) QN < y

@@ -373,6 +373,7 @@ int launch_grid_resample(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
     tg.n = n;
     tg.key = key_of(c);
     tg.stream = c->cfg.stream_id;
+    tg.mrec = ~0ull / (unsigned long long)n;
     return cuda_check(cudaLaunchKernelEx(&lc, kern, qg, tg, AncOut{c->anc}, sk, n, tsum_of(c, SLOT_CDF),
                                          c->bsum, c->st, gate));
 }
@@ -1030,9 +1031,10 @@ struct BatchPlan {
     std::vector<int64_t> n, off, obs_off, rec_off;
     std::vector<int32_t> T, tfirst, sfirst, tile_filter, stile_filter, act_tiles, act_stiles, frac;
     std::vector<uint32_t> stream_of;
+    std::vector<unsigned long long> mrec;  // floor((2^64 - 1) / N) per filter
     std::vector<double> log_n;
     size_t o_fst, o_bs, o_rec, o_part, o_tsum, o_x, o_lw, o_anc, o_obs, o_n, o_off, o_obs_off, o_rec_off, o_T,
-        o_tfirst, o_sfirst, o_tf, o_stf, o_act, o_acts, o_stream, o_logn, o_frac, total = 0;
+        o_tfirst, o_sfirst, o_tf, o_stf, o_act, o_acts, o_stream, o_mrec, o_logn, o_frac, total = 0;
     size_t rsize = 4;
 };
 
@@ -1063,6 +1065,7 @@ bool batch_plan(const smc_config *cfg, const int64_t *n, const int32_t *T, int32
     P.sfirst.resize(nf + 1);
     P.frac.resize(nf);
     P.stream_of.resize(nf);
+    P.mrec.resize(nf);
     P.log_n.resize(nf);
     int64_t o = 0, oo = 0;
     int32_t tf = 0, sf = 0;
@@ -1081,6 +1084,7 @@ bool batch_plan(const smc_config *cfg, const int64_t *n, const int32_t *T, int32
         sf += (int32_t)((n[b] + kScanTile - 1) / kScanTile);
         P.frac[i] = 61 - ceil_log2(n[b]);
         P.stream_of[i] = cfg->stream_id + (uint32_t)b;
+        P.mrec[i] = ~0ull / (unsigned long long)n[b];
         P.log_n[i] = std::log((double)n[b]);
     }
     P.tfirst[nf] = tf;
@@ -1131,6 +1135,7 @@ bool batch_plan(const smc_config *cfg, const int64_t *n, const int32_t *T, int32
     P.o_act = take(4 * (size_t)P.tmax);
     P.o_acts = take(4 * (size_t)P.tmax);
     P.o_stream = take(4 * (size_t)nf);
+    P.o_mrec = take(8 * (size_t)nf);
     P.o_logn = take(8 * (size_t)nf);
     P.o_frac = take(4 * (size_t)nf);
     P.total = off_b;
@@ -1208,6 +1213,7 @@ BatchArgs<R> batch_args(smc_batch *bt) {
     B.rec_off = at<int64_t>(bt, P.o_rec_off);
     B.n_iter = at<int32_t>(bt, P.o_T);
     B.stream_of = at<uint32_t>(bt, P.o_stream);
+    B.mrec = at<unsigned long long>(bt, P.o_mrec);
     B.log_n = at<double>(bt, P.o_logn);
     B.frac = at<int32_t>(bt, P.o_frac);
     B.tmax = P.tmax;
@@ -1334,6 +1340,7 @@ int smc_batch_create(smc_batch **out, const smc_config *cfg, const int64_t *n, c
     if (!rc) rc = up(P.o_act, P.act_tiles.data(), 4 * (size_t)P.tmax);
     if (!rc) rc = up(P.o_acts, P.act_stiles.data(), 4 * (size_t)P.tmax);
     if (!rc) rc = up(P.o_stream, P.stream_of.data(), 4 * (size_t)nf);
+    if (!rc) rc = up(P.o_mrec, P.mrec.data(), 8 * (size_t)nf);
     if (!rc) rc = up(P.o_logn, P.log_n.data(), 8 * (size_t)nf);
     if (!rc) rc = up(P.o_frac, P.frac.data(), 4 * (size_t)nf);
     if (!rc) rc = cuda_check(cudaStreamSynchronize(bt->stream));
@@ -1750,8 +1757,13 @@ extern "C" int smc_resample_systematic_noalloc(const float *d_log_weight, int64_
     const uint2 key = make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
     tile_reduce_kernel<QGen<float>><<<tiles, kBlock, 0, stream>>>(qg, n, s->tsum, nullptr, &st->scan_ticket[SLOT_CDF],
                                                                    st, 1);
+    GridTargets<false> tg{};
+    tg.n = n;
+    tg.key = key;
+    tg.stream = stream_id;
+    tg.mrec = ~0ull / (unsigned long long)n;
     scan_select_kernel<QGen<float>, GridTargets<false>, AncOut, NoSink><<<tiles, kBlock, 0, stream>>>(
-        qg, GridTargets<false>{n, key, stream_id, 0, 0}, AncOut{d_ancestors}, NoSink{}, n, s->tsum, nullptr, st, 1,
+        qg, tg, AncOut{d_ancestors}, NoSink{}, n, s->tsum, nullptr, st, 1,
         0);
     return cuda_check(cudaGetLastError());
 }

@@ -15,6 +15,11 @@ void shim_df_div(float ah, float al, float bh, float bl, float *out) {
     out[1] = r.lo;
 }
 double shim_df_to_double(float hi, float lo) { return smc::df_to_double(smc::DF{hi, lo}); }
+void shim_df_from_u64(unsigned long long x, float *out) {
+    const smc::DF r = smc::df_from_u64(x);
+    out[0] = r.hi;
+    out[1] = r.lo;
+}
 void shim_df_from_int(long long x, float *out) {
     const smc::DF r = smc::df_from_int(x);
     out[0] = r.hi;
@@ -26,7 +31,7 @@ void shim_df_from_int(long long x, float *out) {
 void shim_grid_tau(unsigned long long qn, unsigned long long n, unsigned long long k0, unsigned long long c,
                    int count, int incremental, unsigned long long *out) {
     smc::GridDiv d;
-    d.init(qn, n);
+    d.init(qn, n, ~0ull / n);
     uint64_t u, v;
     d.start(k0, u, v);
     uint64_t rem = 0, t = 0;

@@ -31,6 +31,7 @@ def shim(tmp_path_factory):
     lib.shim_df_to_double.argtypes = [ctypes.c_float, ctypes.c_float]
     lib.shim_df_to_double.restype = ctypes.c_double
     lib.shim_df_from_int.argtypes = [ctypes.c_longlong, ctypes.c_void_p]
+    lib.shim_df_from_u64.argtypes = [ctypes.c_ulonglong, ctypes.c_void_p]
     lib.shim_grid_tau.argtypes = [ctypes.c_ulonglong] * 4 + [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
     return lib
 
@@ -101,6 +102,11 @@ def test_df_conversions(shim):
     for _ in range(1000):
         hi, lo = _df(rng.normal() * 10 ** rng.uniform(-5, 5))
         assert shim.shim_df_to_double(hi, lo) == hi + lo
+    for x in [0, 1, 3, (1 << 24) - 1, (1 << 24) + 1, (1 << 40) + 12345, (1 << 62) - 1, (1 << 64) - 1] + \
+            [int(v) for v in rng.integers(0, 1 << 63, size=2000, dtype=np.uint64)]:
+        shim.shim_df_from_u64(x, out)
+        got = decimal.Decimal(float(out[0])) + decimal.Decimal(float(out[1]))
+        assert abs(got - x) <= max(x, 1) * decimal.Decimal(2) ** -47, x
     assert shim.shim_df_to_double(float("inf"), 0.0) == float("inf")
     assert np.isnan(shim.shim_df_to_double(float("nan"), 0.0))
     assert shim.shim_df_to_double(-0.0, 0.0) == 0.0
