@@ -192,9 +192,16 @@ int smc_iterate(smc_ctx *ctx, int32_t n);
  * iteration and copies its record to *h_record.  Synchronises. */
 int smc_iterate_host(smc_ctx *ctx, const double *h_obs_t, smc_record *h_record);
 
-/* WeightSet::add_log_weight: lw_i += incw_i (n_particles values of the
- * context's precision), then normaliser, ESS and the resample decision of
- * the current iteration. */
+/* WeightSet::add_log_weight (Sec. 4.1.6): multiply the current weights by
+ * exp(incw_i), i.e. lw_i += incw_i (n_particles values of the context's
+ * precision, host or device).  The normaliser L_t, ESS, filtered means and
+ * resample decision of the current iteration t are computed again and its
+ * record rewritten; the evidence increment L_t is replaced by the new one
+ * (log Z_t = log Z_{t-1} + L'_t).  SMC_E_STATE when a resampling of
+ * iteration t has already been queued (the current particle system is the
+ * pending gather) or before smc_initialize.  A host incw is consumed before
+ * the call returns; a device incw must stay valid until the stream reaches
+ * the call. */
 int smc_add_log_weight(smc_ctx *ctx, const void *incw, int on_device);
 
 /* ESS of the current weights.  h_ess == NULL: no synchronisation. */
@@ -224,10 +231,33 @@ int smc_read_ancestors(smc_ctx *ctx, int32_t *dst, int on_device);
 int smc_read_cdf(smc_ctx *ctx, uint64_t *dst, int on_device);
 int smc_read_history(smc_ctx *ctx, smc_record *h_records, int32_t count, int32_t *n_written);
 
-/* Writers for restarts and checkpoints: replace the state / log-weights of
- * the current iteration (layouts as above). */
+/* Writers: replace the state / log-weights of the current iteration
+ * (layouts as above).  smc_write_log_weight then recomputes L_t, ESS, means
+ * and the decision as smc_add_log_weight does (with a zero increment), so
+ * the evidence increment of iteration t becomes that of the new weights;
+ * SMC_E_STATE while a resampling is pending.  Both synchronise. */
 int smc_write_state(smc_ctx *ctx, const void *src, int on_device);
 int smc_write_log_weight(smc_ctx *ctx, const void *src, int on_device);
+
+/* Checkpoint / resume.  A checkpoint holds the complete sampler state after
+ * the last queued call: the device state block (iteration, buffers,
+ * normaliser, evidence and path-sampling accumulators, annealing alpha_t,
+ * pending-resampling flag), the record ring, the current particle state and
+ * log-weights and the pending ancestors.  The random numbers are
+ * counter-based, so the checkpoint needs no generator state: restoring it
+ * into a context created with the same configuration (and given the same
+ * data with smc_set_data first, CV models) continues bit-identically to an
+ * uninterrupted run.
+ * smc_checkpoint: h_blob == NULL stores the size in *bytes; otherwise
+ * *bytes is the capacity of h_blob (SMC_E_ARG and the size in *bytes when
+ * too small) and becomes the size written.  Synchronises.
+ * smc_restore: SMC_E_ARG when the blob does not match the context's
+ * configuration (model, precision, scheme, N, seed, stream id, record ring);
+ * SMC_E_STATE when the CV data do not reach the checkpoint's iteration.
+ * Not available with SMC_FLAG_RECORD (SMC_E_ARG): the gradient recording is
+ * not part of a checkpoint. */
+int smc_checkpoint(smc_ctx *ctx, void *h_blob, size_t *bytes);
+int smc_restore(smc_ctx *ctx, const void *h_blob, size_t bytes);
 
 /* Gradient of the log-likelihood estimate (CV models, SMC_FLAG_RECORD) with
  * respect to theta = (sd_pos, sd_vel, obs_scale, obs_df) at the context's

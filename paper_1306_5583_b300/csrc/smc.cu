@@ -15,6 +15,7 @@
 #include "gmm_kernels.cuh"
 #include "batch_kernels.cuh"
 #include "grad_kernels.cuh"
+#include "weight_kernels.cuh"
 
 using namespace smc;
 
@@ -44,7 +45,7 @@ int ceil_log2(int64_t n) {
 }
 
 struct Layout {
-    size_t st, rec, part, x, lw, anc, Q, tsum, bsum, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, alpha;
+    size_t st, rec, part, x, lw, anc, Q, tsum, bsum, inc, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, alpha;
     size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, total;
     int ck;           // steps between checkpoints (record mode)
     int64_t nck;      // checkpoints
@@ -115,6 +116,7 @@ Layout make_layout(const smc_config *c) {
     L.Q = take((size_t)n * 8);
     L.tsum = take((size_t)kScanSlots * L.ntiles_status * 8);
     L.bsum = take((size_t)kMaxCoopGrid * 8);  // block sums of the cooperative kernels
+    L.inc = take((size_t)L.ld * rs);            // staged increments of smc_add_log_weight
     L.cnt = take(sorts ? (size_t)L.nbuckets * 4 : 0);
     L.fill = take(sorts ? (size_t)L.nbuckets * 4 : 0);
     L.boff = take(sorts ? (size_t)L.nbuckets * 8 : 0);
@@ -211,8 +213,8 @@ __global__ void reset_state_kernel(DevState *st) {
 
 // the resampling threshold for the FP32 finalize: a DF value and a mode
 // (always at >= 1, never at <= 0, otherwise compare ESS < threshold N)
-template <typename R>
-void set_threshold_df(PfArgs<R> &a, double thr) {
+template <class A>
+void set_threshold_df(A &a, double thr) {
     a.thr_mode = thr >= 1.0 ? 1 : (thr <= 0.0 ? 2 : 0);
     a.thr_df[0] = (float)thr;
     a.thr_df[1] = (float)(thr - (double)a.thr_df[0]);
@@ -436,6 +438,35 @@ int launch_resample(smc_ctx *c, int gate) {
 
 int resample_any(smc_ctx *c, int gate) {
     return (c->cfg.precision == 32) ? launch_resample<float>(c, gate) : launch_resample<double>(c, gate);
+}
+
+// lw += (staged increments in c->inc), normaliser and decision again
+template <typename R>
+int launch_add_log_weight(smc_ctx *c) {
+    AddArgs<R> a{};
+    a.n = c->cfg.n_particles;
+    const bool gmm = c->cfg.model == SMC_MODEL_GMM;
+    for (int b = 0; b < 2; ++b) {
+        a.lw[b] = static_cast<const R *>(c->lw[b]);
+        a.lw_w[b] = static_cast<R *>(c->lw[b]);
+        const R *base = static_cast<const R *>(c->x[b]);
+        a.h[b][0] = gmm ? nullptr : base;
+        a.h[b][1] = gmm ? nullptr : base + c->L.ld;
+    }
+    a.incw = reinterpret_cast<const R *>(c->ws + c->L.inc);
+    a.rec = c->rec;
+    a.rec_cap = c->cfg.max_records;
+    a.st = c->st;
+    a.part = c->part;
+    a.threshold = c->cfg.threshold;
+    set_threshold_df(a, c->cfg.threshold);
+    a.gmm = gmm ? 1 : 0;
+    add_log_weight_kernel<R><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(a);
+    return cuda_check(cudaGetLastError());
+}
+
+int add_log_weight_any(smc_ctx *c) {
+    return (c->cfg.precision == 32) ? launch_add_log_weight<float>(c) : launch_add_log_weight<double>(c);
 }
 
 int read_state(smc_ctx *c) {
@@ -810,20 +841,134 @@ int smc_write_state(smc_ctx *c, const void *src, int on_device) {
 
 int smc_write_log_weight(smc_ctx *c, const void *src, int on_device) {
     if (!c || !src) return SMC_E_ARG;
+    if (!c->initialized) return SMC_E_STATE;
     int rc = read_state(c);
     if (rc) return rc;
+    if (c->host_st.ready) return SMC_E_STATE;  // a resampling is pending
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    rc = cuda_check(cudaMemcpyAsync(c->lw[c->host_st.cur_lw & 1], src, (size_t)c->cfg.n_particles * c->L.rsize, k,
-                                    c->stream));
+    const size_t bytes = (size_t)c->cfg.n_particles * c->L.rsize;
+    rc = cuda_check(cudaMemcpyAsync(c->lw[c->host_st.cur_lw & 1], src, bytes, k, c->stream));
+    // then the normaliser, ESS, evidence increment and decision of the new weights (a zero increment)
+    if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + c->L.inc, 0, bytes, c->stream));
+    if (!rc) rc = add_log_weight_any(c);
     if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream));
     return rc;
 }
 
 int smc_add_log_weight(smc_ctx *c, const void *incw, int on_device) {
-    (void)c;
-    (void)incw;
-    (void)on_device;
-    return SMC_E_ARG;  // implemented with the generic reweighting kernel
+    if (!c || !incw) return SMC_E_ARG;
+    if (!c->initialized) return SMC_E_STATE;
+    int rc = read_state(c);
+    if (rc) return rc;
+    if (c->host_st.ready) return SMC_E_STATE;  // a resampling is pending
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    rc = cuda_check(cudaMemcpyAsync(c->ws + c->L.inc, incw, (size_t)c->cfg.n_particles * c->L.rsize, k, c->stream));
+    if (!rc) rc = add_log_weight_any(c);
+    if (!rc && !on_device) rc = cuda_check(cudaStreamSynchronize(c->stream));  // the host buffer may go away
+    return rc;
+}
+
+// ---- checkpoint / restore ----
+struct CkptHeader {
+    char magic[8];  // "SMCCKPT1"
+    int32_t model, precision, scheme, d;
+    int64_t n;
+    int32_t max_records, t_host;
+    uint64_t seed;
+    uint32_t stream_id, state_size;
+    uint64_t total;
+};
+
+static size_t ckpt_bytes(const smc_ctx *c) {
+    const size_t n = (size_t)c->cfg.n_particles, rs = c->L.rsize;
+    return sizeof(CkptHeader) + sizeof(DevState) + sizeof(smc_record) * (size_t)c->cfg.max_records +
+           (size_t)c->L.d * n * rs + n * rs + n * 4;
+}
+
+int smc_checkpoint(smc_ctx *c, void *h_blob, size_t *bytes) {
+    if (!c || !bytes) return SMC_E_ARG;
+    if (!c->initialized) return SMC_E_STATE;
+    if (recording(c)) return SMC_E_ARG;
+    const size_t need = ckpt_bytes(c);
+    if (!h_blob) {
+        *bytes = need;
+        return SMC_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return SMC_E_ARG;
+    }
+    int rc = read_state(c);
+    if (rc) return rc;
+    char *p = static_cast<char *>(h_blob);
+    CkptHeader h{};
+    std::memcpy(h.magic, "SMCCKPT1", 8);
+    h.model = c->cfg.model;
+    h.precision = c->cfg.precision;
+    h.scheme = c->cfg.scheme;
+    h.d = c->L.d;
+    h.n = c->cfg.n_particles;
+    h.max_records = c->cfg.max_records;
+    h.t_host = c->t_host;
+    h.seed = c->cfg.seed;
+    h.stream_id = c->cfg.stream_id;
+    h.state_size = (uint32_t)sizeof(DevState);
+    h.total = need;
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    std::memcpy(p, &c->host_st, sizeof(DevState));
+    p += sizeof(DevState);
+    const size_t n = (size_t)c->cfg.n_particles, rs = c->L.rsize;
+    rc = cuda_check(cudaMemcpyAsync(p, c->rec, sizeof(smc_record) * (size_t)c->cfg.max_records,
+                                    cudaMemcpyDeviceToHost, c->stream));
+    p += sizeof(smc_record) * (size_t)c->cfg.max_records;
+    if (!rc) rc = copy_rows(c, p, c->x[c->host_st.cur & 1], c->L.d, true, 0);
+    p += (size_t)c->L.d * n * rs;
+    if (!rc) rc = copy_out(c, p, c->lw[c->host_st.cur_lw & 1], n * rs, 0);
+    p += n * rs;
+    if (!rc) rc = copy_out(c, p, c->anc, n * 4, 0);
+    if (!rc) *bytes = need;
+    return rc;
+}
+
+int smc_restore(smc_ctx *c, const void *h_blob, size_t bytes) {
+    if (!c || !h_blob) return SMC_E_ARG;
+    if (recording(c)) return SMC_E_ARG;
+    if (bytes < sizeof(CkptHeader)) return SMC_E_ARG;
+    CkptHeader h;
+    std::memcpy(&h, h_blob, sizeof(h));
+    if (std::memcmp(h.magic, "SMCCKPT1", 8) != 0 || h.model != c->cfg.model || h.precision != c->cfg.precision ||
+        h.scheme != c->cfg.scheme || h.d != c->L.d || h.n != c->cfg.n_particles ||
+        h.max_records != c->cfg.max_records || h.seed != c->cfg.seed || h.stream_id != c->cfg.stream_id ||
+        h.state_size != sizeof(DevState) || h.total != ckpt_bytes(c) || bytes < h.total)
+        return SMC_E_ARG;
+    if (c->cfg.model != SMC_MODEL_GMM && h.t_host >= c->n_obs) return SMC_E_STATE;  // data first
+    const char *p = static_cast<const char *>(h_blob) + sizeof(h);
+    DevState s;
+    std::memcpy(&s, p, sizeof(s));
+    p += sizeof(s);
+    // counters of kernels in flight are idle at a checkpoint; start them clean
+    s.error = 0;
+    s.ticket = 0;
+    s.grid_count = 0;
+    s.grid_depart = 0;
+    for (int k = 0; k < kScanSlots; ++k) s.scan_ticket[k] = 0;
+    const size_t n = (size_t)c->cfg.n_particles, rs = c->L.rsize;
+    int rc = cuda_check(cudaMemcpyAsync(c->st, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(c->rec, p, sizeof(smc_record) * (size_t)c->cfg.max_records,
+                                             cudaMemcpyHostToDevice, c->stream));
+    p += sizeof(smc_record) * (size_t)c->cfg.max_records;
+    if (!rc) rc = copy_rows(c, c->x[s.cur & 1], p, c->L.d, false, 0);
+    p += (size_t)c->L.d * n * rs;
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(c->lw[s.cur_lw & 1], p, n * rs, cudaMemcpyHostToDevice, c->stream));
+    p += n * rs;
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(c->anc, p, n * 4, cudaMemcpyHostToDevice, c->stream));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream));
+    if (rc) return rc;
+    c->t_host = h.t_host;
+    c->initialized = 1;
+    c->host_st = s;
+    return SMC_OK;
 }
 
 int smc_sync(smc_ctx *c) {

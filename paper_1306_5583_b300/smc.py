@@ -82,6 +82,8 @@ _SIGS = {
     "smc_write_state": (_I, [_P, _P, _I]),
     "smc_write_log_weight": (_I, [_P, _P, _I]),
     "smc_sync": (_I, [_P]),
+    "smc_checkpoint": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "smc_restore": (_I, [_P, _P, ctypes.c_size_t]),
     "smc_error_string": (ctypes.c_char_p, [_I]),
     "smc_philox4x32_10": (_I, [_P, ctypes.POINTER(ctypes.c_uint32), _P, ctypes.c_int64, _P]),
     "smc_pf_grad": (_I, [_P, _P]),
@@ -323,9 +325,23 @@ class Sampler:
         return out
 
     def add_log_weight(self, incw):
+        """lw += incw for the current iteration (normaliser, ESS, decision again)."""
         a = np.ascontiguousarray(np.asarray(incw, dtype=self.rdtype))
         assert a.shape == (self.n,)
         check(lib().smc_add_log_weight(self.ctx, a.ctypes.data_as(_P), 0), "smc_add_log_weight")
+
+    def checkpoint(self):
+        """The complete sampler state as bytes (see smc_checkpoint)."""
+        size = ctypes.c_size_t(0)
+        check(lib().smc_checkpoint(self.ctx, None, ctypes.byref(size)), "smc_checkpoint")
+        buf = ctypes.create_string_buffer(size.value)
+        check(lib().smc_checkpoint(self.ctx, ctypes.cast(buf, _P), ctypes.byref(size)), "smc_checkpoint")
+        return buf.raw[:size.value]
+
+    def restore(self, blob):
+        """Continue from a checkpoint of a sampler with the same configuration."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        check(lib().smc_restore(self.ctx, ctypes.cast(buf, _P), len(blob)), "smc_restore")
 
 
 def philox4x32_10(ctr, key):

@@ -1,0 +1,138 @@
+"""GPU tests of the state-changing calls of the boundary: WeightSet::
+add_log_weight (Sec. 4.1.6), replacing the log-weights, and checkpoint /
+resume (a restored sampler continues bit-identically)."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import assert_close, cv_params, make_pf, need_gpu, torch
+from oracle import weights as ow
+from paper_1306_5583_b300 import smc, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _moved(precision, n=6000, T=12, threshold=0.3, seed=4, steps=4):
+    """A filter after `steps` full iterations and one more move (no
+    resampling pending)."""
+    s, y, op = make_pf(n, T, precision, threshold=threshold, seed=seed)
+    s.initialize()
+    for _ in range(steps):
+        s.move()
+        s.resample()
+    s.move()
+    return s
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_add_log_weight_matches_oracle(precision):
+    need_gpu()
+    s = _moved(precision)
+    rel = 1e-12 if precision == 64 else 1e-5
+    lw = s.log_weight()
+    x = s.state().astype(np.float64)
+    before = s.history(2)
+    rec0, prev = before[-1], before[-2]
+    inc = (np.random.default_rng(1).standard_normal(s.n) * 0.7).astype(lw.dtype)
+    s.add_log_weight(inc)
+    lw2 = s.log_weight()
+    assert np.array_equal(lw2, (lw + inc).astype(lw.dtype))
+    rec = s.history(1)[0]
+    assert rec["t"] == rec0["t"] and rec["status"] == 0
+    m, L = ow.log_sum_exp(lw2.astype(np.float64))
+    W = np.exp(lw2.astype(np.float64) - L)
+    assert_close(rec["L"], L, rel, "L")
+    assert_close(rec["ess"], 1.0 / np.sum(W * W), 10 * rel, "ESS")
+    assert_close([rec["mean_x"], rec["mean_y"]], [np.sum(W * x[0]), np.sum(W * x[1])], 10 * rel, "means")
+    # the evidence increment of iteration t is replaced, not added
+    assert abs(rec["logZ"] - (prev["logZ"] + rec["L"])) < 1e-9
+    assert rec["resampled"] == (rec["ess"] < 0.3 * s.n)
+    s.resample()
+    s.move()  # the filter carries on
+    assert s.history(1)[0]["status"] == 0
+
+
+def test_add_log_weight_after_queued_resampling_is_rejected():
+    need_gpu()
+    s, y, op = make_pf(2000, 8, 32, threshold=1.0, seed=1)
+    s.initialize()  # t = 0 resampled (threshold 1): the gather is pending
+    with pytest.raises(smc.SMCError) as e:
+        s.add_log_weight(np.zeros(s.n, np.float32))
+    assert e.value.code == smc.E_STATE
+
+
+def test_write_log_weight_recomputes_the_normaliser():
+    need_gpu()
+    s = _moved(64)
+    prev = s.history(2)[-2]
+    lw = np.random.default_rng(2).standard_normal(s.n) * 2.0 - 5.0
+    s.write_log_weight(lw)
+    assert np.array_equal(s.log_weight(), lw)
+    rec = s.history(1)[0]
+    m, L = ow.log_sum_exp(lw)
+    assert_close(rec["L"], L, 1e-12, "L")
+    assert abs(rec["logZ"] - (prev["logZ"] + L)) < 1e-9
+
+
+def _snapshot(s, T):
+    return (s.state(), s.log_weight(), s.ancestors(), s.log_evidence(), [tuple(sorted(r.items())) for r in s.history(T)])
+
+
+@pytest.mark.parametrize("scheme,precision", [("systematic", 32), ("multinomial", 32), ("residual", 64)])
+def test_checkpoint_resume_is_bit_identical_pf(scheme, precision):
+    need_gpu()
+    n, T, k1 = 20000, 30, 11
+    p = cv_params()
+    _, y = workloads.cv_data(T, seed=3, **p)
+    mk = lambda: smc.Sampler(smc.make_config(model="cv", n=n, precision=precision, scheme=scheme, threshold=0.5,
+                                             seed=7, max_data=T, max_records=T, cv=p))
+    a = mk()
+    a.set_data(y)
+    a.initialize()
+    a.iterate(k1)
+    blob = a.checkpoint()
+    a.iterate(T - 1 - k1)
+    ref = _snapshot(a, T)
+    b = mk()
+    b.set_data(y)
+    b.restore(blob)
+    assert b.iteration() == k1
+    b.iterate(T - 1 - k1)
+    got = _snapshot(b, T)
+    for u, v in zip(ref, got):
+        if isinstance(u, np.ndarray):
+            assert np.array_equal(u, v)
+        else:
+            assert u == v
+
+
+def test_checkpoint_resume_is_bit_identical_gmm():
+    need_gpu()
+    from test_gpu_gmm import make_gmm
+    T, k1 = 40, 17
+    a, y, _ = make_gmm(4096, nd=300, T=T, seed=5)
+    a.initialize()
+    a.iterate(k1)
+    blob = a.checkpoint()
+    a.iterate(T - k1)
+    ref = (a.state(), a.log_weight(), a.log_evidence(), a.path_sampling())
+    b, _, _ = make_gmm(4096, nd=300, T=T, seed=5)
+    b.restore(blob)
+    b.iterate(T - k1)
+    got = (b.state(), b.log_weight(), b.log_evidence(), b.path_sampling())
+    for u, v in zip(ref, got):
+        assert np.array_equal(np.asarray(u), np.asarray(v))
+
+
+def test_restore_rejects_another_configuration():
+    need_gpu()
+    s, y, op = make_pf(3000, 10, 32, seed=1)
+    s.initialize()
+    blob = s.checkpoint()
+    other, _, _ = make_pf(3000, 10, 32, seed=2)
+    with pytest.raises(smc.SMCError) as e:
+        other.restore(blob)
+    assert e.value.code == smc.E_ARG
+    with pytest.raises(smc.SMCError):
+        s.restore(blob[:100])
