@@ -259,6 +259,20 @@ int smc_write_log_weight(smc_ctx *ctx, const void *src, int on_device);
 int smc_checkpoint(smc_ctx *ctx, void *h_blob, size_t *bytes);
 int smc_restore(smc_ctx *ctx, const void *h_blob, size_t bytes);
 
+/* Tempered log-target of the Gaussian-mixture model and its gradient (the
+ * target of the Langevin move, Sec. 5.2 model), at `count` caller-given
+ * points in unconstrained coordinates u = (mu_1..r, log lambda_1..r,
+ * z_1..r-1), z_j = log(omega_j / omega_r):
+ *   gamma(u) = log prior(theta) + alpha l(theta) + sum_j log lambda_j
+ *              + sum_j log omega_j   (the last two: log |d theta / d u|),
+ * l the log-likelihood of the context's data.  d_u: (3r - 1) rows of
+ * `count` values (row-major, the context's precision, device); d_logt:
+ * count values; d_grad: (3r - 1) rows of count values (d gamma / d u).  The
+ * gradient is the hand-written adjoint through the per-datum log-sum-exp.
+ * 0 <= alpha <= 1.  Asynchronous on the context's stream; SMC_E_STATE
+ * before smc_set_data; SMC_E_ARG for other models. */
+int smc_gmm_log_target(smc_ctx *ctx, const void *d_u, int64_t count, double alpha, void *d_logt, void *d_grad);
+
 /* Gradient of the log-likelihood estimate (CV models, SMC_FLAG_RECORD) with
  * respect to theta = (sd_pos, sd_vel, obs_scale, obs_df) at the context's
  * parameters, after a complete forward run (smc_initialize, then

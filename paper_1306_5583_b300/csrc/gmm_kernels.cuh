@@ -416,6 +416,61 @@ __device__ __forceinline__ uint32_t mala_move(const GmmArgs<R> &a, Theta<R, NC> 
     return 0u;
 }
 
+// ---- tempered log-target and its gradient at given points -------------------
+// gamma_alpha(u) = log-prior(theta(u)) + alpha l(theta(u)) + log |d theta / d u|
+// in u = (mu, log lambda, z), z_j = log(omega_j / omega_r): the target of the
+// Langevin move, with the same expressions (Sec. 5.2 model; the gradient is
+// the hand-written adjoint through the per-datum log-sum-exp).  One quad of
+// lanes per point; u and grad are (3r - 1) rows of pitch ldu.
+template <typename R, int NC>
+__global__ void __launch_bounds__(kBlock) gmm_log_target_kernel(GmmArgs<R> a, const R *u, int64_t count,
+                                                                int64_t ldu, double alpha, R *logt, R *grad) {
+    constexpr int D = 3 * NC - 1;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    const R *ys = reinterpret_cast<const R *>(s_raw);
+    stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), a.st);
+    const int q = threadIdx.x & (kQuad - 1);
+    const int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kQuad;
+    const bool active = i < count;
+    const int64_t ii = active ? i : count - 1;
+    R uu[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) uu[k] = u[(int64_t)k * ldu + ii];
+    Theta<R, NC> th;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        th.mu[j] = uu[j];
+        th.lam[j] = Math<R>::exp(uu[NC + j]);
+    }
+    R vmax = 0;
+#pragma unroll
+    for (int j = 0; j < NC - 1; ++j) vmax = fmax(vmax, uu[2 * NC + j]);
+    R sum = 0;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        th.om[j] = Math<R>::exp(((j < NC - 1) ? uu[2 * NC + j] : R(0)) - vmax);
+        sum += th.om[j];
+    }
+#pragma unroll
+    for (int j = 0; j < NC; ++j) th.om[j] = th.om[j] / sum;
+    const double lp = gmm_log_prior<R, NC>(a, th.mu, th.lam, th.om);
+    const double ll = gmm_loglik_grad_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi, th.gm,
+                                                  th.gl, th.gz);
+    if (!active || q != 0) return;
+    double jac = 0;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) jac += double(uu[NC + j]) + double(Math<R>::log(th.om[j]));
+    logt[ii] = R(lp + alpha * ll + jac);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        grad[(int64_t)j * ldu + ii] =
+            R(-(double(th.mu[j]) - a.mu0) * a.inv_sd0 * a.inv_sd0 + alpha * double(th.gm[j]));
+        grad[(int64_t)(NC + j) * ldu + ii] = R(a.shape_m1 - a.rate * double(th.lam[j]) + 1.0 + alpha * double(th.gl[j]));
+        if (j < NC - 1)
+            grad[(int64_t)(2 * NC + j) * ldu + ii] = R(1.0 - NC * double(th.om[j]) + alpha * double(th.gz[j]));
+    }
+}
+
 // ---- init: theta ~ prior, equal weights, U_0 --------------------------------
 template <typename R, int NC, bool G>
 __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {

@@ -32,6 +32,7 @@ int gmm_setup(smc_ctx *c);
 void gmm_release(smc_ctx *c);
 int gmm_launch_reweight(smc_ctx *c);
 int gmm_launch_mcmc(smc_ctx *c);
+int gmm_log_target_any(smc_ctx *c, const void *u, int64_t count, double alpha, void *logt, void *grad);
 
 constexpr size_t kAlign = 256;
 constexpr int kMaxCoopGrid = 2048;  // blocks of a cooperative launch (B300: at most 148 x 8)
@@ -971,6 +972,13 @@ int smc_restore(smc_ctx *c, const void *h_blob, size_t bytes) {
     return SMC_OK;
 }
 
+int smc_gmm_log_target(smc_ctx *c, const void *d_u, int64_t count, double alpha, void *d_logt, void *d_grad) {
+    if (!c || !d_u || !d_logt || !d_grad || count < 1 || !(alpha >= 0.0) || !(alpha <= 1.0)) return SMC_E_ARG;
+    if (c->cfg.model != SMC_MODEL_GMM) return SMC_E_ARG;
+    if (c->n_obs < 1) return SMC_E_STATE;
+    return gmm_log_target_any(c, d_u, count, alpha, d_logt, d_grad);
+}
+
 int smc_sync(smc_ctx *c) {
     if (!c) return SMC_E_ARG;
     return read_state(c);
@@ -1136,6 +1144,39 @@ int gmm_launch(smc_ctx *c, GmmKernel k) {
         case 8: return gmm_launch_nc<R, 8>(c, k);
     }
     return SMC_E_ARG;
+}
+
+// tempered log-target and gradient at count given points (rows of pitch count)
+template <typename R, int NC>
+int gmm_log_target_nc(smc_ctx *c, const void *u, int64_t count, double alpha, void *logt, void *grad) {
+    GmmArgs<R> a = gmm_args<R>(c);
+    const size_t smem = (((size_t)a.nd * sizeof(R)) + 15) & ~size_t(15);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(gmm_log_target_kernel<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const unsigned g = (unsigned)((kQuad * count + kBlock - 1) / kBlock);
+    gmm_log_target_kernel<R, NC><<<g, kBlock, smem, c->stream>>>(a, static_cast<const R *>(u), count, count, alpha,
+                                                                 static_cast<R *>(logt), static_cast<R *>(grad));
+    return cuda_check(cudaGetLastError());
+}
+
+template <typename R>
+int gmm_log_target_r(smc_ctx *c, const void *u, int64_t count, double alpha, void *logt, void *grad) {
+    switch (c->cfg.gmm.n_comp) {
+        case 1: return gmm_log_target_nc<R, 1>(c, u, count, alpha, logt, grad);
+        case 2: return gmm_log_target_nc<R, 2>(c, u, count, alpha, logt, grad);
+        case 3: return gmm_log_target_nc<R, 3>(c, u, count, alpha, logt, grad);
+        case 4: return gmm_log_target_nc<R, 4>(c, u, count, alpha, logt, grad);
+        case 5: return gmm_log_target_nc<R, 5>(c, u, count, alpha, logt, grad);
+        case 6: return gmm_log_target_nc<R, 6>(c, u, count, alpha, logt, grad);
+        case 7: return gmm_log_target_nc<R, 7>(c, u, count, alpha, logt, grad);
+        case 8: return gmm_log_target_nc<R, 8>(c, u, count, alpha, logt, grad);
+    }
+    return SMC_E_ARG;
+}
+
+int gmm_log_target_any(smc_ctx *c, const void *u, int64_t count, double alpha, void *logt, void *grad) {
+    return (c->cfg.precision == 32) ? gmm_log_target_r<float>(c, u, count, alpha, logt, grad)
+                                    : gmm_log_target_r<double>(c, u, count, alpha, logt, grad);
 }
 
 int gmm_launch_any(smc_ctx *c, GmmKernel k) {

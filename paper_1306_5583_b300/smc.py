@@ -83,6 +83,7 @@ _SIGS = {
     "smc_write_log_weight": (_I, [_P, _P, _I]),
     "smc_sync": (_I, [_P]),
     "smc_checkpoint": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "smc_gmm_log_target": (_I, [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P]),
     "smc_restore": (_I, [_P, _P, ctypes.c_size_t]),
     "smc_error_string": (ctypes.c_char_p, [_I]),
     "smc_philox4x32_10": (_I, [_P, ctypes.POINTER(ctypes.c_uint32), _P, ctypes.c_int64, _P]),
@@ -329,6 +330,21 @@ class Sampler:
         a = np.ascontiguousarray(np.asarray(incw, dtype=self.rdtype))
         assert a.shape == (self.n,)
         check(lib().smc_add_log_weight(self.ctx, a.ctypes.data_as(_P), 0), "smc_add_log_weight")
+
+    def gmm_log_target(self, u, alpha):
+        """Tempered log-target and its gradient at points u (count, 3r - 1) in
+        unconstrained coordinates (a CUDA tensor of the context's precision);
+        returns (log_target (count,), grad (count, 3r - 1)) as CUDA tensors."""
+        torch = self.torch
+        uu = u.detach().to(device=self.device, dtype=self.tdtype).t().contiguous()
+        count = uu.shape[1]
+        logt = torch.empty(count, dtype=self.tdtype, device=self.device)
+        grad = torch.empty_like(uu)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))  # u is ready
+        check(lib().smc_gmm_log_target(self.ctx, _P(uu.data_ptr()), count, float(alpha), _P(logt.data_ptr()),
+                                       _P(grad.data_ptr())), "smc_gmm_log_target")
+        self.sync()  # the outputs are complete on return
+        return logt, grad.t()
 
     def checkpoint(self):
         """The complete sampler state as bytes (see smc_checkpoint)."""
