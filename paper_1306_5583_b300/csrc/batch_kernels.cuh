@@ -29,6 +29,7 @@ struct BatchArgs {
     R *lw[2];
     int32_t *anc;
     const double *obs;
+    const R *obs_r;               // observations in R (converted after each smc_batch_set_data)
     smc_record *rec;
     Partial *part;
     unsigned long long *tsum;
@@ -48,6 +49,7 @@ struct BatchArgs {
     const uint32_t *stream_of;    // Philox stream of each filter
     const unsigned long long *mrec;  // floor((2^64 - 1) / N) of each filter
     const double *log_n;          // log N of each filter
+    const R *neg_log_n;           // -log N of each filter in R
     const int32_t *frac;          // fixed-point fraction bits of each filter
     int32_t tmax;
     int32_t stratified;
@@ -64,6 +66,8 @@ __device__ __forceinline__ PfArgs<R> filter_args(const BatchArgs<R> &B, int b) {
     a.n = B.n[b];
     a.anc = B.anc + o;
     a.obs = B.obs + 2 * B.obs_off[b];
+    a.obs_r = B.obs_r + 2 * B.obs_off[b];
+    a.neg_log_n = B.neg_log_n[b];
     a.rec = B.rec + B.rec_off[b];
     a.rec_cap = B.n_iter[b];
     a.st = &B.fst[b];

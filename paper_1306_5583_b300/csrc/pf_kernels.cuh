@@ -22,6 +22,8 @@ struct PfArgs {
     R *lw[2];            // [buffer]
     const int32_t *anc;  // ancestors of the pending resampling step
     const double *obs;   // (n_obs, 2) observations
+    const R *obs_r;      // the same in R (read by every thread: no conversion in the kernel)
+    R neg_log_n;         // -log N in R
     smc_record *rec;
     int32_t rec_cap;
     DevState *st;
@@ -90,16 +92,8 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
             load_k<R, E>(lws, i0, n, lwin);
         }
     }
-    // per-block constants converted once (no per-thread float64 work)
-    __shared__ R s_c[3];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_c[0] = R(a.obs[2 * t]);
-        s_c[1] = R(a.obs[2 * t + 1]);
-        s_c[2] = R(-a.log_n);
-    }
-    __syncthreads();
-    const R yx = s_c[0], yy = s_c[1], base_eq = s_c[2];
+    // observation y_t (one broadcast load) and -log N, already in R
+    const R yx = __ldcg(a.obs_r + 2 * t), yy = __ldcg(a.obs_r + 2 * t + 1), base_eq = a.neg_log_n;
     R s0[E], s1[E], s2[E], s3[E], lwv[E], zero[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) {

@@ -35,6 +35,12 @@ int gmm_launch_mcmc(smc_ctx *c);
 int gmm_log_target_any(smc_ctx *c, const void *u, int64_t count, double alpha, void *logt, void *grad);
 
 constexpr size_t kAlign = 256;
+
+// float copy of observations / data for the FP32 kernels
+__global__ void to_float_kernel(const double *src, float *dst, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (float)src[i];
+}
 constexpr int kMaxCoopGrid = 2048;  // blocks of a cooperative launch (B300: at most 148 x 8)
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
@@ -247,6 +253,8 @@ PfArgs<R> pf_args(smc_ctx *c) {
     }
     a.anc = c->anc;
     a.obs = c->obs;
+    a.obs_r = (sizeof(R) == 4) ? reinterpret_cast<const R *>(c->obs_f) : reinterpret_cast<const R *>(c->obs);
+    a.neg_log_n = R(-std::log((double)n));
     a.rec = c->rec;
     a.rec_cap = g.max_records;
     a.st = c->st;
@@ -718,6 +726,8 @@ int smc_iterate_host(smc_ctx *c, const double *h_obs_t, smc_record *h_record) {
         if (t >= c->cfg.max_data) return SMC_E_ARG;
         rc = cuda_check(cudaMemcpyAsync(c->obs + 2 * (size_t)t, h_obs_t, 16, cudaMemcpyHostToDevice, c->stream));
         if (rc) return rc;
+        to_float_kernel<<<1, 32, 0, c->stream>>>(c->obs + 2 * (size_t)t, c->obs_f + 2 * (size_t)t, 2);
+        if ((rc = cuda_check(cudaGetLastError()))) return rc;
         if (c->n_obs < t + 1) c->n_obs = t + 1;
     }
     rc = smc_iterate(c, 1);
@@ -1022,11 +1032,6 @@ extern "C" int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], u
 // ------------------------------------------------------------------ GMM --
 namespace {
 
-__global__ void to_float_kernel(const double *src, float *dst, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = (float)src[i];
-}
-
 double gmm_alpha(const smc_gmm_params &g, int32_t t) {
     const double x = (double)t / (double)g.n_iter;
     double a = (g.schedule == SMC_ALPHA_LINEAR) ? x : std::pow(x, g.power);
@@ -1045,8 +1050,8 @@ int gmm_setup(smc_ctx *c) {
 }
 
 int gmm_on_data(smc_ctx *c) {
-    if (c->cfg.model != SMC_MODEL_GMM) return SMC_OK;
-    const int64_t n = c->n_obs;
+    // float copy of the data for the FP32 kernels (every model)
+    const int64_t n = (c->cfg.model == SMC_MODEL_GMM) ? c->n_obs : 2 * c->n_obs;
     to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->obs, c->obs_f, n);
     return cuda_check(cudaGetLastError());
 }
@@ -1220,7 +1225,8 @@ struct BatchPlan {
     std::vector<unsigned long long> mrec;  // floor((2^64 - 1) / N) per filter
     std::vector<double> log_n;
     size_t o_fst, o_bs, o_rec, o_part, o_tsum, o_x, o_lw, o_anc, o_obs, o_n, o_off, o_obs_off, o_rec_off, o_T,
-        o_tfirst, o_sfirst, o_tf, o_stf, o_act, o_acts, o_stream, o_mrec, o_logn, o_frac, total = 0;
+        o_tfirst, o_sfirst, o_tf, o_stf, o_act, o_acts, o_stream, o_mrec, o_logn, o_nlogn, o_obs_f, o_frac,
+        total = 0;
     size_t rsize = 4;
 };
 
@@ -1309,6 +1315,7 @@ bool batch_plan(const smc_config *cfg, const int64_t *n, const int32_t *T, int32
     P.o_lw = take(2 * (size_t)P.ntot * P.rsize);
     P.o_anc = take(4 * (size_t)P.ntot);
     P.o_obs = take(16 * (size_t)oo);
+    P.o_obs_f = take(8 * (size_t)oo);  // float copy (FP32 batches)
     P.o_n = take(8 * (size_t)nf);
     P.o_off = take(8 * (size_t)nf);
     P.o_obs_off = take(8 * (size_t)nf);
@@ -1323,6 +1330,7 @@ bool batch_plan(const smc_config *cfg, const int64_t *n, const int32_t *T, int32
     P.o_stream = take(4 * (size_t)nf);
     P.o_mrec = take(8 * (size_t)nf);
     P.o_logn = take(8 * (size_t)nf);
+    P.o_nlogn = take(8 * (size_t)nf);  // -log N in the batch precision
     P.o_frac = take(4 * (size_t)nf);
     P.total = off_b;
     return true;
@@ -1401,6 +1409,8 @@ BatchArgs<R> batch_args(smc_batch *bt) {
     B.stream_of = at<uint32_t>(bt, P.o_stream);
     B.mrec = at<unsigned long long>(bt, P.o_mrec);
     B.log_n = at<double>(bt, P.o_logn);
+    B.neg_log_n = at<R>(bt, P.o_nlogn);
+    B.obs_r = (sizeof(R) == 4) ? at<R>(bt, P.o_obs_f) : reinterpret_cast<const R *>(B.obs);
     B.frac = at<int32_t>(bt, P.o_frac);
     B.tmax = P.tmax;
     B.stratified = (g.scheme == SMC_STRATIFIED) ? 1 : 0;
@@ -1528,6 +1538,13 @@ int smc_batch_create(smc_batch **out, const smc_config *cfg, const int64_t *n, c
     if (!rc) rc = up(P.o_stream, P.stream_of.data(), 4 * (size_t)nf);
     if (!rc) rc = up(P.o_mrec, P.mrec.data(), 8 * (size_t)nf);
     if (!rc) rc = up(P.o_logn, P.log_n.data(), 8 * (size_t)nf);
+    std::vector<double> nl64(nf);
+    std::vector<float> nl32(nf);
+    for (int32_t i = 0; i < nf; ++i) {
+        nl64[i] = -P.log_n[i];
+        nl32[i] = (float)nl64[i];
+    }
+    if (!rc) rc = (P.rsize == 4) ? up(P.o_nlogn, nl32.data(), 4 * (size_t)nf) : up(P.o_nlogn, nl64.data(), 8 * (size_t)nf);
     if (!rc) rc = up(P.o_frac, P.frac.data(), 4 * (size_t)nf);
     if (!rc) rc = cuda_check(cudaStreamSynchronize(bt->stream));
     if (rc) {
@@ -1549,8 +1566,14 @@ int smc_batch_set_data(smc_batch *bt, int32_t filter, const double *obs, int on_
     if (!bt || !obs || filter < 0 || filter >= bt->P.nf) return SMC_E_ARG;
     const int32_t i = bt->inv[filter];
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    int rc = cuda_check(cudaMemcpyAsync(at<double>(bt, bt->P.o_obs) + 2 * bt->P.obs_off[i], obs,
-                                        16 * (size_t)bt->P.T[i], k, bt->stream));
+    double *dst = at<double>(bt, bt->P.o_obs) + 2 * bt->P.obs_off[i];
+    int rc = cuda_check(cudaMemcpyAsync(dst, obs, 16 * (size_t)bt->P.T[i], k, bt->stream));
+    if (!rc && bt->P.rsize == 4) {
+        const int64_t m = 2 * (int64_t)bt->P.T[i];
+        to_float_kernel<<<(unsigned)((m + 255) / 256), 256, 0, bt->stream>>>(
+            dst, at<float>(bt, bt->P.o_obs_f) + 2 * bt->P.obs_off[i], m);
+        rc = cuda_check(cudaGetLastError());
+    }
     if (!rc && !on_device) rc = cuda_check(cudaStreamSynchronize(bt->stream));
     return rc;
 }
