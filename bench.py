@@ -71,6 +71,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, device=None):
+    """Largest value of x over all ranks of the process group (the job's
+    time is that of its slowest replica); x itself on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ws, n, ms_per_step):
+    """Whole-job particle-updates/s: every rank advances its own replica of
+    n particles by one iteration per step."""
+    return ws * n / (ms_per_step * 1e-3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -216,14 +234,9 @@ def run_ours(args):
             ms_per_step=float(np.mean(r["step_ms"])),
             move_us=float(np.mean(r["move_ms"]) * 1e3),
             resample_fraction=r["resample_frac"])
-    total_ms = float(np.sum(main["step_ms"]))
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(main["step_ms"])), dev)
     ms_per_step = total_ms / args.steps
-    value = ws * n / (ms_per_step * 1e-3)
+    value = job_throughput(ws, n, ms_per_step)
 
     # dominant kernel: the fused move/weight kernel (its own events)
     move_us = float(np.mean(main["move_ms"]) * 1e3)
@@ -484,7 +497,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scheme", default="systematic")
-    ap.add_argument("--n", type=int, default=N_FULL)
+    ap.add_argument("--n-particles", dest="n", type=int, default=N_FULL)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the GMM, batched and gradient sections")
     ap.add_argument("--schemes", default="systematic,stratified,multinomial,residual")
