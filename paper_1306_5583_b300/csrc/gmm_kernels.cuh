@@ -55,9 +55,33 @@ struct GmmArgs {
     double mu0, sd0, inv_sd0, lp_const, shape_m1, rate;
     double half_nd_log2pi;  // nd log(2 pi) / 2
     double mala_eps;        // Langevin step size
+    // the same constants in float for the FP32 instantiation (no per-thread float64)
+    float mu0_f, inv_sd0_f, lp_const_f, shape_m1_f, rate_f, mala_eps_f;
+    float hnl_f[2];         // half_nd_log2pi as a double-float value
     uint2 key;
     uint32_t stream;
 };
+
+// Model constants in the kernel's precision R (the FP64 instantiation keeps
+// its float64 values; the FP32 one uses the float copies).
+template <typename R>
+struct GmmC {
+    R mu0, inv_sd0, lp_const, shape_m1, rate, eps;
+};
+template <typename R>
+__device__ __forceinline__ GmmC<R> gmm_c(const GmmArgs<R> &a) {
+    if constexpr (sizeof(R) == 8) return GmmC<R>{a.mu0, a.inv_sd0, a.lp_const, a.shape_m1, a.rate, a.mala_eps};
+    else return GmmC<R>{a.mu0_f, a.inv_sd0_f, a.lp_const_f, a.shape_m1_f, a.rate_f, a.mala_eps_f};
+}
+
+// Metropolis log-ratio of the tempered target from (log-prior, log-likelihood)
+// pairs.  FP64: as written; FP32: grouped so that the nearly equal
+// log-likelihoods cancel exactly (Sterbenz) before the multiplication by alpha.
+template <typename R>
+__device__ __forceinline__ R mh_delta(R lp2, R lp, R ll2, R ll, R a_t) {
+    if constexpr (sizeof(R) == 8) return (lp2 + a_t * ll2) - (lp + a_t * ll);
+    else return (lp2 - lp) + a_t * (ll2 - ll);
+}
 
 // moves of the mcmc kernel
 constexpr int kMoveRW = 0;
@@ -100,11 +124,32 @@ struct Kahan {
     }
 };
 
+// The quad's four partial sums (Kahan pairs s - c) added up and converted
+// from log2 to log, minus nd log(2 pi) / 2: float64 on the FP64 path,
+// double-float (rounded to float at the end) on the FP32 path.
+template <typename R>
+__device__ __forceinline__ R quad_log_sum(R s, R c, const GmmArgs<R> &a) {
+    if constexpr (sizeof(R) == 8) {
+        double v = double(s) - double(c);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        return v * kLn2 - a.half_nd_log2pi;
+    } else {
+        constexpr float kLn2Hi = (float)kLn2;
+        constexpr float kLn2Lo = (float)(kLn2 - (double)kLn2Hi);
+        DF v = two_sum(s, -c);
+        v = df_add(v, df_shfl_xor(v, 1));
+        v = df_add(v, df_shfl_xor(v, 2));
+        const DF r = df_add(df_mul(v, DF{kLn2Hi, kLn2Lo}), DF{-a.hnl_f[0], -a.hnl_f[1]});
+        return r.hi + r.lo;
+    }
+}
+
 // Log-likelihood of one particle: lanes q = 0..3 of a quad each take data
-// k = q, q + 4, ...; returns the full l(theta) (float64) in all four lanes.
+// k = q, q + 4, ...; returns the full l(theta) in all four lanes.
 template <typename R, int NC>
-__device__ __forceinline__ double gmm_loglik_quad(const R (&mu)[NC], const R (&lam)[NC], const R (&om)[NC],
-                                                  const R *__restrict__ ys, int nd, int q, double half_nd_log2pi) {
+__device__ __forceinline__ R gmm_loglik_quad(const R (&mu)[NC], const R (&lam)[NC], const R (&om)[NC],
+                                             const R *__restrict__ ys, int nd, int q, const GmmArgs<R> &ga) {
     R c2[NC], h2[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
@@ -135,10 +180,7 @@ __device__ __forceinline__ double gmm_loglik_quad(const R (&mu)[NC], const R (&l
         }
         acc.add(msum + Base2<R>::lg2(prod));
     }
-    double v = double(acc.s) - double(acc.c);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    return v * kLn2 - half_nd_log2pi;
+    return quad_log_sum<R>(acc.s, acc.c, ga);
 }
 
 // Log-likelihood and its gradient in (mu, log lambda, log(omega_j / omega_r))
@@ -146,10 +188,9 @@ __device__ __forceinline__ double gmm_loglik_quad(const R (&mu)[NC], const R (&l
 // sum_k rho_kj lambda_j (y_k - mu_j), sum_k rho_kj (1 - lambda_j (y_k - mu_j)^2) / 2
 // and sum_k (rho_kj - omega_j), with rho the responsibilities.
 template <typename R, int NC>
-__device__ __forceinline__ double gmm_loglik_grad_quad(const R (&mu)[NC], const R (&lam)[NC], const R (&om)[NC],
-                                                       const R *__restrict__ ys, int nd, int q,
-                                                       double half_nd_log2pi, R (&gm)[NC], R (&gl)[NC],
-                                                       R (&gz)[NC]) {
+__device__ __forceinline__ R gmm_loglik_grad_quad(const R (&mu)[NC], const R (&lam)[NC], const R (&om)[NC],
+                                                  const R *__restrict__ ys, int nd, int q, const GmmArgs<R> &ga,
+                                                  R (&gm)[NC], R (&gl)[NC], R (&gz)[NC]) {
     R c2[NC], h2[NC], sd[NC], sl[NC], sr[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
@@ -191,9 +232,7 @@ __device__ __forceinline__ double gmm_loglik_grad_quad(const R (&mu)[NC], const 
         }
         acc.add(msum + Base2<R>::lg2(prod));
     }
-    double v = double(acc.s) - double(acc.c);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    const R total = quad_log_sum<R>(acc.s, acc.c, ga);
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         sd[j] += __shfl_xor_sync(0xffffffffu, sd[j], 1);
@@ -206,22 +245,23 @@ __device__ __forceinline__ double gmm_loglik_grad_quad(const R (&mu)[NC], const 
         gl[j] = R(0.5) * (sr[j] - lam[j] * sl[j]);
         gz[j] = sr[j] - R(nd) * om[j];
     }
-    return v * kLn2 - half_nd_log2pi;
+    return total;
 }
 
 template <typename R, int NC>
-__device__ __forceinline__ double gmm_log_prior(const GmmArgs<R> &a, const R (&mu)[NC], const R (&lam)[NC],
-                                                const R (&om)[NC]) {
-    double lp = a.lp_const;
+__device__ __forceinline__ R gmm_log_prior(const GmmArgs<R> &a, const R (&mu)[NC], const R (&lam)[NC],
+                                           const R (&om)[NC]) {
+    const GmmC<R> k = gmm_c<R>(a);
+    R lp = k.lp_const;
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        const double z = (double(mu[j]) - a.mu0) * a.inv_sd0;
-        lp += -0.5 * z * z - a.rate * double(lam[j]);
-        if (a.shape_m1 != 0.0) lp += a.shape_m1 * double(Math<R>::log(lam[j]));
+        const R z = (mu[j] - k.mu0) * k.inv_sd0;
+        lp += R(-0.5) * z * z - k.rate * lam[j];
+        if (k.shape_m1 != R(0)) lp += k.shape_m1 * Math<R>::log(lam[j]);
         bad |= !(lam[j] > R(0)) || !(om[j] >= R(0));
     }
-    return bad ? -INFINITY : lp;
+    return bad ? Math<R>::neg_inf() : lp;
 }
 
 // r standard normals from draws 0 and 1 of (index, t, tag)
@@ -323,23 +363,24 @@ __device__ __forceinline__ void store_theta(R *x, int64_t ld, int64_t i, const T
 // log(omega_j / omega_r), targeting gamma = log-prior + alpha l + sum log lambda
 // + sum log omega, from the cached likelihood gradient at the current point.
 // Returns 1 when accepted.  All four lanes of a quad take the same decision.
+// Arithmetic in R (float64 on the FP64 path).
 template <typename R, int NC>
-__device__ __forceinline__ uint32_t mala_move(const GmmArgs<R> &a, Theta<R, NC> &th, double &lp, double &ll,
-                                              double a_t, uint32_t ii, uint32_t t, const R *ys, int q) {
+__device__ __forceinline__ uint32_t mala_move(const GmmArgs<R> &a, Theta<R, NC> &th, R &lp, R &ll, R a_t,
+                                              uint32_t ii, uint32_t t, const R *ys, int q) {
     constexpr int D = 3 * NC - 1;
-    const double eps = a.mala_eps, h = 0.5 * eps * eps;
-    const double a_m1 = a.shape_m1;
+    const GmmC<R> k = gmm_c<R>(a);
+    const R eps = k.eps, h = R(0.5) * eps * eps;
     // gradient of gamma at the current point
     R u[D], g[D], xi[D];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         u[j] = th.mu[j];
         u[NC + j] = Math<R>::log(th.lam[j]);
-        g[j] = R(-(double(th.mu[j]) - a.mu0) * a.inv_sd0 * a.inv_sd0 + a_t * double(th.gm[j]));
-        g[NC + j] = R(a_m1 - a.rate * double(th.lam[j]) + 1.0 + a_t * double(th.gl[j]));
+        g[j] = -(th.mu[j] - k.mu0) * k.inv_sd0 * k.inv_sd0 + a_t * th.gm[j];
+        g[NC + j] = k.shape_m1 - k.rate * th.lam[j] + R(1) + a_t * th.gl[j];
         if (j < NC - 1) {
             u[2 * NC + j] = Math<R>::log(th.om[j] / th.om[NC - 1]);
-            g[2 * NC + j] = R(1.0 - NC * double(th.om[j]) + a_t * double(th.gz[j]));
+            g[2 * NC + j] = R(1) - R(NC) * th.om[j] + a_t * th.gz[j];
         }
     }
     // 3r - 1 normals from draws 0, 1, 2, ... of TAG_MALA
@@ -352,11 +393,11 @@ __device__ __forceinline__ uint32_t mala_move(const GmmArgs<R> &a, Theta<R, NC> 
             if (4 * c + m < D) xi[4 * c + m] = z4[m];
     }
     R up[D];
-    double xi2 = 0;
+    R xi2 = 0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        up[k] = R(double(u[k]) + h * double(g[k]) + eps * double(xi[k]));
-        xi2 += double(xi[k]) * double(xi[k]);
+    for (int kk = 0; kk < D; ++kk) {
+        up[kk] = u[kk] + h * g[kk] + eps * xi[kk];
+        xi2 += xi[kk] * xi[kk];
     }
     Theta<R, NC> p2;
 #pragma unroll
@@ -375,31 +416,34 @@ __device__ __forceinline__ uint32_t mala_move(const GmmArgs<R> &a, Theta<R, NC> 
     }
 #pragma unroll
     for (int j = 0; j < NC; ++j) p2.om[j] = p2.om[j] / sum;
-    const double lp2 = gmm_log_prior<R, NC>(a, p2.mu, p2.lam, p2.om);
-    const double ll2 =
-        gmm_loglik_grad_quad<R, NC>(p2.mu, p2.lam, p2.om, ys, a.nd, q, a.half_nd_log2pi, p2.gm, p2.gl, p2.gz);
-    double jac = 0, jac2 = 0, bwd = 0;
+    const R lp2 = gmm_log_prior<R, NC>(a, p2.mu, p2.lam, p2.om);
+    const R ll2 = gmm_loglik_grad_quad<R, NC>(p2.mu, p2.lam, p2.om, ys, a.nd, q, a, p2.gm, p2.gl, p2.gz);
+    R jac = 0, jac2 = 0, bwd = 0;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        jac += double(u[NC + j]) + double(Math<R>::log(th.om[j]));
-        jac2 += double(up[NC + j]) + double(Math<R>::log(p2.om[j]));
+        jac += u[NC + j] + Math<R>::log(th.om[j]);
+        jac2 += up[NC + j] + Math<R>::log(p2.om[j]);
     }
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        const double gpm = -(double(p2.mu[j]) - a.mu0) * a.inv_sd0 * a.inv_sd0 + a_t * double(p2.gm[j]);
-        const double gpl = a_m1 - a.rate * double(p2.lam[j]) + 1.0 + a_t * double(p2.gl[j]);
-        const double rm = double(u[j]) - double(up[j]) - h * gpm;
-        const double rl = double(u[NC + j]) - double(up[NC + j]) - h * gpl;
+        const R gpm = -(p2.mu[j] - k.mu0) * k.inv_sd0 * k.inv_sd0 + a_t * p2.gm[j];
+        const R gpl = k.shape_m1 - k.rate * p2.lam[j] + R(1) + a_t * p2.gl[j];
+        const R rm = u[j] - up[j] - h * gpm;
+        const R rl = u[NC + j] - up[NC + j] - h * gpl;
         bwd += rm * rm + rl * rl;
         if (j < NC - 1) {
-            const double gpz = 1.0 - NC * double(p2.om[j]) + a_t * double(p2.gz[j]);
-            const double rz = double(u[2 * NC + j]) - double(up[2 * NC + j]) - h * gpz;
+            const R gpz = R(1) - R(NC) * p2.om[j] + a_t * p2.gz[j];
+            const R rz = u[2 * NC + j] - up[2 * NC + j] - h * gpz;
             bwd += rz * rz;
         }
     }
-    const double delta = (lp2 + a_t * ll2 + jac2) - (lp + a_t * ll + jac) - bwd / (2.0 * eps * eps) + 0.5 * xi2;
+    R delta;
+    if constexpr (sizeof(R) == 8)
+        delta = (lp2 + a_t * ll2 + jac2) - (lp + a_t * ll + jac) - bwd / (2.0 * eps * eps) + 0.5 * xi2;
+    else
+        delta = mh_delta<R>(lp2, lp, ll2, ll, a_t) + (jac2 - jac) - bwd / (R(2) * eps * eps) + R(0.5) * xi2;
     const R lu = mh_log_uniform<R>(a.key, ii, t, TAG_MALA, a.stream);
-    if (double(lu) <= delta) {
+    if (lu <= delta) {
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             th.mu[j] = p2.mu[j];
@@ -453,9 +497,8 @@ __global__ void __launch_bounds__(kBlock) gmm_log_target_kernel(GmmArgs<R> a, co
     }
 #pragma unroll
     for (int j = 0; j < NC; ++j) th.om[j] = th.om[j] / sum;
-    const double lp = gmm_log_prior<R, NC>(a, th.mu, th.lam, th.om);
-    const double ll = gmm_loglik_grad_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi, th.gm,
-                                                  th.gl, th.gz);
+    const double lp = double(gmm_log_prior<R, NC>(a, th.mu, th.lam, th.om));
+    const double ll = double(gmm_loglik_grad_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a, th.gm, th.gl, th.gz));
     if (!active || q != 0) return;
     double jac = 0;
 #pragma unroll
@@ -513,11 +556,9 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
 #pragma unroll
         for (int j = 0; j < NC; ++j) th.om[j] = E[j] / sum;
     }
-    th.lp = R(gmm_log_prior<R, NC>(a, th.mu, th.lam, th.om));
-    const double ll = G ? gmm_loglik_grad_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi, th.gm,
-                                                      th.gl, th.gz)
-                        : gmm_loglik_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi);
-    th.ll = R(ll);
+    th.lp = gmm_log_prior<R, NC>(a, th.mu, th.lam, th.om);
+    th.ll = G ? gmm_loglik_grad_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a, th.gm, th.gl, th.gz)
+              : gmm_loglik_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a);
     const int cur = sv->cur, cur_lw = sv->cur_lw;
     const R lw0 = R(-a.log_n);
     if (active && q == 0) {
@@ -561,8 +602,17 @@ __global__ void __launch_bounds__(kBlock) gmm_reweight_kernel(GmmArgs<R> a) {
     if (sv->error) return;
     const int32_t t = sv->t + 1;
     const double a_t = a.alpha[t], a_p = a.alpha[t - 1];
-    const R dal = R(a_t - a_p);
-    const Shift<R> base(sv->base_shift);
+    // per-block constants converted once: alpha_t - alpha_{t-1} and the
+    // running shift as a split (hi, lo) in R
+    __shared__ R s_k[3];
+    if (threadIdx.x == 0) {
+        s_k[0] = R(a_t - a_p);
+        s_k[1] = R(sv->base_shift);
+        s_k[2] = R(sv->base_shift - double(s_k[1]));
+    }
+    __syncthreads();
+    const R dal = s_k[0];
+    const Shift<R> base(s_k[1], s_k[2]);
     const int cur = sv->cur, cur_lw = sv->cur_lw;
     const R *lw_in = a.lw[cur_lw];
     R *lw_out = a.lw[cur_lw ^ 1];
@@ -609,13 +659,20 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     const DevState *sv = snapshot(st);
     if (sv->error) return;
     if (threadIdx.x < 4) s_acc[threadIdx.x] = 0;
-    stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st);
     const int32_t t = sv->t;
-    const double a_t = a.alpha[t], a_p = (t > 0) ? a.alpha[t - 1] : 0.0;
-    const double aclamp = fmax(a_t, 0.02);
-    const R s_mu = R(0.15 / aclamp);
-    const R s_lam = R((1.0 + sqrt(1.0 / aclamp)) * 0.15);
-    const R s_om = R((1.0 + sqrt(1.0 / aclamp)) * 0.2);
+    // per-block constants, computed once in float64: alpha_t and the
+    // proposal scales from max(alpha_t, 0.02)
+    __shared__ R s_k[4];
+    if (threadIdx.x == 0) {
+        const double at = a.alpha[t];
+        const double aclamp = fmax(at, 0.02);
+        s_k[0] = R(at);
+        s_k[1] = R(0.15 / aclamp);
+        s_k[2] = R((1.0 + sqrt(1.0 / aclamp)) * 0.15);
+        s_k[3] = R((1.0 + sqrt(1.0 / aclamp)) * 0.2);
+    }
+    stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st);  // (its barriers publish s_k)
+    const R a_t = s_k[0], s_mu = s_k[1], s_lam = s_k[2], s_om = s_k[3];
     const bool gather = sv->ready != 0;
     const int cur = sv->cur, cur_lw = sv->cur_lw;
     const int q = threadIdx.x & (kQuad - 1);
@@ -625,7 +682,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     const int64_t src = gather ? (int64_t)__ldg(&a.anc[ii]) : ii;
     Theta<R, NC> th;
     load_theta<R, NC, G>(a.x[cur], a.ld, src, th);
-    double ll = double(th.ll), lp = double(th.lp);
+    R ll = th.ll, lp = th.lp;
     uint32_t acc_mask = 0;
     if (MOVE != kMoveMALA) {
     // block 1: mu
@@ -634,11 +691,11 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
         gmm_normals<R, NC>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_MU, a.stream, z);
 #pragma unroll
         for (int j = 0; j < NC; ++j) mu2[j] = th.mu[j] + s_mu * z[j];
-        const double lp2 = gmm_log_prior<R, NC>(a, mu2, th.lam, th.om);
-        const double ll2 = gmm_loglik_quad<R, NC>(mu2, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi);
-        const double delta = (lp2 + a_t * ll2) - (lp + a_t * ll);
+        const R lp2 = gmm_log_prior<R, NC>(a, mu2, th.lam, th.om);
+        const R ll2 = gmm_loglik_quad<R, NC>(mu2, th.lam, th.om, ys, a.nd, q, a);
+        const R delta = mh_delta<R>(lp2, lp, ll2, ll, a_t);
         const R lu = mh_log_uniform<R>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_MU, a.stream);
-        if (double(lu) <= delta) {
+        if (lu <= delta) {
 #pragma unroll
             for (int j = 0; j < NC; ++j) th.mu[j] = mu2[j];
             lp = lp2;
@@ -650,18 +707,18 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     {
         R z[NC], lam2[NC];
         gmm_normals<R, NC>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_LAMBDA, a.stream, z);
-        double jac = 0;
+        R jac = 0;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             const R dz = s_lam * z[j];
             lam2[j] = Math<R>::exp(Math<R>::log(th.lam[j]) + dz);
-            jac += double(dz);
+            jac += dz;
         }
-        const double lp2 = gmm_log_prior<R, NC>(a, th.mu, lam2, th.om);
-        const double ll2 = gmm_loglik_quad<R, NC>(th.mu, lam2, th.om, ys, a.nd, q, a.half_nd_log2pi);
-        const double delta = (lp2 + a_t * ll2) - (lp + a_t * ll) + jac;
+        const R lp2 = gmm_log_prior<R, NC>(a, th.mu, lam2, th.om);
+        const R ll2 = gmm_loglik_quad<R, NC>(th.mu, lam2, th.om, ys, a.nd, q, a);
+        const R delta = mh_delta<R>(lp2, lp, ll2, ll, a_t) + jac;
         const R lu = mh_log_uniform<R>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_LAMBDA, a.stream);
-        if (double(lu) <= delta) {
+        if (lu <= delta) {
 #pragma unroll
             for (int j = 0; j < NC; ++j) th.lam[j] = lam2[j];
             lp = lp2;
@@ -687,17 +744,17 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
             om2[j] = Math<R>::exp(v[j] - vmax);
             sum += om2[j];
         }
-        double jac = 0;
+        R jac = 0;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             om2[j] = om2[j] / sum;
-            jac += double(Math<R>::log(om2[j])) - double(Math<R>::log(th.om[j]));
+            jac += Math<R>::log(om2[j]) - Math<R>::log(th.om[j]);
         }
-        const double lp2 = gmm_log_prior<R, NC>(a, th.mu, th.lam, om2);
-        const double ll2 = gmm_loglik_quad<R, NC>(th.mu, th.lam, om2, ys, a.nd, q, a.half_nd_log2pi);
-        const double delta = (lp2 + a_t * ll2) - (lp + a_t * ll) + jac;
+        const R lp2 = gmm_log_prior<R, NC>(a, th.mu, th.lam, om2);
+        const R ll2 = gmm_loglik_quad<R, NC>(th.mu, th.lam, om2, ys, a.nd, q, a);
+        const R delta = mh_delta<R>(lp2, lp, ll2, ll, a_t) + jac;
         const R lu = mh_log_uniform<R>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_WEIGHT, a.stream);
-        if (double(lu) <= delta) {
+        if (lu <= delta) {
 #pragma unroll
             for (int j = 0; j < NC; ++j) th.om[j] = om2[j];
             lp = lp2;
@@ -710,11 +767,11 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     }  // random-walk blocks
     if (MOVE == kMoveRWMALA) {
         // the blocks moved theta: refresh the cached gradient at the current point
-        ll = gmm_loglik_grad_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a.half_nd_log2pi, th.gm, th.gl, th.gz);
+        ll = gmm_loglik_grad_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a, th.gm, th.gl, th.gz);
     }
     if (G) acc_mask |= mala_move<R, NC>(a, th, lp, ll, a_t, (uint32_t)ii, (uint32_t)t, ys, q) << 3;
-    th.lp = R(lp);
-    th.ll = R(ll);
+    th.lp = lp;
+    th.ll = ll;
     R lwi = R(-a.log_n);
     if (active && q == 0) {
         store_theta<R, NC, G>(a.x[cur ^ 1], a.ld, i, th);
@@ -741,6 +798,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
             return;
         }
         st->ticket = 0;
+        const double a_t = a.alpha[t], a_p = (t > 0) ? a.alpha[t - 1] : 0.0;
         const double U = c.Sa / c.S1;
         const double plz = st->path_log_z + 0.5 * (a_t - a_p) * (U + st->path_u);
         r->path_u = U;

@@ -1092,6 +1092,14 @@ GmmArgs<R> gmm_args(smc_ctx *c) {
     a.rate = g.rate0;
     a.half_nd_log2pi = 0.5 * (double)c->n_obs * std::log(2.0 * M_PI);
     a.mala_eps = g.mala_step;
+    a.mu0_f = (float)a.mu0;
+    a.inv_sd0_f = (float)a.inv_sd0;
+    a.lp_const_f = (float)a.lp_const;
+    a.shape_m1_f = (float)a.shape_m1;
+    a.rate_f = (float)a.rate;
+    a.mala_eps_f = (float)a.mala_eps;
+    a.hnl_f[0] = (float)a.half_nd_log2pi;
+    a.hnl_f[1] = (float)(a.half_nd_log2pi - (double)a.hnl_f[0]);
     a.key = key_of(c);
     a.stream = cfg.stream_id;
     return a;
