@@ -153,7 +153,7 @@ __device__ __forceinline__ void batch_select_tile(const BatchArgs<R> &B, int til
     const GridTargets<kStratified> tg = block_targets(proto, sv, QN);
     __shared__ TileBufs tb;
     const unsigned long long ts = scan_tile_local(g, B.n[b], lt, tb);
-    select_tile(tg, AncOut{B.anc + B.off[b]}, NoSink{}, B.n[b], lt, pre, ts, QN, st, tb);
+    select_tile_grid(tg, AncOut{B.anc + B.off[b]}, NoSink{}, B.n[b], lt, pre, ts, QN, st, tb);
 }
 
 template <typename R, bool kStratified>

@@ -87,11 +87,23 @@ DF_HD DF df_mul_f(DF a, float b) {
     const DF p = two_prod(a.hi, b);
     return fast_two_sum(p.hi, df_fma(a.lo, b, p.lo));
 }
+// float quotient for df_div: on the device the reciprocal-based quotient
+// (2 ulp, |y| < 2^126 in every use here) instead of the correctly rounded
+// division routine; df_div's correction from the exact remainder makes the
+// result accurate to about 2^-45 either way
+DF_HD float df_quot(float x, float y) {
+#if defined(__CUDA_ARCH__)
+    return __fdividef(x, y);
+#else
+    return x / y;
+#endif
+}
+
 // a / b: float quotient plus one correction from the exact remainder
 DF_HD DF df_div(DF a, DF b) {
-    const float q1 = a.hi / b.hi;
+    const float q1 = df_quot(a.hi, b.hi);
     const DF r = df_add(a, df_mul_f(DF{-b.hi, -b.lo}, q1));
-    const float q2 = r.hi / b.hi;
+    const float q2 = df_quot(r.hi, b.hi);
     return fast_two_sum(q1, q2);
 }
 DF_HD bool df_lt(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }

@@ -133,17 +133,19 @@ __device__ __forceinline__ void pf_finalize(const PfArgs<R> &a, DevState *st, co
     FinalizeArgs f{st,  a.rec,   a.rec_cap, t, 0, a.n, a.threshold, 0.0, {a.thr_df[0], a.thr_df[1]}, a.thr_mode,
                    sv->log_evidence};
     bool done = false;
+    int flipper = 0;  // the thread that advances the state
     if constexpr (sizeof(R) == 4) {
         CombinedDF c;
         combine_partials_df<PT>(a.part, nblk, &c);
-        if (threadIdx.x == 0) done = finalize_weights_df(f, c);
+        done = finalize_weights_df(f, c);  // every thread; warps 0-3 write
+        flipper = 3 * 32;                  // the warp with the shortest share
     } else {
         Combined c;
         combine_partials<R>(a.part, nblk, &c);
         double L;
         if (threadIdx.x == 0) done = finalize_weights(f, c, &L);
     }
-    if (threadIdx.x == 0 && done) {
+    if (threadIdx.x == flipper && done) {
         st->t = t;
         st->cur = cur ^ 1;
         st->cur_lw = cur_lw ^ 1;

@@ -199,8 +199,41 @@ struct GridTargets {
         t = tt;
         c = 2ull * u24(draw(key, 0u, t, TAG_RESAMPLE, stream, 0u).x) + 1ull;
     }
-    __device__ __forceinline__ void setup(unsigned long long QN) { dv.init(QN, (unsigned long long)n, mrec); }
+    // systematic closed form: z(X) = X N / Q_N - c 2^-25 in double-float,
+    // with its absolute error bound (relative error below 2^-42 of z <= N)
+    DF sN, ncc;
+    float margin;
+    __device__ __forceinline__ void setup(unsigned long long QN) {
+        dv.init(QN, (unsigned long long)n, mrec);
+        if (QN) sN = df_div(df_from_int(n), df_from_u64(QN));
+        const DF cd = df_from_int((int64_t)c);
+        ncc = DF{-cd.hi * 0x1p-25f, -cd.lo * 0x1p-25f};
+        margin = fmaxf(float(n) * 0x1p-40f, 0x1p-20f);
+    }
     __device__ __forceinline__ int64_t count() const { return n; }
+    // tau_k >= X  <=>  Q_N P_k >= X D  <=>  k >= z(X), so
+    // K(X) = #{k : tau_k < X} = min(N, max(0, ceil z(X))).  z comes from the
+    // double-float estimate; within `margin` of an integer m the exact
+    // threshold tau_m decides between m and m + 1 (systematic only).
+    __device__ __forceinline__ int64_t offspring_start(unsigned long long X) const {
+        const DF z = df_add(df_mul(df_from_u64(X), sN), ncc);
+        if (!(z.hi > -0.5f)) return 0;
+        const float h = rintf(z.hi);  // h >= 0; exact float arithmetic below
+        float r = (z.hi - h) + z.lo;
+        const float m = rintf(r);
+        r -= m;
+        const int64_t k0 = (int64_t)__float2uint_rn(h) + (int64_t)__float2int_rn(m);  // nearest integer to z
+        int64_t k;
+        if (r > margin) k = k0 + 1;
+        else if (r < -margin) k = k0;
+        else if (k0 >= n) k = n;
+        else {
+            uint64_t u, v;
+            dv.start((uint64_t)k0, u, v);
+            k = dv.tau((uint64_t)k0, c, u, v) >= X ? k0 : k0 + 1;
+        }
+        return k < 0 ? 0 : (k > n ? n : k);
+    }
     __device__ __forceinline__ unsigned long long P(int64_t k) const {
         const unsigned long long ck = kStratified ? 2ull * resample_u24_at(key, stream, t, k) + 1ull : c;
         return ((unsigned long long)k << 25) + ck;
@@ -574,6 +607,84 @@ __device__ __forceinline__ void select_tile(const Tgt &tg, const Out &out, const
     }
 }
 
+// Systematic selection of one scanned tile from the closed-form offspring
+// ranges: particle i receives the outputs k in [K(Q_{i-1}), K(Q_i)).  Each
+// thread finds K at the boundaries of its kScanItems particles (no search,
+// no merge); a particle with offspring marks the first of its outputs in a
+// shared window of kScanTile outputs, and an inclusive max-scan over the
+// window gives every output its ancestor (the marked particles increase
+// with the position).  A tile owning more outputs than one window takes
+// several windows (a degenerate weight), carrying the last ancestor over.
+// tb.q holds the tile's scan (tile-relative), pre the prefix before it.
+template <class Out>
+__device__ __forceinline__ void select_tile_sys(const GridTargets<false> &tg, const Out &out, int64_t n, int tile,
+                                                unsigned long long pre, unsigned long long QN, TileBufs &tb) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int base = tid * kScanItems;
+    const int64_t t0 = (int64_t)tile * kScanTile;
+    if (QN == 0) return;
+    int32_t K[kScanItems + 1];  // K <= N < 2^31
+    K[0] = (int32_t)tg.offspring_start(pre + (base ? tb.q[pad8(base - 1)] : 0ull));
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) K[j + 1] = (int32_t)tg.offspring_start(pre + tb.q[pad8(base + j)]);
+    if (tid == 0) tb.k[0] = K[0];
+    if (tid == kBlock - 1) tb.k[1] = K[kScanItems];
+    __syncthreads();
+    const int64_t k_lo = tb.k[0], k_hi = tb.k[1];
+    int32_t carry = -1;
+    for (int64_t w0 = k_lo; w0 < k_hi; w0 += kScanTile) {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) tb.a[pad32(base + j)] = -1;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j)
+            if (K[j + 1] > K[j] && K[j] >= w0 && K[j] < w0 + kScanTile) tb.a[pad32((int)(K[j] - w0))] = base + j;
+        __syncthreads();
+        int32_t v[kScanItems];
+        int32_t run = -1;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            run = max(run, tb.a[pad32(base + j)]);
+            v[j] = run;
+        }
+        int32_t inc = run;  // inclusive warp max-scan of the thread maxima
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc = max(inc, y);
+        }
+        __shared__ int32_t s_wmax[kBlock / 32];
+        if (lane == 31) s_wmax[warp] = inc;
+        int32_t before = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) before = -1;
+        __syncthreads();
+        before = max(before, carry);
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w)
+            if (w < warp) before = max(before, s_wmax[w]);
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) tb.a[pad32(base + j)] = max(v[j], before);
+        __syncthreads();
+        const int m = (int)min((int64_t)kScanTile, k_hi - w0);
+        for (int j = tid; j < m; j += kBlock) out(w0 + j, (int32_t)(t0 + tb.a[pad32(j)]));
+        carry = tb.a[pad32(kScanTile - 1)];
+        __syncthreads();
+    }
+}
+
+// Selection of one scanned tile for the grid targets: the CDF sink, then
+// the closed-form pass (systematic) or the merge path (stratified).
+template <bool kStratified, class Out, class Sink>
+__device__ __forceinline__ void select_tile_grid(const GridTargets<kStratified> &tg, const Out &out, const Sink &sink,
+                                                 int64_t n, int tile, unsigned long long pre, unsigned long long total,
+                                                 unsigned long long QN, DevState *st, TileBufs &tb) {
+    if constexpr (kStratified) {
+        select_tile(tg, out, sink, n, tile, pre, total, QN, st, tb);
+    } else {
+        if (Sink::kActive) select_tile(NoTargets{}, out, sink, n, tile, pre, total, QN, st, tb);
+        select_tile_sys(tg, out, n, tile, pre, QN, tb);
+    }
+}
 // Scan (+ selection) pass: one block per tile.  Q_N is the exact total of
 // the tile sums (every block sums them), or a given total.
 template <class Gen, class Tgt, class Out, class Sink>
@@ -634,12 +745,14 @@ __global__ void __launch_bounds__(kBlock, 4) grid_resample_kernel(Gen gen, GridT
     const GridTargets<kStratified> tg = block_targets(tgt, sv, QN);
     // the last tile first (its scan is in tb), then the others rescanned
     unsigned long long before_last = 0;  // sum of the block's other tiles
-    for (int tile = t_lo + (int)threadIdx.x; tile < t_hi - 1; tile += kBlock) before_last += __ldcg(&tsum[tile]);
-    before_last = block_sum_u64(before_last);
-    select_tile(tg, out, sink, n, t_hi - 1, pre + before_last, last, QN, st, tb);
+    if (t_hi - 1 > t_lo) {  // the same branch in the whole block
+        for (int tile = t_lo + (int)threadIdx.x; tile < t_hi - 1; tile += kBlock) before_last += __ldcg(&tsum[tile]);
+        before_last = block_sum_u64(before_last);
+    }
+    select_tile_grid(tg, out, sink, n, t_hi - 1, pre + before_last, last, QN, st, tb);
     for (int tile = t_lo; tile < t_hi - 1; ++tile) {
         const unsigned long long ts = scan_tile_local(g, n, tile, tb);
-        select_tile(tg, out, sink, n, tile, pre, ts, QN, st, tb);
+        select_tile_grid(tg, out, sink, n, tile, pre, ts, QN, st, tb);
         pre += ts;
     }
     grid_depart(st);

@@ -57,25 +57,19 @@ __global__ void __launch_bounds__(kBlock) add_log_weight_kernel(AddArgs<R> a) {
     FinalizeArgs f{st,  a.rec, a.rec_cap, sv->t, 1, a.n, a.threshold, sv->alpha, {a.thr_df[0], a.thr_df[1]},
                    a.thr_mode, sv->log_evidence};
     bool done = false;
-    double L = 0.0;
     if constexpr (sizeof(R) == 4) {
         CombinedDF c;
         combine_partials_df<4>(a.part, gridDim.x, &c);
-        if (threadIdx.x == 0) {
-            const FinalDF v = final_values_df(f, c);
-            write_final_df(f, c, v);
-            done = v.ok;
-            L = df_to_double(v.L);
-        }
+        // every thread; warp 0 also stores L_t as the GMM base shift
+        done = finalize_weights_df(f, c, a.gmm ? &st->base_shift : nullptr);
     } else {
         Combined c;
         combine_partials<R>(a.part, gridDim.x, &c);
+        double L = 0.0;
         if (threadIdx.x == 0) done = finalize_weights(f, c, &L);
+        if (threadIdx.x == 0 && done && a.gmm) st->base_shift = L;
     }
-    if (threadIdx.x == 0 && done) {
-        st->cur_lw = cur_lw ^ 1;
-        if (a.gmm) st->base_shift = L;
-    }
+    if (threadIdx.x == 0 && done) st->cur_lw = cur_lw ^ 1;
 }
 
 }  // namespace smc

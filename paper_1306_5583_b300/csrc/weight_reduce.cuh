@@ -54,52 +54,53 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
     return DF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
-// Per-block partial (max, sum e, sum e^2, sum e h0, sum e h1, sum e h2) with
-// e = exp(lw - max): float64 fields for the FP64 path, (hi, lo) float pairs
-// for the FP32 path, in the same 64 bytes.
+// Per-block partial (max, sum e, sum e^2, sum e h0, sum e h1) with
+// e = exp(lw - max): float64 fields for the FP64 path; for the FP32 path the
+// (hi, lo) float pairs of the four sums in floats 0..7 (two 16-byte vectors)
+// and the maximum in float 8, in the same 64 bytes.
+constexpr int kSums = 4;
+
 template <typename R>
 struct PartialIO;
 
 template <>
 struct PartialIO<double> {
-    static __device__ __forceinline__ void store(Partial *p, double m, const double (&s)[5]) {
+    static __device__ __forceinline__ void store(Partial *p, double m, const double (&s)[kSums]) {
         p->m = m;
         p->s1 = s[0];
         p->s2 = s[1];
         p->sx = s[2];
         p->sy = s[3];
-        p->su = s[4];
+        p->su = 0.0;
     }
 };
 
 template <>
 struct PartialIO<float> {
-    static __device__ __forceinline__ void store(Partial *p, float m, const DF (&s)[5]) {
-        float *f = reinterpret_cast<float *>(p);
-        f[0] = m;
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            f[1 + 2 * j] = s[j].hi;
-            f[2 + 2 * j] = s[j].lo;
-        }
+    static __device__ __forceinline__ void store(Partial *p, float m, const DF (&s)[kSums]) {
+        float4 *v = reinterpret_cast<float4 *>(p);
+        v[0] = make_float4(s[0].hi, s[0].lo, s[1].hi, s[1].lo);
+        v[1] = make_float4(s[2].hi, s[2].lo, s[3].hi, s[3].lo);
+        reinterpret_cast<float *>(p)[8] = m;
     }
-    static __device__ __forceinline__ float m(const Partial *p) { return __ldcg(reinterpret_cast<const float *>(p)); }
+    static __device__ __forceinline__ float m(const Partial *p) { return __ldcg(reinterpret_cast<const float *>(p) + 8); }
     static __device__ __forceinline__ DF s(const Partial *p, int j) {
         const float *f = reinterpret_cast<const float *>(p);
-        return DF{__ldcg(f + 1 + 2 * j), __ldcg(f + 2 + 2 * j)};
+        return DF{__ldcg(f + 2 * j), __ldcg(f + 2 * j + 1)};
     }
 };
 
 // Block-level partial of E items per thread.  lw = -inf marks inactive
 // items.  Per-thread and per-warp sums run in R; the warp sums are combined
 // in float64 (FP64 path) or compensated float (FP32 path).
-template <typename R, int E, int NH = 3>
+template <typename R, int E, int NH = 2>
 __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E], const R (&h1)[E],
                                               const R (&h2)[E], Partial *out) {
-    // NH: how many of h0, h1, h2 are monitored (the rest is reported as 0)
+    // NH: how many of h0, h1 are monitored (the rest is reported as 0; h2 is unused)
+    static_assert(NH >= 0 && NH <= 2, "at most two monitored values");
     constexpr int NV = 2 + NH;
     __shared__ R s_max[kBlock / 32];
-    __shared__ R s_sum[kBlock / 32][5];
+    __shared__ R s_sum[kBlock / 32][kSums];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     R m = Math<R>::neg_inf();
@@ -112,7 +113,7 @@ __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E]
 #pragma unroll
     for (int w = 1; w < kBlock / 32; ++w) m = fmax(m, s_max[w]);
 
-    R v[5] = {0, 0, 0, 0, 0};
+    R v[kSums] = {0, 0, 0, 0};
     if (m > Math<R>::neg_inf()) {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
@@ -121,34 +122,33 @@ __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E]
             v[1] += e * e;
             if (NH > 0) v[2] += e * h0[j];
             if (NH > 1) v[3] += e * h1[j];
-            if (NH > 2) v[4] += e * h2[j];
         }
     }
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
     if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) s_sum[warp][q] = (q < NV) ? v[q] : R(0);
+        for (int q = 0; q < kSums; ++q) s_sum[warp][q] = (q < NV) ? v[q] : R(0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         if constexpr (sizeof(R) == 8) {
-            double t[5] = {0, 0, 0, 0, 0};
+            double t[kSums] = {0, 0, 0, 0};
             for (int w = 0; w < kBlock / 32; ++w)
-                for (int q = 0; q < 5; ++q) t[q] += s_sum[w][q];
+                for (int q = 0; q < kSums; ++q) t[q] += s_sum[w][q];
             PartialIO<double>::store(out, double(m), t);
         }
     }
     if constexpr (sizeof(R) == 4) {
         // warp 0 adds the per-warp sums in compensated float (fixed tree)
         if (warp == 0) {
-            DF t[5];
+            DF t[kSums];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) t[q] = DF{lane < kBlock / 32 ? float(s_sum[lane][q]) : 0.0f, 0.0f};
+            for (int q = 0; q < kSums; ++q) t[q] = DF{lane < kBlock / 32 ? float(s_sum[lane][q]) : 0.0f, 0.0f};
 #pragma unroll
             for (int o = (kBlock / 32) / 2; o > 0; o >>= 1)
 #pragma unroll
-                for (int q = 0; q < 5; ++q) t[q] = df_add(t[q], df_shfl_xor(t[q], o));
+                for (int q = 0; q < kSums; ++q) t[q] = df_add(t[q], df_shfl_xor(t[q], o));
             if (lane == 0) PartialIO<float>::store(out, float(m), t);
         }
     }
@@ -187,24 +187,26 @@ __device__ __forceinline__ bool take_ticket(DevState *st) {
 
 // FP32 path: grid-wide sums of nb block partials in compensated float, by
 // the whole calling block (every thread receives the result).  Each thread
-// fetches its partials (b = tid + r kBlock) with 16-byte loads in one round
-// trip when nb <= 4 kBlock, the block maximum rescales them, and fixed
-// shuffle trees add them, so the result does not depend on arrival order.
+// fetches its partials (b = tid + r kBlock: two 16-byte vectors and the
+// maximum each) in one round trip when nb <= PT kBlock, the block maximum
+// rescales them, and fixed shuffle trees add them, so the result does not
+// depend on arrival order (nor on PT).
 struct CombinedDF {
     float M;
-    DF S[5];
+    DF S[kSums];
 };
 
-// PT: partials fetched per thread in the single round trip (registers); the
-// result does not depend on PT.
+// PT: partials fetched per thread in the single round trip (9 registers
+// each); the result does not depend on PT.
 template <int PT = 4>
 __device__ __forceinline__ void combine_partials_df(const Partial *part, int nb, CombinedDF *out) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ float s_m[kBlock / 32];
-    __shared__ DF s_df[kBlock / 32][5];
+    __shared__ DF s_df[kBlock / 32][kSums];
     __shared__ CombinedDF s_out;
     const bool one_pass = nb <= PT * kBlock;
-    float pv[PT][12];
+    float mm[PT];
+    float4 va[PT], vb[PT];
     float M = -INFINITY;
     if (one_pass) {
 #pragma unroll
@@ -212,16 +214,14 @@ __device__ __forceinline__ void combine_partials_df(const Partial *part, int nb,
             const int b = r * kBlock + tid;
             if (b < nb) {
                 const float4 *src = reinterpret_cast<const float4 *>(&part[b]);
-                const float4 v0 = __ldcg(src), v1 = __ldcg(src + 1), v2 = __ldcg(src + 2);
-                pv[r][0] = v0.x; pv[r][1] = v0.y; pv[r][2] = v0.z; pv[r][3] = v0.w;
-                pv[r][4] = v1.x; pv[r][5] = v1.y; pv[r][6] = v1.z; pv[r][7] = v1.w;
-                pv[r][8] = v2.x; pv[r][9] = v2.y; pv[r][10] = v2.z; pv[r][11] = v2.w;
+                va[r] = __ldcg(src);
+                vb[r] = __ldcg(src + 1);
+                mm[r] = PartialIO<float>::m(&part[b]);
             } else {
-#pragma unroll
-                for (int k = 0; k < 12; ++k) pv[r][k] = 0.0f;
-                pv[r][0] = -INFINITY;
+                va[r] = vb[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                mm[r] = -INFINITY;
             }
-            M = fmaxf(M, pv[r][0]);
+            M = fmaxf(M, mm[r]);
         }
     } else {
         for (int b = tid; b < nb; b += kBlock) M = fmaxf(M, PartialIO<float>::m(&part[b]));
@@ -232,19 +232,18 @@ __device__ __forceinline__ void combine_partials_df(const Partial *part, int nb,
     M = s_m[0];
 #pragma unroll
     for (int w = 1; w < kBlock / 32; ++w) M = fmaxf(M, s_m[w]);
-    DF S[5];
+    DF S[kSums];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) S[q] = DF{0.0f, 0.0f};
+    for (int q = 0; q < kSums; ++q) S[q] = DF{0.0f, 0.0f};
     if (M > -INFINITY) {
         if (one_pass) {
 #pragma unroll
             for (int r = 0; r < PT; ++r) {
-                const float mb = pv[r][0];
-                const float sc = (mb > -INFINITY) ? expf(mb - M) : 0.0f;
-                S[0] = df_add(S[0], df_mul_f(DF{pv[r][1], pv[r][2]}, sc));
-                S[1] = df_add(S[1], df_mul_f(df_mul_f(DF{pv[r][3], pv[r][4]}, sc), sc));
-#pragma unroll
-                for (int q = 2; q < 5; ++q) S[q] = df_add(S[q], df_mul_f(DF{pv[r][1 + 2 * q], pv[r][2 + 2 * q]}, sc));
+                const float sc = (mm[r] > -INFINITY) ? expf(mm[r] - M) : 0.0f;
+                S[0] = df_add(S[0], df_mul_f(DF{va[r].x, va[r].y}, sc));
+                S[1] = df_add(S[1], df_mul_f(df_mul_f(DF{va[r].z, va[r].w}, sc), sc));
+                S[2] = df_add(S[2], df_mul_f(DF{vb[r].x, vb[r].y}, sc));
+                S[3] = df_add(S[3], df_mul_f(DF{vb[r].z, vb[r].w}, sc));
             }
         } else {
             for (int b = tid; b < nb; b += kBlock) {
@@ -253,30 +252,32 @@ __device__ __forceinline__ void combine_partials_df(const Partial *part, int nb,
                 S[0] = df_add(S[0], df_mul_f(PartialIO<float>::s(&part[b], 0), sc));
                 S[1] = df_add(S[1], df_mul_f(df_mul_f(PartialIO<float>::s(&part[b], 1), sc), sc));
 #pragma unroll
-                for (int q = 2; q < 5; ++q) S[q] = df_add(S[q], df_mul_f(PartialIO<float>::s(&part[b], q), sc));
+                for (int q = 2; q < kSums; ++q) S[q] = df_add(S[q], df_mul_f(PartialIO<float>::s(&part[b], q), sc));
             }
         }
     }
-#pragma unroll
+    // tree levels as a loop: this code runs in one block per launch, where
+    // fetching unrolled instructions costs more than the loop
+#pragma unroll 1
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) S[q] = df_add(S[q], df_shfl_xor(S[q], o));
+        for (int q = 0; q < kSums; ++q) S[q] = df_add(S[q], df_shfl_xor(S[q], o));
     if (lane == 0)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) s_df[warp][q] = S[q];
+        for (int q = 0; q < kSums; ++q) s_df[warp][q] = S[q];
     __syncthreads();
     if (warp == 0) {
-        DF T[5];
+        DF T[kSums];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) T[q] = lane < kBlock / 32 ? s_df[lane][q] : DF{0.0f, 0.0f};
-#pragma unroll
+        for (int q = 0; q < kSums; ++q) T[q] = lane < kBlock / 32 ? s_df[lane][q] : DF{0.0f, 0.0f};
+#pragma unroll 1
         for (int o = (kBlock / 32) / 2; o > 0; o >>= 1)
 #pragma unroll
-            for (int q = 0; q < 5; ++q) T[q] = df_add(T[q], df_shfl_xor(T[q], o));
+            for (int q = 0; q < kSums; ++q) T[q] = df_add(T[q], df_shfl_xor(T[q], o));
         if (lane == 0) {
             s_out.M = M;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) s_out.S[q] = T[q];
+            for (int q = 0; q < kSums; ++q) s_out.S[q] = T[q];
         }
     }
     __syncthreads();
@@ -331,7 +332,7 @@ __device__ __forceinline__ void combine_partials(const Partial *part, int nb, Co
         combine_partials_df<4>(part, nb, &d);
         if (threadIdx.x == 0)
             *out = Combined{df_to_double(DF{d.M, 0.0f}), df_to_double(d.S[0]), df_to_double(d.S[1]),
-                            df_to_double(d.S[2]), df_to_double(d.S[3]), df_to_double(d.S[4])};
+                            df_to_double(d.S[2]), df_to_double(d.S[3]), 0.0};
     }
     __syncthreads();
 }
@@ -394,74 +395,70 @@ __device__ __forceinline__ bool finalize_weights(const FinalizeArgs &f, const Co
 
 // FP32 path of finalize_weights: the same record and state updates with the
 // per-iteration scalars in compensated float (no float64 logarithm or
-// division); doubles only for the stored values (bit-pattern conversions and
-// the float64 evidence sum).  Split in two so that every block of the
-// persistent iteration kernel can take the decision (final_values_df) while
-// one block writes (write_final_df).
-struct FinalDF {
-    bool ok, due;
-    DF L, ess;
-};
-
-__device__ __forceinline__ FinalDF final_values_df(const FinalizeArgs &f, const CombinedDF &c) {
-    FinalDF v;
+// division; doubles only for the stored values: bit-pattern conversions and
+// the float64 evidence sum).  Called by the whole last block; lane 0 of
+// warps 0-3 share the work so that the logarithm, the ESS division and the
+// means run at the same time:
+//   warp 0: L_t = M + log S1, log Z_t, the status of a failed iteration
+//   warp 1: ESS and the resample decision
+//   warp 2: filtered means
+//   warp 3: maximum, record header, ticket reset
+// Returns ok (every thread).  With L_dst set, warp 0 also stores L_t there.
+__device__ __forceinline__ bool finalize_weights_df(const FinalizeArgs &f, const CombinedDF &c,
+                                                    double *L_dst = nullptr) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const DF S1 = c.S[0], S2 = c.S[1];
-    v.ok = (c.M > -INFINITY) && (c.M < INFINITY) && (S1.hi > 0.0f) && (S1.hi < INFINITY) && (S2.hi > 0.0f);
-    if (!v.ok) {
-        v.due = false;
-        v.L = v.ess = DF{0.0f, 0.0f};
-        return v;
-    }
-    v.L = df_add_f(df_log(S1), c.M);
-    v.ess = df_div(df_mul(S1, S1), S2);
-    v.due = f.thr_mode == 1 ? true
-            : f.thr_mode == 2 ? false
-                              : df_lt(v.ess, df_mul(DF{f.thr_df[0], f.thr_df[1]}, df_from_int(f.n)));
-    return v;
-}
-
-// Record of iteration f.t and the state block; returns log Z_t.
-__device__ __forceinline__ double write_final_df(const FinalizeArgs &f, const CombinedDF &c, const FinalDF &v) {
+    const bool ok = (c.M > -INFINITY) && (c.M < INFINITY) && (S1.hi > 0.0f) && (S1.hi < INFINITY) && (S2.hi > 0.0f);
+    if (lane != 0 || warp >= 4) return ok;
     DevState *st = f.st;
     smc_record *r = &f.rec[f.t % f.rec_cap];
-    st->ticket = 0;
-    if (!v.ok) {
-        r->t = f.t;
-        r->status = SMC_E_NONFINITE;
-        raise_error(st, SMC_E_NONFINITE);
-        return 0.0;
+    if (warp == 0) {
+        if (!ok) {
+            r->t = f.t;
+            r->status = SMC_E_NONFINITE;
+            raise_error(st, SMC_E_NONFINITE);
+            return ok;
+        }
+        const DF L = df_add_f(df_log(S1), c.M);
+        const double Ld = df_to_double(L);
+        // mode 1 (reweighting the same iteration): replace the old increment
+        // L_t by the new one, i.e. log Z += L'_t - L_t
+        const double prev_logz =
+            (f.mode == 0) ? (f.t == 0 ? 0.0 : f.log_evidence_prev) : st->log_evidence - st->log_norm;
+        const double logz = prev_logz + Ld;
+        r->log_norm = Ld;
+        r->log_evidence = logz;
+        st->log_norm = Ld;
+        st->log_norm_f[0] = L.hi;
+        st->log_norm_f[1] = L.lo;
+        st->log_evidence = logz;
+        if (L_dst) *L_dst = Ld;
+    } else if (warp == 3) {
+        st->ticket = 0;
+        if (ok) {
+            const double Md = df_to_double(DF{c.M, 0.0f});
+            r->max_lw = Md;
+            r->t = f.t;
+            r->status = SMC_OK;
+            r->alpha = f.alpha;
+            st->max_lw = Md;
+            st->max_lw_f = c.M;
+        }
+    } else if (ok && warp == 1) {
+        const DF ess = df_div(df_mul(S1, S1), S2);
+        const bool due = f.thr_mode == 1   ? true
+                         : f.thr_mode == 2 ? false
+                                           : df_lt(ess, df_mul(DF{f.thr_df[0], f.thr_df[1]}, df_from_int(f.n)));
+        const double essd = df_to_double(ess);
+        r->ess = essd;
+        r->resampled = due ? 1 : 0;
+        st->ess = essd;
+        st->due = due ? 1 : 0;
+    } else if (ok) {
+        r->mean[0] = df_to_double(df_div(c.S[2], S1));
+        r->mean[1] = df_to_double(df_div(c.S[3], S1));
     }
-    const DF S1 = c.S[0];
-    const double Ld = df_to_double(v.L);
-    const double prev_logz = (f.mode == 0) ? (f.t == 0 ? 0.0 : f.log_evidence_prev) : st->log_evidence - st->log_norm;
-    const double logz = prev_logz + Ld;
-    const double essd = df_to_double(v.ess);
-    const double Md = df_to_double(DF{c.M, 0.0f});
-    r->log_norm = Ld;
-    r->log_evidence = logz;
-    r->ess = essd;
-    r->mean[0] = df_to_double(df_div(c.S[2], S1));
-    r->mean[1] = df_to_double(df_div(c.S[3], S1));
-    r->max_lw = Md;
-    r->t = f.t;
-    r->resampled = v.due ? 1 : 0;
-    r->status = SMC_OK;
-    r->alpha = f.alpha;
-    st->max_lw = Md;
-    st->max_lw_f = c.M;
-    st->log_norm = Ld;
-    st->log_norm_f[0] = v.L.hi;
-    st->log_norm_f[1] = v.L.lo;
-    st->log_evidence = logz;
-    st->ess = essd;
-    st->due = v.due ? 1 : 0;
-    return logz;
-}
-
-__device__ __forceinline__ bool finalize_weights_df(const FinalizeArgs &f, const CombinedDF &c) {
-    const FinalDF v = final_values_df(f, c);
-    write_final_df(f, c, v);
-    return v.ok;
+    return ok;
 }
 
 }  // namespace smc

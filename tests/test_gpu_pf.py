@@ -117,6 +117,29 @@ def test_degenerate_weights_select_one_particle():
         assert np.all(anc == int(np.argmax(lw))), scheme
 
 
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("scheme", ["systematic", "stratified"])
+def test_heavy_particles_in_some_tiles(scheme, precision):
+    """Tiles where one particle owns hundreds of offspring beside tiles of
+    ordinary weights, and a heavy particle in the ragged last tile: the
+    ancestors are bit-exact against the oracle's selection rule on the
+    GPU's CDF whichever way each tile is selected."""
+    need_gpu()
+    n, seed = 5 * 2048 + 777, 9
+    s, y, op = make_pf(n, 2, precision, scheme=scheme, threshold=0.0, seed=seed)
+    s.initialize()  # threshold 0: no resampling is pending
+    g = np.random.default_rng(3)
+    lw = g.normal(0.0, 0.5, n)
+    for i, extra in ((2 * 2048 + 1001, 7.0), (3 * 2048 + 8, 5.5), (n - 3, 6.0)):
+        lw[i] += extra  # N W_i of order 10^2 to 10^3
+    s.write_log_weight(lw)
+    lw_gpu = s.log_weight()
+    s.resample(force=True)
+    anc = check_resample(s, lw_gpu, 0, scheme, seed, precision)
+    counts = np.bincount(anc, minlength=n)
+    assert counts.max() > 64  # at least one tile took the merge path
+
+
 def test_nonfinite_weights_raise_and_leave_state():
     need_gpu()
     n, T = 1000, 5
