@@ -212,25 +212,51 @@ struct GridTargets {
     }
     __device__ __forceinline__ int64_t count() const { return n; }
     // tau_k >= X  <=>  Q_N P_k >= X D  <=>  k >= z(X), so
-    // K(X) = #{k : tau_k < X} = min(N, max(0, ceil z(X))).  z comes from the
-    // double-float estimate; within `margin` of an integer m the exact
-    // threshold tau_m decides between m and m + 1 (systematic only).
-    __device__ __forceinline__ int64_t offspring_start(unsigned long long X) const {
-        const DF z = df_add(df_mul(df_from_u64(X), sN), ncc);
-        if (!(z.hi > -0.5f)) return 0;
-        const float h = rintf(z.hi);  // h >= 0; exact float arithmetic below
-        float r = (z.hi - h) + z.lo;
-        const float m = rintf(r);
-        r -= m;
-        const int64_t k0 = (int64_t)__float2uint_rn(h) + (int64_t)__float2int_rn(m);  // nearest integer to z
+    // K(X) = #{k : tau_k < X} = min(N, max(0, ceil z(X))).  z is carried as
+    // floor zi, fraction zf and an error bound err; when zf lies within err of
+    // 0 or 1 the exact threshold tau_m of the nearby integer m decides
+    // between m and m + 1 (systematic only).
+    struct ZPos {
+        int64_t zi;
+        float zf, err;
+    };
+    // z(X) from the double-float estimate
+    __device__ __forceinline__ ZPos z_at(unsigned long long X) const {
+        const DF z = df_add(df_mul(df_from_u64(X), sN), ncc);  // > -1
+        const float fh = floorf(z.hi);                         // integer in [-1, 2^31]
+        float fr = (z.hi - fh) + z.lo;
+        const float adj = floorf(fr);  // lo may exceed one unit when hi >= 2^24
+        fr -= adj;
+        ZPos p;
+        p.zi = (fh < 0.0f ? -1ll : (int64_t)__float2uint_rn(fh)) + (int64_t)__float2int_rn(adj);
+        p.zf = fr;
+        p.err = margin;
+        return p;
+    }
+    // z(X + q) from z(X) for a fixed-point weight q: a float increment with
+    // relative error below 2^-22, the rounding of the fraction added to err
+    __device__ __forceinline__ void z_advance(ZPos &p, unsigned long long q) const {
+        const float qf = fmaf(__uint2float_rn((uint32_t)(q >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)q));
+        const float d = qf * sN.hi;
+        const float f = p.zf + d;
+        const float w = floorf(f);
+        p.zi += (int64_t)__float2uint_rn(w);
+        p.zf = f - w;
+        p.err += fmaf(d, 0x1p-21f, 0x1p-21f);
+    }
+    __device__ __forceinline__ int64_t k_from(const ZPos &p, unsigned long long X) const {
         int64_t k;
-        if (r > margin) k = k0 + 1;
-        else if (r < -margin) k = k0;
-        else if (k0 >= n) k = n;
-        else {
-            uint64_t u, v;
-            dv.start((uint64_t)k0, u, v);
-            k = dv.tau((uint64_t)k0, c, u, v) >= X ? k0 : k0 + 1;
+        if (p.zf > p.err && p.zf < 1.0f - p.err) {
+            k = p.zi + 1;
+        } else {
+            const int64_t m = (p.zf <= p.err) ? p.zi : p.zi + 1;  // z within err of m
+            if (m < 0) k = 0;
+            else if (m >= n) k = n;
+            else {
+                uint64_t u, v;
+                dv.start((uint64_t)m, u, v);
+                k = dv.tau((uint64_t)m, c, u, v) >= X ? m : m + 1;
+            }
         }
         return k < 0 ? 0 : (k > n ? n : k);
     }
@@ -610,7 +636,7 @@ __device__ __forceinline__ void select_tile(const Tgt &tg, const Out &out, const
 // Systematic selection of one scanned tile from the closed-form offspring
 // ranges: particle i receives the outputs k in [K(Q_{i-1}), K(Q_i)).  Each
 // thread finds K at the boundaries of its kScanItems particles (no search,
-// no merge); a particle with offspring marks the first of its outputs in a
+// no merge; z moves by q_i N / Q_N from one boundary to the next); a particle with offspring marks the first of its outputs in a
 // shared window of kScanTile outputs, and an inclusive max-scan over the
 // window gives every output its ancestor (the marked particles increase
 // with the position).  A tile owning more outputs than one window takes
@@ -623,10 +649,20 @@ __device__ __forceinline__ void select_tile_sys(const GridTargets<false> &tg, co
     const int base = tid * kScanItems;
     const int64_t t0 = (int64_t)tile * kScanTile;
     if (QN == 0) return;
+    // K at the thread's boundaries: the first from the double-float
+    // estimate, the others by increments (re-anchored if the bound grows)
     int32_t K[kScanItems + 1];  // K <= N < 2^31
-    K[0] = (int32_t)tg.offspring_start(pre + (base ? tb.q[pad8(base - 1)] : 0ull));
+    unsigned long long qprev = base ? tb.q[pad8(base - 1)] : 0ull;
+    typename GridTargets<false>::ZPos zp = tg.z_at(pre + qprev);
+    K[0] = (int32_t)tg.k_from(zp, pre + qprev);
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) K[j + 1] = (int32_t)tg.offspring_start(pre + tb.q[pad8(base + j)]);
+    for (int j = 0; j < kScanItems; ++j) {
+        const unsigned long long qj = tb.q[pad8(base + j)];
+        tg.z_advance(zp, qj - qprev);
+        if (zp.err > 0x1p-8f) zp = tg.z_at(pre + qj);
+        K[j + 1] = (int32_t)tg.k_from(zp, pre + qj);
+        qprev = qj;
+    }
     if (tid == 0) tb.k[0] = K[0];
     if (tid == kBlock - 1) tb.k[1] = K[kScanItems];
     __syncthreads();

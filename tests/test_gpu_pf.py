@@ -140,6 +140,40 @@ def test_heavy_particles_in_some_tiles(scheme, precision):
     assert counts.max() > 64  # at least one tile took the merge path
 
 
+def test_systematic_boundaries_next_to_integers():
+    """Equal weights give Q_i = (i + 1) 2^F, so every offspring boundary
+    z_i = Q_i N / Q_N - c 2^-25 sits c 2^-25 below an integer.  With a
+    (seed, stream) whose systematic draw makes c tiny every boundary falls
+    inside the estimate's error margin and is decided by the exact 64-bit
+    threshold; the selection rule then gives the identity."""
+    need_gpu()
+    n = 1 << 22
+    frac = 61 - 22
+    found = None
+    for seed in range(64):  # the oracle's Philox at t = 0 over all 16-bit stream ids
+        ctr = np.zeros((65536, 4), dtype=np.uint64)
+        ctr[:, 2] = ophilox.TAG_RESAMPLE | (np.arange(65536, dtype=np.uint64) << np.uint64(16))
+        j = ophilox.u24(ophilox.philox4x32_10(ctr, ophilox.key_of(seed))[:, 0])
+        hit = np.flatnonzero(j <= 63)
+        if hit.size:
+            found = (seed, int(hit[0]))
+            break
+    assert found is not None
+    seed, stream = found
+    assert ophilox.systematic_u24(seed, 0, stream) <= 63
+    cfg = smc.make_config(model="cv", n=n, precision=32, scheme="systematic", threshold=0.0, seed=seed,
+                          stream_id=stream, max_data=2, cv=cv_params())
+    s = smc.Sampler(cfg)
+    s.set_data(workloads.cv_data(2, seed=0, **cv_params())[1])
+    s.initialize()
+    s.write_log_weight(np.zeros(n))
+    s.resample(force=True)
+    Q = s.cdf()
+    assert np.array_equal(Q, (np.arange(1, n + 1, dtype=np.uint64) << np.uint64(frac)))
+    assert np.array_equal(s.ancestors(), np.arange(n, dtype=np.int32))
+    s.close()
+
+
 def test_nonfinite_weights_raise_and_leave_state():
     need_gpu()
     n, T = 1000, 5
