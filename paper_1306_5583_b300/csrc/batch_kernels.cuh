@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kBlock, 3) batch_pf_kernel(BatchArgs<R> B) {
         const bool gather = (t > 0) && (sv->ready != 0);
         const int nblk = B.tfirst[b + 1] - B.tfirst[b];
         pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part);
-        if (last_arrival(&st->ticket, (uint32_t)nblk)) pf_finalize<R, 1>(a, st, sv, nblk, t, cur, cur_lw);
+        if (last_arrival_after_partial(&st->ticket, (uint32_t)nblk)) pf_finalize<R, 1>(a, st, sv, nblk, t, cur, cur_lw);
     }
     if (last_arrival(&B.bs->ticket, gridDim.x) && threadIdx.x == 0) {
         B.bs->t = t;

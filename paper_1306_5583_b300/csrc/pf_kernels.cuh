@@ -46,8 +46,8 @@ template <typename R>
 __device__ __forceinline__ R cv_loglik(const PfArgs<R> &a, R yx, R yy, R px, R py) {
     const R zx = (yx - px) * a.inv_scale, zy = (yy - py) * a.inv_scale;
     if (a.gaussian) return a.ll_const - R(0.5) * (zx * zx + zy * zy);
-    if constexpr (sizeof(R) == 4)
-        return a.ll_const - a.half_nu1 * (__logf(1.0f + zx * zx * a.inv_nu) + __logf(1.0f + zy * zy * a.inv_nu));
+    if constexpr (sizeof(R) == 4)  // one logarithm of the product (1 + zx^2/nu)(1 + zy^2/nu)
+        return a.ll_const - a.half_nu1 * __logf((1.0f + zx * zx * a.inv_nu) * (1.0f + zy * zy * a.inv_nu));
     else
         return a.ll_const - a.half_nu1 * (Math<R>::log1p(zx * zx * a.inv_nu) + Math<R>::log1p(zy * zy * a.inv_nu));
 }
@@ -58,9 +58,12 @@ __device__ __forceinline__ R cv_loglik(const PfArgs<R> &a, R yx, R yy, R px, R p
 // 16-byte vector loads (or, after resampling, as independent gathers
 // through one vector load of ancestor indices) before any arithmetic, so
 // the memory system sees all of a thread's requests at once.
+// pre_src: the tile's ancestor indices when the caller has fetched them
+// already (the same load_idx4 of the same i0), else null.
 template <typename R>
 __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_t t, int cur, int cur_lw,
-                                        bool gather, Shift<R> Lprev, Partial *part) {
+                                        bool gather, Shift<R> Lprev, Partial *part,
+                                        const int32_t *pre_src = nullptr) {
     constexpr int E = kPfItems;
     const uint32_t n = (uint32_t)a.n;
     const uint32_t i0 = (blk * (uint32_t)kBlock + threadIdx.x) * (uint32_t)E;
@@ -74,15 +77,24 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
     R v0[E], v1[E], v2[E], v3[E], lwin[E];
     if (t > 0) {
         if (gather) {
+            // sorted ancestors: a thread's four sources are mostly the same
+            // or adjacent elements, so the gathers go through L1 (the read
+            // buffer was written by an earlier launch) instead of asking L2
+            // once per item for the same sectors
             int32_t src[E];
-            load_idx4(a.anc, i0, n, src);
+            if (pre_src) {
+#pragma unroll
+                for (int j = 0; j < E; ++j) src[j] = pre_src[j];
+            } else {
+                load_idx4(a.anc, i0, n, src);
+            }
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 const uint32_t sidx = (i0 + j < n) ? (uint32_t)src[j] : 0u;
-                v0[j] = __ldcg(xs0 + sidx);
-                v1[j] = __ldcg(xs1 + sidx);
-                v2[j] = __ldcg(xs2 + sidx);
-                v3[j] = __ldcg(xs3 + sidx);
+                v0[j] = __ldg(xs0 + sidx);
+                v1[j] = __ldg(xs1 + sidx);
+                v2[j] = __ldg(xs2 + sidx);
+                v3[j] = __ldg(xs3 + sidx);
             }
         } else {
             load_k<R, E>(xs0, i0, n, v0);
@@ -156,13 +168,17 @@ __device__ __forceinline__ void pf_finalize(const PfArgs<R> &a, DevState *st, co
 template <typename R>
 __global__ void __launch_bounds__(kBlock, 4) pf_iterate_kernel(PfArgs<R> a) {
     DevState *st = a.st;
-    const DevState *sv = snapshot(st);
+    // the ancestor indices do not depend on the state block: their load is
+    // in flight while the snapshot is read (unused when nothing is gathered)
+    int32_t src[kPfItems];
+    load_idx4(a.anc, (blockIdx.x * (uint32_t)kBlock + threadIdx.x) * (uint32_t)kPfItems, (uint32_t)a.n, src);
+    const DevState *sv = snapshot(st, true);
     if (sv->error) return;
     const int32_t t = sv->t + 1;
     const int cur = sv->cur, cur_lw = sv->cur_lw;
     const bool gather = (t > 0) && (sv->ready != 0);
-    pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part);
-    if (!take_ticket<R>(st)) return;
+    pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part, src);
+    if (!last_arrival_after_partial(&st->ticket, gridDim.x)) return;
     pf_finalize<R>(a, st, sv, gridDim.x, t, cur, cur_lw);
 }
 

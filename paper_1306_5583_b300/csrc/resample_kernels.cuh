@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_resample_kernel(Gen gen, GridT
                                                                Sink sink, int64_t n, unsigned long long *tsum,
                                                                unsigned long long *bsum, DevState *st, int gate) {
     __shared__ TileBufs tb;
-    const DevState *sv = snapshot(st);
+    const DevState *sv = snapshot(st, true);
     if (gated_out(sv, gate)) return;  // the same decision in every block
     Gen g = gen;
     g.prepare(sv);

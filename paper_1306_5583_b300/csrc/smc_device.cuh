@@ -104,13 +104,28 @@ __device__ __forceinline__ void box_muller(R u0, R u1, R &z0, R &z1) {
     z1 = r * s;
 }
 
+// -2 ln u for u in [2^-24, 1] (the uniforms of uniform01): u = 2^e m with
+// m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s), s = (m - 1) / (m + 1),
+// |s| < 0.172, atanh s = s (1 + s^2/3 + s^4/5 + s^6/7) with a relative
+// truncation error below 2^-25.  m - 1 is exact, so the result keeps a
+// relative error of a few 2^-23 also near u = 1, where it is small and the
+// hardware logarithm's absolute error would dominate sqrt(-2 ln u); no
+// special cases arise on this domain.
+__device__ __forceinline__ float neg2_log_unit(float u) {
+    const int bits = __float_as_int(u);
+    const int e = (bits - 0x3F3504F3) >> 23;  // 0x3F3504F3 = sqrt(1/2); arithmetic shift
+    const float m = __int_as_float(bits - (e << 23));
+    const float s = __fdividef(m - 1.0f, m + 1.0f);
+    const float s2 = s * s;
+    const float p = fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 7.0f, 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
+    return fmaf(-1.38629436111989061883f, float(e), -4.0f * s * p);  // -2 (e ln 2 + 2 s p)
+}
+
 // FP32 Box-Muller on the MUFU pipe: the angle is taken in (-pi, pi], where
 // the hardware sine/cosine are accurate to about 2^-21 absolute, using
 // cos(2 pi u) = -cos(2 pi u - pi) and sin(2 pi u) = -sin(2 pi u - pi).
 __device__ __forceinline__ void box_muller_fast(float u0, float u1, float &z0, float &z1) {
-    // the radius needs an accurate log: near u0 = 1 the MUFU log has an
-    // absolute (not relative) error that would dominate sqrt(-2 ln u0)
-    const float r2 = -2.0f * logf(u0);
+    const float r2 = neg2_log_unit(u0);
     const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));  // sqrt on the MUFU pipe (r2 = 0 gives 0)
     const float th = fmaf(6.2831853071795864769f, u1, -3.14159265358979323846f);
     float s, c;
@@ -287,11 +302,13 @@ __device__ __forceinline__ void grid_depart(DevState *st) {
 // every block of a kernel reads the same few words, and letting every warp
 // load them serialises on one L2 line.  Writes still go to the global block.
 // Must be called by all threads of the block.
-__device__ __forceinline__ const DevState *snapshot(const DevState *st) {
+// first_use: the block takes no other snapshot in this launch (no barrier
+// needed before the copy).
+__device__ __forceinline__ const DevState *snapshot(const DevState *st, bool first_use = false) {
     __shared__ __align__(16) DevState s_st;
     constexpr int W = (int)(sizeof(DevState) / 4);
     static_assert(sizeof(DevState) % 4 == 0, "DevState size");
-    __syncthreads();  // a previous snapshot in the same block may still be read
+    if (!first_use) __syncthreads();  // a previous snapshot in the same block may still be read
     const uint32_t *src = reinterpret_cast<const uint32_t *>(st);
     uint32_t *dst = reinterpret_cast<uint32_t *>(&s_st);
     for (int i = threadIdx.x; i < W; i += blockDim.x) dst[i] = __ldcg(src + i);

@@ -90,66 +90,84 @@ struct PartialIO<float> {
     }
 };
 
+// Four warp sums at once: at the first two butterfly levels each lane keeps
+// half of its values and adds its partner's copy of that half (a transpose
+// reduce), so 6 shuffles replace 20; lane 8q (q < 4) ends with the sum of
+// value q.
+template <typename R>
+__device__ __forceinline__ R warp_sum4(R v0, R v1, R v2, R v3) {
+    const int lane = threadIdx.x & 31;
+    const bool up = lane & 16, hi8 = lane & 8;
+    const R a = (up ? v2 : v0) + __shfl_xor_sync(0xffffffffu, up ? v0 : v2, 16);
+    const R b = (up ? v3 : v1) + __shfl_xor_sync(0xffffffffu, up ? v1 : v3, 16);
+    R x = (hi8 ? b : a) + __shfl_xor_sync(0xffffffffu, hi8 ? a : b, 8);
+    x += __shfl_xor_sync(0xffffffffu, x, 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    return x;
+}
+
 // Block-level partial of E items per thread.  lw = -inf marks inactive
-// items.  Per-thread and per-warp sums run in R; the warp sums are combined
-// in float64 (FP64 path) or compensated float (FP32 path).
+// items.  Each warp reduces its own maximum m_w and its sums of
+// e = exp(lw - m_w) in R (no block barrier), then one barrier hands the
+// warp partials to warp 0, which rescales them by exp(m_w - M) to the block
+// maximum M and adds them, in R: the per-warp sums already carry R's
+// rounding, so wider arithmetic across the eight warps adds nothing (the
+// FP32 partial's low words are zero; the grid combine is compensated).
+// Warp 0 stores the partial (lane 0), so a grid ticket taken right after by
+// thread 0 follows the partial in program order and the block's other
+// writes through the barrier.
 template <typename R, int E, int NH = 2>
 __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E], const R (&h1)[E],
                                               const R (&h2)[E], Partial *out) {
     // NH: how many of h0, h1 are monitored (the rest is reported as 0; h2 is unused)
     static_assert(NH >= 0 && NH <= 2, "at most two monitored values");
-    constexpr int NV = 2 + NH;
-    __shared__ R s_max[kBlock / 32];
-    __shared__ R s_sum[kBlock / 32][kSums];
+    constexpr int NW = kBlock / 32;
+    __shared__ R s_max[NW];
+    __shared__ R s_sum[NW][kSums];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     R m = Math<R>::neg_inf();
 #pragma unroll
     for (int j = 0; j < E; ++j) m = fmax(m, lw[j]);
     m = warp_max(m);
-    if (lane == 0) s_max[warp] = m;
-    __syncthreads();
-    m = s_max[0];
-#pragma unroll
-    for (int w = 1; w < kBlock / 32; ++w) m = fmax(m, s_max[w]);
-
-    R v[kSums] = {0, 0, 0, 0};
+    R v0 = 0, v1 = 0, v2 = 0, v3 = 0;
     if (m > Math<R>::neg_inf()) {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
             const R e = (lw[j] > Math<R>::neg_inf()) ? Math<R>::fast_exp(lw[j] - m) : R(0);
-            v[0] += e;
-            v[1] += e * e;
-            if (NH > 0) v[2] += e * h0[j];
-            if (NH > 1) v[3] += e * h1[j];
+            v0 += e;
+            v1 += e * e;
+            if (NH > 0) v2 += e * h0[j];
+            if (NH > 1) v3 += e * h1[j];
         }
     }
-#pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
-    if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < kSums; ++q) s_sum[warp][q] = (q < NV) ? v[q] : R(0);
-    }
+    const R x = warp_sum4(v0, v1, v2, v3);
+    if ((lane & 7) == 0) s_sum[warp][lane >> 3] = x;
+    if (lane == 0) s_max[warp] = m;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if constexpr (sizeof(R) == 8) {
-            double t[kSums] = {0, 0, 0, 0};
-            for (int w = 0; w < kBlock / 32; ++w)
-                for (int q = 0; q < kSums; ++q) t[q] += s_sum[w][q];
-            PartialIO<double>::store(out, double(m), t);
-        }
+    if (warp != 0) return;
+    const R mw = lane < NW ? s_max[lane] : Math<R>::neg_inf();
+    R M = mw;
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(0xffffffffu, M, o));
+    const R sc = (mw > Math<R>::neg_inf()) ? Math<R>::fast_exp(mw - M) : R(0);
+    R t[kSums];
+#pragma unroll
+    for (int q = 0; q < kSums; ++q) {
+        const R w = lane < NW ? s_sum[lane][q] : R(0);
+        t[q] = (q == 1) ? w * sc * sc : w * sc;
     }
-    if constexpr (sizeof(R) == 4) {
-        // warp 0 adds the per-warp sums in compensated float (fixed tree)
-        if (warp == 0) {
-            DF t[kSums];
 #pragma unroll
-            for (int q = 0; q < kSums; ++q) t[q] = DF{lane < kBlock / 32 ? float(s_sum[lane][q]) : 0.0f, 0.0f};
+    for (int o = NW / 2; o > 0; o >>= 1)
 #pragma unroll
-            for (int o = (kBlock / 32) / 2; o > 0; o >>= 1)
-#pragma unroll
-                for (int q = 0; q < kSums; ++q) t[q] = df_add(t[q], df_shfl_xor(t[q], o));
-            if (lane == 0) PartialIO<float>::store(out, float(m), t);
+        for (int q = 0; q < kSums; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
+    if (lane == 0) {
+        if constexpr (sizeof(R) == 8) {
+            PartialIO<double>::store(out, M, t);
+        } else {
+            const DF d[kSums] = {DF{t[0], 0.0f}, DF{t[1], 0.0f}, DF{t[2], 0.0f}, DF{t[3], 0.0f}};
+            PartialIO<float>::store(out, M, d);
         }
     }
 }
@@ -183,6 +201,17 @@ __device__ __forceinline__ bool last_arrival(uint32_t *counter, uint32_t count) 
 template <typename R>
 __device__ __forceinline__ bool take_ticket(DevState *st) {
     return last_arrival(&st->ticket, gridDim.x);
+}
+
+// last_arrival for a block that has just run block_partial: that function's
+// barrier already orders the block's writes before thread 0, which stored
+// the partial itself, so thread 0 arrives at once and one barrier
+// broadcasts the answer.
+__device__ __forceinline__ bool last_arrival_after_partial(uint32_t *counter, uint32_t count) {
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) s_last = (atomic_add_acq_rel(counter, 1u) == count - 1);
+    __syncthreads();
+    return s_last;
 }
 
 // FP32 path: grid-wide sums of nb block partials in compensated float, by
