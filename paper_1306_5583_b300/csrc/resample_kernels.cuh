@@ -199,23 +199,27 @@ struct GridTargets {
         t = tt;
         c = 2ull * u24(draw(key, 0u, t, TAG_RESAMPLE, stream, 0u).x) + 1ull;
     }
-    // systematic closed form: z(X) = X N / Q_N - c 2^-25 in double-float,
-    // with its absolute error bound (relative error below 2^-42 of z <= N)
+    // closed form: z(X) = X N / Q_N - c 2^-25 (systematic) or X N / Q_N
+    // (stratified) in double-float, with its absolute error bound (relative
+    // error below 2^-42 of z <= N)
     DF sN, ncc;
     float margin;
+    unsigned long long qn;
     __device__ __forceinline__ void setup(unsigned long long QN) {
         dv.init(QN, (unsigned long long)n, mrec);
+        qn = QN;
         if (QN) sN = df_div(df_from_int(n), df_from_u64(QN));
-        const DF cd = df_from_int((int64_t)c);
+        const DF cd = df_from_int(kStratified ? 0 : (int64_t)c);
         ncc = DF{-cd.hi * 0x1p-25f, -cd.lo * 0x1p-25f};
         margin = fmaxf(float(n) * 0x1p-40f, 0x1p-20f);
     }
     __device__ __forceinline__ int64_t count() const { return n; }
-    // tau_k >= X  <=>  Q_N P_k >= X D  <=>  k >= z(X), so
-    // K(X) = #{k : tau_k < X} = min(N, max(0, ceil z(X))).  z is carried as
-    // floor zi, fraction zf and an error bound err; when zf lies within err of
-    // 0 or 1 the exact threshold tau_m of the nearby integer m decides
-    // between m and m + 1 (systematic only).
+    // K(X) = #{k : tau_k < X} = the first k with Q_N P_k >= X D, i.e. with
+    // k + c_k 2^-25 >= y = X N / Q_N.  Systematic (c fixed): K = ceil z,
+    // z = y - c 2^-25.  Stratified (c_k in (0, 2^25)): K = k0 = floor y when
+    // c_k0 >= frac(y) 2^25, else k0 + 1.  z is carried as floor zi, fraction
+    // zf and an error bound err; whenever a float decision lies within its
+    // error bound, exact 64-bit / 128-bit thresholds decide.
     struct ZPos {
         int64_t zi;
         float zf, err;
@@ -244,7 +248,40 @@ struct GridTargets {
         p.zf = f - w;
         p.err += fmaf(d, 0x1p-21f, 0x1p-21f);
     }
-    __device__ __forceinline__ int64_t k_from(const ZPos &p, unsigned long long X) const {
+    // stratified draws, four to a Philox call, kept between the boundaries
+    // of a thread (consecutive boundaries mostly fall in the same call)
+    struct DrawCache {
+        int64_t k4 = -1;
+        uint4 w;
+    };
+    __device__ __forceinline__ unsigned long long c_at(int64_t k, DrawCache &dc) const {
+        if ((k >> 2) != dc.k4) {
+            dc.k4 = k >> 2;
+            dc.w = resample_words(key, stream, t, k & ~3ll);
+        }
+        const uint32_t ww = ((k & 3) == 0) ? dc.w.x : ((k & 3) == 1) ? dc.w.y : ((k & 3) == 2) ? dc.w.z : dc.w.w;
+        return 2ull * u24(ww) + 1ull;
+    }
+    __device__ __forceinline__ int64_t k_from(const ZPos &p, unsigned long long X, DrawCache &dc) const {
+        if constexpr (kStratified) {
+            if (!(p.zf > p.err && p.zf < 1.0f - p.err)) return first_at_least(X, qn);  // floor y uncertain
+            const int64_t k0 = p.zi;
+            if (k0 >= n) return n;
+            const unsigned long long ck = c_at(k0, dc);
+            // frac(y) 2^25 with the bound of zf, the product's rounding (2) and
+            // the float conversion of ck < 2^25 (1)
+            const float thr = p.zf * 33554432.0f, tol = fmaf(p.err, 33554432.0f, 4.0f);
+            const float cf = __uint2float_rn((uint32_t)ck);  // ck < 2^25
+            int64_t k;
+            if (cf > thr + tol) k = k0;
+            else if (cf < thr - tol) k = k0 + 1;
+            else {
+                uint64_t u, v;
+                dv.start((uint64_t)k0, u, v);
+                k = dv.tau((uint64_t)k0, ck, u, v) >= X ? k0 : k0 + 1;
+            }
+            return k > n ? n : k;
+        }
         int64_t k;
         if (p.zf > p.err && p.zf < 1.0f - p.err) {
             k = p.zi + 1;
@@ -633,8 +670,8 @@ __device__ __forceinline__ void select_tile(const Tgt &tg, const Out &out, const
     }
 }
 
-// Systematic selection of one scanned tile from the closed-form offspring
-// ranges: particle i receives the outputs k in [K(Q_{i-1}), K(Q_i)).  Each
+// Selection of one scanned tile (systematic, stratified) from the
+// closed-form offspring ranges: particle i receives the outputs k in [K(Q_{i-1}), K(Q_i)).  Each
 // thread finds K at the boundaries of its kScanItems particles (no search,
 // no merge; z moves by q_i N / Q_N from one boundary to the next); a particle with offspring marks the first of its outputs in a
 // shared window of kScanTile outputs, and an inclusive max-scan over the
@@ -642,39 +679,47 @@ __device__ __forceinline__ void select_tile(const Tgt &tg, const Out &out, const
 // with the position).  A tile owning more outputs than one window takes
 // several windows (a degenerate weight), carrying the last ancestor over.
 // tb.q holds the tile's scan (tile-relative), pre the prefix before it.
-template <class Out>
-__device__ __forceinline__ void select_tile_sys(const GridTargets<false> &tg, const Out &out, int64_t n, int tile,
-                                                unsigned long long pre, unsigned long long QN, TileBufs &tb) {
+template <bool kStratified, class Out>
+__device__ __forceinline__ void select_tile_closed(const GridTargets<kStratified> &tg, const Out &out, int64_t n,
+                                                   int tile, unsigned long long pre, unsigned long long QN,
+                                                   TileBufs &tb) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int base = tid * kScanItems;
     const int64_t t0 = (int64_t)tile * kScanTile;
     if (QN == 0) return;
-    // K at the thread's boundaries: the first from the double-float
-    // estimate, the others by increments (re-anchored if the bound grows)
-    int32_t K[kScanItems + 1];  // K <= N < 2^31
-    unsigned long long qprev = base ? tb.q[pad8(base - 1)] : 0ull;
-    typename GridTargets<false>::ZPos zp = tg.z_at(pre + qprev);
-    K[0] = (int32_t)tg.k_from(zp, pre + qprev);
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        const unsigned long long qj = tb.q[pad8(base + j)];
-        tg.z_advance(zp, qj - qprev);
-        if (zp.err > 0x1p-8f) zp = tg.z_at(pre + qj);
-        K[j + 1] = (int32_t)tg.k_from(zp, pre + qj);
-        qprev = qj;
+    // K(Q_i) for the thread's particles i: z at the left boundary from the
+    // double-float estimate, the rest by increments (re-anchored if the
+    // bound grows); kept in shared memory (the tile's threshold buffer,
+    // unused here) as K[i] = the end of particle i's outputs, so particle
+    // i's outputs are [K[i - 1], K[i]) and K[-1] = K(pre) = the tile's first
+    // output
+    int32_t *Kend = reinterpret_cast<int32_t *>(tb.tau);  // pad32 layout, K <= N < 2^31
+    {
+        unsigned long long qprev = base ? tb.q[pad8(base - 1)] : 0ull;
+        typename GridTargets<kStratified>::ZPos zp = tg.z_at(pre + qprev);
+        typename GridTargets<kStratified>::DrawCache dc;
+        if (tid == 0) tb.k[0] = tg.k_from(zp, pre, dc);
+#pragma unroll 1
+        for (int j = 0; j < kScanItems; ++j) {
+            const unsigned long long qj = tb.q[pad8(base + j)];
+            tg.z_advance(zp, qj - qprev);
+            if (zp.err > 0x1p-8f) zp = tg.z_at(pre + qj);
+            Kend[pad32(base + j)] = (int32_t)tg.k_from(zp, pre + qj, dc);
+            qprev = qj;
+        }
     }
-    if (tid == 0) tb.k[0] = K[0];
-    if (tid == kBlock - 1) tb.k[1] = K[kScanItems];
     __syncthreads();
-    const int64_t k_lo = tb.k[0], k_hi = tb.k[1];
+    const int64_t k_lo = tb.k[0], k_hi = Kend[pad32(kScanTile - 1)];
     int32_t carry = -1;
     for (int64_t w0 = k_lo; w0 < k_hi; w0 += kScanTile) {
 #pragma unroll
         for (int j = 0; j < kScanItems; ++j) tb.a[pad32(base + j)] = -1;
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < kScanItems; ++j)
-            if (K[j + 1] > K[j] && K[j] >= w0 && K[j] < w0 + kScanTile) tb.a[pad32((int)(K[j] - w0))] = base + j;
+        for (int j = 0; j < kScanItems; ++j) {
+            const int64_t ks = (base + j) ? Kend[pad32(base + j - 1)] : k_lo, ke = Kend[pad32(base + j)];
+            if (ke > ks && ks >= w0 && ks < w0 + kScanTile) tb.a[pad32((int)(ks - w0))] = base + j;
+        }
         __syncthreads();
         int32_t v[kScanItems];
         int32_t run = -1;
@@ -709,17 +754,13 @@ __device__ __forceinline__ void select_tile_sys(const GridTargets<false> &tg, co
 }
 
 // Selection of one scanned tile for the grid targets: the CDF sink, then
-// the closed-form pass (systematic) or the merge path (stratified).
+// the closed-form pass.
 template <bool kStratified, class Out, class Sink>
 __device__ __forceinline__ void select_tile_grid(const GridTargets<kStratified> &tg, const Out &out, const Sink &sink,
                                                  int64_t n, int tile, unsigned long long pre, unsigned long long total,
                                                  unsigned long long QN, DevState *st, TileBufs &tb) {
-    if constexpr (kStratified) {
-        select_tile(tg, out, sink, n, tile, pre, total, QN, st, tb);
-    } else {
-        if (Sink::kActive) select_tile(NoTargets{}, out, sink, n, tile, pre, total, QN, st, tb);
-        select_tile_sys(tg, out, n, tile, pre, QN, tb);
-    }
+    if (Sink::kActive) select_tile(NoTargets{}, out, sink, n, tile, pre, total, QN, st, tb);
+    select_tile_closed(tg, out, n, tile, pre, QN, tb);
 }
 // Scan (+ selection) pass: one block per tile.  Q_N is the exact total of
 // the tile sums (every block sums them), or a given total.
