@@ -179,6 +179,9 @@ __global__ void __launch_bounds__(kBlock, 4) pf_iterate_kernel(PfArgs<R> a) {
     const bool gather = (t > 0) && (sv->ready != 0);
     pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part, src);
     if (!last_arrival_after_partial(&st->ticket, gridDim.x)) return;
+    // every other block has finished: a programmatic dependent (the one-pass
+    // resampler) may start its launch while this block combines
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     pf_finalize<R>(a, st, sv, gridDim.x, t, cur, cur_lw);
 }
 

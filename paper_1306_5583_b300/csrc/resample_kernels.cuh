@@ -794,6 +794,10 @@ __global__ void __launch_bounds__(kBlock, 4) grid_resample_kernel(Gen gen, GridT
                                                                Sink sink, int64_t n, unsigned long long *tsum,
                                                                unsigned long long *bsum, DevState *st, int gate) {
     __shared__ TileBufs tb;
+    // launched as a programmatic dependent of the move kernel: wait until
+    // that grid has completed and its writes are visible (returns at once
+    // for an ordinary launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const DevState *sv = snapshot(st, true);
     if (gated_out(sv, gate)) return;  // the same decision in every block
     Gen g = gen;

@@ -183,6 +183,8 @@ struct smc_ctx {
     int device;
     DevState host_st;     // last state read back
     cudaGraphExec_t graph;  // one captured iteration (move, resampling, mcmc)
+    int dependent_launch;   // while capturing: launch the one-pass resampler as a programmatic dependent
+    int no_dependent;       // the driver refused the programmatic dependent launch once: capture without
 };
 
 namespace {
@@ -380,6 +382,17 @@ int launch_grid_resample(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
     attr[0].val.cooperative = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
+    cudaLaunchAttribute attr2[2];
+    if (c->dependent_launch) {
+        // programmatic dependent of the move kernel: the blocks become
+        // resident while the move kernel's last block combines the
+        // partials and wait (griddepcontrol.wait) for its completion
+        attr2[0] = attr[0];
+        attr2[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr2[1].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = attr2;
+        lc.numAttrs = 2;
+    }
     GridTargets<kS> tg{};
     tg.n = n;
     tg.key = key_of(c);
@@ -541,8 +554,7 @@ int launch_iteration(smc_ctx *c) {
     return rc;
 }
 
-int build_graph(smc_ctx *c) {
-    if (c->graph) return SMC_OK;
+int build_graph_once(smc_ctx *c) {
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SMC_E_CUDA;
     const int rc = launch_iteration(c);
@@ -555,10 +567,26 @@ int build_graph(smc_ctx *c) {
     const cudaError_t e2 = cudaGraphInstantiate(&c->graph, g, 0);
     cudaGraphDestroy(g);
     if (e2 != cudaSuccess) {
+        cudaGetLastError();
         c->graph = nullptr;
         return SMC_E_CUDA;
     }
     return SMC_OK;
+}
+
+// One iteration captured as a graph.  The one-pass resampler is captured as
+// a programmatic dependent of the move kernel where the driver accepts that
+// for a cooperative launch; otherwise (one refusal) as an ordinary node.
+int build_graph(smc_ctx *c) {
+    if (c->graph) return SMC_OK;
+    if (!c->no_dependent) {
+        c->dependent_launch = 1;
+        const int rc = build_graph_once(c);
+        c->dependent_launch = 0;
+        if (rc == SMC_OK) return SMC_OK;
+        c->no_dependent = 1;
+    }
+    return build_graph_once(c);
 }
 
 int mcmc_any(smc_ctx *c) {
