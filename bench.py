@@ -251,7 +251,7 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers (pinned): H2D of the
     # step's observation, D2H of the step's record
-    e2e = run_e2e(make, headline, args.steps, y, dev, stream, flush) if rank == 0 else None
+    e2e = run_e2e(make, headline, args.steps, max(3, args.warmup), y, dev, stream, flush) if rank == 0 else None
     launches = args.steps * (1 + RESAMPLE_KERNELS[headline])  # kernels of this library in the timed region
     out = {
         "metric": METRIC, "value": value, "unit": "particle-updates/s", "n_gpus": ws, "steps": args.steps,
@@ -289,7 +289,10 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(make, scheme, K, y, dev, stream, flush):
+def run_e2e(make, scheme, K, W, y, dev, stream, flush):
+    """K host-buffer iterations through smc_iterate_host, each timed on the
+    host around the call (which synchronises), after W untimed ones (the
+    first call of a context also captures its iteration graph)."""
     import torch
     from paper_1306_5583_b300 import smc
     s = make(scheme)
@@ -301,7 +304,7 @@ def run_e2e(make, scheme, K, y, dev, stream, flush):
         torch.cuda.synchronize(dev)
         total = 0.0
         steps = 0
-        for k in range(K):
+        for k in range(-W, K):
             t = s.iteration() + 1
             if t >= T_OBS:
                 s.initialize()
@@ -314,11 +317,14 @@ def run_e2e(make, scheme, K, y, dev, stream, flush):
             smc.check(L.smc_iterate_host(s.ctx, ctypes.c_void_p(obs.data_ptr()),
                                          ctypes.cast(ctypes.c_void_p(rec.data_ptr()), ctypes.POINTER(smc.Record))),
                       "smc_iterate_host")
-            total += time.perf_counter() - t0
-            steps += 1
+            if k >= 0:
+                total += time.perf_counter() - t0
+                steps += 1
     s.close()
-    return {"value": s.n * steps / total, "unit": "particle-updates/s", "h2d_bytes_per_step": 16,
-            "d2h_bytes_per_step": ctypes.sizeof(smc.Record), "timing": "host wall clock per call (synchronising)"}
+    # host -> device per step: the observation (2 float64) and its float copy (2 float32)
+    return {"value": s.n * steps / total, "unit": "particle-updates/s", "h2d_bytes_per_step": 16 + 8,
+            "d2h_bytes_per_step": ctypes.sizeof(smc.Record),
+            "timing": f"host wall clock per call (synchronising), {W} untimed calls first"}
 
 
 def mufu_peak_ops(clock_mhz):

@@ -151,8 +151,10 @@ size_t smc_workspace_bytes(const smc_config *cfg);
 
 /* Create a context.  d_workspace: caller-owned device memory of at least
  * smc_workspace_bytes(cfg) bytes, 256-byte aligned; cuda_stream: a
- * cudaStream_t (NULL = legacy default stream).  The context is ready for
- * smc_set_data; *out is NULL on failure. */
+ * cudaStream_t (NULL = legacy default stream).  The context allocates no
+ * device memory; an FP32 particle filter takes an 8-byte pinned host buffer
+ * (smc_iterate_host's staging).  The context is ready for smc_set_data;
+ * *out is NULL on failure. */
 int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t bytes,
                void *cuda_stream);
 int smc_destroy(smc_ctx *ctx);
@@ -189,7 +191,9 @@ int smc_iterate(smc_ctx *ctx, int32_t n);
 
 /* One iteration with host buffers: copies obs_t (CV: 2 float64; may be NULL
  * to use the observation already stored for t) to the device, runs one
- * iteration and copies its record to *h_record.  Synchronises. */
+ * iteration and copies its record to *h_record.  Synchronises.  An FP32
+ * particle filter sends the float copy of obs_t from a 2-float pinned host
+ * buffer that smc_create allocates (cudaMallocHost) and smc_destroy frees. */
 int smc_iterate_host(smc_ctx *ctx, const double *h_obs_t, smc_record *h_record);
 
 /* WeightSet::add_log_weight (Sec. 4.1.6): multiply the current weights by

@@ -183,6 +183,7 @@ struct smc_ctx {
     int device;
     DevState host_st;     // last state read back
     cudaGraphExec_t graph;  // one captured iteration (move, resampling, mcmc)
+    float *h_obs_f;         // pinned: the float copy of one observation for smc_iterate_host (2 floats)
     int dependent_launch;   // while capturing: launch the one-pass resampler as a programmatic dependent
     int no_dependent;       // the driver refused the programmatic dependent launch once: capture without
 };
@@ -653,7 +654,11 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
         rc = cuda_check(cudaGetLastError());
     }
     if (!rc && cfg->model == SMC_MODEL_GMM) rc = gmm_setup(c);
+    // staging buffer of smc_iterate_host's float observation (FP32 particle filters)
+    if (!rc && cfg->model != SMC_MODEL_GMM && cfg->precision == 32)
+        rc = cuda_check(cudaMallocHost(reinterpret_cast<void **>(&c->h_obs_f), 2 * sizeof(float)));
     if (rc) {
+        if (c->h_obs_f) cudaFreeHost(c->h_obs_f);
         delete c;
         return rc;
     }
@@ -664,6 +669,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
 int smc_destroy(smc_ctx *c) {
     if (!c) return SMC_E_ARG;
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->h_obs_f) cudaFreeHost(c->h_obs_f);
     gmm_release(c);
     delete c;
     return SMC_OK;
@@ -754,8 +760,16 @@ int smc_iterate_host(smc_ctx *c, const double *h_obs_t, smc_record *h_record) {
         if (t >= c->cfg.max_data) return SMC_E_ARG;
         rc = cuda_check(cudaMemcpyAsync(c->obs + 2 * (size_t)t, h_obs_t, 16, cudaMemcpyHostToDevice, c->stream));
         if (rc) return rc;
-        to_float_kernel<<<1, 32, 0, c->stream>>>(c->obs + 2 * (size_t)t, c->obs_f + 2 * (size_t)t, 2);
-        if ((rc = cuda_check(cudaGetLastError()))) return rc;
+        if (c->cfg.precision == 32) {
+            // the FP32 kernels read the float copy: rounded here (as a device
+            // conversion would) and sent from the context's pinned buffer,
+            // which this synchronising call leaves free for the next one
+            c->h_obs_f[0] = (float)h_obs_t[0];
+            c->h_obs_f[1] = (float)h_obs_t[1];
+            rc = cuda_check(cudaMemcpyAsync(c->obs_f + 2 * (size_t)t, c->h_obs_f, 2 * sizeof(float),
+                                            cudaMemcpyHostToDevice, c->stream));
+            if (rc) return rc;
+        }
         if (c->n_obs < t + 1) c->n_obs = t + 1;
     }
     rc = smc_iterate(c, 1);

@@ -136,3 +136,36 @@ def test_restore_rejects_another_configuration():
     assert e.value.code == smc.E_ARG
     with pytest.raises(smc.SMCError):
         s.restore(blob[:100])
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_iterate_host_matches_stored_observations(precision):
+    """smc_iterate_host with each observation sent from host memory gives
+    the same records and final particle system, bit for bit, as iterating
+    over the same observations stored up front."""
+    need_gpu()
+    n, T = 5000, 10
+    p = cv_params()
+    _, y = workloads.cv_data(T, seed=0, **p)
+
+    def sampler():
+        cfg = smc.make_config(model="cv", n=n, precision=precision, scheme="systematic", threshold=0.6, seed=2,
+                              max_data=T, cv=p)
+        return smc.Sampler(cfg)
+
+    a = sampler()
+    a.set_data(y)
+    a.initialize()
+    a.iterate(T - 1)
+    ha = a.history(T)
+    b = sampler()
+    b.set_data(y[:1])
+    b.initialize()
+    hb = [b.iterate_host(y[t]).as_dict() for t in range(1, T)]
+    assert any(r["resampled"] for r in ha[1:])
+    for ra, rb in zip(ha[1:], hb):
+        for k in ("t", "L", "logZ", "ess", "mean_x", "mean_y", "resampled"):
+            assert ra[k] == rb[k], (ra["t"], k, ra[k], rb[k])
+    assert np.array_equal(a.state(), b.state())
+    a.close()
+    b.close()
