@@ -296,6 +296,15 @@ int smc_pf_replay(smc_ctx *ctx, const double theta[4], double *h_log_evidence);
  * when that iteration resampled). */
 int smc_read_ancestor_history(smc_ctx *ctx, int32_t t, int32_t *dst, int on_device);
 
+/* Profiling hook: two caller-owned CUDA events (cudaEvent_t, created on the
+ * context's device; NULL clears) recorded immediately before and after the
+ * move kernel inside the iteration graph of smc_iterate, so that their
+ * elapsed time is the move kernel's duration within replayed iterations.
+ * The graph is captured again at the next smc_iterate; the events then
+ * replace the programmatic dependency between the move kernel and the
+ * one-pass resampler by an ordinary one.  No counterpart in the paper. */
+int smc_set_move_events(smc_ctx *ctx, void *ev_before, void *ev_after);
+
 /* Wait for queued work and return the device error word. */
 int smc_sync(smc_ctx *ctx);
 

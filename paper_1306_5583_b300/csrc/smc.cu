@@ -184,6 +184,7 @@ struct smc_ctx {
     DevState host_st;     // last state read back
     cudaGraphExec_t graph;  // one captured iteration (move, resampling, mcmc)
     float *h_obs_f;         // pinned: the float copy of one observation for smc_iterate_host (2 floats)
+    cudaEvent_t ev_move[2]; // profiling: recorded around the move kernel in the iteration graph
     int dependent_launch;   // while capturing: launch the one-pass resampler as a programmatic dependent
     int no_dependent;       // the driver refused the programmatic dependent launch once: capture without
 };
@@ -549,7 +550,14 @@ int launch_iteration(smc_ctx *c) {
         if (!rc) rc = resample_any(c, 1);
         if (!rc) rc = gmm_launch_mcmc(c);
     } else {
+        // external event records: captured as event-record nodes of the graph
+        // (a plain record during capture only orders the captured work)
+        if (c->ev_move[0] &&
+            (rc = cuda_check(cudaEventRecordWithFlags(c->ev_move[0], c->stream, cudaEventRecordExternal))))
+            return rc;
         rc = (c->cfg.precision == 32) ? launch_pf<float>(c) : launch_pf<double>(c);
+        if (!rc && c->ev_move[1])
+            rc = cuda_check(cudaEventRecordWithFlags(c->ev_move[1], c->stream, cudaEventRecordExternal));
         if (!rc) rc = resample_any(c, 1);
     }
     return rc;
@@ -580,7 +588,7 @@ int build_graph_once(smc_ctx *c) {
 // for a cooperative launch; otherwise (one refusal) as an ordinary node.
 int build_graph(smc_ctx *c) {
     if (c->graph) return SMC_OK;
-    if (!c->no_dependent) {
+    if (!c->no_dependent && !c->ev_move[1]) {
         c->dependent_launch = 1;
         const int rc = build_graph_once(c);
         c->dependent_launch = 0;
@@ -1029,6 +1037,17 @@ int smc_gmm_log_target(smc_ctx *c, const void *d_u, int64_t count, double alpha,
     if (c->cfg.model != SMC_MODEL_GMM) return SMC_E_ARG;
     if (c->n_obs < 1) return SMC_E_STATE;
     return gmm_log_target_any(c, d_u, count, alpha, d_logt, d_grad);
+}
+
+int smc_set_move_events(smc_ctx *c, void *ev_before, void *ev_after) {
+    if (!c) return SMC_E_ARG;
+    c->ev_move[0] = static_cast<cudaEvent_t>(ev_before);
+    c->ev_move[1] = static_cast<cudaEvent_t>(ev_after);
+    if (c->graph) {  // captured again, with or without the events, at the next smc_iterate
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return SMC_OK;
 }
 
 int smc_sync(smc_ctx *c) {

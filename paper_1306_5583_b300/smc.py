@@ -82,6 +82,7 @@ _SIGS = {
     "smc_write_state": (_I, [_P, _P, _I]),
     "smc_write_log_weight": (_I, [_P, _P, _I]),
     "smc_sync": (_I, [_P]),
+    "smc_set_move_events": (_I, [_P, _P, _P]),
     "smc_checkpoint": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "smc_gmm_log_target": (_I, [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P]),
     "smc_restore": (_I, [_P, _P, ctypes.c_size_t]),
@@ -249,6 +250,17 @@ class Sampler:
 
     def sync(self):
         check(lib().smc_sync(self.ctx), "smc_sync")
+
+    def set_move_events(self, before=None, after=None):
+        """Record two torch.cuda.Event objects (created with timing) around
+        the move kernel inside the iteration graph (None, None clears)."""
+        def handle(e):
+            if e is None:
+                return None
+            if not e.cuda_event:  # torch creates the event at its first record
+                e.record()
+            return ctypes.c_void_p(e.cuda_event)
+        check(lib().smc_set_move_events(self.ctx, handle(before), handle(after)), "smc_set_move_events")
 
     def ess(self):
         v = ctypes.c_double()

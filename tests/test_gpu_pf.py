@@ -321,3 +321,35 @@ def test_bench_configuration_matches_cdf_path(scheme):
     assert sum(a[4]) > 0
     for u, v in zip(a, b):
         assert np.array_equal(np.asarray(u), np.asarray(v))
+
+
+def test_move_events_in_the_graph_change_nothing():
+    """The profiling events recorded around the move kernel inside the
+    iteration graph time a positive interval and leave every record and
+    the particle system bit-identical."""
+    need_gpu()
+    n, T = 1 << 16, 8
+    p = cv_params()
+    _, y = workloads.cv_data(T, seed=0, **p)
+    outs = []
+    for with_events in (False, True):
+        cfg = smc.make_config(model="cv", n=n, precision=32, scheme="systematic", threshold=0.7, seed=5,
+                              max_data=T, cv=p, keep_cdf=False)
+        stream = torch.cuda.Stream()
+        s = smc.Sampler(cfg, stream=stream)
+        s.set_data(y)
+        with torch.cuda.stream(stream):
+            s.initialize()
+            if with_events:
+                b, a = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.set_move_events(b, a)
+            for _ in range(T - 1):
+                s.iterate(1)
+                if with_events:
+                    stream.synchronize()
+                    assert b.elapsed_time(a) > 0.0
+        s.sync()
+        outs.append((s.state(), s.log_weight(), [(r["L"], r["logZ"], r["resampled"]) for r in s.history(T)]))
+        s.close()
+    a0, a1 = outs
+    assert np.array_equal(a0[0], a1[0]) and np.array_equal(a0[1], a1[1]) and a0[2] == a1[2]
