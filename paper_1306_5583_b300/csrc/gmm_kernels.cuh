@@ -145,8 +145,72 @@ __device__ __forceinline__ R quad_log_sum(R s, R c, const GmmArgs<R> &a) {
     }
 }
 
-// Log-likelihood of one particle: lanes q = 0..3 of a quad each take data
-// k = q, q + 4, ...; returns the full l(theta) in all four lanes.
+// One datum of the likelihood loop: log2 of sum_j omega_j sqrt(lambda_j)
+// exp(-lambda_j (y - mu_j)^2 / 2) as m + log2(s), s in [1, NC] after the
+// shift by the largest term; the group accumulates m and the product of s.
+template <typename R, int NC>
+__device__ __forceinline__ void gmm_datum(R yk, const R (&mu)[NC], const R (&c2)[NC], const R (&h2)[NC], R &msum,
+                                          R &prod) {
+    R a[NC];
+    R m = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const R d = yk - mu[j];
+        a[j] = c2[j] - h2[j] * d * d;
+        m = fmax(m, a[j]);
+    }
+    R s = 0;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) s += Base2<R>::ex2(a[j] - m);
+    msum += m;
+    prod *= s;
+}
+
+// 1 / s for s in [1, NC]: the reciprocal-based quotient (2 ulp) on the FP32
+// path, where the correctly rounded division routine would cost more than
+// the rest of the datum
+template <typename R>
+__device__ __forceinline__ R gmm_inv(R s) {
+    if constexpr (sizeof(R) == 4) return __fdividef(1.0f, s);
+    else return R(1) / s;
+}
+
+// One datum of the likelihood-and-gradient loop: gmm_datum plus the
+// responsibilities' sums sd, sl, sr.
+template <typename R, int NC>
+__device__ __forceinline__ void gmm_datum_grad(R yk, const R (&mu)[NC], const R (&c2)[NC], const R (&h2)[NC],
+                                               R &msum, R &prod, R (&sd)[NC], R (&sl)[NC], R (&sr)[NC]) {
+    R a[NC], d[NC];
+    R m = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        d[j] = yk - mu[j];
+        a[j] = c2[j] - h2[j] * d[j] * d[j];
+        m = fmax(m, a[j]);
+    }
+    R e[NC], s = 0;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        e[j] = Base2<R>::ex2(a[j] - m);
+        s += e[j];
+    }
+    const R inv = gmm_inv(s);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const R rho = e[j] * inv;
+        sd[j] += rho * d[j];
+        sl[j] += rho * d[j] * d[j];
+        sr[j] += rho;
+    }
+    msum += m;
+    prod *= s;
+}
+
+// Log-likelihood of one particle, the data split over the kQuad lanes of
+// its quad (lane q takes y_q, y_{q+4}, ...; the full l(theta) is returned
+// in all four lanes): groups of kGmmGroup data share one lg2 of the product
+// of their sums.  Full groups are unrolled; the ragged end takes a rolled
+// loop (the same groups either way).
 template <typename R, int NC>
 __device__ __forceinline__ R gmm_loglik_quad(const R (&mu)[NC], const R (&lam)[NC], const R (&om)[NC],
                                              const R *__restrict__ ys, int nd, int q, const GmmArgs<R> &ga) {
@@ -158,26 +222,19 @@ __device__ __forceinline__ R gmm_loglik_quad(const R (&mu)[NC], const R (&lam)[N
         h2[j] = R(0.5 * kLog2e) * lam[j];
     }
     Kahan<R> acc;
+    const int cnt = nd > q ? (nd - q + kQuad - 1) / kQuad : 0;  // data of this lane
     int k = q;
-    while (k < nd) {
+#pragma unroll 1
+    for (int gi = cnt / kGmmGroup; gi > 0; --gi, k += kQuad * kGmmGroup) {
+        R msum = 0, prod = 1;
+#pragma unroll
+        for (int g = 0; g < kGmmGroup; ++g) gmm_datum<R, NC>(ys[k + g * kQuad], mu, c2, h2, msum, prod);
+        acc.add(msum + Base2<R>::lg2(prod));
+    }
+    if (k < nd) {
         R msum = 0, prod = 1;
 #pragma unroll 1
-        for (int g = 0; g < kGmmGroup && k < nd; ++g, k += kQuad) {
-            const R yk = ys[k];
-            R a[NC];
-            R m = -INFINITY;
-#pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                const R d = yk - mu[j];
-                a[j] = c2[j] - h2[j] * d * d;
-                m = fmax(m, a[j]);
-            }
-            R s = 0;
-#pragma unroll
-            for (int j = 0; j < NC; ++j) s += Base2<R>::ex2(a[j] - m);
-            msum += m;
-            prod *= s;
-        }
+        for (; k < nd; k += kQuad) gmm_datum<R, NC>(ys[k], mu, c2, h2, msum, prod);
         acc.add(msum + Base2<R>::lg2(prod));
     }
     return quad_log_sum<R>(acc.s, acc.c, ga);
@@ -199,37 +256,20 @@ __device__ __forceinline__ R gmm_loglik_grad_quad(const R (&mu)[NC], const R (&l
         sd[j] = sl[j] = sr[j] = R(0);
     }
     Kahan<R> acc;
+    const int cnt = nd > q ? (nd - q + kQuad - 1) / kQuad : 0;
     int k = q;
-    while (k < nd) {
+#pragma unroll 1
+    for (int gi = cnt / kGmmGroup; gi > 0; --gi, k += kQuad * kGmmGroup) {
+        R msum = 0, prod = 1;
+#pragma unroll
+        for (int g = 0; g < kGmmGroup; ++g)
+            gmm_datum_grad<R, NC>(ys[k + g * kQuad], mu, c2, h2, msum, prod, sd, sl, sr);
+        acc.add(msum + Base2<R>::lg2(prod));
+    }
+    if (k < nd) {
         R msum = 0, prod = 1;
 #pragma unroll 1
-        for (int g = 0; g < kGmmGroup && k < nd; ++g, k += kQuad) {
-            const R yk = ys[k];
-            R a[NC], d[NC];
-            R m = -INFINITY;
-#pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                d[j] = yk - mu[j];
-                a[j] = c2[j] - h2[j] * d[j] * d[j];
-                m = fmax(m, a[j]);
-            }
-            R e[NC], s = 0;
-#pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                e[j] = Base2<R>::ex2(a[j] - m);
-                s += e[j];
-            }
-            const R inv = R(1) / s;
-#pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                const R rho = e[j] * inv;
-                sd[j] += rho * d[j];
-                sl[j] += rho * d[j] * d[j];
-                sr[j] += rho;
-            }
-            msum += m;
-            prod *= s;
-        }
+        for (; k < nd; k += kQuad) gmm_datum_grad<R, NC>(ys[k], mu, c2, h2, msum, prod, sd, sl, sr);
         acc.add(msum + Base2<R>::lg2(prod));
     }
     const R total = quad_log_sum<R>(acc.s, acc.c, ga);
