@@ -166,15 +166,6 @@ __device__ __forceinline__ void gmm_datum(R yk, const R (&mu)[NC], const R (&c2)
     prod *= s;
 }
 
-// 1 / s for s in [1, NC]: the reciprocal-based quotient (2 ulp) on the FP32
-// path, where the correctly rounded division routine would cost more than
-// the rest of the datum
-template <typename R>
-__device__ __forceinline__ R gmm_inv(R s) {
-    if constexpr (sizeof(R) == 4) return __fdividef(1.0f, s);
-    else return R(1) / s;
-}
-
 // One datum of the likelihood-and-gradient loop: gmm_datum plus the
 // responsibilities' sums sd, sl, sr.
 template <typename R, int NC>
@@ -194,7 +185,7 @@ __device__ __forceinline__ void gmm_datum_grad(R yk, const R (&mu)[NC], const R 
         e[j] = Base2<R>::ex2(a[j] - m);
         s += e[j];
     }
-    const R inv = gmm_inv(s);
+    const R inv = fast_rcp(s);  // s in [1, NC]: the division routine would cost more than the datum
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         const R rho = e[j] * inv;

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) pf_adjoint_kernel(AdjArgs<R> a) {
             ds = (zx * zx + zy * zy - R(2)) * a.inv_scale;
             dn = R(0);
         } else {
-            const R qx = R(1) / (a.nu + zx * zx), qy = R(1) / (a.nu + zy * zy);
+            const R qx = fast_rcp(a.nu + zx * zx), qy = fast_rcp(a.nu + zy * zy);
             gx = (a.nu + R(1)) * zx * qx * a.inv_scale;
             gy = (a.nu + R(1)) * zy * qy * a.inv_scale;
             ds = (R(-2) + (a.nu + R(1)) * (zx * zx * qx + zy * zy * qy)) * a.inv_scale;
@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(kBlock) pf_adjoint_kernel(AdjArgs<R> a) {
         }
         const R b0 = f0[j] + g * gx, b1 = f1[j] + g * gy, b2 = f2[j], b3 = f3[j];
         R e[4] = {0, 0, 0, 0};
-        if (a.t > 0) normals4<R>(draw(a.key, i0 + j, (uint32_t)a.t, TAG_MOVE, a.stream, 0u), e);
+        // the forward move's own noise (the same transform as pf_tile)
+        if (a.t > 0) normals4_fast<R>(draw(a.key, i0 + j, (uint32_t)a.t, TAG_MOVE, a.stream, 0u), e);
         sg[j] = ok ? g : R(0);
         sds[j] = ok ? g * ds : R(0);
         sdn[j] = ok ? g * dn : R(0);

@@ -93,6 +93,15 @@ struct Math<double> {
     static __device__ __forceinline__ double neg_inf() { return -__longlong_as_double(0x7ff0000000000000ll); }
 };
 
+// 1 / x: the reciprocal-based float quotient (2 ulp; x within the normal
+// range) on the FP32 path instead of the correctly rounded division
+// routine, exact division in float64
+template <typename R>
+__device__ __forceinline__ R fast_rcp(R x) {
+    if constexpr (sizeof(R) == 4) return __fdividef(1.0f, x);
+    else return R(1) / x;
+}
+
 // Box-Muller pair from two uniforms in (0, 1]: z0 = r cos(2 pi u1),
 // z1 = r sin(2 pi u1), r = sqrt(-2 ln u0).
 template <typename R>
