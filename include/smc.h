@@ -52,6 +52,10 @@ extern "C" {
 #define SMC_E_TIMEOUT 4    /* a bounded device wait gave up */
 #define SMC_E_CUDA 5       /* a CUDA runtime call failed */
 #define SMC_E_STATE 6      /* call out of order (e.g. move before initialize) */
+#define SMC_E_RANGE 7      /* a device counter left its range: a 24-bit multinomial draw
+                            * value drawn 256 times in one resampling step (probability
+                            * below 1e-60 per step for N <= 2^30); the step's ancestors
+                            * are not valid */
 
 /* resampling schemes (Sec. 2.1; Douc et al. 2005); the paper's default is
  * stratified (Sec. 4.1.3) */

@@ -193,11 +193,12 @@ struct GridTargets {
     uint32_t t;
     unsigned long long c;  // 2j + 1 (systematic)
     unsigned long long mrec;  // floor((2^64 - 1) / n), from the host
+    unsigned long long c_fixed;  // nonzero: c itself instead of a draw (the multinomial value thresholds)
     GridDiv dv;
     __device__ __forceinline__ void prepare(const DevState *st) { prepare_at((uint32_t)st->t); }
     __device__ __forceinline__ void prepare_at(uint32_t tt) {
         t = tt;
-        c = 2ull * u24(draw(key, 0u, t, TAG_RESAMPLE, stream, 0u).x) + 1ull;
+        c = c_fixed ? c_fixed : 2ull * u24(draw(key, 0u, t, TAG_RESAMPLE, stream, 0u).x) + 1ull;
     }
     // closed form: z(X) = X N / Q_N - c 2^-25 (systematic) or X N / Q_N
     // (stratified) in double-float, with its absolute error bound (relative
@@ -679,10 +680,18 @@ __device__ __forceinline__ void select_tile(const Tgt &tg, const Out &out, const
 // with the position).  A tile owning more outputs than one window takes
 // several windows (a degenerate weight), carrying the last ancestor over.
 // tb.q holds the tile's scan (tile-relative), pre the prefix before it.
-template <bool kStratified, class Out>
+// The closed form gives an index K0(X) into the targets' own count; kmap
+// turns it into the output count K(X) (the identity for systematic and
+// stratified targets; the draw histogram for multinomial value thresholds).
+struct KIdentity {
+    __device__ __forceinline__ int64_t operator()(int64_t k) const { return k; }
+    __device__ __forceinline__ void map_items(int32_t *, int, int64_t *) const {}
+};
+
+template <bool kStratified, class Out, class KMap = KIdentity>
 __device__ __forceinline__ void select_tile_closed(const GridTargets<kStratified> &tg, const Out &out, int64_t n,
                                                    int tile, unsigned long long pre, unsigned long long QN,
-                                                   TileBufs &tb) {
+                                                   TileBufs &tb, const KMap &kmap = KMap{}) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int base = tid * kScanItems;
     const int64_t t0 = (int64_t)tile * kScanTile;
@@ -698,7 +707,7 @@ __device__ __forceinline__ void select_tile_closed(const GridTargets<kStratified
         unsigned long long qprev = base ? tb.q[pad8(base - 1)] : 0ull;
         typename GridTargets<kStratified>::ZPos zp = tg.z_at(pre + qprev);
         typename GridTargets<kStratified>::DrawCache dc;
-        if (tid == 0) tb.k[0] = tg.k_from(zp, pre, dc);
+        if (tid == 0) tb.k[0] = tg.k_from(zp, pre, dc);  // mapped with the thread's own entries
 #pragma unroll 1
         for (int j = 0; j < kScanItems; ++j) {
             const unsigned long long qj = tb.q[pad8(base + j)];
@@ -707,6 +716,7 @@ __device__ __forceinline__ void select_tile_closed(const GridTargets<kStratified
             Kend[pad32(base + j)] = (int32_t)tg.k_from(zp, pre + qj, dc);
             qprev = qj;
         }
+        kmap.map_items(Kend, base, tid == 0 ? &tb.k[0] : nullptr);
     }
     __syncthreads();
     const int64_t k_lo = tb.k[0], k_hi = Kend[pad32(kScanTile - 1)];
@@ -755,12 +765,13 @@ __device__ __forceinline__ void select_tile_closed(const GridTargets<kStratified
 
 // Selection of one scanned tile for the grid targets: the CDF sink, then
 // the closed-form pass.
-template <bool kStratified, class Out, class Sink>
+template <bool kStratified, class Out, class Sink, class KMap = KIdentity>
 __device__ __forceinline__ void select_tile_grid(const GridTargets<kStratified> &tg, const Out &out, const Sink &sink,
                                                  int64_t n, int tile, unsigned long long pre, unsigned long long total,
-                                                 unsigned long long QN, DevState *st, TileBufs &tb) {
+                                                 unsigned long long QN, DevState *st, TileBufs &tb,
+                                                 const KMap &kmap = KMap{}) {
     if (Sink::kActive) select_tile(NoTargets{}, out, sink, n, tile, pre, total, QN, st, tb);
-    select_tile_closed(tg, out, n, tile, pre, QN, tb);
+    select_tile_closed(tg, out, n, tile, pre, QN, tb, kmap);
 }
 // Scan (+ selection) pass: one block per tile.  Q_N is the exact total of
 // the tile sums (every block sums them), or a given total.
@@ -835,6 +846,257 @@ __global__ void __launch_bounds__(kBlock, 4) grid_resample_kernel(Gen gen, GridT
         const unsigned long long ts = scan_tile_local(g, n, tile, tb);
         select_tile_grid(tg, out, sink, n, tile, pre, ts, QN, st, tb);
         pre += ts;
+    }
+    grid_depart(st);
+}
+
+// ------------------------------------------- multinomial by a histogram --
+//
+// Multinomial selection (P_k = m (2 j_(k) + 1), D = m 2^25, j_(k) the sorted
+// draws) without a sort: output k goes to the first i with
+// Q_i 2^25 > Q_N (2 j_(k) + 1), so particle i receives the outputs
+// [H(v(Q_{i-1})), H(v(Q_i))), where H(v) = #{k : j_k < v} and v(X) is the
+// smallest s with Q_N (2 s + 1) >= X 2^25, i.e. v(X) = ceil(X 2^24 / Q_N - 1/2):
+// the systematic closed form with n = 2^24 and c = 2^24 (GridTargets with
+// c_fixed).  H comes from a histogram of the draws, one byte per value.
+
+// the sum of the four bytes of x
+__device__ __forceinline__ uint32_t byte_sum(uint32_t x) {
+    x = (x & 0x00FF00FFu) + ((x >> 8) & 0x00FF00FFu);
+    return (x & 0xFFFFu) + (x >> 16);
+}
+// the bytes of x with index below p (p may lie outside 0..4)
+__device__ __forceinline__ uint32_t bytes_below(uint32_t x, int p) {
+    return p >= 4 ? x : (p <= 0 ? 0u : x & ((1u << (8 * p)) - 1u));
+}
+
+struct HistArgs {
+    uint32_t *hist;  // [kHistWords]: byte counts of the values (cleared by each use)
+    uint32_t *hpre;  // [kHistBuckets] bucket prefix within its histogram tile
+    uint32_t *htot;  // [kHistTiles] histogram tile totals
+};
+
+// Offset (32-bit words) of the histogram tile prefix in the tile's threshold
+// buffer, past the offspring ends of select_tile_closed.
+constexpr int kHistTpreOffset = kScanTile + kScanTile / 8;
+static_assert(kHistTpreOffset >= kScanTile + kScanTile / 32, "clear of the offspring ends");
+static_assert(kHistTpreOffset + kHistTiles <= 2 * (kScanTile + kScanTile / 8), "inside the threshold buffer");
+
+// H(v) for v in [0, 2^24]: the tile prefix (shared memory), the bucket
+// prefix and the bytes below v in its bucket
+struct HistMap {
+    const uint4 *hist;
+    const uint32_t *hpre;
+    const uint32_t *tpre;
+    int64_t m;  // number of draws
+    __device__ __forceinline__ int64_t finish(int64_t v, uint4 w, uint32_t hp) const {
+        if (v >= (int64_t(1) << kHistValueBits)) return m;
+        const int64_t bk = v >> 4;
+        const int p = (int)(v & 15);
+        const uint32_t in = byte_sum(bytes_below(w.x, p)) + byte_sum(bytes_below(w.y, p - 4)) +
+                            byte_sum(bytes_below(w.z, p - 8)) + byte_sum(bytes_below(w.w, p - 12));
+        return (int64_t)tpre[bk / kScanTile] + (int64_t)hp + (int64_t)in;
+    }
+    __device__ __forceinline__ int64_t bucket(int64_t v) const {
+        return min(v, (int64_t(1) << kHistValueBits) - 1) >> 4;
+    }
+    // Loads through L1: neighbouring boundaries of a thread and a warp share
+    // buckets, and no SM loads these lines before the grid barrier whose
+    // acquire orders them after the writes.
+    __device__ __forceinline__ int64_t operator()(int64_t v) const {
+        const int64_t bk = bucket(v);
+        return finish(v, hist[bk], hpre[bk]);
+    }
+    // K[base + j] = H(K[base + j]) for the kScanItems entries of a thread
+    // and, where given, *k0 = H(*k0) (with the first four): four lookups at a
+    // time, their loads issued together
+    __device__ __forceinline__ void map_items(int32_t *K, int base, int64_t *k0) const {
+#pragma unroll
+        for (int h = 0; h < kScanItems; h += 4) {
+            int64_t v[5];
+            uint4 w[5];
+            uint32_t hp[5];
+            const int cnt = (h == 0 && k0) ? 5 : 4;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                if (j < cnt) {
+                    v[j] = (j < 4) ? (int64_t)K[pad32(base + h + j)] : *k0;
+                    const int64_t bk = bucket(v[j]);
+                    w[j] = hist[bk];
+                    hp[j] = hpre[bk];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) K[pad32(base + h + j)] = (int32_t)finish(v[j], w[j], hp[j]);
+            if (cnt == 5) *k0 = finish(v[4], w[4], hp[4]);
+        }
+    }
+};
+
+// The block's share of the draws k in [0, m) of iteration t (Philox calls
+// [calls b / G, calls (b + 1) / G)) counted into the histogram.  A byte that
+// wraps lowers the histogram's total by 255 or 256, which the selection
+// phase detects.
+__device__ __forceinline__ void hist_draws(uint2 key, uint32_t stream, uint32_t t, int64_t m, uint32_t *hist, int b,
+                                           int G) {
+    const int64_t calls = (m + 3) >> 2;
+    const int64_t c_lo = calls * b / G, c_hi = calls * (b + 1) / G;
+    for (int64_t cc = c_lo + threadIdx.x; cc < c_hi; cc += kBlock) {
+        const uint4 w = resample_words(key, stream, t, 4 * cc);
+        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (4 * cc + j < m) {
+                const uint32_t v = u24(ww[j]);
+                atomicAdd(&hist[v >> 2], 1u << (8u * (v & 3u)));
+            }
+        }
+    }
+}
+
+// Bucket prefixes of histogram tile ht within the tile (thread t takes the
+// buckets r kBlock + t, coalesced) and the tile's total.
+__device__ __forceinline__ void hist_scan_tile(const uint4 *h, uint32_t *hpre, uint32_t *htot, int ht) {
+    __shared__ uint32_t s_w[kScanItems][kBlock / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t b0 = (int64_t)ht * kScanTile;
+    uint32_t c[kScanItems], inc[kScanItems];
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const uint4 w = __ldcg(&h[b0 + r * kBlock + tid]);
+        c[r] = byte_sum(w.x) + byte_sum(w.y) + byte_sum(w.z) + byte_sum(w.w);
+        inc[r] = c[r];
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int r = 0; r < kScanItems; ++r) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc[r], o);
+            if (lane >= o) inc[r] += y;
+        }
+    }
+    __syncthreads();  // s_w may still be read for the previous tile
+    if (lane == 31)
+#pragma unroll
+        for (int r = 0; r < kScanItems; ++r) s_w[r][warp] = inc[r];
+    __syncthreads();
+    uint32_t row = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        uint32_t wpre = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) {
+            const uint32_t x = s_w[r][w];
+            tot += x;
+            wpre += (w < warp) ? x : 0u;
+        }
+        hpre[b0 + r * kBlock + tid] = row + wpre + inc[r] - c[r];
+        row += tot;
+    }
+    if (tid == 0) htot[ht] = row;
+}
+
+// Exclusive prefix of the histogram tile totals into tpre (shared memory),
+// by the whole block; returns the histogram's total to every thread.
+__device__ __forceinline__ uint32_t hist_tile_prefix(const uint32_t *htot, uint32_t *tpre) {
+    static_assert(kHistTiles == 2 * kBlock, "two histogram tiles per thread");
+    __shared__ uint32_t s_w[kBlock / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t a = __ldcg(&htot[2 * tid]), b = __ldcg(&htot[2 * tid + 1]);
+    uint32_t inc = a + b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) {
+        const uint32_t x = s_w[w];
+        tot += x;
+        wpre += (w < warp) ? x : 0u;
+    }
+    const uint32_t ex = wpre + inc - (a + b);
+    tpre[2 * tid] = ex;
+    tpre[2 * tid + 1] = ex + a;
+    __syncthreads();
+    return tot;
+}
+
+// One-pass multinomial resampling: a cooperative launch of one full wave.
+// Phase 1: the block's share of the histogram cleared (full-line stores: the
+// lines are allocated in L2 without a DRAM read) and the tile sums of its
+// weight tiles (the last tile's scan kept); grid barrier; phase 2: the
+// block's share of the N draws counted into the histogram (L2 atomics);
+// grid barrier; phase 3: the bucket prefixes of its histogram tiles; grid
+// barrier; phase 4: selection of its weight tiles with K(X) = H(v(X)).  A
+// block may own no weight tile or no histogram tile.
+template <typename R, class Sink>
+__global__ void __launch_bounds__(kBlock, 4) grid_multinomial_kernel(QGen<R> gen, GridTargets<false> tgt, AncOut out,
+                                                                  Sink sink, int64_t n, unsigned long long *tsum,
+                                                                  unsigned long long *bsum, HistArgs h, DevState *st,
+                                                                  int gate) {
+    __shared__ TileBufs tb;
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // as in grid_resample_kernel
+    const DevState *sv = snapshot(st, true);
+    if (gated_out(sv, gate)) return;
+    QGen<R> g = gen;
+    g.prepare(sv);
+    const int G = gridDim.x, b = blockIdx.x;
+    {
+        uint4 *h4 = reinterpret_cast<uint4 *>(h.hist);
+        const int64_t z_hi = kHistBuckets * (b + 1) / G;
+        for (int64_t i = kHistBuckets * b / G + threadIdx.x; i < z_hi; i += kBlock) h4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+    const int t_lo = (int)((int64_t)ntiles * b / G), t_hi = (int)((int64_t)ntiles * (b + 1) / G);
+    unsigned long long bs = 0, last = 0;
+    for (int tile = t_lo; tile < t_hi - 1; ++tile) {
+        const unsigned long long s = tile_sum(g, n, tile);  // to thread 0
+        if (threadIdx.x == 0) {
+            tsum[tile] = s;
+            bs += s;
+        }
+    }
+    if (t_hi > t_lo) last = scan_tile_local(g, n, t_hi - 1, tb);
+    if (threadIdx.x == 0) {
+        if (t_hi > t_lo) tsum[t_hi - 1] = last;
+        bsum[b] = bs + last;
+    }
+    if (!grid_barrier(st, G)) return;
+    if (b == 0 && threadIdx.x == 0) st->ready = 1;
+    hist_draws(tgt.key, tgt.stream, (uint32_t)sv->t, n, h.hist, b, G);
+    // the block's weight prefix and targets (the block sums are complete)
+    // while the other blocks' atomics drain
+    unsigned long long pre = 0, QN = 0, before_last = 0;  // before_last: sum of the block's other tiles
+    GridTargets<false> tg{};
+    if (t_hi > t_lo) {  // the same branch in the whole block
+        tile_prefix_total(bsum, b, G, &pre, &QN);
+        tg = block_targets(tgt, sv, QN);
+        if (t_hi - 1 > t_lo) {
+            for (int tile = t_lo + (int)threadIdx.x; tile < t_hi - 1; tile += kBlock)
+                before_last += __ldcg(&tsum[tile]);
+            before_last = block_sum_u64(before_last);
+        }
+    }
+    if (!grid_barrier(st, 2 * G)) return;
+    const int h_lo = (int)((int64_t)kHistTiles * b / G), h_hi = (int)((int64_t)kHistTiles * (b + 1) / G);
+    for (int ht = h_lo; ht < h_hi; ++ht) hist_scan_tile(reinterpret_cast<const uint4 *>(h.hist), h.hpre, h.htot, ht);
+    if (!grid_barrier(st, 3 * G)) return;
+    if (t_hi > t_lo) {
+        uint32_t *tpre = reinterpret_cast<uint32_t *>(tb.tau) + kHistTpreOffset;
+        const uint32_t total = hist_tile_prefix(h.htot, tpre);
+        if (total != (uint32_t)n && threadIdx.x == 0) raise_error(st, SMC_E_RANGE);  // a wrapped count
+        const HistMap km{reinterpret_cast<const uint4 *>(h.hist), h.hpre, tpre, n};
+        select_tile_grid(tg, out, sink, n, t_hi - 1, pre + before_last, last, QN, st, tb, km);
+        for (int tile = t_lo; tile < t_hi - 1; ++tile) {
+            const unsigned long long ts = scan_tile_local(g, n, tile, tb);
+            select_tile_grid(tg, out, sink, n, tile, pre, ts, QN, st, tb, km);
+            pre += ts;
+        }
     }
     grid_depart(st);
 }

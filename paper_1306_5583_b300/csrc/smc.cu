@@ -53,6 +53,7 @@ int ceil_log2(int64_t n) {
 
 struct Layout {
     size_t st, rec, part, x, lw, anc, Q, tsum, bsum, inc, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, alpha;
+    size_t dhist, dpre, dtot;  // multinomial draw histogram, bucket prefixes, tile totals
     size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, total;
     int ck;           // steps between checkpoints (record mode)
     int64_t nck;      // checkpoints
@@ -102,8 +103,9 @@ Layout make_layout(const smc_config *c) {
     const int B = std::min(24, std::max(1, ceil_log2(n)));
     L.bucket_shift = 24 - B;
     L.nbuckets = int64_t(1) << B;
-    const bool sorts = (c->scheme == SMC_MULTINOMIAL || c->scheme == SMC_RESIDUAL);
+    const bool sorts = (c->scheme == SMC_RESIDUAL);
     const bool resid = (c->scheme == SMC_RESIDUAL);
+    const bool hists = (c->scheme == SMC_MULTINOMIAL);
     const int64_t bucket_tiles = sorts ? (L.nbuckets + kScanTile - 1) / kScanTile : 0;
     L.ntiles_status = std::max<int64_t>(L.ntiles, bucket_tiles);
     size_t off = 0;
@@ -135,6 +137,9 @@ Layout make_layout(const smc_config *c) {
     L.obs = take((size_t)obs_vals * 8);
     L.obs_f = take((size_t)obs_vals * 4);
     L.alpha = take((c->model == SMC_MODEL_GMM) ? ((size_t)c->gmm.n_iter + 1) * 8 : 0);
+    L.dhist = take(hists ? (size_t)kHistWords * 4 : 0);
+    L.dpre = take(hists ? (size_t)kHistBuckets * 4 : 0);
+    L.dtot = take(hists ? (size_t)kHistTiles * 4 : 0);
     const bool rec = (c->flags & SMC_FLAG_RECORD) && c->model != SMC_MODEL_GMM;
     L.ck = (c->checkpoint_every > 0) ? c->checkpoint_every : 16;
     L.nck = rec ? (c->max_data + L.ck - 1) / L.ck : 0;
@@ -171,6 +176,8 @@ struct smc_ctx {
     uint32_t *cnt, *fill;
     unsigned long long *boff;
     uint32_t *sorted;
+    uint32_t *dhist;  // multinomial draw histogram: byte counts (cleared by each use)
+    uint32_t *dpre, *dtot;
     unsigned long long *RQ;
     uint32_t *extra;
     unsigned long long *O;
@@ -355,13 +362,9 @@ SortedTargets sorted_targets(smc_ctx *c, int from_residual) {
 // cooperative launch, so every block is resident and the kernel's grid
 // barrier completes; at most one block per scan tile.
 
-template <typename R, bool kS, class Sink>
-int launch_grid_resample(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
-    const int64_t n = c->cfg.n_particles;
-    const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
-    auto kern = grid_resample_kernel<QGen<R>, kS, Sink>;
-    static int per_sm[64] = {};  // resident blocks per SM, per device (this instantiation)
-    static int sms[64] = {};
+// Resident blocks of a cooperative kernel on the current device (cached per
+// kernel by the caller's arrays, indexed by device).
+int coop_capacity(const void *kern, int (&per_sm)[64], int (&sms)[64], int *slots) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SMC_E_CUDA;
     if (!per_sm[dev]) {
@@ -373,35 +376,73 @@ int launch_grid_resample(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
         sms[dev] = m;
         per_sm[dev] = b;
     }
-    const int grid = std::max(1, std::min({ntiles, per_sm[dev] * sms[dev], kMaxCoopGrid}));
+    *slots = per_sm[dev] * sms[dev];
+    return SMC_OK;
+}
+
+// Cooperative launch on the context's stream; while capturing the iteration
+// graph, also a programmatic dependent of the move kernel: the blocks become
+// resident while the move kernel's last block combines the partials and wait
+// (griddepcontrol.wait) for its completion.
+template <class... KArgs, class... Args>
+int launch_coop(smc_ctx *c, int grid, void (*kern)(KArgs...), Args... args) {
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)grid);
     lc.blockDim = dim3(kBlock);
     lc.dynamicSmemBytes = 0;
     lc.stream = c->stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = attr;
-    lc.numAttrs = 1;
-    cudaLaunchAttribute attr2[2];
-    if (c->dependent_launch) {
-        // programmatic dependent of the move kernel: the blocks become
-        // resident while the move kernel's last block combines the
-        // partials and wait (griddepcontrol.wait) for its completion
-        attr2[0] = attr[0];
-        attr2[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr2[1].val.programmaticStreamSerializationAllowed = 1;
-        lc.attrs = attr2;
-        lc.numAttrs = 2;
-    }
+    lc.numAttrs = c->dependent_launch ? 2 : 1;
+    return cuda_check(cudaLaunchKernelEx(&lc, kern, args...));
+}
+
+// One-pass systematic / stratified resampling (grid_resample_kernel): at
+// most one block per scan tile.
+template <typename R, bool kS, class Sink>
+int launch_grid_resample(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
+    const int64_t n = c->cfg.n_particles;
+    const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+    auto kern = grid_resample_kernel<QGen<R>, kS, Sink>;
+    static int per_sm[64] = {}, sms[64] = {};  // this instantiation
+    int slots = 0;
+    if (int rc = coop_capacity(reinterpret_cast<const void *>(kern), per_sm, sms, &slots)) return rc;
+    const int grid = std::max(1, std::min({ntiles, slots, kMaxCoopGrid}));
     GridTargets<kS> tg{};
     tg.n = n;
     tg.key = key_of(c);
     tg.stream = c->cfg.stream_id;
     tg.mrec = ~0ull / (unsigned long long)n;
-    return cuda_check(cudaLaunchKernelEx(&lc, kern, qg, tg, AncOut{c->anc}, sk, n, tsum_of(c, SLOT_CDF),
-                                         c->bsum, c->st, gate));
+    return launch_coop(c, grid, kern, qg, tg, AncOut{c->anc}, sk, n, tsum_of(c, SLOT_CDF), c->bsum, c->st, gate);
+}
+
+// One-pass multinomial resampling (grid_multinomial_kernel): one full wave
+// (blocks without a weight tile still count draws and scan the histogram).
+// The value thresholds v(X) = ceil(X 2^24 / Q_N - 1/2) are the systematic
+// closed form with n = 2^24 and c = 2^24.
+template <typename R, class Sink>
+int launch_grid_multinomial(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
+    const int64_t n = c->cfg.n_particles;
+    auto kern = grid_multinomial_kernel<R, Sink>;
+    static int per_sm[64] = {}, sms[64] = {};
+    int slots = 0;
+    if (int rc = coop_capacity(reinterpret_cast<const void *>(kern), per_sm, sms, &slots)) return rc;
+    const int grid = std::max(1, std::min(slots, kMaxCoopGrid));
+    GridTargets<false> tg{};
+    tg.n = int64_t(1) << kHistValueBits;
+    tg.key = key_of(c);
+    tg.stream = c->cfg.stream_id;
+    tg.c_fixed = 1ull << kHistValueBits;
+    tg.mrec = ~0ull >> kHistValueBits;  // floor((2^64 - 1) / 2^24)
+    HistArgs h;
+    h.hist = c->dhist;
+    h.hpre = c->dpre;
+    h.htot = c->dtot;
+    return launch_coop(c, grid, kern, qg, tg, AncOut{c->anc}, sk, n, tsum_of(c, SLOT_CDF), c->bsum, h, c->st, gate);
 }
 
 template <typename R>
@@ -423,15 +464,15 @@ int launch_resample(smc_ctx *c, int gate) {
         case SMC_STRATIFIED:
             return keep ? launch_grid_resample<R, true>(c, qg, qsink, gate)
                         : launch_grid_resample<R, true>(c, qg, NoSink{}, gate);
+        case SMC_MULTINOMIAL:
+            return keep ? launch_grid_multinomial<R>(c, qg, qsink, gate)
+                        : launch_grid_multinomial<R>(c, qg, NoSink{}, gate);
         default:
             break;
     }
     // tile sums of the fixed-point weights
     if ((rc = launch_reduce(c, qg, n, SLOT_CDF, gate))) return rc;
     switch (c->cfg.scheme) {
-        case SMC_MULTINOMIAL:
-            if ((rc = launch_uniform_sort(c, 0, gate))) return rc;
-            return launch_scan_select(c, qg, sorted_targets(c, 0), AncOut{c->anc}, qsink, n, SLOT_CDF, gate, 1);
         case SMC_RESIDUAL: {
             if (keep && (rc = launch_scan_select(c, qg, NoTargets{}, AncOut{nullptr}, qsink, n, SLOT_CDF, gate, 0)))
                 return rc;
@@ -643,6 +684,9 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->fill = reinterpret_cast<uint32_t *>(c->ws + L.fill);
     c->boff = reinterpret_cast<unsigned long long *>(c->ws + L.boff);
     c->sorted = reinterpret_cast<uint32_t *>(c->ws + L.sorted);
+    c->dhist = reinterpret_cast<uint32_t *>(c->ws + L.dhist);
+    c->dpre = reinterpret_cast<uint32_t *>(c->ws + L.dpre);
+    c->dtot = reinterpret_cast<uint32_t *>(c->ws + L.dtot);
     c->RQ = reinterpret_cast<unsigned long long *>(c->ws + L.RQ);
     c->extra = reinterpret_cast<uint32_t *>(c->ws + L.extra);
     c->O = reinterpret_cast<unsigned long long *>(c->ws + L.O);
@@ -1064,6 +1108,7 @@ const char *smc_error_string(int code) {
         case SMC_E_TIMEOUT: return "a bounded device wait gave up";
         case SMC_E_CUDA: return "CUDA runtime error";
         case SMC_E_STATE: return "call out of order";
+        case SMC_E_RANGE: return "a device counter left its range";
     }
     return "unknown error";
 }

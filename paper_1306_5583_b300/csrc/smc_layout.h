@@ -16,6 +16,14 @@ constexpr int kScanTile = kBlock * kScanItems;  // 2048 elements per scan tile
 constexpr int kScanSlots = 6;                   // independent scans per iteration
 constexpr uint32_t kSpinLimit = 1u << 24;       // bounded waits (about 1 s with backoff)
 
+// Histogram of the 24-bit multinomial draws: one byte count per value, four
+// to a 32-bit word, 16 values (one uint4) to a bucket, kScanTile buckets to a
+// histogram tile.
+constexpr int kHistValueBits = 24;
+constexpr int64_t kHistWords = int64_t(1) << (kHistValueBits - 2);
+constexpr int64_t kHistBuckets = int64_t(1) << (kHistValueBits - 4);
+constexpr int kHistTiles = (int)(kHistBuckets / kScanTile);  // 512
+
 // Philox purpose tags (counter word 2, low 16 bits)
 constexpr uint32_t TAG_INIT = 1;
 constexpr uint32_t TAG_MOVE = 2;

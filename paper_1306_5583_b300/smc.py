@@ -11,7 +11,7 @@ import numpy as np
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsmc.so")
 
-OK, E_ARG, E_WORKSPACE, E_NONFINITE, E_TIMEOUT, E_CUDA, E_STATE = range(7)
+OK, E_ARG, E_WORKSPACE, E_NONFINITE, E_TIMEOUT, E_CUDA, E_STATE, E_RANGE = range(8)
 MULTINOMIAL, STRATIFIED, SYSTEMATIC, RESIDUAL = range(4)
 SCHEMES = {"multinomial": MULTINOMIAL, "stratified": STRATIFIED, "systematic": SYSTEMATIC,
            "residual": RESIDUAL}

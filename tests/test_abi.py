@@ -85,6 +85,6 @@ def test_create_rejects_bad_workspace_without_touching_the_device(L):
 
 
 def test_error_strings(L):
-    for code in range(7):
+    for code in range(8):
         assert L.smc_error_string(code)
     assert L.smc_error_string(99) == b"unknown error"

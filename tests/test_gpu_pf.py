@@ -118,7 +118,7 @@ def test_degenerate_weights_select_one_particle():
 
 
 @pytest.mark.parametrize("precision", [32, 64])
-@pytest.mark.parametrize("scheme", ["systematic", "stratified"])
+@pytest.mark.parametrize("scheme", ["systematic", "stratified", "multinomial"])
 def test_heavy_particles_in_some_tiles(scheme, precision):
     """Tiles where one particle owns hundreds of offspring beside tiles of
     ordinary weights, and a heavy particle in the ragged last tile: the
@@ -269,6 +269,15 @@ def test_full_size_sampled(scheme):
         assert np.all(np.diff(Q.astype(np.float64)) >= 0)
         a = s.ancestors().astype(np.int64)
         assert np.all(np.diff(a) >= 0) and a.min() >= 0 and a.max() < n
+        if scheme == "multinomial":
+            # output k: the first i with Q_i 2^25 > Q_N (2 j_(k) + 1), j_(k) the sorted draws
+            import bisect
+            QN = int(Q[-1])
+            js = np.sort(ophilox.resample_u24(seed, t, n).astype(np.int64))
+            Qlist = [int(v) for v in Q.astype(object)]
+            for k in g.choice(n, size=300, replace=False):
+                thr = (QN * (2 * int(js[k]) + 1)) >> 25
+                assert a[k] == bisect.bisect_right(Qlist, thr)
         if scheme in ("systematic", "stratified"):
             QN = int(Q[-1])
             ks = g.choice(n, size=300, replace=False)
@@ -286,6 +295,42 @@ def test_full_size_sampled(scheme):
             q = np.diff(np.concatenate([[0], Q.astype(object)])).astype(object)
             zero = np.array([int(v) == 0 for v in q])
             assert not np.any(zero[a])
+
+
+@pytest.mark.parametrize("n", [3 * (1 << 20) + 17, 5 * 2048 + 1])
+def test_multinomial_one_pass_sizes(n):
+    """Multinomial selection by the draw histogram where every block owns
+    several weight tiles (N above one wave of tiles) and where most blocks
+    own none: three forced resamplings in a row (the two histograms
+    alternate) give the oracle's ancestors on the GPU's CDF: a full
+    comparison at the small size, sampled outputs at the large one."""
+    need_gpu()
+    import bisect
+    seed = 4
+    s, y, op = make_pf(n, 4, 32, scheme="multinomial", threshold=0.0, seed=seed)
+    s.initialize()
+    g = np.random.default_rng(5)
+    for t in range(3):
+        if t:
+            s.move()  # the gather of the previous ancestors; iteration t
+        lw = g.normal(0.0, 1.5, n)
+        s.write_log_weight(lw)
+        lw_gpu = s.log_weight()
+        s.resample(force=True)
+        if n < 1 << 16:
+            check_resample(s, lw_gpu, t, "multinomial", seed, 32)
+            continue
+        Q = s.cdf()
+        a = s.ancestors().astype(np.int64)
+        assert np.all(np.diff(a) >= 0) and a.min() >= 0 and a.max() < n
+        QN = int(Q[-1])
+        js = np.sort(ophilox.resample_u24(seed, t, n).astype(np.int64))
+        Qlist = [int(v) for v in Q.astype(object)]
+        ks = np.concatenate([g.choice(n, size=400, replace=False), [0, n - 1]])
+        for k in ks:
+            thr = (QN * (2 * int(js[k]) + 1)) >> 25
+            assert a[k] == bisect.bisect_right(Qlist, thr), (t, k)
+    s.close()
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
