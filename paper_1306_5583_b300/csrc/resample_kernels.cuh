@@ -8,15 +8,16 @@
 //   systematic  P_k = 2^25 k + 2j + 1        D = N 2^25  (one j per iteration)
 //   stratified  P_k = 2^25 k + 2j_k + 1      D = N 2^25  (j_k independent)
 //   multinomial P_k = m (2 j_(k) + 1)        D = m 2^25  (j_(k) the sorted iid j's)
-//   expansion   P_k = k                      D = N       (offspring CDF, O_N = N)
-// and a_k = min{ i : Q_i D > Q_N P_k }.
+// and a_k = min{ i : Q_i D > Q_N P_k }.  Residual resampling takes the
+// multinomial targets on its residual weights (m = R draws) and puts the
+// deterministic copies in front of each particle's draws.
 //
-// Scans are reduce-then-scan (no inter-block waits): a tile-sum pass, then a
-// pass in which each tile adds the sums of the tiles before it, scans its
-// own values in shared memory and, when targets are given, selects the
-// ancestors whose targets fall in its CDF range (a contiguous range of
-// outputs, found in closed form or from the bucket ends of the sorted
-// uniforms) by a search over the shared-memory CDF tile.
+// Every scheme runs as one cooperative kernel (a grid barrier between the
+// scan of the weights and the selection) in which particle i writes its own
+// outputs [K(Q_{i-1}), K(Q_i)), K from a closed form (systematic,
+// stratified) or from a histogram of the draws (multinomial, residual).
+// The reduce-then-scan kernels with a merge-path search per output serve the
+// allocation-free systematic entry and the batched filters.
 #pragma once
 
 #include "grid_threshold.h"
@@ -72,13 +73,6 @@ __device__ __forceinline__ void gen_items(const Gen &g, int64_t i0, int64_t n, u
     }
 }
 
-// values read from an array (bucket counts)
-struct CountGen {
-    const uint32_t *cnt;
-    __device__ __forceinline__ void prepare(const DevState *) {}
-    __device__ __forceinline__ unsigned long long operator()(int64_t i) const { return cnt[i]; }
-};
-
 // floor(n q / qn) for q <= qn < 2^62, n < 2^31 (exact: float estimate, then
 // integer correction with 128-bit products)
 __device__ __forceinline__ unsigned long long floor_nq_over(unsigned long long n, unsigned long long q,
@@ -93,51 +87,6 @@ __device__ __forceinline__ unsigned long long floor_nq_over(unsigned long long n
     return d;
 }
 
-// residual resampling: deterministic copies d_i = floor(N q_i / Q_N)
-template <typename R>
-struct ResidualParts {
-    QGen<R> qg;
-    int64_t n;
-    unsigned long long qn;
-    __device__ __forceinline__ void prepare(const DevState *st) {
-        qg.prepare(st);
-        qn = st->qn;
-    }
-    __device__ __forceinline__ unsigned long long q(int64_t i) const { return qg(i); }
-    __device__ __forceinline__ unsigned long long d_of(unsigned long long qi) const {
-        return floor_nq_over((unsigned long long)n, qi, qn);
-    }
-};
-
-// residual weights r_i = rem_i >> s, rem_i = N q_i - d_i Q_N,
-// s = max(0, bitlen(R Q_N) - 62)
-template <typename R>
-struct ResidualRGen {
-    ResidualParts<R> p;
-    int shift;
-    __device__ __forceinline__ void prepare(const DevState *st) {
-        p.prepare(st);
-        const unsigned long long sd = st->sum_d;
-        const unsigned long long Rn = sd < (unsigned long long)p.n ? (unsigned long long)p.n - sd : 0ull;
-        shift = max(0, bitlen128(mul64(Rn, p.qn)) - 62);
-    }
-    __device__ __forceinline__ unsigned long long operator()(int64_t i) const {
-        const unsigned long long qi = p.q(i);
-        const unsigned long long di = p.d_of(qi);
-        const unsigned long long rem = (unsigned long long)p.n * qi - di * p.qn;  // < Q_N, exact mod 2^64
-        return rem >> shift;
-    }
-};
-
-// final offspring counts o_i = d_i + (residual draws of i)
-template <typename R>
-struct ResidualOGen {
-    ResidualParts<R> p;
-    const uint32_t *extra;
-    __device__ __forceinline__ void prepare(const DevState *st) { p.prepare(st); }
-    __device__ __forceinline__ unsigned long long operator()(int64_t i) const { return p.d_of(p.q(i)) + extra[i]; }
-};
-
 // ---------------------------------------------------------------- sinks --
 
 struct NoSink {
@@ -145,7 +94,7 @@ struct NoSink {
     __device__ __forceinline__ void operator()(int64_t, unsigned long long, DevState *) const {}
 };
 
-struct StoreSink {  // inclusive prefix sums to an array (the fixed-point CDF, bucket ends)
+struct StoreSink {  // inclusive prefix sums to an array (the fixed-point CDF)
     static constexpr bool kActive = true;
     unsigned long long *dst;
     __device__ __forceinline__ void operator()(int64_t i, unsigned long long v, DevState *) const {
@@ -347,83 +296,11 @@ struct GridTargets {
     }
 };
 
-// Sorted iid draws j_(0) <= ... <= j_(m-1) (multinomial selection, also the
-// residual step with m = R), P_k = m (2 j_(k) + 1), D = m 2^25, so
-// tau_k = floor(QN (2 j_(k) + 1) / 2^25).  The rank of a threshold comes from
-// the bucket ends of the sort plus a scan of one (small) bucket.
-struct SortedTargets {
-    static constexpr bool kActive = true;
-    const uint32_t *sorted;
-    const unsigned long long *bend;  // inclusive bucket ends
-    int bucket_shift;
-    int64_t n_total;
-    int from_residual;
-    unsigned long long m, qn;
-    __device__ __forceinline__ void prepare(const DevState *st) {
-        const unsigned long long sd = st->sum_d;
-        m = from_residual ? (sd < (unsigned long long)n_total ? (unsigned long long)n_total - sd : 0ull)
-                          : (unsigned long long)n_total;
-    }
-    __device__ __forceinline__ void setup(unsigned long long QN) { qn = QN; }
-    __device__ __forceinline__ int64_t count() const { return (int64_t)m; }
-    // first k with QN m (2 s_k + 1) >= X m 2^25, i.e. 2 s_k + 1 >= X 2^25 / QN,
-    // i.e. s_k >= v with v the smallest s such that 2 s + 1 >= ceil(X 2^25 / QN)
-    __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long QN) const {
-        if (m == 0) return 0;
-        // c = ceil(X 2^25 / QN) <= 2^25 (X <= QN): double-float estimate, exact correction
-        const U128 y{X >> 39, X << 25};
-        const DF e = df_div(df_from_u64(X), df_from_u64(QN));
-        long long c0 = (long long)__float2uint_ru(fmaxf(e.hi * 33554432.0f, 0.0f));
-        if (c0 > (1ll << 25) + 1) c0 = (1ll << 25) + 1;
-        unsigned long long cc = (unsigned long long)c0;
-        while (cc > 0 && !gt128(y, mul64(cc - 1, QN))) --cc;  // (cc - 1) QN < y
-        while (gt128(y, mul64(cc, QN))) ++cc;                  // y <= cc QN
-        if (cc > (1ull << 25)) return (int64_t)m;
-        const unsigned long long v = cc / 2;
-        if (v >= (1ull << 24)) return (int64_t)m;
-        const int64_t b = (int64_t)(v >> bucket_shift);
-        int64_t lo = b ? (int64_t)bend[b - 1] : 0;
-        const int64_t hi = (int64_t)bend[b];
-        while (lo < hi && sorted[lo] < v) ++lo;
-        return lo;
-    }
-    __device__ __forceinline__ void thresholds(int64_t k0, unsigned long long (&tau)[kScanItems]) const {
-#pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            const unsigned long long s = (k0 + j < (int64_t)m) ? (unsigned long long)sorted[k0 + j] : 0ull;
-            const U128 p = mul64(qn, 2ull * s + 1ull);
-            tau[j] = (p.hi << 39) | (p.lo >> 25);
-        }
-    }
-};
-
-// Expansion of an offspring CDF O (O_N = N, so QN = D and tau_k = k):
-// a_k = min{i : O_i > k}.
-struct ExpandTargets {
-    static constexpr bool kActive = true;
-    int64_t n;
-    __device__ __forceinline__ void prepare(const DevState *) {}
-    __device__ __forceinline__ void setup(unsigned long long) {}
-    __device__ __forceinline__ int64_t count() const { return n; }
-    __device__ __forceinline__ int64_t first_at_least(unsigned long long X, unsigned long long) const {
-        return (int64_t)min(X, (unsigned long long)n);
-    }
-    __device__ __forceinline__ void thresholds(int64_t k0, unsigned long long (&tau)[kScanItems]) const {
-#pragma unroll
-        for (int j = 0; j < kScanItems; ++j) tau[j] = (unsigned long long)(k0 + j);
-    }
-};
-
 // ----------------------------------------------------------------- outputs --
 
 struct AncOut {
     int32_t *anc;
     __device__ __forceinline__ void operator()(int64_t k, int32_t a) const { anc[k] = a; }
-};
-
-struct CountOut {  // residual draws: histogram of the selected particles
-    uint32_t *extra;
-    __device__ __forceinline__ void operator()(int64_t, int32_t a) const { atomicAdd(&extra[a], 1u); }
 };
 
 // ---------------------------------------------------------------- kernels --
@@ -568,14 +445,10 @@ struct TileBufs {
     int64_t k[2];                                       // the tile's output range
 };
 
-// Inclusive scan of the tile's values into tb.q (tile-relative; zeros past
-// n); returns the tile's total to every thread.
-template <class Gen>
-__device__ __forceinline__ unsigned long long scan_tile_local(const Gen &g, int64_t n, int tile, TileBufs &tb) {
+// Inclusive scan of kScanItems values per thread (thread t owns the tile
+// entries t kScanItems + j) into tb.q; returns the total to every thread.
+__device__ __forceinline__ unsigned long long scan_items_q(unsigned long long (&loc)[kScanItems], TileBufs &tb) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t t0 = (int64_t)tile * kScanTile;
-    unsigned long long loc[kScanItems];
-    gen_items(g, t0 + (int64_t)tid * kScanItems, n, loc);
     unsigned long long acc = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
@@ -595,6 +468,15 @@ __device__ __forceinline__ unsigned long long scan_tile_local(const Gen &g, int6
     for (int j = 0; j < kScanItems; ++j) tb.q[pad8(tid * kScanItems + j)] = base + loc[j];
     __syncthreads();
     return tb.q[pad8(kScanTile - 1)];
+}
+
+// Inclusive scan of the tile's values into tb.q (tile-relative; zeros past
+// n); returns the tile's total to every thread.
+template <class Gen>
+__device__ __forceinline__ unsigned long long scan_tile_local(const Gen &g, int64_t n, int tile, TileBufs &tb) {
+    unsigned long long loc[kScanItems];
+    gen_items(g, (int64_t)tile * kScanTile + (int64_t)threadIdx.x * kScanItems, n, loc);
+    return scan_items_q(loc, tb);
 }
 
 // Selection for one scanned tile (tb.q holds its tile-relative prefix sums,
@@ -1101,116 +983,177 @@ __global__ void __launch_bounds__(kBlock, 4) grid_multinomial_kernel(QGen<R> gen
     grid_depart(st);
 }
 
-// ------------------------------------------------- sorting iid uniforms --
+// ------------------------------------------------- residual, one pass --
+//
+// Residual resampling (deterministic copies d_i = floor(N q_i / Q_N), then
+// R = N - sum d multinomial draws on the residual weights
+// r_i = (N q_i - d_i Q_N) >> s, s = max(0, bitlen(R Q_N) - 62)) with the
+// offspring in particle order: particle i owns the outputs [O_{i-1}, O_i),
+// O_i = D_i + H_R(v(RQ_i)), D and RQ the prefix sums of d and r, H_R the
+// histogram count of the R draws below a value and v the multinomial value
+// threshold taken on RQ_N.
 
-struct UniformSortArgs {
-    uint2 key;
-    uint32_t stream;
-    int64_t n_total;      // N
-    int from_residual;    // count = N - sum_d (residual step) or N
-    int bucket_shift;     // bucket = j >> bucket_shift
-    uint32_t *cnt;        // [nbuckets], zero on entry
-    uint32_t *fill;       // [nbuckets], zero on entry
-    unsigned long long *bend;  // [nbuckets] inclusive bucket ends
-    uint32_t *sorted;     // [N]
-    int64_t nbuckets;
+// per-tile and per-block sums of the three passes (q, d, r)
+struct ResidualSums {
+    unsigned long long *tq, *td, *tr;  // [ntiles]
+    unsigned long long *bq, *bd, *br;  // [gridDim.x]
 };
 
-__device__ __forceinline__ int64_t draw_count(const UniformSortArgs &a, const DevState *st) {
-    if (!a.from_residual) return a.n_total;
-    const unsigned long long sd = st->sum_d;
-    return sd < (unsigned long long)a.n_total ? a.n_total - (int64_t)sd : 0;
-}
-
-__global__ void __launch_bounds__(kBlock) bucket_count_kernel(UniformSortArgs a, DevState *st, int gate) {
-    const DevState *sv = snapshot(st);
-    if (gated_out(sv, gate)) return;
-    const int64_t count = draw_count(a, sv);
-    const uint32_t t = (uint32_t)sv->t;
-    const int64_t k4 = 4 * ((int64_t)blockIdx.x * kBlock + threadIdx.x);
-    if (k4 >= count) return;
-    const uint4 w = resample_words(a.key, a.stream, t, k4);
-    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+// d_i and r_i of the thread's kScanItems particles from the tile's q scan in
+// tb.q (zeros past n give zeros)
+__device__ __forceinline__ void residual_items(const TileBufs &tb, unsigned long long N, unsigned long long QN,
+                                               int shift, unsigned long long (&d)[kScanItems],
+                                               unsigned long long (&r)[kScanItems]) {
+    const int base = threadIdx.x * kScanItems;
+    unsigned long long prev = base ? tb.q[pad8(base - 1)] : 0ull;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (k4 + j < count) atomicAdd(&a.cnt[u24(ww[j]) >> a.bucket_shift], 1u);
-}
-
-__global__ void __launch_bounds__(kBlock) bucket_scatter_kernel(UniformSortArgs a, DevState *st, int gate) {
-    const DevState *sv = snapshot(st);
-    if (gated_out(sv, gate)) return;
-    const int64_t count = draw_count(a, sv);
-    const uint32_t t = (uint32_t)sv->t;
-    const int64_t k4 = 4 * ((int64_t)blockIdx.x * kBlock + threadIdx.x);
-    if (k4 >= count) return;
-    const uint4 w = resample_words(a.key, a.stream, t, k4);
-    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        if (k4 + j < count) {
-            const uint32_t jj = u24(ww[j]);
-            const int64_t b = jj >> a.bucket_shift;
-            const unsigned long long start = a.bend[b] - a.cnt[b];
-            const uint32_t pos = atomicAdd(&a.fill[b], 1u);
-            a.sorted[start + pos] = jj;
-        }
+    for (int j = 0; j < kScanItems; ++j) {
+        const unsigned long long qc = tb.q[pad8(base + j)];
+        const unsigned long long qi = qc - prev;
+        prev = qc;
+        d[j] = floor_nq_over(N, qi, QN);
+        r[j] = (N * qi - d[j] * QN) >> shift;  // the remainder is below Q_N: exact modulo 2^64
     }
 }
 
-// one thread per bucket: insertion sort of the (few) values in the bucket,
-// then clear the counters for the next use
-__global__ void __launch_bounds__(kBlock) bucket_sort_kernel(UniformSortArgs a, DevState *st, int gate) {
-    const DevState *sv = snapshot(st);
+// The residual count map: O = H_R(v) + the deterministic copies up to the
+// boundary (d0 before the tile, dloc[j] the tile-relative inclusive prefix)
+struct ResidualMap {
+    HistMap hm;
+    int64_t d0;
+    const int32_t *dloc;  // pad32 layout
+    __device__ __forceinline__ void map_items(int32_t *K, int base, int64_t *k0) const {
+        hm.map_items(K, base, k0);
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) K[pad32(base + j)] += (int32_t)(d0 + dloc[pad32(base + j)]);
+        if (k0) *k0 += d0;
+    }
+};
+
+// q, d and r of one tile into the tile buffers for the selection: the q scan
+// in tb.q on entry (kept or rescanned); on exit tb.q holds the r scan and
+// tb.a the d scan (tile-relative, int32: at most N)
+__device__ __forceinline__ void residual_tile_scans(TileBufs &tb, unsigned long long N, unsigned long long QN,
+                                                    int shift) {
+    unsigned long long d[kScanItems], r[kScanItems];
+    residual_items(tb, N, QN, shift, d, r);
+    scan_items_q(d, tb);  // d scan (every thread has read its q entries before the first barrier inside)
+    const int base = threadIdx.x * kScanItems;
+    int32_t *dl = tb.a;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) dl[pad32(base + j)] = (int32_t)tb.q[pad8(base + j)];
+    scan_items_q(r, tb);
+}
+
+// One-pass residual resampling: a cooperative launch of one full wave.
+// Phase 1: histogram share cleared, q tile sums (a block with one tile keeps
+// its q scan until phase 3); barrier; phase 2: Q_N, d sums (and the stored
+// CDF); barrier; phase 3: R and s, the R draws into the histogram, r sums;
+// barrier; phase 4: histogram tiles, the block's r prefix and targets;
+// barrier; phase 5: selection.  Blocks with several tiles rescan the q of
+// every tile in every phase.
+template <typename R, class Sink>
+__global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, GridTargets<false> tgt, AncOut out,
+                                                               Sink sink, int64_t n, ResidualSums rs, HistArgs h,
+                                                               DevState *st, int gate) {
+    __shared__ TileBufs tb;
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // as in grid_resample_kernel
+    const DevState *sv = snapshot(st, true);
     if (gated_out(sv, gate)) return;
-    const int64_t b = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-    if (b >= a.nbuckets) return;
-    const uint32_t c = a.cnt[b];
-    if (c > 1) {
-        const unsigned long long lo = a.bend[b] - c;
-        for (uint32_t i = 1; i < c; ++i) {
-            const uint32_t v = a.sorted[lo + i];
-            uint32_t j = i;
-            while (j > 0 && a.sorted[lo + j - 1] > v) {
-                a.sorted[lo + j] = a.sorted[lo + j - 1];
-                --j;
+    QGen<R> g = gen;
+    g.prepare(sv);
+    const int G = gridDim.x, b = blockIdx.x;
+    const unsigned long long N = (unsigned long long)n;
+    {
+        uint4 *h4 = reinterpret_cast<uint4 *>(h.hist);
+        const int64_t z_hi = kHistBuckets * (b + 1) / G;
+        for (int64_t i = kHistBuckets * b / G + threadIdx.x; i < z_hi; i += kBlock) h4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+    const int t_lo = (int)((int64_t)ntiles * b / G), t_hi = (int)((int64_t)ntiles * (b + 1) / G);
+    const bool keep = (t_hi - t_lo == 1);  // the one tile's q scan stays in tb.q
+    // phase 1: q tile sums
+    unsigned long long bq = 0;
+    for (int tile = t_lo; tile < t_hi; ++tile) {
+        const unsigned long long s = scan_tile_local(g, n, tile, tb);
+        if (threadIdx.x == 0) rs.tq[tile] = s;
+        bq += s;
+    }
+    if (threadIdx.x == 0) rs.bq[b] = bq;
+    if (!grid_barrier(st, G)) return;
+    if (b == 0 && threadIdx.x == 0) st->ready = 1;
+    // phase 2: d sums; the CDF of q where it is stored
+    unsigned long long pre_q, QN;
+    tile_prefix_total(rs.bq, b, G, &pre_q, &QN);
+    unsigned long long bd = 0;
+    for (int tile = t_lo; tile < t_hi; ++tile) {
+        const unsigned long long ts = keep ? bq : scan_tile_local(g, n, tile, tb);
+        unsigned long long d[kScanItems], r[kScanItems];
+        residual_items(tb, N, QN, 0, d, r);
+        unsigned long long sd = 0;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) sd += d[j];
+        sd = block_sum_u64(sd);
+        if (threadIdx.x == 0) rs.td[tile] = sd;
+        bd += sd;
+        if (Sink::kActive) select_tile(NoTargets{}, out, sink, n, tile, pre_q, ts, QN, st, tb);
+        pre_q += ts;
+    }
+    if (threadIdx.x == 0) rs.bd[b] = bd;
+    if (!grid_barrier(st, 2 * G)) return;
+    // phase 3: R, s, the draws; r sums (a kept tile also gets its d and r scans)
+    unsigned long long pre_d, Dtot;
+    tile_prefix_total(rs.bd, b, G, &pre_d, &Dtot);
+    const unsigned long long Rn = Dtot < N ? N - Dtot : 0ull;
+    const int shift = max(0, bitlen128(mul64(Rn, QN)) - 62);
+    hist_draws(tgt.key, tgt.stream, (uint32_t)sv->t, (int64_t)Rn, h.hist, b, G);
+    unsigned long long br = 0;
+    for (int tile = t_lo; tile < t_hi; ++tile) {
+        unsigned long long sr;
+        if (keep) {
+            residual_tile_scans(tb, N, QN, shift);
+            sr = tb.q[pad8(kScanTile - 1)];
+        } else {
+            scan_tile_local(g, n, tile, tb);
+            unsigned long long d[kScanItems], r[kScanItems];
+            residual_items(tb, N, QN, shift, d, r);
+            sr = 0;
+#pragma unroll
+            for (int j = 0; j < kScanItems; ++j) sr += r[j];
+            sr = block_sum_u64(sr);
+        }
+        if (threadIdx.x == 0) rs.tr[tile] = sr;
+        br += sr;
+    }
+    if (threadIdx.x == 0) rs.br[b] = br;
+    if (!grid_barrier(st, 3 * G)) return;
+    // phase 4: histogram tiles; the r prefix and the targets on RQ_N
+    const int h_lo = (int)((int64_t)kHistTiles * b / G), h_hi = (int)((int64_t)kHistTiles * (b + 1) / G);
+    for (int ht = h_lo; ht < h_hi; ++ht) hist_scan_tile(reinterpret_cast<const uint4 *>(h.hist), h.hpre, h.htot, ht);
+    unsigned long long pre_r, RQN;
+    tile_prefix_total(rs.br, b, G, &pre_r, &RQN);
+    // RQ_N = 0 exactly when R = 0: any positive total then gives v = 0 and H = 0
+    const GridTargets<false> tg = block_targets(tgt, sv, RQN ? RQN : 1ull);
+    if (!grid_barrier(st, 4 * G)) return;
+    // phase 5: selection
+    if (t_hi > t_lo) {  // the same branch in the whole block
+        uint32_t *tpre = reinterpret_cast<uint32_t *>(tb.tau) + kHistTpreOffset;
+        const uint32_t total = hist_tile_prefix(h.htot, tpre);
+        if (total != (uint32_t)Rn && threadIdx.x == 0) raise_error(st, SMC_E_RANGE);  // a wrapped count
+        const HistMap hm{reinterpret_cast<const uint4 *>(h.hist), h.hpre, tpre, (int64_t)Rn};
+        unsigned long long d0 = pre_d, r0 = pre_r;
+        for (int tile = t_lo; tile < t_hi; ++tile) {
+            if (!keep) {
+                scan_tile_local(g, n, tile, tb);
+                residual_tile_scans(tb, N, QN, shift);
             }
-            a.sorted[lo + j] = v;
+            const ResidualMap km{hm, (int64_t)d0, tb.a};
+            select_tile_closed(tg, out, n, tile, r0, RQN ? RQN : 1ull, tb, km);
+            d0 += __ldcg(&rs.td[tile]);
+            r0 += __ldcg(&rs.tr[tile]);
         }
     }
-    a.cnt[b] = 0;
-    a.fill[b] = 0;
-}
-
-// ----------------------------------------------------------- residual ----
-
-// sum_i d_i -> st->sum_d (zeroed before the launch); clears the residual
-// draw histogram
-template <typename R>
-__global__ void __launch_bounds__(kBlock) residual_d_kernel(ResidualParts<R> p, uint32_t *extra, DevState *st,
-                                                            int gate) {
-    __shared__ unsigned long long s_w[kBlock / 32];
-    const DevState *sv = snapshot(st);
-    if (gated_out(sv, gate)) return;
-    ResidualParts<R> pp = p;
-    pp.prepare(sv);
-    const int64_t i0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
-    unsigned long long acc = 0;
-#pragma unroll
-    for (int r = 0; r < kScanItems; ++r) {
-        const int64_t i = i0 + r * kBlock;
-        if (i < pp.n) {
-            acc += pp.d_of(pp.q(i));
-            extra[i] = 0u;
-        }
-    }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long s = 0;
-        for (int w = 0; w < kBlock / 32; ++w) s += s_w[w];
-        atomicAdd(&st->sum_d, s);
-    }
+    grid_depart(st);
 }
 
 }  // namespace smc

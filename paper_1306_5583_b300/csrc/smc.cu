@@ -52,7 +52,7 @@ int ceil_log2(int64_t n) {
 }
 
 struct Layout {
-    size_t st, rec, part, x, lw, anc, Q, tsum, bsum, inc, cnt, fill, boff, sorted, RQ, extra, O, obs, obs_f, alpha;
+    size_t st, rec, part, x, lw, anc, Q, tsum, bsum, inc, obs, obs_f, alpha;
     size_t dhist, dpre, dtot;  // multinomial draw histogram, bucket prefixes, tile totals
     size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, total;
     int ck;           // steps between checkpoints (record mode)
@@ -61,9 +61,6 @@ struct Layout {
     int64_t ld;       // row pitch in elements (N rounded up to 64: 16-byte aligned rows)
     int64_t nbw;      // blocks of the weighting kernels
     int64_t ntiles;   // scan tiles of an N-element scan
-    int64_t nbuckets;
-    int64_t ntiles_status;
-    int bucket_shift;
     size_t rsize;
 };
 
@@ -100,14 +97,7 @@ Layout make_layout(const smc_config *c) {
     L.ld = (n + 63) & ~int64_t(63);
     L.nbw = (n + kPfTile - 1) / kPfTile;
     L.ntiles = (n + kScanTile - 1) / kScanTile;
-    const int B = std::min(24, std::max(1, ceil_log2(n)));
-    L.bucket_shift = 24 - B;
-    L.nbuckets = int64_t(1) << B;
-    const bool sorts = (c->scheme == SMC_RESIDUAL);
-    const bool resid = (c->scheme == SMC_RESIDUAL);
-    const bool hists = (c->scheme == SMC_MULTINOMIAL);
-    const int64_t bucket_tiles = sorts ? (L.nbuckets + kScanTile - 1) / kScanTile : 0;
-    L.ntiles_status = std::max<int64_t>(L.ntiles, bucket_tiles);
+    const bool hists = (c->scheme == SMC_MULTINOMIAL || c->scheme == SMC_RESIDUAL);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -123,16 +113,9 @@ Layout make_layout(const smc_config *c) {
     L.lw = take(2 * (size_t)L.ld * rs);
     L.anc = take((size_t)L.ld * 4);
     L.Q = take((size_t)n * 8);
-    L.tsum = take((size_t)kScanSlots * L.ntiles_status * 8);
-    L.bsum = take((size_t)kMaxCoopGrid * 8);  // block sums of the cooperative kernels
+    L.tsum = take((size_t)kScanSlots * L.ntiles * 8);
+    L.bsum = take((size_t)3 * kMaxCoopGrid * 8);  // block sums of the cooperative kernels (three for residual)
     L.inc = take((size_t)L.ld * rs);            // staged increments of smc_add_log_weight
-    L.cnt = take(sorts ? (size_t)L.nbuckets * 4 : 0);
-    L.fill = take(sorts ? (size_t)L.nbuckets * 4 : 0);
-    L.boff = take(sorts ? (size_t)L.nbuckets * 8 : 0);
-    L.sorted = take(sorts ? (size_t)n * 4 : 0);
-    L.RQ = take(resid ? (size_t)n * 8 : 0);
-    L.extra = take(resid ? (size_t)n * 4 : 0);
-    L.O = take(resid ? (size_t)n * 8 : 0);
     const int64_t obs_vals = (c->model == SMC_MODEL_GMM) ? c->max_data : 2 * c->max_data;
     L.obs = take((size_t)obs_vals * 8);
     L.obs_f = take((size_t)obs_vals * 4);
@@ -173,14 +156,9 @@ struct smc_ctx {
     unsigned long long *Q;
     unsigned long long *tsum;
     unsigned long long *bsum;  // block sums of the cooperative kernels (kMaxCoopGrid)
-    uint32_t *cnt, *fill;
-    unsigned long long *boff;
     uint32_t *sorted;
     uint32_t *dhist;  // multinomial draw histogram: byte counts (cleared by each use)
     uint32_t *dpre, *dtot;
-    unsigned long long *RQ;
-    uint32_t *extra;
-    unsigned long long *O;
     double *obs;
     float *obs_f;
     double *alpha;
@@ -212,7 +190,6 @@ __global__ void reset_state_kernel(DevState *st) {
     st->ready = 0;
     st->error = 0;
     st->ticket = 0;
-    st->count_r = 0;
     st->max_lw = 0;
     st->log_norm = 0;
     st->max_lw_f = 0;
@@ -222,8 +199,6 @@ __global__ void reset_state_kernel(DevState *st) {
     st->alpha = 0;
     st->path_u = 0;
     st->path_log_z = 0;
-    st->qn = 0;
-    st->sum_d = 0;
     st->grid_count = 0;
     st->grid_depart = 0;
     for (int i = 0; i < 4; ++i) st->accept[i] = 0;
@@ -291,76 +266,7 @@ int launch_pf(smc_ctx *c) {
     return cuda_check(cudaGetLastError());
 }
 
-unsigned long long *tsum_of(smc_ctx *c, int slot) { return c->tsum + (size_t)slot * c->L.ntiles_status; }
-
-// tile-sum pass: tsum[slot][tile]; with want_total the exact total also goes
-// to st->scan_total[slot] (otherwise the scan pass sums the tiles itself)
-template <class Gen>
-int launch_reduce(smc_ctx *c, Gen g, int64_t n, int slot, int gate, bool want_total = false) {
-    const unsigned grid = (unsigned)((n + kScanTile - 1) / kScanTile);
-    tile_reduce_kernel<Gen><<<grid, kBlock, 0, c->stream>>>(
-        g, n, tsum_of(c, slot), want_total ? &c->st->scan_total[slot] : nullptr, &c->st->scan_ticket[slot], c->st,
-        gate);
-    return cuda_check(cudaGetLastError());
-}
-
-// scan pass (after launch_reduce on the same slot) with optional selection
-template <class Gen, class Tgt, class Out, class Sink>
-int launch_scan_select(smc_ctx *c, Gen g, Tgt tg, Out o, Sink sk, int64_t n, int slot, int gate, int set_ready) {
-    const unsigned grid = (unsigned)((n + kScanTile - 1) / kScanTile);
-    scan_select_kernel<Gen, Tgt, Out, Sink><<<grid, kBlock, 0, c->stream>>>(g, tg, o, sk, n, tsum_of(c, slot), nullptr,
-                                                                            c->st, gate, set_ready);
-    return cuda_check(cudaGetLastError());
-}
-
-UniformSortArgs sort_args(smc_ctx *c, int from_residual) {
-    UniformSortArgs a;
-    a.key = key_of(c);
-    a.stream = c->cfg.stream_id;
-    a.n_total = c->cfg.n_particles;
-    a.from_residual = from_residual;
-    a.bucket_shift = c->L.bucket_shift;
-    a.cnt = c->cnt;
-    a.fill = c->fill;
-    a.bend = c->boff;
-    a.sorted = c->sorted;
-    a.nbuckets = c->L.nbuckets;
-    return a;
-}
-
-// sorted iid 24-bit uniforms (N of them, or R for the residual step)
-int launch_uniform_sort(smc_ctx *c, int from_residual, int gate) {
-    UniformSortArgs a = sort_args(c, from_residual);
-    const int64_t n = c->cfg.n_particles;
-    const unsigned g4 = (unsigned)((n + 4 * kBlock - 1) / (4 * kBlock));
-    int rc;
-    bucket_count_kernel<<<g4, kBlock, 0, c->stream>>>(a, c->st, gate);
-    if ((rc = cuda_check(cudaGetLastError()))) return rc;
-    if ((rc = launch_reduce(c, CountGen{c->cnt}, c->L.nbuckets, SLOT_BUCKET, gate))) return rc;
-    if ((rc = launch_scan_select(c, CountGen{c->cnt}, NoTargets{}, AncOut{nullptr}, StoreSink{c->boff},
-                                 c->L.nbuckets, SLOT_BUCKET, gate, 0)))
-        return rc;
-    bucket_scatter_kernel<<<g4, kBlock, 0, c->stream>>>(a, c->st, gate);
-    if ((rc = cuda_check(cudaGetLastError()))) return rc;
-    const unsigned gb = (unsigned)((c->L.nbuckets + kBlock - 1) / kBlock);
-    bucket_sort_kernel<<<gb, kBlock, 0, c->stream>>>(a, c->st, gate);
-    return cuda_check(cudaGetLastError());
-}
-
-SortedTargets sorted_targets(smc_ctx *c, int from_residual) {
-    SortedTargets tg;
-    tg.sorted = c->sorted;
-    tg.bend = c->boff;
-    tg.bucket_shift = c->L.bucket_shift;
-    tg.n_total = c->cfg.n_particles;
-    tg.from_residual = from_residual;
-    tg.m = 0;
-    return tg;
-}
-
-// One-pass systematic / stratified resampling (grid_resample_kernel): a
-// cooperative launch, so every block is resident and the kernel's grid
-// barrier completes; at most one block per scan tile.
+unsigned long long *tsum_of(smc_ctx *c, int slot) { return c->tsum + (size_t)slot * c->L.ntiles; }
 
 // Resident blocks of a cooperative kernel on the current device (cached per
 // kernel by the caller's arrays, indexed by device).
@@ -445,11 +351,40 @@ int launch_grid_multinomial(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
     return launch_coop(c, grid, kern, qg, tg, AncOut{c->anc}, sk, n, tsum_of(c, SLOT_CDF), c->bsum, h, c->st, gate);
 }
 
+// One-pass residual resampling (grid_residual_kernel): one full wave; the
+// q, d and r tile sums in three scan slots, the block sums in three rows.
+template <typename R, class Sink>
+int launch_grid_residual(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
+    const int64_t n = c->cfg.n_particles;
+    auto kern = grid_residual_kernel<R, Sink>;
+    static int per_sm[64] = {}, sms[64] = {};
+    int slots = 0;
+    if (int rc = coop_capacity(reinterpret_cast<const void *>(kern), per_sm, sms, &slots)) return rc;
+    const int grid = std::max(1, std::min(slots, kMaxCoopGrid));
+    GridTargets<false> tg{};
+    tg.n = int64_t(1) << kHistValueBits;
+    tg.key = key_of(c);
+    tg.stream = c->cfg.stream_id;
+    tg.c_fixed = 1ull << kHistValueBits;
+    tg.mrec = ~0ull >> kHistValueBits;
+    HistArgs h;
+    h.hist = c->dhist;
+    h.hpre = c->dpre;
+    h.htot = c->dtot;
+    ResidualSums rs;
+    rs.tq = tsum_of(c, SLOT_CDF);
+    rs.td = tsum_of(c, SLOT_RES_D);
+    rs.tr = tsum_of(c, SLOT_RES_R);
+    rs.bq = c->bsum;
+    rs.bd = c->bsum + kMaxCoopGrid;
+    rs.br = c->bsum + 2 * kMaxCoopGrid;
+    return launch_coop(c, grid, kern, qg, tg, AncOut{c->anc}, sk, n, rs, h, c->st, gate);
+}
+
 template <typename R>
 int launch_resample(smc_ctx *c, int gate) {
     const int64_t n = c->cfg.n_particles;
     const bool keep = (c->cfg.flags & SMC_FLAG_KEEP_CDF) != 0;
-    int rc;
     QGen<R> qg;
     qg.lw[0] = static_cast<const R *>(c->lw[0]);
     qg.lw[1] = static_cast<const R *>(c->lw[1]);
@@ -457,7 +392,7 @@ int launch_resample(smc_ctx *c, int gate) {
     qg.cur_lw = nullptr;
     qg.m = 0;
     const StoreSink qsink{keep ? c->Q : nullptr};
-    switch (c->cfg.scheme) {  // one pass
+    switch (c->cfg.scheme) {  // one cooperative pass each
         case SMC_SYSTEMATIC:
             return keep ? launch_grid_resample<R, false>(c, qg, qsink, gate)
                         : launch_grid_resample<R, false>(c, qg, NoSink{}, gate);
@@ -467,36 +402,10 @@ int launch_resample(smc_ctx *c, int gate) {
         case SMC_MULTINOMIAL:
             return keep ? launch_grid_multinomial<R>(c, qg, qsink, gate)
                         : launch_grid_multinomial<R>(c, qg, NoSink{}, gate);
+        case SMC_RESIDUAL:
+            return keep ? launch_grid_residual<R>(c, qg, qsink, gate) : launch_grid_residual<R>(c, qg, NoSink{}, gate);
         default:
             break;
-    }
-    // tile sums of the fixed-point weights
-    if ((rc = launch_reduce(c, qg, n, SLOT_CDF, gate))) return rc;
-    switch (c->cfg.scheme) {
-        case SMC_RESIDUAL: {
-            if (keep && (rc = launch_scan_select(c, qg, NoTargets{}, AncOut{nullptr}, qsink, n, SLOT_CDF, gate, 0)))
-                return rc;
-            // Q_N for the residual generators (the tile-sum pass again, with its total)
-            if ((rc = launch_reduce(c, qg, n, SLOT_CDF, gate, true))) return rc;
-            if ((rc = cuda_check(cudaMemcpyAsync(&c->st->qn, &c->st->scan_total[SLOT_CDF], 8,
-                                                 cudaMemcpyDeviceToDevice, c->stream))))
-                return rc;
-            if ((rc = cuda_check(cudaMemsetAsync(&c->st->sum_d, 0, sizeof(unsigned long long), c->stream))))
-                return rc;
-            ResidualParts<R> p{qg, n, 0};
-            const unsigned gt = (unsigned)((n + kScanTile - 1) / kScanTile);
-            residual_d_kernel<R><<<gt, kBlock, 0, c->stream>>>(p, c->extra, c->st, gate);
-            if ((rc = cuda_check(cudaGetLastError()))) return rc;
-            ResidualRGen<R> rg{p, 0};
-            if ((rc = launch_reduce(c, rg, n, SLOT_RES_R, gate, true))) return rc;
-            if ((rc = launch_uniform_sort(c, 1, gate))) return rc;
-            if ((rc = launch_scan_select(c, rg, sorted_targets(c, 1), CountOut{c->extra}, NoSink{}, n, SLOT_RES_R,
-                                         gate, 0)))
-                return rc;
-            ResidualOGen<R> og{p, c->extra};
-            if ((rc = launch_reduce(c, og, n, SLOT_RES_O, gate, true))) return rc;
-            return launch_scan_select(c, og, ExpandTargets{n}, AncOut{c->anc}, NoSink{}, n, SLOT_RES_O, gate, 1);
-        }
     }
     return SMC_E_ARG;
 }
@@ -680,16 +589,9 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->Q = reinterpret_cast<unsigned long long *>(c->ws + L.Q);
     c->tsum = reinterpret_cast<unsigned long long *>(c->ws + L.tsum);
     c->bsum = reinterpret_cast<unsigned long long *>(c->ws + L.bsum);
-    c->cnt = reinterpret_cast<uint32_t *>(c->ws + L.cnt);
-    c->fill = reinterpret_cast<uint32_t *>(c->ws + L.fill);
-    c->boff = reinterpret_cast<unsigned long long *>(c->ws + L.boff);
-    c->sorted = reinterpret_cast<uint32_t *>(c->ws + L.sorted);
     c->dhist = reinterpret_cast<uint32_t *>(c->ws + L.dhist);
     c->dpre = reinterpret_cast<uint32_t *>(c->ws + L.dpre);
     c->dtot = reinterpret_cast<uint32_t *>(c->ws + L.dtot);
-    c->RQ = reinterpret_cast<unsigned long long *>(c->ws + L.RQ);
-    c->extra = reinterpret_cast<uint32_t *>(c->ws + L.extra);
-    c->O = reinterpret_cast<unsigned long long *>(c->ws + L.O);
     c->obs = reinterpret_cast<double *>(c->ws + L.obs);
     c->obs_f = reinterpret_cast<float *>(c->ws + L.obs_f);
     c->alpha = reinterpret_cast<double *>(c->ws + L.alpha);
@@ -700,7 +602,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     cudaGetDevice(&c->device);
     // zero the state block, records, scan status words and bucket counters
     int rc = cuda_check(cudaMemsetAsync(c->ws, 0, L.part, c->stream));
-    if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + L.tsum, 0, L.boff - L.tsum, c->stream));
+    if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + L.tsum, 0, L.inc - L.tsum, c->stream));
     if (!rc) {
         reset_state_kernel<<<1, 1, 0, c->stream>>>(c->st);
         rc = cuda_check(cudaGetLastError());

@@ -36,9 +36,8 @@ constexpr uint32_t DRAW_MH_UNIFORM = 16;
 
 // scan slots
 constexpr int SLOT_CDF = 0;      // fixed-point weight CDF
-constexpr int SLOT_BUCKET = 1;   // bucket offsets of the uniform sort
-constexpr int SLOT_RES_R = 2;    // residual-weight CDF
-constexpr int SLOT_RES_O = 3;    // residual final offspring CDF
+constexpr int SLOT_RES_D = 2;    // residual: tile sums of the deterministic copies
+constexpr int SLOT_RES_R = 3;    // residual: tile sums of the residual weights
 
 struct DevState {
     int32_t t;        // last completed iteration, -1 before initialize
@@ -48,7 +47,7 @@ struct DevState {
     int32_t error;    // device error word (SMC_E_*)
     int32_t cur_lw;   // which log-weight buffer is current
     uint32_t ticket;  // last-block ticket of the weighting kernels
-    uint32_t count_r; // residual: number of residual draws R
+    uint32_t pad1;
     double max_lw;    // M_t = max_i lw_t,i (the fixed-point shift)
     double log_norm;  // L_t
     double log_evidence;
@@ -57,8 +56,6 @@ struct DevState {
     double path_u;    // GMM U_t
     double path_log_z;
     double base_shift;  // log W_i = lw_i - base_shift (GMM; 0 after a gather resets lw to -log N)
-    unsigned long long qn;     // fixed-point total of the last weight CDF
-    unsigned long long sum_d;  // residual: sum of the deterministic copies
     uint32_t scan_ticket[kScanSlots];   // last-block tickets of the tile-sum passes
     unsigned long long scan_total[kScanSlots];  // exact totals of the tile-sum passes
     uint32_t accept[4];                 // GMM accepted moves per block and Langevin (last mcmc)

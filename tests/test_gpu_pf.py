@@ -118,7 +118,7 @@ def test_degenerate_weights_select_one_particle():
 
 
 @pytest.mark.parametrize("precision", [32, 64])
-@pytest.mark.parametrize("scheme", ["systematic", "stratified", "multinomial"])
+@pytest.mark.parametrize("scheme", SCHEMES)
 def test_heavy_particles_in_some_tiles(scheme, precision):
     """Tiles where one particle owns hundreds of offspring beside tiles of
     ordinary weights, and a heavy particle in the ragged last tile: the
@@ -269,6 +269,8 @@ def test_full_size_sampled(scheme):
         assert np.all(np.diff(Q.astype(np.float64)) >= 0)
         a = s.ancestors().astype(np.int64)
         assert np.all(np.diff(a) >= 0) and a.min() >= 0 and a.max() < n
+        if scheme in ("multinomial", "residual") and t == 1:
+            check_resample(s, lw, t, scheme, seed, 32)  # every output against the oracle
         if scheme == "multinomial":
             # output k: the first i with Q_i 2^25 > Q_N (2 j_(k) + 1), j_(k) the sorted draws
             import bisect
@@ -297,39 +299,38 @@ def test_full_size_sampled(scheme):
             assert not np.any(zero[a])
 
 
+@pytest.mark.parametrize("scheme", ["multinomial", "residual"])
 @pytest.mark.parametrize("n", [3 * (1 << 20) + 17, 5 * 2048 + 1])
-def test_multinomial_one_pass_sizes(n):
-    """Multinomial selection by the draw histogram where every block owns
-    several weight tiles (N above one wave of tiles) and where most blocks
-    own none: three forced resamplings in a row (the two histograms
-    alternate) give the oracle's ancestors on the GPU's CDF: a full
-    comparison at the small size, sampled outputs at the large one."""
+def test_histogram_one_pass_sizes(scheme, n):
+    """Multinomial and residual selection by the draw histogram where every
+    block owns several weight tiles (N above one wave of tiles) and where
+    most blocks own none: three forced resamplings in a row give the
+    oracle's ancestors on the GPU's CDF, every output compared."""
     need_gpu()
-    import bisect
     seed = 4
-    s, y, op = make_pf(n, 4, 32, scheme="multinomial", threshold=0.0, seed=seed)
+    s, y, op = make_pf(n, 4, 32, scheme=scheme, threshold=0.0, seed=seed)
     s.initialize()
     g = np.random.default_rng(5)
     for t in range(3):
         if t:
             s.move()  # the gather of the previous ancestors; iteration t
-        lw = g.normal(0.0, 1.5, n)
-        s.write_log_weight(lw)
+        s.write_log_weight(g.normal(0.0, 1.5, n))
         lw_gpu = s.log_weight()
         s.resample(force=True)
-        if n < 1 << 16:
-            check_resample(s, lw_gpu, t, "multinomial", seed, 32)
-            continue
-        Q = s.cdf()
-        a = s.ancestors().astype(np.int64)
-        assert np.all(np.diff(a) >= 0) and a.min() >= 0 and a.max() < n
-        QN = int(Q[-1])
-        js = np.sort(ophilox.resample_u24(seed, t, n).astype(np.int64))
-        Qlist = [int(v) for v in Q.astype(object)]
-        ks = np.concatenate([g.choice(n, size=400, replace=False), [0, n - 1]])
-        for k in ks:
-            thr = (QN * (2 * int(js[k]) + 1)) >> 25
-            assert a[k] == bisect.bisect_right(Qlist, thr), (t, k)
+        check_resample(s, lw_gpu, t, scheme, seed, 32)
+    s.close()
+
+
+def test_residual_without_draws():
+    """Equal weights at N = 2^k: every d_i = N q_i / Q_N = 1 exactly, so
+    R = 0, no residual draws and the identity ancestors."""
+    need_gpu()
+    n = 1 << 16
+    s, y, op = make_pf(n, 2, 32, scheme="residual", threshold=0.0, seed=2)
+    s.initialize()
+    s.write_log_weight(np.zeros(n))
+    s.resample(force=True)
+    assert np.array_equal(s.ancestors(), np.arange(n, dtype=np.int32))
     s.close()
 
 
