@@ -156,9 +156,10 @@ size_t smc_workspace_bytes(const smc_config *cfg);
 /* Create a context.  d_workspace: caller-owned device memory of at least
  * smc_workspace_bytes(cfg) bytes, 256-byte aligned; cuda_stream: a
  * cudaStream_t (NULL = legacy default stream).  The context allocates no
- * device memory; an FP32 particle filter takes an 8-byte pinned host buffer
- * (smc_iterate_host's staging).  The context is ready for smc_set_data;
- * *out is NULL on failure. */
+ * device memory; it takes a small pinned host buffer mapped into the device's
+ * address space (cudaHostAlloc, cudaHostAllocMapped: smc_iterate_host's
+ * staging).  The context is ready for smc_set_data; *out is NULL on
+ * failure. */
 int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t bytes,
                void *cuda_stream);
 int smc_destroy(smc_ctx *ctx);
@@ -195,9 +196,13 @@ int smc_iterate(smc_ctx *ctx, int32_t n);
 
 /* One iteration with host buffers: copies obs_t (CV: 2 float64; may be NULL
  * to use the observation already stored for t) to the device, runs one
- * iteration and copies its record to *h_record.  Synchronises.  An FP32
- * particle filter sends the float copy of obs_t from a 2-float pinned host
- * buffer that smc_create allocates (cudaMallocHost) and smc_destroy frees. */
+ * iteration and copies its record to *h_record.  Synchronises; returns the
+ * device error word of the step.  SMC_E_ARG past the last observation (or
+ * the GMM schedule).  On a non-default stream (and without SMC_FLAG_RECORD)
+ * the step is one graph launch: obs_t is placed in the context's mapped
+ * pinned staging, which the graph's first kernel reads (and stores, with
+ * its float copy, as row t), and its last kernel writes the record and the
+ * error word there.  Otherwise the copies are stream copies. */
 int smc_iterate_host(smc_ctx *ctx, const double *h_obs_t, smc_record *h_record);
 
 /* WeightSet::add_log_weight (Sec. 4.1.6): multiply the current weights by

@@ -37,6 +37,12 @@ struct PfArgs {
     int32_t gaussian;
     uint2 key;
     uint32_t stream;
+    // smc_iterate_host's graph (zero / null otherwise): the kernel is a
+    // programmatic dependent of the kernel that stores the step's observation
+    // (it waits for that grid just before reading y_t), and the record and
+    // error word go to the staging in mapped host memory
+    int32_t obs_after_wait;
+    HostIO *hio_out;
 };
 
 // log g(Y_t | X_t): full Student-t (or Gaussian) density of both position
@@ -105,7 +111,12 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
         }
     }
     // observation y_t (one broadcast load) and -log N, already in R
-    const R yx = __ldcg(a.obs_r + 2 * t), yy = __ldcg(a.obs_r + 2 * t + 1), base_eq = a.neg_log_n;
+    R yx = R(0), yy = R(0);
+    if (!a.obs_after_wait) {
+        yx = __ldcg(a.obs_r + 2 * t);
+        yy = __ldcg(a.obs_r + 2 * t + 1);
+    }
+    const R base_eq = a.neg_log_n;
     R s0[E], s1[E], s2[E], s3[E], lwv[E], zero[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) {
@@ -124,6 +135,14 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
             s2[j] = v2[j] + a.sd_vel * z[2];
             s3[j] = v3[j] + a.sd_vel * z[3];
         }
+    }
+    if (a.obs_after_wait) {  // the move above overlapped the grid that stores y_t
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        yx = __ldcg(a.obs_r + 2 * t);
+        yy = __ldcg(a.obs_r + 2 * t + 1);
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
         const R b = (t == 0 || gather) ? base_eq : Lprev.sub_from(lwin[j]);
         lwv[j] = (i0 + j < n) ? b + cv_loglik(a, yx, yy, s0[j], s1[j]) : Math<R>::neg_inf();
     }
@@ -163,6 +182,19 @@ __device__ __forceinline__ void pf_finalize(const PfArgs<R> &a, DevState *st, co
         st->cur_lw = cur_lw ^ 1;
         st->ready = 0;
     }
+    if (a.hio_out) {  // smc_iterate_host: the record and the error word to the mapped staging
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            static_assert(sizeof(smc_record) % 4 == 0, "record words");
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(&a.rec[t % a.rec_cap]);
+            volatile uint32_t *dst = reinterpret_cast<volatile uint32_t *>(&a.hio_out->rec);
+            for (int i = threadIdx.x; i < (int)(sizeof(smc_record) / 4); i += 32) dst[i] = __ldcg(src + i);
+            if (threadIdx.x == 0) {
+                const int32_t e = *reinterpret_cast<volatile int32_t *>(&st->error);
+                if (e) a.hio_out->status = e;
+            }
+        }
+    }
 }
 
 template <typename R>
@@ -173,7 +205,10 @@ __global__ void __launch_bounds__(kBlock, 4) pf_iterate_kernel(PfArgs<R> a) {
     int32_t src[kPfItems];
     load_idx4(a.anc, (blockIdx.x * (uint32_t)kBlock + threadIdx.x) * (uint32_t)kPfItems, (uint32_t)a.n, src);
     const DevState *sv = snapshot(st, true);
-    if (sv->error) return;
+    if (sv->error) {  // an earlier step failed: nothing runs, the error goes back to smc_iterate_host
+        if (a.hio_out && blockIdx.x == 0 && threadIdx.x == 0) a.hio_out->status = sv->error;
+        return;
+    }
     const int32_t t = sv->t + 1;
     const int cur = sv->cur, cur_lw = sv->cur_lw;
     const bool gather = (t > 0) && (sv->ready != 0);

@@ -300,7 +300,13 @@ struct GridTargets {
 
 struct AncOut {
     int32_t *anc;
+    int32_t *host_err = nullptr;  // smc_iterate_host's graph: the mapped staging's error word
     __device__ __forceinline__ void operator()(int64_t k, int32_t a) const { anc[k] = a; }
+    // after a failure in this kernel: the device error word to the staging
+    __device__ __forceinline__ void report(const DevState *st) const {
+        if (host_err && threadIdx.x == 0)
+            *reinterpret_cast<volatile int32_t *>(host_err) = *reinterpret_cast<const volatile int32_t *>(&st->error);
+    }
 };
 
 // ---------------------------------------------------------------- kernels --
@@ -712,7 +718,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_resample_kernel(Gen gen, GridT
         tsum[t_hi - 1] = last;
         bsum[b] = bs + last;
     }
-    if (!grid_barrier(st, gridDim.x)) return;
+    if (!grid_barrier(st, gridDim.x)) return out.report(st);
     if (b == 0 && threadIdx.x == 0) st->ready = 1;
     unsigned long long pre, QN;
     tile_prefix_total(bsum, b, G, &pre, &QN);
@@ -948,7 +954,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_multinomial_kernel(QGen<R> gen
         if (t_hi > t_lo) tsum[t_hi - 1] = last;
         bsum[b] = bs + last;
     }
-    if (!grid_barrier(st, G)) return;
+    if (!grid_barrier(st, G)) return out.report(st);
     if (b == 0 && threadIdx.x == 0) st->ready = 1;
     hist_draws(tgt.key, tgt.stream, (uint32_t)sv->t, n, h.hist, b, G);
     // the block's weight prefix and targets (the block sums are complete)
@@ -964,14 +970,17 @@ __global__ void __launch_bounds__(kBlock, 4) grid_multinomial_kernel(QGen<R> gen
             before_last = block_sum_u64(before_last);
         }
     }
-    if (!grid_barrier(st, 2 * G)) return;
+    if (!grid_barrier(st, 2 * G)) return out.report(st);
     const int h_lo = (int)((int64_t)kHistTiles * b / G), h_hi = (int)((int64_t)kHistTiles * (b + 1) / G);
     for (int ht = h_lo; ht < h_hi; ++ht) hist_scan_tile(reinterpret_cast<const uint4 *>(h.hist), h.hpre, h.htot, ht);
-    if (!grid_barrier(st, 3 * G)) return;
+    if (!grid_barrier(st, 3 * G)) return out.report(st);
     if (t_hi > t_lo) {
         uint32_t *tpre = reinterpret_cast<uint32_t *>(tb.tau) + kHistTpreOffset;
         const uint32_t total = hist_tile_prefix(h.htot, tpre);
-        if (total != (uint32_t)n && threadIdx.x == 0) raise_error(st, SMC_E_RANGE);  // a wrapped count
+        if (total != (uint32_t)n && threadIdx.x == 0) {  // a wrapped count
+            raise_error(st, SMC_E_RANGE);
+            out.report(st);
+        }
         const HistMap km{reinterpret_cast<const uint4 *>(h.hist), h.hpre, tpre, n};
         select_tile_grid(tg, out, sink, n, t_hi - 1, pre + before_last, last, QN, st, tb, km);
         for (int tile = t_lo; tile < t_hi - 1; ++tile) {
@@ -1080,7 +1089,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
         bq += s;
     }
     if (threadIdx.x == 0) rs.bq[b] = bq;
-    if (!grid_barrier(st, G)) return;
+    if (!grid_barrier(st, G)) return out.report(st);
     if (b == 0 && threadIdx.x == 0) st->ready = 1;
     // phase 2: d sums; the CDF of q where it is stored
     unsigned long long pre_q, QN;
@@ -1100,7 +1109,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
         pre_q += ts;
     }
     if (threadIdx.x == 0) rs.bd[b] = bd;
-    if (!grid_barrier(st, 2 * G)) return;
+    if (!grid_barrier(st, 2 * G)) return out.report(st);
     // phase 3: R, s, the draws; r sums (a kept tile also gets its d and r scans)
     unsigned long long pre_d, Dtot;
     tile_prefix_total(rs.bd, b, G, &pre_d, &Dtot);
@@ -1126,7 +1135,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
         br += sr;
     }
     if (threadIdx.x == 0) rs.br[b] = br;
-    if (!grid_barrier(st, 3 * G)) return;
+    if (!grid_barrier(st, 3 * G)) return out.report(st);
     // phase 4: histogram tiles; the r prefix and the targets on RQ_N
     const int h_lo = (int)((int64_t)kHistTiles * b / G), h_hi = (int)((int64_t)kHistTiles * (b + 1) / G);
     for (int ht = h_lo; ht < h_hi; ++ht) hist_scan_tile(reinterpret_cast<const uint4 *>(h.hist), h.hpre, h.htot, ht);
@@ -1134,12 +1143,15 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
     tile_prefix_total(rs.br, b, G, &pre_r, &RQN);
     // RQ_N = 0 exactly when R = 0: any positive total then gives v = 0 and H = 0
     const GridTargets<false> tg = block_targets(tgt, sv, RQN ? RQN : 1ull);
-    if (!grid_barrier(st, 4 * G)) return;
+    if (!grid_barrier(st, 4 * G)) return out.report(st);
     // phase 5: selection
     if (t_hi > t_lo) {  // the same branch in the whole block
         uint32_t *tpre = reinterpret_cast<uint32_t *>(tb.tau) + kHistTpreOffset;
         const uint32_t total = hist_tile_prefix(h.htot, tpre);
-        if (total != (uint32_t)Rn && threadIdx.x == 0) raise_error(st, SMC_E_RANGE);  // a wrapped count
+        if (total != (uint32_t)Rn && threadIdx.x == 0) {  // a wrapped count
+            raise_error(st, SMC_E_RANGE);
+            out.report(st);
+        }
         const HistMap hm{reinterpret_cast<const uint4 *>(h.hist), h.hpre, tpre, (int64_t)Rn};
         unsigned long long d0 = pre_d, r0 = pre_r;
         for (int tile = t_lo; tile < t_hi; ++tile) {

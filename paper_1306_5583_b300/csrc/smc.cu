@@ -168,7 +168,10 @@ struct smc_ctx {
     int device;
     DevState host_st;     // last state read back
     cudaGraphExec_t graph;  // one captured iteration (move, resampling, mcmc)
-    float *h_obs_f;         // pinned: the float copy of one observation for smc_iterate_host (2 floats)
+    HostIO *hio;            // smc_iterate_host's staging: pinned, mapped (host address)
+    HostIO *hio_d;          // the same buffer's device address
+    cudaGraphExec_t graph_host;  // one iteration reading and writing the staging (smc_iterate_host)
+    int capture_host_io;    // while capturing graph_host: the kernels get the staging's addresses
     cudaEvent_t ev_move[2]; // profiling: recorded around the move kernel in the iteration graph
     int dependent_launch;   // while capturing: launch the one-pass resampler as a programmatic dependent
     int no_dependent;       // the driver refused the programmatic dependent launch once: capture without
@@ -202,6 +205,36 @@ __global__ void reset_state_kernel(DevState *st) {
     st->grid_count = 0;
     st->grid_depart = 0;
     for (int i = 0; i < 4; ++i) st->accept[i] = 0;
+}
+
+// smc_iterate_host on a particle filter, first node of its graph: the
+// observation of iteration t + 1 from the mapped staging into the workspace
+// (and its float copy, rounded as on the host).  The move kernel, its
+// programmatic dependent, starts at once and waits for this grid only
+// before it reads y_t.
+__global__ void host_obs_kernel(const HostIO *io, const DevState *st, double *obs, float *obs_f) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (threadIdx.x != 0 || st->error) return;
+    const volatile HostIO *v = io;
+    if (!v->has_obs) return;
+    const int64_t t = (int64_t)st->t + 1;
+    const double x = v->obs[0], y = v->obs[1];
+    obs[2 * t] = x;
+    obs[2 * t + 1] = y;
+    obs_f[2 * t] = __double2float_rn(x);
+    obs_f[2 * t + 1] = __double2float_rn(y);
+}
+
+// smc_iterate_host on a GMM sampler, last node of its graph: the record of
+// iteration t and the device error word into the mapped staging (one warp;
+// the particle filters' move kernel writes them itself)
+__global__ void host_rec_kernel(HostIO *io, const DevState *st, const smc_record *rec, int32_t max_records) {
+    const int32_t t = st->t;
+    static_assert(sizeof(smc_record) % 4 == 0, "record words");
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(rec + (t >= 0 ? t % max_records : 0));
+    volatile uint32_t *dst = reinterpret_cast<volatile uint32_t *>(&io->rec);
+    for (int i = threadIdx.x; i < (int)(sizeof(smc_record) / 4); i += 32) dst[i] = src[i];
+    if (threadIdx.x == 0) io->status = st->error;
 }
 
 // the resampling threshold for the FP32 finalize: a DF value and a mode
@@ -256,17 +289,41 @@ PfArgs<R> pf_args(smc_ctx *c) {
     set_obs_params(a, g.cv.obs_scale, g.cv.obs_df, g.model == SMC_MODEL_CV_GAUSS);
     a.key = key_of(c);
     a.stream = g.stream_id;
+    a.obs_after_wait = 0;
+    a.hio_out = c->capture_host_io ? c->hio_d : nullptr;
     return a;
 }
 
 template <typename R>
 int launch_pf(smc_ctx *c) {
     PfArgs<R> a = pf_args<R>(c);
+    if (c->capture_host_io && c->dependent_launch) {
+        // smc_iterate_host's graph: a programmatic dependent of host_obs_kernel
+        a.obs_after_wait = 1;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)c->L.nbw);
+        lc.blockDim = dim3(kBlock);
+        lc.stream = c->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        return cuda_check(cudaLaunchKernelEx(&lc, pf_iterate_kernel<R>, a));
+    }
     pf_iterate_kernel<R><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(a);
     return cuda_check(cudaGetLastError());
 }
 
 unsigned long long *tsum_of(smc_ctx *c, int slot) { return c->tsum + (size_t)slot * c->L.ntiles; }
+
+// The ancestor output of the resampling kernels (and, while graph_host is
+// captured, the staging's error word for their failures).
+AncOut anc_out(smc_ctx *c) {
+    AncOut o{c->anc};
+    o.host_err = c->capture_host_io ? &c->hio_d->status : nullptr;
+    return o;
+}
 
 // Resident blocks of a cooperative kernel on the current device (cached per
 // kernel by the caller's arrays, indexed by device).
@@ -323,7 +380,7 @@ int launch_grid_resample(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
     tg.key = key_of(c);
     tg.stream = c->cfg.stream_id;
     tg.mrec = ~0ull / (unsigned long long)n;
-    return launch_coop(c, grid, kern, qg, tg, AncOut{c->anc}, sk, n, tsum_of(c, SLOT_CDF), c->bsum, c->st, gate);
+    return launch_coop(c, grid, kern, qg, tg, anc_out(c), sk, n, tsum_of(c, SLOT_CDF), c->bsum, c->st, gate);
 }
 
 // One-pass multinomial resampling (grid_multinomial_kernel): one full wave
@@ -348,7 +405,7 @@ int launch_grid_multinomial(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
     h.hist = c->dhist;
     h.hpre = c->dpre;
     h.htot = c->dtot;
-    return launch_coop(c, grid, kern, qg, tg, AncOut{c->anc}, sk, n, tsum_of(c, SLOT_CDF), c->bsum, h, c->st, gate);
+    return launch_coop(c, grid, kern, qg, tg, anc_out(c), sk, n, tsum_of(c, SLOT_CDF), c->bsum, h, c->st, gate);
 }
 
 // One-pass residual resampling (grid_residual_kernel): one full wave; the
@@ -378,7 +435,7 @@ int launch_grid_residual(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
     rs.bq = c->bsum;
     rs.bd = c->bsum + kMaxCoopGrid;
     rs.br = c->bsum + 2 * kMaxCoopGrid;
-    return launch_coop(c, grid, kern, qg, tg, AncOut{c->anc}, sk, n, rs, h, c->st, gate);
+    return launch_coop(c, grid, kern, qg, tg, anc_out(c), sk, n, rs, h, c->st, gate);
 }
 
 template <typename R>
@@ -513,39 +570,60 @@ int launch_iteration(smc_ctx *c) {
     return rc;
 }
 
-int build_graph_once(smc_ctx *c) {
+// one iteration; host_io: smc_iterate_host's, which reads the observation
+// from the mapped staging (a one-warp first kernel, overlapped with the move)
+// and writes the record and error word back there (the particle filters'
+// kernels themselves; a GMM sampler through a last one-warp kernel)
+int launch_iteration_io(smc_ctx *c, bool host_io) {
+    if (!host_io) return launch_iteration(c);
+    if (c->cfg.model == SMC_MODEL_GMM) {
+        if (int rc = launch_iteration(c)) return rc;
+        host_rec_kernel<<<1, 32, 0, c->stream>>>(c->hio_d, c->st, c->rec, c->cfg.max_records);
+        return cuda_check(cudaGetLastError());
+    }
+    host_obs_kernel<<<1, 32, 0, c->stream>>>(c->hio_d, c->st, c->obs, c->obs_f);
+    if (int rc = cuda_check(cudaGetLastError())) return rc;
+    c->capture_host_io = 1;
+    const int rc = launch_iteration(c);
+    c->capture_host_io = 0;
+    return rc;
+}
+
+int build_graph_once(smc_ctx *c, cudaGraphExec_t *dst, bool host_io) {
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SMC_E_CUDA;
-    const int rc = launch_iteration(c);
+    const int rc = launch_iteration_io(c, host_io);
     const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (rc || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
         return rc ? rc : SMC_E_CUDA;
     }
-    const cudaError_t e2 = cudaGraphInstantiate(&c->graph, g, 0);
+    const cudaError_t e2 = cudaGraphInstantiate(dst, g, 0);
     cudaGraphDestroy(g);
     if (e2 != cudaSuccess) {
         cudaGetLastError();
-        c->graph = nullptr;
+        *dst = nullptr;
         return SMC_E_CUDA;
     }
     return SMC_OK;
 }
 
-// One iteration captured as a graph.  The one-pass resampler is captured as
-// a programmatic dependent of the move kernel where the driver accepts that
-// for a cooperative launch; otherwise (one refusal) as an ordinary node.
-int build_graph(smc_ctx *c) {
-    if (c->graph) return SMC_OK;
+// One iteration captured as a graph (host_io: the graph of smc_iterate_host).
+// The one-pass resampler is captured as a programmatic dependent of the move
+// kernel where the driver accepts that for a cooperative launch; otherwise
+// (one refusal) as an ordinary node.
+int build_graph(smc_ctx *c, bool host_io = false) {
+    cudaGraphExec_t *dst = host_io ? &c->graph_host : &c->graph;
+    if (*dst) return SMC_OK;
     if (!c->no_dependent && !c->ev_move[1]) {
         c->dependent_launch = 1;
-        const int rc = build_graph_once(c);
+        const int rc = build_graph_once(c, dst, host_io);
         c->dependent_launch = 0;
         if (rc == SMC_OK) return SMC_OK;
         c->no_dependent = 1;
     }
-    return build_graph_once(c);
+    return build_graph_once(c, dst, host_io);
 }
 
 int mcmc_any(smc_ctx *c) {
@@ -599,6 +677,10 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->t_host = -1;
     c->initialized = 0;
     c->graph = nullptr;
+    c->graph_host = nullptr;
+    c->capture_host_io = 0;
+    c->hio = nullptr;
+    c->hio_d = nullptr;
     cudaGetDevice(&c->device);
     // zero the state block, records, scan status words and bucket counters
     int rc = cuda_check(cudaMemsetAsync(c->ws, 0, L.part, c->stream));
@@ -608,14 +690,15 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
         rc = cuda_check(cudaGetLastError());
     }
     if (!rc && cfg->model == SMC_MODEL_GMM) rc = gmm_setup(c);
-    // staging buffer of smc_iterate_host's float observation (FP32 particle filters)
-    if (!rc && cfg->model != SMC_MODEL_GMM && cfg->precision == 32)
-        rc = cuda_check(cudaMallocHost(reinterpret_cast<void **>(&c->h_obs_f), 2 * sizeof(float)));
+    // smc_iterate_host's staging: pinned and mapped into the device's address space
+    if (!rc) rc = cuda_check(cudaHostAlloc(reinterpret_cast<void **>(&c->hio), sizeof(HostIO), cudaHostAllocMapped));
+    if (!rc) rc = cuda_check(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->hio_d), c->hio, 0));
     if (rc) {
-        if (c->h_obs_f) cudaFreeHost(c->h_obs_f);
+        if (c->hio) cudaFreeHost(c->hio);
         delete c;
         return rc;
     }
+    std::memset(c->hio, 0, sizeof(HostIO));
     *out = c;
     return SMC_OK;
 }
@@ -623,7 +706,8 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
 int smc_destroy(smc_ctx *c) {
     if (!c) return SMC_E_ARG;
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    if (c->h_obs_f) cudaFreeHost(c->h_obs_f);
+    if (c->graph_host) cudaGraphExecDestroy(c->graph_host);
+    if (c->hio) cudaFreeHost(c->hio);
     gmm_release(c);
     delete c;
     return SMC_OK;
@@ -709,18 +793,40 @@ int smc_iterate_host(smc_ctx *c, const double *h_obs_t, smc_record *h_record) {
     if (!c || !h_record) return SMC_E_ARG;
     if (!c->initialized) return SMC_E_STATE;
     const int32_t t = c->t_host + 1;
+    const bool with_obs = h_obs_t && c->cfg.model != SMC_MODEL_GMM;
+    if (with_obs && t >= c->cfg.max_data) return SMC_E_ARG;
+    const int64_t limit = (c->cfg.model == SMC_MODEL_GMM)
+                              ? c->cfg.gmm.n_iter
+                              : std::max<int64_t>(c->n_obs, with_obs ? t + 1 : 0) - 1;
+    if (t > limit) return SMC_E_ARG;
     int rc;
-    if (h_obs_t && c->cfg.model != SMC_MODEL_GMM) {
-        if (t >= c->cfg.max_data) return SMC_E_ARG;
+    if (c->stream != nullptr && !recording(c)) {
+        // one graph launch: the observation goes in and the record comes out
+        // through the mapped staging, read and written by the graph's kernels
+        if ((rc = build_graph(c, true))) return rc;
+        c->hio->status = SMC_OK;
+        c->hio->has_obs = with_obs ? 1 : 0;
+        if (with_obs) {
+            c->hio->obs[0] = h_obs_t[0];
+            c->hio->obs[1] = h_obs_t[1];
+        }
+        if (cudaGraphLaunch(c->graph_host, c->stream) != cudaSuccess) return SMC_E_CUDA;
+        if ((rc = cuda_check(cudaStreamSynchronize(c->stream)))) return rc;
+        if (with_obs && c->n_obs < t + 1) c->n_obs = t + 1;
+        c->t_host = t;
+        std::memcpy(h_record, &c->hio->rec, sizeof(smc_record));
+        return c->hio->status;
+    }
+    if (with_obs) {
         rc = cuda_check(cudaMemcpyAsync(c->obs + 2 * (size_t)t, h_obs_t, 16, cudaMemcpyHostToDevice, c->stream));
         if (rc) return rc;
         if (c->cfg.precision == 32) {
-            // the FP32 kernels read the float copy: rounded here (as a device
-            // conversion would) and sent from the context's pinned buffer,
+            // the FP32 kernels read the float copy: rounded here (as the device
+            // conversion does) and sent from the context's pinned staging,
             // which this synchronising call leaves free for the next one
-            c->h_obs_f[0] = (float)h_obs_t[0];
-            c->h_obs_f[1] = (float)h_obs_t[1];
-            rc = cuda_check(cudaMemcpyAsync(c->obs_f + 2 * (size_t)t, c->h_obs_f, 2 * sizeof(float),
+            c->hio->obs_f[0] = (float)h_obs_t[0];
+            c->hio->obs_f[1] = (float)h_obs_t[1];
+            rc = cuda_check(cudaMemcpyAsync(c->obs_f + 2 * (size_t)t, c->hio->obs_f, 2 * sizeof(float),
                                             cudaMemcpyHostToDevice, c->stream));
             if (rc) return rc;
         }
@@ -992,6 +1098,10 @@ int smc_set_move_events(smc_ctx *c, void *ev_before, void *ev_after) {
     if (c->graph) {  // captured again, with or without the events, at the next smc_iterate
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
+    }
+    if (c->graph_host) {
+        cudaGraphExecDestroy(c->graph_host);
+        c->graph_host = nullptr;
     }
     return SMC_OK;
 }

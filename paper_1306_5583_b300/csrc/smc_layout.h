@@ -68,6 +68,17 @@ struct DevState {
     uint32_t pad3;
 };
 
+// Staging of smc_iterate_host in pinned host memory mapped into the device's
+// address space: the device reads the step's observation and writes the
+// step's record and error word through it (no separate copies).
+struct HostIO {
+    double obs[2];     // the observation of the next iteration (CV models)
+    float obs_f[2];    // its float copy (the copy path without the graph)
+    int32_t has_obs;   // 1: obs holds the next observation
+    int32_t status;    // the device error word after the step
+    smc_record rec;    // the step's record
+};
+
 struct Partial {  // one per block of a weighting kernel
     double m, s1, s2, sx, sy, su;
     double pad[2];

@@ -138,11 +138,14 @@ def test_restore_rejects_another_configuration():
         s.restore(blob[:100])
 
 
+@pytest.mark.parametrize("on_stream", [False, True])
 @pytest.mark.parametrize("precision", [32, 64])
-def test_iterate_host_matches_stored_observations(precision):
+def test_iterate_host_matches_stored_observations(precision, on_stream):
     """smc_iterate_host with each observation sent from host memory gives
     the same records and final particle system, bit for bit, as iterating
-    over the same observations stored up front."""
+    over the same observations stored up front: on the legacy stream (stream
+    copies) and on a stream of its own (one graph launch, the observation
+    and the record through the mapped staging)."""
     need_gpu()
     n, T = 5000, 10
     p = cv_params()
@@ -151,7 +154,7 @@ def test_iterate_host_matches_stored_observations(precision):
     def sampler():
         cfg = smc.make_config(model="cv", n=n, precision=precision, scheme="systematic", threshold=0.6, seed=2,
                               max_data=T, cv=p)
-        return smc.Sampler(cfg)
+        return smc.Sampler(cfg, stream=torch.cuda.Stream() if on_stream else None)
 
     a = sampler()
     a.set_data(y)
@@ -167,5 +170,71 @@ def test_iterate_host_matches_stored_observations(precision):
         for k in ("t", "L", "logZ", "ess", "mean_x", "mean_y", "resampled"):
             assert ra[k] == rb[k], (ra["t"], k, ra[k], rb[k])
     assert np.array_equal(a.state(), b.state())
+    a.close()
+    b.close()
+
+
+def test_iterate_host_graph_stored_data_limits_and_errors():
+    """The graph path of smc_iterate_host: with the observations stored up
+    front a NULL observation replays them (records equal to smc_iterate);
+    a step past the last observation is refused; a NaN observation comes
+    back as the step's device error word."""
+    need_gpu()
+    n, T = 4096, 6
+    p = cv_params()
+    _, y = workloads.cv_data(T, seed=0, **p)
+
+    def sampler():
+        cfg = smc.make_config(model="cv", n=n, precision=32, scheme="stratified", threshold=0.7, seed=3,
+                              max_data=T, cv=p)
+        s = smc.Sampler(cfg, stream=torch.cuda.Stream())
+        s.set_data(y)
+        s.initialize()
+        return s
+
+    a, b = sampler(), sampler()
+    a.iterate(T - 1)
+    ha = a.history(T)
+    hb = [b.iterate_host(None).as_dict() for _ in range(1, T)]
+    for ra, rb in zip(ha[1:], hb):
+        assert ra == rb
+    with pytest.raises(smc.SMCError) as e:
+        b.iterate_host(None)
+    assert e.value.code == smc.E_ARG
+    c = sampler()
+    c.iterate_host(y[1])
+    bad = y[2].copy()
+    bad[0] = np.nan
+    with pytest.raises(smc.SMCError) as e:
+        c.iterate_host(bad)
+    assert e.value.code == smc.E_NONFINITE
+    for s in (a, b, c):
+        s.close()
+
+
+def test_iterate_host_graph_gmm():
+    """GMM sampler stepped through smc_iterate_host on a stream (no
+    observation): the same records as smc_iterate."""
+    need_gpu()
+    y = workloads.gmm_data(300, seed=1)
+    T = 12
+
+    def sampler():
+        cfg = smc.make_config(model="gmm", n=2048, precision=32, scheme="systematic", threshold=0.5, seed=4,
+                              max_data=300, max_records=T + 1,
+                              gmm=dict(n_comp=3, n_iter=T, power=4.0, move=smc.GMM_RW))
+        s = smc.Sampler(cfg, stream=torch.cuda.Stream())
+        s.set_data(y)
+        s.initialize()
+        return s
+
+    a, b = sampler(), sampler()
+    a.iterate(T)
+    ha = a.history(T + 1)
+    hb = [b.iterate_host().as_dict() for _ in range(T)]
+    for ra, rb in zip(ha[1:], hb):
+        assert ra == rb
+    with pytest.raises(smc.SMCError):
+        b.iterate_host()
     a.close()
     b.close()
