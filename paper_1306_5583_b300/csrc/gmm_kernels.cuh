@@ -171,12 +171,13 @@ __device__ __forceinline__ void gmm_datum(R yk, const R (&mu)[NC], const R (&c2)
 template <typename R, int NC>
 __device__ __forceinline__ void gmm_datum_grad(R yk, const R (&mu)[NC], const R (&c2)[NC], const R (&h2)[NC],
                                                R &msum, R &prod, R (&sd)[NC], R (&sl)[NC], R (&sr)[NC]) {
-    R a[NC], d[NC];
+    R a[NC], d[NC], dd[NC];
     R m = -INFINITY;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         d[j] = yk - mu[j];
-        a[j] = c2[j] - h2[j] * d[j] * d[j];
+        dd[j] = d[j] * d[j];  // shared by the exponent and the second-moment sum
+        a[j] = c2[j] - h2[j] * dd[j];
         m = fmax(m, a[j]);
     }
     R e[NC], s = 0;
@@ -190,7 +191,7 @@ __device__ __forceinline__ void gmm_datum_grad(R yk, const R (&mu)[NC], const R 
     for (int j = 0; j < NC; ++j) {
         const R rho = e[j] * inv;
         sd[j] += rho * d[j];
-        sl[j] += rho * d[j] * d[j];
+        sl[j] += rho * dd[j];
         sr[j] += rho;
     }
     msum += m;
