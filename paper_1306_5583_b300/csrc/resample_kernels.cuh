@@ -422,7 +422,7 @@ __device__ __forceinline__ void tile_prefix_total(const unsigned long long *tsum
 // broadcast, so per-block constants (a Philox draw, 64-bit divisions) are
 // computed once.
 template <class Tgt>
-__device__ __forceinline__ Tgt block_targets(const Tgt &proto, const DevState *sv, unsigned long long QN) {
+__device__ __forceinline__ const Tgt &block_targets_ref(const Tgt &proto, const DevState *sv, unsigned long long QN) {
     __shared__ Tgt s_tg;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -433,6 +433,10 @@ __device__ __forceinline__ Tgt block_targets(const Tgt &proto, const DevState *s
     }
     __syncthreads();
     return s_tg;
+}
+template <class Tgt>
+__device__ __forceinline__ Tgt block_targets(const Tgt &proto, const DevState *sv, unsigned long long QN) {
+    return block_targets_ref(proto, sv, QN);
 }
 
 // Shared-memory buffers of one scan tile (declared once per kernel).  The
@@ -572,8 +576,9 @@ __device__ __forceinline__ void select_tile(const Tgt &tg, const Out &out, const
 // turns it into the output count K(X) (the identity for systematic and
 // stratified targets; the draw histogram for multinomial value thresholds).
 struct KIdentity {
+    static constexpr bool kActive = false;
     __device__ __forceinline__ int64_t operator()(int64_t k) const { return k; }
-    __device__ __forceinline__ void map_items(int32_t *, int, int64_t *) const {}
+    __device__ __forceinline__ void map_block(int32_t *, int64_t *) const {}
 };
 
 template <bool kStratified, class Out, class KMap = KIdentity>
@@ -604,7 +609,10 @@ __device__ __forceinline__ void select_tile_closed(const GridTargets<kStratified
             Kend[pad32(base + j)] = (int32_t)tg.k_from(zp, pre + qj, dc);
             qprev = qj;
         }
-        kmap.map_items(Kend, base, tid == 0 ? &tb.k[0] : nullptr);
+    }
+    if constexpr (KMap::kActive) {  // the count map over the tile's entries, thread t taking t + r kBlock
+        __syncthreads();
+        kmap.map_block(Kend, &tb.k[0]);
     }
     __syncthreads();
     const int64_t k_lo = tb.k[0], k_hi = Kend[pad32(kScanTile - 1)];
@@ -758,11 +766,21 @@ __device__ __forceinline__ uint32_t bytes_below(uint32_t x, int p) {
     return p >= 4 ? x : (p <= 0 ? 0u : x & ((1u << (8 * p)) - 1u));
 }
 
+// Bucket record written by the histogram scan: x = the bucket's prefix within
+// its histogram tile, bit 31 set when a value of the bucket was drawn more
+// than 3 times; y = the bucket's 16 counts as 2-bit fields (valid without
+// that bit).  One 8-byte load then serves a lookup, and the count below a
+// value is two population counts.
 struct HistArgs {
     uint32_t *hist;  // [kHistWords]: byte counts of the values (cleared by each use)
-    uint32_t *hpre;  // [kHistBuckets] bucket prefix within its histogram tile
+    uint2 *hrec;     // [kHistBuckets] bucket records
     uint32_t *htot;  // [kHistTiles] histogram tile totals
 };
+
+// the four byte counts of x (each at most 3) as 2-bit fields
+__device__ __forceinline__ uint32_t pack2(uint32_t x) {
+    return (x & 0x3u) | ((x >> 6) & 0xCu) | ((x >> 12) & 0x30u) | ((x >> 18) & 0xC0u);
+}
 
 // Offset (32-bit words) of the histogram tile prefix in the tile's threshold
 // buffer, past the offspring ends of select_tile_closed.
@@ -771,53 +789,57 @@ static_assert(kHistTpreOffset >= kScanTile + kScanTile / 32, "clear of the offsp
 static_assert(kHistTpreOffset + kHistTiles <= 2 * (kScanTile + kScanTile / 8), "inside the threshold buffer");
 
 // H(v) for v in [0, 2^24]: the tile prefix (shared memory), the bucket
-// prefix and the bytes below v in its bucket
+// prefix and the draws below v in its bucket (from the record, or from the
+// byte counts of a bucket with a value drawn more than 3 times)
 struct HistMap {
     const uint4 *hist;
-    const uint32_t *hpre;
+    const uint2 *hrec;
     const uint32_t *tpre;
     int64_t m;  // number of draws
-    __device__ __forceinline__ int64_t finish(int64_t v, uint4 w, uint32_t hp) const {
-        if (v >= (int64_t(1) << kHistValueBits)) return m;
-        const int64_t bk = v >> 4;
-        const int p = (int)(v & 15);
-        const uint32_t in = byte_sum(bytes_below(w.x, p)) + byte_sum(bytes_below(w.y, p - 4)) +
-                            byte_sum(bytes_below(w.z, p - 8)) + byte_sum(bytes_below(w.w, p - 12));
-        return (int64_t)tpre[bk / kScanTile] + (int64_t)hp + (int64_t)in;
-    }
     __device__ __forceinline__ int64_t bucket(int64_t v) const {
         return min(v, (int64_t(1) << kHistValueBits) - 1) >> 4;
     }
-    // Loads through L1: neighbouring boundaries of a thread and a warp share
-    // buckets, and no SM loads these lines before the grid barrier whose
-    // acquire orders them after the writes.
-    __device__ __forceinline__ int64_t operator()(int64_t v) const {
-        const int64_t bk = bucket(v);
-        return finish(v, hist[bk], hpre[bk]);
-    }
-    // K[base + j] = H(K[base + j]) for the kScanItems entries of a thread
-    // and, where given, *k0 = H(*k0) (with the first four): four lookups at a
-    // time, their loads issued together
-    __device__ __forceinline__ void map_items(int32_t *K, int base, int64_t *k0) const {
-#pragma unroll
-        for (int h = 0; h < kScanItems; h += 4) {
-            int64_t v[5];
-            uint4 w[5];
-            uint32_t hp[5];
-            const int cnt = (h == 0 && k0) ? 5 : 4;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                if (j < cnt) {
-                    v[j] = (j < 4) ? (int64_t)K[pad32(base + h + j)] : *k0;
-                    const int64_t bk = bucket(v[j]);
-                    w[j] = hist[bk];
-                    hp[j] = hpre[bk];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) K[pad32(base + h + j)] = (int32_t)finish(v[j], w[j], hp[j]);
-            if (cnt == 5) *k0 = finish(v[4], w[4], hp[4]);
+    __device__ __forceinline__ int64_t finish(int64_t v, uint2 r) const {
+        if (v >= (int64_t(1) << kHistValueBits)) return m;
+        const int64_t bk = v >> 4;
+        const int p = (int)(v & 15);
+        uint32_t in;
+        if (r.x >> 31) {
+            const uint4 w = hist[bk];
+            in = byte_sum(bytes_below(w.x, p)) + byte_sum(bytes_below(w.y, p - 4)) +
+                 byte_sum(bytes_below(w.z, p - 8)) + byte_sum(bytes_below(w.w, p - 12));
+        } else {
+            const uint32_t f = r.y & ((1u << (2 * p)) - 1u);  // the fields below p (2p <= 30)
+            in = (uint32_t)__popc(f & 0x55555555u) + 2u * (uint32_t)__popc(f & 0xAAAAAAAAu);
         }
+        return (int64_t)tpre[bk / kScanTile] + (int64_t)(r.x & 0x7FFFFFFFu) + (int64_t)in;
+    }
+    // Loads through L1: neighbouring boundaries of a thread and a warp share
+    // records, and no SM loads these lines before the grid barrier whose
+    // acquire orders them after the writes.
+    __device__ __forceinline__ int64_t operator()(int64_t v) const { return finish(v, hrec[bucket(v)]); }
+    // K[e] = H(K[e]) for the tile's entries e = threadIdx.x + j kBlock (a
+    // warp's loads then cover neighbouring particles, whose records are
+    // neighbours) and, in thread 0, *k0 = H(*k0): every record load issued
+    // first
+    static constexpr bool kActive = true;
+    __device__ __forceinline__ void map_block(int32_t *K, int64_t *k0) const {
+        int32_t v[kScanItems];
+        uint2 r[kScanItems];
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            v[j] = K[pad32((int)threadIdx.x + j * kBlock)];
+            r[j] = hrec[bucket(v[j])];
+        }
+        int64_t v0 = 0;
+        uint2 r0 = make_uint2(0u, 0u);
+        if (threadIdx.x == 0) {
+            v0 = *k0;
+            r0 = hrec[bucket(v0)];
+        }
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) K[pad32((int)threadIdx.x + j * kBlock)] = (int32_t)finish(v[j], r[j]);
+        if (threadIdx.x == 0) *k0 = finish(v0, r0);
     }
 };
 
@@ -844,16 +866,18 @@ __device__ __forceinline__ void hist_draws(uint2 key, uint32_t stream, uint32_t 
 
 // Bucket prefixes of histogram tile ht within the tile (thread t takes the
 // buckets r kBlock + t, coalesced) and the tile's total.
-__device__ __forceinline__ void hist_scan_tile(const uint4 *h, uint32_t *hpre, uint32_t *htot, int ht) {
+__device__ __forceinline__ void hist_scan_tile(const uint4 *h, uint2 *hrec, uint32_t *htot, int ht) {
     __shared__ uint32_t s_w[kScanItems][kBlock / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t b0 = (int64_t)ht * kScanTile;
-    uint32_t c[kScanItems], inc[kScanItems];
+    // c: the bucket's count (at most 16 * 255) with the record's bit 31
+    uint32_t c[kScanItems], inc[kScanItems], f2[kScanItems];
 #pragma unroll
     for (int r = 0; r < kScanItems; ++r) {
         const uint4 w = __ldcg(&h[b0 + r * kBlock + tid]);
-        c[r] = byte_sum(w.x) + byte_sum(w.y) + byte_sum(w.z) + byte_sum(w.w);
-        inc[r] = c[r];
+        inc[r] = byte_sum(w.x) + byte_sum(w.y) + byte_sum(w.z) + byte_sum(w.w);
+        c[r] = inc[r] | (((w.x | w.y | w.z | w.w) & 0xFCFCFCFCu) ? 0x80000000u : 0u);
+        f2[r] = pack2(w.x) | (pack2(w.y) << 8) | (pack2(w.z) << 16) | (pack2(w.w) << 24);
     }
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -878,7 +902,8 @@ __device__ __forceinline__ void hist_scan_tile(const uint4 *h, uint32_t *hpre, u
             tot += x;
             wpre += (w < warp) ? x : 0u;
         }
-        hpre[b0 + r * kBlock + tid] = row + wpre + inc[r] - c[r];
+        const uint32_t prefix = row + wpre + inc[r] - (c[r] & 0x7FFFFFFFu);
+        hrec[b0 + r * kBlock + tid] = make_uint2(prefix | (c[r] & 0x80000000u), f2[r]);
         row += tot;
     }
     if (tid == 0) htot[ht] = row;
@@ -960,10 +985,10 @@ __global__ void __launch_bounds__(kBlock, 4) grid_multinomial_kernel(QGen<R> gen
     // the block's weight prefix and targets (the block sums are complete)
     // while the other blocks' atomics drain
     unsigned long long pre = 0, QN = 0, before_last = 0;  // before_last: sum of the block's other tiles
-    GridTargets<false> tg{};
+    const GridTargets<false> *tg = nullptr;  // the block's copy in shared memory (no registers across phases)
     if (t_hi > t_lo) {  // the same branch in the whole block
         tile_prefix_total(bsum, b, G, &pre, &QN);
-        tg = block_targets(tgt, sv, QN);
+        tg = &block_targets_ref(tgt, sv, QN);
         if (t_hi - 1 > t_lo) {
             for (int tile = t_lo + (int)threadIdx.x; tile < t_hi - 1; tile += kBlock)
                 before_last += __ldcg(&tsum[tile]);
@@ -972,7 +997,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_multinomial_kernel(QGen<R> gen
     }
     if (!grid_barrier(st, 2 * G)) return out.report(st);
     const int h_lo = (int)((int64_t)kHistTiles * b / G), h_hi = (int)((int64_t)kHistTiles * (b + 1) / G);
-    for (int ht = h_lo; ht < h_hi; ++ht) hist_scan_tile(reinterpret_cast<const uint4 *>(h.hist), h.hpre, h.htot, ht);
+    for (int ht = h_lo; ht < h_hi; ++ht) hist_scan_tile(reinterpret_cast<const uint4 *>(h.hist), h.hrec, h.htot, ht);
     if (!grid_barrier(st, 3 * G)) return out.report(st);
     if (t_hi > t_lo) {
         uint32_t *tpre = reinterpret_cast<uint32_t *>(tb.tau) + kHistTpreOffset;
@@ -981,11 +1006,11 @@ __global__ void __launch_bounds__(kBlock, 4) grid_multinomial_kernel(QGen<R> gen
             raise_error(st, SMC_E_RANGE);
             out.report(st);
         }
-        const HistMap km{reinterpret_cast<const uint4 *>(h.hist), h.hpre, tpre, n};
-        select_tile_grid(tg, out, sink, n, t_hi - 1, pre + before_last, last, QN, st, tb, km);
+        const HistMap km{reinterpret_cast<const uint4 *>(h.hist), h.hrec, tpre, n};
+        select_tile_grid(*tg, out, sink, n, t_hi - 1, pre + before_last, last, QN, st, tb, km);
         for (int tile = t_lo; tile < t_hi - 1; ++tile) {
             const unsigned long long ts = scan_tile_local(g, n, tile, tb);
-            select_tile_grid(tg, out, sink, n, tile, pre, ts, QN, st, tb, km);
+            select_tile_grid(*tg, out, sink, n, tile, pre, ts, QN, st, tb, km);
             pre += ts;
         }
     }
@@ -1028,14 +1053,18 @@ __device__ __forceinline__ void residual_items(const TileBufs &tb, unsigned long
 // The residual count map: O = H_R(v) + the deterministic copies up to the
 // boundary (d0 before the tile, dloc[j] the tile-relative inclusive prefix)
 struct ResidualMap {
+    static constexpr bool kActive = true;
     HistMap hm;
     int64_t d0;
     const int32_t *dloc;  // pad32 layout
-    __device__ __forceinline__ void map_items(int32_t *K, int base, int64_t *k0) const {
-        hm.map_items(K, base, k0);
+    __device__ __forceinline__ void map_block(int32_t *K, int64_t *k0) const {
+        hm.map_block(K, k0);  // the same entries per thread as below
 #pragma unroll
-        for (int j = 0; j < kScanItems; ++j) K[pad32(base + j)] += (int32_t)(d0 + dloc[pad32(base + j)]);
-        if (k0) *k0 += d0;
+        for (int j = 0; j < kScanItems; ++j) {
+            const int e = pad32((int)threadIdx.x + j * kBlock);
+            K[e] += (int32_t)(d0 + dloc[e]);
+        }
+        if (threadIdx.x == 0) *k0 += d0;
     }
 };
 
@@ -1138,7 +1167,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
     if (!grid_barrier(st, 3 * G)) return out.report(st);
     // phase 4: histogram tiles; the r prefix and the targets on RQ_N
     const int h_lo = (int)((int64_t)kHistTiles * b / G), h_hi = (int)((int64_t)kHistTiles * (b + 1) / G);
-    for (int ht = h_lo; ht < h_hi; ++ht) hist_scan_tile(reinterpret_cast<const uint4 *>(h.hist), h.hpre, h.htot, ht);
+    for (int ht = h_lo; ht < h_hi; ++ht) hist_scan_tile(reinterpret_cast<const uint4 *>(h.hist), h.hrec, h.htot, ht);
     unsigned long long pre_r, RQN;
     tile_prefix_total(rs.br, b, G, &pre_r, &RQN);
     // RQ_N = 0 exactly when R = 0: any positive total then gives v = 0 and H = 0
@@ -1152,7 +1181,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
             raise_error(st, SMC_E_RANGE);
             out.report(st);
         }
-        const HistMap hm{reinterpret_cast<const uint4 *>(h.hist), h.hpre, tpre, (int64_t)Rn};
+        const HistMap hm{reinterpret_cast<const uint4 *>(h.hist), h.hrec, tpre, (int64_t)Rn};
         unsigned long long d0 = pre_d, r0 = pre_r;
         for (int tile = t_lo; tile < t_hi; ++tile) {
             if (!keep) {

@@ -53,7 +53,7 @@ int ceil_log2(int64_t n) {
 
 struct Layout {
     size_t st, rec, part, x, lw, anc, Q, tsum, bsum, inc, obs, obs_f, alpha;
-    size_t dhist, dpre, dtot;  // multinomial draw histogram, bucket prefixes, tile totals
+    size_t dhist, drec, dtot;  // multinomial / residual draw histogram, bucket records, tile totals
     size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, total;
     int ck;           // steps between checkpoints (record mode)
     int64_t nck;      // checkpoints
@@ -121,7 +121,7 @@ Layout make_layout(const smc_config *c) {
     L.obs_f = take((size_t)obs_vals * 4);
     L.alpha = take((c->model == SMC_MODEL_GMM) ? ((size_t)c->gmm.n_iter + 1) * 8 : 0);
     L.dhist = take(hists ? (size_t)kHistWords * 4 : 0);
-    L.dpre = take(hists ? (size_t)kHistBuckets * 4 : 0);
+    L.drec = take(hists ? (size_t)kHistBuckets * 8 : 0);
     L.dtot = take(hists ? (size_t)kHistTiles * 4 : 0);
     const bool rec = (c->flags & SMC_FLAG_RECORD) && c->model != SMC_MODEL_GMM;
     L.ck = (c->checkpoint_every > 0) ? c->checkpoint_every : 16;
@@ -158,7 +158,8 @@ struct smc_ctx {
     unsigned long long *bsum;  // block sums of the cooperative kernels (kMaxCoopGrid)
     uint32_t *sorted;
     uint32_t *dhist;  // multinomial draw histogram: byte counts (cleared by each use)
-    uint32_t *dpre, *dtot;
+    uint2 *drec;
+    uint32_t *dtot;
     double *obs;
     float *obs_f;
     double *alpha;
@@ -403,7 +404,7 @@ int launch_grid_multinomial(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
     tg.mrec = ~0ull >> kHistValueBits;  // floor((2^64 - 1) / 2^24)
     HistArgs h;
     h.hist = c->dhist;
-    h.hpre = c->dpre;
+    h.hrec = c->drec;
     h.htot = c->dtot;
     return launch_coop(c, grid, kern, qg, tg, anc_out(c), sk, n, tsum_of(c, SLOT_CDF), c->bsum, h, c->st, gate);
 }
@@ -426,7 +427,7 @@ int launch_grid_residual(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
     tg.mrec = ~0ull >> kHistValueBits;
     HistArgs h;
     h.hist = c->dhist;
-    h.hpre = c->dpre;
+    h.hrec = c->drec;
     h.htot = c->dtot;
     ResidualSums rs;
     rs.tq = tsum_of(c, SLOT_CDF);
@@ -668,7 +669,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->tsum = reinterpret_cast<unsigned long long *>(c->ws + L.tsum);
     c->bsum = reinterpret_cast<unsigned long long *>(c->ws + L.bsum);
     c->dhist = reinterpret_cast<uint32_t *>(c->ws + L.dhist);
-    c->dpre = reinterpret_cast<uint32_t *>(c->ws + L.dpre);
+    c->drec = reinterpret_cast<uint2 *>(c->ws + L.drec);
     c->dtot = reinterpret_cast<uint32_t *>(c->ws + L.dtot);
     c->obs = reinterpret_cast<double *>(c->ws + L.obs);
     c->obs_f = reinterpret_cast<float *>(c->ws + L.obs_f);
