@@ -198,19 +198,18 @@ struct GridTargets {
         p.zf = f - w;
         p.err += fmaf(d, 0x1p-21f, 0x1p-21f);
     }
-    // stratified draws, four to a Philox call, kept between the boundaries
-    // of a thread (consecutive boundaries mostly fall in the same call)
+    // stratified draws: a block's table of 2j + 1 for the outputs
+    // [kb, kb + cnt) in shared memory, in two pieces of kScanTile entries;
+    // past it (a tile with still more outputs) one Philox call per boundary
     struct DrawCache {
-        int64_t k4 = -1;
-        uint4 w;
+        const uint32_t *tab0 = nullptr, *tab1 = nullptr;
+        int64_t kb = 0;
+        int cnt = 0;
     };
     __device__ __forceinline__ unsigned long long c_at(int64_t k, DrawCache &dc) const {
-        if ((k >> 2) != dc.k4) {
-            dc.k4 = k >> 2;
-            dc.w = resample_words(key, stream, t, k & ~3ll);
-        }
-        const uint32_t ww = ((k & 3) == 0) ? dc.w.x : ((k & 3) == 1) ? dc.w.y : ((k & 3) == 2) ? dc.w.z : dc.w.w;
-        return 2ull * u24(ww) + 1ull;
+        const int64_t i = k - dc.kb;
+        if (i >= 0 && i < dc.cnt) return i < kScanTile ? dc.tab0[i] : dc.tab1[i - kScanTile];
+        return 2ull * resample_u24_at(key, stream, t, k) + 1ull;
     }
     __device__ __forceinline__ int64_t k_from(const ZPos &p, unsigned long long X, DrawCache &dc) const {
         if constexpr (kStratified) {
@@ -596,10 +595,38 @@ __device__ __forceinline__ void select_tile_closed(const GridTargets<kStratified
     // i's outputs are [K[i - 1], K[i]) and K[-1] = K(pre) = the tile's first
     // output
     int32_t *Kend = reinterpret_cast<int32_t *>(tb.tau);  // pad32 layout, K <= N < 2^31
+    typename GridTargets<kStratified>::DrawCache dc;
+    if constexpr (kStratified) {
+        // the draws of the tile's outputs, from about its first one
+        // (floor(Q_pre N / Q_N), rounded down to a Philox call) to past its
+        // last, at most 2 kScanTile of them: uniform Philox calls into the
+        // ancestor buffer (unused until the windows) and the threshold buffer
+        // past the offspring ends, so that no thread calls Philox for a
+        // boundary inside that range
+        constexpr int kTab1 = kScanTile + kScanTile / 32 + 1;  // 32-bit words: past Kend
+        static_assert(kTab1 + kScanTile <= 2 * (kScanTile + kScanTile / 8), "inside the threshold buffer");
+        const int64_t kb = max(tg.z_at(pre).zi, (int64_t)0) & ~int64_t(3);
+        const int64_t ke = min(tg.z_at(pre + tb.q[pad8(kScanTile - 1)]).zi + 2, n);  // past the last output
+        const int calls = (int)min((ke - kb + 3) >> 2, (int64_t)(2 * kScanTile / 4));
+        uint32_t *tab0 = reinterpret_cast<uint32_t *>(tb.a);
+        uint32_t *tab1 = reinterpret_cast<uint32_t *>(tb.tau) + kTab1;
+        for (int c = tid; c < calls; c += kBlock) {
+            const uint4 w = resample_words(tg.key, tg.stream, tg.t, kb + 4 * (int64_t)c);
+            uint32_t *d = (4 * c < kScanTile) ? tab0 + 4 * c : tab1 + (4 * c - kScanTile);
+            d[0] = 2u * u24(w.x) + 1u;
+            d[1] = 2u * u24(w.y) + 1u;
+            d[2] = 2u * u24(w.z) + 1u;
+            d[3] = 2u * u24(w.w) + 1u;
+        }
+        __syncthreads();
+        dc.tab0 = tab0;
+        dc.tab1 = tab1;
+        dc.kb = kb;
+        dc.cnt = 4 * max(calls, 0);
+    }
     {
         unsigned long long qprev = base ? tb.q[pad8(base - 1)] : 0ull;
         typename GridTargets<kStratified>::ZPos zp = tg.z_at(pre + qprev);
-        typename GridTargets<kStratified>::DrawCache dc;
         if (tid == 0) tb.k[0] = tg.k_from(zp, pre, dc);  // mapped with the thread's own entries
 #pragma unroll 1
         for (int j = 0; j < kScanItems; ++j) {
