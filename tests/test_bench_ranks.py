@@ -58,3 +58,5 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["steps"] == 1 and d["warmup"] == 3  # K as given; W raised to the minimum of 3
+    assert d["config"]["oracle_sample_particles"] == 4096
