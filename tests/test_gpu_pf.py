@@ -140,6 +140,26 @@ def test_heavy_particles_in_some_tiles(scheme, precision):
     assert counts.max() > 64  # some tile spans several output windows
 
 
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_one_particle_owns_most_outputs(scheme):
+    """One particle carries about 94 % of the weight: its tile owns some
+    10^4 outputs, more than a block's shared-memory table of stratified
+    draws (4096) and several selection windows; the ancestors are the
+    oracle's on the GPU's CDF."""
+    need_gpu()
+    n, seed = 5 * 2048 + 777, 12
+    s, y, op = make_pf(n, 2, 32, scheme=scheme, threshold=0.0, seed=seed)
+    s.initialize()
+    lw = np.random.default_rng(4).normal(0.0, 0.5, n)
+    heavy = 3 * 2048 + 17
+    lw[heavy] += 12.0
+    s.write_log_weight(lw)
+    lw_gpu = s.log_weight()
+    s.resample(force=True)
+    anc = check_resample(s, lw_gpu, 0, scheme, seed, 32)
+    assert np.count_nonzero(anc == heavy) > 4096 + 2048
+
+
 @pytest.mark.parametrize("scheme", ["systematic", "stratified"])
 def test_boundaries_next_to_integers(scheme):
     """Equal weights give Q_i = (i + 1) 2^F, so every offspring boundary
