@@ -107,6 +107,21 @@ __device__ __forceinline__ R warp_sum4(R v0, R v1, R v2, R v3) {
     return x;
 }
 
+// The same transpose reduce for four double-float sums: lanes 8q .. 8q + 7
+// end with the warp total of sum q (six double-float additions per lane
+// instead of twenty for four separate trees).
+__device__ __forceinline__ DF df_warp_sum4(DF v0, DF v1, DF v2, DF v3) {
+    const int lane = threadIdx.x & 31;
+    const bool up = lane & 16, hi8 = lane & 8;
+    const DF a = df_add(up ? v2 : v0, df_shfl_xor(up ? v0 : v2, 16));
+    const DF b = df_add(up ? v3 : v1, df_shfl_xor(up ? v1 : v3, 16));
+    DF x = df_add(hi8 ? b : a, df_shfl_xor(hi8 ? a : b, 8));
+    x = df_add(x, df_shfl_xor(x, 4));
+    x = df_add(x, df_shfl_xor(x, 2));
+    x = df_add(x, df_shfl_xor(x, 1));
+    return x;
+}
+
 // Block-level partial of E items per thread.  lw = -inf marks inactive
 // items.  Each warp reduces its own maximum m_w and its sums of
 // e = exp(lw - m_w) in R (no block barrier), then one barrier hands the
@@ -285,29 +300,20 @@ __device__ __forceinline__ void combine_partials_df(const Partial *part, int nb,
             }
         }
     }
-    // tree levels as a loop: this code runs in one block per launch, where
-    // fetching unrolled instructions costs more than the loop
-#pragma unroll 1
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < kSums; ++q) S[q] = df_add(S[q], df_shfl_xor(S[q], o));
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < kSums; ++q) s_df[warp][q] = S[q];
+    // the warp's four sums by a transpose reduce: lanes 8q .. 8q + 7 hold sum q
+    static_assert(kSums == 4 && kBlock / 32 == 8, "four sums, eight warps");
+    const DF x = df_warp_sum4(S[0], S[1], S[2], S[3]);
+    if ((lane & 7) == 0) s_df[warp][lane >> 3] = x;
     __syncthreads();
     if (warp == 0) {
-        DF T[kSums];
-#pragma unroll
-        for (int q = 0; q < kSums; ++q) T[q] = lane < kBlock / 32 ? s_df[lane][q] : DF{0.0f, 0.0f};
-#pragma unroll 1
-        for (int o = (kBlock / 32) / 2; o > 0; o >>= 1)
-#pragma unroll
-            for (int q = 0; q < kSums; ++q) T[q] = df_add(T[q], df_shfl_xor(T[q], o));
-        if (lane == 0) {
-            s_out.M = M;
-#pragma unroll
-            for (int q = 0; q < kSums; ++q) s_out.S[q] = T[q];
-        }
+        // one value per lane (lane 8q + w: sum q of warp w), reduced within
+        // each group of eight lanes
+        DF y = s_df[lane & 7][lane >> 3];
+        y = df_add(y, df_shfl_xor(y, 4));
+        y = df_add(y, df_shfl_xor(y, 2));
+        y = df_add(y, df_shfl_xor(y, 1));
+        if ((lane & 7) == 0) s_out.S[lane >> 3] = y;
+        if (lane == 0) s_out.M = M;
     }
     __syncthreads();
     *out = s_out;
