@@ -52,10 +52,10 @@ extern "C" {
 #define SMC_E_TIMEOUT 4    /* a bounded device wait gave up */
 #define SMC_E_CUDA 5       /* a CUDA runtime call failed */
 #define SMC_E_STATE 6      /* call out of order (e.g. move before initialize) */
-#define SMC_E_RANGE 7      /* a device counter left its range: a 24-bit multinomial draw
-                            * value drawn 256 times in one resampling step (probability
-                            * below 1e-60 per step for N <= 2^30); the step's ancestors
-                            * are not valid */
+#define SMC_E_RANGE 7      /* a device counter left its range: a 24-bit multinomial or
+                            * residual draw value drawn 256 times in one resampling step
+                            * (probability below 1e-60 per step for N <= 2^30); the
+                            * step's ancestors are not valid */
 
 /* resampling schemes (Sec. 2.1; Douc et al. 2005); the paper's default is
  * stratified (Sec. 4.1.3) */
@@ -182,7 +182,10 @@ int smc_move(smc_ctx *ctx);
 
 /* Resampling of the current iteration when its ESS test asked for it (or
  * always, when force != 0): fixed-point CDF and ancestor selection by the
- * configured scheme.  The particle gather happens in the next move/mcmc. */
+ * configured scheme, one cooperative kernel (systematic and stratified:
+ * closed-form offspring ranges; multinomial and residual: a histogram of the
+ * 24-bit draws; a multinomial or residual context holds 24 MB of workspace
+ * for it).  The particle gather happens in the next move/mcmc. */
 int smc_resample(smc_ctx *ctx, int force);
 
 /* mcmc queue (Sec. 4.1.3): GMM: the three random-walk Metropolis blocks on

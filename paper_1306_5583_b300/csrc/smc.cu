@@ -683,7 +683,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->hio = nullptr;
     c->hio_d = nullptr;
     cudaGetDevice(&c->device);
-    // zero the state block, records, scan status words and bucket counters
+    // zero the state block, records, scan status words and block sums
     int rc = cuda_check(cudaMemsetAsync(c->ws, 0, L.part, c->stream));
     if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + L.tsum, 0, L.inc - L.tsum, c->stream));
     if (!rc) {
