@@ -73,13 +73,13 @@ __device__ __forceinline__ void gen_items(const Gen &g, int64_t i0, int64_t n, u
     }
 }
 
-// floor(n q / qn) for q <= qn < 2^62, n < 2^31 (exact: float estimate, then
-// integer correction with 128-bit products)
+// floor(n q / qn) for q <= qn < 2^62, n < 2^31 (exact: float estimate from
+// inv_qn ~ 1 / qn, then integer correction with 128-bit products)
 __device__ __forceinline__ unsigned long long floor_nq_over(unsigned long long n, unsigned long long q,
-                                                            unsigned long long qn) {
+                                                            unsigned long long qn, float inv_qn) {
     if (qn == 0 || q > qn) return 0;
     const U128 num = mul64(n, q);
-    float est = (float(n) * float(q)) / float(qn);
+    float est = float(n) * float(q) * inv_qn;
     unsigned long long d = (unsigned long long)fmaxf(est, 0.0f);
     if (d > n) d = n;
     while (d > 0 && gt128(mul64(d, qn), num)) --d;
@@ -1067,12 +1067,13 @@ __device__ __forceinline__ void residual_items(const TileBufs &tb, unsigned long
                                                unsigned long long (&r)[kScanItems]) {
     const int base = threadIdx.x * kScanItems;
     unsigned long long prev = base ? tb.q[pad8(base - 1)] : 0ull;
+    const float inv_qn = QN ? __fdividef(1.0f, float(QN)) : 0.0f;  // the estimate's error is corrected exactly
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const unsigned long long qc = tb.q[pad8(base + j)];
         const unsigned long long qi = qc - prev;
         prev = qc;
-        d[j] = floor_nq_over(N, qi, QN);
+        d[j] = floor_nq_over(N, qi, QN, inv_qn);
         r[j] = (N * qi - d[j] * QN) >> shift;  // the remainder is below Q_N: exact modulo 2^64
     }
 }
@@ -1097,11 +1098,24 @@ struct ResidualMap {
 
 // q, d and r of one tile into the tile buffers for the selection: the q scan
 // in tb.q on entry (kept or rescanned); on exit tb.q holds the r scan and
-// tb.a the d scan (tile-relative, int32: at most N)
+// tb.a the d scan (tile-relative, int32: at most N).  d_known: the thread's
+// own entries of tb.a already hold its d_i (kept from the d-sum pass).
 __device__ __forceinline__ void residual_tile_scans(TileBufs &tb, unsigned long long N, unsigned long long QN,
-                                                    int shift) {
+                                                    int shift, bool d_known = false) {
     unsigned long long d[kScanItems], r[kScanItems];
-    residual_items(tb, N, QN, shift, d, r);
+    if (d_known) {
+        const int b0 = threadIdx.x * kScanItems;
+        unsigned long long prev = b0 ? tb.q[pad8(b0 - 1)] : 0ull;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const unsigned long long qc = tb.q[pad8(b0 + j)];
+            d[j] = (unsigned long long)(uint32_t)tb.a[pad32(b0 + j)];
+            r[j] = (N * (qc - prev) - d[j] * QN) >> shift;
+            prev = qc;
+        }
+    } else {
+        residual_items(tb, N, QN, shift, d, r);
+    }
     scan_items_q(d, tb);  // d scan (every thread has read its q entries before the first barrier inside)
     const int base = threadIdx.x * kScanItems;
     int32_t *dl = tb.a;
@@ -1157,7 +1171,10 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
         residual_items(tb, N, QN, 0, d, r);
         unsigned long long sd = 0;
 #pragma unroll
-        for (int j = 0; j < kScanItems; ++j) sd += d[j];
+        for (int j = 0; j < kScanItems; ++j) {
+            sd += d[j];
+            if (keep) tb.a[pad32((int)threadIdx.x * kScanItems + j)] = (int32_t)d[j];  // kept for phase 3
+        }
         sd = block_sum_u64(sd);
         if (threadIdx.x == 0) rs.td[tile] = sd;
         bd += sd;
@@ -1176,7 +1193,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
     for (int tile = t_lo; tile < t_hi; ++tile) {
         unsigned long long sr;
         if (keep) {
-            residual_tile_scans(tb, N, QN, shift);
+            residual_tile_scans(tb, N, QN, shift, true);
             sr = tb.q[pad8(kScanTile - 1)];
         } else {
             scan_tile_local(g, n, tile, tb);
