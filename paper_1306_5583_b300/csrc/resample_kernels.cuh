@@ -970,10 +970,11 @@ __device__ __forceinline__ uint32_t hist_tile_prefix(const uint32_t *htot, uint3
 // Phase 1: the block's share of the histogram cleared (full-line stores: the
 // lines are allocated in L2 without a DRAM read) and the tile sums of its
 // weight tiles (the last tile's scan kept); grid barrier; phase 2: the
-// block's share of the N draws counted into the histogram (L2 atomics);
-// grid barrier; phase 3: the bucket prefixes of its histogram tiles; grid
-// barrier; phase 4: selection of its weight tiles with K(X) = H(v(X)).  A
-// block may own no weight tile or no histogram tile.
+// block's share of the N draws counted into the histogram (L2 atomics), then
+// its weight prefix and targets; grid barrier; phase 3: the bucket records
+// of its histogram tiles; grid barrier; phase 4: selection of its weight
+// tiles with K(X) = H(v(X)).  A block may own no weight tile or no
+// histogram tile.
 template <typename R, class Sink>
 __global__ void __launch_bounds__(kBlock, 4) grid_multinomial_kernel(QGen<R> gen, GridTargets<false> tgt, AncOut out,
                                                                   Sink sink, int64_t n, unsigned long long *tsum,
@@ -1126,11 +1127,12 @@ __device__ __forceinline__ void residual_tile_scans(TileBufs &tb, unsigned long 
 
 // One-pass residual resampling: a cooperative launch of one full wave.
 // Phase 1: histogram share cleared, q tile sums (a block with one tile keeps
-// its q scan until phase 3); barrier; phase 2: Q_N, d sums (and the stored
-// CDF); barrier; phase 3: R and s, the R draws into the histogram, r sums;
-// barrier; phase 4: histogram tiles, the block's r prefix and targets;
-// barrier; phase 5: selection.  Blocks with several tiles rescan the q of
-// every tile in every phase.
+// its q scan until phase 3); barrier; phase 2: Q_N, d sums (a block with one
+// tile keeps its d_i until phase 3; the stored CDF); barrier; phase 3: R and
+// s, the R draws into the histogram, r sums (a kept tile gets its d and r
+// scans); barrier; phase 4: the bucket records of the block's histogram
+// tiles, its r prefix and targets; barrier; phase 5: selection.  Blocks with
+// several tiles rescan the q of every tile in every phase.
 template <typename R, class Sink>
 __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, GridTargets<false> tgt, AncOut out,
                                                                Sink sink, int64_t n, ResidualSums rs, HistArgs h,
