@@ -197,8 +197,10 @@ __device__ __forceinline__ void pf_finalize(const PfArgs<R> &a, DevState *st, co
     }
 }
 
+// Five blocks per SM for FP32 (48 registers, no spills; six spill), four
+// for FP64.
 template <typename R>
-__global__ void __launch_bounds__(kBlock, 4) pf_iterate_kernel(PfArgs<R> a) {
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 4) pf_iterate_kernel(PfArgs<R> a) {
     DevState *st = a.st;
     // the ancestor indices do not depend on the state block: their load is
     // in flight while the snapshot is read (unused when nothing is gathered)
