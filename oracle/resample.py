@@ -164,3 +164,80 @@ def resample(scheme, lw, seed, t, stream=0):
     Q = cdf(q)
     return {"systematic": systematic, "stratified": stratified,
             "multinomial": multinomial}[scheme](Q, seed, t, stream)
+
+
+# ---- the plain real-weight definition (Sec. 2.1), no quantisation --------
+#
+# The schemes above run on exact fixed-point weights.  What they stand for
+# is the textbook definition on the real normalised weights: the CDF
+# C_i = w_0 + ... + w_i of w_i = exp(lw_i - m) in float64, the target of
+# output k scaled to C_N (systematic C_N (k + u) / N, stratified
+# C_N (k + u_k) / N, multinomial C_N u_(k)), and the ancestor
+# a_k = min{i : C_i > U_k}.  The residual step (Douc et al. 2005) keeps
+# floor(N W_i) copies of particle i and draws the other R = N - sum floor(N W_i)
+# multinomially on the residual weights N W_i - floor(N W_i).  The uniforms
+# are the same Philox midpoints (2j + 1) / 2^25 as above.  These functions are
+# the pin of the fixed-point schemes: both must give the same ancestors except
+# where a target lies within the quantisation error of a CDF boundary.
+
+def plain_weights(lw):
+    """w_i = exp(lw_i - max lw) in float64 (the largest weight is 1)."""
+    lw = np.asarray(lw, dtype=np.float64)
+    m = float(np.max(lw))
+    if not math.isfinite(m):
+        raise FloatingPointError("all log-weights are -inf or NaN")
+    return np.exp(lw - m)
+
+
+def plain_select(C, U):
+    """a_k = min{i : C_i > U_k} on a float64 CDF C (non-decreasing).  A target
+    at or above C_N (a rounding artefact) goes to the last particle with a
+    positive weight, so that a zero weight is never selected."""
+    C = np.asarray(C, dtype=np.float64)
+    a = np.searchsorted(C, np.asarray(U, dtype=np.float64), side="right").astype(np.int64)
+    last = int(np.flatnonzero(np.diff(np.concatenate([[0.0], C])) > 0)[-1])
+    return np.minimum(a, last)
+
+
+def _mid(j):
+    return (2.0 * np.asarray(j, dtype=np.float64) + 1.0) / float(1 << 25)
+
+
+def plain_resample(scheme, lw, seed, t, stream=0):
+    """Ancestors of the named scheme on the float64 CDF of the real weights
+    (sorted, like the fixed-point schemes)."""
+    w = plain_weights(lw)
+    n = w.shape[0]
+    k = np.arange(n, dtype=np.float64)
+    if scheme == "residual":
+        return _plain_residual(w, seed, t, stream)
+    C = np.cumsum(w)
+    CN = C[-1]
+    if scheme == "systematic":
+        U = CN * (k + _mid(philox.systematic_u24(seed, t, stream))) / n
+    elif scheme == "stratified":
+        U = CN * (k + _mid(philox.resample_u24(seed, t, n, stream))) / n
+    elif scheme == "multinomial":
+        U = CN * np.sort(_mid(philox.resample_u24(seed, t, n, stream)))
+    else:
+        raise ValueError(scheme)
+    return plain_select(C, U)
+
+
+def plain_residual_parts(w):
+    """floor(N W_i), R and the residual weights N W_i - floor(N W_i), float64."""
+    n = w.shape[0]
+    nw = n * (w / np.sum(w))
+    d = np.floor(nw)
+    return d.astype(np.int64), int(n - d.sum()), nw - d
+
+
+def _plain_residual(w, seed, t, stream):
+    n = w.shape[0]
+    d, R, r = plain_residual_parts(w)
+    counts = d.copy()
+    if R > 0:
+        RC = np.cumsum(r)
+        U = RC[-1] * np.sort(_mid(philox.resample_u24(seed, t, R, stream)))
+        counts += np.bincount(plain_select(RC, U), minlength=n)
+    return expand(counts)

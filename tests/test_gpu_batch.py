@@ -61,3 +61,44 @@ def test_batch_tune_and_iterate_in_pieces():
     assert np.array_equal(a, bt.log_evidence())
     with pytest.raises(smc.SMCError):
         bt.iterate(1)   # past the longest filter
+
+
+def test_batch_fp64_filters_match_the_oracle():
+    """FP64 batch: a one-particle filter, a ragged one (N = 2049, one
+    particle past a tile), one at the paper's N = 1000 and one of 2^14
+    particles, each against the free-running oracle filter on the same
+    Philox stream (stream id = filter index): records at the FP64
+    tolerances of the plain path, identical resampling decisions, final
+    particle system within 1e-10."""
+    need_gpu()
+    from gpu_common import assert_close, oracle_params
+    from oracle import cv as ocv
+    ns = [1, 2049, 1000, 1 << 14]
+    ts = [6, 14, 20, 10]
+    seed, thr = 21, 0.7
+    p = dict(workloads.CV_DEFAULT)
+    cfg = smc.make_config(model="cv", n=1, precision=64, scheme="systematic", threshold=thr, seed=seed,
+                          max_data=max(ts), keep_cdf=False)
+    bt = smc.Batch(cfg, ns, ts)
+    data = [_data(T, 1 + b) for b, T in enumerate(ts)]
+    for b in range(len(ns)):
+        bt.set_data(b, data[b])
+    bt.run()
+    lz = bt.log_evidence()
+    op = oracle_params(p)
+    any_resampled = False
+    for b, (n, T) in enumerate(zip(ns, ts)):
+        ref, last = ocv.run(data[b], n, seed, op, scheme="systematic", threshold=thr, stream=b)
+        hb = bt.history(b, T)
+        assert len(hb) == T
+        for r, o in zip(hb, ref):
+            assert r["t"] == o["t"]
+            assert r["resampled"] == o["resampled"], (b, r["t"])
+            assert abs(r["L"] - o["L"]) < 1e-9, (b, r["t"])
+            assert abs(r["logZ"] - o["logZ"]) < 1e-9, (b, r["t"])
+            assert abs(r["ess"] - o["ess"]) < 1e-7 * n
+            assert abs(r["mean_x"] - o["mean_x"]) < 1e-9 and abs(r["mean_y"] - o["mean_y"]) < 1e-9
+            any_resampled |= bool(o["resampled"])
+        assert_close(bt.state(b), last.x, 1e-10, f"final state of filter {b}")
+        assert abs(lz[b] - ref[-1]["logZ"]) < 1e-9
+    assert any_resampled
