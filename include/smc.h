@@ -21,7 +21,9 @@
  *   asynchronously; errors raised on the device (non-finite weights, a
  *   bounded wait that gave up) are kept in a device error word and returned
  *   by the next call that synchronises (smc_ess with a host pointer,
- *   smc_log_evidence, smc_path_sampling, smc_read_*, smc_sync).
+ *   smc_log_evidence, smc_path_sampling, smc_read_*, smc_sync).  smc_read_*
+ *   still copy their data when the error word is set (the particle system of
+ *   a failed step is the one before it) and return the error.
  * * Memory: the caller owns the device workspace (size from
  *   smc_workspace_bytes, 256-byte aligned) and the stream; the context holds
  *   non-owning pointers into them and host memory of its own.  Host buffers
@@ -68,6 +70,9 @@ extern "C" {
 #define SMC_FLAG_KEEP_CDF 1u  /* store the fixed-point CDF of each resampling step (smc_read_cdf) */
 #define SMC_FLAG_RECORD 2u    /* CV models: record the ancestors of every step and a state checkpoint
                                  every checkpoint_every steps, for smc_pf_grad / smc_pf_replay */
+#define SMC_FLAG_POST_MEAN 4u /* CV models: also record the post-resampling filtered mean (mean_post;
+                                 Sec. 4.1.5 evaluates monitors after the whole iteration) with one
+                                 more kernel after each resampling step */
 
 /* models */
 #define SMC_MODEL_CV 0        /* Sec. 5.1: constant-velocity tracking, Student-t observations */
@@ -145,7 +150,9 @@ typedef struct {
     int32_t status;       /* SMC_OK or an error code */
     int32_t pad;
     double accept_mala;   /* GMM: acceptance rate of the Langevin move */
-    double pad2;
+    double mean_post[2];  /* PF with SMC_FLAG_POST_MEAN: mean of the positions over the particle system
+                             that ends the iteration (1/N sum_k pos_{a_k} after resampling, else the
+                             weighted mean); NaN without the flag */
 } smc_record;
 
 typedef struct smc_ctx smc_ctx;
@@ -369,6 +376,22 @@ int smc_batch_read_state(smc_batch *b, int32_t filter, void *dst, int on_device)
 int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], uint32_t *d_out, int64_t n,
                       void *cuda_stream);
 
+/* Failure detection (bounded device waits).  Every wait of a kernel on
+ * another block (the grid barriers of the cooperative resampling kernels, the
+ * bulk-copy wait of the GMM kernels) polls at most a fixed number of times,
+ * then raises SMC_E_TIMEOUT in the context's device error word and returns
+ * instead of hanging.  smc_set_wait_limit sets that number of polls on the
+ * current device (default 2^24, about a second; 0 restores the default); it
+ * applies to later launches of every context on the device.
+ * smc_wait_selftest queues on the context's stream one block that waits at
+ * the grid barrier for a second block that does not exist: after the limit
+ * the wait gives up, the next synchronising call returns SMC_E_TIMEOUT, and
+ * nothing but the error word changes (smc_restore of an earlier checkpoint,
+ * or smc_initialize, clears it).  No failure detection in the paper; this is
+ * the device half of the host-side status codes. */
+int smc_set_wait_limit(uint32_t polls);
+int smc_wait_selftest(smc_ctx *ctx);
+
 /* Systematic resampling straight from N float32 log-weights (device) into N
  * int32 ancestors (device), for callers that cannot allocate device memory:
  * code running inside a region that a framework's allocator owns, a loop
@@ -385,10 +408,21 @@ int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], uint32_t *d_
  * on a device shares the array and leaves its contents behind (each call
  * clears what it needs first), so calls that overlap on the GPU (other
  * streams, other threads) race: serialise them.  d_log_weight must be
- * 16-byte aligned.  Asynchronous on cuda_stream; a log-weight maximum that is
- * not finite makes the call write nothing. */
+ * 16-byte aligned.  Asynchronous on cuda_stream: a NaN log-weight, or a maximum
+ * that is not finite (all -inf), makes the call write nothing and leaves
+ * SMC_E_NONFINITE in the array's status word, which
+ * smc_resample_noalloc_status reads.  The cached device address is that of
+ * the device's primary context: after cudaDeviceReset the process must not
+ * call this entry point again. */
 int smc_resample_systematic_noalloc(const float *d_log_weight, int64_t n, uint64_t seed, uint32_t stream_id,
                                     int32_t t, int32_t *d_ancestors, void *cuda_stream);
+
+/* Status of the last smc_resample_systematic_noalloc call queued on this
+ * device: waits for cuda_stream, then stores SMC_OK or SMC_E_NONFINITE
+ * (nothing was written to d_ancestors) in *h_status.  A 4-byte copy from the
+ * library's array into a local variable; allocates nothing.  Returns
+ * SMC_E_CUDA if the copy or the wait fails. */
+int smc_resample_noalloc_status(void *cuda_stream, int32_t *h_status);
 
 #ifdef __cplusplus
 }

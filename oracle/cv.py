@@ -25,6 +25,10 @@ Follows Sec. 5.1.1 (the model and Algorithm 1) in float64:
 * monitor: the filtered mean sum_i W_t,i pos_i of the two positions, taken
   after weighting and before resampling (reading: vSMC records monitors after
   the whole iteration; the pre-resampling estimate is the lower-variance one).
+  The post-resampling mean (Sec. 4.1.5 evaluates monitors after the whole
+  iteration) is also reported: (1/N) sum_k pos_{a_k} over the resampled
+  system when the iteration resampled, else the weighted mean itself (the
+  particle system after the iteration is then the weighted one).
 * the log-likelihood estimate log Z-hat = sum_t L_t, L_t the log-sum-exp of
   lw_t = log W_{t-1} + log g(y_t | x_t) (Sec. 2.2 ratio estimator).
 
@@ -133,6 +137,16 @@ def step(x_prev, lw_prev, L_prev, ancestors, t, y_t, seed, p, threshold, stream=
     return weigh(move(x_prev, t, seed, p, stream), base, y_t, p, threshold)
 
 
+def post_resampling_mean(r, ancestors):
+    """Mean of the two positions over the particle system that ends the
+    iteration: equally weighted copies x_{a_k} after resampling, else the
+    weighted system (its weighted mean)."""
+    if ancestors is None:
+        return r.mean_x, r.mean_y
+    a = np.asarray(ancestors, dtype=np.int64)
+    return float(np.mean(r.x[0][a])), float(np.mean(r.x[1][a]))
+
+
 def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, record_ancestors=False):
     """Whole filter over observations y (T, 2).  Returns per-iteration
     records and the final state."""
@@ -146,8 +160,9 @@ def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, record_ance
             r = step(r_prev.x, r_prev.lw, r_prev.L, anc, t, y[t], seed, p, threshold, stream)
         logZ += r.L
         anc = resample.resample(scheme, r.lw, seed, t, stream) if r.resample else None
+        post = post_resampling_mean(r, anc)
         rec = dict(t=t, L=r.L, logZ=logZ, ess=r.ess, mean_x=r.mean_x, mean_y=r.mean_y,
-                   resampled=r.resample)
+                   resampled=r.resample, post_mean_x=post[0], post_mean_y=post[1])
         if record_ancestors:
             rec["ancestors"] = anc
         recs.append(rec)

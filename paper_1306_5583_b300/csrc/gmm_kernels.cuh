@@ -313,8 +313,11 @@ __device__ __forceinline__ R mh_log_uniform(uint2 key, uint32_t i, uint32_t t, u
 }
 
 // Bulk-copy (TMA) the data into shared memory; bounded wait on the mbarrier.
-__device__ __forceinline__ void stage_data(void *smem_dst, const void *gsrc, uint32_t bytes, DevState *st) {
+// Returns false to every thread when the copy did not complete within the
+// wait limit (SMC_E_TIMEOUT raised): the caller must not read the tile.
+__device__ __forceinline__ bool stage_data(void *smem_dst, const void *gsrc, uint32_t bytes, DevState *st) {
     __shared__ alignas(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_done;
     const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&s_mbar);
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem_dst);
     if (threadIdx.x == 0) {
@@ -330,15 +333,32 @@ __device__ __forceinline__ void stage_data(void *smem_dst, const void *gsrc, uin
             : "memory");
     }
     uint32_t done = 0;
-    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+    for (uint32_t it = 0; it < c_wait_limit && !done; ++it) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
             : "r"(mbar)
             : "memory");
     }
-    if (!done) raise_error(st, SMC_E_TIMEOUT);
+    if (!done) {
+        // the copy did not complete in time: raise the error, then wait once
+        // more (bounded) so that a late copy does not land in the shared
+        // memory of a later block; the caller skips its compute either way
+        raise_error(st, SMC_E_TIMEOUT);
+        uint32_t late = 0;
+        for (uint32_t it = 0; it < c_wait_limit && !late; ++it) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(late)
+                : "r"(mbar)
+                : "memory");
+        }
+    }
+    if (threadIdx.x == 0) s_done = 1u;
     __syncthreads();
+    if (!done) atomicAnd(&s_done, 0u);  // any thread that gave up
+    __syncthreads();
+    return s_done != 0u;
 }
 
 // ---- state rows -------------------------------------------------------------
@@ -504,7 +524,7 @@ __global__ void __launch_bounds__(kBlock) gmm_log_target_kernel(GmmArgs<R> a, co
     constexpr int D = 3 * NC - 1;
     extern __shared__ __align__(16) unsigned char s_raw[];
     const R *ys = reinterpret_cast<const R *>(s_raw);
-    stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), a.st);
+    if (!stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), a.st)) return;
     const int q = threadIdx.x & (kQuad - 1);
     const int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kQuad;
     const bool active = i < count;
@@ -554,7 +574,7 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
     DevState *st = a.st;
     const DevState *sv = snapshot(st);
     if (sv->error) return;
-    stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st);
+    if (!stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st)) return;
     const int q = threadIdx.x & (kQuad - 1);
     const int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kQuad;
     const bool active = i < a.n;
@@ -703,7 +723,9 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
         s_k[2] = R((1.0 + sqrt(1.0 / aclamp)) * 0.15);
         s_k[3] = R((1.0 + sqrt(1.0 / aclamp)) * 0.2);
     }
-    stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st);  // (its barriers publish s_k)
+    // (its barriers publish s_k); a copy that timed out leaves the data tile
+    // unread: the block stops and the error word invalidates the step
+    if (!stage_data(s_raw, a.y, (uint32_t)(((size_t)a.nd * sizeof(R) + 15) & ~size_t(15)), st)) return;
     const R a_t = s_k[0], s_mu = s_k[1], s_lam = s_k[2], s_om = s_k[3];
     const bool gather = sv->ready != 0;
     const int cur = sv->cur, cur_lw = sv->cur_lw;

@@ -222,4 +222,133 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 4) pf_iterate_ker
     pf_finalize<R>(a, st, sv, gridDim.x, t, cur, cur_lw);
 }
 
+// Post-resampling filtered mean (SMC_FLAG_POST_MEAN), after the resampling
+// step of iteration t: the mean of the two positions over the particle
+// system that ends the iteration (Sec. 4.1.5 evaluates monitors after the
+// whole iteration), i.e. (1/N) sum_k pos_{a_k} over the pending ancestors
+// when the iteration resampled, else the weighted mean already in the
+// record.  Per-thread and per-block sums in R, the block sums added by the
+// last block in a fixed order (double-float on the FP32 path, float64 on
+// the FP64 path): deterministic.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) post_mean_kernel(PfArgs<R> a) {
+    DevState *st = a.st;
+    const DevState *sv = snapshot(st, true);
+    if (sv->error || sv->t < 0) return;
+    smc_record *r = &a.rec[sv->t % a.rec_cap];
+    // the result also goes to smc_iterate_host's staging (whose record the
+    // move kernel has already written)
+    volatile double *hmp = a.hio_out ? a.hio_out->rec.mean_post : nullptr;
+    if (!sv->ready) {  // no resampling: the weighted system ends the iteration
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            r->mean_post[0] = r->mean[0];
+            r->mean_post[1] = r->mean[1];
+            if (hmp) {
+                hmp[0] = r->mean[0];
+                hmp[1] = r->mean[1];
+            }
+        }
+        return;
+    }
+    const uint32_t n = (uint32_t)a.n;
+    const R *x0 = sv->cur ? a.x[1][0] : a.x[0][0], *x1 = sv->cur ? a.x[1][1] : a.x[0][1];
+    const uint32_t i0 = (blockIdx.x * (uint32_t)kBlock + threadIdx.x) * (uint32_t)kPfItems;
+    int32_t src[kPfItems];
+    load_idx4(a.anc, i0, n, src);
+    R sx = R(0), sy = R(0);
+#pragma unroll
+    for (int j = 0; j < kPfItems; ++j)
+        if (i0 + j < n) {
+            sx += __ldg(x0 + src[j]);
+            sy += __ldg(x1 + src[j]);
+        }
+    __shared__ R s_w[2][kBlock / 32];
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_w[0][warp] = sx;
+        s_w[1][warp] = sy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R bx = R(0), by = R(0);
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) {
+            bx += s_w[0][w];
+            by += s_w[1][w];
+        }
+        R *pp = reinterpret_cast<R *>(&a.part[blockIdx.x]);
+        pp[0] = bx;
+        pp[1] = by;
+    }
+    if (!last_arrival(&st->ticket, gridDim.x)) return;
+    // the last block: the block sums in a fixed order
+    const int nb = (int)gridDim.x;
+    if constexpr (sizeof(R) == 4) {
+        DF tx{0.0f, 0.0f}, ty{0.0f, 0.0f};
+        for (int b = threadIdx.x; b < nb; b += kBlock) {
+            const float *pp = reinterpret_cast<const float *>(&a.part[b]);
+            tx = df_add_f(tx, __ldcg(pp));
+            ty = df_add_f(ty, __ldcg(pp + 1));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tx = df_add(tx, df_shfl_xor(tx, o));
+            ty = df_add(ty, df_shfl_xor(ty, o));
+        }
+        __shared__ DF s_df[2][kBlock / 32];
+        if (lane == 0) {
+            s_df[0][warp] = tx;
+            s_df[1][warp] = ty;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DF X = s_df[0][0], Y = s_df[1][0];
+#pragma unroll
+            for (int w = 1; w < kBlock / 32; ++w) {
+                X = df_add(X, s_df[0][w]);
+                Y = df_add(Y, s_df[1][w]);
+            }
+            r->mean_post[0] = df_to_double(X) / (double)a.n;
+            r->mean_post[1] = df_to_double(Y) / (double)a.n;
+            if (hmp) {
+                hmp[0] = r->mean_post[0];
+                hmp[1] = r->mean_post[1];
+            }
+            st->ticket = 0;
+        }
+    } else {
+        double tx = 0.0, ty = 0.0;
+        for (int b = threadIdx.x; b < nb; b += kBlock) {
+            const double *pp = reinterpret_cast<const double *>(&a.part[b]);
+            tx += __ldcg(pp);
+            ty += __ldcg(pp + 1);
+        }
+        tx = warp_sum(tx);
+        ty = warp_sum(ty);
+        __shared__ double s_d[2][kBlock / 32];
+        if (lane == 0) {
+            s_d[0][warp] = tx;
+            s_d[1][warp] = ty;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double X = 0.0, Y = 0.0;
+#pragma unroll
+            for (int w = 0; w < kBlock / 32; ++w) {
+                X += s_d[0][w];
+                Y += s_d[1][w];
+            }
+            r->mean_post[0] = X / (double)a.n;
+            r->mean_post[1] = Y / (double)a.n;
+            if (hmp) {
+                hmp[0] = r->mean_post[0];
+                hmp[1] = r->mean_post[1];
+            }
+            st->ticket = 0;
+        }
+    }
+}
+
 }  // namespace smc

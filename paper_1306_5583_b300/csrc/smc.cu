@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -208,6 +209,21 @@ __global__ void reset_state_kernel(DevState *st) {
     for (int i = 0; i < 4; ++i) st->accept[i] = 0;
 }
 
+// Self-test of the bounded device waits: one block runs the grid barrier of
+// the cooperative kernels for a grid of two blocks, so the second arrival
+// never comes; the wait gives up after c_wait_limit polls and raises
+// SMC_E_TIMEOUT.  The barrier counters are cleared afterwards (as the last
+// departure of a real launch does).  Nothing else in the state changes.
+__global__ void wait_selftest_kernel(DevState *st) {
+    const bool ok = grid_barrier(st, 2u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->grid_count = 0;
+        st->grid_depart = 0;
+        if (ok) raise_error(st, SMC_E_STATE);  // cannot happen: nothing else arrives
+    }
+}
+
 // smc_iterate_host on a particle filter, first node of its graph: the
 // observation of iteration t + 1 from the mapped staging into the workspace
 // (and its float copy, rounded as on the host).  The move kernel, its
@@ -313,6 +329,17 @@ int launch_pf(smc_ctx *c) {
         return cuda_check(cudaLaunchKernelEx(&lc, pf_iterate_kernel<R>, a));
     }
     pf_iterate_kernel<R><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(a);
+    return cuda_check(cudaGetLastError());
+}
+
+// SMC_FLAG_POST_MEAN (particle filters): the post-resampling mean of the
+// iteration just resampled, into its record
+int launch_post_mean(smc_ctx *c) {
+    if (!(c->cfg.flags & SMC_FLAG_POST_MEAN) || c->cfg.model == SMC_MODEL_GMM) return SMC_OK;
+    if (c->cfg.precision == 32)
+        post_mean_kernel<float><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(pf_args<float>(c));
+    else
+        post_mean_kernel<double><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(pf_args<double>(c));
     return cuda_check(cudaGetLastError());
 }
 
@@ -567,6 +594,7 @@ int launch_iteration(smc_ctx *c) {
         if (!rc && c->ev_move[1])
             rc = cuda_check(cudaEventRecordWithFlags(c->ev_move[1], c->stream, cudaEventRecordExternal));
         if (!rc) rc = resample_any(c, 1);
+        if (!rc) rc = launch_post_mean(c);
     }
     return rc;
 }
@@ -743,6 +771,7 @@ int smc_initialize(smc_ctx *c) {
     }
     if (rc) return rc;
     rc = resample_any(c, 1);
+    if (!rc) rc = launch_post_mean(c);
     if (!rc) rc = record_after_resample(c);
     return rc;
 }
@@ -755,7 +784,8 @@ int smc_move(smc_ctx *c) {
 int smc_resample(smc_ctx *c, int force) {
     if (!c) return SMC_E_ARG;
     if (!c->initialized) return SMC_E_STATE;
-    const int rc = resample_any(c, force ? 0 : 1);
+    int rc = resample_any(c, force ? 0 : 1);
+    if (!rc) rc = launch_post_mean(c);
     return rc ? rc : record_after_resample(c);
 }
 
@@ -783,6 +813,7 @@ int smc_iterate(smc_ctx *c, int32_t n) {
     for (int32_t i = 0; i < n; ++i) {
         int rc = move_any(c);
         if (!rc) rc = resample_any(c, 1);
+        if (!rc) rc = launch_post_mean(c);
         if (!rc) rc = record_after_resample(c);
         if (!rc) rc = mcmc_any(c);
         if (rc) return rc;
@@ -879,7 +910,7 @@ int smc_state_dim(const smc_ctx *c, int32_t *d) {
 static int copy_out(smc_ctx *c, void *dst, const void *src, size_t bytes, int on_device) {
     if (!dst) return SMC_E_ARG;
     int rc = read_state(c);  // also surfaces device errors
-    if (rc != SMC_OK && rc != SMC_E_NONFINITE) return rc;
+    if (rc == SMC_E_CUDA) return rc;  // a device error word still lets the data be read
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     int rc2 = cuda_check(cudaMemcpyAsync(dst, src, bytes, k, c->stream));
     if (!rc2) rc2 = cuda_check(cudaStreamSynchronize(c->stream));
@@ -901,7 +932,7 @@ static int copy_rows(smc_ctx *c, void *dst, const void *src, int rows, bool to_c
 int smc_read_state(smc_ctx *c, void *dst, int on_device) {
     if (!c || !dst) return SMC_E_ARG;
     int rc = read_state(c);
-    if (rc != SMC_OK && rc != SMC_E_NONFINITE) return rc;
+    if (rc == SMC_E_CUDA) return rc;  // a device error word still lets the data be read
     const int rc2 = copy_rows(c, dst, c->x[c->host_st.cur & 1], c->L.d, true, on_device);
     return rc2 ? rc2 : rc;
 }
@@ -909,7 +940,7 @@ int smc_read_state(smc_ctx *c, void *dst, int on_device) {
 int smc_read_log_weight(smc_ctx *c, void *dst, int on_device) {
     if (!c) return SMC_E_ARG;
     int rc = read_state(c);
-    if (rc != SMC_OK && rc != SMC_E_NONFINITE) return rc;
+    if (rc == SMC_E_CUDA) return rc;  // a device error word still lets the data be read
     return copy_out(c, dst, c->lw[c->host_st.cur_lw & 1], (size_t)c->cfg.n_particles * c->L.rsize, on_device);
 }
 
@@ -927,7 +958,7 @@ int smc_read_cdf(smc_ctx *c, uint64_t *dst, int on_device) {
 int smc_read_history(smc_ctx *c, smc_record *h, int32_t count, int32_t *n_written) {
     if (!c || !h || count < 0) return SMC_E_ARG;
     int rc = read_state(c);
-    if (rc != SMC_OK && rc != SMC_E_NONFINITE) return rc;
+    if (rc == SMC_E_CUDA) return rc;  // a device error word still lets the data be read
     const int32_t last = c->host_st.t;
     const int32_t avail = (last < 0) ? 0 : std::min<int32_t>(last + 1, c->cfg.max_records);
     const int32_t m = std::min(count, avail);
@@ -1110,6 +1141,17 @@ int smc_set_move_events(smc_ctx *c, void *ev_before, void *ev_after) {
 int smc_sync(smc_ctx *c) {
     if (!c) return SMC_E_ARG;
     return read_state(c);
+}
+
+int smc_set_wait_limit(uint32_t polls) {
+    const uint32_t v = polls ? polls : kSpinLimit;
+    return cuda_check(cudaMemcpyToSymbol(c_wait_limit, &v, sizeof(v)));
+}
+
+int smc_wait_selftest(smc_ctx *c) {
+    if (!c) return SMC_E_ARG;
+    wait_selftest_kernel<<<1, kBlock, 0, c->stream>>>(c->st);
+    return cuda_check(cudaGetLastError());
 }
 
 const char *smc_error_string(int code) {
@@ -2013,23 +2055,28 @@ struct NoAllocScratch {
     DevState st;
     unsigned long long tsum[kNoAllocMaxTiles];
     int max_key;
+    int nan_seen;  // a NaN log-weight was read (the maximum alone would drop it)
 };
 // every GPU that loads the library holds this array (about 17 KB) until exit
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-NoAllocScratch *g_noalloc_ptr[64] = {};  // device address of the array, per device
+// device address of the array, per device: looked up once per device
+// (concurrent first calls from several host threads store the same value)
+std::atomic<NoAllocScratch *> g_noalloc_ptr[64];
 
 // one-time set-up on the current device: the array's device address (in
 // host code its name is only a host-side stand-in)
 int noalloc_scratch(NoAllocScratch **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SMC_E_CUDA;
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SMC_E_CUDA;
-        g_noalloc_ptr[dev] = static_cast<NoAllocScratch *>(p);
+    NoAllocScratch *p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void *q = nullptr;
+        if (cudaGetSymbolAddress(&q, g_noalloc_scratch) != cudaSuccess || !q) return SMC_E_CUDA;
+        p = static_cast<NoAllocScratch *>(q);
+        g_noalloc_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return SMC_OK;
 }
 
@@ -2040,7 +2087,8 @@ __device__ __forceinline__ int float_key(float f) {
 }
 __device__ __forceinline__ float key_float(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
 
-// clear the shared scratch for this call: state block and running maximum
+// clear the shared scratch for this call: state block, running maximum and
+// the NaN flag
 __global__ void noalloc_clear_kernel(NoAllocScratch *s, int32_t t) {
     DevState *st = &s->st;
     const int W = (int)(sizeof(DevState) / 4);
@@ -2050,22 +2098,30 @@ __global__ void noalloc_clear_kernel(NoAllocScratch *s, int32_t t) {
         st->t = t;
         st->due = 1;
         s->max_key = float_key(-INFINITY);
+        s->nan_seen = 0;
     }
 }
 
 __global__ void __launch_bounds__(kBlock) noalloc_max_kernel(const float *lw, int64_t n, NoAllocScratch *s) {
     float m = -INFINITY;
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
-        m = fmaxf(m, lw[i]);
+    bool nan = false;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
+        const float v = lw[i];
+        nan |= (v != v);
+        m = fmaxf(m, v);
+    }
     m = warp_maxf(m);
+    if (__any_sync(0xffffffffu, nan) && (threadIdx.x & 31) == 0) s->nan_seen = 1;
     if ((threadIdx.x & 31) == 0) atomicMax(&s->max_key, float_key(m));
 }
 
+// a NaN or a maximum that is not finite: the call fails like the context
+// API's weighting step (SMC_E_NONFINITE) and the later kernels write nothing
 __global__ void noalloc_set_max_kernel(NoAllocScratch *s) {
     const float m = key_float(s->max_key);
     s->st.max_lw = (double)m;
     s->st.max_lw_f = m;
-    if (!(m > -INFINITY) || !(m < INFINITY)) s->st.error = SMC_E_NONFINITE;
+    if (s->nan_seen || !(m > -INFINITY) || !(m < INFINITY)) s->st.error = SMC_E_NONFINITE;
 }
 
 }  // namespace
@@ -2102,4 +2158,17 @@ extern "C" int smc_resample_systematic_noalloc(const float *d_log_weight, int64_
         qg, tg, AncOut{d_ancestors}, NoSink{}, n, s->tsum, nullptr, st, 1,
         0);
     return cuda_check(cudaGetLastError());
+}
+
+extern "C" int smc_resample_noalloc_status(void *cuda_stream, int32_t *h_status) {
+    if (!h_status) return SMC_E_ARG;
+    NoAllocScratch *s = nullptr;
+    int rc = noalloc_scratch(&s);
+    if (rc) return rc;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    int32_t v = 0;
+    if ((rc = cuda_check(cudaMemcpyAsync(&v, &s->st.error, sizeof(v), cudaMemcpyDeviceToHost, stream)))) return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(stream)))) return rc;
+    *h_status = v;
+    return SMC_OK;
 }

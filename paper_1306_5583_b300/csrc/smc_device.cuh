@@ -260,6 +260,10 @@ __device__ __forceinline__ int bitlen128(U128 a) {
 // ---- bounded spin (never waits forever: sets the error word and gives up) --
 __device__ __forceinline__ void raise_error(DevState *st, int code) { atomicCAS(&st->error, 0, code); }
 
+// Polls a bounded wait makes before it gives up (kSpinLimit unless
+// smc_set_wait_limit changed it on this device).
+__constant__ uint32_t c_wait_limit = kSpinLimit;
+
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -273,7 +277,7 @@ __device__ __forceinline__ uint32_t atom_add_release_u32(uint32_t *p, uint32_t v
 
 // Barrier over the whole grid of a cooperative launch (every block resident
 // at once).  Thread 0 publishes the block's writes and counts its arrival,
-// then polls with acquire loads, at most kSpinLimit times; on timeout it
+// then polls with acquire loads, at most c_wait_limit times; on timeout it
 // raises SMC_E_TIMEOUT and the block gives up (returns false).  The k-th
 // barrier of a launch waits for k * gridDim.x arrivals (target); the counter
 // starts at zero and grid_depart() clears it at the end of the launch.
@@ -285,7 +289,7 @@ __device__ __forceinline__ bool grid_barrier(DevState *st, uint32_t target) {
         uint32_t it = 0;
         bool ok = true;
         while (ld_acquire_u32(&st->grid_count) < target) {
-            if (++it >= kSpinLimit) {
+            if (++it >= c_wait_limit) {
                 ok = false;
                 break;
             }

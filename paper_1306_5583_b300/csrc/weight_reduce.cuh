@@ -412,6 +412,7 @@ __device__ __forceinline__ bool finalize_weights(const FinalizeArgs &f, const Co
     r->ess = ess;
     r->mean[0] = c.Sa / c.S1;
     r->mean[1] = c.Sb / c.S1;
+    r->mean_post[0] = r->mean_post[1] = __longlong_as_double(0x7ff8000000000000ll);  // set by post_mean_kernel
     r->max_lw = c.M;
     r->t = f.t;
     r->resampled = due ? 1 : 0;
@@ -492,6 +493,7 @@ __device__ __forceinline__ bool finalize_weights_df(const FinalizeArgs &f, const
     } else if (ok) {
         r->mean[0] = df_to_double(df_div(c.S[2], S1));
         r->mean[1] = df_to_double(df_div(c.S[3], S1));
+        r->mean_post[0] = r->mean_post[1] = __longlong_as_double(0x7ff8000000000000ll);  // set by post_mean_kernel
     }
     return ok;
 }

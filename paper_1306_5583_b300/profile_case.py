@@ -1,6 +1,7 @@
 """Small, bounded workloads for kernel profiling (ncu captures of one kernel).
 
     python -m paper_1306_5583_b300.profile_case pf   --n 1048576 --iters 4 --threshold 1.0
+    python -m paper_1306_5583_b300.profile_case step --n 1048576 --iters 4 --threshold 1.0
     python -m paper_1306_5583_b300.profile_case gmm  --n 65536 --iters 3 --move rw
     python -m paper_1306_5583_b300.profile_case grad --n 262144 --iters 40
     python -m paper_1306_5583_b300.profile_case batch --count 64 --iters 20
@@ -28,6 +29,24 @@ def pf(a):
     for _ in range(a.iters):
         s.move()
         s.resample()
+    return s.log_evidence()
+
+
+def step(a):
+    """Replayed iterations (smc_iterate on a non-default stream): the
+    captured iteration graph the benchmark times."""
+    p = dict(workloads.CV_DEFAULT)
+    T = a.iters + 2
+    _, y = workloads.cv_data(T, seed=0, **p)
+    cfg = smc.make_config(model="cv", n=a.n, precision=32, scheme=a.scheme, threshold=a.threshold, seed=1,
+                          max_data=T, cv=p, keep_cdf=False)
+    stream = torch.cuda.Stream()
+    s = smc.Sampler(cfg, stream=stream)
+    s.set_data(y)
+    with torch.cuda.stream(stream):
+        s.initialize()
+        s.iterate(a.iters)
+        stream.synchronize()
     return s.log_evidence()
 
 
@@ -74,7 +93,7 @@ def batch(a):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["pf", "gmm", "grad", "batch"])
+    ap.add_argument("case", choices=["pf", "step", "gmm", "grad", "batch"])
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--iters", type=int, default=4)
     ap.add_argument("--threshold", type=float, default=1.0)
@@ -82,7 +101,7 @@ def main():
     ap.add_argument("--move", default="rw")
     ap.add_argument("--count", type=int, default=64)
     a = ap.parse_args()
-    v = {"pf": pf, "gmm": gmm, "grad": grad, "batch": batch}[a.case](a)
+    v = {"pf": pf, "step": step, "gmm": gmm, "grad": grad, "batch": batch}[a.case](a)
     torch.cuda.synchronize()
     print(f"{a.case} ok {v:.6f}")
 

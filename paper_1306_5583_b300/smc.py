@@ -46,13 +46,14 @@ class Record(ctypes.Structure):
                 ("mean", ctypes.c_double * 2), ("max_lw", ctypes.c_double), ("path_u", ctypes.c_double),
                 ("path_log_z", ctypes.c_double), ("alpha", ctypes.c_double), ("accept", ctypes.c_double * 3),
                 ("t", ctypes.c_int32), ("resampled", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("accept_mala", ctypes.c_double), ("pad2", ctypes.c_double)]
+                ("pad", ctypes.c_int32), ("accept_mala", ctypes.c_double), ("mean_post", ctypes.c_double * 2)]
 
     def as_dict(self):
         return dict(t=self.t, L=self.log_norm, logZ=self.log_evidence, ess=self.ess, mean_x=self.mean[0],
                     mean_y=self.mean[1], max_lw=self.max_lw, path_u=self.path_u, path_log_z=self.path_log_z,
                     alpha=self.alpha, accept=tuple(self.accept), accept_mala=self.accept_mala,
-                    resampled=bool(self.resampled), status=self.status)
+                    resampled=bool(self.resampled), status=self.status, post_mean_x=self.mean_post[0],
+                    post_mean_y=self.mean_post[1])
 
 
 _P = ctypes.c_void_p
@@ -93,6 +94,9 @@ _SIGS = {
     "smc_read_ancestor_history": (_I, [_P, ctypes.c_int32, _P, _I]),
     "smc_resample_systematic_noalloc": (_I, [_P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32,
                                              _P, _P]),
+    "smc_resample_noalloc_status": (_I, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "smc_set_wait_limit": (_I, [ctypes.c_uint32]),
+    "smc_wait_selftest": (_I, [_P]),
     "smc_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), _P, _P, ctypes.c_int32]),
     "smc_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Config), _P, _P, ctypes.c_int32, _P,
                               ctypes.c_size_t, _P]),
@@ -140,11 +144,12 @@ def check(code, where):
 
 FLAG_KEEP_CDF = 1
 FLAG_RECORD = 2
+FLAG_POST_MEAN = 4
 
 
 def make_config(model="cv", n=1024, precision=32, scheme="systematic", threshold=0.5, seed=0, stream_id=0,
                 max_records=None, max_data=1000, cv=None, gmm=None, keep_cdf=True, record=False,
-                checkpoint_every=16):
+                checkpoint_every=16, post_mean=False):
     c = Config()
     c.model = {"cv": MODEL_CV, "cv_gauss": MODEL_CV_GAUSS, "gmm": MODEL_GMM}[model]
     c.precision = precision
@@ -153,7 +158,8 @@ def make_config(model="cv", n=1024, precision=32, scheme="systematic", threshold
     c.threshold = float(threshold)
     c.seed = int(seed)
     c.stream_id = int(stream_id)
-    c.flags = (FLAG_KEEP_CDF if keep_cdf else 0) | (FLAG_RECORD if record else 0)
+    c.flags = ((FLAG_KEEP_CDF if keep_cdf else 0) | (FLAG_RECORD if record else 0)
+               | (FLAG_POST_MEAN if post_mean else 0))
     c.checkpoint_every = int(checkpoint_every)
     c.max_data = int(max_data)
     c.max_records = int(max_records if max_records is not None else max(2, max_data + 1))
@@ -250,6 +256,9 @@ class Sampler:
 
     def sync(self):
         check(lib().smc_sync(self.ctx), "smc_sync")
+
+    def wait_selftest(self):
+        check(lib().smc_wait_selftest(self.ctx), "smc_wait_selftest")
 
     def set_move_events(self, before=None, after=None):
         """Record two torch.cuda.Event objects (created with timing) around
@@ -370,6 +379,12 @@ class Sampler:
         """Continue from a checkpoint of a sampler with the same configuration."""
         buf = ctypes.create_string_buffer(bytes(blob), len(blob))
         check(lib().smc_restore(self.ctx, ctypes.cast(buf, _P), len(blob)), "smc_restore")
+
+
+def set_wait_limit(polls):
+    """Polls a bounded device wait makes before raising SMC_E_TIMEOUT on the
+    current device (0: the default, 2^24)."""
+    check(lib().smc_set_wait_limit(int(polls)), "smc_set_wait_limit")
 
 
 def philox4x32_10(ctr, key):

@@ -419,3 +419,66 @@ def test_move_events_in_the_graph_change_nothing():
         s.close()
     a0, a1 = outs
     assert np.array_equal(a0[0], a1[0]) and np.array_equal(a0[1], a1[1]) and a0[2] == a1[2]
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_post_resampling_mean_fp64_matches_oracle(scheme):
+    """SMC_FLAG_POST_MEAN: the record's post-resampling mean equals the
+    oracle's (mean of the selected copies after a resampling step, the
+    weighted mean otherwise), FP64, N = 1000, free-running."""
+    need_gpu()
+    n, T, seed = 1000, 30, 6
+    p = cv_params()
+    _, y = workloads.cv_data(T, seed=0, **p)
+    cfg = smc.make_config(model="cv", n=n, precision=64, scheme=scheme, threshold=0.5, seed=seed, max_data=T,
+                          cv=p, post_mean=True)
+    s = smc.Sampler(cfg)
+    s.set_data(y)
+    s.initialize()
+    s.iterate(T - 1)
+    recs = s.history(T)
+    ref, _ = ocv.run(y, n, seed, oracle_params(p), scheme=scheme, threshold=0.5)
+    assert any(o["resampled"] for o in ref) and not all(o["resampled"] for o in ref)
+    for r, o in zip(recs, ref):
+        assert r["resampled"] == o["resampled"]
+        assert abs(r["post_mean_x"] - o["post_mean_x"]) < 1e-9, (r["t"], r["post_mean_x"], o["post_mean_x"])
+        assert abs(r["post_mean_y"] - o["post_mean_y"]) < 1e-9
+    s.close()
+
+
+def test_post_resampling_mean_fp32_graph_and_host_call():
+    """FP32 through the replayed graph and through smc_iterate_host: the
+    post-resampling mean equals the mean of the GPU's own selected copies
+    (1e-5), and without the flag the field is NaN."""
+    need_gpu()
+    n, T = 50000, 8
+    p = cv_params()
+    _, y = workloads.cv_data(T, seed=1, **p)
+    stream = torch.cuda.Stream()
+    for host in (False, True):
+        cfg = smc.make_config(model="cv", n=n, precision=32, scheme="systematic", threshold=1.0, seed=2,
+                              max_data=T, cv=p, post_mean=True)
+        s = smc.Sampler(cfg, stream=stream)
+        s.set_data(y)
+        with torch.cuda.stream(stream):
+            s.initialize()
+            for t in range(1, T):
+                if host:
+                    rec = s.iterate_host(y[t]).as_dict()
+                else:
+                    s.iterate(1)
+                    rec = s.history(t + 1)[-1]
+                stream.synchronize()
+                x = s.state()
+                a = s.ancestors().astype(np.int64)
+                assert rec["resampled"]
+                assert abs(rec["post_mean_x"] - float(np.mean(x[0][a].astype(np.float64)))) < 1e-5
+                assert abs(rec["post_mean_y"] - float(np.mean(x[1][a].astype(np.float64)))) < 1e-5
+        s.close()
+    cfg = smc.make_config(model="cv", n=n, precision=32, scheme="systematic", threshold=1.0, seed=2, max_data=T,
+                          cv=p)
+    s = smc.Sampler(cfg)
+    s.set_data(y)
+    s.initialize()
+    s.iterate(2)
+    assert all(np.isnan(r["post_mean_x"]) for r in s.history(3))

@@ -91,3 +91,24 @@ def test_first_step_is_importance_sampling_from_the_prior():
     x = cv.init_state(500, 9, p)
     ll = cv.loglik(x, y0, p)
     assert abs(r.L - (np.log(np.mean(np.exp(ll - ll.max()))) + ll.max())) < 1e-12
+
+
+def test_post_resampling_mean_is_the_mean_of_the_copies():
+    """The post-resampling monitor: without resampling it is the weighted
+    mean; with it, the plain mean of the selected copies, whose expectation
+    over the resampling draws is the weighted mean (unbiased resampling)."""
+    import math as _m
+    from oracle import cv as _cv, resample as _rs
+    p = _cv.CVParams()
+    y = np.array([[0.3, -0.2], [0.5, 0.1]])
+    r = _cv.init_step(400, y[0], 3, p, 0.5)
+    assert _cv.post_resampling_mean(r, None) == (r.mean_x, r.mean_y)
+    a = _rs.resample("multinomial", r.lw, 3, 0)
+    mx, my = _cv.post_resampling_mean(r, a)
+    assert mx == float(np.mean(r.x[0][a])) and my == float(np.mean(r.x[1][a]))
+    vals = [_cv.post_resampling_mean(r, _rs.resample("multinomial", r.lw, 3, t))[0] for t in range(300)]
+    W = np.exp(r.lw - r.L)
+    sd = _m.sqrt(float(np.sum(W * (r.x[0] - r.mean_x) ** 2)) / 400)
+    assert abs(np.mean(vals) - r.mean_x) < 5 * sd / _m.sqrt(300)
+    recs, _ = _cv.run(np.array([[0.1, 0.0]] * 6), 300, 2, p, threshold=1.0)
+    assert all(rr["resampled"] for rr in recs)

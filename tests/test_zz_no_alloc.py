@@ -41,3 +41,34 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     lw = torch.zeros(16, dtype=torch.float32, device="cuda")
     out = torch.zeros(16, dtype=torch.int32, device="cuda")
     assert _noalloc(lw, n, 1, 0, out) == smc.E_ARG
+
+
+def _status():
+    v = ctypes.c_int32(-1)
+    assert smc.lib().smc_resample_noalloc_status(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                                  ctypes.byref(v)) == smc.OK
+    return v.value
+
+
+@pytest.mark.parametrize("bad", ["nan", "all_neg_inf"])
+def test_noalloc_reports_nonfinite_weights_and_writes_nothing(bad):
+    """A NaN log-weight (which a maximum alone would skip) or all weights
+    zero: the call writes no ancestor and its status word says
+    SMC_E_NONFINITE, as the context API's weighting step does; a good call
+    afterwards clears the status."""
+    need_gpu()
+    n = 5000
+    lw = torch.randn(n, dtype=torch.float32, device="cuda")
+    if bad == "nan":
+        lw[1234] = float("nan")
+    else:
+        lw.fill_(float("-inf"))
+    out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    assert _noalloc(lw, n, 3, 1, out) == smc.OK
+    assert _status() == smc.E_NONFINITE
+    assert bool((out == -1).all())
+    good = torch.randn(n, dtype=torch.float32, device="cuda")
+    assert _noalloc(good, n, 3, 1, out) == smc.OK
+    assert _status() == smc.OK
+    o = out.cpu().numpy()
+    assert o.min() >= 0 and np.all(np.diff(o) >= 0)
