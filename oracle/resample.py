@@ -33,6 +33,10 @@ CUDA path):
   selection on the r-CDF with R sorted iid uniforms; the final ancestors are
   the sorted expansion of the counts d_i + (residual draws of i).
 
+Residual variants (Douc et al. 2005): the R residual outputs drawn by
+systematic (one uniform) or stratified (one uniform per output) selection on
+the residual CDF instead of multinomially, targets P_k / D with D = R 2^25.
+
 Parity pins (tests/test_oracle_resample.py): sum of counts = N; exact
 unbiasedness E[o_i] = N q_i / Q_N by enumeration of all 2^24 systematic
 uniforms for tiny N; Monte Carlo unbiasedness (5 sigma) for stratified,
@@ -131,16 +135,27 @@ def residual_parts(q):
     return d, R, r, s
 
 
-def residual(q, seed, t, stream=0):
+def residual(q, seed, t, stream=0, step="multinomial"):
     """Residual resampling from the fixed-point weights q (not their CDF:
-    the deterministic part needs the individual q_i)."""
+    the deterministic part needs the individual q_i).  step: how the R
+    residual outputs are drawn on the residual weights -- "multinomial"
+    (R sorted iid uniforms), "systematic" (one uniform, targets (k + u) / R)
+    or "stratified" (targets (k + u_k) / R), the residual variants listed by
+    Douc et al. (2005)."""
     n = len(q)
     d, R, r, _ = residual_parts(q)
     counts = np.array(d, dtype=np.int64)
     if R > 0:
         RQ = cdf(r)
-        P, D = multinomial_targets(R, philox.resample_u24(seed, t, R, stream))
-        # multinomial_targets scales by its own count R: P = R (2 j + 1), D = R 2^25
+        if step == "multinomial":
+            P, D = multinomial_targets(R, philox.resample_u24(seed, t, R, stream))
+            # multinomial_targets scales by its own count R: P = R (2 j + 1), D = R 2^25
+        elif step == "systematic":
+            P, D = systematic_targets(R, philox.systematic_u24(seed, t, stream))
+        elif step == "stratified":
+            P, D = stratified_targets(R, philox.resample_u24(seed, t, R, stream))
+        else:
+            raise ValueError(step)
         extra = select(RQ, P, D)
         counts += np.bincount(extra, minlength=n)
     return expand(counts)
@@ -156,11 +171,15 @@ def offspring(a, n):
     return np.bincount(np.asarray(a, dtype=np.int64), minlength=n)
 
 
+RESIDUAL_STEPS = {"residual": "multinomial", "residual_systematic": "systematic",
+                  "residual_stratified": "stratified"}
+
+
 def resample(scheme, lw, seed, t, stream=0):
     """Ancestors for the named scheme from raw log-weights."""
     q = quantise(lw)
-    if scheme == "residual":
-        return residual(q, seed, t, stream)
+    if scheme in RESIDUAL_STEPS:
+        return residual(q, seed, t, stream, RESIDUAL_STEPS[scheme])
     Q = cdf(q)
     return {"systematic": systematic, "stratified": stratified,
             "multinomial": multinomial}[scheme](Q, seed, t, stream)
@@ -209,8 +228,8 @@ def plain_resample(scheme, lw, seed, t, stream=0):
     w = plain_weights(lw)
     n = w.shape[0]
     k = np.arange(n, dtype=np.float64)
-    if scheme == "residual":
-        return _plain_residual(w, seed, t, stream)
+    if scheme in RESIDUAL_STEPS:
+        return _plain_residual(w, seed, t, stream, RESIDUAL_STEPS[scheme])
     C = np.cumsum(w)
     CN = C[-1]
     if scheme == "systematic":
@@ -232,12 +251,48 @@ def plain_residual_parts(w):
     return d.astype(np.int64), int(n - d.sum()), nw - d
 
 
-def _plain_residual(w, seed, t, stream):
+def plain_residual_targets(R, seed, t, stream, step):
+    """Targets of the R residual outputs as fractions of the residual total."""
+    k = np.arange(R, dtype=np.float64)
+    if step == "multinomial":
+        return np.sort(_mid(philox.resample_u24(seed, t, R, stream)))
+    if step == "systematic":
+        return (k + _mid(philox.systematic_u24(seed, t, stream))) / R
+    if step == "stratified":
+        return (k + _mid(philox.resample_u24(seed, t, R, stream))) / R
+    raise ValueError(step)
+
+
+def _plain_residual(w, seed, t, stream, step="multinomial"):
     n = w.shape[0]
     d, R, r = plain_residual_parts(w)
     counts = d.copy()
     if R > 0:
         RC = np.cumsum(r)
-        U = RC[-1] * np.sort(_mid(philox.resample_u24(seed, t, R, stream)))
+        U = RC[-1] * plain_residual_targets(R, seed, t, stream, step)
         counts += np.bincount(plain_select(RC, U), minlength=n)
     return expand(counts)
+
+
+# ---- the in-place ("j stays j") ancestor permutation (Sec. 4.1.2) -------
+#
+# The sampler's copy(N, copy_from) lets a resampling step say, for every new
+# particle k, which old particle it copies.  Any arrangement of the ancestor
+# multiset is the same resampled system; the in-place arrangement keeps
+# every surviving particle in its own slot (copy_from[j] = j whenever
+# particle j has offspring), so an in-place copy touches only the slots of
+# particles without offspring.  Reading (the paper does not fix the order of
+# the other slots): the extra copies, in increasing order of parent, fill the
+# empty slots in increasing order.
+
+def stay_permutation(ancestors):
+    """copy_from with survivors in place, from any ancestor array."""
+    a = np.sort(np.asarray(ancestors, dtype=np.int64))
+    n = a.shape[0]
+    o = np.bincount(a, minlength=n)
+    out = np.arange(n, dtype=np.int64)
+    empty = np.flatnonzero(o == 0)
+    extras = np.repeat(np.arange(n, dtype=np.int64), np.maximum(o - 1, 0))
+    assert empty.shape == extras.shape
+    out[empty] = extras
+    return out

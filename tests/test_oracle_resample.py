@@ -139,3 +139,65 @@ def test_degenerate_single_particle_weight():
 def test_equal_weights_systematic_is_identity():
     a = resample.resample("systematic", np.zeros(37), 8, 2)
     assert np.array_equal(a, np.arange(37))
+
+
+RESIDUAL_VARIANTS = ["residual_systematic", "residual_stratified"]
+
+
+@pytest.mark.parametrize("scheme", RESIDUAL_VARIANTS)
+def test_residual_variants_keep_floor_copies_and_are_unbiased(scheme):
+    """Douc et al.'s residual variants: floor(N W_i) copies always, counts
+    sum to N, and E[R_i] = N W_i (Monte Carlo, 5 sigma)."""
+    n = 6
+    W = _W(LW6)
+    M = 6000
+    acc = np.zeros(n)
+    acc2 = np.zeros(n)
+    for t in range(M):
+        o = resample.offspring(resample.resample(scheme, LW6, seed=12, t=t), n)
+        assert o.sum() == n and np.all(o >= np.floor(n * W + 1e-12))
+        acc += o
+        acc2 += o * o
+    mean = acc / M
+    sd = np.sqrt(np.maximum(acc2 / M - mean ** 2, 1e-12) / M)
+    assert np.all(np.abs(mean - n * W) <= 5 * sd + 1e-3), (mean, n * W, sd)
+
+
+def test_residual_systematic_is_exactly_unbiased_on_a_uniform_grid():
+    """With one uniform for all R residual outputs, the counts averaged over
+    an evenly spaced grid of u equal N W_i up to the grid spacing, and each
+    residual count is within one of R r_i / sum r (systematic property)."""
+    n = 6
+    q = resample.quantise(LW6)
+    d, R, r, _ = resample.residual_parts(q)
+    RQ = resample.cdf(r)
+    W = _W(LW6)
+    G = 4096
+    acc = np.zeros(n)
+    rs = sum(r)
+    for gidx in range(G):
+        j = gidx * (1 << 24) // G + 313
+        P, D = resample.systematic_targets(R, j)
+        extra = resample.offspring(resample.select(RQ, P, D), n)
+        assert np.all(np.abs(extra - R * np.array(r, dtype=float) / rs) < 1.0 + 1e-9)
+        acc += np.array(d) + extra
+    assert np.max(np.abs(acc / G - n * W)) <= 2 * n / G
+
+
+def test_stay_permutation_by_hand_and_invariants():
+    """The in-place copy_from: a hand-worked case, then the invariants on
+    random ancestor sets (same multiset, survivors in their own slot, the
+    empty slots filled by the extra copies in increasing order)."""
+    a = np.array([0, 0, 0, 2, 3, 3])
+    # offspring 3, 0, 1, 2, 0, 0: slots 1, 4, 5 are empty; extras 0, 0, 3
+    assert resample.stay_permutation(a).tolist() == [0, 0, 2, 3, 0, 3]
+    g = np.random.default_rng(6)
+    for n in (1, 2, 9, 500):
+        for scheme in ("systematic", "multinomial", "residual"):
+            anc = resample.resample(scheme, g.normal(scale=2.0, size=n), 1, int(g.integers(100)))
+            p = resample.stay_permutation(anc)
+            assert np.array_equal(np.sort(p), anc)
+            o = resample.offspring(anc, n)
+            assert np.all(p[o > 0] == np.flatnonzero(o > 0))
+            assert np.all(np.diff(p[o == 0]) >= 0)
+    assert resample.stay_permutation(np.arange(7)).tolist() == list(range(7))

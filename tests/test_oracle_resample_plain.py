@@ -18,7 +18,7 @@ A target falls within delta of one of the N boundaries with probability
 about 2 delta N, so a vector of N outputs expects about 2 delta N^2
 mismatches: below 0.2 at N = 2^16 with the worst-case float64 term, far
 less with the typical one.  Over this test's 600 174 outputs per scheme the
-count is 0 for all four schemes; the test allows 2.
+count is 0 for all six schemes; the test allows 2.
 """
 import math
 
@@ -28,7 +28,7 @@ import pytest
 from oracle import philox
 from oracle import resample as R
 
-SCHEMES = ["systematic", "stratified", "multinomial", "residual"]
+SCHEMES = ["systematic", "stratified", "multinomial", "residual", "residual_systematic", "residual_stratified"]
 
 
 def _vectors():
@@ -91,8 +91,9 @@ def _check_plain(scheme, lw, seed, t):
     n = w.shape[0]
     assert a_pl.shape == (n,) and np.all(np.diff(a_pl) >= 0)
     assert not np.any(w[a_pl] == 0.0)
-    if scheme != "residual":
+    if scheme not in R.RESIDUAL_STEPS:
         return _mismatches_within(a_fp, a_pl, np.cumsum(w), _targets(scheme, n, seed, t), _delta(w)), 0
+    step = R.RESIDUAL_STEPS[scheme]
     # residual: the deterministic copies, then the multinomial residual draws
     q = R.quantise(lw)
     d_fp, R_fp, r_fp, s = R.residual_parts(q)
@@ -109,11 +110,15 @@ def _check_plain(scheme, lw, seed, t):
     if R_fp == 0:
         assert np.array_equal(a_fp, a_pl)
         return 0, 0
-    js = philox.resample_u24(seed, t, R_fp)
-    P, D = R.multinomial_targets(R_fp, js)
+    if step == "multinomial":
+        P, D = R.multinomial_targets(R_fp, philox.resample_u24(seed, t, R_fp))
+    elif step == "systematic":
+        P, D = R.systematic_targets(R_fp, philox.systematic_u24(seed, t))
+    else:
+        P, D = R.stratified_targets(R_fp, philox.resample_u24(seed, t, R_fp))
     x_fp = R.select(R.cdf(r_fp), P, D)
     RC = np.cumsum(r_pl)
-    p = np.sort((2 * np.asarray(js, dtype=np.float64) + 1) / 2.0 ** 25)
+    p = R.plain_residual_targets(R_fp, seed, t, 0, step)
     x_pl = R.plain_select(RC, RC[-1] * p)
     eps = elem + 2.0 ** s / QN
     delta_res = 2 * n * eps / max(RC[-1] - n * eps, 1e-300) + (n + 4) * 2.0 ** -52
@@ -159,11 +164,12 @@ def test_plain_definition_catches_a_shifted_target():
     assert np.array_equal(R.plain_select(C_eq, np.arange(8, dtype=np.float64)), np.arange(8))
 
 
-def test_plain_residual_keeps_floor_copies_and_sums_to_n():
+@pytest.mark.parametrize("scheme", ["residual", "residual_systematic", "residual_stratified"])
+def test_plain_residual_keeps_floor_copies_and_sums_to_n(scheme):
     g = np.random.default_rng(8)
     for n in (5, 97, 1000):
         lw = g.normal(scale=1.5, size=n)
-        a = R.plain_resample("residual", lw, 2, 7)
+        a = R.plain_resample(scheme, lw, 2, 7)
         w = R.plain_weights(lw)
         o = R.offspring(a, n)
         assert o.sum() == n
