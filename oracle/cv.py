@@ -147,9 +147,10 @@ def post_resampling_mean(r, ancestors):
     return float(np.mean(r.x[0][a])), float(np.mean(r.x[1][a]))
 
 
-def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, record_ancestors=False):
+def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, record_ancestors=False, inplace=False):
     """Whole filter over observations y (T, 2).  Returns per-iteration
-    records and the final state."""
+    records and the final state.  inplace: each step's ancestors in the
+    in-place copy_from arrangement (``resample.stay_permutation``)."""
     T = y.shape[0]
     recs = []
     r = init_step(n, y[0], seed, p, threshold, stream)
@@ -160,6 +161,8 @@ def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, record_ance
             r = step(r_prev.x, r_prev.lw, r_prev.L, anc, t, y[t], seed, p, threshold, stream)
         logZ += r.L
         anc = resample.resample(scheme, r.lw, seed, t, stream) if r.resample else None
+        if inplace and anc is not None:
+            anc = resample.stay_permutation(anc)
         post = post_resampling_mean(r, anc)
         rec = dict(t=t, L=r.L, logZ=logZ, ess=r.ess, mean_x=r.mean_x, mean_y=r.mean_y,
                    resampled=r.resample, post_mean_x=post[0], post_mean_y=post[1])

@@ -67,8 +67,9 @@ class GMMParams:
     shape0: int = 1
     rate0: float = 1.0
     T: int = 500
-    schedule: str = "prior"
+    schedule: str = "prior"     # "linear", "prior" ((t/T)^power) or "adaptive" (CESS = ess_target N)
     power: float = 5.0
+    ess_target: float = 0.5
 
 
 def alpha(t, p):
@@ -213,6 +214,51 @@ def reweight(lw_prev, L_prev, resampled_prev, llik, a_prev, a_t):
     return lw, L
 
 
+# ---- adaptive tempering (Sec. 5.2.3 annealing schemes; ESS of Sec. 2.1) --
+# Reading: the paper fixes alpha_t by a schedule; its adaptive variant here
+# picks alpha_t so that the effective sample size of the incremental weights
+# w_i = exp((alpha_t - alpha_{t-1}) l_i) under the current normalised weights
+# W_{t-1,i}, the conditional ESS
+#     CESS = N (sum_i W_i w_i)^2 / sum_i W_i w_i^2,
+# equals rho N (CESS = N at alpha_t = alpha_{t-1}; the plain ESS of the
+# product weights would already be below target when W_{t-1} is uneven).
+# alpha_t = 1 when CESS at alpha = 1 is at least rho N; otherwise bisection on
+# delta = alpha_t - alpha_{t-1} in [0, 1 - alpha_{t-1}] for a fixed number
+# of halvings, keeping the lower end (CESS >= rho N there).
+
+ADAPT_STEPS = 40
+
+
+def log_cess(logW, llik, delta):
+    """log CESS(delta) for normalised log-weights logW (float64)."""
+    n = logW.shape[0]
+    x = logW + delta * llik
+    y = logW + 2.0 * delta * llik
+    mx, my = float(np.max(x)), float(np.max(y))
+    a = mx + math.log(float(np.sum(np.exp(x - mx))))
+    b = my + math.log(float(np.sum(np.exp(y - my))))
+    return math.log(n) + 2.0 * a - b
+
+
+def adaptive_alpha(logW, llik, a_prev, rho, steps=ADAPT_STEPS):
+    """alpha_t of the CESS-targeted schedule."""
+    n = logW.shape[0]
+    target = math.log(rho * n)
+    hi = 1.0 - a_prev
+    if hi <= 0.0:
+        return 1.0
+    if log_cess(logW, llik, hi) >= target:
+        return 1.0
+    lo = 0.0
+    for _ in range(steps):
+        mid = 0.5 * (lo + hi)
+        if log_cess(logW, llik, mid) >= target:
+            lo = mid
+        else:
+            hi = mid
+    return min(1.0, a_prev + lo)
+
+
 def path_u(lw, L, resampled, llik):
     n = llik.shape[0]
     if resampled:
@@ -223,7 +269,10 @@ def path_u(lw, L, resampled, llik):
 def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, keep=False, move="rw", eps=0.05):
     """Whole sampler.  Returns (log Z standard, log Z path sampling, records).
     move: "rw" (the three random-walk blocks), "mala" (one Langevin move) or
-    "rw_mala" (the blocks, then one Langevin move)."""
+    "rw_mala" (the blocks, then one Langevin move).  With p.schedule
+    "adaptive", alpha_t comes from adaptive_alpha with rho = p.ess_target and
+    p.T is the most iterations run; iterations after alpha reaches 1 only
+    move (their increment is zero)."""
     s = init_state(n, y, seed, p, stream)
     lw = np.full(n, -math.log(n))
     L = 0.0
@@ -233,7 +282,11 @@ def run(y, n, seed, p, scheme="systematic", threshold=0.5, stream=0, keep=False,
     logz_ds, logz_ps = 0.0, 0.0
     recs = []
     for t in range(1, p.T + 1):
-        a_t = alpha(t, p)
+        if p.schedule == "adaptive":
+            logW = weights.previous_log_weight(lw, L, resampled, n)
+            a_t = adaptive_alpha(logW, s.llik, a_prev, p.ess_target)
+        else:
+            a_t = alpha(t, p)
         lw, L = reweight(lw, L, resampled, s.llik, a_prev, a_t)
         W = np.exp(lw - L)
         e = 1.0 / float(np.sum(W * W))

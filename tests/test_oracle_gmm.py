@@ -183,3 +183,52 @@ def test_mala_leaves_the_prior_invariant():
     assert stats.kstest(s.mu[0], stats.norm(0, 10).cdf).pvalue > 1e-4
     assert stats.kstest(s.lam[1], stats.expon().cdf).pvalue > 1e-4
     assert stats.kstest(s.om[2], stats.beta(1, 2).cdf).pvalue > 1e-4
+
+
+def test_adaptive_alpha_two_point_closed_form():
+    """Uniform W and l_i in {0, -c} (half each): CESS(delta) =
+    N (1 + u)^2 / (2 (1 + u^2)) with u = exp(-c delta), so CESS = rho N at
+    u = ((1 - 2 rho) root of (1 - 2 rho) u^2 + 2 u + (1 - 2 rho) = 0); the
+    bisection lands on that delta, CESS(0) = N, and a constant likelihood
+    (CESS = N for every delta) jumps straight to alpha = 1."""
+    n, c = 1000, 37.0
+    logW = np.full(n, -math.log(n))
+    ll = np.where(np.arange(n) % 2 == 0, 0.0, -c)
+    assert abs(gmm.log_cess(logW, ll, 0.0) - math.log(n)) < 1e-12
+    for rho in (0.75, 0.9, 0.6):
+        A = 1 - 2 * rho
+        u = (-2 + math.sqrt(4 - 4 * A * A)) / (2 * A)   # the root in (0, 1)
+        delta = -math.log(u) / c
+        a_prev = 0.125
+        a = gmm.adaptive_alpha(logW, ll, a_prev, rho)
+        assert abs((a - a_prev) - delta) < 1e-9, (rho, a - a_prev, delta)
+        assert abs(gmm.log_cess(logW, ll, a - a_prev) - math.log(rho * n)) < 1e-8
+    assert gmm.adaptive_alpha(logW, np.full(n, -3.0), 0.25, 0.5) == 1.0
+    assert gmm.adaptive_alpha(logW, ll, 1.0, 0.5) == 1.0
+
+
+def test_adaptive_schedule_r1_evidence_against_quadrature():
+    """The CESS-targeted schedule as a whole: alpha increases to 1 within
+    the iteration cap, the standard estimate matches the r = 1 quadrature
+    value (the same bar as the fixed schedule), and the path-sampling
+    estimate, whose trapezoid rule is biased on a coarse alpha grid,
+    approaches it as the CESS target (and so the number of steps) grows."""
+    g = np.random.default_rng(4)
+    y = 1.0 + g.standard_normal(20)
+    truth = _r1_log_evidence(y, gmm.GMMParams(r=1))
+    ds, ps_err, steps = [], {}, {}
+    for rho in (0.8, 0.99):
+        p = gmm.GMMParams(r=1, T=400, schedule="adaptive", ess_target=rho)
+        errs = []
+        for seed in range(3 if rho == 0.8 else 1):
+            a, b, recs = gmm.run(y, 2000, seed, p)
+            al = [r.alpha for r in recs]
+            assert all(x2 >= x1 for x1, x2 in zip(al, al[1:])) and al[-1] == 1.0
+            steps[rho] = sum(1 for x in al if x < 1.0)
+            if rho == 0.8:
+                ds.append(a)
+            errs.append(abs(b - truth))
+        ps_err[rho] = float(np.mean(errs))
+    assert abs(np.mean(ds) - truth) < 0.05, (np.mean(ds), truth)
+    assert steps[0.8] < steps[0.99] < 400
+    assert ps_err[0.99] < 0.15 and ps_err[0.99] < ps_err[0.8], ps_err
