@@ -869,4 +869,202 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     }
 }
 
+// ---- adaptive tempering (SMC_ALPHA_ADAPTIVE) ---------------------------------
+// alpha_t such that the conditional ESS of the incremental weights
+// w_i = exp(delta l_i), delta = alpha_t - alpha_{t-1}, under the current
+// normalised weights W_i,
+//     CESS(delta) = N (sum_i W_i w_i)^2 / sum_i W_i w_i^2   (Sec. 2.1 ESS),
+// equals rho N (the annealing schemes of Sec. 5.2.3 made adaptive):
+// alpha_t = 1 when CESS(1 - alpha_{t-1}) >= rho N, else kAdaptSteps halvings
+// of [0, 1 - alpha_{t-1}] keeping the lower end.  One cooperative wave; each
+// block keeps its particles' (log W_i, l_i), and every evaluation is a block
+// partial (max and sum of exp for x = log W + delta l and y = log W +
+// 2 delta l), a grid barrier, and the same fixed-order combine in every
+// block, so that every block takes the same decision and the midpoints are
+// float64 values computed identically everywhere.
+constexpr int kAdaptSteps = 40;
+
+template <typename R>
+struct AlphaPartial {  // one per block and evaluation
+    R mx, sx, my, sy;
+};
+
+// log CESS - log(rho N) >= 0 from the block partials, by one warp (lane 0
+// receives the answer): float64 on the FP64 path, double-float sums and
+// logarithms on the FP32 path (no float64 arithmetic there).
+template <typename R>
+__device__ __forceinline__ bool alpha_cess_ge(const AlphaPartial<R> *part, int G, double log_n, double log_target) {
+    const int lane = threadIdx.x & 31;
+    R MX = Math<R>::neg_inf(), MY = Math<R>::neg_inf();
+    for (int q = lane; q < G; q += 32) {
+        MX = fmax(MX, __ldcg(&part[q].mx));
+        MY = fmax(MY, __ldcg(&part[q].my));
+    }
+    MX = warp_max(MX);
+    MY = warp_max(MY);
+    if constexpr (sizeof(R) == 8) {
+        double ax = 0.0, ay = 0.0;
+        for (int q = lane; q < G; q += 32) {
+            const double pmx = __ldcg(&part[q].mx), pmy = __ldcg(&part[q].my);
+            if (pmx > -INFINITY) ax += __ldcg(&part[q].sx) * exp(pmx - MX);
+            if (pmy > -INFINITY) ay += __ldcg(&part[q].sy) * exp(pmy - MY);
+        }
+        ax = warp_sum(ax);
+        ay = warp_sum(ay);
+        if (!(ax > 0.0) || !(ay > 0.0)) return false;
+        return 2.0 * (MX + log(ax)) - (MY + log(ay)) + log_n >= log_target;
+    } else {
+        DF ax{0.0f, 0.0f}, ay{0.0f, 0.0f};
+        for (int q = lane; q < G; q += 32) {
+            const float pmx = __ldcg(&part[q].mx), pmy = __ldcg(&part[q].my);
+            if (pmx > -INFINITY) ax = df_add(ax, two_prod(__ldcg(&part[q].sx), __expf(pmx - MX)));
+            if (pmy > -INFINITY) ay = df_add(ay, two_prod(__ldcg(&part[q].sy), __expf(pmy - MY)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ax = df_add(ax, df_shfl_xor(ax, o));
+            ay = df_add(ay, df_shfl_xor(ay, o));
+        }
+        if (!(ax.hi > 0.0f) || !(ay.hi > 0.0f)) return false;
+        // 2 (MX + log A) - (MY + log B) + log N - log(rho N), in double-float
+        DF v = df_add(df_add_f(df_add(df_log(ax), df_log(ax)), 2.0f * MX), DF{-MY, 0.0f});
+        const DF lb = df_log(ay);
+        v = df_add(v, DF{-lb.hi, -lb.lo});
+        const float ln_hi = float(log_n - log_target);
+        const float ln_lo = float((log_n - log_target) - double(ln_hi));
+        v = df_add(v, DF{ln_hi, ln_lo});
+        return v.hi >= 0.0f;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock, 4) gmm_alpha_kernel(GmmArgs<R> a, int32_t ll_row, double log_target,
+                                                              double *alpha_out) {
+    DevState *st = a.st;
+    const DevState *sv = snapshot(st, true);
+    if (sv->error) return;
+    const int32_t t = sv->t + 1;
+    const double a_prev = a.alpha[t - 1];
+    const int G = gridDim.x, b = blockIdx.x;
+    const int64_t i_lo = a.n * b / G, i_hi = a.n * (b + 1) / G;
+    const int cur = sv->cur, cur_lw = sv->cur_lw;
+    const R *lw_in = a.lw[cur_lw];
+    const R *ll = a.x[cur] + (int64_t)ll_row * a.ld;
+    __shared__ R s_k[2];
+    if (threadIdx.x == 0) {  // the reweighting kernel's split of the running shift
+        s_k[0] = R(sv->base_shift);
+        s_k[1] = R(sv->base_shift - double(s_k[0]));
+    }
+    __syncthreads();
+    const Shift<R> base(s_k[0], s_k[1]);
+    // the thread's first kMax particles kept in registers, the rest read
+    // again at every evaluation
+    constexpr int kMax = 4;
+    R lwk[kMax], llk[kMax];
+#pragma unroll
+    for (int j = 0; j < kMax; ++j) {
+        const int64_t i = i_lo + threadIdx.x + (int64_t)j * kBlock;
+        lwk[j] = (i < i_hi) ? base.sub_from(lw_in[i]) : Math<R>::neg_inf();
+        llk[j] = (i < i_hi) ? ll[i] : R(0);
+    }
+    const int64_t i_rest = i_lo + threadIdx.x + (int64_t)kMax * kBlock;
+    AlphaPartial<R> *part = reinterpret_cast<AlphaPartial<R> *>(a.part);
+    __shared__ R s_red[4][kBlock / 32];
+    __shared__ int s_ge;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double log_n = log(double(a.n));
+    double lo = 0.0, hi = 1.0 - a_prev, delta = 0.0;
+    bool done = !(hi > 0.0);
+    uint32_t barriers = 0;
+    for (int step = -1; step < kAdaptSteps && !done; ++step) {
+        const double d = (step < 0) ? hi : 0.5 * (lo + hi);
+        const R dr = R(d), d2 = R(2.0 * d);
+        // block partial: maxima, then sums of exp relative to them
+        R mx = Math<R>::neg_inf(), my = Math<R>::neg_inf();
+#pragma unroll
+        for (int j = 0; j < kMax; ++j) {
+            mx = fmax(mx, lwk[j] + dr * llk[j]);
+            my = fmax(my, lwk[j] + d2 * llk[j]);
+        }
+        for (int64_t i = i_rest; i < i_hi; i += kBlock) {
+            const R w = base.sub_from(lw_in[i]), l = ll[i];
+            mx = fmax(mx, w + dr * l);
+            my = fmax(my, w + d2 * l);
+        }
+        mx = warp_max(mx);
+        my = warp_max(my);
+        if (lane == 0) {
+            s_red[0][warp] = mx;
+            s_red[1][warp] = my;
+        }
+        __syncthreads();
+        mx = s_red[0][0];
+        my = s_red[1][0];
+#pragma unroll
+        for (int w = 1; w < kBlock / 32; ++w) {
+            mx = fmax(mx, s_red[0][w]);
+            my = fmax(my, s_red[1][w]);
+        }
+        R sx = R(0), sy = R(0);
+        if (mx > Math<R>::neg_inf()) {
+#pragma unroll
+            for (int j = 0; j < kMax; ++j)
+                if (lwk[j] > Math<R>::neg_inf()) {
+                    sx += Math<R>::fast_exp(lwk[j] + dr * llk[j] - mx);
+                    sy += Math<R>::fast_exp(lwk[j] + d2 * llk[j] - my);
+                }
+            for (int64_t i = i_rest; i < i_hi; i += kBlock) {
+                const R w = base.sub_from(lw_in[i]), l = ll[i];
+                if (w > Math<R>::neg_inf()) {
+                    sx += Math<R>::fast_exp(w + dr * l - mx);
+                    sy += Math<R>::fast_exp(w + d2 * l - my);
+                }
+            }
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) {
+            s_red[2][warp] = sx;
+            s_red[3][warp] = sy;
+        }
+        __syncthreads();
+        // partials of consecutive evaluations alternate between two halves:
+        // a block writing evaluation e + 2 has passed the barrier of e + 1,
+        // which every block reaches only after reading the partials of e
+        AlphaPartial<R> *pe = part + (size_t)(barriers & 1u) * (size_t)G;
+        if (threadIdx.x == 0) {
+            R tx = R(0), ty = R(0);
+#pragma unroll
+            for (int w = 0; w < kBlock / 32; ++w) {
+                tx += s_red[2][w];
+                ty += s_red[3][w];
+            }
+            pe[b] = AlphaPartial<R>{mx, tx, my, ty};
+        }
+        ++barriers;
+        if (!grid_barrier(st, barriers * (uint32_t)G)) return;
+        // every block: the same combine in the same order
+        if (warp == 0) {
+            const bool ge = alpha_cess_ge<R>(pe, G, log_n, log_target);
+            if (lane == 0) s_ge = ge ? 1 : 0;
+        }
+        __syncthreads();
+        const bool ge = s_ge != 0;
+        if (step < 0) {
+            if (ge) {
+                delta = hi;
+                done = true;
+            }
+        } else if (ge) {
+            lo = d;
+        } else {
+            hi = d;
+        }
+        __syncthreads();  // s_red and s_ge are reused by the next evaluation
+    }
+    if (!done) delta = lo;
+    if (b == 0 && threadIdx.x == 0) alpha_out[t] = fmin(1.0, a_prev + delta);
+    if (barriers) grid_depart(st);
+}
+
 }  // namespace smc

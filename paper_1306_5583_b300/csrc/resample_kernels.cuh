@@ -1045,6 +1045,160 @@ __global__ void __launch_bounds__(kBlock, 4) grid_multinomial_kernel(QGen<R> gen
     grid_depart(st);
 }
 
+// ------------------------------------- in-place ("j stays j") ancestors --
+//
+// The copy(N, copy_from) convention of Sec. 4.1.2 lets copy_from[k] name the
+// parent of new particle k in any arrangement of the ancestor multiset.  The
+// in-place arrangement keeps every particle with offspring in its own slot
+// (copy_from[j] = j) and fills the slots of particles without offspring with
+// the extra copies, both in increasing order, so that a gather reads almost
+// only its own slot.  From the sorted ancestors a_k: output k is a first copy
+// when k = 0 or a_k != a_{k-1}; the extra copies in increasing k are the
+// extras in increasing parent order; with F_k the first copies up to k and
+// S_j the survivors below slot j,
+//     extra[k - F_k] = a_k (k not a first copy),   surv[a_k] = 1 (first copy),
+//     copy_from[j] = j if surv[j], else extra[j - S_j].
+// One cooperative wave over tiles of kScanTile outputs, three grid barriers.
+
+// Exclusive block scan of one count per thread; *total receives the sum.
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t s_w[kBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    uint32_t pre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) {
+        if (w < warp) pre += s_w[w];
+        tot += s_w[w];
+    }
+    *total = tot;
+    return pre + inc - v;
+}
+
+struct InplaceArgs {
+    int32_t *anc;
+    int32_t *extra;   // [N] extra copies in order
+    int32_t *surv;    // [N] 1 where the particle has offspring
+    unsigned long long *tf, *ts;  // per-tile counts of first copies and of survivors
+    unsigned long long *bf, *bs;  // per-block counts
+};
+
+__global__ void __launch_bounds__(kBlock, 4) inplace_kernel(InplaceArgs ia, int64_t n, DevState *st) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const DevState *sv = snapshot(st, true);
+    if (sv->error || !sv->ready) return;  // nothing was resampled
+    const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+    const int G = gridDim.x, b = blockIdx.x;
+    const int t_lo = (int)((int64_t)ntiles * b / G), t_hi = (int)((int64_t)ntiles * (b + 1) / G);
+    const int base = threadIdx.x * kScanItems;
+    // phase 1: first copies per tile; the survivor flags of the tile cleared
+    unsigned long long bf = 0;
+    for (int tile = t_lo; tile < t_hi; ++tile) {
+        const int64_t k0 = (int64_t)tile * kScanTile + base;
+        uint32_t f = 0;
+        int32_t prev = (k0 > 0 && k0 - 1 < n) ? __ldcg(ia.anc + k0 - 1) : -1;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const int64_t k = k0 + j;
+            if (k < n) {
+                const int32_t a = __ldcg(ia.anc + k);
+                f += (a != prev) ? 1u : 0u;
+                prev = a;
+                ia.surv[k] = 0;
+            }
+        }
+        uint32_t tot;
+        block_excl_scan_u32(f, &tot);
+        if (threadIdx.x == 0) ia.tf[tile] = tot;
+        bf += tot;
+    }
+    if (threadIdx.x == 0) ia.bf[b] = bf;
+    if (!grid_barrier(st, G)) return;
+    // phase 2: extras to their rank, survivor flags
+    unsigned long long pre, total;
+    tile_prefix_total(ia.bf, b, G, &pre, &total);
+    for (int tile = t_lo; tile < t_hi; ++tile) {
+        const int64_t k0 = (int64_t)tile * kScanTile + base;
+        int32_t a[kScanItems];
+        bool first[kScanItems];
+        uint32_t f = 0;
+        int32_t prev = (k0 > 0 && k0 - 1 < n) ? __ldcg(ia.anc + k0 - 1) : -1;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const int64_t k = k0 + j;
+            a[j] = (k < n) ? __ldcg(ia.anc + k) : -1;
+            first[j] = (k < n) && (a[j] != prev);
+            f += first[j] ? 1u : 0u;
+            prev = a[j];
+        }
+        uint32_t tot;
+        unsigned long long F = pre + block_excl_scan_u32(f, &tot);  // first copies before the thread's items
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const int64_t k = k0 + j;
+            if (k >= n) break;
+            if (first[j]) {
+                ++F;
+                ia.surv[a[j]] = 1;
+            } else {
+                ia.extra[k - (int64_t)F] = a[j];
+            }
+        }
+        pre += tot;
+    }
+    if (!grid_barrier(st, 2 * G)) return;
+    // phase 3: survivors per tile
+    unsigned long long bs = 0;
+    for (int tile = t_lo; tile < t_hi; ++tile) {
+        const int64_t j0 = (int64_t)tile * kScanTile + base;
+        uint32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j)
+            if (j0 + j < n) c += (uint32_t)__ldcg(ia.surv + j0 + j);
+        uint32_t tot;
+        block_excl_scan_u32(c, &tot);
+        if (threadIdx.x == 0) ia.ts[tile] = tot;
+        bs += tot;
+    }
+    if (threadIdx.x == 0) ia.bs[b] = bs;
+    if (!grid_barrier(st, 3 * G)) return;
+    // phase 4: the arrangement
+    tile_prefix_total(ia.bs, b, G, &pre, &total);
+    for (int tile = t_lo; tile < t_hi; ++tile) {
+        const int64_t j0 = (int64_t)tile * kScanTile + base;
+        int32_t sv8[kScanItems];
+        uint32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            sv8[j] = (j0 + j < n) ? __ldcg(ia.surv + j0 + j) : 0;
+            c += (uint32_t)sv8[j];
+        }
+        uint32_t tot;
+        unsigned long long S = pre + block_excl_scan_u32(c, &tot);  // survivors before the thread's slots
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const int64_t jj = j0 + j;
+            if (jj >= n) break;
+            if (sv8[j]) {
+                ia.anc[jj] = (int32_t)jj;
+                ++S;
+            } else {
+                ia.anc[jj] = __ldcg(ia.extra + (jj - (int64_t)S));
+            }
+        }
+        pre += tot;
+    }
+    grid_depart(st);
+}
+
 // ------------------------------------------------- residual, one pass --
 //
 // Residual resampling (deterministic copies d_i = floor(N q_i / Q_N), then
@@ -1125,6 +1279,37 @@ __device__ __forceinline__ void residual_tile_scans(TileBufs &tb, unsigned long 
     scan_items_q(r, tb);
 }
 
+// The residual count map of the systematic and stratified residual steps:
+// O = K_R(RQ) from the closed form over the R residual outputs, plus the
+// deterministic copies up to the boundary (d0 before the tile, dl[j] the
+// tile-relative inclusive prefix of the entries the thread maps).  The
+// entries are taken into registers before the selection: the stratified
+// selection stages its draw table in the buffer that held them.
+struct DPrefixMap {
+    static constexpr bool kActive = true;
+    int64_t d0;
+    int32_t dl[kScanItems];
+    // from the d scan (pad32 layout); the caller synchronises the block
+    // before anything overwrites dloc
+    __device__ __forceinline__ void load(const int32_t *dloc) {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) dl[j] = dloc[pad32((int)threadIdx.x + j * kBlock)];
+    }
+    __device__ __forceinline__ void map_block(int32_t *K, int64_t *k0) const {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) K[pad32((int)threadIdx.x + j * kBlock)] += (int32_t)(d0 + dl[j]);
+        if (threadIdx.x == 0) *k0 += d0;
+    }
+};
+
+// Residual steps: the R residual outputs drawn multinomially (a histogram
+// of R iid draws, as for multinomial resampling), systematically (one
+// uniform, targets (k + u) / R) or stratified (targets (k + u_k) / R).
+constexpr int kResMultinomial = 0, kResSystematic = 1, kResStratified = 2;
+
+template <int kMode>
+using ResidualTargets = GridTargets<kMode == kResStratified>;
+
 // One-pass residual resampling: a cooperative launch of one full wave.
 // Phase 1: histogram share cleared, q tile sums (a block with one tile keeps
 // its q scan until phase 3); barrier; phase 2: Q_N, d sums (a block with one
@@ -1132,11 +1317,14 @@ __device__ __forceinline__ void residual_tile_scans(TileBufs &tb, unsigned long 
 // s, the R draws into the histogram, r sums (a kept tile gets its d and r
 // scans); barrier; phase 4: the bucket records of the block's histogram
 // tiles, its r prefix and targets; barrier; phase 5: selection.  Blocks with
-// several tiles rescan the q of every tile in every phase.
-template <typename R, class Sink>
-__global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, GridTargets<false> tgt, AncOut out,
+// several tiles rescan the q of every tile in every phase.  The systematic
+// and stratified residual steps use no histogram: their targets are the
+// closed form over R outputs (set up on the device once R is known).
+template <typename R, class Sink, int kMode = kResMultinomial>
+__global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, ResidualTargets<kMode> tgt, AncOut out,
                                                                Sink sink, int64_t n, ResidualSums rs, HistArgs h,
                                                                DevState *st, int gate) {
+    constexpr bool kHist = (kMode == kResMultinomial);
     __shared__ TileBufs tb;
     asm volatile("griddepcontrol.wait;" ::: "memory");  // as in grid_resample_kernel
     const DevState *sv = snapshot(st, true);
@@ -1145,7 +1333,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
     g.prepare(sv);
     const int G = gridDim.x, b = blockIdx.x;
     const unsigned long long N = (unsigned long long)n;
-    {
+    if constexpr (kHist) {
         uint4 *h4 = reinterpret_cast<uint4 *>(h.hist);
         const int64_t z_hi = kHistBuckets * (b + 1) / G;
         for (int64_t i = kHistBuckets * b / G + threadIdx.x; i < z_hi; i += kBlock) h4[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -1190,7 +1378,7 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
     tile_prefix_total(rs.bd, b, G, &pre_d, &Dtot);
     const unsigned long long Rn = Dtot < N ? N - Dtot : 0ull;
     const int shift = max(0, bitlen128(mul64(Rn, QN)) - 62);
-    hist_draws(tgt.key, tgt.stream, (uint32_t)sv->t, (int64_t)Rn, h.hist, b, G);
+    if constexpr (kHist) hist_draws(tgt.key, tgt.stream, (uint32_t)sv->t, (int64_t)Rn, h.hist, b, G);
     unsigned long long br = 0;
     for (int tile = t_lo; tile < t_hi; ++tile) {
         unsigned long long sr;
@@ -1212,32 +1400,59 @@ __global__ void __launch_bounds__(kBlock, 4) grid_residual_kernel(QGen<R> gen, G
     if (threadIdx.x == 0) rs.br[b] = br;
     if (!grid_barrier(st, 3 * G)) return out.report(st);
     // phase 4: histogram tiles; the r prefix and the targets on RQ_N
-    const int h_lo = (int)((int64_t)kHistTiles * b / G), h_hi = (int)((int64_t)kHistTiles * (b + 1) / G);
-    for (int ht = h_lo; ht < h_hi; ++ht) hist_scan_tile(reinterpret_cast<const uint4 *>(h.hist), h.hrec, h.htot, ht);
+    if constexpr (kHist) {
+        const int h_lo = (int)((int64_t)kHistTiles * b / G), h_hi = (int)((int64_t)kHistTiles * (b + 1) / G);
+        for (int ht = h_lo; ht < h_hi; ++ht)
+            hist_scan_tile(reinterpret_cast<const uint4 *>(h.hist), h.hrec, h.htot, ht);
+    }
     unsigned long long pre_r, RQN;
     tile_prefix_total(rs.br, b, G, &pre_r, &RQN);
     // RQ_N = 0 exactly when R = 0: any positive total then gives v = 0 and H = 0
-    const GridTargets<false> tg = block_targets(tgt, sv, RQN ? RQN : 1ull);
-    if (!grid_barrier(st, 4 * G)) return out.report(st);
+    // (and for the closed form over R = 0 outputs, K = 0 everywhere)
+    ResidualTargets<kMode> proto = tgt;
+    if constexpr (!kHist) {
+        proto.n = (int64_t)Rn;
+        proto.mrec = Rn ? ~0ull / Rn : 0ull;
+    }
+    const ResidualTargets<kMode> tg = block_targets(proto, sv, RQN ? RQN : 1ull);
+    if constexpr (kHist) {
+        if (!grid_barrier(st, 4 * G)) return out.report(st);
+    }
     // phase 5: selection
     if (t_hi > t_lo) {  // the same branch in the whole block
-        uint32_t *tpre = reinterpret_cast<uint32_t *>(tb.tau) + kHistTpreOffset;
-        const uint32_t total = hist_tile_prefix(h.htot, tpre);
-        if (total != (uint32_t)Rn && threadIdx.x == 0) {  // a wrapped count
-            raise_error(st, SMC_E_RANGE);
-            out.report(st);
-        }
-        const HistMap hm{reinterpret_cast<const uint4 *>(h.hist), h.hrec, tpre, (int64_t)Rn};
         unsigned long long d0 = pre_d, r0 = pre_r;
-        for (int tile = t_lo; tile < t_hi; ++tile) {
-            if (!keep) {
-                scan_tile_local(g, n, tile, tb);
-                residual_tile_scans(tb, N, QN, shift);
+        if constexpr (kHist) {
+            uint32_t *tpre = reinterpret_cast<uint32_t *>(tb.tau) + kHistTpreOffset;
+            const uint32_t total = hist_tile_prefix(h.htot, tpre);
+            if (total != (uint32_t)Rn && threadIdx.x == 0) {  // a wrapped count
+                raise_error(st, SMC_E_RANGE);
+                out.report(st);
             }
-            const ResidualMap km{hm, (int64_t)d0, tb.a};
-            select_tile_closed(tg, out, n, tile, r0, RQN ? RQN : 1ull, tb, km);
-            d0 += __ldcg(&rs.td[tile]);
-            r0 += __ldcg(&rs.tr[tile]);
+            const HistMap hm{reinterpret_cast<const uint4 *>(h.hist), h.hrec, tpre, (int64_t)Rn};
+            for (int tile = t_lo; tile < t_hi; ++tile) {
+                if (!keep) {
+                    scan_tile_local(g, n, tile, tb);
+                    residual_tile_scans(tb, N, QN, shift);
+                }
+                const ResidualMap km{hm, (int64_t)d0, tb.a};
+                select_tile_closed(tg, out, n, tile, r0, RQN ? RQN : 1ull, tb, km);
+                d0 += __ldcg(&rs.td[tile]);
+                r0 += __ldcg(&rs.tr[tile]);
+            }
+        } else {
+            for (int tile = t_lo; tile < t_hi; ++tile) {
+                if (!keep) {
+                    scan_tile_local(g, n, tile, tb);
+                    residual_tile_scans(tb, N, QN, shift);
+                }
+                DPrefixMap km;
+                km.d0 = (int64_t)d0;
+                km.load(tb.a);
+                __syncthreads();  // every thread holds its d prefix before tb.a is reused
+                select_tile_closed(tg, out, n, tile, r0, RQN ? RQN : 1ull, tb, km);
+                d0 += __ldcg(&rs.td[tile]);
+                r0 += __ldcg(&rs.tr[tile]);
+            }
         }
     }
     grid_depart(st);

@@ -12,7 +12,7 @@ from oracle import cv as ocv
 from oracle import resample as ores
 from paper_1306_5583_b300 import smc, workloads
 
-SCHEMES = ["systematic", "stratified", "multinomial", "residual"]
+SCHEMES = ["systematic", "stratified", "multinomial", "residual", "residual_systematic", "residual_stratified"]
 
 
 def need_gpu():
@@ -71,8 +71,8 @@ def check_resample(s, lw_gpu, t, scheme, seed, precision):
     qr = np.array([float(v) for v in q_ref])
     tol = (4e-6 if precision == 32 else 1e-13) * qr + 2.0
     assert np.all(np.abs(qg - qr) <= tol), "fixed-point weights"
-    if scheme == "residual":
-        ref = ores.residual(q_gpu, seed, t)
+    if scheme in ores.RESIDUAL_STEPS:
+        ref = ores.residual(q_gpu, seed, t, step=ores.RESIDUAL_STEPS[scheme])
     else:
         ref = {"systematic": ores.systematic, "stratified": ores.stratified,
                "multinomial": ores.multinomial}[scheme](Qi, seed, t)

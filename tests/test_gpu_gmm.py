@@ -15,17 +15,18 @@ pytestmark = pytest.mark.gpu
 
 
 def make_gmm(n, nd=1000, r=4, T=500, precision=32, scheme="systematic", threshold=0.5, seed=0, data_seed=0,
-             schedule="prior", power=5.0, shape0=1, rate0=1.0, move="rw", eps=0.05):
+             schedule="prior", power=5.0, shape0=1, rate0=1.0, move="rw", eps=0.05, ess_target=0.5):
     y = workloads.gmm_data(nd, seed=data_seed)
     mv = {"rw": smc.GMM_RW, "mala": smc.GMM_MALA, "rw_mala": smc.GMM_RW_MALA}[move]
     cfg = smc.make_config(model="gmm", n=n, precision=precision, scheme=scheme, threshold=threshold, seed=seed,
                           max_data=nd, max_records=T + 1,
                           gmm=dict(n_comp=r, n_iter=T, power=power, shape0=shape0, rate0=rate0, move=mv,
-                                   mala_step=eps,
-                                   schedule=smc.ALPHA_LINEAR if schedule == "linear" else smc.ALPHA_PRIOR))
+                                   mala_step=eps, ess_target=ess_target,
+                                   schedule={"linear": smc.ALPHA_LINEAR, "prior": smc.ALPHA_PRIOR,
+                                             "adaptive": smc.ALPHA_ADAPTIVE}[schedule]))
     s = smc.Sampler(cfg)
     s.set_data(y)
-    op = ogmm.GMMParams(r=r, T=T, power=power, schedule=schedule, shape0=shape0, rate0=rate0)
+    op = ogmm.GMMParams(r=r, T=T, power=power, schedule=schedule, shape0=shape0, rate0=rate0, ess_target=ess_target)
     return s, y, op
 
 
@@ -330,3 +331,63 @@ def test_mala_full_run_fp64_matches_oracle():
     assert [g["resampled"] for g in gpu] == [o.resampled for o in recs]
     assert abs(s.log_evidence() - ds_ref) < 1e-8
     assert abs(s.path_sampling() - ps_ref) < 1e-8
+
+
+def test_adaptive_schedule_fp64_matches_oracle():
+    """CESS-targeted tempering, FP64, free-running: the device's bisection
+    picks the oracle's alpha_t at every iteration (the same float64
+    midpoints and decisions), alpha reaches 1, and both evidence estimates
+    match the oracle within 1e-8."""
+    need_gpu()
+    n, nd, r, T, seed = 2048, 100, 2, 40, 3
+    s, y, op = make_gmm(n, nd=nd, r=r, T=T, precision=64, seed=seed, schedule="adaptive", ess_target=0.6)
+    s.initialize()
+    s.iterate(T)
+    ds_ref, ps_ref, recs = ogmm.run(y, n, seed, op)
+    gpu = s.history(T + 1)[1:]
+    al_gpu = [g["alpha"] for g in gpu]
+    al_ref = [o.alpha for o in recs]
+    assert max(abs(a - b) for a, b in zip(al_gpu, al_ref)) < 1e-12, (al_gpu[:5], al_ref[:5])
+    assert al_ref[-1] == 1.0 and 3 < sum(1 for a in al_ref if a < 1.0) < T
+    assert [g["resampled"] for g in gpu] == [o.resampled for o in recs]
+    assert abs(s.log_evidence() - ds_ref) < 1e-8
+    assert abs(s.path_sampling() - ps_ref) < 1e-8
+
+
+def test_adaptive_alpha_fp32_hits_the_cess_target():
+    """FP32 at the benchmark's size: every alpha_t the device picks puts the
+    conditional ESS of the GPU's own weights and log-likelihoods at the
+    target (to float accuracy) unless it jumped to 1, and checkpoint resume
+    continues the adaptive schedule bit for bit."""
+    need_gpu()
+    n, T, rho = 1 << 16, 40, 0.5
+    s, y, op = make_gmm(n, nd=1000, r=4, T=T, precision=32, seed=5, schedule="adaptive", ess_target=rho)
+    s.initialize()
+    steps = 0
+    blob = None
+    for t in range(1, 13):
+        x = s.state().astype(np.float64)
+        lw = s.log_weight().astype(np.float64)
+        prev = s.history(1)[0]
+        logW = np.full(n, -math.log(n)) if prev["resampled"] else lw - prev["L"]
+        llik = x[3 * 4 + 1]
+        s.move()
+        rec = s.history(1)[0]
+        a_t, a_p = rec["alpha"], prev["alpha"]
+        assert a_t > a_p or a_p == 1.0
+        if a_t < 1.0:
+            steps += 1
+            lc = ogmm.log_cess(logW, llik, a_t - a_p)
+            assert abs(lc - math.log(rho * n)) < 2e-4, (t, lc, math.log(rho * n))
+        s.resample()
+        s.mcmc()
+        if t == 6:
+            blob = s.checkpoint()
+    assert steps >= 3
+    s.iterate(5)
+    ref = s.history(1)[0]
+    b, _, _ = make_gmm(n, nd=1000, r=4, T=T, precision=32, seed=5, schedule="adaptive", ess_target=rho)
+    b.restore(blob)
+    b.iterate(6 + 5)
+    got = b.history(1)[0]
+    assert got["alpha"] == ref["alpha"] and got["logZ"] == ref["logZ"]

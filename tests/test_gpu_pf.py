@@ -289,7 +289,7 @@ def test_full_size_sampled(scheme):
         assert np.all(np.diff(Q.astype(np.float64)) >= 0)
         a = s.ancestors().astype(np.int64)
         assert np.all(np.diff(a) >= 0) and a.min() >= 0 and a.max() < n
-        if scheme in ("multinomial", "residual") and t == 1:
+        if (scheme == "multinomial" or scheme.startswith("residual")) and t == 1:
             check_resample(s, lw, t, scheme, seed, 32)  # every output against the oracle
         if scheme == "multinomial":
             # output k: the first i with Q_i 2^25 > Q_N (2 j_(k) + 1), j_(k) the sorted draws
@@ -319,13 +319,14 @@ def test_full_size_sampled(scheme):
             assert not np.any(zero[a])
 
 
-@pytest.mark.parametrize("scheme", ["multinomial", "residual"])
+@pytest.mark.parametrize("scheme", ["multinomial", "residual", "residual_systematic", "residual_stratified"])
 @pytest.mark.parametrize("n", [3 * (1 << 20) + 17, 5 * 2048 + 1])
 def test_histogram_one_pass_sizes(scheme, n):
-    """Multinomial and residual selection by the draw histogram where every
-    block owns several weight tiles (N above one wave of tiles) and where
-    most blocks own none: three forced resamplings in a row give the
-    oracle's ancestors on the GPU's CDF, every output compared."""
+    """Multinomial and residual selection (by the draw histogram, or by the
+    closed form over the residual outputs) where every block owns several
+    weight tiles (N above one wave of tiles) and where most blocks own none:
+    three forced resamplings in a row give the oracle's ancestors on the
+    GPU's CDF, every output compared."""
     need_gpu()
     seed = 4
     s, y, op = make_pf(n, 4, 32, scheme=scheme, threshold=0.0, seed=seed)
@@ -341,12 +342,13 @@ def test_histogram_one_pass_sizes(scheme, n):
     s.close()
 
 
-def test_residual_without_draws():
+@pytest.mark.parametrize("scheme", ["residual", "residual_systematic", "residual_stratified"])
+def test_residual_without_draws(scheme):
     """Equal weights at N = 2^k: every d_i = N q_i / Q_N = 1 exactly, so
     R = 0, no residual draws and the identity ancestors."""
     need_gpu()
     n = 1 << 16
-    s, y, op = make_pf(n, 2, 32, scheme="residual", threshold=0.0, seed=2)
+    s, y, op = make_pf(n, 2, 32, scheme=scheme, threshold=0.0, seed=2)
     s.initialize()
     s.write_log_weight(np.zeros(n))
     s.resample(force=True)
@@ -482,3 +484,56 @@ def test_post_resampling_mean_fp32_graph_and_host_call():
     s.initialize()
     s.iterate(2)
     assert all(np.isnan(r["post_mean_x"]) for r in s.history(3))
+
+
+@pytest.mark.parametrize("scheme", ["systematic", "multinomial", "residual_stratified"])
+def test_inplace_ancestors_match_oracle(scheme):
+    """SMC_FLAG_INPLACE: the step's ancestors in the in-place copy_from
+    arrangement (survivors keep their slot) equal the oracle's arrangement of
+    its own ancestors on the GPU's CDF, with heavy particles in several tiles
+    and a ragged last tile; then an FP64 run with the arrangement matches
+    the oracle filter run the same way."""
+    need_gpu()
+    n, seed = 5 * 2048 + 777, 9
+    p = cv_params()
+    _, y = workloads.cv_data(3, seed=0, **p)
+    cfg = smc.make_config(model="cv", n=n, precision=32, scheme=scheme, threshold=0.0, seed=seed, max_data=3,
+                          cv=p, inplace=True)
+    s = smc.Sampler(cfg)
+    s.set_data(y)
+    s.initialize()
+    g = np.random.default_rng(3)
+    lw = g.normal(0.0, 0.7, n)
+    for i, extra in ((2 * 2048 + 1001, 7.0), (3 * 2048 + 8, 5.5), (n - 3, 6.0)):
+        lw[i] += extra
+    s.write_log_weight(lw)
+    lw_gpu = s.log_weight()
+    s.resample(force=True)
+    Qi = [int(v) for v in s.cdf().astype(object)]
+    q_gpu = [Qi[0]] + [Qi[i] - Qi[i - 1] for i in range(1, n)]
+    if scheme in ores.RESIDUAL_STEPS:
+        ref = ores.residual(q_gpu, seed, 0, step=ores.RESIDUAL_STEPS[scheme])
+    else:
+        ref = {"systematic": ores.systematic, "multinomial": ores.multinomial}[scheme](Qi, seed, 0)
+    anc = s.ancestors().astype(np.int64)
+    assert np.array_equal(anc, ores.stay_permutation(ref))
+    o = np.bincount(anc, minlength=n)
+    assert np.count_nonzero(anc == np.arange(n)) == np.count_nonzero(o)
+    s.close()
+    # end to end in FP64
+    T, n2 = 25, 1000
+    _, y2 = workloads.cv_data(T, seed=0, **p)
+    cfg = smc.make_config(model="cv", n=n2, precision=64, scheme=scheme, threshold=0.5, seed=3, max_data=T, cv=p,
+                          inplace=True)
+    s = smc.Sampler(cfg)
+    s.set_data(y2)
+    s.initialize()
+    s.iterate(T - 1)
+    recs = s.history(T)
+    ref_recs, last = ocv.run(y2, n2, 3, oracle_params(p), scheme=scheme, threshold=0.5, inplace=True)
+    assert any(o["resampled"] for o in ref_recs)
+    for r, o in zip(recs, ref_recs):
+        assert r["resampled"] == o["resampled"]
+        assert abs(r["logZ"] - o["logZ"]) < 1e-9
+    assert_close(s.state(), last.x, 1e-10, "final state")
+    s.close()
