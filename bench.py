@@ -46,9 +46,14 @@ SCAN_BYTES_PER_PARTICLE = 12     # log-weight read 4 B + CDF write 8 B
 SELECT_BYTES_PER_PARTICLE = 12   # CDF read 8 B + ancestor write 4 B
 FLUSH_BYTES = 1 << 30  # written between timed iterations: 8x the 126 MB L2
 HEAD_START = 8         # extra flushes queued before the timed loop so the host runs ahead of the GPU
-# kernels of one resampling step (launched every iteration; they exit after
-# reading the state block when the ESS test did not ask for resampling)
-RESAMPLE_KERNELS = {"systematic": 1, "stratified": 1, "multinomial": 7, "residual": 12}
+# kernels of one resampling step (one cooperative kernel for every scheme,
+# launched every iteration; it exits after reading the state block when the
+# ESS test did not ask for resampling)
+RESAMPLE_KERNELS = {"systematic": 1, "stratified": 1, "multinomial": 1, "residual": 1,
+                    "residual_systematic": 1, "residual_stratified": 1}
+# algorithmic bytes per particle of a resampling step beyond the move:
+# log-weight re-read 4 B + ancestor write 4 B + ancestor read 4 B
+RESAMPLE_BYTES_PER_PARTICLE = 12
 # DRAM bytes (read + write) of one launch of the move kernel, from the ncu
 # capture summarised in this file (null when the file is absent)
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "pf_iterate_cv_gather_2e20.md")
@@ -273,6 +278,17 @@ def run_ours(args):
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                 "fallback 6.4 TB/s"}
 
+    # the whole iteration (move kernel, resampler and launch gaps) against the
+    # same peak: expected algorithmic bytes per particle-update over the
+    # event-timed step
+    f_res = main["resample_frac"]
+    it_bytes = PF_BYTES_PER_PARTICLE + RESAMPLE_BYTES_PER_PARTICLE * f_res
+    it_achieved = it_bytes * n / (ms_per_step * 1e-3) / 1e9
+    roofline["iteration"] = {"achieved": round(it_achieved, 1), "frac": round(it_achieved / peak, 4),
+                             "bytes_per_particle": round(it_bytes, 2),
+                             "definition": "(40 B + 12 B x resample fraction) x N / ms_per_step: the whole "
+                                           "iteration, kernels plus launch and completion gaps"}
+
     # end to end through the C ABI with host buffers (pinned): H2D of the
     # step's observation, D2H of the step's record
     e2e = run_e2e(make, headline, args.steps, max(3, args.warmup), y, dev, stream, flush) if rank == 0 else None
@@ -293,15 +309,16 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(n, 8)
+        if not args.no_extra:
+            out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(n, 8)
     if rank == 0 and not args.no_extra:
-        clk = (clocks or {}).get("sm_mhz", 2032)
         extra = {}
-        g = bench_gmm(dev, stream, move="rw")
-        g["mufu_frac_of_peak"] = g["mufu_ops_per_s"] / mufu_peak_ops(clk)
-        extra["gmm_rw_n2^16"] = g
-        gm = bench_gmm(dev, stream, n=1 << 18, move="mala")
-        gm["mufu_frac_of_peak"] = gm["mufu_ops_per_s"] / mufu_peak_ops(clk)
-        extra["gmm_mala_n2^18"] = gm
+        mufu = mufu_peak(dev)
+        extra["mufu_peak_measured"] = mufu
+        extra["config0_fp64_n1000_T100"] = bench_config0(dev, stream)
+        extra["gmm_rw_n2^16"] = bench_gmm(dev, stream, mufu, move="rw")
+        extra["gmm_mala_n2^18"] = bench_gmm(dev, stream, mufu, n=1 << 18, move="mala")
+        extra["gmm_rw_vs_mala_n2^18"] = bench_gmm_accuracy(dev, stream, seeds=args.gmm_seeds)
         extra["pf_grad_n2^18_T500"] = bench_pf_grad(dev, stream)
         extra["batched_256"] = bench_batched(dev, stream)
         out["extra"] = extra
@@ -360,16 +377,37 @@ def run_e2e(make, scheme, K, W, y, dev, stream, flush):
                             "max": round(float(np.max(per_call)) * 1e6, 1)}}
 
 
-def mufu_peak_ops(clock_mhz):
-    """MUFU (special-function) issue rate: 16 ops per clock per SM (4 per
-    SM sub-partition), 148 SMs."""
-    return 148 * 16 * clock_mhz * 1e6
+def mufu_peak(dev):
+    """The special-function pipe's measured issue rate (smc_mufu_rate, a
+    kernel of independent ex2 / lg2 chains), in MUFU operations per second,
+    with the SM clock sampled while it ran."""
+    from paper_1306_5583_b300 import smc
+    import torch
+    torch.cuda.synchronize(dev)
+    with Clocks(dev.index if dev.index is not None else 0) as clk:
+        rates = {kind: max(smc.mufu_rate(k, 8, 1 << 14)[0] for _ in range(5))
+                 for k, kind in enumerate(("ex2_lg2", "ex2", "lg2"))}
+    c = clk.summary() or {}
+    mhz = c.get("sm_mhz") or 2032
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    per_clk = {k: v / (sms * mhz * 1e6) for k, v in rates.items()}
+    # the GMM likelihood is almost all ex2 (n r per datum against n / 8 lg2):
+    # its roofline is the ex2 rate
+    return {"ops_per_s": rates["ex2"], "ops_per_s_by_kind": rates, "ops_per_clk_per_sm_by_kind": per_clk,
+            "sm_mhz": mhz, "sms": sms,
+            "how": "smc_mufu_rate: 8 blocks/SM x 256 threads x 8 independent chains of ex2.approx and/or "
+                   "lg2.approx, 2^14 rounds, best of 5 event-timed launches per kind; the peak used is ex2's"}
 
 
-def bench_gmm(dev, stream, n=1 << 16, T=500, move="rw", K=20):
+def bench_gmm(dev, stream, mufu, n=1 << 16, T=500, move="rw", K=20):
     """GMM tempered sampler (Sec. 5.2): iterations per second and the MUFU
     roofline of the mcmc kernel, plus both evidence estimates of a full
-    run."""
+    run.  The algorithmic count is the method's: per particle and iteration
+    each Metropolis block evaluates n r exponentials and n logarithms
+    (3 blocks: 15 000 for n = 1000, r = 4); a Langevin move evaluates the
+    likelihood and its gradient once (n r + n).  The kernel itself folds
+    eight logarithms into one (n / 8), which the implementation count
+    reports beside it."""
     import torch
     from paper_1306_5583_b300 import smc, workloads
     y = workloads.gmm_data(1000, seed=0)
@@ -380,6 +418,8 @@ def bench_gmm(dev, stream, n=1 << 16, T=500, move="rw", K=20):
     s = smc.Sampler(cfg, stream=stream, device=dev)
     s.set_data(y)
     with torch.cuda.stream(stream):
+        s.initialize()
+        s.iterate(1)  # captures the iteration graph
         s.initialize()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -402,19 +442,73 @@ def bench_gmm(dev, stream, n=1 << 16, T=500, move="rw", K=20):
         torch.cuda.synchronize(dev)
         mcmc_ms = float(np.median([a.elapsed_time(b) for a, b in mk]))
     s.close()
-    # MUFU ops per particle and iteration: per Metropolis block n (r ex2 + 1/8 lg2);
-    # a Langevin move adds one reciprocal per datum and counts as one block
-    per_block = 1000 * (4 + 1.0 / 8)
-    mufu = n * (3 * per_block if move == "rw" else 1000 * (4 + 1 + 1.0 / 8))
+    nd, r = 1000, 4
+    algo = n * (3 * nd * (r + 1) if move == "rw" else nd * (r + 1))
+    impl = n * (3 * nd * (r + 1.0 / 8) if move == "rw" else nd * (r + 1 + 1.0 / 8))
+    rate = algo / (mcmc_ms * 1e-3)
     return {"n_particles": n, "iterations": T, "move": move, "ms_full_run": full_ms,
             "particle_updates_per_s": n * T / (full_ms * 1e-3), "log_evidence_standard": ds,
             "log_evidence_path_sampling": ps, "mcmc_kernel_us": mcmc_ms * 1e3,
-            "mufu_ops_per_s": mufu / (mcmc_ms * 1e-3)}
+            "mufu_ops_per_particle_iteration_algorithmic": algo / n,
+            "mufu_ops_per_particle_iteration_kernel": impl / n,
+            "mufu_ops_per_s_algorithmic": rate,
+            "mufu_frac_of_measured_peak": rate / mufu["ops_per_s"],
+            "mufu_frac_of_measured_peak_kernel_count": impl / (mcmc_ms * 1e-3) / mufu["ops_per_s"]}
+
+
+def bench_gmm_accuracy(dev, stream, n=1 << 18, T=500, seeds=8):
+    """The random-walk and Langevin samplers at the same N: mean and
+    standard deviation of both evidence estimates over seeds, the
+    event-timed run, and the time each needs to reach the smaller of the two
+    standard deviations (replicates averaged: time x (sd / sd_common)^2)."""
+    import torch
+    from paper_1306_5583_b300 import smc, workloads
+    y = workloads.gmm_data(1000, seed=0)
+    out = {}
+    for move in ("rw", "mala"):
+        mv = {"rw": smc.GMM_RW, "mala": smc.GMM_MALA}[move]
+        ds, ps, ms = [], [], []
+        for seed in range(seeds):
+            cfg = smc.make_config(model="gmm", n=n, precision=32, scheme="systematic", threshold=0.5, seed=100 + seed,
+                                  max_data=1000, max_records=T + 1, keep_cdf=False,
+                                  gmm=dict(n_comp=4, n_iter=T, power=5.0, move=mv, mala_step=0.05))
+            s = smc.Sampler(cfg, stream=stream, device=dev)
+            s.set_data(y)
+            with torch.cuda.stream(stream):
+                s.initialize()
+                s.iterate(1)
+                s.initialize()
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.iterate(T)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms.append(e0.elapsed_time(e1))
+                ds.append(s.log_evidence())
+                ps.append(s.path_sampling())
+            s.close()
+        out[move] = {"log_evidence_standard_mean": float(np.mean(ds)), "log_evidence_standard_sd": float(np.std(ds, ddof=1)),
+                     "log_evidence_path_mean": float(np.mean(ps)), "log_evidence_path_sd": float(np.std(ps, ddof=1)),
+                     "ms_per_run": float(np.mean(ms))}
+    sd_common = min(out["rw"]["log_evidence_standard_sd"], out["mala"]["log_evidence_standard_sd"])
+    for move in ("rw", "mala"):
+        o = out[move]
+        o["ms_to_common_sd"] = o["ms_per_run"] * (o["log_evidence_standard_sd"] / sd_common) ** 2
+    out["n_particles"] = n
+    out["seeds"] = seeds
+    out["common_sd"] = sd_common
+    return out
 
 
 def bench_batched(dev, stream, count=256):
     """Config 4: 256 filters of uneven N and T in one launch per kernel per
-    iteration, against the same 256 filters run one by one (plain API)."""
+    iteration, against the same 256 filters run one by one through the plain
+    API.  Both arms are timed by CUDA events on one stream around the
+    iteration work only: every plain context is created, given its data and
+    has its iteration graph captured before the timed region, which then
+    holds each filter's initialize + iterate(T_b - 1); the batched arm holds
+    the batch's initialize + run after the autotuner."""
     import torch
     from paper_1306_5583_b300 import smc, workloads
     ns, ts = workloads.batch_shapes(count, seed=0)
@@ -427,18 +521,19 @@ def bench_batched(dev, stream, count=256):
     for b in range(count):
         bt.set_data(b, data[b])
     with torch.cuda.stream(stream):
-        grid = bt.tune()
+        shape = bt.tune()
+        bt.run()  # the iteration graph is captured here
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        bt.initialize()
         bt.run()
         e1.record(stream)
         torch.cuda.synchronize(dev)
         batch_ms = e0.elapsed_time(e1)
         lz_batch = bt.log_evidence()
     bt.close()
-    t0 = time.perf_counter()
-    lz_plain = np.empty(count)
+    plain = []
     with torch.cuda.stream(stream):
         for b in range(count):
             pc = smc.make_config(model="cv", n=int(ns[b]), precision=32, scheme="systematic", threshold=0.5, seed=3,
@@ -446,58 +541,120 @@ def bench_batched(dev, stream, count=256):
             s = smc.Sampler(pc, stream=stream, device=dev)
             s.set_data(data[b])
             s.initialize()
-            s.iterate(int(ts[b]) - 1)
-            lz_plain[b] = s.log_evidence()
-            s.close()
+            if int(ts[b]) > 1:
+                s.iterate(1)  # captures the context's iteration graph
+            plain.append(s)
         torch.cuda.synchronize(dev)
-    plain_s = time.perf_counter() - t0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for b, s in enumerate(plain):
+            s.initialize()
+            s.iterate(int(ts[b]) - 1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms = e0.elapsed_time(e1)
+        lz_plain = np.array([s.log_evidence() for s in plain])
+    for s in plain:
+        s.close()
     return {"filters": count, "particle_updates": work, "batched_ms": batch_ms,
-            "batched_particle_updates_per_s": work / (batch_ms * 1e-3), "plain_one_by_one_s": plain_s,
-            "plain_particle_updates_per_s": work / plain_s, "speedup": plain_s / (batch_ms * 1e-3),
-            "autotuned_blocks_per_sm": grid, "log_evidence_identical": bool(np.array_equal(lz_batch, lz_plain))}
+            "batched_particle_updates_per_s": work / (batch_ms * 1e-3), "plain_one_by_one_ms": plain_ms,
+            "plain_particle_updates_per_s": work / (plain_ms * 1e-3), "speedup": plain_ms / batch_ms,
+            "autotuned": {"blocks_per_sm": shape[0], "tiles_per_item": shape[1]},
+            "timing": "CUDA events around initialize + all iterations in both arms; contexts, data and graphs "
+                      "prepared before the timed region",
+            "log_evidence_identical": bool(np.array_equal(lz_batch, lz_plain))}
 
 
 def bench_pf_grad(dev, stream, n=1 << 18, T=500):
-    """Config 3b: gradient of the log-likelihood estimate (recorded forward,
-    then the reverse sweep with recomputation) against the plain forward."""
+    """Config 3b: the gradient of the log-likelihood estimate (the reverse
+    sweep with recomputation over a recorded forward run) against the plain
+    forward run, both CUDA-event timed after a warm-up (graph capture and
+    first-launch costs outside the timed region)."""
     import torch
     from paper_1306_5583_b300 import smc, workloads
     p = dict(workloads.CV_DEFAULT)
     _, y = workloads.cv_data(T, seed=0, **p)
     out = {}
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
     for rec in (False, True):
         cfg = smc.make_config(model="cv", n=n, precision=32, scheme="systematic", threshold=0.5, seed=1, max_data=T,
                               cv=p, keep_cdf=False, record=rec, checkpoint_every=16)
         s = smc.Sampler(cfg, stream=stream, device=dev)
         s.set_data(y)
         with torch.cuda.stream(stream):
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
             s.initialize()
             s.iterate(T - 1)
-            torch.cuda.synchronize(dev)
-            out["forward_recorded_s" if rec else "forward_s"] = time.perf_counter() - t0
             if rec:
-                t0 = time.perf_counter()
+                s.pf_grad()
+            torch.cuda.synchronize(dev)
+            e0, e1 = ev()
+            e0.record(stream)
+            s.initialize()
+            s.iterate(T - 1)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            out["forward_recorded_ms" if rec else "forward_ms"] = e0.elapsed_time(e1)
+            if rec:
+                e0, e1 = ev()
+                e0.record(stream)
                 g = s.pf_grad()
-                out["gradient_s"] = time.perf_counter() - t0
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                out["gradient_ms"] = e0.elapsed_time(e1)
                 out["gradient"] = [float(v) for v in g]
         s.close()
-    out["gradient_over_forward"] = out["gradient_s"] / out["forward_s"]
+    out["gradient_over_forward"] = out["gradient_ms"] / out["forward_ms"]
+    out["gradient_plus_recorded_forward_over_forward"] = (out["gradient_ms"] + out["forward_recorded_ms"]) / out["forward_ms"]
     out["n_particles"] = n
     out["iterations"] = T
     return out
 
 
+def bench_config0(dev, stream, T=100, n=1000, reps=5):
+    """Config 0: the FP64 particle filter at the paper's example size
+    (N = 1000, T = 100): device time per iteration of the replayed graph."""
+    import torch
+    from paper_1306_5583_b300 import smc, workloads
+    p = dict(workloads.CV_DEFAULT)
+    _, y = workloads.cv_data(T, seed=0, **p)
+    cfg = smc.make_config(model="cv", n=n, precision=64, scheme="systematic", threshold=0.5, seed=0, max_data=T, cv=p,
+                          keep_cdf=False)
+    s = smc.Sampler(cfg, stream=stream, device=dev)
+    s.set_data(y)
+    ms = []
+    with torch.cuda.stream(stream):
+        s.initialize()
+        s.iterate(1)
+        for _ in range(reps):
+            s.initialize()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.iterate(T - 1)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        lz = s.log_evidence()
+    s.close()
+    per_it = float(np.median(ms)) / (T - 1)
+    return {"n_particles": n, "iterations": T, "precision": "f64", "us_per_iteration": per_it * 1e3,
+            "particle_updates_per_s": n / (per_it * 1e-3), "log_evidence": lz,
+            "bound": "launch latency (tiny N)"}
+
+
 def cpu_baseline(n, iters):
-    """The FP64 oracle on `iters` iterations at the full N (bounded sample)."""
+    """The FP64 oracle on `iters` iterations at the full N (bounded sample),
+    one process."""
     from oracle import cv as ocv
+    from oracle import resample as ores
     from paper_1306_5583_b300 import workloads
     p = dict(workloads.CV_DEFAULT)
     _, y = workloads.cv_data(T_OBS, seed=0, **p)
     op = ocv.CVParams(**p)
     r = ocv.init_step(n, y[0], 1, op, 0.5)
-    from oracle import resample as ores
     anc = ores.resample("systematic", r.lw, 1, 0) if r.resample else None
     t0 = time.perf_counter()
     for t in range(1, iters + 1):
@@ -507,6 +664,56 @@ def cpu_baseline(n, iters):
     return {"value": n * iters / dt, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
             "sample": f"{iters} iterations of the same filter at N={n} (numpy float64 + exact integer "
                       f"resampling), single process"}
+
+
+def _oracle_block_move(args):
+    """One block of particles through the oracle's move and weight (a
+    worker of the all-core baseline)."""
+    from oracle import cv as ocv
+    x_blk, base_blk, i0, t, y_t, seed, params = args
+    op = ocv.CVParams(**params)
+    idx = np.arange(i0, i0 + x_blk.shape[1])
+    x = ocv.move(x_blk, t, seed, op, index=idx)
+    return x, base_blk + ocv.loglik(x, y_t, op)
+
+
+def cpu_baseline_all_cores(n, iters):
+    """The same oracle, particle-parallel over every core the process may
+    use (os.sched_getaffinity): the move and weight of each block of
+    particles in a worker process (a spawn pool, started before any further
+    GPU work), the normaliser, ESS test and exact integer resampling in the
+    parent, as in the one-process run."""
+    import multiprocessing as mp
+    from oracle import cv as ocv
+    from oracle import resample as ores
+    from oracle import weights as ow
+    from paper_1306_5583_b300 import workloads
+    cores = len(os.sched_getaffinity(0))
+    p = dict(workloads.CV_DEFAULT)
+    _, y = workloads.cv_data(T_OBS, seed=0, **p)
+    op = ocv.CVParams(**p)
+    r = ocv.init_step(n, y[0], 1, op, 0.5)
+    anc = ores.resample("systematic", r.lw, 1, 0) if r.resample else None
+    x, lw, L = r.x, r.lw, r.L
+    bounds = np.linspace(0, n, cores + 1).astype(np.int64)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_block_move, [(x[:, :8], np.zeros(8), 0, 1, y[1], 1, p)] * cores)  # workers warm
+        t0 = time.perf_counter()
+        for t in range(1, iters + 1):
+            xs = x[:, anc] if anc is not None else x
+            base = np.full(n, -math.log(n)) if anc is not None else lw - L
+            parts = pool.map(_oracle_block_move, [(xs[:, a:b], base[a:b], int(a), t, y[t], 1, p)
+                                                  for a, b in zip(bounds[:-1], bounds[1:])])
+            x = np.concatenate([q[0] for q in parts], axis=1)
+            lw = np.concatenate([q[1] for q in parts])
+            _, L = ow.log_sum_exp(lw)
+            W = np.exp(lw - L)
+            res = ow.resample_decision(1.0 / float(np.sum(W * W)), n, 0.5)
+            anc = ores.resample("systematic", lw, 1, t) if res else None
+        dt = time.perf_counter() - t0
+    return {"value": n * iters / dt, "unit": "particle-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{iters} iterations at N={n}: move and weight in {cores} spawned worker processes over "
+                      f"particle blocks, normaliser and exact integer resampling in the parent"}
 
 
 def run_reference(args):
@@ -564,7 +771,9 @@ def main():
     ap.add_argument("--n-particles", dest="n", type=int, default=N_FULL)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the GMM, batched and gradient sections")
-    ap.add_argument("--schemes", default="systematic,stratified,multinomial,residual")
+    ap.add_argument("--schemes", default="systematic,stratified,multinomial,residual,residual_systematic,"
+                                         "residual_stratified")
+    ap.add_argument("--gmm-seeds", dest="gmm_seeds", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -64,7 +64,9 @@ extern "C" {
 #define SMC_MULTINOMIAL 0
 #define SMC_STRATIFIED 1
 #define SMC_SYSTEMATIC 2
-#define SMC_RESIDUAL 3
+#define SMC_RESIDUAL 3              /* floor(N W_i) copies, then multinomial on the residual weights */
+#define SMC_RESIDUAL_SYSTEMATIC 4   /* the same copies, the R residual outputs drawn systematically */
+#define SMC_RESIDUAL_STRATIFIED 5   /* ... or stratified (Douc et al. 2005 list both variants) */
 
 /* config flags */
 #define SMC_FLAG_KEEP_CDF 1u  /* store the fixed-point CDF of each resampling step (smc_read_cdf) */
@@ -73,6 +75,11 @@ extern "C" {
 #define SMC_FLAG_POST_MEAN 4u /* CV models: also record the post-resampling filtered mean (mean_post;
                                  Sec. 4.1.5 evaluates monitors after the whole iteration) with one
                                  more kernel after each resampling step */
+#define SMC_FLAG_INPLACE 8u   /* arrange each step's ancestors in place (copy_from of Sec. 4.1.2):
+                                 a particle with offspring keeps its own slot, the extra copies fill
+                                 the slots of particles without offspring in increasing order
+                                 (smc_read_ancestors then returns that arrangement); one more kernel
+                                 after each resampling step; not with SMC_FLAG_RECORD */
 
 /* models */
 #define SMC_MODEL_CV 0        /* Sec. 5.1: constant-velocity tracking, Student-t observations */
@@ -90,6 +97,12 @@ extern "C" {
 /* GMM annealing schedules (Sec. 5.2.3) */
 #define SMC_ALPHA_LINEAR 0  /* alpha_t = t / T */
 #define SMC_ALPHA_PRIOR 1   /* alpha_t = (t / T)^p */
+#define SMC_ALPHA_ADAPTIVE 2 /* alpha_t chosen on the device at every iteration so that the conditional
+                                ESS of the incremental weights, N (sum W_i w_i)^2 / sum W_i w_i^2 with
+                                w_i = exp((alpha_t - alpha_{t-1}) l_i), equals ess_target N (or
+                                alpha_t = 1 when it stays above that at alpha = 1): 40 halvings of
+                                [0, 1 - alpha_{t-1}] in one cooperative kernel; the chosen alpha_t
+                                is in the record; later iterations keep alpha = 1 */
 
 /* Almost-constant-velocity model parameters (Sec. 5.1.1). */
 typedef struct {
@@ -105,8 +118,8 @@ typedef struct {
 /* Gaussian-mixture model and sampler parameters (Sec. 5.2.1-5.2.3). */
 typedef struct {
     int32_t n_comp;       /* r, 1..8 */
-    int32_t schedule;     /* SMC_ALPHA_LINEAR or SMC_ALPHA_PRIOR */
-    int32_t n_iter;       /* T_r: alpha reaches 1 at t = T_r */
+    int32_t schedule;     /* SMC_ALPHA_LINEAR, SMC_ALPHA_PRIOR or SMC_ALPHA_ADAPTIVE */
+    int32_t n_iter;       /* T_r: alpha reaches 1 at t = T_r (adaptive: the most iterations) */
     int32_t shape0;       /* Gamma prior shape of each precision (integer >= 1) */
     double power;         /* p of the prior schedule */
     double mu0, sd0;      /* normal prior of each mean */
@@ -114,6 +127,7 @@ typedef struct {
     int32_t move;         /* SMC_GMM_RW, SMC_GMM_MALA or SMC_GMM_RW_MALA */
     int32_t reserved;
     double mala_step;     /* Langevin step size epsilon */
+    double ess_target;    /* SMC_ALPHA_ADAPTIVE: rho in (0, 1), the conditional ESS target rho N */
 } smc_gmm_params;
 
 typedef struct {
@@ -358,10 +372,14 @@ int smc_batch_initialize(smc_batch *b);
 int smc_batch_iterate(smc_batch *b, int32_t n);
 /* initialize, then iterate until every filter has used all its observations */
 int smc_batch_run(smc_batch *b);
-/* autotuner: times the persistent grid sizes 1, 2, 4 and 8 blocks per SM on
- * the first iterations, keeps the fastest (returned in *blocks_per_sm) and
- * re-initializes */
-int smc_batch_tune(smc_batch *b, int32_t *blocks_per_sm);
+/* autotuner: times every launch shape of the persistent kernels -- 1, 2, 3,
+ * 4, 6 or 8 resident blocks per SM, each block taking 1, 2 or 4 consecutive
+ * tiles per work item -- on the first 10 iterations, keeps the fastest
+ * (returned in *blocks_per_sm and *tiles_per_item; either may be NULL) and
+ * re-initializes.  The tile (1024 particles, 4 per thread, 256 threads) is
+ * not searched: it fixes the reduction order that makes every filter
+ * bit-identical to its plain run. */
+int smc_batch_tune(smc_batch *b, int32_t *blocks_per_sm, int32_t *tiles_per_item);
 /* per-filter log-evidence estimates, n_filters values in caller order */
 int smc_batch_log_evidence(smc_batch *b, double *h_out);
 int smc_batch_read_history(smc_batch *b, int32_t filter, smc_record *h_records, int32_t count,
@@ -375,6 +393,63 @@ int smc_batch_read_state(smc_batch *b, int32_t filter, void *dst, int on_device)
  * n x 4 uint32 (row-major), key 2 uint32 (host). */
 int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], uint32_t *d_out, int64_t n,
                       void *cuda_stream);
+
+/* One shard of a particle filter partitioned over ranks (one GPU each; the
+ * paper's MPI module, Sec. 3.1, normalises the weight set across ranks).
+ * A filter of n_global particles is split in blocks: this context's
+ * n_particles particles are the filter's [offset, offset + n_particles), with
+ * those global Philox indices, so every particle evolves as in one context of
+ * n_global particles.  CV models, systematic or stratified resampling,
+ * without SMC_FLAG_RECORD, _INPLACE or _POST_MEAN; smc_move, smc_resample and
+ * smc_iterate refuse a shard (SMC_E_STATE).  One iteration, every rank
+ * (the caller runs the collectives between the calls, all buffers device
+ * memory on the context's stream):
+ *   smc_shard_move(ctx, d_partial)      move + weight; this shard's partial
+ *                                       (64 bytes) into d_partial
+ *   all-gather of the partials in rank order into d_partials (world x 64 B)
+ *   smc_shard_finalize(ctx, d_partials, world)
+ *                                       global normaliser, ESS, evidence,
+ *                                       means and resampling decision, the
+ *                                       same on every rank (record of step t)
+ *   then, when the record says resampled:
+ *   smc_shard_total(ctx, d_total)       this shard's fixed-point total (uint64)
+ *   all-gather of the totals into d_totals (world x uint64)
+ *   smc_shard_select(ctx, d_totals, rank, world, d_src, d_range)
+ *                                       the global outputs of this shard's
+ *                                       particles: d_src[k] = local source of
+ *                                       output k (n_global int32), d_range =
+ *                                       [k_lo, k_hi) (2 int64)
+ *   smc_shard_pack(ctx, d_src, k_lo, k_hi - k_lo, d_send)
+ *                                       the copies' states (4 values each, the
+ *                                       context's precision) in output order
+ *   all-to-all: the copies for output slots [o_d, o_d + n_d) go to rank d
+ *   smc_shard_unpack(ctx, d_recv)       the received n_particles copies (output
+ *                                       order = slot order) become the shard's
+ *                                       particles, log-weights -log n_global
+ * smc_shard_configure marks the context as a shard (before smc_initialize,
+ * which then only resets the state: iteration 0 is a smc_shard_move like the
+ * others).  Errors: SMC_E_ARG for an unsupported configuration or
+ * inconsistent sizes, SMC_E_STATE for a call on a context that is not a
+ * shard. */
+int smc_shard_configure(smc_ctx *ctx, int64_t n_global, int64_t offset);
+int smc_shard_move(smc_ctx *ctx, void *d_partial);
+int smc_shard_finalize(smc_ctx *ctx, const void *d_partials, int32_t world);
+int smc_shard_total(smc_ctx *ctx, uint64_t *d_total);
+int smc_shard_select(smc_ctx *ctx, const uint64_t *d_totals, int32_t rank, int32_t world, int32_t *d_src,
+                     int64_t *d_range);
+int smc_shard_pack(smc_ctx *ctx, const int32_t *d_src, int64_t k_lo, int64_t count, void *d_send);
+int smc_shard_unpack(smc_ctx *ctx, const void *d_recv);
+
+/* Measurement: issue rate of the special-function (MUFU) pipe of the current
+ * device, the roofline denominator of the likelihood-bound GMM moves (no
+ * counterpart in the paper).  One launch of blocks_per_sm x SMs blocks of 256
+ * threads, each running 8 independent chains of MUFU approximations for
+ * iters rounds -- kind 0: alternating ex2 / lg2, 1: ex2 alone, 2: lg2
+ * alone -- after one warm-up launch; *ops_per_s receives MUFU operations per
+ * second and *ms the timed launch's duration (CUDA events on a private
+ * stream).  Allocates a small buffer; returns SMC_E_ARG for a bad argument
+ * and SMC_E_CUDA if a CUDA call fails. */
+int smc_mufu_rate(int32_t kind, int32_t blocks_per_sm, int32_t iters, double *ops_per_s, double *ms);
 
 /* Failure detection (bounded device waits).  Every wait of a kernel on
  * another block (the grid barriers of the cooperative resampling kernels, the

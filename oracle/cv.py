@@ -83,16 +83,21 @@ def loglik(x, y_t, p):
     return (2 * c - 0.5 * (nu + 1) * (np.log1p(zx * zx / nu) + np.log1p(zy * zy / nu)))
 
 
-def init_state(n, seed, p, stream=0):
-    eps = philox.normals(seed, np.arange(n), 0, philox.TAG_INIT, 4, stream)
+def init_state(n, seed, p, stream=0, index=None):
+    """Prior draws of particles `index` (default 0 .. n-1; a sub-range lets
+    the particles be drawn in independent blocks)."""
+    idx = np.arange(n) if index is None else np.asarray(index)
+    eps = philox.normals(seed, idx, 0, philox.TAG_INIT, 4, stream)
     return np.stack([eps[0] * p.sd_pos0, eps[1] * p.sd_pos0,
                      eps[2] * p.sd_vel0, eps[3] * p.sd_vel0])
 
 
-def move(x, t, seed, p, stream=0):
-    """One draw of X_t = A X_{t-1} + V_t per particle (Algorithm 1)."""
+def move(x, t, seed, p, stream=0, index=None):
+    """One draw of X_t = A X_{t-1} + V_t per particle (Algorithm 1); the
+    columns of x are the particles `index` (default 0 .. n-1)."""
     n = x.shape[1]
-    eps = philox.normals(seed, np.arange(n), t, philox.TAG_MOVE, 4, stream)
+    idx = np.arange(n) if index is None else np.asarray(index)
+    eps = philox.normals(seed, idx, t, philox.TAG_MOVE, 4, stream)
     return np.stack([x[0] + p.delta * x[2] + p.sd_pos * eps[0],
                      x[1] + p.delta * x[3] + p.sd_pos * eps[1],
                      x[2] + p.sd_vel * eps[2],

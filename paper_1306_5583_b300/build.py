@@ -1,6 +1,8 @@
 """Build step: compile the CUDA sources into in-tree shared libraries.
 
-* ``paper_1306_5583_b300/libsmc.so``: the SMC hot path behind include/smc.h.
+* ``paper_1306_5583_b300/libsmc.so``: the SMC hot path behind include/smc.h
+  (csrc/smc.cu) and the special-function pipe rate measurement
+  (csrc/mufu_peak.cu).
 * ``tests/gpu_support/libcurand_philox.so``: a test-only kernel that calls
   the CUDA toolkit's own Philox4x32-10 (curand device API) so the GPU tests
   can cross-check the library's generator against an independent
@@ -54,7 +56,7 @@ def build(force=False, verbose=False):
     nvcc = _nvcc()
     out = []
     if force or _stale(LIB, _sources()):
-        cmd = [nvcc, *ARCH, *FLAGS, "-o", LIB + ".tmp", os.path.join(CSRC, "smc.cu")]
+        cmd = [nvcc, *ARCH, *FLAGS, "-o", LIB + ".tmp", os.path.join(CSRC, "smc.cu"), os.path.join(CSRC, "mufu_peak.cu")]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         out.append(_run(cmd))

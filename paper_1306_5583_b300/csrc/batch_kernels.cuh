@@ -53,6 +53,7 @@ struct BatchArgs {
     const int32_t *frac;          // fixed-point fraction bits of each filter
     int32_t tmax;
     int32_t stratified;
+    int32_t chunk;                // consecutive tiles a block takes per step of its grid-stride walk
 };
 
 template <typename R>
@@ -82,18 +83,19 @@ __global__ void __launch_bounds__(kBlock, 3) batch_pf_kernel(BatchArgs<R> B) {
     const int32_t t = B.bs->t + 1;
     if (t >= B.tmax) return;
     const int nact = B.act_tiles[t];
-    for (int tile = blockIdx.x; tile < nact; tile += gridDim.x) {
-        const int b = B.tile_filter[tile];
-        DevState *st = &B.fst[b];
-        const DevState *sv = snapshot(st);
-        if (sv->error) continue;
-        const PfArgs<R> a = filter_args(B, b);
-        const int cur = sv->cur, cur_lw = sv->cur_lw;
-        const bool gather = (t > 0) && (sv->ready != 0);
-        const int nblk = B.tfirst[b + 1] - B.tfirst[b];
-        pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part);
-        if (last_arrival_after_partial(&st->ticket, (uint32_t)nblk)) pf_finalize<R, 1>(a, st, sv, nblk, t, cur, cur_lw);
-    }
+    for (int item = blockIdx.x; item * B.chunk < nact; item += gridDim.x)
+        for (int tile = item * B.chunk; tile < min(nact, (item + 1) * B.chunk); ++tile) {
+            const int b = B.tile_filter[tile];
+            DevState *st = &B.fst[b];
+            const DevState *sv = snapshot(st);
+            if (sv->error) continue;
+            const PfArgs<R> a = filter_args(B, b);
+            const int cur = sv->cur, cur_lw = sv->cur_lw;
+            const bool gather = (t > 0) && (sv->ready != 0);
+            const int nblk = B.tfirst[b + 1] - B.tfirst[b];
+            pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part);
+            if (last_arrival_after_partial(&st->ticket, (uint32_t)nblk)) pf_finalize<R, 1>(a, st, sv, nblk, t, cur, cur_lw);
+        }
     if (last_arrival(&B.bs->ticket, gridDim.x) && threadIdx.x == 0) {
         B.bs->t = t;
         B.bs->ticket = 0;
@@ -117,23 +119,24 @@ __global__ void __launch_bounds__(kBlock) batch_reduce_kernel(BatchArgs<R> B) {
     const int32_t t = B.bs->t;
     if (t < 0 || t >= B.tmax) return;
     const int nact = B.act_stiles[t];
-    for (int tile = blockIdx.x; tile < nact; tile += gridDim.x) {
-        const int b = B.stile_filter[tile];
-        DevState *st = &B.fst[b];
-        const DevState *sv = snapshot(st);
-        if (gated_out(sv, 1)) continue;
-        const QGen<R> g = filter_qgen(B, b, sv);
-        const int ns = B.sfirst[b + 1] - B.sfirst[b];
-        const unsigned long long s = tile_sum(g, B.n[b], tile - B.sfirst[b]);
-        if (threadIdx.x == 0) B.tsum[tile] = s;
-        if (last_arrival(&st->scan_ticket[SLOT_CDF], (uint32_t)ns)) {
-            const unsigned long long tot = sum_tiles(B.tsum + B.sfirst[b], ns);
-            if (threadIdx.x == 0) {
-                st->scan_total[SLOT_CDF] = tot;
-                st->scan_ticket[SLOT_CDF] = 0;
+    for (int item = blockIdx.x; item * B.chunk < nact; item += gridDim.x)
+        for (int tile = item * B.chunk; tile < min(nact, (item + 1) * B.chunk); ++tile) {
+            const int b = B.stile_filter[tile];
+            DevState *st = &B.fst[b];
+            const DevState *sv = snapshot(st);
+            if (gated_out(sv, 1)) continue;
+            const QGen<R> g = filter_qgen(B, b, sv);
+            const int ns = B.sfirst[b + 1] - B.sfirst[b];
+            const unsigned long long s = tile_sum(g, B.n[b], tile - B.sfirst[b]);
+            if (threadIdx.x == 0) B.tsum[tile] = s;
+            if (last_arrival(&st->scan_ticket[SLOT_CDF], (uint32_t)ns)) {
+                const unsigned long long tot = sum_tiles(B.tsum + B.sfirst[b], ns);
+                if (threadIdx.x == 0) {
+                    st->scan_total[SLOT_CDF] = tot;
+                    st->scan_ticket[SLOT_CDF] = 0;
+                }
             }
         }
-    }
 }
 
 template <typename R, bool kStratified>
@@ -161,13 +164,14 @@ __global__ void __launch_bounds__(kBlock) batch_select_kernel(BatchArgs<R> B) {
     const int32_t t = B.bs->t;
     if (t < 0 || t >= B.tmax) return;
     const int nact = B.act_stiles[t];
-    for (int tile = blockIdx.x; tile < nact; tile += gridDim.x) {
-        const int b = B.stile_filter[tile];
-        DevState *st = &B.fst[b];
-        const DevState *sv = snapshot(st);
-        if (gated_out(sv, 1)) continue;
-        batch_select_tile<R, kStratified>(B, tile, b, st, sv);
-    }
+    for (int item = blockIdx.x; item * B.chunk < nact; item += gridDim.x)
+        for (int tile = item * B.chunk; tile < min(nact, (item + 1) * B.chunk); ++tile) {
+            const int b = B.stile_filter[tile];
+            DevState *st = &B.fst[b];
+            const DevState *sv = snapshot(st);
+            if (gated_out(sv, 1)) continue;
+            batch_select_tile<R, kStratified>(B, tile, b, st, sv);
+        }
 }
 
 __global__ void batch_reset_kernel(DevState *fst, int nf, BatchState *bs) {

@@ -37,6 +37,7 @@ struct PfArgs {
     int32_t gaussian;
     uint2 key;
     uint32_t stream;
+    uint32_t index0;     // Philox index of particle 0 (a shard of a larger filter: its first global index)
     // smc_iterate_host's graph (zero / null otherwise): the kernel is a
     // programmatic dependent of the kernel that stores the step's observation
     // (it waits for that grid just before reading y_t), and the record and
@@ -123,13 +124,13 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
         R z[4];
         zero[j] = R(0);
         if (t == 0) {
-            normals4_fast<R>(draw(a.key, i0 + j, 0u, TAG_INIT, a.stream, 0u), z);
+            normals4_fast<R>(draw(a.key, a.index0 + i0 + j, 0u, TAG_INIT, a.stream, 0u), z);
             s0[j] = a.sd_pos0 * z[0];
             s1[j] = a.sd_pos0 * z[1];
             s2[j] = a.sd_vel0 * z[2];
             s3[j] = a.sd_vel0 * z[3];
         } else {
-            normals4_fast<R>(draw(a.key, i0 + j, (uint32_t)t, TAG_MOVE, a.stream, 0u), z);
+            normals4_fast<R>(draw(a.key, a.index0 + i0 + j, (uint32_t)t, TAG_MOVE, a.stream, 0u), z);
             s0[j] = v0[j] + a.delta * v2[j] + a.sd_pos * z[0];
             s1[j] = v1[j] + a.delta * v3[j] + a.sd_pos * z[1];
             s2[j] = v2[j] + a.sd_vel * z[2];

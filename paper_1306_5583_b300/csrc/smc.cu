@@ -13,6 +13,7 @@
 
 #include "pf_kernels.cuh"
 #include "resample_kernels.cuh"
+#include "shard_kernels.cuh"
 #include "gmm_kernels.cuh"
 #include "batch_kernels.cuh"
 #include "grad_kernels.cuh"
@@ -55,7 +56,7 @@ int ceil_log2(int64_t n) {
 struct Layout {
     size_t st, rec, part, x, lw, anc, Q, tsum, bsum, inc, obs, obs_f, alpha;
     size_t dhist, drec, dtot;  // multinomial / residual draw histogram, bucket records, tile totals
-    size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, total;
+    size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, inpl, total;
     int ck;           // steps between checkpoints (record mode)
     int64_t nck;      // checkpoints
     int d;            // state rows
@@ -71,15 +72,19 @@ bool valid_config(const smc_config *c) {
     if (c->precision != 32 && c->precision != 64) return false;
     if (c->n_particles < 1 || c->n_particles > (int64_t(1) << 30)) return false;
     if (c->max_records < 2) return false;
-    if (c->scheme < SMC_MULTINOMIAL || c->scheme > SMC_RESIDUAL) return false;
+    if (c->scheme < SMC_MULTINOMIAL || c->scheme > SMC_RESIDUAL_STRATIFIED) return false;
     if (!(c->threshold == c->threshold)) return false;
     if (c->max_data < 1) return false;
+    if ((c->flags & SMC_FLAG_INPLACE) && (c->flags & SMC_FLAG_RECORD)) return false;  // the gradient needs sorted ancestors
     if (c->model == SMC_MODEL_GMM) {
         if (!kGmmEnabled) return false;
         if (c->gmm.n_comp < 1 || c->gmm.n_comp > kGmmMaxComp) return false;
         if (c->gmm.n_iter < 1 || c->gmm.shape0 < 1 || !(c->gmm.rate0 > 0) || !(c->gmm.sd0 > 0)) return false;
         if (c->gmm.move < SMC_GMM_RW || c->gmm.move > SMC_GMM_RW_MALA) return false;
         if (c->gmm.move != SMC_GMM_RW && !(c->gmm.mala_step > 0)) return false;
+        if (c->gmm.schedule < SMC_ALPHA_LINEAR || c->gmm.schedule > SMC_ALPHA_ADAPTIVE) return false;
+        if (c->gmm.schedule == SMC_ALPHA_ADAPTIVE && !(c->gmm.ess_target > 0.0 && c->gmm.ess_target < 1.0))
+            return false;
         if (c->max_data > kGmmMaxData) return false;
     } else {
         if (!(c->cv.obs_scale > 0) || !(c->cv.obs_df > 0)) return false;
@@ -137,6 +142,7 @@ Layout make_layout(const smc_config *c) {
     L.rep = take(rec ? 2 * 5 * row : 0);
     L.rep_part = take(rec ? sizeof(Partial) * (size_t)std::max<int64_t>(L.nbw, 1) : 0);
     L.scal = take(rec ? 256 : 0);
+    L.inpl = take((c->flags & SMC_FLAG_INPLACE) ? 2 * (size_t)L.ld * 4 : 0);  // extras and survivor flags
     L.total = off;
     return L;
 }
@@ -177,6 +183,8 @@ struct smc_ctx {
     cudaEvent_t ev_move[2]; // profiling: recorded around the move kernel in the iteration graph
     int dependent_launch;   // while capturing: launch the one-pass resampler as a programmatic dependent
     int no_dependent;       // the driver refused the programmatic dependent launch once: capture without
+    int64_t shard_n;        // a shard of a partitioned filter: the filter's N (0: not a shard)
+    int64_t shard_off;      // and the global index of the shard's first particle
 };
 
 namespace {
@@ -306,6 +314,11 @@ PfArgs<R> pf_args(smc_ctx *c) {
     set_obs_params(a, g.cv.obs_scale, g.cv.obs_df, g.model == SMC_MODEL_CV_GAUSS);
     a.key = key_of(c);
     a.stream = g.stream_id;
+    a.index0 = (uint32_t)c->shard_off;
+    if (c->shard_n) {  // equal weights after resampling are 1 / N of the whole filter
+        a.neg_log_n = R(-std::log((double)c->shard_n));
+        a.log_n = std::log((double)c->shard_n);
+    }
     a.obs_after_wait = 0;
     a.hio_out = c->capture_host_io ? c->hio_d : nullptr;
     return a;
@@ -344,6 +357,10 @@ int launch_post_mean(smc_ctx *c) {
 }
 
 unsigned long long *tsum_of(smc_ctx *c, int slot) { return c->tsum + (size_t)slot * c->L.ntiles; }
+
+// SMC_FLAG_INPLACE: the step's sorted ancestors rearranged in place
+// (inplace_kernel), one cooperative wave after each resampling step
+int launch_inplace(smc_ctx *c);
 
 // The ancestor output of the resampling kernels (and, while graph_host is
 // captured, the staging's error word for their failures).
@@ -438,20 +455,28 @@ int launch_grid_multinomial(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
 
 // One-pass residual resampling (grid_residual_kernel): one full wave; the
 // q, d and r tile sums in three scan slots, the block sums in three rows.
-template <typename R, class Sink>
+// kMode: the residual step (multinomial draws through the histogram, or the
+// systematic / stratified closed form over the R residual outputs).
+template <typename R, class Sink, int kMode = kResMultinomial>
 int launch_grid_residual(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
     const int64_t n = c->cfg.n_particles;
-    auto kern = grid_residual_kernel<R, Sink>;
+    auto kern = grid_residual_kernel<R, Sink, kMode>;
     static int per_sm[64] = {}, sms[64] = {};
     int slots = 0;
     if (int rc = coop_capacity(reinterpret_cast<const void *>(kern), per_sm, sms, &slots)) return rc;
     const int grid = std::max(1, std::min(slots, kMaxCoopGrid));
-    GridTargets<false> tg{};
-    tg.n = int64_t(1) << kHistValueBits;
+    ResidualTargets<kMode> tg{};
     tg.key = key_of(c);
     tg.stream = c->cfg.stream_id;
-    tg.c_fixed = 1ull << kHistValueBits;
-    tg.mrec = ~0ull >> kHistValueBits;
+    if (kMode == kResMultinomial) {
+        tg.n = int64_t(1) << kHistValueBits;
+        tg.c_fixed = 1ull << kHistValueBits;
+        tg.mrec = ~0ull >> kHistValueBits;
+    } else {
+        tg.n = n;  // replaced by R on the device
+        tg.c_fixed = 0;
+        tg.mrec = ~0ull / (unsigned long long)n;
+    }
     HistArgs h;
     h.hist = c->dhist;
     h.hrec = c->drec;
@@ -464,6 +489,60 @@ int launch_grid_residual(smc_ctx *c, const QGen<R> &qg, Sink sk, int gate) {
     rs.bd = c->bsum + kMaxCoopGrid;
     rs.br = c->bsum + 2 * kMaxCoopGrid;
     return launch_coop(c, grid, kern, qg, tg, anc_out(c), sk, n, rs, h, c->st, gate);
+}
+
+// q_i = floor(exp(lw_i - M) 2^F) over the context's log-weight buffers
+template <typename R>
+QGen<R> qgen_of(const smc_ctx *c) {
+    QGen<R> qg;
+    qg.lw[0] = static_cast<const R *>(c->lw[0]);
+    qg.lw[1] = static_cast<const R *>(c->lw[1]);
+    qg.frac = 61 - ceil_log2(c->cfg.n_particles);
+    qg.cur_lw = nullptr;
+    qg.m = 0;
+    return qg;
+}
+
+// the global outputs of a shard's particles (smc_shard_select)
+template <typename R, bool kS>
+int shard_select_t(smc_ctx *c, const uint64_t *d_totals, int32_t rank, int32_t world, int32_t *d_src,
+                   int64_t *d_range) {
+    const int64_t n = c->cfg.n_particles;
+    const unsigned tiles = (unsigned)((n + kScanTile - 1) / kScanTile);
+    QGen<R> qg = qgen_of<R>(c);
+    qg.frac = 61 - ceil_log2(c->shard_n);
+    GridTargets<kS> tg{};
+    tg.n = c->shard_n;
+    tg.key = key_of(c);
+    tg.stream = c->cfg.stream_id;
+    tg.mrec = ~0ull / (unsigned long long)c->shard_n;
+    shard_select_kernel<R, kS><<<tiles, kBlock, 0, c->stream>>>(
+        qg, tg, n, tsum_of(c, SLOT_CDF), reinterpret_cast<const unsigned long long *>(d_totals), rank, world, d_src,
+        d_range, c->st);
+    return cuda_check(cudaGetLastError());
+}
+
+int launch_inplace(smc_ctx *c) {
+    if (!(c->cfg.flags & SMC_FLAG_INPLACE)) return SMC_OK;
+    const int64_t n = c->cfg.n_particles;
+    const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+    static int per_sm[64] = {}, sms[64] = {};
+    int slots = 0;
+    if (int rc = coop_capacity(reinterpret_cast<const void *>(inplace_kernel), per_sm, sms, &slots)) return rc;
+    const int grid = std::max(1, std::min({ntiles, slots, kMaxCoopGrid}));
+    InplaceArgs ia;
+    ia.anc = c->anc;
+    ia.extra = reinterpret_cast<int32_t *>(c->ws + c->L.inpl);
+    ia.surv = ia.extra + c->L.ld;
+    ia.tf = tsum_of(c, 4);
+    ia.ts = tsum_of(c, 5);
+    ia.bf = c->bsum;
+    ia.bs = c->bsum + kMaxCoopGrid;
+    const int dep = c->dependent_launch;
+    c->dependent_launch = 0;  // an ordinary node after the resampler
+    const int rc = launch_coop(c, grid, inplace_kernel, ia, n, c->st);
+    c->dependent_launch = dep;
+    return rc;
 }
 
 template <typename R>
@@ -489,6 +568,12 @@ int launch_resample(smc_ctx *c, int gate) {
                         : launch_grid_multinomial<R>(c, qg, NoSink{}, gate);
         case SMC_RESIDUAL:
             return keep ? launch_grid_residual<R>(c, qg, qsink, gate) : launch_grid_residual<R>(c, qg, NoSink{}, gate);
+        case SMC_RESIDUAL_SYSTEMATIC:
+            return keep ? launch_grid_residual<R, StoreSink, kResSystematic>(c, qg, qsink, gate)
+                        : launch_grid_residual<R, NoSink, kResSystematic>(c, qg, NoSink{}, gate);
+        case SMC_RESIDUAL_STRATIFIED:
+            return keep ? launch_grid_residual<R, StoreSink, kResStratified>(c, qg, qsink, gate)
+                        : launch_grid_residual<R, NoSink, kResStratified>(c, qg, NoSink{}, gate);
         default:
             break;
     }
@@ -568,7 +653,7 @@ int record_after_resample(smc_ctx *c) {
 }
 
 int move_any(smc_ctx *c) {
-    if (!c->initialized) return SMC_E_STATE;
+    if (!c->initialized || c->shard_n) return SMC_E_STATE;
     if (c->cfg.model == SMC_MODEL_GMM) return gmm_move(c);
     if (c->t_host + 1 >= c->n_obs) return SMC_E_ARG;
     const int rc = (c->cfg.precision == 32) ? launch_pf<float>(c) : launch_pf<double>(c);
@@ -583,6 +668,7 @@ int launch_iteration(smc_ctx *c) {
     if (c->cfg.model == SMC_MODEL_GMM) {
         rc = gmm_launch_reweight(c);
         if (!rc) rc = resample_any(c, 1);
+        if (!rc) rc = launch_inplace(c);
         if (!rc) rc = gmm_launch_mcmc(c);
     } else {
         // external event records: captured as event-record nodes of the graph
@@ -594,6 +680,7 @@ int launch_iteration(smc_ctx *c) {
         if (!rc && c->ev_move[1])
             rc = cuda_check(cudaEventRecordWithFlags(c->ev_move[1], c->stream, cudaEventRecordExternal));
         if (!rc) rc = resample_any(c, 1);
+        if (!rc) rc = launch_inplace(c);
         if (!rc) rc = launch_post_mean(c);
     }
     return rc;
@@ -762,6 +849,7 @@ int smc_initialize(smc_ctx *c) {
     if (rc) return rc;
     c->initialized = 1;
     c->t_host = -1;
+    if (c->shard_n) return SMC_OK;  // a shard's first step (t = 0) is smc_shard_move and the rest of the exchange
     if (c->cfg.model == SMC_MODEL_GMM) {
         rc = gmm_initialize(c);
     } else {
@@ -771,6 +859,7 @@ int smc_initialize(smc_ctx *c) {
     }
     if (rc) return rc;
     rc = resample_any(c, 1);
+    if (!rc) rc = launch_inplace(c);
     if (!rc) rc = launch_post_mean(c);
     if (!rc) rc = record_after_resample(c);
     return rc;
@@ -783,8 +872,9 @@ int smc_move(smc_ctx *c) {
 
 int smc_resample(smc_ctx *c, int force) {
     if (!c) return SMC_E_ARG;
-    if (!c->initialized) return SMC_E_STATE;
+    if (!c->initialized || c->shard_n) return SMC_E_STATE;
     int rc = resample_any(c, force ? 0 : 1);
+    if (!rc) rc = launch_inplace(c);
     if (!rc) rc = launch_post_mean(c);
     return rc ? rc : record_after_resample(c);
 }
@@ -796,7 +886,7 @@ int smc_mcmc(smc_ctx *c) {
 
 int smc_iterate(smc_ctx *c, int32_t n) {
     if (!c || n < 0) return SMC_E_ARG;
-    if (!c->initialized) return SMC_E_STATE;
+    if (!c->initialized || c->shard_n) return SMC_E_STATE;
     // graph replay: every kernel reads the iteration index from the device
     // state, so one captured iteration serves every t (host bookkeeping and
     // the recording copies are not captured)
@@ -813,6 +903,7 @@ int smc_iterate(smc_ctx *c, int32_t n) {
     for (int32_t i = 0; i < n; ++i) {
         int rc = move_any(c);
         if (!rc) rc = resample_any(c, 1);
+        if (!rc) rc = launch_inplace(c);
         if (!rc) rc = launch_post_mean(c);
         if (!rc) rc = record_after_resample(c);
         if (!rc) rc = mcmc_any(c);
@@ -823,7 +914,7 @@ int smc_iterate(smc_ctx *c, int32_t n) {
 
 int smc_iterate_host(smc_ctx *c, const double *h_obs_t, smc_record *h_record) {
     if (!c || !h_record) return SMC_E_ARG;
-    if (!c->initialized) return SMC_E_STATE;
+    if (!c->initialized || c->shard_n) return SMC_E_STATE;
     const int32_t t = c->t_host + 1;
     const bool with_obs = h_obs_t && c->cfg.model != SMC_MODEL_GMM;
     if (with_obs && t >= c->cfg.max_data) return SMC_E_ARG;
@@ -1108,6 +1199,10 @@ int smc_restore(smc_ctx *c, const void *h_blob, size_t bytes) {
     if (!rc) rc = cuda_check(cudaMemcpyAsync(c->lw[s.cur_lw & 1], p, n * rs, cudaMemcpyHostToDevice, c->stream));
     p += n * rs;
     if (!rc) rc = cuda_check(cudaMemcpyAsync(c->anc, p, n * 4, cudaMemcpyHostToDevice, c->stream));
+    // an adaptive schedule lives on the device: its current alpha (kept in
+    // the state block) goes back into the schedule for the next iteration
+    if (!rc && c->cfg.model == SMC_MODEL_GMM && c->cfg.gmm.schedule == SMC_ALPHA_ADAPTIVE && h.t_host >= 0)
+        rc = cuda_check(cudaMemcpyAsync(c->alpha + h.t_host, &s.alpha, 8, cudaMemcpyHostToDevice, c->stream));
     if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream));
     if (rc) return rc;
     c->t_host = h.t_host;
@@ -1154,6 +1249,110 @@ int smc_wait_selftest(smc_ctx *c) {
     return cuda_check(cudaGetLastError());
 }
 
+// ---- one shard of a filter partitioned over ranks --------------------------
+
+int smc_shard_configure(smc_ctx *c, int64_t n_global, int64_t offset) {
+    if (!c) return SMC_E_ARG;
+    const smc_config &g = c->cfg;
+    if (g.model == SMC_MODEL_GMM || (g.scheme != SMC_SYSTEMATIC && g.scheme != SMC_STRATIFIED)) return SMC_E_ARG;
+    if (g.flags & (SMC_FLAG_RECORD | SMC_FLAG_INPLACE | SMC_FLAG_POST_MEAN)) return SMC_E_ARG;
+    if (offset < 0 || n_global < offset + g.n_particles || n_global > (int64_t(1) << 30)) return SMC_E_ARG;
+    c->shard_n = n_global;
+    c->shard_off = offset;
+    c->initialized = 0;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return SMC_OK;
+}
+
+int smc_shard_move(smc_ctx *c, void *d_partial) {
+    if (!c || !d_partial) return SMC_E_ARG;
+    if (!c->shard_n || !c->initialized) return SMC_E_STATE;
+    if (c->t_host + 1 >= c->n_obs) return SMC_E_ARG;
+    if (c->cfg.precision == 32)
+        pf_shard_move_kernel<float><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(pf_args<float>(c),
+                                                                                  static_cast<Partial *>(d_partial));
+    else
+        pf_shard_move_kernel<double><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(pf_args<double>(c),
+                                                                                   static_cast<Partial *>(d_partial));
+    const int rc = cuda_check(cudaGetLastError());
+    if (!rc) c->t_host += 1;
+    return rc;
+}
+
+int smc_shard_finalize(smc_ctx *c, const void *d_partials, int32_t world) {
+    if (!c || !d_partials || world < 1) return SMC_E_ARG;
+    if (!c->shard_n) return SMC_E_STATE;
+    const Partial *p = static_cast<const Partial *>(d_partials);
+    if (c->cfg.precision == 32)
+        pf_shard_finalize_kernel<float><<<1, kBlock, 0, c->stream>>>(pf_args<float>(c), p, world, c->shard_n);
+    else
+        pf_shard_finalize_kernel<double><<<1, kBlock, 0, c->stream>>>(pf_args<double>(c), p, world, c->shard_n);
+    return cuda_check(cudaGetLastError());
+}
+
+int smc_shard_total(smc_ctx *c, uint64_t *d_total) {
+    if (!c || !d_total) return SMC_E_ARG;
+    if (!c->shard_n) return SMC_E_STATE;
+    const int64_t n = c->cfg.n_particles;
+    const unsigned tiles = (unsigned)((n + kScanTile - 1) / kScanTile);
+    const int frac = 61 - ceil_log2(c->shard_n);
+    unsigned long long *tot = reinterpret_cast<unsigned long long *>(d_total);
+    if (c->cfg.precision == 32) {
+        QGen<float> qg = qgen_of<float>(c);
+        qg.frac = frac;
+        tile_reduce_kernel<QGen<float>><<<tiles, kBlock, 0, c->stream>>>(qg, n, tsum_of(c, SLOT_CDF), tot,
+                                                                          &c->st->scan_ticket[SLOT_CDF], c->st, 1);
+    } else {
+        QGen<double> qg = qgen_of<double>(c);
+        qg.frac = frac;
+        tile_reduce_kernel<QGen<double>><<<tiles, kBlock, 0, c->stream>>>(qg, n, tsum_of(c, SLOT_CDF), tot,
+                                                                           &c->st->scan_ticket[SLOT_CDF], c->st, 1);
+    }
+    return cuda_check(cudaGetLastError());
+}
+
+
+int smc_shard_select(smc_ctx *c, const uint64_t *d_totals, int32_t rank, int32_t world, int32_t *d_src,
+                     int64_t *d_range) {
+    if (!c || !d_totals || !d_src || !d_range || world < 1 || rank < 0 || rank >= world) return SMC_E_ARG;
+    if (!c->shard_n) return SMC_E_STATE;
+    const bool strat = c->cfg.scheme == SMC_STRATIFIED;
+    if (c->cfg.precision == 32)
+        return strat ? shard_select_t<float, true>(c, d_totals, rank, world, d_src, d_range)
+                     : shard_select_t<float, false>(c, d_totals, rank, world, d_src, d_range);
+    return strat ? shard_select_t<double, true>(c, d_totals, rank, world, d_src, d_range)
+                 : shard_select_t<double, false>(c, d_totals, rank, world, d_src, d_range);
+}
+
+int smc_shard_pack(smc_ctx *c, const int32_t *d_src, int64_t k_lo, int64_t count, void *d_send) {
+    if (!c || !d_src || k_lo < 0 || count < 0 || (count && !d_send)) return SMC_E_ARG;
+    if (!c->shard_n) return SMC_E_STATE;
+    if (!count) return SMC_OK;
+    const unsigned g = (unsigned)((count + kBlock - 1) / kBlock);
+    if (c->cfg.precision == 32)
+        shard_pack_kernel<float><<<g, kBlock, 0, c->stream>>>(pf_args<float>(c), d_src, k_lo, count,
+                                                              static_cast<float *>(d_send));
+    else
+        shard_pack_kernel<double><<<g, kBlock, 0, c->stream>>>(pf_args<double>(c), d_src, k_lo, count,
+                                                               static_cast<double *>(d_send));
+    return cuda_check(cudaGetLastError());
+}
+
+int smc_shard_unpack(smc_ctx *c, const void *d_recv) {
+    if (!c || !d_recv) return SMC_E_ARG;
+    if (!c->shard_n) return SMC_E_STATE;
+    const unsigned g = (unsigned)((c->cfg.n_particles + kBlock - 1) / kBlock);
+    if (c->cfg.precision == 32)
+        shard_unpack_kernel<float><<<g, kBlock, 0, c->stream>>>(pf_args<float>(c), static_cast<const float *>(d_recv));
+    else
+        shard_unpack_kernel<double><<<g, kBlock, 0, c->stream>>>(pf_args<double>(c),
+                                                                 static_cast<const double *>(d_recv));
+    return cuda_check(cudaGetLastError());
+}
+
 const char *smc_error_string(int code) {
     switch (code) {
         case SMC_OK: return "ok";
@@ -1194,6 +1393,7 @@ extern "C" int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], u
 namespace {
 
 double gmm_alpha(const smc_gmm_params &g, int32_t t) {
+    if (g.schedule == SMC_ALPHA_ADAPTIVE) return 0.0;  // alpha_0; the rest is chosen on the device
     const double x = (double)t / (double)g.n_iter;
     double a = (g.schedule == SMC_ALPHA_LINEAR) ? x : std::pow(x, g.power);
     return std::min(1.0, std::max(0.0, a));
@@ -1357,7 +1557,30 @@ int gmm_launch_any(smc_ctx *c, GmmKernel k) {
     return (c->cfg.precision == 32) ? gmm_launch<float>(c, k) : gmm_launch<double>(c, k);
 }
 
-int gmm_launch_reweight(smc_ctx *c) { return gmm_launch_any(c, GMM_REWEIGHT); }
+// SMC_ALPHA_ADAPTIVE: alpha_t of the coming iteration (gmm_alpha_kernel),
+// written into the schedule array before the reweighting reads it
+template <typename R>
+int gmm_launch_alpha(smc_ctx *c) {
+    static int per_sm[64] = {}, sms[64] = {};
+    int slots = 0;
+    if (int rc = coop_capacity(reinterpret_cast<const void *>(gmm_alpha_kernel<R>), per_sm, sms, &slots)) return rc;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)slots, c->L.nbw, (int64_t)kMaxCoopGrid}));
+    const double log_target = std::log(c->cfg.gmm.ess_target * (double)c->cfg.n_particles);
+    const int dep = c->dependent_launch;
+    c->dependent_launch = 0;  // the first kernel of the iteration: an ordinary node
+    const int rc = launch_coop(c, grid, gmm_alpha_kernel<R>, gmm_args<R>(c), (int32_t)(3 * c->cfg.gmm.n_comp + 1),
+                               log_target, c->alpha);
+    c->dependent_launch = dep;
+    return rc;
+}
+
+int gmm_launch_reweight(smc_ctx *c) {
+    if (c->cfg.gmm.schedule == SMC_ALPHA_ADAPTIVE) {
+        const int rc = (c->cfg.precision == 32) ? gmm_launch_alpha<float>(c) : gmm_launch_alpha<double>(c);
+        if (rc) return rc;
+    }
+    return gmm_launch_any(c, GMM_REWEIGHT);
+}
 int gmm_launch_mcmc(smc_ctx *c) { return gmm_launch_any(c, GMM_MCMC); }
 
 int gmm_initialize(smc_ctx *c) {
@@ -1368,7 +1591,7 @@ int gmm_initialize(smc_ctx *c) {
 
 int gmm_move(smc_ctx *c) {
     if (c->t_host + 1 > c->cfg.gmm.n_iter) return SMC_E_ARG;
-    const int rc = gmm_launch_any(c, GMM_REWEIGHT);
+    const int rc = gmm_launch_reweight(c);
     if (!rc) c->t_host += 1;
     return rc;
 }
@@ -1404,6 +1627,8 @@ bool batch_valid(const smc_config *cfg, const int64_t *n, const int32_t *T, int3
     if (cfg->model != SMC_MODEL_CV && cfg->model != SMC_MODEL_CV_GAUSS) return false;
     if (cfg->precision != 32 && cfg->precision != 64) return false;
     if (cfg->scheme != SMC_SYSTEMATIC && cfg->scheme != SMC_STRATIFIED) return false;
+    // per-context options the batched kernels do not implement
+    if (cfg->flags & (SMC_FLAG_RECORD | SMC_FLAG_POST_MEAN | SMC_FLAG_INPLACE)) return false;
     if (!(cfg->threshold == cfg->threshold) || !(cfg->cv.obs_scale > 0) || !(cfg->cv.obs_df > 0)) return false;
     for (int32_t b = 0; b < nf; ++b)
         if (n[b] < 1 || n[b] > (int64_t(1) << 30) || T[b] < 1) return false;
@@ -1516,8 +1741,9 @@ struct smc_batch {
     int32_t t_host;
     int initialized;
     int grid_per_sm;
+    int chunk;  // tiles per work item of the persistent kernels
     cudaGraphExec_t graph;
-    int graph_grid;
+    int graph_grid, graph_chunk;
     std::vector<int32_t> inv;  // caller -> internal
 };
 
@@ -1583,6 +1809,7 @@ BatchArgs<R> batch_args(smc_batch *bt) {
     B.frac = at<int32_t>(bt, P.o_frac);
     B.tmax = P.tmax;
     B.stratified = (g.scheme == SMC_STRATIFIED) ? 1 : 0;
+    B.chunk = bt->chunk;
     return B;
 }
 
@@ -1618,7 +1845,7 @@ int batch_reset_and_init(smc_batch *bt) {
 
 int batch_graph(smc_batch *bt) {
     const int grid = batch_grid(bt);
-    if (bt->graph && bt->graph_grid == grid) return SMC_OK;
+    if (bt->graph && bt->graph_grid == grid && bt->graph_chunk == bt->chunk) return SMC_OK;
     if (bt->graph) {
         cudaGraphExecDestroy(bt->graph);
         bt->graph = nullptr;
@@ -1638,6 +1865,7 @@ int batch_graph(smc_batch *bt) {
         return SMC_E_CUDA;
     }
     bt->graph_grid = grid;
+    bt->graph_chunk = bt->chunk;
     return SMC_OK;
 }
 
@@ -1683,6 +1911,7 @@ int smc_batch_create(smc_batch **out, const smc_config *cfg, const int64_t *n, c
     cudaGetDevice(&bt->device);
     cudaDeviceGetAttribute(&bt->nsm, cudaDevAttrMultiProcessorCount, bt->device);
     bt->grid_per_sm = 4;
+    bt->chunk = 1;
     bt->graph = nullptr;
     bt->graph_grid = 0;
     bt->t_host = -1;
@@ -1779,34 +2008,45 @@ int smc_batch_run(smc_batch *bt) {
     return smc_batch_iterate(bt, bt->P.tmax - 1);
 }
 
-int smc_batch_tune(smc_batch *bt, int32_t *blocks_per_sm) {
+int smc_batch_tune(smc_batch *bt, int32_t *blocks_per_sm, int32_t *tiles_per_item) {
     if (!bt) return SMC_E_ARG;
-    const int cand[4] = {1, 2, 4, 8};
+    // the launch shape of the persistent kernels: resident blocks per SM and
+    // consecutive tiles per work item (the tile itself, kPfTile particles of
+    // kPfItems per thread in blocks of kBlock threads, fixes the reduction
+    // order that makes every filter bit-identical to its plain run)
+    const int cand_g[6] = {1, 2, 3, 4, 6, 8};
+    const int cand_c[3] = {1, 2, 4};
     float best = 1e30f;
-    int best_g = bt->grid_per_sm;
+    int best_g = bt->grid_per_sm, best_c = bt->chunk;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SMC_E_CUDA;
-    const int reps = std::min(3, bt->P.tmax - 1);
-    for (int c : cand) {
-        bt->grid_per_sm = c;
-        int rc = batch_reset_and_init(bt);
-        if (rc) return rc;
-        cudaEventRecord(e0, bt->stream);
-        for (int r = 0; r < reps; ++r)
-            if ((rc = batch_iteration(bt, batch_grid(bt)))) return rc;
-        cudaEventRecord(e1, bt->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) return SMC_E_CUDA;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            best_g = c;
+    const int reps = std::min(10, bt->P.tmax - 1);
+    for (int c : cand_c) {
+        for (int g : cand_g) {
+            bt->grid_per_sm = g;
+            bt->chunk = c;
+            int rc = batch_reset_and_init(bt);
+            if (rc) return rc;
+            cudaEventRecord(e0, bt->stream);
+            for (int r = 0; r < reps; ++r)
+                if ((rc = batch_iteration(bt, batch_grid(bt)))) return rc;
+            cudaEventRecord(e1, bt->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return SMC_E_CUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_g = g;
+                best_c = c;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     bt->grid_per_sm = best_g;
+    bt->chunk = best_c;
     if (blocks_per_sm) *blocks_per_sm = best_g;
+    if (tiles_per_item) *tiles_per_item = best_c;
     return batch_reset_and_init(bt);
 }
 

@@ -14,9 +14,9 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsmc.so"
 OK, E_ARG, E_WORKSPACE, E_NONFINITE, E_TIMEOUT, E_CUDA, E_STATE, E_RANGE = range(8)
 MULTINOMIAL, STRATIFIED, SYSTEMATIC, RESIDUAL = range(4)
 SCHEMES = {"multinomial": MULTINOMIAL, "stratified": STRATIFIED, "systematic": SYSTEMATIC,
-           "residual": RESIDUAL}
+           "residual": RESIDUAL, "residual_systematic": RESIDUAL + 1, "residual_stratified": RESIDUAL + 2}
 MODEL_CV, MODEL_CV_GAUSS, MODEL_GMM = range(3)
-ALPHA_LINEAR, ALPHA_PRIOR = range(2)
+ALPHA_LINEAR, ALPHA_PRIOR, ALPHA_ADAPTIVE = range(3)
 GMM_RW, GMM_MALA, GMM_RW_MALA = range(3)
 
 
@@ -30,7 +30,7 @@ class GMMParams(ctypes.Structure):
     _fields_ = [("n_comp", ctypes.c_int32), ("schedule", ctypes.c_int32), ("n_iter", ctypes.c_int32),
                 ("shape0", ctypes.c_int32), ("power", ctypes.c_double), ("mu0", ctypes.c_double),
                 ("sd0", ctypes.c_double), ("rate0", ctypes.c_double), ("move", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("mala_step", ctypes.c_double)]
+                ("reserved", ctypes.c_int32), ("mala_step", ctypes.c_double), ("ess_target", ctypes.c_double)]
 
 
 class Config(ctypes.Structure):
@@ -96,6 +96,15 @@ _SIGS = {
                                              _P, _P]),
     "smc_resample_noalloc_status": (_I, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "smc_set_wait_limit": (_I, [ctypes.c_uint32]),
+    "smc_shard_configure": (_I, [_P, ctypes.c_int64, ctypes.c_int64]),
+    "smc_shard_move": (_I, [_P, _P]),
+    "smc_shard_finalize": (_I, [_P, _P, ctypes.c_int32]),
+    "smc_shard_total": (_I, [_P, _P]),
+    "smc_shard_select": (_I, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "smc_shard_pack": (_I, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P]),
+    "smc_shard_unpack": (_I, [_P, _P]),
+    "smc_mufu_rate": (_I, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double)]),
     "smc_wait_selftest": (_I, [_P]),
     "smc_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), _P, _P, ctypes.c_int32]),
     "smc_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Config), _P, _P, ctypes.c_int32, _P,
@@ -105,7 +114,7 @@ _SIGS = {
     "smc_batch_initialize": (_I, [_P]),
     "smc_batch_iterate": (_I, [_P, ctypes.c_int32]),
     "smc_batch_run": (_I, [_P]),
-    "smc_batch_tune": (_I, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "smc_batch_tune": (_I, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "smc_batch_log_evidence": (_I, [_P, _P]),
     "smc_batch_read_history": (_I, [_P, ctypes.c_int32, ctypes.POINTER(Record), ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]),
@@ -145,11 +154,12 @@ def check(code, where):
 FLAG_KEEP_CDF = 1
 FLAG_RECORD = 2
 FLAG_POST_MEAN = 4
+FLAG_INPLACE = 8
 
 
 def make_config(model="cv", n=1024, precision=32, scheme="systematic", threshold=0.5, seed=0, stream_id=0,
                 max_records=None, max_data=1000, cv=None, gmm=None, keep_cdf=True, record=False,
-                checkpoint_every=16, post_mean=False):
+                checkpoint_every=16, post_mean=False, inplace=False):
     c = Config()
     c.model = {"cv": MODEL_CV, "cv_gauss": MODEL_CV_GAUSS, "gmm": MODEL_GMM}[model]
     c.precision = precision
@@ -159,7 +169,7 @@ def make_config(model="cv", n=1024, precision=32, scheme="systematic", threshold
     c.seed = int(seed)
     c.stream_id = int(stream_id)
     c.flags = ((FLAG_KEEP_CDF if keep_cdf else 0) | (FLAG_RECORD if record else 0)
-               | (FLAG_POST_MEAN if post_mean else 0))
+               | (FLAG_POST_MEAN if post_mean else 0) | (FLAG_INPLACE if inplace else 0))
     c.checkpoint_every = int(checkpoint_every)
     c.max_data = int(max_data)
     c.max_records = int(max_records if max_records is not None else max(2, max_data + 1))
@@ -168,7 +178,7 @@ def make_config(model="cv", n=1024, precision=32, scheme="systematic", threshold
     for k, v in p.items():
         setattr(c.cv, k, float(v))
     g = dict(n_comp=4, schedule=ALPHA_PRIOR, n_iter=500, shape0=1, power=5.0, mu0=0.0, sd0=10.0, rate0=1.0,
-             move=GMM_RW, mala_step=0.05)
+             move=GMM_RW, mala_step=0.05, ess_target=0.5)
     g.update(gmm or {})
     for k, v in g.items():
         setattr(c.gmm, k, v)
@@ -381,6 +391,16 @@ class Sampler:
         check(lib().smc_restore(self.ctx, ctypes.cast(buf, _P), len(blob)), "smc_restore")
 
 
+def mufu_rate(kind=0, blocks_per_sm=8, iters=4096):
+    """(MUFU operations per second, ms) of the special-function pipe
+    microbenchmark on the current device (smc_mufu_rate; kind 0 alternating
+    ex2 / lg2, 1 ex2, 2 lg2)."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    check(lib().smc_mufu_rate(int(kind), int(blocks_per_sm), int(iters), ctypes.byref(ops), ctypes.byref(ms)),
+          "smc_mufu_rate")
+    return ops.value, ms.value
+
+
 def set_wait_limit(polls):
     """Polls a bounded device wait makes before raising SMC_E_TIMEOUT on the
     current device (0: the default, 2^24)."""
@@ -454,9 +474,10 @@ class Batch:
         check(lib().smc_batch_run(self.ctx), "smc_batch_run")
 
     def tune(self):
-        v = ctypes.c_int32()
-        check(lib().smc_batch_tune(self.ctx, ctypes.byref(v)), "smc_batch_tune")
-        return v.value
+        """(blocks per SM, tiles per work item) chosen by the autotuner."""
+        v, c = ctypes.c_int32(), ctypes.c_int32()
+        check(lib().smc_batch_tune(self.ctx, ctypes.byref(v), ctypes.byref(c)), "smc_batch_tune")
+        return v.value, c.value
 
     def log_evidence(self):
         out = np.empty(self.nf, dtype=np.float64)

@@ -52,8 +52,8 @@ def test_batch_tune_and_iterate_in_pieces():
     bt = smc.Batch(cfg, NS, TS)
     for b, T in enumerate(TS):
         bt.set_data(b, _data(T, 1 + b))
-    g = bt.tune()
-    assert g in (1, 2, 4, 8)
+    g, c = bt.tune()
+    assert g in (1, 2, 3, 4, 6, 8) and c in (1, 2, 4)
     bt.iterate(4)
     bt.iterate(max(TS) - 1 - 4)
     a = bt.log_evidence()
@@ -102,3 +102,25 @@ def test_batch_fp64_filters_match_the_oracle():
         assert_close(bt.state(b), last.x, 1e-10, f"final state of filter {b}")
         assert abs(lz[b] - ref[-1]["logZ"]) < 1e-9
     assert any_resampled
+
+
+def test_batch_launch_shapes_give_identical_results():
+    """Whatever launch shape the autotuner picks (blocks per SM, tiles per
+    work item), every filter's results are the same bit for bit: two
+    batches of the same filters, one tuned, one on the default shape."""
+    need_gpu()
+    cfg = smc.make_config(model="cv", n=1, precision=32, scheme="systematic", threshold=0.6, seed=9,
+                          max_data=max(TS), keep_cdf=False)
+    out = []
+    for tune in (False, True):
+        bt = smc.Batch(cfg, NS, TS)
+        for b, T in enumerate(TS):
+            bt.set_data(b, _data(T, 1 + b))
+        if tune:
+            bt.tune()
+        bt.run()
+        out.append((bt.log_evidence(), [bt.state(b) for b in range(len(NS))]))
+        bt.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    for a, b in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, b)

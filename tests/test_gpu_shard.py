@@ -1,0 +1,101 @@
+"""GPU: the device steps of the sharded filter (smc_shard_*).  Two or three
+shards of one filter in one process, advanced in lockstep with copies in
+place of the collectives (shard.run_local), against one context of the
+whole filter: when every step resamples the particle systems are
+identical bit for bit (the same Philox streams by global index, the same
+exact fixed-point selection), and the records agree to the rounding of the
+normaliser's summation order; with the ESS threshold they also match the
+FP64 oracle."""
+import numpy as np
+import pytest
+
+from gpu_common import need_gpu, oracle_params, torch
+from oracle import cv as ocv
+from paper_1306_5583_b300 import shard, smc, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _single(n, T, precision, scheme, threshold, seed, y):
+    cfg = smc.make_config(model="cv", n=n, precision=precision, scheme=scheme, threshold=threshold, seed=seed,
+                          max_data=T, keep_cdf=False)
+    s = smc.Sampler(cfg)
+    s.set_data(y)
+    s.initialize()
+    return s
+
+
+def _shards(n, world, T, precision, scheme, threshold, seed, y):
+    cfg = smc.make_config(model="cv", n=n, precision=precision, scheme=scheme, threshold=threshold, seed=seed,
+                          max_data=T, keep_cdf=False)
+    out = []
+    for r in range(world):
+        sh = shard.Shard(cfg, n, r, world)
+        sh.set_data(y)
+        sh.initialize()
+        out.append(sh)
+    return out
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("scheme", ["systematic", "stratified"])
+@pytest.mark.parametrize("n,world", [(5000, 2), (70001, 3)])
+def test_shards_equal_one_context_when_every_step_resamples(precision, scheme, n, world):
+    need_gpu()
+    T, seed = 8, 5
+    _, y = workloads.cv_data(T, seed=1, **workloads.CV_DEFAULT)
+    one = _single(n, T, precision, scheme, 1.0, seed, y)
+    shs = _shards(n, world, T, precision, scheme, 1.0, seed, y)
+    # after each step the shards hold the resampled copies (the exchange
+    # materialises them); the single context holds the weighted particles
+    # and the ancestors its next move gathers by
+    def resampled(s):
+        return s.state()[:, s.ancestors().astype(np.int64)]
+
+    recs = shard.run_local(shs, 1)  # t = 0
+    assert np.array_equal(np.concatenate([s.state() for s in shs], axis=1), resampled(one))
+    for t in range(1, T):
+        one.iterate(1)
+        recs += shard.run_local(shs, 1)
+        x = np.concatenate([s.state() for s in shs], axis=1)
+        assert np.array_equal(x, resampled(one)), t
+    ref = one.history(T)
+    tol = 1e-5 if precision == 32 else 1e-11
+    for r, o in zip(recs, ref):
+        assert r["t"] == o["t"] and r["resampled"] and o["resampled"]
+        assert r["max_lw"] == o["max_lw"]
+        assert abs(r["L"] - o["L"]) < tol and abs(r["logZ"] - o["logZ"]) < tol * T
+    for s in shs:
+        s.close()
+    one.close()
+
+
+def test_fp64_shards_with_the_ess_test_match_the_oracle():
+    need_gpu()
+    n, T, seed, thr = 3001, 30, 2, 0.5
+    _, y = workloads.cv_data(T, seed=0, **workloads.CV_DEFAULT)
+    shs = _shards(n, 2, T, 64, "systematic", thr, seed, y)
+    recs = shard.run_local(shs, T)
+    ref, last = ocv.run(y, n, seed, oracle_params(dict(workloads.CV_DEFAULT)), scheme="systematic", threshold=thr)
+    assert any(o["resampled"] for o in ref) and not all(o["resampled"] for o in ref)
+    for r, o in zip(recs, ref):
+        assert r["resampled"] == o["resampled"], r["t"]
+        assert abs(r["L"] - o["L"]) < 1e-9 and abs(r["logZ"] - o["logZ"]) < 1e-9
+        assert abs(r["mean_x"] - o["mean_x"]) < 1e-9
+    for s in shs:
+        s.close()
+
+
+def test_shard_refusals():
+    need_gpu()
+    cfg = smc.make_config(model="cv", n=100, precision=32, scheme="multinomial", max_data=4)
+    s = smc.Sampler(cfg)
+    assert smc.lib().smc_shard_configure(s.ctx, 200, 0) == smc.E_ARG   # scheme
+    cfg = smc.make_config(model="cv", n=100, precision=32, scheme="systematic", max_data=4)
+    s = smc.Sampler(cfg)
+    assert smc.lib().smc_shard_configure(s.ctx, 150, 60) == smc.E_ARG  # past the filter
+    assert smc.lib().smc_shard_configure(s.ctx, 200, 100) == smc.OK
+    s.set_data(np.zeros((4, 2)))
+    s.initialize()
+    with pytest.raises(smc.SMCError):
+        s.iterate(1)  # a shard moves only through the exchange
