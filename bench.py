@@ -243,6 +243,27 @@ def run_ours(args):
         return dict(step_ms=step_ms, move_ms=move_ms, graph_move_ms=graph_move_ms, wall_s=t_wall,
                     resample_frac=frac_res)
 
+    def full_run(scheme):
+        """The whole filter of T = 1000 observations as one smc_iterate(999)
+        on the replayed graph, CUDA events around it (no L2 flush between its
+        iterations: the run as a user makes it)."""
+        s = make(scheme)
+        with torch.cuda.stream(stream):
+            s.initialize()
+            s.iterate(1)  # captures the graph
+            s.initialize()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.iterate(T_OBS - 1)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            lz = s.log_evidence()
+        s.close()
+        return {"iterations": T_OBS - 1, "ms": ms, "us_per_iteration": ms * 1e3 / (T_OBS - 1),
+                "particle_updates_per_s": n * (T_OBS - 1) / (ms * 1e-3), "log_evidence": lz}
+
     headline = args.scheme
     with Clocks(local) as clk:
         main = timed(headline, args.steps, args.warmup)
@@ -256,6 +277,8 @@ def run_ours(args):
             move_us=float(np.mean(r["graph_move_ms"]) * 1e3),
             move_us_standalone=float(np.mean(r["move_ms"]) * 1e3),
             resample_fraction=r["resample_frac"])
+        if sc == headline:
+            per_scheme[sc]["full_run_T1000"] = full_run(sc)
     total_ms = max_over_ranks(float(np.sum(main["step_ms"])), dev)
     ms_per_step = total_ms / args.steps
     value = job_throughput(ws, n, ms_per_step)

@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
 // 2 delta l), a grid barrier, and the same fixed-order combine in every
 // block, so that every block takes the same decision and the midpoints are
 // float64 values computed identically everywhere.
-constexpr int kAdaptSteps = 40;
+constexpr int kAdaptSteps = 40;  // halvings
 
 template <typename R>
 struct AlphaPartial {  // one per block and evaluation
@@ -937,9 +937,16 @@ __device__ __forceinline__ bool alpha_cess_ge(const AlphaPartial<R> *part, int G
     }
 }
 
+// Candidates per grid barrier: the upper end of the interval (first round
+// only) and the seven midpoints of the next three halvings, evaluated
+// together; the walk down that subtree takes exactly the decisions that
+// three sequential halvings would take, on the same float64 midpoints.
+constexpr int kAdaptLevels = 3;
+constexpr int kAdaptCand = (1 << kAdaptLevels);  // 7 midpoints + the upper end
+
 template <typename R>
 __global__ void __launch_bounds__(kBlock, 4) gmm_alpha_kernel(GmmArgs<R> a, int32_t ll_row, double log_target,
-                                                              double *alpha_out) {
+                                                              double *alpha_out, AlphaPartial<R> *part) {
     DevState *st = a.st;
     const DevState *sv = snapshot(st, true);
     if (sv->error) return;
@@ -958,7 +965,7 @@ __global__ void __launch_bounds__(kBlock, 4) gmm_alpha_kernel(GmmArgs<R> a, int3
     __syncthreads();
     const Shift<R> base(s_k[0], s_k[1]);
     // the thread's first kMax particles kept in registers, the rest read
-    // again at every evaluation
+    // again at every round
     constexpr int kMax = 4;
     R lwk[kMax], llk[kMax];
 #pragma unroll
@@ -968,99 +975,123 @@ __global__ void __launch_bounds__(kBlock, 4) gmm_alpha_kernel(GmmArgs<R> a, int3
         llk[j] = (i < i_hi) ? ll[i] : R(0);
     }
     const int64_t i_rest = i_lo + threadIdx.x + (int64_t)kMax * kBlock;
-    AlphaPartial<R> *part = reinterpret_cast<AlphaPartial<R> *>(a.part);
-    __shared__ R s_red[4][kBlock / 32];
-    __shared__ int s_ge;
+    __shared__ double s_d[kAdaptCand];       // the round's candidates
+    __shared__ R s_red[4][kAdaptCand][kBlock / 32];
+    __shared__ int s_ge[kAdaptCand];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double log_n = log(double(a.n));
     double lo = 0.0, hi = 1.0 - a_prev, delta = 0.0;
     bool done = !(hi > 0.0);
+    int levels = 0;  // halvings taken
     uint32_t barriers = 0;
-    for (int step = -1; step < kAdaptSteps && !done; ++step) {
-        const double d = (step < 0) ? hi : 0.5 * (lo + hi);
-        const R dr = R(d), d2 = R(2.0 * d);
-        // block partial: maxima, then sums of exp relative to them
-        R mx = Math<R>::neg_inf(), my = Math<R>::neg_inf();
-#pragma unroll
-        for (int j = 0; j < kMax; ++j) {
-            mx = fmax(mx, lwk[j] + dr * llk[j]);
-            my = fmax(my, lwk[j] + d2 * llk[j]);
-        }
-        for (int64_t i = i_rest; i < i_hi; i += kBlock) {
-            const R w = base.sub_from(lw_in[i]), l = ll[i];
-            mx = fmax(mx, w + dr * l);
-            my = fmax(my, w + d2 * l);
-        }
-        mx = warp_max(mx);
-        my = warp_max(my);
-        if (lane == 0) {
-            s_red[0][warp] = mx;
-            s_red[1][warp] = my;
+    while (!done && levels < kAdaptSteps) {
+        const bool first = (barriers == 0);
+        // candidates: the subtree's midpoints in heap order (0; 1, 2; 3..6),
+        // each the midpoint of its interval as a sequential halving computes
+        // it; slot 7 the upper end in the first round
+        if (threadIdx.x == 0) {
+            double m[7];
+            m[0] = 0.5 * (lo + hi);
+            m[1] = 0.5 * (lo + m[0]);
+            m[2] = 0.5 * (m[0] + hi);
+            m[3] = 0.5 * (lo + m[1]);
+            m[4] = 0.5 * (m[1] + m[0]);
+            m[5] = 0.5 * (m[0] + m[2]);
+            m[6] = 0.5 * (m[2] + hi);
+            for (int c = 0; c < 7; ++c) s_d[c] = m[c];
+            s_d[7] = hi;
         }
         __syncthreads();
-        mx = s_red[0][0];
-        my = s_red[1][0];
+        AlphaPartial<R> *pe = part + (size_t)(barriers & 1u) * kAdaptCand * (size_t)G;
+#pragma unroll 1
+        for (int c = 0; c < kAdaptCand; ++c) {
+            if (c == 7 && !first) break;
+            const R dr = R(s_d[c]), d2 = R(2.0 * s_d[c]);
+            R mx = Math<R>::neg_inf(), my = Math<R>::neg_inf();
 #pragma unroll
-        for (int w = 1; w < kBlock / 32; ++w) {
-            mx = fmax(mx, s_red[0][w]);
-            my = fmax(my, s_red[1][w]);
-        }
-        R sx = R(0), sy = R(0);
-        if (mx > Math<R>::neg_inf()) {
-#pragma unroll
-            for (int j = 0; j < kMax; ++j)
-                if (lwk[j] > Math<R>::neg_inf()) {
-                    sx += Math<R>::fast_exp(lwk[j] + dr * llk[j] - mx);
-                    sy += Math<R>::fast_exp(lwk[j] + d2 * llk[j] - my);
-                }
+            for (int j = 0; j < kMax; ++j) {
+                mx = fmax(mx, lwk[j] + dr * llk[j]);
+                my = fmax(my, lwk[j] + d2 * llk[j]);
+            }
             for (int64_t i = i_rest; i < i_hi; i += kBlock) {
                 const R w = base.sub_from(lw_in[i]), l = ll[i];
-                if (w > Math<R>::neg_inf()) {
-                    sx += Math<R>::fast_exp(w + dr * l - mx);
-                    sy += Math<R>::fast_exp(w + d2 * l - my);
+                mx = fmax(mx, w + dr * l);
+                my = fmax(my, w + d2 * l);
+            }
+            mx = warp_max(mx);
+            my = warp_max(my);
+            if (lane == 0) {
+                s_red[0][c][warp] = mx;
+                s_red[1][c][warp] = my;
+            }
+            __syncthreads();
+            mx = s_red[0][c][0];
+            my = s_red[1][c][0];
+#pragma unroll
+            for (int w = 1; w < kBlock / 32; ++w) {
+                mx = fmax(mx, s_red[0][c][w]);
+                my = fmax(my, s_red[1][c][w]);
+            }
+            R sx = R(0), sy = R(0);
+            if (mx > Math<R>::neg_inf()) {
+#pragma unroll
+                for (int j = 0; j < kMax; ++j)
+                    if (lwk[j] > Math<R>::neg_inf()) {
+                        sx += Math<R>::fast_exp(lwk[j] + dr * llk[j] - mx);
+                        sy += Math<R>::fast_exp(lwk[j] + d2 * llk[j] - my);
+                    }
+                for (int64_t i = i_rest; i < i_hi; i += kBlock) {
+                    const R w = base.sub_from(lw_in[i]), l = ll[i];
+                    if (w > Math<R>::neg_inf()) {
+                        sx += Math<R>::fast_exp(w + dr * l - mx);
+                        sy += Math<R>::fast_exp(w + d2 * l - my);
+                    }
                 }
             }
-        }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        if (lane == 0) {
-            s_red[2][warp] = sx;
-            s_red[3][warp] = sy;
-        }
-        __syncthreads();
-        // partials of consecutive evaluations alternate between two halves:
-        // a block writing evaluation e + 2 has passed the barrier of e + 1,
-        // which every block reaches only after reading the partials of e
-        AlphaPartial<R> *pe = part + (size_t)(barriers & 1u) * (size_t)G;
-        if (threadIdx.x == 0) {
-            R tx = R(0), ty = R(0);
-#pragma unroll
-            for (int w = 0; w < kBlock / 32; ++w) {
-                tx += s_red[2][w];
-                ty += s_red[3][w];
+            sx = warp_sum(sx);
+            sy = warp_sum(sy);
+            if (lane == 0) {
+                s_red[2][c][warp] = sx;
+                s_red[3][c][warp] = sy;
             }
-            pe[b] = AlphaPartial<R>{mx, tx, my, ty};
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                R tx = R(0), ty = R(0);
+#pragma unroll
+                for (int w = 0; w < kBlock / 32; ++w) {
+                    tx += s_red[2][c][w];
+                    ty += s_red[3][c][w];
+                }
+                // partials of consecutive rounds alternate between two
+                // halves: a block writing round e + 2 has passed the barrier
+                // of e + 1, reached by every block after it read round e
+                pe[(size_t)c * G + b] = AlphaPartial<R>{mx, tx, my, ty};
+            }
         }
         ++barriers;
         if (!grid_barrier(st, barriers * (uint32_t)G)) return;
-        // every block: the same combine in the same order
-        if (warp == 0) {
-            const bool ge = alpha_cess_ge<R>(pe, G, log_n, log_target);
-            if (lane == 0) s_ge = ge ? 1 : 0;
+        // every block: the same combines in the same order, one warp per candidate
+        if (warp < kAdaptCand && (warp < 7 || first)) {
+            const bool ge = alpha_cess_ge<R>(pe + (size_t)warp * G, G, log_n, log_target);
+            if (lane == 0) s_ge[warp] = ge ? 1 : 0;
         }
         __syncthreads();
-        const bool ge = s_ge != 0;
-        if (step < 0) {
-            if (ge) {
-                delta = hi;
-                done = true;
-            }
-        } else if (ge) {
-            lo = d;
+        if (first && s_ge[7]) {
+            delta = hi;
+            done = true;
         } else {
-            hi = d;
+            // walk the subtree: at node k the answer sends the interval to
+            // [mid, hi] (CESS still at least the target) or [lo, mid]
+            int k = 0;
+            for (int l = 0; l < kAdaptLevels && levels < kAdaptSteps; ++l, ++levels) {
+                const double mid = s_d[k];
+                const bool ge = s_ge[k] != 0;
+                if (ge) lo = mid;
+                else hi = mid;
+                k = 2 * k + (ge ? 2 : 1);
+            }
         }
-        __syncthreads();  // s_red and s_ge are reused by the next evaluation
+        __syncthreads();  // s_d, s_red and s_ge are reused by the next round
     }
     if (!done) delta = lo;
     if (b == 0 && threadIdx.x == 0) alpha_out[t] = fmin(1.0, a_prev + delta);

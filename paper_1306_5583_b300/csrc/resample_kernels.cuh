@@ -73,14 +73,21 @@ __device__ __forceinline__ void gen_items(const Gen &g, int64_t i0, int64_t n, u
     }
 }
 
+// A 64-bit integer as a float from its 32-bit halves: the 64-bit
+// integer <-> float conversions run on the FP64 pipe (1/64 of the FP32
+// rate on B300); the result is within a few float ulps, for estimates.
+__device__ __forceinline__ float u64_to_float(unsigned long long x) {
+    return fmaf(__uint2float_rn((uint32_t)(x >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)x));
+}
+
 // floor(n q / qn) for q <= qn < 2^62, n < 2^31 (exact: float estimate from
 // inv_qn ~ 1 / qn, then integer correction with 128-bit products)
 __device__ __forceinline__ unsigned long long floor_nq_over(unsigned long long n, unsigned long long q,
                                                             unsigned long long qn, float inv_qn) {
     if (qn == 0 || q > qn) return 0;
     const U128 num = mul64(n, q);
-    float est = float(n) * float(q) * inv_qn;
-    unsigned long long d = (unsigned long long)fmaxf(est, 0.0f);
+    const float est = u64_to_float(n) * u64_to_float(q) * inv_qn;  // below 2^31 + rounding
+    unsigned long long d = (unsigned long long)__float2uint_rz(fminf(fmaxf(est, 0.0f), 4294967040.0f));
     if (d > n) d = n;
     while (d > 0 && gt128(mul64(d, qn), num)) --d;
     while (!gt128(mul64(d + 1, qn), num)) ++d;
@@ -1222,7 +1229,7 @@ __device__ __forceinline__ void residual_items(const TileBufs &tb, unsigned long
                                                unsigned long long (&r)[kScanItems]) {
     const int base = threadIdx.x * kScanItems;
     unsigned long long prev = base ? tb.q[pad8(base - 1)] : 0ull;
-    const float inv_qn = QN ? __fdividef(1.0f, float(QN)) : 0.0f;  // the estimate's error is corrected exactly
+    const float inv_qn = QN ? __fdividef(1.0f, u64_to_float(QN)) : 0.0f;  // the estimate's error is corrected exactly
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const unsigned long long qc = tb.q[pad8(base + j)];

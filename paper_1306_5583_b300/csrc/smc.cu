@@ -56,7 +56,7 @@ int ceil_log2(int64_t n) {
 struct Layout {
     size_t st, rec, part, x, lw, anc, Q, tsum, bsum, inc, obs, obs_f, alpha;
     size_t dhist, drec, dtot;  // multinomial / residual draw histogram, bucket records, tile totals
-    size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, inpl, total;
+    size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, inpl, adapt, total;
     int ck;           // steps between checkpoints (record mode)
     int64_t nck;      // checkpoints
     int d;            // state rows
@@ -143,6 +143,10 @@ Layout make_layout(const smc_config *c) {
     L.rep_part = take(rec ? sizeof(Partial) * (size_t)std::max<int64_t>(L.nbw, 1) : 0);
     L.scal = take(rec ? 256 : 0);
     L.inpl = take((c->flags & SMC_FLAG_INPLACE) ? 2 * (size_t)L.ld * 4 : 0);  // extras and survivor flags
+    // adaptive tempering: two rounds of candidate partials per block
+    L.adapt = take((c->model == SMC_MODEL_GMM && c->gmm.schedule == SMC_ALPHA_ADAPTIVE)
+                       ? 2 * (size_t)kAdaptCand * kMaxCoopGrid * sizeof(AlphaPartial<double>)
+                       : 0);
     L.total = off;
     return L;
 }
@@ -1569,7 +1573,7 @@ int gmm_launch_alpha(smc_ctx *c) {
     const int dep = c->dependent_launch;
     c->dependent_launch = 0;  // the first kernel of the iteration: an ordinary node
     const int rc = launch_coop(c, grid, gmm_alpha_kernel<R>, gmm_args<R>(c), (int32_t)(3 * c->cfg.gmm.n_comp + 1),
-                               log_target, c->alpha);
+                               log_target, c->alpha, reinterpret_cast<AlphaPartial<R> *>(c->ws + c->L.adapt));
     c->dependent_launch = dep;
     return rc;
 }

@@ -3,6 +3,9 @@
     python -m paper_1306_5583_b300.profile_case pf   --n 1048576 --iters 4 --threshold 1.0
     python -m paper_1306_5583_b300.profile_case step --n 1048576 --iters 4 --threshold 1.0
     python -m paper_1306_5583_b300.profile_case gmm  --n 65536 --iters 3 --move rw
+    python -m paper_1306_5583_b300.profile_case gmm  --n 65536 --iters 3 --schedule adaptive
+    python -m paper_1306_5583_b300.profile_case pf   --n 1048576 --iters 4 --scheme residual_systematic
+    python -m paper_1306_5583_b300.profile_case pf   --n 1048576 --iters 4 --inplace
     python -m paper_1306_5583_b300.profile_case grad --n 262144 --iters 40
     python -m paper_1306_5583_b300.profile_case batch --count 64 --iters 20
 
@@ -22,7 +25,7 @@ def pf(a):
     T = a.iters + 2
     _, y = workloads.cv_data(T, seed=0, **p)
     cfg = smc.make_config(model="cv", n=a.n, precision=32, scheme=a.scheme, threshold=a.threshold, seed=1,
-                          max_data=T, cv=p, keep_cdf=False)
+                          max_data=T, cv=p, keep_cdf=False, inplace=a.inplace)
     s = smc.Sampler(cfg)
     s.set_data(y)
     s.initialize()
@@ -53,9 +56,10 @@ def step(a):
 def gmm(a):
     y = workloads.gmm_data(1000, seed=0)
     mv = {"rw": smc.GMM_RW, "mala": smc.GMM_MALA, "rw_mala": smc.GMM_RW_MALA}[a.move]
+    sched = {"prior": smc.ALPHA_PRIOR, "adaptive": smc.ALPHA_ADAPTIVE}[a.schedule]
     cfg = smc.make_config(model="gmm", n=a.n, precision=32, scheme="systematic", threshold=0.5, seed=1,
                           max_data=1000, max_records=a.iters + 2,
-                          gmm=dict(n_comp=4, n_iter=500, move=mv, mala_step=0.05))
+                          gmm=dict(n_comp=4, n_iter=500, move=mv, mala_step=0.05, schedule=sched))
     s = smc.Sampler(cfg)
     s.set_data(y)
     s.initialize()
@@ -99,6 +103,8 @@ def main():
     ap.add_argument("--threshold", type=float, default=1.0)
     ap.add_argument("--scheme", default="systematic")
     ap.add_argument("--move", default="rw")
+    ap.add_argument("--schedule", default="prior", choices=["prior", "adaptive"])
+    ap.add_argument("--inplace", action="store_true")
     ap.add_argument("--count", type=int, default=64)
     a = ap.parse_args()
     v = {"pf": pf, "step": step, "gmm": gmm, "grad": grad, "batch": batch}[a.case](a)
