@@ -334,6 +334,7 @@ def run_ours(args):
         out["cpu_baseline"] = cpu_baseline(n, 8)
         if not args.no_extra:
             out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(n, 8)
+            out["cpu_baseline"]["other_configs"] = oracle_baselines()
     if rank == 0 and not args.no_extra:
         extra = {}
         mufu = mufu_peak(dev)
@@ -737,6 +738,50 @@ def cpu_baseline_all_cores(n, iters):
     return {"value": n * iters / dt, "unit": "particle-updates/s", "cores": cores, "kind": "oracle",
             "sample": f"{iters} iterations at N={n}: move and weight in {cores} spawned worker processes over "
                       f"particle blocks, normaliser and exact integer resampling in the parent"}
+
+
+def oracle_baselines():
+    """The FP64 oracle (numpy, one process) on bounded samples of the other
+    configurations, in particle-updates per second: config 0 in full
+    (N = 1000, T = 100); the GMM sampler (configs 2, 3a) on one iteration at
+    N = 2^12 late in the schedule (each particle-update costs the same at
+    any N); the gradient (config 3b) on a recorded forward run plus its
+    reverse sweep at N = 2^10, T = 50; the batched filters (config 4) run
+    the particle filter's arithmetic, whose rate the config-1 baseline
+    gives."""
+    from oracle import cv as ocv
+    from oracle import gmm as ogmm
+    from oracle import grad as ograd
+    from oracle import resample as ores
+    from paper_1306_5583_b300 import workloads
+    p = dict(workloads.CV_DEFAULT)
+    op = ocv.CVParams(**p)
+    out = {}
+    _, y = workloads.cv_data(100, seed=0, **p)
+    t0 = time.perf_counter()
+    ocv.run(y, 1000, 0, op, scheme="systematic", threshold=0.5)
+    out["config0_fp64_n1000_T100"] = {"value": 1000 * 99 / (time.perf_counter() - t0), "sample": "the whole run"}
+    yg = workloads.gmm_data(1000, seed=0)
+    gp = ogmm.GMMParams(r=4, T=500, power=5.0)
+    n = 1 << 12
+    for move in ("rw", "mala"):
+        st = ogmm.init_state(n, yg, 1, gp)
+        t, a_t = 450, ogmm.alpha(450, gp)
+        t0 = time.perf_counter()
+        if move == "rw":
+            ogmm.mcmc(st, a_t, t, yg, 1, gp)
+        else:
+            ogmm.mala_step(st, a_t, t, yg, 1, gp, eps=0.05)
+        out[f"gmm_{move}"] = {"value": n / (time.perf_counter() - t0),
+                              "sample": f"one {move} move of N = {n} at t = {t}, n = 1000, r = 4"}
+    _, yc = workloads.cv_data(50, seed=0, **p)
+    t0 = time.perf_counter()
+    anc = ograd.base_run(yc, 1 << 10, 1, op)
+    ograd.gradient(yc, 1 << 10, 1, op, anc)
+    out["pf_grad"] = {"value": (1 << 10) * 50 / (time.perf_counter() - t0),
+                      "sample": "recorded forward run and reverse sweep, N = 2^10, T = 50 (forward + gradient "
+                                "per particle-update)"}
+    return out
 
 
 def run_reference(args):

@@ -892,8 +892,10 @@ struct AlphaPartial {  // one per block and evaluation
 // log CESS - log(rho N) >= 0 from the block partials, by one warp (lane 0
 // receives the answer): float64 on the FP64 path, double-float sums and
 // logarithms on the FP32 path (no float64 arithmetic there).
+// ln_rel = log N - log(rho N) as a double-float (hi, lo) value
 template <typename R>
-__device__ __forceinline__ bool alpha_cess_ge(const AlphaPartial<R> *part, int G, double log_n, double log_target) {
+__device__ __forceinline__ bool alpha_cess_ge(const AlphaPartial<R> *part, int G, double log_n, double log_target,
+                                              DF ln_rel) {
     const int lane = threadIdx.x & 31;
     R MX = Math<R>::neg_inf(), MY = Math<R>::neg_inf();
     for (int q = lane; q < G; q += 32) {
@@ -930,9 +932,7 @@ __device__ __forceinline__ bool alpha_cess_ge(const AlphaPartial<R> *part, int G
         DF v = df_add(df_add_f(df_add(df_log(ax), df_log(ax)), 2.0f * MX), DF{-MY, 0.0f});
         const DF lb = df_log(ay);
         v = df_add(v, DF{-lb.hi, -lb.lo});
-        const float ln_hi = float(log_n - log_target);
-        const float ln_lo = float((log_n - log_target) - double(ln_hi));
-        v = df_add(v, DF{ln_hi, ln_lo});
+        v = df_add(v, ln_rel);
         return v.hi >= 0.0f;
     }
 }
@@ -976,10 +976,22 @@ __global__ void __launch_bounds__(kBlock, 4) gmm_alpha_kernel(GmmArgs<R> a, int3
     }
     const int64_t i_rest = i_lo + threadIdx.x + (int64_t)kMax * kBlock;
     __shared__ double s_d[kAdaptCand];       // the round's candidates
+    __shared__ R s_dr[2][kAdaptCand];          // and their float conversions (d, 2d), made once per block
     __shared__ R s_red[4][kAdaptCand][kBlock / 32];
     __shared__ int s_ge[kAdaptCand];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double log_n = log(double(a.n));
+    // float64 constants computed once per block (float64 is 1/64 of the
+    // FP32 rate on B300)
+    __shared__ DF s_ln;
+    __shared__ double s_logn;
+    if (threadIdx.x == 0) {
+        s_logn = log(double(a.n));
+        const float h = float(s_logn - log_target);
+        s_ln = DF{h, float((s_logn - log_target) - double(h))};
+    }
+    __syncthreads();
+    const double log_n = s_logn;
+    const DF ln_rel = s_ln;
     double lo = 0.0, hi = 1.0 - a_prev, delta = 0.0;
     bool done = !(hi > 0.0);
     int levels = 0;  // halvings taken
@@ -1000,13 +1012,17 @@ __global__ void __launch_bounds__(kBlock, 4) gmm_alpha_kernel(GmmArgs<R> a, int3
             m[6] = 0.5 * (m[2] + hi);
             for (int c = 0; c < 7; ++c) s_d[c] = m[c];
             s_d[7] = hi;
+            for (int c = 0; c < kAdaptCand; ++c) {
+                s_dr[0][c] = R(s_d[c]);
+                s_dr[1][c] = R(2.0 * s_d[c]);
+            }
         }
         __syncthreads();
         AlphaPartial<R> *pe = part + (size_t)(barriers & 1u) * kAdaptCand * (size_t)G;
 #pragma unroll 1
         for (int c = 0; c < kAdaptCand; ++c) {
             if (c == 7 && !first) break;
-            const R dr = R(s_d[c]), d2 = R(2.0 * s_d[c]);
+            const R dr = s_dr[0][c], d2 = s_dr[1][c];
             R mx = Math<R>::neg_inf(), my = Math<R>::neg_inf();
 #pragma unroll
             for (int j = 0; j < kMax; ++j) {
@@ -1072,7 +1088,7 @@ __global__ void __launch_bounds__(kBlock, 4) gmm_alpha_kernel(GmmArgs<R> a, int3
         if (!grid_barrier(st, barriers * (uint32_t)G)) return;
         // every block: the same combines in the same order, one warp per candidate
         if (warp < kAdaptCand && (warp < 7 || first)) {
-            const bool ge = alpha_cess_ge<R>(pe + (size_t)warp * G, G, log_n, log_target);
+            const bool ge = alpha_cess_ge<R>(pe + (size_t)warp * G, G, log_n, log_target, ln_rel);
             if (lane == 0) s_ge[warp] = ge ? 1 : 0;
         }
         __syncthreads();
