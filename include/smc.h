@@ -219,7 +219,16 @@ int smc_resample(smc_ctx *ctx, int force);
 int smc_mcmc(smc_ctx *ctx);
 
 /* Sampler::iterate: n iterations of (move, resample, mcmc), replayed from a
- * captured CUDA graph. */
+ * captured CUDA graph (on a non-default stream, without SMC_FLAG_RECORD):
+ * whole chunks of 8 iterations per graph launch, the rest one iteration per
+ * launch.  Called while the caller is capturing the context's stream (a
+ * particle filter whose one-iteration graph exists, i.e. after one earlier
+ * smc_iterate on that stream), the n iterations' kernels are recorded into
+ * the caller's graph instead, and the context counts them as run: the caller
+ * owns the replays, and an iteration replayed past the observation buffer
+ * (max_data rows) raises SMC_E_RANGE on the device and runs nothing.
+ * SMC_E_STATE for a capture otherwise (a GMM sampler, SMC_FLAG_RECORD, no
+ * graph yet, an invalidated capture). */
 int smc_iterate(smc_ctx *ctx, int32_t n);
 
 /* One iteration with host buffers: copies obs_t (CV: 2 float64; may be NULL

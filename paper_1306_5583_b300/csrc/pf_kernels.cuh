@@ -44,6 +44,9 @@ struct PfArgs {
     // error word go to the staging in mapped host memory
     int32_t obs_after_wait;
     HostIO *hio_out;
+    // rows of the observation buffer: an iteration past it (a caller's graph
+    // replayed more often than the data allow) raises SMC_E_RANGE
+    int32_t obs_cap;
 };
 
 // log g(Y_t | X_t): full Student-t (or Gaussian) density of both position
@@ -213,6 +216,13 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 4) pf_iterate_ker
         return;
     }
     const int32_t t = sv->t + 1;
+    if (t >= a.obs_cap) {  // the same in every block: nothing runs
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            raise_error(st, SMC_E_RANGE);
+            if (a.hio_out) a.hio_out->status = SMC_E_RANGE;
+        }
+        return;
+    }
     const int cur = sv->cur, cur_lw = sv->cur_lw;
     const bool gather = (t > 0) && (sv->ready != 0);
     pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part, src);

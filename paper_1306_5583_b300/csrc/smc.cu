@@ -44,6 +44,7 @@ __global__ void to_float_kernel(const double *src, float *dst, int64_t n) {
     if (i < n) dst[i] = (float)src[i];
 }
 constexpr int kMaxCoopGrid = 2048;  // blocks of a cooperative launch (B300: at most 148 x 8)
+constexpr int kIterChunk = 8;       // iterations per graph launch of smc_iterate (n >= kIterChunk)
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -183,6 +184,7 @@ struct smc_ctx {
     HostIO *hio;            // smc_iterate_host's staging: pinned, mapped (host address)
     HostIO *hio_d;          // the same buffer's device address
     cudaGraphExec_t graph_host;  // one iteration reading and writing the staging (smc_iterate_host)
+    cudaGraphExec_t graph_chunk; // kIterChunk iterations in one graph (smc_iterate with n >= kIterChunk)
     int capture_host_io;    // while capturing graph_host: the kernels get the staging's addresses
     cudaEvent_t ev_move[2]; // profiling: recorded around the move kernel in the iteration graph
     int dependent_launch;   // while capturing: launch the one-pass resampler as a programmatic dependent
@@ -325,6 +327,7 @@ PfArgs<R> pf_args(smc_ctx *c) {
     }
     a.obs_after_wait = 0;
     a.hio_out = c->capture_host_io ? c->hio_d : nullptr;
+    a.obs_cap = (int32_t)c->cfg.max_data;
     return a;
 }
 
@@ -709,10 +712,20 @@ int launch_iteration_io(smc_ctx *c, bool host_io) {
     return rc;
 }
 
-int build_graph_once(smc_ctx *c, cudaGraphExec_t *dst, bool host_io) {
+void drop_graphs(smc_ctx *c) {
+    for (cudaGraphExec_t *g : {&c->graph, &c->graph_host, &c->graph_chunk})
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+}
+
+// iterations: how many consecutive iterations the graph holds (host_io: 1)
+int build_graph_once(smc_ctx *c, cudaGraphExec_t *dst, bool host_io, int iterations = 1) {
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SMC_E_CUDA;
-    const int rc = launch_iteration_io(c, host_io);
+    int rc = SMC_OK;
+    for (int i = 0; i < iterations && !rc; ++i) rc = launch_iteration_io(c, host_io);
     const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (rc || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -744,6 +757,17 @@ int build_graph(smc_ctx *c, bool host_io = false) {
         c->no_dependent = 1;
     }
     return build_graph_once(c, dst, host_io);
+}
+
+// kIterChunk iterations in one graph, with the launch form the one-iteration
+// graph settled on (build_graph first)
+int build_graph_chunk(smc_ctx *c) {
+    if (c->graph_chunk) return SMC_OK;
+    if (int rc = build_graph(c)) return rc;
+    c->dependent_launch = (!c->no_dependent && !c->ev_move[1]) ? 1 : 0;
+    const int rc = build_graph_once(c, &c->graph_chunk, false, kIterChunk);
+    c->dependent_launch = 0;
+    return rc;
 }
 
 int mcmc_any(smc_ctx *c) {
@@ -798,6 +822,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->initialized = 0;
     c->graph = nullptr;
     c->graph_host = nullptr;
+    c->graph_chunk = nullptr;
     c->capture_host_io = 0;
     c->hio = nullptr;
     c->hio_d = nullptr;
@@ -825,8 +850,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
 
 int smc_destroy(smc_ctx *c) {
     if (!c) return SMC_E_ARG;
-    if (c->graph) cudaGraphExecDestroy(c->graph);
-    if (c->graph_host) cudaGraphExecDestroy(c->graph_host);
+    drop_graphs(c);
     if (c->hio) cudaFreeHost(c->hio);
     gmm_release(c);
     delete c;
@@ -895,11 +919,34 @@ int smc_iterate(smc_ctx *c, int32_t n) {
     // state, so one captured iteration serves every t (host bookkeeping and
     // the recording copies are not captured)
     const int64_t limit = (c->cfg.model == SMC_MODEL_GMM) ? c->cfg.gmm.n_iter : c->n_obs - 1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (c->stream != nullptr && cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess) return SMC_E_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) {
+        // the caller is capturing the context's stream: the n iterations'
+        // kernels go into the caller's graph (particle filters; the launch
+        // form of the context's own iteration graph, which must exist)
+        if (cs != cudaStreamCaptureStatusActive || c->cfg.model == SMC_MODEL_GMM || recording(c) || !c->graph)
+            return SMC_E_STATE;
+        if (c->t_host + (int64_t)n > limit) return SMC_E_ARG;
+        c->dependent_launch = (!c->no_dependent && !c->ev_move[1]) ? 1 : 0;
+        int rc = SMC_OK;
+        for (int32_t i = 0; i < n && !rc; ++i) rc = launch_iteration(c);
+        c->dependent_launch = 0;
+        if (rc) return rc;
+        c->t_host += n;
+        return SMC_OK;
+    }
     if (c->stream != nullptr && !recording(c) && n > 0) {
         if (c->t_host + (int64_t)n > limit) return SMC_E_ARG;
         int rc = build_graph(c);
         if (rc) return rc;
-        for (int32_t i = 0; i < n; ++i)
+        int32_t i = 0;
+        if (n >= kIterChunk) {  // whole chunks of iterations per graph launch
+            if ((rc = build_graph_chunk(c))) return rc;
+            for (; i + kIterChunk <= n; i += kIterChunk)
+                if (cudaGraphLaunch(c->graph_chunk, c->stream) != cudaSuccess) return SMC_E_CUDA;
+        }
+        for (; i < n; ++i)
             if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return SMC_E_CUDA;
         c->t_host += n;
         return SMC_OK;
@@ -1226,14 +1273,7 @@ int smc_set_move_events(smc_ctx *c, void *ev_before, void *ev_after) {
     if (!c) return SMC_E_ARG;
     c->ev_move[0] = static_cast<cudaEvent_t>(ev_before);
     c->ev_move[1] = static_cast<cudaEvent_t>(ev_after);
-    if (c->graph) {  // captured again, with or without the events, at the next smc_iterate
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-    }
-    if (c->graph_host) {
-        cudaGraphExecDestroy(c->graph_host);
-        c->graph_host = nullptr;
-    }
+    drop_graphs(c);  // captured again, with or without the events, at the next smc_iterate
     return SMC_OK;
 }
 
@@ -1264,10 +1304,7 @@ int smc_shard_configure(smc_ctx *c, int64_t n_global, int64_t offset) {
     c->shard_n = n_global;
     c->shard_off = offset;
     c->initialized = 0;
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-    }
+    drop_graphs(c);
     return SMC_OK;
 }
 
