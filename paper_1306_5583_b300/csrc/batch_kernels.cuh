@@ -93,7 +93,11 @@ __global__ void __launch_bounds__(kBlock, 3) batch_pf_kernel(BatchArgs<R> B) {
             const int cur = sv->cur, cur_lw = sv->cur_lw;
             const bool gather = (t > 0) && (sv->ready != 0);
             const int nblk = B.tfirst[b + 1] - B.tfirst[b];
-            pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part);
+            if constexpr (sizeof(R) == 8)  // the plain double-precision move tiles: one particle per thread
+                pf_tile<R, 1>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part,
+                              nullptr, (uint32_t)pf64_move_threads(a.n));
+            else
+                pf_tile<R>(a, (uint32_t)(tile - B.tfirst[b]), t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part);
             if (last_arrival_after_partial(&st->ticket, (uint32_t)nblk)) pf_finalize<R, 1>(a, st, sv, nblk, t, cur, cur_lw);
         }
     if (last_arrival(&B.bs->ticket, gridDim.x) && threadIdx.x == 0) {

@@ -47,7 +47,48 @@ struct PfArgs {
     // rows of the observation buffer: an iteration past it (a caller's graph
     // replayed more often than the data allow) raises SMC_E_RANGE
     int32_t obs_cap;
+    // active threads per block of the double-precision move kernel (one
+    // particle each); the float kernel uses every thread, four particles each
+    uint32_t tile_threads;
 };
+
+// E consecutive elements from i0 (zeros past n): 16-byte vectors where E
+// elements fill them, else guarded scalar loads; the same for stores.
+template <typename R, int E>
+__device__ __forceinline__ void load_e(const R *__restrict__ p, uint32_t i0, uint32_t n, R (&v)[E]) {
+    if constexpr ((E * sizeof(R)) % 16 == 0) {
+        load_k<R, E>(p, i0, n, v);
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) v[j] = (i0 + j < n) ? __ldcg(p + i0 + j) : R(0);
+    }
+}
+template <typename R, int E>
+__device__ __forceinline__ void store_e(R *__restrict__ p, uint32_t i0, uint32_t n, const R (&v)[E]) {
+    if constexpr ((E * sizeof(R)) % 16 == 0) {
+        store_k<R, E>(p, i0, n, v);
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j)
+            if (i0 + j < n) p[i0 + j] = v[j];
+    }
+}
+template <int E>
+__device__ __forceinline__ void load_idx_e(const int32_t *__restrict__ p, uint32_t i0, uint32_t n, int32_t (&v)[E]) {
+    if constexpr (E == 4) {
+        load_idx4(p, i0, n, v);
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) v[j] = (i0 + j < n) ? __ldcg(p + i0 + j) : 0;
+    }
+}
+
+// First particle of a thread: E per thread, tile_threads active threads per
+// block (the others get n: no particle).
+template <int E>
+__device__ __forceinline__ uint32_t tile_first(uint32_t blk, uint32_t tile_threads, uint32_t n) {
+    return (threadIdx.x < tile_threads) ? (blk * tile_threads + threadIdx.x) * (uint32_t)E : n;
+}
 
 // log g(Y_t | X_t): full Student-t (or Gaussian) density of both position
 // coordinates.  FP32 uses log(1 + a) on the MUFU pipe (absolute error of a
@@ -62,21 +103,24 @@ __device__ __forceinline__ R cv_loglik(const PfArgs<R> &a, R yx, R yy, R px, R p
         return a.ll_const - a.half_nu1 * (Math<R>::log1p(zx * zx * a.inv_nu) + Math<R>::log1p(zy * zy * a.inv_nu));
 }
 
-// One tile (kPfTile particles, block-local index blk) of the fused
+// One tile (E tile_threads particles, block-local index blk) of the fused
 // gather + move + weight step, ending in the tile's block partial.  One
-// thread owns kPfItems consecutive particles: every input is fetched with
+// thread owns E consecutive particles: every input is fetched with
 // 16-byte vector loads (or, after resampling, as independent gathers
 // through one vector load of ancestor indices) before any arithmetic, so
 // the memory system sees all of a thread's requests at once.
 // pre_src: the tile's ancestor indices when the caller has fetched them
 // already (the same load_idx4 of the same i0), else null.
-template <typename R>
+// E particles per thread and tile_threads active threads per block (the
+// move kernel's double-precision tiles: E = 1, 64 or 256 threads; every
+// other caller: E = 4, all 256 threads, i.e. 1024-particle tiles).  The
+// arithmetic of a particle does not depend on the tiling.
+template <typename R, int E = kPfItems>
 __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_t t, int cur, int cur_lw,
                                         bool gather, Shift<R> Lprev, Partial *part,
-                                        const int32_t *pre_src = nullptr) {
-    constexpr int E = kPfItems;
+                                        const int32_t *pre_src = nullptr, uint32_t tile_threads = kBlock) {
     const uint32_t n = (uint32_t)a.n;
-    const uint32_t i0 = (blk * (uint32_t)kBlock + threadIdx.x) * (uint32_t)E;
+    const uint32_t i0 = tile_first<E>(blk, tile_threads, n);
     // buffer selection by value (no dynamic indexing of the pointer table)
     const R *xs0 = cur ? a.x[1][0] : a.x[0][0], *xs1 = cur ? a.x[1][1] : a.x[0][1];
     const R *xs2 = cur ? a.x[1][2] : a.x[0][2], *xs3 = cur ? a.x[1][3] : a.x[0][3];
@@ -96,7 +140,7 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
 #pragma unroll
                 for (int j = 0; j < E; ++j) src[j] = pre_src[j];
             } else {
-                load_idx4(a.anc, i0, n, src);
+                load_idx_e<E>(a.anc, i0, n, src);
             }
 #pragma unroll
             for (int j = 0; j < E; ++j) {
@@ -107,11 +151,11 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
                 v3[j] = __ldg(xs3 + sidx);
             }
         } else {
-            load_k<R, E>(xs0, i0, n, v0);
-            load_k<R, E>(xs1, i0, n, v1);
-            load_k<R, E>(xs2, i0, n, v2);
-            load_k<R, E>(xs3, i0, n, v3);
-            load_k<R, E>(lws, i0, n, lwin);
+            load_e<R, E>(xs0, i0, n, v0);
+            load_e<R, E>(xs1, i0, n, v1);
+            load_e<R, E>(xs2, i0, n, v2);
+            load_e<R, E>(xs3, i0, n, v3);
+            load_e<R, E>(lws, i0, n, lwin);
         }
     }
     // observation y_t (one broadcast load) and -log N, already in R
@@ -150,11 +194,11 @@ __device__ __forceinline__ void pf_tile(const PfArgs<R> &a, uint32_t blk, int32_
         const R b = (t == 0 || gather) ? base_eq : Lprev.sub_from(lwin[j]);
         lwv[j] = (i0 + j < n) ? b + cv_loglik(a, yx, yy, s0[j], s1[j]) : Math<R>::neg_inf();
     }
-    store_k<R, E>(xd0, i0, n, s0);
-    store_k<R, E>(xd1, i0, n, s1);
-    store_k<R, E>(xd2, i0, n, s2);
-    store_k<R, E>(xd3, i0, n, s3);
-    store_k<R, E>(lwd, i0, n, lwv);
+    store_e<R, E>(xd0, i0, n, s0);
+    store_e<R, E>(xd1, i0, n, s1);
+    store_e<R, E>(xd2, i0, n, s2);
+    store_e<R, E>(xd3, i0, n, s3);
+    store_e<R, E>(lwd, i0, n, lwv);
     block_partial<R, E, 2>(lwv, s0, s1, zero, &part[blk]);
 }
 
@@ -202,14 +246,17 @@ __device__ __forceinline__ void pf_finalize(const PfArgs<R> &a, DevState *st, co
 }
 
 // Five blocks per SM for FP32 (48 registers, no spills; six spill), four
-// for FP64.
+// for FP64.  FP32: four particles per thread, 1024-particle tiles; FP64: one
+// particle per thread, a.tile_threads per block.
 template <typename R>
 __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 4) pf_iterate_kernel(PfArgs<R> a) {
+    constexpr int E = (sizeof(R) == 4) ? kPfItems : 1;
+    const uint32_t tt = (sizeof(R) == 4) ? (uint32_t)kBlock : a.tile_threads;
     DevState *st = a.st;
     // the ancestor indices do not depend on the state block: their load is
     // in flight while the snapshot is read (unused when nothing is gathered)
-    int32_t src[kPfItems];
-    load_idx4(a.anc, (blockIdx.x * (uint32_t)kBlock + threadIdx.x) * (uint32_t)kPfItems, (uint32_t)a.n, src);
+    int32_t src[E];
+    load_idx_e<E>(a.anc, tile_first<E>(blockIdx.x, tt, (uint32_t)a.n), (uint32_t)a.n, src);
     const DevState *sv = snapshot(st, true);
     if (sv->error) {  // an earlier step failed: nothing runs, the error goes back to smc_iterate_host
         if (a.hio_out && blockIdx.x == 0 && threadIdx.x == 0) a.hio_out->status = sv->error;
@@ -225,7 +272,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 4) pf_iterate_ker
     }
     const int cur = sv->cur, cur_lw = sv->cur_lw;
     const bool gather = (t > 0) && (sv->ready != 0);
-    pf_tile<R>(a, blockIdx.x, t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part, src);
+    pf_tile<R, E>(a, blockIdx.x, t, cur, cur_lw, gather, log_norm_shift<R>(sv), a.part, src, tt);
     if (!last_arrival_after_partial(&st->ticket, gridDim.x)) return;
     // every other block has finished: a programmatic dependent (the one-pass
     // resampler) may start its launch while this block combines

@@ -63,6 +63,8 @@ struct Layout {
     int d;            // state rows
     int64_t ld;       // row pitch in elements (N rounded up to 64: 16-byte aligned rows)
     int64_t nbw;      // blocks of the weighting kernels
+    int64_t nbw_move; // blocks of the particle filter's move kernel
+    int32_t move_threads;  // active threads per block of that kernel
     int64_t ntiles;   // scan tiles of an N-element scan
     size_t rsize;
 };
@@ -103,6 +105,13 @@ Layout make_layout(const smc_config *c) {
               : 4;
     L.ld = (n + 63) & ~int64_t(63);
     L.nbw = (n + kPfTile - 1) / kPfTile;
+    // the double-precision particle filter's move kernel: one particle per
+    // thread in tiles of 64 (N <= 2^16) or 256 threads, so that a small
+    // filter's float64 work (Box-Muller, Student-t, exponentials) spreads over
+    // many SMs instead of one SM's float64 units
+    const bool pf64 = c->model != SMC_MODEL_GMM && c->precision == 64;
+    L.move_threads = pf64 ? pf64_move_threads(n) : kBlock;
+    L.nbw_move = pf64 ? (n + L.move_threads - 1) / L.move_threads : L.nbw;
     L.ntiles = (n + kScanTile - 1) / kScanTile;
     const bool hists = (c->scheme == SMC_MULTINOMIAL || c->scheme == SMC_RESIDUAL);
     size_t off = 0;
@@ -114,7 +123,7 @@ Layout make_layout(const smc_config *c) {
     L.st = take(sizeof(DevState));
     L.rec = take(sizeof(smc_record) * (size_t)c->max_records);
     const int64_t nblk = (c->model == SMC_MODEL_GMM) ? std::max<int64_t>(L.nbw, (kQuad * n + kBlock - 1) / kBlock)
-                                                     : L.nbw;
+                                                     : std::max<int64_t>(L.nbw, L.nbw_move);
     L.part = take(sizeof(Partial) * (size_t)std::max<int64_t>(nblk, 1));
     L.x = take(2 * (size_t)L.d * L.ld * rs);
     L.lw = take(2 * (size_t)L.ld * rs);
@@ -328,6 +337,7 @@ PfArgs<R> pf_args(smc_ctx *c) {
     a.obs_after_wait = 0;
     a.hio_out = c->capture_host_io ? c->hio_d : nullptr;
     a.obs_cap = (int32_t)c->cfg.max_data;
+    a.tile_threads = (uint32_t)c->L.move_threads;
     return a;
 }
 
@@ -338,7 +348,7 @@ int launch_pf(smc_ctx *c) {
         // smc_iterate_host's graph: a programmatic dependent of host_obs_kernel
         a.obs_after_wait = 1;
         cudaLaunchConfig_t lc = {};
-        lc.gridDim = dim3((unsigned)c->L.nbw);
+        lc.gridDim = dim3((unsigned)c->L.nbw_move);
         lc.blockDim = dim3(kBlock);
         lc.stream = c->stream;
         cudaLaunchAttribute attr[1];
@@ -348,7 +358,7 @@ int launch_pf(smc_ctx *c) {
         lc.numAttrs = 1;
         return cuda_check(cudaLaunchKernelEx(&lc, pf_iterate_kernel<R>, a));
     }
-    pf_iterate_kernel<R><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(a);
+    pf_iterate_kernel<R><<<(unsigned)c->L.nbw_move, kBlock, 0, c->stream>>>(a);
     return cuda_check(cudaGetLastError());
 }
 
@@ -1706,7 +1716,9 @@ bool batch_plan(const smc_config *cfg, const int64_t *n, const int32_t *T, int32
         P.rec_off[i] = oo;
         oo += T[b];
         P.tfirst[i] = tf;
-        tf += (int32_t)((n[b] + kPfTile - 1) / kPfTile);
+        // the move tiles of the plain filter of the same precision
+        const int64_t tile_n = (cfg->precision == 64) ? pf64_move_threads(n[b]) : kPfTile;
+        tf += (int32_t)((n[b] + tile_n - 1) / tile_n);
         P.sfirst[i] = sf;
         sf += (int32_t)((n[b] + kScanTile - 1) / kScanTile);
         P.frac[i] = 61 - ceil_log2(n[b]);
@@ -2052,9 +2064,9 @@ int smc_batch_run(smc_batch *bt) {
 int smc_batch_tune(smc_batch *bt, int32_t *blocks_per_sm, int32_t *tiles_per_item) {
     if (!bt) return SMC_E_ARG;
     // the launch shape of the persistent kernels: resident blocks per SM and
-    // consecutive tiles per work item (the tile itself, kPfTile particles of
-    // kPfItems per thread in blocks of kBlock threads, fixes the reduction
-    // order that makes every filter bit-identical to its plain run)
+    // consecutive tiles per work item (the tile itself, the plain move
+    // kernel's tile of the same precision, fixes the reduction order that
+    // makes every filter bit-identical to its plain run)
     const int cand_g[6] = {1, 2, 3, 4, 6, 8};
     const int cand_c[3] = {1, 2, 4};
     float best = 1e30f;

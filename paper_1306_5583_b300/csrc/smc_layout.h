@@ -16,6 +16,13 @@ constexpr int kScanTile = kBlock * kScanItems;  // 2048 elements per scan tile
 constexpr int kScanSlots = 6;                   // independent scans per iteration
 constexpr uint32_t kSpinLimit = 1u << 24;       // bounded waits (about 1 s with backoff)
 
+// Active threads per block of the double-precision particle filter's move
+// tiles (one particle per thread): 64 for N <= 2^16, so that a small filter's
+// float64 work spreads over many SMs, else every thread of the block.  The
+// plain filter and the batched filters tile the same way (same partials,
+// same normaliser).
+__host__ __device__ constexpr int pf64_move_threads(int64_t n) { return n <= 65536 ? 64 : kBlock; }
+
 // Histogram of the 24-bit multinomial draws: one byte count per value, four
 // to a 32-bit word, 16 values (one uint4) to a bucket, kScanTile buckets to a
 // histogram tile.

@@ -90,6 +90,25 @@ struct PartialIO<float> {
     }
 };
 
+// Explicitly rounded multiply, add and fused multiply-add: the reductions
+// spell out which products are fused, so every kernel that inlines them
+// (a plain filter, the batched filters) rounds the same way.
+template <typename R>
+__device__ __forceinline__ R fma_x(R a, R b, R c) {
+    if constexpr (sizeof(R) == 4) return __fmaf_rn(a, b, c);
+    else return __fma_rn(a, b, c);
+}
+template <typename R>
+__device__ __forceinline__ R mul_x(R a, R b) {
+    if constexpr (sizeof(R) == 4) return __fmul_rn(a, b);
+    else return __dmul_rn(a, b);
+}
+template <typename R>
+__device__ __forceinline__ R add_x(R a, R b) {
+    if constexpr (sizeof(R) == 4) return __fadd_rn(a, b);
+    else return __dadd_rn(a, b);
+}
+
 // Four warp sums at once: at the first two butterfly levels each lane keeps
 // half of its values and adds its partner's copy of that half (a transpose
 // reduce), so 6 shuffles replace 20; lane 8q (q < 4) ends with the sum of
@@ -151,10 +170,10 @@ __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E]
 #pragma unroll
         for (int j = 0; j < E; ++j) {
             const R e = (lw[j] > Math<R>::neg_inf()) ? Math<R>::fast_exp(lw[j] - m) : R(0);
-            v0 += e;
-            v1 += e * e;
-            if (NH > 0) v2 += e * h0[j];
-            if (NH > 1) v3 += e * h1[j];
+            v0 = add_x(v0, e);
+            v1 = fma_x(e, e, v1);
+            if (NH > 0) v2 = fma_x(e, h0[j], v2);
+            if (NH > 1) v3 = fma_x(e, h1[j], v3);
         }
     }
     const R x = warp_sum4(v0, v1, v2, v3);
@@ -171,7 +190,7 @@ __device__ __forceinline__ void block_partial(const R (&lw)[E], const R (&h0)[E]
 #pragma unroll
     for (int q = 0; q < kSums; ++q) {
         const R w = lane < NW ? s_sum[lane][q] : R(0);
-        t[q] = (q == 1) ? w * sc * sc : w * sc;
+        t[q] = (q == 1) ? mul_x(mul_x(w, sc), sc) : mul_x(w, sc);
     }
 #pragma unroll
     for (int o = NW / 2; o > 0; o >>= 1)
@@ -340,11 +359,11 @@ __device__ __forceinline__ void combine_partials(const Partial *part, int nb, Co
             for (int b = threadIdx.x; b < nb; b += kBlock) {
                 const double mb = __ldcg(&part[b].m);
                 const double sc = (mb > -INFINITY) ? exp(mb - M) : 0.0;
-                S[0] += __ldcg(&part[b].s1) * sc;
-                S[1] += __ldcg(&part[b].s2) * sc * sc;
-                S[2] += __ldcg(&part[b].sx) * sc;
-                S[3] += __ldcg(&part[b].sy) * sc;
-                S[4] += __ldcg(&part[b].su) * sc;
+                S[0] = fma_x(__ldcg(&part[b].s1), sc, S[0]);
+                S[1] = fma_x(mul_x(__ldcg(&part[b].s2), sc), sc, S[1]);
+                S[2] = fma_x(__ldcg(&part[b].sx), sc, S[2]);
+                S[3] = fma_x(__ldcg(&part[b].sy), sc, S[3]);
+                S[4] = fma_x(__ldcg(&part[b].su), sc, S[4]);
             }
         }
         for (int q = 0; q < 5; ++q) S[q] = warp_sum(S[q]);
