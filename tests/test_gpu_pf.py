@@ -63,6 +63,27 @@ def test_fp64_filter_end_to_end(scheme):
     assert abs(s.log_evidence() - ref[-1]["logZ"]) < 1e-9
 
 
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 65536, 65537])
+def test_fp64_move_tiling_boundaries(n):
+    """FP64 move tiles: one particle per thread, 64 threads per block up to
+    N = 2^16 and 256 above; sizes on both sides of a tile and of the
+    switch, ragged last tiles included, against the free-running oracle."""
+    need_gpu()
+    T, seed = 6, 7
+    s, y, op = make_pf(n, T, 64, scheme="systematic", seed=seed, threshold=0.9)
+    s.initialize()
+    s.iterate(T - 1)
+    recs = s.history(T)
+    ref, last = ocv.run(y, n, seed, op, scheme="systematic", threshold=0.9)
+    for r, o in zip(recs, ref):
+        assert r["resampled"] == o["resampled"], r["t"]
+        assert abs(r["logZ"] - o["logZ"]) < 1e-9
+        assert abs(r["ess"] - o["ess"]) < 1e-9 * n
+        assert abs(r["mean_x"] - o["mean_x"]) < 1e-9
+    assert_close(s.state(), last.x, 1e-10, "final state")
+    assert_close(s.log_weight(), last.lw, 1e-10, "final log-weights")
+
+
 @pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("n", [1, 3, 1000, 2049, 20000])
 def test_fp32_teacher_forced_steps(scheme, n):
