@@ -376,6 +376,13 @@ size_t smc_batch_workspace_bytes(const smc_config *cfg, const int64_t *n_particl
 int smc_batch_create(smc_batch **out, const smc_config *cfg, const int64_t *n_particles, const int32_t *n_iter,
                      int32_t n_filters, void *d_workspace, size_t bytes, void *cuda_stream);
 int smc_batch_destroy(smc_batch *b);
+/* Philox stream of each filter (stream_ids[f] for filter f, host array of
+ * n_filters words; the default is cfg->stream_id + f).  A filter's draws
+ * depend only on the key, its stream and the counters (Sec. 3.4: one
+ * counter-based stream per unit of work), so a subset of a batch run on
+ * another GPU with the same stream ids reproduces those filters exactly.
+ * Call before smc_batch_initialize; synchronises. */
+int smc_batch_set_streams(smc_batch *b, const uint32_t *stream_ids);
 /* observations of filter `filter`: n_iter[filter] rows of (x_obs, y_obs) float64 */
 int smc_batch_set_data(smc_batch *b, int32_t filter, const double *obs, int on_device);
 /* iteration 0 of every filter (prior draw, weighting by Y_0, resampling) */

@@ -2013,6 +2013,15 @@ int smc_batch_destroy(smc_batch *bt) {
     return SMC_OK;
 }
 
+int smc_batch_set_streams(smc_batch *bt, const uint32_t *stream_ids) {
+    if (!bt || !stream_ids) return SMC_E_ARG;
+    for (int32_t f = 0; f < bt->P.nf; ++f) bt->P.stream_of[bt->inv[f]] = stream_ids[f];
+    int rc = cuda_check(cudaMemcpyAsync(bt->ws + bt->P.o_stream, bt->P.stream_of.data(), 4 * (size_t)bt->P.nf,
+                                        cudaMemcpyHostToDevice, bt->stream));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(bt->stream));  // the host vector may change again
+    return rc;
+}
+
 int smc_batch_set_data(smc_batch *bt, int32_t filter, const double *obs, int on_device) {
     if (!bt || !obs || filter < 0 || filter >= bt->P.nf) return SMC_E_ARG;
     const int32_t i = bt->inv[filter];

@@ -24,6 +24,11 @@ evolves exactly as in a single context of N particles.  One iteration:
 The fixed-point CDF makes the global selection exact and order-independent,
 so the sharded filter's ancestors are those of one context of N particles.
 
+Independent filters (the batched form) need no exchange: ``assign_filters``
+packs them over ranks by cost N_b T_b, each rank runs its share as one
+batch on the filters' own Philox streams, and ``run_batch_over_ranks``
+gathers the log-evidence estimates at the end.
+
 Every data-parallel step runs in the library's kernels; this module only
 plans the exchange and calls the collectives.  ``Collectives`` wraps
 torch.distributed (NCCL between GPUs, gloo on CPU); ``run_local`` drives
@@ -92,6 +97,12 @@ class Collectives:
         parts = [torch.empty_like(t) for _ in range(self.world)]
         self.dist.all_gather(parts, t, group=self.group)
         return torch.cat(parts)
+
+    def all_gather_object(self, obj):
+        """Every rank's picklable obj, in rank order."""
+        out = [None] * self.world
+        self.dist.all_gather_object(out, obj, group=self.group)
+        return out
 
     def all_to_all(self, send, send_counts, recv_counts, width):
         """Rank-order all-to-all of rows of `width` values."""
@@ -212,3 +223,58 @@ def run_local(shards, steps):
                 s.unpack(torch.cat(pieces))
         recs.append(rr[0])
     return recs
+
+
+# ---- independent filters of a batch spread over ranks ------------------------
+
+def assign_filters(cost, world):
+    """The filters of a batch split over `world` ranks by cost (N_b T_b
+    particle-updates): in decreasing cost (ties by index) each filter goes
+    to the rank with the smallest load so far (ties to the lower rank), the
+    greedy longest-processing-time packing, whose largest load is within
+    4/3 of the best possible.  Returns, per rank, its filters in increasing
+    index order."""
+    cost = [int(c) for c in cost]
+    if world < 1 or any(c < 0 for c in cost):
+        raise ValueError("assign_filters: world >= 1 and costs >= 0")
+    load = [0] * world
+    mine = [[] for _ in range(world)]
+    for b in sorted(range(len(cost)), key=lambda i: (-cost[i], i)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        load[r] += cost[b]
+        mine[r].append(b)
+    return [sorted(m) for m in mine]
+
+
+def gpu_batch_runner(config, n, T, obs, streams, stream=None, device=None):
+    """One rank's filters as one batch on its GPU (smc.Batch), each with its
+    own Philox stream; returns their log-evidence estimates."""
+    b = smc.Batch(config, n, T, stream=stream, device=device)
+    try:
+        b.set_streams(streams)
+        for f, y in enumerate(obs):
+            b.set_data(f, y)
+        b.run()
+        return [float(v) for v in b.log_evidence()]
+    finally:
+        b.close()
+
+
+def run_batch_over_ranks(config, n, T, obs, comm, runner=gpu_batch_runner, **runner_kw):
+    """Independent filters spread over ranks (no collective on the data
+    path): rank `comm.rank` runs the filters `assign_filters` gives it, each
+    on the Philox stream config.stream_id + its index in the whole batch, so
+    every filter computes what it computes in one batch of all of them; one
+    gather of (index, log-evidence) pairs at the end.  Returns every
+    filter's log-evidence in filter order on every rank."""
+    mine = assign_filters([int(a) * int(b) for a, b in zip(n, T)], comm.world)[comm.rank]
+    res = {}
+    if mine:
+        vals = runner(config, [int(n[b]) for b in mine], [int(T[b]) for b in mine], [obs[b] for b in mine],
+                      [(int(config.stream_id) + b) & 0xFFFFFFFF for b in mine], **runner_kw)
+        res = dict(zip(mine, vals))
+    out = np.full(len(n), np.nan)
+    for part in comm.all_gather_object(res):
+        for b, v in part.items():
+            out[b] = v
+    return out

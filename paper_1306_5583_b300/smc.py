@@ -110,6 +110,7 @@ _SIGS = {
     "smc_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Config), _P, _P, ctypes.c_int32, _P,
                               ctypes.c_size_t, _P]),
     "smc_batch_destroy": (_I, [_P]),
+    "smc_batch_set_streams": (_I, [_P, _P]),
     "smc_batch_set_data": (_I, [_P, ctypes.c_int32, _P, _I]),
     "smc_batch_initialize": (_I, [_P]),
     "smc_batch_iterate": (_I, [_P, ctypes.c_int32]),
@@ -463,6 +464,13 @@ class Batch:
         a = np.ascontiguousarray(np.asarray(obs, dtype=np.float64))
         assert a.shape == (int(self.T[filter_index]), 2)
         check(lib().smc_batch_set_data(self.ctx, int(filter_index), a.ctypes.data_as(_P), 0), "smc_batch_set_data")
+
+    def set_streams(self, stream_ids):
+        """Philox stream of each filter (smc_batch_set_streams)."""
+        ids = np.ascontiguousarray(np.asarray(stream_ids, dtype=np.uint32))
+        if ids.shape != (self.nf,):
+            raise SMCError(E_ARG, "smc_batch_set_streams")
+        check(lib().smc_batch_set_streams(self.ctx, ids.ctypes.data_as(_P)), "smc_batch_set_streams")
 
     def initialize(self):
         check(lib().smc_batch_initialize(self.ctx), "smc_batch_initialize")

@@ -136,3 +136,29 @@ def test_batch_launch_shapes_give_identical_results():
     assert np.array_equal(out[0][0], out[1][0])
     for a, b in zip(out[0][1], out[1][1]):
         assert np.array_equal(a, b)
+
+
+def test_batch_split_over_ranks_equals_one_batch():
+    """The filters of a batch split as two ranks would run them
+    (shard.assign_filters by cost N_b T_b, each subset one batch with the
+    filters' own Philox streams via smc_batch_set_streams): every filter's
+    log-evidence is bit-identical to the one-batch run."""
+    need_gpu()
+    from paper_1306_5583_b300 import shard
+    cfg = smc.make_config(model="cv", n=1, precision=32, scheme="systematic", threshold=0.6, seed=5, stream_id=3,
+                          max_data=max(TS), keep_cdf=False)
+    data = [_data(T, 1 + b) for b, T in enumerate(TS)]
+    whole = smc.Batch(cfg, NS, TS)
+    for b, y in enumerate(data):
+        whole.set_data(b, y)
+    whole.run()
+    ref = whole.log_evidence()
+    whole.close()
+    parts = shard.assign_filters([n * T for n, T in zip(NS, TS)], 2)
+    assert all(parts)
+    got = np.full(len(NS), np.nan)
+    for mine in parts:
+        vals = shard.gpu_batch_runner(cfg, [NS[b] for b in mine], [TS[b] for b in mine], [data[b] for b in mine],
+                                      [3 + b for b in mine])
+        got[mine] = vals
+    assert np.array_equal(got, np.asarray(ref, dtype=np.float64))

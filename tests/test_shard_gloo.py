@@ -183,3 +183,87 @@ def test_two_gloo_ranks_equal_the_single_process_filter(n_global, threshold):
         assert np.array_equal(x, last.x)  # bit for bit: every step resampled, ancestors exact
     else:
         assert np.max(np.abs(x - last.x)) < 1e-10
+
+
+# ---- independent filters of a batch spread over ranks ------------------------
+
+def test_assign_filters_packs_by_cost():
+    rng = np.random.default_rng(3)
+    for world in (1, 2, 3, 8):
+        cost = [int(v) for v in rng.integers(1, 10_000, size=37)]
+        parts = shard.assign_filters(cost, world)
+        assert sorted(b for p in parts for b in p) == list(range(37))  # every filter once
+        assert all(p == sorted(p) for p in parts)
+        loads = [sum(cost[b] for b in p) for p in parts]
+        bound = max(max(cost), sum(cost) / world)  # no packing does better than this
+        assert max(loads) <= 4 / 3 * bound + 1e-9
+    assert shard.assign_filters([1, 1, 1], 4) == [[0], [1], [2], []]
+    assert shard.assign_filters([5, 3, 3, 2, 2, 1], 2) == [[0, 3, 5], [1, 2, 4]]
+    with pytest.raises(ValueError):
+        shard.assign_filters([1, -1], 2)
+
+
+def _oracle_batch_runner(config, n, T, obs, streams):
+    """Stand-in for one rank's batch: each filter as the oracle's run on its
+    own Philox stream (the GPU batch is checked against plain runs and the
+    oracle in tests/test_gpu_batch.py)."""
+    p = ocv.CVParams(**workloads.CV_DEFAULT)
+    return [ocv.run(y, nb, int(config.seed), p, scheme="systematic", threshold=0.5, stream=s)[0][-1]["logZ"]
+            for nb, y, s in zip(n, obs, streams)]
+
+
+BATCH_N = [40, 7, 64, 3, 25, 16, 1]
+BATCH_T = [6, 9, 4, 8, 5, 7, 3]
+
+
+def _batch_data():
+    return [workloads.cv_data(t, seed=1 + b, **workloads.CV_DEFAULT)[1] for b, t in enumerate(BATCH_T)]
+
+
+def _batch_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1306_5583_b300 import smc
+        cfg = smc.make_config(model="cv", n=1, precision=64, seed=SEED, stream_id=11)
+        lz = shard.run_batch_over_ranks(cfg, BATCH_N, BATCH_T, _batch_data(), shard.Collectives(),
+                                        runner=_oracle_batch_runner)
+        out.put((rank, lz.tolist()))
+    except Exception as e:
+        out.put(repr(e))
+        raise
+    finally:
+        dist.destroy_process_group()
+
+
+def test_batch_over_two_gloo_ranks_equals_one_rank():
+    """Two ranks, each running its share of the filters on their own Philox
+    streams, gather the same log-evidence as one rank running them all."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batch_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    import queue
+    got = []
+    for _ in range(240):
+        try:
+            got.append(q.get(timeout=1))
+            if len(got) == 2:
+                break
+        except queue.Empty:
+            if any(p.exitcode not in (None, 0) for p in procs):
+                break
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():
+            p.kill()
+    assert len(got) == 2 and all(isinstance(g, tuple) for g in got), got
+    assert all(p.exitcode == 0 for p in procs)
+    from paper_1306_5583_b300 import smc
+    cfg = smc.make_config(model="cv", n=1, precision=64, seed=SEED, stream_id=11)
+    ref = _oracle_batch_runner(cfg, BATCH_N, BATCH_T, _batch_data(), [11 + b for b in range(len(BATCH_N))])
+    for _, lz in got:
+        assert lz == ref  # bit for bit: the same arithmetic on the same streams
