@@ -419,9 +419,11 @@ int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], uint32_t *d_
  * A filter of n_global particles is split in blocks: this context's
  * n_particles particles are the filter's [offset, offset + n_particles), with
  * those global Philox indices, so every particle evolves as in one context of
- * n_global particles.  CV models, systematic or stratified resampling,
- * without SMC_FLAG_RECORD, _INPLACE or _POST_MEAN; smc_move, smc_resample and
- * smc_iterate refuse a shard (SMC_E_STATE).  One iteration, every rank
+ * n_global particles.  CV models and the mixture sampler (with a fixed
+ * schedule; Sec. 5.2.5 runs the mixture sampler over MPI ranks), systematic
+ * or stratified resampling, without SMC_FLAG_RECORD, _INPLACE or _POST_MEAN;
+ * smc_move, smc_resample and smc_iterate refuse a shard (SMC_E_STATE).  One
+ * iteration, every rank
  * (the caller runs the collectives between the calls, all buffers device
  * memory on the context's stream):
  *   smc_shard_move(ctx, d_partial)      move + weight; this shard's partial
@@ -446,11 +448,22 @@ int smc_philox4x32_10(const uint32_t *d_ctr, const uint32_t key[2], uint32_t *d_
  *   smc_shard_unpack(ctx, d_recv)       the received n_particles copies (output
  *                                       order = slot order) become the shard's
  *                                       particles, log-weights -log n_global
+ *   the mixture sampler then (iterations t >= 1):
+ *   smc_shard_mcmc(ctx, d_partial)      the Metropolis / Langevin moves of the
+ *                                       shard's particles; its partial (64 B,
+ *                                       with the shard's accepted-move counts)
+ *   all-gather of the partials into d_partials
+ *   smc_shard_mcmc_finalize(ctx, d_partials, world)
+ *                                       path-sampling integrand U_t and
+ *                                       acceptance rates of the whole sampler
+ * For the mixture sampler smc_shard_move is the reweighting at alpha_t (and
+ * at iteration 0 the prior draws), smc_shard_finalize its normaliser and
+ * decision.  The pack and unpack carry every state row (d values a copy).
  * smc_shard_configure marks the context as a shard (before smc_initialize,
  * which then only resets the state: iteration 0 is a smc_shard_move like the
  * others).  Errors: SMC_E_ARG for an unsupported configuration or
  * inconsistent sizes, SMC_E_STATE for a call on a context that is not a
- * shard. */
+ * shard or out of order. */
 int smc_shard_configure(smc_ctx *ctx, int64_t n_global, int64_t offset);
 int smc_shard_move(smc_ctx *ctx, void *d_partial);
 int smc_shard_finalize(smc_ctx *ctx, const void *d_partials, int32_t world);
@@ -459,6 +472,8 @@ int smc_shard_select(smc_ctx *ctx, const uint64_t *d_totals, int32_t rank, int32
                      int64_t *d_range);
 int smc_shard_pack(smc_ctx *ctx, const int32_t *d_src, int64_t k_lo, int64_t count, void *d_send);
 int smc_shard_unpack(smc_ctx *ctx, const void *d_recv);
+int smc_shard_mcmc(smc_ctx *ctx, void *d_partial);
+int smc_shard_mcmc_finalize(smc_ctx *ctx, const void *d_partials, int32_t world);
 
 /* Measurement: issue rate of the special-function (MUFU) pipe of the current
  * device, the roofline denominator of the likelihood-bound GMM moves (no

@@ -60,6 +60,12 @@ struct GmmArgs {
     float hnl_f[2];         // half_nd_log2pi as a double-float value
     uint2 key;
     uint32_t stream;
+    // a shard of a sampler partitioned over ranks: the Philox index of
+    // particle 0 (its global index), and where the init, reweight and mcmc
+    // kernels put the shard's combined partial instead of finalising (null:
+    // a whole sampler)
+    uint32_t index0;
+    Partial *shard_out;
 };
 
 // Model constants in the kernel's precision R (the FP64 instantiation keeps
@@ -567,6 +573,109 @@ __global__ void __launch_bounds__(kBlock) gmm_log_target_kernel(GmmArgs<R> a, co
 }
 
 // ---- init: theta ~ prior, equal weights, U_0 --------------------------------
+// ---- finalisation of the init, reweight and mcmc kernels (thread 0 of
+// the last block, or of gmm_shard_finalize_kernel on every rank's partials
+// of a partitioned sampler) ---------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void gmm_init_finish(const GmmArgs<R> &a, DevState *st, const Combined &c, int cur,
+                                                int cur_lw) {
+    FinalizeArgs f{st, a.rec, a.rec_cap, 0, 0, a.n, a.threshold, 0.0};
+    double L;
+    if (finalize_weights(f, c, &L)) {
+        const double U0 = c.Sa / c.S1;
+        smc_record *r = &a.rec[0];
+        r->path_u = U0;
+        r->path_log_z = 0.0;
+        r->log_evidence = 0.0;  // the prior is normalised: log Z_0 = 0
+        st->log_evidence = 0.0;
+        st->path_u = U0;
+        st->path_log_z = 0.0;
+        st->alpha = 0.0;
+        st->base_shift = L;
+        st->t = 0;
+        st->cur = cur ^ 1;
+        st->cur_lw = cur_lw ^ 1;
+        st->ready = 0;
+        st->gathered = 0;
+        st->accept[0] = st->accept[1] = st->accept[2] = st->accept[3] = 0;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void gmm_reweight_finish(const GmmArgs<R> &a, DevState *st, const Combined &c, int32_t t,
+                                                    int cur_lw, double a_t) {
+    FinalizeArgs f{st, a.rec, a.rec_cap, t, 0, a.n, a.threshold, a_t};
+    double L;
+    if (finalize_weights(f, c, &L)) {
+        smc_record *r = &a.rec[t % a.rec_cap];
+        r->path_u = st->path_u;
+        r->path_log_z = st->path_log_z;
+        st->alpha = a_t;
+        st->base_shift = L;
+        st->t = t;
+        st->cur_lw = cur_lw ^ 1;
+        st->accept[0] = st->accept[1] = st->accept[2] = st->accept[3] = 0;
+    }
+}
+
+// accepted moves per block in st->accept (summed over the ranks for a
+// partitioned sampler); rates over a.n particles
+template <typename R, int MOVE>
+__device__ __forceinline__ void gmm_mcmc_finish(const GmmArgs<R> &a, DevState *st, const Combined &c, int32_t t,
+                                                int cur, bool gather) {
+    constexpr bool G = (MOVE != kMoveRW);
+    smc_record *r = &a.rec[t % a.rec_cap];
+    if (!(c.S1 > 0.0)) {
+        raise_error(st, SMC_E_NONFINITE);
+        r->status = SMC_E_NONFINITE;
+        st->ticket = 0;
+        return;
+    }
+    st->ticket = 0;
+    const double a_t = a.alpha[t], a_p = (t > 0) ? a.alpha[t - 1] : 0.0;
+    const double U = c.Sa / c.S1;
+    const double plz = st->path_log_z + 0.5 * (a_t - a_p) * (U + st->path_u);
+    r->path_u = U;
+    r->path_log_z = plz;
+    for (int b = 0; b < 3; ++b)
+        r->accept[b] = (MOVE == kMoveMALA) ? 0.0 : double(*(volatile uint32_t *)&st->accept[b]) / double(a.n);
+    r->accept_mala = G ? double(*(volatile uint32_t *)&st->accept[3]) / double(a.n) : 0.0;
+    st->path_u = U;
+    st->path_log_z = plz;
+    st->cur = cur ^ 1;
+    if (gather) st->base_shift = 0.0;
+    st->gathered = gather ? 1 : 0;
+    st->ready = 0;
+}
+
+// A shard's partial (the last block, whole block): its blocks' partials
+// combined in a fixed order into one partial of the partial layout (FP32:
+// double-float sums and the float maximum; FP64: float64 fields); with
+// accept, bytes 48..63 (unused by both layouts) carry the shard's four
+// accepted-move counts.
+constexpr int kShardAcceptOffset = 48;
+template <typename R>
+__device__ __forceinline__ void gmm_shard_partial_out(DevState *st, const Partial *part, int nb, Partial *out,
+                                                      bool accept) {
+    if constexpr (sizeof(R) == 4) {
+        CombinedDF c;
+        combine_partials_df<4>(part, nb, &c);
+        if (threadIdx.x == 0) PartialIO<float>::store(out, c.M, c.S);
+    } else {
+        Combined c;
+        combine_partials<R>(part, nb, &c);
+        if (threadIdx.x == 0) {
+            const double s4[kSums] = {c.S1, c.S2, c.Sa, c.Sb};
+            PartialIO<double>::store(out, c.M, s4);
+        }
+    }
+    if (threadIdx.x == 0) {
+        uint32_t *w = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(out) + kShardAcceptOffset);
+        for (int k = 0; k < 4; ++k) w[k] = accept ? *(volatile uint32_t *)&st->accept[k] : 0u;
+        st->ticket = 0;
+    }
+}
+
 template <typename R, int NC, bool G>
 __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -582,7 +691,7 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
     Theta<R, NC> th;
     {
         R z[NC];
-        gmm_normals<R, NC>(a.key, (uint32_t)ii, 0u, TAG_INIT, a.stream, z);
+        gmm_normals<R, NC>(a.key, (a.index0 + (uint32_t)ii), 0u, TAG_INIT, a.stream, z);
 #pragma unroll
         for (int j = 0; j < NC; ++j) th.mu[j] = R(a.mu0) + R(a.sd0) * z[j];
         const int shape = (int)a.shape_m1 + 1;
@@ -591,7 +700,7 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
             R e = 0;
             for (int m = 0; m < shape; ++m) {
                 const int idx = j * shape + m;
-                const uint4 w = draw(a.key, (uint32_t)ii, 0u, TAG_INIT, a.stream, 8u + (uint32_t)(idx >> 2));
+                const uint4 w = draw(a.key, (a.index0 + (uint32_t)ii), 0u, TAG_INIT, a.stream, 8u + (uint32_t)(idx >> 2));
                 const uint32_t ww = (idx & 3) == 0 ? w.x : (idx & 3) == 1 ? w.y : (idx & 3) == 2 ? w.z : w.w;
                 e -= Math<R>::log(uniform01<R>(ww));
             }
@@ -600,7 +709,7 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
         R E[NC], sum = 0;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
-            const uint4 w = draw(a.key, (uint32_t)ii, 0u, TAG_INIT, a.stream, 64u + (uint32_t)(j >> 2));
+            const uint4 w = draw(a.key, (a.index0 + (uint32_t)ii), 0u, TAG_INIT, a.stream, 64u + (uint32_t)(j >> 2));
             const uint32_t ww = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
             E[j] = -Math<R>::log(uniform01<R>(ww));
             sum += E[j];
@@ -620,30 +729,13 @@ __global__ void __launch_bounds__(kBlock) gmm_init_kernel(GmmArgs<R> a) {
     R lwv[1] = {(active && q == 0) ? lw0 : Math<R>::neg_inf()};
     R h0[1] = {th.ll}, zero[1] = {R(0)};
     block_partial<R, 1, 1>(lwv, h0, zero, zero, &a.part[blockIdx.x]);
+    if (a.shard_out) {  // a shard: its combined partial, finalised with every rank's (gmm_shard_finalize_kernel)
+        if (take_ticket<R>(st)) gmm_shard_partial_out<R>(st, a.part, gridDim.x, a.shard_out, false);
+        return;
+    }
     Combined c;
     if (!last_block_combine<R>(st, a.part, &c)) return;
-    if (threadIdx.x == 0) {
-        FinalizeArgs f{st, a.rec, a.rec_cap, 0, 0, a.n, a.threshold, 0.0};
-        double L;
-        if (finalize_weights(f, c, &L)) {
-            const double U0 = c.Sa / c.S1;
-            smc_record *r = &a.rec[0];
-            r->path_u = U0;
-            r->path_log_z = 0.0;
-            r->log_evidence = 0.0;  // the prior is normalised: log Z_0 = 0
-            st->log_evidence = 0.0;
-            st->path_u = U0;
-            st->path_log_z = 0.0;
-            st->alpha = 0.0;
-            st->base_shift = L;
-            st->t = 0;
-            st->cur = cur ^ 1;
-            st->cur_lw = cur_lw ^ 1;
-            st->ready = 0;
-            st->gathered = 0;
-            st->accept[0] = st->accept[1] = st->accept[2] = st->accept[3] = 0;
-        }
-    }
+    if (threadIdx.x == 0) gmm_init_finish<R>(a, st, c, cur, cur_lw);
 }
 
 // ---- reweight: lw_t = log W_{t-1} + dalpha l ---------------------------------
@@ -682,22 +774,13 @@ __global__ void __launch_bounds__(kBlock) gmm_reweight_kernel(GmmArgs<R> a) {
         }
     }
     block_partial<R, kPfItems, 0>(lwv, zero, zero, zero, &a.part[blockIdx.x]);
+    if (a.shard_out) {
+        if (take_ticket<R>(st)) gmm_shard_partial_out<R>(st, a.part, gridDim.x, a.shard_out, false);
+        return;
+    }
     Combined c;
     if (!last_block_combine<R>(st, a.part, &c)) return;
-    if (threadIdx.x == 0) {
-        FinalizeArgs f{st, a.rec, a.rec_cap, t, 0, a.n, a.threshold, a_t};
-        double L;
-        if (finalize_weights(f, c, &L)) {
-            smc_record *r = &a.rec[t % a.rec_cap];
-            r->path_u = st->path_u;
-            r->path_log_z = st->path_log_z;
-            st->alpha = a_t;
-            st->base_shift = L;
-            st->t = t;
-            st->cur_lw = cur_lw ^ 1;
-            st->accept[0] = st->accept[1] = st->accept[2] = st->accept[3] = 0;
-        }
-    }
+    if (threadIdx.x == 0) gmm_reweight_finish<R>(a, st, c, t, cur_lw, a_t);
 }
 
 // ---- mcmc: gather, three Metropolis blocks, path sampling -------------------
@@ -742,13 +825,13 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     // block 1: mu
     {
         R z[NC], mu2[NC];
-        gmm_normals<R, NC>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_MU, a.stream, z);
+        gmm_normals<R, NC>(a.key, (a.index0 + (uint32_t)ii), (uint32_t)t, TAG_MH_MU, a.stream, z);
 #pragma unroll
         for (int j = 0; j < NC; ++j) mu2[j] = th.mu[j] + s_mu * z[j];
         const R lp2 = gmm_log_prior<R, NC>(a, mu2, th.lam, th.om);
         const R ll2 = gmm_loglik_quad<R, NC>(mu2, th.lam, th.om, ys, a.nd, q, a);
         const R delta = mh_delta<R>(lp2, lp, ll2, ll, a_t);
-        const R lu = mh_log_uniform<R>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_MU, a.stream);
+        const R lu = mh_log_uniform<R>(a.key, (a.index0 + (uint32_t)ii), (uint32_t)t, TAG_MH_MU, a.stream);
         if (lu <= delta) {
 #pragma unroll
             for (int j = 0; j < NC; ++j) th.mu[j] = mu2[j];
@@ -760,7 +843,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     // block 2: log lambda
     {
         R z[NC], lam2[NC];
-        gmm_normals<R, NC>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_LAMBDA, a.stream, z);
+        gmm_normals<R, NC>(a.key, (a.index0 + (uint32_t)ii), (uint32_t)t, TAG_MH_LAMBDA, a.stream, z);
         R jac = 0;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
@@ -771,7 +854,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
         const R lp2 = gmm_log_prior<R, NC>(a, th.mu, lam2, th.om);
         const R ll2 = gmm_loglik_quad<R, NC>(th.mu, lam2, th.om, ys, a.nd, q, a);
         const R delta = mh_delta<R>(lp2, lp, ll2, ll, a_t) + jac;
-        const R lu = mh_log_uniform<R>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_LAMBDA, a.stream);
+        const R lu = mh_log_uniform<R>(a.key, (a.index0 + (uint32_t)ii), (uint32_t)t, TAG_MH_LAMBDA, a.stream);
         if (lu <= delta) {
 #pragma unroll
             for (int j = 0; j < NC; ++j) th.lam[j] = lam2[j];
@@ -783,7 +866,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     // block 3: additive log-ratios of the weights
     if (NC > 1) {
         R z[NC], om2[NC];
-        gmm_normals<R, NC>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_WEIGHT, a.stream, z);
+        gmm_normals<R, NC>(a.key, (a.index0 + (uint32_t)ii), (uint32_t)t, TAG_MH_WEIGHT, a.stream, z);
         R v[NC];
         R vmax = 0;  // the last log-ratio is 0
 #pragma unroll
@@ -807,7 +890,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
         const R lp2 = gmm_log_prior<R, NC>(a, th.mu, th.lam, om2);
         const R ll2 = gmm_loglik_quad<R, NC>(th.mu, th.lam, om2, ys, a.nd, q, a);
         const R delta = mh_delta<R>(lp2, lp, ll2, ll, a_t) + jac;
-        const R lu = mh_log_uniform<R>(a.key, (uint32_t)ii, (uint32_t)t, TAG_MH_WEIGHT, a.stream);
+        const R lu = mh_log_uniform<R>(a.key, (a.index0 + (uint32_t)ii), (uint32_t)t, TAG_MH_WEIGHT, a.stream);
         if (lu <= delta) {
 #pragma unroll
             for (int j = 0; j < NC; ++j) th.om[j] = om2[j];
@@ -823,7 +906,7 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
         // the blocks moved theta: refresh the cached gradient at the current point
         ll = gmm_loglik_grad_quad<R, NC>(th.mu, th.lam, th.om, ys, a.nd, q, a, th.gm, th.gl, th.gz);
     }
-    if (G) acc_mask |= mala_move<R, NC>(a, th, lp, ll, a_t, (uint32_t)ii, (uint32_t)t, ys, q) << 3;
+    if (G) acc_mask |= mala_move<R, NC>(a, th, lp, ll, a_t, (a.index0 + (uint32_t)ii), (uint32_t)t, ys, q) << 3;
     th.lp = lp;
     th.ll = ll;
     R lwi = R(-a.log_n);
@@ -841,31 +924,43 @@ __global__ void __launch_bounds__(kBlock) gmm_mcmc_kernel(GmmArgs<R> a) {
     R lwv[1] = {(active && q == 0) ? lwi : Math<R>::neg_inf()};
     R h0[1] = {th.ll}, zero[1] = {R(0)};
     block_partial<R, 1, 1>(lwv, h0, zero, zero, &a.part[blockIdx.x]);
+    if (a.shard_out) {
+        if (take_ticket<R>(st)) gmm_shard_partial_out<R>(st, a.part, gridDim.x, a.shard_out, true);
+        return;
+    }
     Combined c;
     if (!last_block_combine<R>(st, a.part, &c)) return;
-    if (threadIdx.x == 0) {
-        smc_record *r = &a.rec[t % a.rec_cap];
-        if (!(c.S1 > 0.0)) {
-            raise_error(st, SMC_E_NONFINITE);
-            r->status = SMC_E_NONFINITE;
-            st->ticket = 0;
-            return;
+    if (threadIdx.x == 0) gmm_mcmc_finish<R, MOVE>(a, st, c, t, cur, gather);
+}
+
+// A partitioned sampler's finalisation on every rank's shard partials (rank
+// order, gathered): kind 0 after the init kernels (t = 0), 1 after the
+// reweight kernels, 2 after the mcmc kernels (the ranks' accepted-move
+// counts summed into st->accept first).  a.n is the sampler's N.  The same
+// finalisation functions as a whole sampler's, on the combined partials.
+template <typename R, int MOVE>
+__global__ void __launch_bounds__(kBlock) gmm_shard_finalize_kernel(GmmArgs<R> a, const Partial *parts, int world,
+                                                                    int kind) {
+    DevState *st = a.st;
+    const DevState *sv = snapshot(st, true);
+    if (sv->error) return;
+    Combined c;
+    combine_partials<R>(parts, world, &c);  // every thread; thread 0 holds the result
+    if (threadIdx.x != 0) return;
+    if (kind == 0) {
+        gmm_init_finish<R>(a, st, c, sv->cur, sv->cur_lw);
+    } else if (kind == 1) {
+        const int32_t t = sv->t + 1;
+        gmm_reweight_finish<R>(a, st, c, t, sv->cur_lw, a.alpha[t]);
+    } else {
+        for (int k = 0; k < 4; ++k) {
+            uint32_t v = 0;
+            for (int r = 0; r < world; ++r)
+                v += *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(&parts[r]) +
+                                                         kShardAcceptOffset + 4 * k);
+            st->accept[k] = v;
         }
-        st->ticket = 0;
-        const double a_t = a.alpha[t], a_p = (t > 0) ? a.alpha[t - 1] : 0.0;
-        const double U = c.Sa / c.S1;
-        const double plz = st->path_log_z + 0.5 * (a_t - a_p) * (U + st->path_u);
-        r->path_u = U;
-        r->path_log_z = plz;
-        for (int b = 0; b < 3; ++b)
-            r->accept[b] = (MOVE == kMoveMALA) ? 0.0 : double(*(volatile uint32_t *)&st->accept[b]) / double(a.n);
-        r->accept_mala = G ? double(*(volatile uint32_t *)&st->accept[3]) / double(a.n) : 0.0;
-        st->path_u = U;
-        st->path_log_z = plz;
-        st->cur = cur ^ 1;
-        if (gather) st->base_shift = 0.0;
-        st->gathered = gather ? 1 : 0;
-        st->ready = 0;
+        gmm_mcmc_finish<R, MOVE>(a, st, c, sv->t, sv->cur, false);
     }
 }
 

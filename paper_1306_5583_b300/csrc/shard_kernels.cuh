@@ -142,4 +142,36 @@ __global__ void __launch_bounds__(kBlock) shard_unpack_kernel(PfArgs<R> a, const
     }
 }
 
+// The same for d state rows of pitch ld (the mixture sampler's rows:
+// parameters, log-prior, log-likelihood and, for Langevin moves, the cached
+// gradient).
+template <typename R>
+__global__ void __launch_bounds__(kBlock) shard_pack_rows_kernel(const R *x0, const R *x1, int64_t ld, int d,
+                                                                 const DevState *st, const int32_t *src, int64_t k_lo,
+                                                                 int64_t count, R *send) {
+    const int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    if (j >= count) return;
+    const int cur = *reinterpret_cast<const volatile int32_t *>(&st->cur);
+    const R *x = cur ? x1 : x0;
+    const int32_t s = src[k_lo + j];
+    for (int r = 0; r < d; ++r) send[(int64_t)d * j + r] = x[(int64_t)r * ld + s];
+}
+
+// The received copies become the shard's particles with log-weights -log N_g
+// and no pending shift (the next reweighting starts from log W = -log N_g).
+template <typename R>
+__global__ void __launch_bounds__(kBlock) shard_unpack_rows_kernel(R *x0, R *x1, R *lw0, R *lw1, int64_t ld, int d,
+                                                                   int64_t n, R neg_log_n, DevState *st,
+                                                                   const R *recv) {
+    const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    const int cur = *reinterpret_cast<const volatile int32_t *>(&st->cur);
+    const int cur_lw = *reinterpret_cast<const volatile int32_t *>(&st->cur_lw);
+    if (i < n) {
+        R *x = cur ? x1 : x0;
+        for (int r = 0; r < d; ++r) x[(int64_t)r * ld + i] = recv[(int64_t)d * i + r];
+        (cur_lw ? lw1 : lw0)[i] = neg_log_n;
+    }
+    if (i == 0) st->base_shift = 0.0;
+}
+
 }  // namespace smc

@@ -35,6 +35,10 @@ void gmm_release(smc_ctx *c);
 int gmm_launch_reweight(smc_ctx *c);
 int gmm_launch_mcmc(smc_ctx *c);
 int gmm_log_target_any(smc_ctx *c, const void *u, int64_t count, double alpha, void *logt, void *grad);
+// a mixture shard: kernel kind 0 init, 1 reweight, 2 mcmc, its partial to d_partial; and the
+// finalisation of a kind on every rank's partials
+int gmm_shard_launch(smc_ctx *c, int kind, void *d_partial);
+int gmm_shard_finalize_any(smc_ctx *c, const void *d_partials, int32_t world, int kind);
 
 constexpr size_t kAlign = 256;
 
@@ -200,6 +204,8 @@ struct smc_ctx {
     int no_dependent;       // the driver refused the programmatic dependent launch once: capture without
     int64_t shard_n;        // a shard of a partitioned filter: the filter's N (0: not a shard)
     int64_t shard_off;      // and the global index of the shard's first particle
+    void *shard_out;        // while launching a mixture shard's kernel: where its partial goes
+    int shard_pending;      // the mixture shard's partial awaiting smc_shard_finalize: 0 init, 1 reweight
 };
 
 namespace {
@@ -1308,7 +1314,10 @@ int smc_wait_selftest(smc_ctx *c) {
 int smc_shard_configure(smc_ctx *c, int64_t n_global, int64_t offset) {
     if (!c) return SMC_E_ARG;
     const smc_config &g = c->cfg;
-    if (g.model == SMC_MODEL_GMM || (g.scheme != SMC_SYSTEMATIC && g.scheme != SMC_STRATIFIED)) return SMC_E_ARG;
+    if (g.scheme != SMC_SYSTEMATIC && g.scheme != SMC_STRATIFIED) return SMC_E_ARG;
+    // a partitioned mixture sampler takes a fixed schedule (an adaptive
+    // alpha would need a grid-wide search over every rank's particles)
+    if (g.model == SMC_MODEL_GMM && g.gmm.schedule == SMC_ALPHA_ADAPTIVE) return SMC_E_ARG;
     if (g.flags & (SMC_FLAG_RECORD | SMC_FLAG_INPLACE | SMC_FLAG_POST_MEAN)) return SMC_E_ARG;
     if (offset < 0 || n_global < offset + g.n_particles || n_global > (int64_t(1) << 30)) return SMC_E_ARG;
     c->shard_n = n_global;
@@ -1321,6 +1330,16 @@ int smc_shard_configure(smc_ctx *c, int64_t n_global, int64_t offset) {
 int smc_shard_move(smc_ctx *c, void *d_partial) {
     if (!c || !d_partial) return SMC_E_ARG;
     if (!c->shard_n || !c->initialized) return SMC_E_STATE;
+    if (c->cfg.model == SMC_MODEL_GMM) {  // iteration 0: the prior draws; then the reweighting
+        const int kind = (c->t_host < 0) ? 0 : 1;
+        if (kind == 1 && c->t_host + 1 > c->cfg.gmm.n_iter) return SMC_E_ARG;
+        const int rc = gmm_shard_launch(c, kind, d_partial);
+        if (!rc) {
+            c->t_host += 1;
+            c->shard_pending = kind;
+        }
+        return rc;
+    }
     if (c->t_host + 1 >= c->n_obs) return SMC_E_ARG;
     if (c->cfg.precision == 32)
         pf_shard_move_kernel<float><<<(unsigned)c->L.nbw, kBlock, 0, c->stream>>>(pf_args<float>(c),
@@ -1336,6 +1355,7 @@ int smc_shard_move(smc_ctx *c, void *d_partial) {
 int smc_shard_finalize(smc_ctx *c, const void *d_partials, int32_t world) {
     if (!c || !d_partials || world < 1) return SMC_E_ARG;
     if (!c->shard_n) return SMC_E_STATE;
+    if (c->cfg.model == SMC_MODEL_GMM) return gmm_shard_finalize_any(c, d_partials, world, c->shard_pending);
     const Partial *p = static_cast<const Partial *>(d_partials);
     if (c->cfg.precision == 32)
         pf_shard_finalize_kernel<float><<<1, kBlock, 0, c->stream>>>(pf_args<float>(c), p, world, c->shard_n);
@@ -1378,11 +1398,36 @@ int smc_shard_select(smc_ctx *c, const uint64_t *d_totals, int32_t rank, int32_t
                  : shard_select_t<double, false>(c, d_totals, rank, world, d_src, d_range);
 }
 
+int smc_shard_mcmc(smc_ctx *c, void *d_partial) {
+    if (!c || !d_partial) return SMC_E_ARG;
+    if (!c->shard_n || !c->initialized) return SMC_E_STATE;
+    if (c->cfg.model != SMC_MODEL_GMM || c->t_host < 1) return SMC_E_STATE;
+    return gmm_shard_launch(c, 2, d_partial);
+}
+
+int smc_shard_mcmc_finalize(smc_ctx *c, const void *d_partials, int32_t world) {
+    if (!c || !d_partials || world < 1) return SMC_E_ARG;
+    if (!c->shard_n || c->cfg.model != SMC_MODEL_GMM || c->t_host < 1) return SMC_E_STATE;
+    return gmm_shard_finalize_any(c, d_partials, world, 2);
+}
+
 int smc_shard_pack(smc_ctx *c, const int32_t *d_src, int64_t k_lo, int64_t count, void *d_send) {
     if (!c || !d_src || k_lo < 0 || count < 0 || (count && !d_send)) return SMC_E_ARG;
     if (!c->shard_n) return SMC_E_STATE;
     if (!count) return SMC_OK;
     const unsigned g = (unsigned)((count + kBlock - 1) / kBlock);
+    if (c->cfg.model == SMC_MODEL_GMM) {  // every state row of the mixture sampler
+        const int d = (int)c->L.d;
+        if (c->cfg.precision == 32)
+            shard_pack_rows_kernel<float><<<g, kBlock, 0, c->stream>>>(
+                static_cast<const float *>(c->x[0]), static_cast<const float *>(c->x[1]), c->L.ld, d, c->st, d_src,
+                k_lo, count, static_cast<float *>(d_send));
+        else
+            shard_pack_rows_kernel<double><<<g, kBlock, 0, c->stream>>>(
+                static_cast<const double *>(c->x[0]), static_cast<const double *>(c->x[1]), c->L.ld, d, c->st,
+                d_src, k_lo, count, static_cast<double *>(d_send));
+        return cuda_check(cudaGetLastError());
+    }
     if (c->cfg.precision == 32)
         shard_pack_kernel<float><<<g, kBlock, 0, c->stream>>>(pf_args<float>(c), d_src, k_lo, count,
                                                               static_cast<float *>(d_send));
@@ -1396,6 +1441,20 @@ int smc_shard_unpack(smc_ctx *c, const void *d_recv) {
     if (!c || !d_recv) return SMC_E_ARG;
     if (!c->shard_n) return SMC_E_STATE;
     const unsigned g = (unsigned)((c->cfg.n_particles + kBlock - 1) / kBlock);
+    if (c->cfg.model == SMC_MODEL_GMM) {
+        const int d = (int)c->L.d;
+        const int64_t n = c->cfg.n_particles;
+        const double nl = -std::log((double)c->shard_n);
+        if (c->cfg.precision == 32)
+            shard_unpack_rows_kernel<float><<<g, kBlock, 0, c->stream>>>(
+                static_cast<float *>(c->x[0]), static_cast<float *>(c->x[1]), static_cast<float *>(c->lw[0]),
+                static_cast<float *>(c->lw[1]), c->L.ld, d, n, (float)nl, c->st, static_cast<const float *>(d_recv));
+        else
+            shard_unpack_rows_kernel<double><<<g, kBlock, 0, c->stream>>>(
+                static_cast<double *>(c->x[0]), static_cast<double *>(c->x[1]), static_cast<double *>(c->lw[0]),
+                static_cast<double *>(c->lw[1]), c->L.ld, d, n, nl, c->st, static_cast<const double *>(d_recv));
+        return cuda_check(cudaGetLastError());
+    }
     if (c->cfg.precision == 32)
         shard_unpack_kernel<float><<<g, kBlock, 0, c->stream>>>(pf_args<float>(c), static_cast<const float *>(d_recv));
     else
@@ -1514,10 +1573,33 @@ GmmArgs<R> gmm_args(smc_ctx *c) {
     a.hnl_f[1] = (float)(a.half_nd_log2pi - (double)a.hnl_f[0]);
     a.key = key_of(c);
     a.stream = cfg.stream_id;
+    a.index0 = (uint32_t)c->shard_off;
+    a.shard_out = static_cast<Partial *>(c->shard_out);
+    if (c->shard_n) a.log_n = std::log((double)c->shard_n);  // equal weights are 1 / N of the whole sampler
     return a;
 }
 
 enum GmmKernel { GMM_INIT, GMM_REWEIGHT, GMM_MCMC };
+
+// a mixture shard's finalisation on every rank's partials (kind: 0 init,
+// 1 reweight, 2 mcmc), the sampler's N in place of the shard's
+template <typename R, int MOVE>
+int gmm_shard_finalize_move(smc_ctx *c, const Partial *parts, int32_t world, int kind) {
+    GmmArgs<R> a = gmm_args<R>(c);
+    a.n = c->shard_n;
+    a.shard_out = nullptr;
+    gmm_shard_finalize_kernel<R, MOVE><<<1, kBlock, 0, c->stream>>>(a, parts, world, kind);
+    return cuda_check(cudaGetLastError());
+}
+template <typename R>
+int gmm_shard_finalize_r(smc_ctx *c, const Partial *parts, int32_t world, int kind) {
+    switch (c->cfg.gmm.move) {
+        case SMC_GMM_RW: return gmm_shard_finalize_move<R, kMoveRW>(c, parts, world, kind);
+        case SMC_GMM_MALA: return gmm_shard_finalize_move<R, kMoveMALA>(c, parts, world, kind);
+        case SMC_GMM_RW_MALA: return gmm_shard_finalize_move<R, kMoveRWMALA>(c, parts, world, kind);
+    }
+    return SMC_E_ARG;
+}
 
 template <typename R, int NC, int MOVE>
 int gmm_launch_move(smc_ctx *c, GmmKernel k) {
@@ -1623,6 +1705,19 @@ int gmm_launch_alpha(smc_ctx *c) {
                                log_target, c->alpha, reinterpret_cast<AlphaPartial<R> *>(c->ws + c->L.adapt));
     c->dependent_launch = dep;
     return rc;
+}
+
+int gmm_shard_launch(smc_ctx *c, int kind, void *d_partial) {
+    c->shard_out = d_partial;
+    const int rc = gmm_launch_any(c, kind == 0 ? GMM_INIT : kind == 1 ? GMM_REWEIGHT : GMM_MCMC);
+    c->shard_out = nullptr;
+    return rc;
+}
+
+int gmm_shard_finalize_any(smc_ctx *c, const void *d_partials, int32_t world, int kind) {
+    const Partial *p = static_cast<const Partial *>(d_partials);
+    return (c->cfg.precision == 32) ? gmm_shard_finalize_r<float>(c, p, world, kind)
+                                    : gmm_shard_finalize_r<double>(c, p, world, kind);
 }
 
 int gmm_launch_reweight(smc_ctx *c) {

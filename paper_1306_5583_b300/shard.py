@@ -1,7 +1,9 @@
-"""A particle filter partitioned over ranks: one shard per GPU, the weight
-set normalised across ranks and resampling global (the paper's MPI module,
-Sec. 3.1, and its distributed weights; Sec. 5.2.5 runs the GMM sampler that
-way).
+"""A particle filter or the mixture sampler partitioned over ranks: one
+shard per GPU, the weight set normalised across ranks and resampling global
+(the paper's MPI module, Sec. 3.1, and its distributed weights; Sec. 5.2.5
+runs the GMM sampler that way).  The mixture sampler's iteration adds its
+moves after the exchange and one more gather of partials for the
+path-sampling integrand and the acceptance rates.
 
 A filter of N particles is split in blocks: rank r holds the particles
 [off_r, off_r + n_r) under their global Philox indices, so each particle
@@ -131,6 +133,8 @@ class Shard:
         self.ctx = self.sampler.ctx
         smc.check(smc.lib().smc_shard_configure(self.ctx, self.n_global, offs[self.rank]), "smc_shard_configure")
         dev = self.sampler.device
+        self.gmm = config.model == smc.MODEL_GMM
+        self.width = self.sampler.dim  # state values per copy in the exchange
         self.rdtype = torch.float32 if config.precision == 32 else torch.float64
         self.partial = torch.zeros(PARTIAL_BYTES, dtype=torch.uint8, device=dev)
         self.total = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -165,13 +169,23 @@ class Shard:
         return self.range
 
     def pack(self, k_lo, count):
-        send = self.torch.empty(max(count, 1) * 4, dtype=self.rdtype, device=self.partial.device)
+        send = self.torch.empty(max(count, 1) * self.width, dtype=self.rdtype, device=self.partial.device)
         smc.check(smc.lib().smc_shard_pack(self.ctx, self._p(self.src), int(k_lo), int(count), self._p(send)),
                   "smc_shard_pack")
-        return send[:count * 4]
+        return send[:count * self.width]
 
     def unpack(self, recv):
         smc.check(smc.lib().smc_shard_unpack(self.ctx, self._p(recv)), "smc_shard_unpack")
+
+    def mcmc(self):
+        """The mixture sampler's moves of the shard's particles; its partial."""
+        smc.check(smc.lib().smc_shard_mcmc(self.ctx, self._p(self.partial)), "smc_shard_mcmc")
+        return self.partial
+
+    def mcmc_finalize(self, partials):
+        smc.check(smc.lib().smc_shard_mcmc_finalize(self.ctx, self._p(partials), self.world),
+                  "smc_shard_mcmc_finalize")
+        return self.sampler.history(1)[0]
 
     def state(self):
         return self.sampler.state()
@@ -191,7 +205,9 @@ def step(shard, comm):
         send_counts, recv_counts = plan_exchange(ranges, shard.offs, shard.sizes, shard.rank)
         k_lo = int(ranges[shard.rank][0])
         send = shard.pack(k_lo, int(ranges[shard.rank][1]) - k_lo)
-        shard.unpack(comm.all_to_all(send, send_counts, recv_counts, 4))
+        shard.unpack(comm.all_to_all(send, send_counts, recv_counts, shard.width))
+    if shard.gmm and rec["t"] >= 1:  # the mixture sampler's moves, then its path-sampling record
+        rec = shard.mcmc_finalize(comm.all_gather(shard.mcmc()))
     return rec
 
 
@@ -216,11 +232,15 @@ def run_local(shards, steps):
             for me, s in enumerate(shards):
                 _, recv_counts = plan_exchange(ranges, s.offs, s.sizes, me)
                 pieces = []
+                w = s.width
                 for src in range(world):
                     send, counts = sends[src]
-                    start = sum(counts[:me]) * 4
-                    pieces.append(send[start:start + counts[me] * 4])
+                    start = sum(counts[:me]) * w
+                    pieces.append(send[start:start + counts[me] * w])
                 s.unpack(torch.cat(pieces))
+        if shards[0].gmm and rr[0]["t"] >= 1:
+            parts = torch.cat([s.mcmc().clone() for s in shards])
+            rr = [s.mcmc_finalize(parts) for s in shards]
         recs.append(rr[0])
     return recs
 

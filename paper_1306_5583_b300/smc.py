@@ -103,6 +103,8 @@ _SIGS = {
     "smc_shard_select": (_I, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "smc_shard_pack": (_I, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P]),
     "smc_shard_unpack": (_I, [_P, _P]),
+    "smc_shard_mcmc": (_I, [_P, _P]),
+    "smc_shard_mcmc_finalize": (_I, [_P, _P, ctypes.c_int32]),
     "smc_mufu_rate": (_I, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)]),
     "smc_wait_selftest": (_I, [_P]),

@@ -99,3 +99,87 @@ def test_shard_refusals():
     s.initialize()
     with pytest.raises(smc.SMCError):
         s.iterate(1)  # a shard moves only through the exchange
+
+
+def _gmm_cfg(n, T, precision, move, threshold, nd):
+    mv = {"rw": smc.GMM_RW, "mala": smc.GMM_MALA}[move]
+    return smc.make_config(model="gmm", n=n, precision=precision, scheme="systematic", threshold=threshold, seed=3,
+                           max_data=nd, max_records=T + 1, keep_cdf=False,
+                           gmm=dict(n_comp=2, n_iter=T, move=mv, mala_step=0.05, schedule=smc.ALPHA_PRIOR))
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("move", ["rw", "mala"])
+@pytest.mark.parametrize("n,world", [(3001, 2), (4096, 3)])
+def test_gmm_shards_equal_one_context(precision, move, n, world):
+    """The mixture sampler partitioned over shards (reweight, global
+    resampling and exchange, the moves, the path-sampling gather) against
+    one sampler: identical particles after every iteration when every step
+    resamples; the records (normaliser, evidence, path sampling, acceptance)
+    to the rounding of the sums' order."""
+    need_gpu()
+    T, nd = 7, 200
+    y = workloads.gmm_data(nd, seed=0)
+    one = smc.Sampler(_gmm_cfg(n, T, precision, move, 1.0, nd))
+    one.set_data(y)
+    one.initialize()
+    shs = []
+    for r in range(world):
+        sh = shard.Shard(_gmm_cfg(n, T, precision, move, 1.0, nd), n, r, world)
+        sh.set_data(y)
+        sh.initialize()
+        shs.append(sh)
+    recs = shard.run_local(shs, 1)  # t = 0: the prior draws
+    assert np.array_equal(np.concatenate([s.state() for s in shs], axis=1), one.state())
+    for t in range(1, T):
+        one.iterate(1)
+        recs += shard.run_local(shs, 1)
+        assert np.array_equal(np.concatenate([s.state() for s in shs], axis=1), one.state()), t
+    ref = one.history(T)
+    tol = 1e-5 if precision == 32 else 1e-10
+    for r, o in zip(recs, ref):
+        assert r["t"] == o["t"] and r["resampled"] == o["resampled"]
+        for k in ("L", "logZ", "path_u", "path_log_z"):
+            assert abs(r[k] - o[k]) <= tol * max(1.0, abs(o[k])), (r["t"], k, r[k], o[k])
+        assert r["accept"] == o["accept"] and r["accept_mala"] == o["accept_mala"]
+    for s in shs:
+        s.close()
+    one.close()
+
+
+def test_gmm_shard_refuses_an_adaptive_schedule():
+    need_gpu()
+    cfg = _gmm_cfg(1000, 5, 32, "rw", 0.5, 50)
+    cfg.gmm.schedule = smc.ALPHA_ADAPTIVE
+    with pytest.raises(smc.SMCError) as e:
+        shard.Shard(cfg, 2000, 0, 2)
+    assert e.value.code == smc.E_ARG
+
+
+def test_gmm_fp64_shards_with_the_ess_test_equal_one_context():
+    """With the ESS test (some steps resample, some not): the same decisions,
+    particles and records as one sampler."""
+    need_gpu()
+    n, T, nd = 5000, 12, 200
+    y = workloads.gmm_data(nd, seed=0)
+    one = smc.Sampler(_gmm_cfg(n, T, 64, "rw", 0.5, nd))
+    one.set_data(y)
+    one.initialize()
+    one.iterate(T - 1)
+    shs = []
+    for r in range(2):
+        sh = shard.Shard(_gmm_cfg(n, T, 64, "rw", 0.5, nd), n, r, 2)
+        sh.set_data(y)
+        sh.initialize()
+        shs.append(sh)
+    recs = shard.run_local(shs, T)
+    ref = one.history(T)
+    assert any(o["resampled"] for o in ref[1:]) and not all(o["resampled"] for o in ref[1:])
+    for r, o in zip(recs, ref):
+        assert r["resampled"] == o["resampled"]
+        for k in ("L", "logZ", "ess", "path_log_z"):
+            assert abs(r[k] - o[k]) <= 1e-9 * max(1.0, abs(o[k])), (r["t"], k, r[k], o[k])
+    assert np.array_equal(np.concatenate([s.state() for s in shs], axis=1), one.state())
+    for s in shs:
+        s.close()
+    one.close()

@@ -28,6 +28,7 @@ class OracleShard:
 
     def __init__(self, n_global, rank, world, y, threshold):
         self.n_global, self.rank, self.world = n_global, rank, world
+        self.gmm, self.width = False, 4  # a particle filter: four state values per copy
         self.offs, self.sizes = shard.partition(n_global, world)
         self.n = self.sizes[rank]
         self.idx = np.arange(self.offs[rank], self.offs[rank] + self.n)
