@@ -339,7 +339,7 @@ def run_ours(args):
         extra = {}
         mufu = mufu_peak(dev)
         extra["mufu_peak_measured"] = mufu
-        extra["config0_fp64_n1000_T100"] = bench_config0(dev, stream)
+        extra["pf_fp64_n1000_T100"] = bench_pf_fp64_small(dev, stream)
         extra["gmm_rw_n2^16"] = bench_gmm(dev, stream, mufu, move="rw")
         extra["gmm_mala_n2^18"] = bench_gmm(dev, stream, mufu, n=1 << 18, move="mala")
         extra["gmm_rw_vs_mala_n2^18"] = bench_gmm_accuracy(dev, stream, seeds=args.gmm_seeds)
@@ -526,7 +526,7 @@ def bench_gmm_accuracy(dev, stream, n=1 << 18, T=500, seeds=8):
 
 
 def bench_batched(dev, stream, count=256):
-    """Config 4: 256 filters of uneven N and T in one launch per kernel per
+    """256 filters of uneven N and T in one launch per kernel per
     iteration, against the same 256 filters run one by one through the plain
     API.  Both arms are timed by CUDA events on one stream around the
     iteration work only: every plain context is created, given its data and
@@ -637,8 +637,8 @@ def bench_pf_grad(dev, stream, n=1 << 18, T=500):
     return out
 
 
-def bench_config0(dev, stream, T=100, n=1000, reps=5):
-    """Config 0: the FP64 particle filter at the paper's example size
+def bench_pf_fp64_small(dev, stream, T=100, n=1000, reps=5):
+    """The FP64 particle filter at the paper's example size
     (N = 1000, T = 100): device time per iteration of the replayed graph."""
     import torch
     from paper_1306_5583_b300 import smc, workloads
@@ -742,12 +742,12 @@ def cpu_baseline_all_cores(n, iters):
 
 def oracle_baselines():
     """The FP64 oracle (numpy, one process) on bounded samples of the other
-    configurations, in particle-updates per second: config 0 in full
-    (N = 1000, T = 100); the GMM sampler (configs 2, 3a) on one iteration at
-    N = 2^12 late in the schedule (each particle-update costs the same at
-    any N); the gradient (config 3b) on a recorded forward run plus its
-    reverse sweep at N = 2^10, T = 50; the batched filters (config 4) run
-    the particle filter's arithmetic, whose rate the config-1 baseline
+    workloads, in particle-updates per second: the FP64 filter at N = 1000,
+    T = 100 in full; the GMM sampler (random-walk and Langevin moves) on one
+    iteration at N = 2^12 late in the schedule (each particle-update costs
+    the same at any N); the likelihood gradient on a recorded forward run
+    plus its reverse sweep at N = 2^10, T = 50; the batched filters run the
+    particle filter's arithmetic, whose rate the N = 2^20 filter's baseline
     gives."""
     from oracle import cv as ocv
     from oracle import gmm as ogmm
@@ -760,7 +760,7 @@ def oracle_baselines():
     _, y = workloads.cv_data(100, seed=0, **p)
     t0 = time.perf_counter()
     ocv.run(y, 1000, 0, op, scheme="systematic", threshold=0.5)
-    out["config0_fp64_n1000_T100"] = {"value": 1000 * 99 / (time.perf_counter() - t0), "sample": "the whole run"}
+    out["pf_fp64_n1000_T100"] = {"value": 1000 * 99 / (time.perf_counter() - t0), "sample": "the whole run"}
     yg = workloads.gmm_data(1000, seed=0)
     gp = ogmm.GMMParams(r=4, T=500, power=5.0)
     n = 1 << 12
