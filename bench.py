@@ -329,6 +329,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
+        "device": device_summary(dev),
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(n, 8)
@@ -352,6 +353,16 @@ def run_ours(args):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def device_summary(dev):
+    """The GPU the numbers come from, read at run time: name, SM count and
+    L2 size (the flush writes FLUSH_BYTES between timed iterations)."""
+    import torch
+    pr = torch.cuda.get_device_properties(dev)
+    l2 = int(getattr(pr, "L2_cache_size", 0))
+    return {"name": pr.name, "sms": int(pr.multi_processor_count), "l2_bytes": l2,
+            "flush_over_l2": round(FLUSH_BYTES / l2, 2) if l2 else None}
 
 
 def run_e2e(make, scheme, K, W, y, dev, stream, flush):
