@@ -68,15 +68,16 @@ def test_chunked_iterate_fp64_matches_oracle():
     s.close()
 
 
-@pytest.mark.parametrize("threshold", [0.5, 1.0])
-def test_iterations_in_a_callers_graph(threshold):
+@pytest.mark.parametrize("precision,scheme,threshold", [(32, "systematic", 0.5), (32, "systematic", 1.0),
+                                                        (64, "stratified", 0.5), (32, "multinomial", 0.5)])
+def test_iterations_in_a_callers_graph(precision, scheme, threshold):
     """Iterations recorded into the caller's capture and replayed by the
     caller give the same particles and records as smc_iterate."""
     need_gpu()
     n, T, W, K = 50000, 40, 3, 12
     stream = torch.cuda.Stream()
-    s, _, _ = _sampler(n, T, 32, "systematic", threshold, stream)
-    ref, _, _ = _sampler(n, T, 32, "systematic", threshold, stream)
+    s, _, _ = _sampler(n, T, precision, scheme, threshold, stream)
+    ref, _, _ = _sampler(n, T, precision, scheme, threshold, stream)
     with torch.cuda.stream(stream):
         s.initialize()
         s.iterate(1)  # the context's own iteration graph (the launch form the capture takes)
