@@ -248,10 +248,14 @@ __device__ __forceinline__ void pf_finalize(const PfArgs<R> &a, DevState *st, co
 // Five blocks per SM for FP32 (48 registers, no spills; six spill), four
 // for FP64.  FP32: four particles per thread, 1024-particle tiles; FP64: one
 // particle per thread, a.tile_threads per block.
-template <typename R>
+template <typename R, bool kChain = false>
 __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 5 : 4) pf_iterate_kernel(PfArgs<R> a) {
     constexpr int E = (sizeof(R) == 4) ? kPfItems : 1;
     const uint32_t tt = (sizeof(R) == 4) ? (uint32_t)kBlock : a.tile_threads;
+    // kChain: a later iteration of a captured chain, launched as a
+    // programmatic dependent of the previous iteration's last kernel; it
+    // waits for that grid before it reads anything
+    if constexpr (kChain) asm volatile("griddepcontrol.wait;" ::: "memory");
     DevState *st = a.st;
     // the ancestor indices do not depend on the state block: their load is
     // in flight while the snapshot is read (unused when nothing is gathered)

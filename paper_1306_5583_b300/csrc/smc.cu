@@ -202,6 +202,9 @@ struct smc_ctx {
     cudaEvent_t ev_move[2]; // profiling: recorded around the move kernel in the iteration graph
     int dependent_launch;   // while capturing: launch the one-pass resampler as a programmatic dependent
     int no_dependent;       // the driver refused the programmatic dependent launch once: capture without
+    int chain_move;         // while capturing a later iteration of a chain: the move kernel is a
+                            // programmatic dependent of the previous iteration's last kernel
+    int no_chain;           // the driver refused that once: chains capture ordinary edges
     int64_t shard_n;        // a shard of a partitioned filter: the filter's N (0: not a shard)
     int64_t shard_off;      // and the global index of the shard's first particle
     void *shard_out;        // while launching a mixture shard's kernel: where its partial goes
@@ -350,6 +353,20 @@ PfArgs<R> pf_args(smc_ctx *c) {
 template <typename R>
 int launch_pf(smc_ctx *c) {
     PfArgs<R> a = pf_args<R>(c);
+    if (c->chain_move) {
+        // a later iteration of a captured chain: its blocks launch while the
+        // previous iteration's last kernel completes and wait for it first
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)c->L.nbw_move);
+        lc.blockDim = dim3(kBlock);
+        lc.stream = c->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        return cuda_check(cudaLaunchKernelEx(&lc, pf_iterate_kernel<R, true>, a));
+    }
     if (c->capture_host_io && c->dependent_launch) {
         // smc_iterate_host's graph: a programmatic dependent of host_obs_kernel
         a.obs_after_wait = 1;
@@ -737,11 +754,16 @@ void drop_graphs(smc_ctx *c) {
 }
 
 // iterations: how many consecutive iterations the graph holds (host_io: 1)
-int build_graph_once(smc_ctx *c, cudaGraphExec_t *dst, bool host_io, int iterations = 1) {
+// chain: the move kernels after the first as programmatic dependents (PF)
+int build_graph_once(smc_ctx *c, cudaGraphExec_t *dst, bool host_io, int iterations = 1, bool chain = false) {
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SMC_E_CUDA;
     int rc = SMC_OK;
-    for (int i = 0; i < iterations && !rc; ++i) rc = launch_iteration_io(c, host_io);
+    for (int i = 0; i < iterations && !rc; ++i) {
+        c->chain_move = (i > 0 && chain) ? 1 : 0;
+        rc = launch_iteration_io(c, host_io);
+    }
+    c->chain_move = 0;
     const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (rc || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -781,7 +803,14 @@ int build_graph_chunk(smc_ctx *c) {
     if (c->graph_chunk) return SMC_OK;
     if (int rc = build_graph(c)) return rc;
     c->dependent_launch = (!c->no_dependent && !c->ev_move[1]) ? 1 : 0;
-    const int rc = build_graph_once(c, &c->graph_chunk, false, kIterChunk);
+    // the particle filters' move kernels after the first wait for the
+    // previous iteration as programmatic dependents (no event node between)
+    const bool chain = c->dependent_launch && !c->no_chain && c->cfg.model != SMC_MODEL_GMM && !c->ev_move[0];
+    int rc = build_graph_once(c, &c->graph_chunk, false, kIterChunk, chain);
+    if (rc != SMC_OK && chain) {  // refused once: ordinary edges from now on
+        c->no_chain = 1;
+        rc = build_graph_once(c, &c->graph_chunk, false, kIterChunk);
+    }
     c->dependent_launch = 0;
     return rc;
 }
