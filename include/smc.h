@@ -138,7 +138,7 @@ typedef struct {
     int32_t model;        /* SMC_MODEL_* */
     int32_t precision;    /* 32: FP32 per particle, FP64 normaliser and evidence;
                              64: FP64 throughout */
-    int64_t n_particles;  /* N >= 1 */
+    int64_t n_particles;  /* 1 <= N <= 2^30 (smc_create refuses others) */
     int32_t max_records;  /* iteration records kept on the device (ring), >= 2 */
     int32_t scheme;       /* SMC_* resampling scheme */
     double threshold;     /* resample when ESS < threshold * N; >= 1 always, <= 0 never */

@@ -1104,6 +1104,18 @@ static int copy_out(smc_ctx *c, void *dst, const void *src, size_t bytes, int on
     return rc2 ? rc2 : rc;
 }
 
+// One copy per row: the runtime's pitched copies refuse pitches above
+// 2^31 - 1 bytes, which rows of more than 2^29 floats exceed.
+static int copy_pitched(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, int rows,
+                        cudaMemcpyKind k, cudaStream_t stream) {
+    for (int r = 0; r < rows; ++r) {
+        const int rc = cuda_check(cudaMemcpyAsync(static_cast<char *>(dst) + (size_t)r * dpitch,
+                                                  static_cast<const char *>(src) + (size_t)r * spitch, width, k, stream));
+        if (rc) return rc;
+    }
+    return SMC_OK;
+}
+
 // state rows are stored with a pitch of ld elements; callers see d x N packed
 static int copy_rows(smc_ctx *c, void *dst, const void *src, int rows, bool to_caller, int on_device) {
     const size_t w = (size_t)c->cfg.n_particles * c->L.rsize, pitch = (size_t)c->L.ld * c->L.rsize;
@@ -1111,7 +1123,7 @@ static int copy_rows(smc_ctx *c, void *dst, const void *src, int rows, bool to_c
     if (to_caller) k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     else k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t dpitch = to_caller ? w : pitch, spitch = to_caller ? pitch : w;
-    int rc = cuda_check(cudaMemcpy2DAsync(dst, dpitch, src, spitch, w, (size_t)rows, k, c->stream));
+    int rc = copy_pitched(dst, dpitch, src, spitch, w, rows, k, c->stream);
     if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream));
     return rc;
 }
@@ -2272,8 +2284,7 @@ int smc_batch_read_state(smc_batch *bt, int32_t filter, void *dst, int on_device
     const size_t rs = P.rsize;
     const char *base = bt->ws + P.o_x + (size_t)(h[i].cur & 1) * 4 * P.ntot * rs + (size_t)P.off[i] * rs;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    int rc2 = cuda_check(cudaMemcpy2DAsync(dst, (size_t)P.n[i] * rs, base, (size_t)P.ntot * rs, (size_t)P.n[i] * rs, 4,
-                                           k, bt->stream));
+    int rc2 = copy_pitched(dst, (size_t)P.n[i] * rs, base, (size_t)P.ntot * rs, (size_t)P.n[i] * rs, 4, k, bt->stream);
     if (!rc2) rc2 = cuda_check(cudaStreamSynchronize(bt->stream));
     return rc2 ? rc2 : rc;
 }

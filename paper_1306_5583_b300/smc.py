@@ -325,6 +325,22 @@ class Sampler:
         check(lib().smc_read_cdf(self.ctx, out.ctypes.data_as(_P), 0), "smc_read_cdf")
         return out
 
+    # -- readers into device tensors (the same layouts, copied on the device) --
+    def read_device(self, what):
+        """A new device tensor holding the context's current `what`:
+        "state" (d x N), "log_weight" (N), "ancestors" (N int32) or "cdf"
+        (N fixed-point values, as int64 bit patterns: every value is below
+        2^62).  Only the device-to-device copy of smc_read_* runs; nothing
+        crosses to the host."""
+        torch = self.torch
+        shape, dtype, fn = {"state": ((self.dim, self.n), self.tdtype, "smc_read_state"),
+                            "log_weight": ((self.n,), self.tdtype, "smc_read_log_weight"),
+                            "ancestors": ((self.n,), torch.int32, "smc_read_ancestors"),
+                            "cdf": ((self.n,), torch.int64, "smc_read_cdf")}[what]
+        out = torch.empty(shape, dtype=dtype, device=self.device)
+        check(getattr(lib(), fn)(self.ctx, _P(out.data_ptr()), 1), fn)
+        return out
+
     def history(self, count):
         recs = (Record * count)()
         n = ctypes.c_int32()
