@@ -1104,8 +1104,9 @@ static int copy_out(smc_ctx *c, void *dst, const void *src, size_t bytes, int on
     return rc2 ? rc2 : rc;
 }
 
-// One copy per row: the runtime's pitched copies refuse pitches above
-// 2^31 - 1 bytes, which rows of more than 2^29 floats exceed.
+// One copy per row: pitched copies are specified for pitches up to
+// cudaDevAttrMaxPitch (2^31 - 1 bytes), which rows of more than 2^29
+// floats exceed.
 static int copy_pitched(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, int rows,
                         cudaMemcpyKind k, cudaStream_t stream) {
     for (int r = 0; r < rows; ++r) {
