@@ -14,7 +14,8 @@ Checked, per iteration (Algorithm 1, every iteration resampling):
   and sampled outputs k against the selection rule on the GPU's CDF:
   a_k is the first i with Q_i > the target of k, i.e.
   Q_{a_k - 1} <= target < Q_{a_k} (Q_{-1} = 0), which fixes a_k uniquely
-  without the whole CDF on the host.
+  without the whole CDF on the host (systematic, stratified and, for the
+  first step, multinomial).
 """
 import math
 
@@ -111,6 +112,51 @@ def test_maximum_size_sampled(scheme):
             for k, j, a_k, q_lo, q_hi in zip(ks, js, ak, lo, hi):
                 target = (QN * ((int(k) << 25) + 2 * j + 1)) // (n << 25)
                 assert int(q_lo) <= target < int(q_hi), (scheme, t, int(k), int(a_k))
+    finally:
+        s.close()
+        torch.cuda.empty_cache()
+
+
+def test_maximum_size_multinomial():
+    """Multinomial resampling of the first step at N = 2^30: about 64 draws
+    per 24-bit value, so every bucket of the kernel's draw histogram takes
+    its byte-count path.  Sampled outputs k against the rule
+    a_k = the first i with Q_i > Q_N (2 j_(k) + 1) / 2^25 on the GPU's CDF,
+    j_(k) the k-th smallest of the oracle's 2^30 draws (their histogram,
+    from a spawned process pool started before the GPU work)."""
+    import multiprocessing as mp
+    import os
+
+    import draw_hist
+
+    need_gpu()
+    n, seed = N_MAX, 0
+    _need_memory(100 << 30)
+    cores = max(1, min(16, len(os.sched_getaffinity(0))))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        counts = draw_hist.draw_counts(seed, 0, n, pool, 4 * cores)
+    assert counts.max() < 256  # no byte of the kernel's histogram wraps
+    H = np.concatenate([[0], np.cumsum(counts)])  # H[v] = #{k : j_k < v}
+    assert H[-1] == n
+    s, y, op = make_pf(n, 2, 32, scheme="multinomial", seed=seed, threshold=1.0)
+    try:
+        s.initialize()  # the first move, then (always) resampling at t = 0
+        assert s.history(1)[0]["resampled"]
+        Q = s.read_device("cdf")
+        assert bool(torch.all(Q[1:] >= Q[:-1]))
+        QN = int(Q[-1])
+        a = s.read_device("ancestors")
+        assert bool(torch.all(a[1:] >= a[:-1])) and int(a[0]) >= 0 and int(a[-1]) < n
+        g = np.random.default_rng(11)
+        ks = np.unique(np.concatenate([g.choice(n, size=3000, replace=False), [0, n - 1]]))
+        js = np.searchsorted(H, ks, side="right") - 1  # H[j] <= k < H[j + 1]: the k-th smallest draw
+        ak = _host(a, ks).astype(np.int64)
+        hi = _host(Q, ak).astype(object)
+        lo = np.where(ak > 0, _host(Q, np.maximum(ak - 1, 0)), 0).astype(object)
+        del Q, a
+        for k, j, a_k, q_lo, q_hi in zip(ks, js, ak, lo, hi):
+            target = (QN * (2 * int(j) + 1)) >> 25
+            assert int(q_lo) <= target < int(q_hi), (int(k), int(j), int(a_k))
     finally:
         s.close()
         torch.cuda.empty_cache()

@@ -71,3 +71,18 @@ def test_streams_differ_by_every_counter_word():
         w = philox.draw_words(1, args["index"], args["t"], args["tag"], args["stream"], args["draw"])[0]
         assert not np.array_equal(w, base)
     assert not np.array_equal(philox.draw_words(2, [5], 2, philox.TAG_MOVE)[0], base)
+
+
+def test_draw_histogram_helper_counts_the_resampling_draws():
+    """tests/draw_hist.py (the large-N tests' draw histogram, computed a
+    range of Philox calls at a time) counts exactly the draws of
+    resample_u24, split over any number of parts."""
+    import draw_hist
+
+    class Serial:
+        imap_unordered = staticmethod(map)
+
+    n = 4 * 5003
+    want = np.bincount(philox.resample_u24(3, 7, n), minlength=1 << 24)
+    for parts in (1, 3, 8):
+        assert np.array_equal(draw_hist.draw_counts(3, 7, n, Serial(), parts), want)
