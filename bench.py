@@ -291,7 +291,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = PF_BYTES_PER_PARTICLE * n / (move_us * 1e-6) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": measured_traffic(), "kernel": "pf_iterate_kernel<float>",
+                "frac": round(achieved / peak, 4), "traffic": measured_traffic(), "kernel": "pf_iterate_kernel<float, 0>",
                 "kernel_us": round(move_us, 2),
                 "kernel_timing": "mean over the timed steps of CUDA events captured immediately before and after the "
                                  "move kernel in the iteration graph (L2 flushed before each step); a standalone "
