@@ -63,11 +63,13 @@ def test_fp64_filter_end_to_end(scheme):
     assert abs(s.log_evidence() - ref[-1]["logZ"]) < 1e-9
 
 
-@pytest.mark.parametrize("n", [1, 63, 64, 65, 65536, 65537])
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 65536, 65537, 262144, 262145, (1 << 20) + 3])
 def test_fp64_move_tiling_boundaries(n):
     """FP64 move tiles: one particle per thread, 64 threads per block up to
     N = 2^16 and 256 above; sizes on both sides of a tile and of the
-    switch, ragged last tiles included, against the free-running oracle."""
+    switch, ragged last tiles included, and on both sides of 1024 blocks,
+    above which the last block combines the block partials in several
+    passes; against the free-running oracle."""
     need_gpu()
     T, seed = 6, 7
     s, y, op = make_pf(n, T, 64, scheme="systematic", seed=seed, threshold=0.9)
