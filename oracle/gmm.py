@@ -143,12 +143,14 @@ def proposal_scales(a):
     return 0.15 / a, (1 + math.sqrt(1 / a)) * 0.15, (1 + math.sqrt(1 / a)) * 0.2
 
 
-def mh_block(s, block, a_t, t, y, seed, p, stream=0, return_delta=False):
+def mh_block(s, block, a_t, t, y, seed, p, stream=0, return_delta=False, slots=None):
     """One Metropolis random-walk block at alpha_t.  Returns the new state
     and the acceptance indicators (and the log acceptance ratio and log u
-    when asked)."""
+    when asked).  slots: the particles' slots, i.e. their Philox counter
+    indices (default 0 .. n-1; a subset of a larger system for sampled
+    checks)."""
     n = s.mu.shape[1]
-    idx = np.arange(n)
+    idx = np.arange(n) if slots is None else np.asarray(slots)
     s_mu, s_lam, s_om = proposal_scales(a_t)
     tag = {"mu": philox.TAG_MH_MU, "lambda": philox.TAG_MH_LAMBDA, "weight": philox.TAG_MH_WEIGHT}[block]
     r = p.r
@@ -385,10 +387,12 @@ def grad_log_target_u(u, a_t, y, p):
     return np.concatenate([g_mu, g_lam, g_z]), ll
 
 
-def mala_step(s, a_t, t, y, seed, p, eps=0.05, stream=0, return_delta=False):
+def mala_step(s, a_t, t, y, seed, p, eps=0.05, stream=0, return_delta=False, slots=None):
+    """One Langevin (MALA) move at alpha_t in the unconstrained coordinates;
+    slots as in mh_block."""
     n = s.mu.shape[1]
     r = p.r
-    idx = np.arange(n)
+    idx = np.arange(n) if slots is None else np.asarray(slots)
     u = to_unconstrained(s.mu, s.lam, s.om)
     g, _ = grad_log_target_u(u, a_t, y, p)
     xi = philox.normals(seed, idx, t, philox.TAG_MALA, 3 * r - 1, stream)

@@ -242,44 +242,13 @@ def test_benchmark_size_sampled():
         a_t = ogmm.alpha(t, op)
         for block in ("mu", "lambda", "weight"):
             ll_before = st.llik.copy()
-            st, acc, delta, logu = _mh_block_at(st, block, a_t, t, y, seed, op, idx)
+            st, acc, delta, logu = ogmm.mh_block(st, block, a_t, t, y, seed, op, return_delta=True, slots=idx)
             near |= np.abs(delta - logu) < _tie_window(32, a_t, ll_before, delta)
         ok = ~near
         gm, gl, go, glp, gll = split_state(x[:, idx], r)
         assert_close(gm[:, ok], st.mu[:, ok], 1e-5, f"mu t={t}")
         assert_close(gll[ok], st.llik[ok], 1e-5, f"l t={t}")
         assert near.sum() <= 10
-
-
-def _mh_block_at(s, block, a_t, t, y, seed, p, idx):
-    """oracle.gmm.mh_block for particles at slots idx (counter = slot)."""
-    import oracle.gmm as m
-    s_mu, s_lam, s_om = m.proposal_scales(a_t)
-    tag = {"mu": ophilox.TAG_MH_MU, "lambda": ophilox.TAG_MH_LAMBDA, "weight": ophilox.TAG_MH_WEIGHT}[block]
-    r = p.r
-    mu, lam, om = s.mu.copy(), s.lam.copy(), s.om.copy()
-    jac = np.zeros(idx.size)
-    if block == "mu":
-        mu = mu + s_mu * ophilox.normals(seed, idx, t, tag, r)
-    elif block == "lambda":
-        z = s_lam * ophilox.normals(seed, idx, t, tag, r)
-        lam = np.exp(np.log(lam) + z)
-        jac = z.sum(axis=0)
-    else:
-        zr = np.log(om[:-1] / om[-1:]) + s_om * ophilox.normals(seed, idx, t, tag, r - 1)
-        full = np.concatenate([zr, np.zeros((1, idx.size))])
-        e = np.exp(full - full.max(axis=0))
-        om = e / e.sum(axis=0)
-        jac = np.log(om).sum(axis=0) - np.log(s.om).sum(axis=0)
-    lp = m.log_prior(mu, lam, om, p)
-    ll = m.log_lik(mu, lam, om, y)
-    delta = (lp + a_t * ll) - (s.lprior + a_t * s.llik) + jac
-    w = ophilox.draw_words(seed, idx, t, tag, 0, ophilox.DRAW_MH_UNIFORM)
-    logu = np.log(ophilox.uniform(w[:, 0]))
-    acc = logu <= delta
-    new = m.State(np.where(acc, mu, s.mu), np.where(acc, lam, s.lam), np.where(acc, om, s.om),
-                  np.where(acc, lp, s.lprior), np.where(acc, ll, s.llik))
-    return new, acc, delta, logu
 
 
 @pytest.mark.parametrize("precision,move,r", [(64, "mala", 4), (32, "mala", 4), (32, "rw_mala", 3), (32, "mala", 1)])
@@ -404,3 +373,43 @@ def test_adaptive_alpha_fp32_hits_the_cess_target():
     b.iterate(6 + 5)
     got = b.history(1)[0]
     assert got["alpha"] == ref["alpha"] and got["logZ"] == ref["logZ"]
+
+
+def test_langevin_benchmark_size_sampled():
+    """The Langevin workload at its benchmarked size (N = 2^18, n = 1000,
+    r = 4, step 0.05, FP32; 4096 blocks of mcmc partials, combined in
+    several passes): sampled particles of a few iterations against the
+    oracle's MALA step at their own slots, and their cached likelihood
+    gradients against the oracle's."""
+    need_gpu()
+    n, r, seed, eps = 1 << 18, 4, 0, 0.05
+    s, y, op = make_gmm(n, nd=1000, r=r, T=500, precision=32, seed=seed, move="mala", eps=eps)
+    s.initialize()
+    g = np.random.default_rng(9)
+    idx = np.sort(g.choice(n, size=512, replace=False))
+    near_total = 0
+    for t in range(1, 4):
+        s.move()
+        rec = s.history(1)[0]
+        s.resample()
+        src = s.ancestors().astype(np.int64)[idx] if rec["resampled"] else idx
+        xin = s.state().astype(np.float64)[:, src]
+        mu, lam, om = xin[:r], xin[r:2 * r], xin[2 * r:3 * r]
+        st = ogmm.State(mu.copy(), lam.copy(), om.copy(), ogmm.log_prior(mu, lam, om, op),
+                        ogmm.log_lik(mu, lam, om, y))
+        _, gm, gl, gz = ogmm.loglik_grad(st.mu, st.lam, st.om, y)
+        ref = np.concatenate([gm, gl, gz])
+        assert_close(xin[3 * r + 2:], ref, 2e-4 * np.max(np.abs(ref)), f"cached gradient t={t}")
+        a_t = ogmm.alpha(t, op)
+        ll_before = st.llik.copy()
+        st, acc, delta, logu = ogmm.mala_step(st, a_t, t, y, seed, op, eps=eps, return_delta=True, slots=idx)
+        near = np.abs(delta - logu) < _tie_window(32, a_t, ll_before, delta)
+        near_total += int(near.sum())
+        s.mcmc()
+        x = s.state().astype(np.float64)[:, idx]
+        ok = ~near
+        assert_close(x[:r][:, ok], st.mu[:, ok], 1e-5, f"mu t={t}")
+        assert_close(x[r:2 * r][:, ok], st.lam[:, ok], 1e-5, f"lambda t={t}")
+        assert_close(x[2 * r:3 * r][:, ok], st.om[:, ok], 1e-5, f"omega t={t}")
+        assert_close(x[3 * r + 1][ok], st.llik[ok], 1e-5, f"log-likelihood t={t}")
+    assert near_total <= 0.01 * idx.size * 3 + 2

@@ -185,6 +185,29 @@ def test_mala_leaves_the_prior_invariant():
     assert stats.kstest(s.om[2], stats.beta(1, 2).cdf).pvalue > 1e-4
 
 
+def test_moves_at_slots_equal_the_same_particles_of_the_whole_system():
+    """mh_block and mala_step with explicit slots (the Philox counter index
+    of each particle) give exactly the rows of the whole system's move at
+    those slots: a particle's move depends on its own slot only."""
+    p = gmm.GMMParams(r=3)
+    y = workloads.gmm_data(40, seed=1)
+    s = gmm.init_state(300, y, 4, p)
+    sub = np.array([0, 7, 8, 150, 299])
+    a_t = 0.3
+    for block in ("mu", "lambda", "weight"):
+        whole, acc_w, d_w, u_w = gmm.mh_block(s, block, a_t, 5, y, 4, p, return_delta=True)
+        part, acc_p, d_p, u_p = gmm.mh_block(s.take(sub), block, a_t, 5, y, 4, p, return_delta=True, slots=sub)
+        assert np.array_equal(part.mu, whole.mu[:, sub]) and np.array_equal(part.om, whole.om[:, sub])
+        assert np.array_equal(d_p, d_w[sub]) and np.array_equal(u_p, u_w[sub]) and np.array_equal(acc_p, acc_w[sub])
+    whole, acc_w, d_w, u_w = gmm.mala_step(s, a_t, 6, y, 4, p, eps=0.05, return_delta=True)
+    part, acc_p, d_p, u_p = gmm.mala_step(s.take(sub), a_t, 6, y, 4, p, eps=0.05, return_delta=True, slots=sub)
+    assert np.array_equal(part.lam, whole.lam[:, sub]) and np.array_equal(d_p, d_w[sub])
+    assert np.array_equal(acc_p, acc_w[sub])
+    # the default slots are 0 .. n - 1
+    same, _ = gmm.mh_block(s, "mu", a_t, 5, y, 4, p, slots=np.arange(300))
+    assert np.array_equal(same.mu, gmm.mh_block(s, "mu", a_t, 5, y, 4, p)[0].mu)
+
+
 def test_adaptive_alpha_two_point_closed_form():
     """Uniform W and l_i in {0, -c} (half each): CESS(delta) =
     N (1 + u)^2 / (2 (1 + u^2)) with u = exp(-c delta), so CESS = rho N at
