@@ -51,6 +51,22 @@ def test_fp32_gradient_matches_oracle():
     assert abs(s.pf_replay(th) - s.log_evidence()) < 1e-6 * abs(s.log_evidence())
 
 
+def test_fp32_gradient_at_the_benchmarked_size():
+    """N = 2^18 with a checkpoint every 16 iterations, the benchmarked
+    launch configuration (T = 40 instead of 500 keeps the oracle's reverse
+    sweep to seconds; three checkpoint segments, the last one ragged): the
+    FP32 gradient and estimate against the oracle's float64 ones on the
+    GPU-recorded resampling."""
+    need_gpu()
+    n, T, seed = 1 << 18, 40, 1
+    s, y, op, anc = _run(n, T, 32, seed=seed, threshold=0.5, ck=16)
+    assert any(a is not None for a in anc[:-1]) and any(a is None for a in anc[:-1])
+    g = s.pf_grad()
+    J, gref = ograd.gradient(y, n, seed, op, anc)
+    assert abs(s.log_evidence() - J) < 1e-4 + 1e-6 * abs(J), (s.log_evidence(), J)
+    assert np.allclose(g, gref, rtol=1e-4, atol=1e-4 * np.abs(gref).max()), (g, gref)
+
+
 def test_fp64_gradient_matches_finite_differences_of_the_gpu_replay():
     """Central differences (h = 1e-3 relative) of the GPU's own replayed
     estimate, in float64 where the difference quotient is not dominated by
