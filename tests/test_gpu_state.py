@@ -156,8 +156,18 @@ def test_iterate_host_matches_stored_observations(precision, on_stream):
     over the same observations stored up front: on the legacy stream (stream
     copies) and on a stream of its own (one graph launch, the observation
     and the record through the mapped staging)."""
+    _host_vs_stored(precision, on_stream, 5000)
+
+
+def test_iterate_host_at_the_benchmarked_size():
+    """The same at N = 2^20 in FP32 on a stream of its own: the end-to-end
+    call as the benchmark makes it."""
+    _host_vs_stored(32, True, 1 << 20)
+
+
+def _host_vs_stored(precision, on_stream, n):
     need_gpu()
-    n, T = 5000, 10
+    T = 10
     p = cv_params()
     _, y = workloads.cv_data(T, seed=0, **p)
 
