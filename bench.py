@@ -405,12 +405,14 @@ def run_e2e(make, scheme, K, W, y, dev, stream, flush):
     s.close()
     # host -> device per step: the observation (2 float64) and its flag word, read from the
     # context's mapped pinned staging by the first kernel of the call's graph; device -> host:
-    # the step's record, written there by the move kernel (the error word only on an error)
+    # the step's record, written there by the move kernel (the error word only on an error),
+    # and the call's sequence number, written by the graph's last kernel
     return {"value": s.n * steps / total, "unit": "particle-updates/s", "h2d_bytes_per_step": 16 + 4,
-            "d2h_bytes_per_step": ctypes.sizeof(smc.Record),
-            "timing": f"host wall clock per call (synchronising), {W} untimed calls first; one graph launch "
-                      "per call, the observation and the record through mapped pinned memory, the call's "
-                      "ctypes arguments built once before the loop",
+            "d2h_bytes_per_step": ctypes.sizeof(smc.Record) + 4,
+            "timing": f"host wall clock per call, {W} untimed calls first; one graph launch per call, the "
+                      "observation and the record through mapped pinned memory, the call returning when the "
+                      "graph's last kernel has written its sequence number there; the call's ctypes arguments "
+                      "built once before the loop",
             "per_call_us": {"p50": round(float(np.percentile(per_call, 50)) * 1e6, 1),
                             "p90": round(float(np.percentile(per_call, 90)) * 1e6, 1),
                             "max": round(float(np.max(per_call)) * 1e6, 1)}}

@@ -233,13 +233,18 @@ int smc_iterate(smc_ctx *ctx, int32_t n);
 
 /* One iteration with host buffers: copies obs_t (CV: 2 float64; may be NULL
  * to use the observation already stored for t) to the device, runs one
- * iteration and copies its record to *h_record.  Synchronises; returns the
- * device error word of the step.  SMC_E_ARG past the last observation (or
- * the GMM schedule).  On a non-default stream (and without SMC_FLAG_RECORD)
- * the step is one graph launch: obs_t is placed in the context's mapped
- * pinned staging, which the graph's first kernel reads (and stores, with
- * its float copy, as row t), and its last kernel writes the record and the
- * error word there.  Otherwise the copies are stream copies. */
+ * iteration and copies its record to *h_record.  Returns once the step is
+ * done, with the device error word of the step.  SMC_E_ARG past the last
+ * observation (or the GMM schedule).  On a non-default stream (and without
+ * SMC_FLAG_RECORD) the step is one graph launch: obs_t is placed in the
+ * context's mapped pinned staging, which the graph's first kernel reads
+ * (and stores, with its float copy, as row t); the record and the error
+ * word are written there, and the graph's last kernel then writes the
+ * call's sequence number, on which the call waits (spinning on the host,
+ * up to a second, then synchronising the stream) instead of synchronising:
+ * every kernel of the step has completed when it returns, but a CUDA fault
+ * of the step surfaces only at the next call that synchronises.  Otherwise
+ * the copies are stream copies and the call synchronises. */
 int smc_iterate_host(smc_ctx *ctx, const double *h_obs_t, smc_record *h_record);
 
 /* WeightSet::add_log_weight (Sec. 4.1.6): multiply the current weights by

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <cstring>
 #include <new>
@@ -61,7 +62,7 @@ int ceil_log2(int64_t n) {
 struct Layout {
     size_t st, rec, part, x, lw, anc, Q, tsum, bsum, inc, obs, obs_f, alpha;
     size_t dhist, drec, dtot;  // multinomial / residual draw histogram, bucket records, tile totals
-    size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, inpl, adapt, total;
+    size_t hist, ckpt, seg, gbar, xbar, at, rep, rep_part, scal, inpl, adapt, done, total;
     int ck;           // steps between checkpoints (record mode)
     int64_t nck;      // checkpoints
     int d;            // state rows
@@ -161,6 +162,7 @@ Layout make_layout(const smc_config *c) {
     L.adapt = take((c->model == SMC_MODEL_GMM && c->gmm.schedule == SMC_ALPHA_ADAPTIVE)
                        ? 2 * (size_t)kAdaptCand * kMaxCoopGrid * sizeof(AlphaPartial<double>)
                        : 0);
+    L.done = take(sizeof(uint32_t));  // smc_iterate_host's sequence counter
     L.total = off;
     return L;
 }
@@ -209,6 +211,8 @@ struct smc_ctx {
     int64_t shard_off;      // and the global index of the shard's first particle
     void *shard_out;        // while launching a mixture shard's kernel: where its partial goes
     int shard_pending;      // the mixture shard's partial awaiting smc_shard_finalize: 0 init, 1 reweight
+    uint32_t *done_seq = nullptr;  // smc_iterate_host's device counter (the workspace's last word)
+    uint32_t done_want = 0;        // and the host's count of its launches
 };
 
 namespace {
@@ -261,6 +265,17 @@ __global__ void wait_selftest_kernel(DevState *st) {
 // (and its float copy, rounded as on the host).  The move kernel, its
 // programmatic dependent, starts at once and waits for this grid only
 // before it reads y_t.
+// smc_iterate_host, last node of its graph: the call's sequence number
+// (a device counter, advanced here) into the mapped staging, after every
+// earlier kernel of the call has completed; the host waits on it instead of
+// synchronising the stream
+__global__ void host_done_kernel(HostIO *io, uint32_t *seq) {
+    const uint32_t v = *seq + 1u;
+    *seq = v;
+    __threadfence_system();
+    reinterpret_cast<volatile HostIO *>(io)->done = v;
+}
+
 __global__ void host_obs_kernel(const HostIO *io, const DevState *st, double *obs, float *obs_f) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (threadIdx.x != 0 || st->error) return;
@@ -735,14 +750,17 @@ int launch_iteration_io(smc_ctx *c, bool host_io) {
     if (c->cfg.model == SMC_MODEL_GMM) {
         if (int rc = launch_iteration(c)) return rc;
         host_rec_kernel<<<1, 32, 0, c->stream>>>(c->hio_d, c->st, c->rec, c->cfg.max_records);
-        return cuda_check(cudaGetLastError());
+    } else {
+        host_obs_kernel<<<1, 32, 0, c->stream>>>(c->hio_d, c->st, c->obs, c->obs_f);
+        if (int rc = cuda_check(cudaGetLastError())) return rc;
+        c->capture_host_io = 1;
+        const int rc = launch_iteration(c);
+        c->capture_host_io = 0;
+        if (rc) return rc;
     }
-    host_obs_kernel<<<1, 32, 0, c->stream>>>(c->hio_d, c->st, c->obs, c->obs_f);
     if (int rc = cuda_check(cudaGetLastError())) return rc;
-    c->capture_host_io = 1;
-    const int rc = launch_iteration(c);
-    c->capture_host_io = 0;
-    return rc;
+    host_done_kernel<<<1, 1, 0, c->stream>>>(c->hio_d, c->done_seq);
+    return cuda_check(cudaGetLastError());
 }
 
 void drop_graphs(smc_ctx *c) {
@@ -862,6 +880,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     c->obs = reinterpret_cast<double *>(c->ws + L.obs);
     c->obs_f = reinterpret_cast<float *>(c->ws + L.obs_f);
     c->alpha = reinterpret_cast<double *>(c->ws + L.alpha);
+    c->done_seq = reinterpret_cast<uint32_t *>(c->ws + L.done);
     c->n_obs = 0;
     c->t_host = -1;
     c->initialized = 0;
@@ -875,6 +894,7 @@ int smc_create(smc_ctx **out, const smc_config *cfg, void *d_workspace, size_t b
     // zero the state block, records, scan status words and block sums
     int rc = cuda_check(cudaMemsetAsync(c->ws, 0, L.part, c->stream));
     if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + L.tsum, 0, L.inc - L.tsum, c->stream));
+    if (!rc) rc = cuda_check(cudaMemsetAsync(c->done_seq, 0, sizeof(uint32_t), c->stream));
     if (!rc) {
         reset_state_kernel<<<1, 1, 0, c->stream>>>(c->st);
         rc = cuda_check(cudaGetLastError());
@@ -1030,7 +1050,16 @@ int smc_iterate_host(smc_ctx *c, const double *h_obs_t, smc_record *h_record) {
             c->hio->obs[1] = h_obs_t[1];
         }
         if (cudaGraphLaunch(c->graph_host, c->stream) != cudaSuccess) return SMC_E_CUDA;
-        if ((rc = cuda_check(cudaStreamSynchronize(c->stream)))) return rc;
+        // the graph's last kernel writes the call's sequence number once the
+        // record and the error word are in the staging: wait for it (a
+        // second bounded by the clock, then a synchronise, which also
+        // surfaces a fault)
+        const uint32_t want = ++c->done_want;
+        const volatile uint32_t *done = &c->hio->done;
+        const auto t0 = std::chrono::steady_clock::now();
+        for (uint32_t spin = 1; *done != want; ++spin)
+            if (!(spin & 0xFFFFu) && std::chrono::steady_clock::now() - t0 > std::chrono::seconds(1)) break;
+        if (*done != want && (rc = cuda_check(cudaStreamSynchronize(c->stream)))) return rc;
         if (with_obs && c->n_obs < t + 1) c->n_obs = t + 1;
         c->t_host = t;
         std::memcpy(h_record, &c->hio->rec, sizeof(smc_record));

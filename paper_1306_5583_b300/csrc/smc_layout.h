@@ -84,6 +84,8 @@ struct HostIO {
     int32_t has_obs;   // 1: obs holds the next observation
     int32_t status;    // the device error word after the step
     smc_record rec;    // the step's record
+    uint32_t done;     // the call's sequence number, written by the call's last kernel
+    uint32_t pad;
 };
 
 struct Partial {  // one per block of a weighting kernel
