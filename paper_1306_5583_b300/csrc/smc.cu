@@ -260,11 +260,6 @@ __global__ void wait_selftest_kernel(DevState *st) {
     }
 }
 
-// smc_iterate_host on a particle filter, first node of its graph: the
-// observation of iteration t + 1 from the mapped staging into the workspace
-// (and its float copy, rounded as on the host).  The move kernel, its
-// programmatic dependent, starts at once and waits for this grid only
-// before it reads y_t.
 // smc_iterate_host, last node of its graph: the call's sequence number
 // (a device counter, advanced here) into the mapped staging, after every
 // earlier kernel of the call has completed; the host waits on it instead of
@@ -276,6 +271,11 @@ __global__ void host_done_kernel(HostIO *io, uint32_t *seq) {
     reinterpret_cast<volatile HostIO *>(io)->done = v;
 }
 
+// smc_iterate_host on a particle filter, first node of its graph: the
+// observation of iteration t + 1 from the mapped staging into the workspace
+// (and its float copy, rounded as on the host).  The move kernel, its
+// programmatic dependent, starts at once and waits for this grid only
+// before it reads y_t.
 __global__ void host_obs_kernel(const HostIO *io, const DevState *st, double *obs, float *obs_f) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (threadIdx.x != 0 || st->error) return;
