@@ -8,10 +8,11 @@
  *   one iteration = move queue, ESS test and resampling, mcmc queue,
  *   monitors (Sec. 4.1.3)                  -> smc_move, smc_resample, smc_mcmc
  *   Sampler::iterate(n)                    -> smc_iterate
- *   (a plan that names smc_weight and smc_run: the weight update, normaliser
- *   and ESS test of a particle filter are part of smc_move -- vSMC's move
- *   queue -- and smc_run is smc_iterate; for the GMM sampler smc_move is the
- *   reweighting at alpha_t and smc_mcmc the Metropolis / Langevin moves)
+ *   (there is no separate smc_weight or smc_run: the weight update,
+ *   normaliser and ESS test of a particle filter are part of smc_move --
+ *   vSMC's move queue -- and a run of iterations is smc_iterate; for the GMM
+ *   sampler smc_move is the reweighting at alpha_t and smc_mcmc the
+ *   Metropolis / Langevin moves)
  *   WeightSet::add_log_weight (Sec. 4.1.6) -> smc_add_log_weight
  *   NormalizingConstant / Path estimates   -> smc_log_evidence, smc_path_sampling
  *   read_weight / read_log_weight          -> smc_read_log_weight
