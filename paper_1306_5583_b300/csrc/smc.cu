@@ -203,10 +203,10 @@ struct smc_ctx {
     int capture_host_io;    // while capturing graph_host: the kernels get the staging's addresses
     cudaEvent_t ev_move[2]; // profiling: recorded around the move kernel in the iteration graph
     int dependent_launch;   // while capturing: launch the one-pass resampler as a programmatic dependent
-    int no_dependent;       // the driver refused the programmatic dependent launch once: capture without
+    int no_dependent;       // the CUDA driver refused the programmatic dependent launch once: capture without
     int chain_move;         // while capturing a later iteration of a chain: the move kernel is a
                             // programmatic dependent of the previous iteration's last kernel
-    int no_chain;           // the driver refused that once: chains capture ordinary edges
+    int no_chain;           // the CUDA driver refused that once: chains capture ordinary edges
     int64_t shard_n;        // a shard of a partitioned filter: the filter's N (0: not a shard)
     int64_t shard_off;      // and the global index of the shard's first particle
     void *shard_out;        // while launching a mixture shard's kernel: where its partial goes
@@ -800,7 +800,7 @@ int build_graph_once(smc_ctx *c, cudaGraphExec_t *dst, bool host_io, int iterati
 
 // One iteration captured as a graph (host_io: the graph of smc_iterate_host).
 // The one-pass resampler is captured as a programmatic dependent of the move
-// kernel where the driver accepts that for a cooperative launch; otherwise
+// kernel where the CUDA driver accepts that for a cooperative launch; otherwise
 // (one refusal) as an ordinary node.
 int build_graph(smc_ctx *c, bool host_io = false) {
     cudaGraphExec_t *dst = host_io ? &c->graph_host : &c->graph;
