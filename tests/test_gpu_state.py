@@ -297,3 +297,37 @@ def test_bounded_wait_gives_up_and_the_context_recovers():
     ref.iterate(T - 1 - 3)
     assert np.array_equal(s.state(), ref.state())
     assert s.log_evidence() == ref.log_evidence()
+
+
+@pytest.mark.parametrize("move", ["rw", "mala"])
+def test_iterate_host_mixture_sampler(move):
+    """smc_iterate_host on the mixture sampler (its graph ends with the
+    record kernel and the completion word): every record equals the one
+    smc_iterate writes, bit for bit, and so does the final particle
+    system."""
+    need_gpu()
+    n, T, nd = 4096, 12, 200
+    y = workloads.gmm_data(nd, seed=0)
+    mv = {"rw": smc.GMM_RW, "mala": smc.GMM_MALA}[move]
+
+    def sampler():
+        cfg = smc.make_config(model="gmm", n=n, precision=32, scheme="systematic", threshold=0.5, seed=4,
+                              max_data=nd, max_records=T + 1,
+                              gmm=dict(n_comp=3, n_iter=T, power=5.0, move=mv, mala_step=0.05))
+        s = smc.Sampler(cfg, stream=torch.cuda.Stream())
+        s.set_data(y)
+        s.initialize()
+        return s
+
+    a, b = sampler(), sampler()
+    a.iterate(T)
+    ha = a.history(T + 1)
+    hb = [b.iterate_host(None).as_dict() for _ in range(T)]
+    for ra, rb in zip(ha[1:], hb):
+        assert {k: _bits(v) for k, v in ra.items()} == {k: _bits(v) for k, v in rb.items()}
+    assert np.array_equal(a.state(), b.state())
+    with pytest.raises(smc.SMCError) as e:
+        b.iterate_host(None)  # past the schedule
+    assert e.value.code == smc.E_ARG
+    a.close()
+    b.close()
