@@ -37,10 +37,12 @@ def _shards(n, world, T, precision, scheme, threshold, seed, y):
     return out
 
 
-@pytest.mark.parametrize("precision", [32, 64])
-@pytest.mark.parametrize("scheme", ["systematic", "stratified"])
-@pytest.mark.parametrize("n,world", [(5000, 2), (70001, 3)])
+@pytest.mark.parametrize("precision,scheme,n,world",
+                         [(p, sc, n, w) for p in (32, 64) for sc in ("systematic", "stratified")
+                          for n, w in ((5000, 2), (70001, 3))] + [(32, "systematic", (1 << 20) + 5, 2)])
 def test_shards_equal_one_context_when_every_step_resamples(precision, scheme, n, world):
+    """Shards in one process against one context; the last case is the
+    benchmarked size (two shards of about 2^19 particles, ragged)."""
     need_gpu()
     T, seed = 8, 5
     _, y = workloads.cv_data(T, seed=1, **workloads.CV_DEFAULT)
