@@ -162,3 +162,43 @@ def test_batch_split_over_ranks_equals_one_batch():
                                       [3 + b for b in mine])
         got[mine] = vals
     assert np.array_equal(got, np.asarray(ref, dtype=np.float64))
+
+
+def test_benchmarked_batch_equals_plain_runs():
+    """The benchmarked batch: 256 filters, N log-uniform in [2^10, 2^18],
+    T uniform in [50, 2000], FP32, systematic at ESS < N/2, launch shape
+    from the autotuner.  Every filter's log-evidence equals its plain run's
+    bit for bit; the records and final particles of the four smallest and
+    four largest filters too."""
+    need_gpu()
+    ns, ts = workloads.batch_shapes(256, seed=0)
+    p = dict(workloads.CV_DEFAULT)
+    data = [workloads.cv_data(int(T), seed=1 + b, **p)[1] for b, T in enumerate(ts)]
+    cfg = smc.make_config(model="cv", n=1, precision=32, scheme="systematic", threshold=0.5, seed=3,
+                          max_data=int(ts.max()), keep_cdf=False, cv=p)
+    bt = smc.Batch(cfg, ns, ts)
+    for b in range(len(ns)):
+        bt.set_data(b, data[b])
+    bt.tune()
+    bt.initialize()
+    bt.run()
+    lz = bt.log_evidence()
+    order = np.argsort(ns)
+    full = set(order[:4].tolist()) | set(order[-4:].tolist())
+    for b in range(len(ns)):
+        n, T = int(ns[b]), int(ts[b])
+        pc = smc.make_config(model="cv", n=n, precision=32, scheme="systematic", threshold=0.5, seed=3,
+                             stream_id=b, max_data=T, keep_cdf=False, cv=p)
+        s = smc.Sampler(pc)
+        s.set_data(data[b])
+        s.initialize()
+        if T > 1:
+            s.iterate(T - 1)
+        assert lz[b] == s.log_evidence(), (b, n, T)
+        if b in full:
+            hp, hb = s.history(T), bt.history(b, T)
+            assert [(r["t"], r["resampled"], r["L"], r["ess"]) for r in hp] == \
+                   [(r["t"], r["resampled"], r["L"], r["ess"]) for r in hb], b
+            assert np.array_equal(s.state(), bt.state(b)), b
+        s.close()
+    bt.close()
