@@ -38,12 +38,13 @@ def test_philox_matches_oracle_and_curand():
     assert np.array_equal(do.cpu().numpy().view(np.uint32), ref)
 
 
-@pytest.mark.parametrize("scheme", SCHEMES)
-def test_fp64_filter_end_to_end(scheme):
-    """FP64, N = 1000 (the paper's example size), T = 40: records, ancestors
-    and the final particle system match the free-running oracle."""
+@pytest.mark.parametrize("scheme,T,seed", [(sc, 40, 3) for sc in SCHEMES] + [("systematic", 100, 0)])
+def test_fp64_filter_end_to_end(scheme, T, seed):
+    """FP64, N = 1000 (the paper's example size): records, ancestors and the
+    final particle system match the free-running oracle; the last case is
+    the benchmarked run (T = 100, Philox key 0, data seed 0)."""
     need_gpu()
-    n, T, seed = 1000, 40, 3
+    n = 1000
     s, y, op = make_pf(n, T, 64, scheme=scheme, seed=seed)
     s.initialize()
     s.iterate(T - 1)
